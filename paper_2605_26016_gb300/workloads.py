@@ -1,0 +1,69 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only describes inputs: lattice cells, sublattice positions, moments,
+coupling constants and seeded random spin fields.  It holds none of the
+method's arithmetic, so both the CUDA path and the CPU oracle may use it.
+
+Workloads (all synthetic; the paper's benchmark lattices are synthetic too):
+
+* ``sc_nn``      simple cubic, nearest-neighbour exchange J = 1 meV, B = 1 T along z,
+                 mu = 1 mu_B, alpha = 0.1, periodic, deterministic Heun, dt = 0.1 fs.
+* ``bcc_4shell`` bcc as two sublattices of the conventional cell, exchange on
+                 four distance shells J = 20, 10, -1, 0.5 meV, mu = 2.2 mu_B,
+                 uniaxial K = 0.005 meV along z, T = 300 K, alpha = 0.05, dt = 0.1 fs.
+* ``sc_j123``    simple cubic, J1 = 1, J2 = -0.164, J3 = -0.082 meV on distance
+                 shells, periodic in x, y and open in z, mu = 1 mu_B.
+* ``sc_j123_dmi`` simple cubic, J1..J3 as above plus interfacial DMI D = 0.1 meV
+                 on the first shell, mu = 2.2 mu_B, alpha = 0.1, T = 50 K, periodic.
+
+Spins are float64 arrays of shape (3, nsub, nz, ny, nx): three component planes,
+sublattice-major, x fastest.  Random spins are uniform on the sphere:
+z = 2u - 1, phi = 2 pi v with u, v from numpy's PCG64 seeded generator.
+"""
+import numpy as np
+
+# lattice constant of the cubic cell in nm (bcc Fe); it only enters the dipolar term
+A_NM = 0.287
+
+SC_POS = [[0.0, 0.0, 0.0]]
+BCC_POS = [[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]]
+
+
+def cubic_cell(a=A_NM):
+    return (np.eye(3) * a).tolist()
+
+
+WORKLOADS = {
+    "sc_nn": dict(pos=SC_POS, mu=[1.0], shells=[1.0], dmi=None, B=[0.0, 0.0, 1.0], K=None,
+                  alpha=0.1, T=0.0, dt=0.1, pbc=(1, 1, 1), seed=1),
+    "bcc_4shell": dict(pos=BCC_POS, mu=[2.2, 2.2], shells=[20.0, 10.0, -1.0, 0.5], dmi=None, B=[0.0, 0.0, 0.0],
+                       K=(0.005, [0.0, 0.0, 1.0]), alpha=0.05, T=300.0, dt=0.1, pbc=(1, 1, 1), seed=2),
+    "sc_j123": dict(pos=SC_POS, mu=[1.0], shells=[1.0, -0.164, -0.082], dmi=None, B=[0.0, 0.0, 0.0], K=None,
+                    alpha=0.1, T=0.0, dt=0.1, pbc=(1, 1, 0), seed=3),
+    "sc_j123_dmi": dict(pos=SC_POS, mu=[2.2], shells=[1.0, -0.164, -0.082], dmi=(1, 0, 0.1), B=[0.0, 0.0, 0.0],
+                        K=None, alpha=0.1, T=50.0, dt=0.1, pbc=(1, 1, 1), seed=5),
+}
+
+
+def random_spins(nsub, n, seed):
+    """Uniform random unit spins, shape (3, nsub, nz, ny, nx), float64."""
+    nx, ny, nz = n
+    rng = np.random.default_rng(seed)
+    m = nsub * nx * ny * nz
+    u = rng.random(m)
+    v = rng.random(m)
+    z = 2.0 * u - 1.0
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = 2.0 * np.pi * v
+    S = np.stack([r * np.cos(phi), r * np.sin(phi), z]).reshape(3, nsub, nz, ny, nx)
+    return np.ascontiguousarray(S)
+
+
+def uniform_spins(nsub, n, direction):
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.sqrt((d * d).sum())
+    nx, ny, nz = n
+    S = np.empty((3, nsub, nz, ny, nx))
+    for c in range(3):
+        S[c] = d[c]
+    return S

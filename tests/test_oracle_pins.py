@@ -1,0 +1,342 @@
+"""Pins of the CPU oracle against results fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: textbook
+coordination numbers, closed-form lattice sums for ferromagnets, spirals,
+cycloids and helices, the derivative relation b = -dE/dS, the analytic
+single-spin LLG solution, the invariants of undamped dynamics, the Langevin
+function of a thermal spin, and the statistics of the normal noise.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle_models import oracle_model
+from paper_2605_26016_gb300.workloads import A_NM, BCC_POS, SC_POS, cubic_cell, random_spins, uniform_spins
+
+C = oracle.constants()
+MU_B, GAMMA, K_B = C["mu_B"], C["gamma"], C["k_B"]
+
+
+def test_paper_constants_golden():
+    # tests/golden/paper_constants.txt: the paper rounds mu_B to 5.7884e-2 meV/T
+    vals = {}
+    with open(__file__.replace("test_oracle_pins.py", "golden/paper_constants.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split()
+                vals[k] = float(v)
+    assert abs(MU_B - vals["mu_B_meV_per_T"]) < 0.5e-6
+    assert vals["hopfion_J2_over_J1"] == 0.188
+
+
+def _coordination(pos, shell, n=(9, 9, 9)):
+    m = oracle.Model(n, (1, 1, 1), cubic_cell(1.0), pos, [1.0] * len(pos))
+    m.add_shell_exchange(shell, 1.0)
+    m.build()
+    counts = set()
+    for s in range(len(pos)):
+        jj, JJ = m.site_pairs(s * n[0] * n[1] * n[2] + 40)
+        counts.add(len(jj))
+        assert np.allclose(JJ, np.eye(3)[None])
+    assert len(counts) == 1
+    return counts.pop(), m.shell_radii(shell)[-1]
+
+
+@pytest.mark.parametrize("shell,count,radius", [(1, 6, 1.0), (2, 12, math.sqrt(2)), (3, 8, math.sqrt(3)),
+                                                (4, 6, 2.0)])
+def test_sc_shells(shell, count, radius):
+    c, r = _coordination(SC_POS, shell)
+    assert c == count and abs(r - radius) < 1e-12
+
+
+@pytest.mark.parametrize("shell,count,radius", [(1, 8, math.sqrt(3) / 2), (2, 6, 1.0), (3, 12, math.sqrt(2)),
+                                                (4, 24, math.sqrt(11) / 2)])
+def test_bcc_shells(shell, count, radius):
+    c, r = _coordination(BCC_POS, shell)
+    assert c == count and abs(r - radius) < 1e-12
+
+
+def test_open_boundary_drops_bonds():
+    m = oracle.Model((4, 4, 4), (1, 1, 0), cubic_cell(), SC_POS, [1.0])
+    m.add_shell_exchange(1, 1.0)
+    m.build()
+    assert len(m.site_pairs(0)[0]) == 5            # z = 0 face
+    assert len(m.site_pairs(16)[0]) == 6           # z = 1 interior
+    assert len(m.site_pairs(3 * 16 + 5)[0]) == 5   # z = 3 face
+    assert m.npair() == 64 * 6 - 2 * 16
+
+
+def test_bond_reverse_is_transpose():
+    # an unordered bond between sublattices expands into two directed bonds,
+    # the reverse one carrying the transposed tensor (J_ji^{ba} = J_ij^{ab})
+    rng = np.random.default_rng(7)
+    J = rng.normal(size=(3, 3))
+    m = oracle.Model((5, 5, 5), (1, 1, 1), cubic_cell(), BCC_POS, [1.0, 1.0])
+    m.add_bond(0, 1, (1, 0, -1), J)
+    m.build()
+    n3 = 125
+    i = 2 * 25 + 2 * 5 + 2          # sublattice 0, cell (2,2,2)
+    jj, JJ = m.site_pairs(i)
+    assert len(jj) == 1 and jj[0] == n3 + 1 * 25 + 2 * 5 + 3 and np.array_equal(JJ[0], J)
+    jb, Jb = m.site_pairs(n3 + 1 * 25 + 2 * 5 + 3)  # sublattice 1, cell (3,2,1) -> back to (2,2,2)
+    assert len(jb) == 1 and jb[0] == i and np.array_equal(Jb[0], J.T)
+
+
+def test_ferromagnet_closed_form():
+    # uniform state: b = (sum_k z_k J_k) S + mu mu_B B + 2 K (S.n) n, per-site energy
+    # -1/2 sum z_k J_k - mu mu_B B.S - K (S.n)^2 (bcc coordination 8, 6, 12, 24)
+    n = (6, 6, 6)
+    m, w = oracle_model("bcc_4shell", n, B=[0.3, -0.2, 1.5])
+    d = np.array([0.3, -0.5, 0.8])
+    d /= np.linalg.norm(d)
+    S = uniform_spins(2, n, d)
+    Jsum = sum(z * J for z, J in zip((8, 6, 12, 24), w["shells"]))
+    K = w["K"][0]
+    mu = w["mu"][0]
+    expect = Jsum * d + mu * MU_B * np.array(w["B"]) + 2 * K * d[2] * np.array([0, 0, 1.0])
+    b = m.field(S)
+    assert np.abs(b - expect[:, None, None, None, None]).max() < 1e-12
+    e = m.energy(S) / (2 * 216)
+    e_expect = -0.5 * Jsum - mu * MU_B * np.dot(w["B"], d) - K * d[2] ** 2
+    assert abs(e - e_expect) < 1e-12
+
+
+def _spiral(pos, n, q):
+    nx, ny, nz = n
+    S = np.empty((3, len(pos), nz, ny, nx))
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    for s, p in enumerate(pos):
+        ph = q[0] * (x + p[0]) + q[1] * (y + p[1]) + q[2] * (z + p[2])
+        S[0, s], S[1, s], S[2, s] = np.cos(ph), np.sin(ph), 0.0
+    return S
+
+
+def test_sc_spiral_closed_form():
+    # flat spiral S = (cos q.r, sin q.r, 0): b = J(q) S with the simple-cubic lattice sums
+    n = (12, 8, 6)
+    J = [1.0, -0.3, 0.25, 0.1]
+    m = oracle.Model(n, (1, 1, 1), cubic_cell(), SC_POS, [1.0])
+    for k, Jk in enumerate(J):
+        m.add_shell_exchange(k + 1, Jk)
+    m.build()
+    q = 2 * np.pi * np.array([1 / 12, 2 / 8, 1 / 6])
+    cx, cy, cz = np.cos(q)
+    Jq = (2 * J[0] * (cx + cy + cz) + 4 * J[1] * (cx * cy + cy * cz + cz * cx) + 8 * J[2] * cx * cy * cz
+          + 2 * J[3] * (np.cos(2 * q[0]) + np.cos(2 * q[1]) + np.cos(2 * q[2])))
+    S = _spiral(SC_POS, n, q)
+    assert np.abs(m.field(S) - Jq * S).max() < 1e-12
+
+
+def test_bcc_spiral_closed_form():
+    n = (8, 8, 8)
+    m, w = oracle_model("bcc_4shell", n, K=None)
+    J = w["shells"]
+    q = 2 * np.pi * np.array([1 / 8, 3 / 8, 2 / 8])
+    c = np.cos(q)
+    h = np.cos(q / 2)
+    t = np.cos(3 * q / 2)
+    Jq = (8 * J[0] * h[0] * h[1] * h[2] + 2 * J[1] * c.sum() + 4 * J[2] * (c[0] * c[1] + c[1] * c[2] + c[2] * c[0])
+          + 8 * J[3] * (t[0] * h[1] * h[2] + h[0] * t[1] * h[2] + h[0] * h[1] * t[2]))
+    S = _spiral(BCC_POS, n, q)
+    assert np.abs(m.field(S) - Jq * S).max() < 1e-11
+
+
+def test_interfacial_dmi_cycloid():
+    # cycloid S = (sin qx, 0, cos qx) with interfacial D_ij = D (z x r_ij): b = (J(q) + 2 D sin q) S,
+    # per-site energy -1/2 (J(q) + 2 D sin q) (pair energy -J S_i.S_j - D_ij.(S_i x S_j))
+    n = (16, 4, 4)
+    J1, D = 1.3, 0.4
+    m = oracle.Model(n, (1, 1, 1), cubic_cell(), SC_POS, [1.0])
+    m.add_shell_exchange(1, J1)
+    m.add_dmi(1, 0, D)
+    m.build()
+    q = 2 * np.pi * 3 / 16
+    x = np.arange(16)[None, None, :] * np.ones((4, 4, 1))
+    S = np.stack([np.sin(q * x), np.zeros_like(x), np.cos(q * x)])[:, None]
+    lam = 2 * J1 * (np.cos(q) + 2) + 2 * D * np.sin(q)
+    assert np.abs(m.field(S) - lam * S).max() < 1e-12
+    assert abs(m.energy(S) / 256 + 0.5 * lam) < 1e-12
+
+
+def test_bulk_dmi_helix():
+    # helix S = (cos qz, sin qz, 0) with bulk D_ij = D r_ij: b = (J(q) + 2 D sin q) S
+    n = (4, 4, 16)
+    J1, D = 0.7, -0.25
+    m = oracle.Model(n, (1, 1, 1), cubic_cell(), SC_POS, [1.0])
+    m.add_shell_exchange(1, J1)
+    m.add_dmi(1, 1, D)
+    m.build()
+    q = 2 * np.pi * 5 / 16
+    z = np.arange(16)[:, None, None] * np.ones((1, 4, 4))
+    S = np.stack([np.cos(q * z), np.sin(q * z), np.zeros_like(z)])[:, None]
+    lam = 2 * J1 * (np.cos(q) + 2) + 2 * D * np.sin(q)
+    assert np.abs(m.field(S) - lam * S).max() < 1e-12
+
+
+def test_field_is_minus_energy_gradient():
+    # b_i = -dH/dS_i for every term (bilinear incl. a general non-symmetric tensor bond, DMI,
+    # Zeeman, anisotropy), checked by central differences on a small open/periodic lattice
+    n = (4, 5, 3)
+    rng = np.random.default_rng(11)
+    m, w = oracle_model("bcc_4shell", n, pbc=(1, 1, 0), B=[0.4, -1.0, 2.0], build=False)
+    m.add_dmi(2, 1, 0.7)
+    m.add_dmi(1, 1, -0.3)
+    m.add_bond(0, 1, (0, -1, 1), rng.normal(size=(3, 3)))
+    m.add_bond(1, 1, (1, 0, 0), rng.normal(size=(3, 3)))
+    m.set_anisotropy(1, -0.8, [1.0, 1.0, 0.0])
+    m.build()
+    S = random_spins(2, n, 5)
+    b = m.field(S)
+    h = 1e-5
+    for flat in rng.choice(S.size, 40, replace=False):
+        Sp = S.copy().reshape(-1)
+        Sm = S.copy().reshape(-1)
+        Sp[flat] += h
+        Sm[flat] -= h
+        g = (m.energy(Sp) - m.energy(Sm)) / (2 * h)
+        assert abs(-g - b.reshape(-1)[flat]) < 1e-6 * max(1.0, abs(g))
+
+
+def _single_spin(B0, mu=1.0):
+    m = oracle.Model((1, 1, 1), (0, 0, 0), cubic_cell(), SC_POS, [mu])
+    m.set_zeeman([0.0, 0.0, B0])
+    m.build()
+    return m
+
+
+def _larmor_rmse(dt, alpha=0.1, B0=10.0, t_end=100000.0, sample=1000.0):
+    m = _single_spin(B0)
+    th0 = math.pi / 3
+    S = np.array([math.sin(th0), 0.0, math.cos(th0)]).reshape(3, 1, 1, 1, 1)
+    gp = GAMMA / (1 + alpha * alpha)
+    err2 = []
+    per = int(round(sample / dt))
+    for k in range(1, int(t_end / sample) + 1):
+        S = m.heun(S, dt, alpha, nsteps=per)
+        t = k * sample
+        ph = gp * B0 * t
+        th = 2 * math.atan(math.tan(th0 / 2) * math.exp(-alpha * gp * B0 * t))
+        ex = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+        err2.append(((S.reshape(3) - ex) ** 2).sum())
+    return math.sqrt(np.mean(err2))
+
+
+def test_larmor_precession_second_order():
+    # single spin in B || z: phi = gamma' B t, tan(theta/2) = tan(theta0/2) exp(-alpha gamma' B t);
+    # the Heun trajectory error falls as dt^2 (the fp64 curve of the single-spin benchmark)
+    r = [_larmor_rmse(dt) for dt in (2.0, 4.0, 8.0)]
+    assert r[0] < 1e-3
+    for a, b in zip(r, r[1:]):
+        assert 3.4 < b / a < 4.6
+
+
+def test_undamped_invariants():
+    # alpha = 0, T = 0: |S| = 1 to rounding, energy conserved up to O(dt^2)
+    n = (6, 6, 6)
+    m, w = oracle_model("sc_j123", n, pbc=(1, 1, 1), B=[0.0, 0.0, 3.0])
+    S0 = random_spins(1, n, 21)
+    E0 = m.energy(S0)
+    drifts = []
+    # random spins are strongly chaotic: the dt^2 regime starts below ~0.5 fs
+    for dt, steps in ((0.25, 1600), (0.125, 3200)):
+        S = m.heun(S0, dt, 0.0, nsteps=steps)
+        assert np.abs(np.sqrt((S ** 2).sum(0)) - 1).max() < 1e-14
+        drifts.append(abs(m.energy(S) - E0))
+    assert drifts[0] < 1e-4 * abs(E0)
+    assert 3.0 < drifts[0] / drifts[1] < 5.0
+
+
+def test_isotropic_exchange_conserves_total_spin():
+    n = (6, 6, 6)
+    m, w = oracle_model("sc_j123", n, pbc=(1, 1, 1))
+    S0 = random_spins(1, n, 22)
+    M0 = S0.reshape(3, -1).sum(1)
+    d = []
+    for dt, steps in ((1.0, 200), (0.5, 400)):
+        S = m.heun(S0, dt, 0.0, nsteps=steps)
+        d.append(np.abs(S.reshape(3, -1).sum(1) - M0).max())
+    # the Heun error of the total spin is at least second order (here it is third)
+    assert d[0] < 1e-4 * 216
+    assert d[0] / d[1] > 3.5
+
+
+def _langevin(x):
+    return 1.0 / math.tanh(x) - 1.0 / x
+
+
+@pytest.mark.slow
+def test_thermal_spin_langevin_function():
+    # independent spins in B at temperature T: <S_z> -> L(mu mu_B B / kB T) (Langevin function),
+    # which pins the thermal-field amplitude sigma = sqrt(2 alpha kB T / (gamma mu mu_B dt))
+    n = (16, 16, 16)
+    B0, alpha, dt = 5.0, 1.0, 1.0
+    x = 1.0
+    T = MU_B * B0 / (K_B * x)
+    m = oracle.Model(n, (1, 1, 1), cubic_cell(), SC_POS, [1.0])
+    m.set_zeeman([0.0, 0.0, B0])
+    m.build()
+    S = uniform_spins(1, n, [0, 0, 1])
+    S = m.heun(S, dt, alpha, T=T, seed=99, step0=0, nsteps=7000)
+    acc = []
+    step = 7000
+    for _ in range(40):
+        S = m.heun(S, dt, alpha, T=T, seed=99, step0=step, nsteps=500)
+        step += 500
+        acc.append(S[2].mean())
+    assert abs(np.mean(acc) - _langevin(x)) < 0.015
+
+
+def test_normal_noise_statistics():
+    from scipy import stats
+    eta = oracle.normals(12345, 3, 1000, 100000, 17).astype(np.float64)
+    N = eta.size
+    assert abs(eta.mean()) < 5 / math.sqrt(N)
+    assert abs(eta.var() - 1) < 5 * math.sqrt(2 / N)
+    assert abs(stats.kurtosis(eta.reshape(-1), fisher=False) - 3) < 5 * math.sqrt(24 / N)
+    for c in range(3):
+        assert stats.kstest(eta[:, c], "norm").pvalue > 1e-3
+    cc = np.corrcoef(eta.T)
+    assert np.abs(cc - np.eye(3)).max() < 5 / math.sqrt(eta.shape[0])
+
+
+def test_noise_is_counter_based():
+    a = oracle.normals(7, 0, 50, 10, 3)
+    b = oracle.normals(7, 0, 55, 5, 3)
+    assert np.array_equal(a[5:], b)
+    assert not np.array_equal(oracle.normals(7, 0, 50, 10, 4), a)
+    assert not np.array_equal(oracle.normals(8, 0, 50, 10, 3), a)
+    assert not np.array_equal(oracle.normals(7, 1, 50, 10, 3), a)
+
+
+def test_philox_words_uniform():
+    from scipy import stats
+    words = np.array([oracle.philox4x32_10((i, 0, 5, 0), (1, 2)) for i in range(20000)], dtype=np.float64)
+    u = (words + 0.5) / 2.0 ** 32
+    for c in range(4):
+        assert stats.kstest(u[:, c], "uniform").pvalue > 1e-3
+    bits = np.unpackbits(np.array(words, dtype=np.uint32).view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 5 * 0.5 / math.sqrt(bits.size)
+
+
+def test_stochastic_step_uses_same_noise_in_both_stages():
+    # with J = 0 one stochastic Heun step of a single spin equals the deterministic Heun step in the
+    # constant field B_ext + sigma*eta (eta from the site/step counter), which is only true if the
+    # predictor and corrector share eta
+    n = (2, 1, 1)
+    m = oracle.Model(n, (1, 1, 1), cubic_cell(), SC_POS, [2.0])
+    m.set_zeeman([0.1, 0.2, 1.0])
+    m.build()
+    S0 = random_spins(1, n, 3)
+    dt, alpha, T = 0.5, 0.3, 80.0
+    S1 = m.heun(S0, dt, alpha, T=T, seed=42, step0=9, nsteps=1)
+    eta = oracle.normals(42, 0, 0, 2, 9).astype(np.float64)
+    sigma = math.sqrt(2 * alpha * K_B * T / (GAMMA * 2.0 * MU_B * dt))
+    for i in range(2):
+        mi = oracle.Model((1, 1, 1), (0, 0, 0), cubic_cell(), SC_POS, [2.0])
+        mi.set_zeeman(np.array([0.1, 0.2, 1.0]) + sigma * eta[i])
+        mi.build()
+        ref = mi.heun(S0[:, :, :, :, i:i + 1], dt, alpha, nsteps=1)
+        assert np.abs(ref.reshape(3) - S1[:, 0, 0, 0, i]).max() < 1e-15
