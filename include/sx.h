@@ -1,0 +1,240 @@
+/*
+ * sx.h -- C ABI of the GB300 (sm_103a) atomistic spin library.
+ *
+ * The library evaluates the effective field of a translation-invariant spin
+ * Hamiltonian on a crystal of n[0] x n[1] x n[2] unit cells with nsub
+ * sublattices, and advances the spins with the normalised Heun scheme of the
+ * (stochastic) Landau-Lifshitz-Gilbert equation.  It follows the Methods
+ * section of arXiv 2605.26016 ("SpinX"):
+ *   - "Spin Hamiltonian and effective fields": H = H_bil + H_Z + H_ani + H_dip,
+ *     H_bil = -1/2 sum_{i,j} S_i^T J_ij S_j over directed bonds with
+ *     J_ji = J_ij^T, J_ij = J I + DMI matrix, reduced field b_i = -dH/dS_i in
+ *     meV, physical field B_i = b_i / (mu_i mu_B) in tesla;
+ *   - "Backend representations": the bilinear field is the multi-channel
+ *     convolution b_a(R) = sum_b sum_delta K_ab(delta) S_b(R + delta) over
+ *     sublattice channels; open faces drop the missing neighbours;
+ *   - "Atomistic spin dynamics": LLG right-hand side and normalised Heun;
+ *   - "Stochastic Landau-Lifshitz-Gilbert simulations": thermal field
+ *     sigma eta with sigma = sqrt(2 alpha kB T / (gamma mu mu_B dt)).
+ *
+ * Units: meV, tesla, fs, nm, kelvin.  Constants (CODATA 2018):
+ *   mu_B = 5.7883818060e-2 meV/T, gamma = 1.76085963023e-4 rad/(fs T),
+ *   k_B = 8.617333262e-2 meV/K.
+ *
+ * Spin layout.  A spin field is a caller-owned array of 3*nsite doubles in
+ * device memory, nsite = nsub*n[2]*n[1]*n[0]: three component planes
+ * [c][sub][z][y][x], x fastest (site index ((sub*nz + z)*ny + y)*nx + x).
+ * Fields b use the same layout.  Arrays must be 8-byte aligned and must not
+ * overlap unless stated.
+ *
+ * Ownership.  The caller owns every spin and field buffer.  The library owns
+ * its context, coupling tables, plans and workspaces; they are allocated by
+ * sx_plan and freed by sx_destroy.
+ *
+ * Errors.  Every call returns an sx_status (0 = SX_OK, negative on error) and
+ * sets a thread-local message read with sx_last_error().  No call aborts,
+ * throws across the ABI or traps on the device.  Arguments are checked before
+ * any work is queued.  Device calls are asynchronous on the given stream
+ * (a cudaStream_t passed as void*; NULL = legacy default stream) unless they
+ * return a host value, in which case they synchronise that stream.
+ *
+ * Thread safety.  Calls on one context must not run concurrently.  Distinct
+ * contexts are independent.
+ */
+#ifndef SX_H
+#define SX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SX_MAX_SUB 8
+#define SX_MAX_SHELL 16
+
+typedef struct sx_ctx sx_ctx;
+
+typedef enum {
+  SX_OK = 0,
+  SX_ERR_ARG = -1,         /* bad argument, size or layout */
+  SX_ERR_UNSUPPORTED = -2, /* valid request this build or plan cannot serve */
+  SX_ERR_OOM = -3,         /* device or host allocation failed */
+  SX_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+  SX_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+  SX_ERR_NUMERIC = -6,     /* non-finite or zero-length spin met */
+  SX_ERR_STATE = -7        /* call out of order (e.g. no plan yet) */
+} sx_status;
+
+typedef enum {
+  SX_BACKEND_GATHER = 0,   /* per-site gather over the directed-bond table (any range) */
+  SX_BACKEND_STENCIL = 1,  /* shared-memory halo stencil, fused Heun step (sparse convolution) */
+  SX_BACKEND_IGEMM_TC = 2, /* tcgen05 implicit GEMM (dense convolution) */
+  SX_BACKEND_FFT = 3       /* reciprocal-space kernel (FFT convolution, dipolar) */
+} sx_backend;
+
+typedef enum {
+  SX_PREC_FP64 = 0, /* field, torque and state update in FP64 */
+  SX_PREC_FP32 = 1, /* field and torque in FP32, spin state FP64 ("mixed precision") */
+  SX_PREC_TF32 = 2, /* field on tensor cores, TF32 inputs, FP32 accumulate; state FP64 */
+  SX_PREC_BF16 = 3  /* field on tensor cores, BF16 inputs, FP32 accumulate; state FP64 */
+} sx_precision;
+
+typedef enum { SX_DMI_INTERFACIAL = 0, SX_DMI_BULK = 1 } sx_dmi_kind;
+
+/* Crystal.  Cell vectors a[k] are rows in nm; sub_pos are fractional
+ * coordinates; mu[s] is the moment of sublattice s in Bohr magnetons
+ * ("Spin Hamiltonian and effective fields": mu_i = mu_i mu_B S_i).
+ * pbc[k] = 1 makes axis k periodic, 0 makes it open (free faces). */
+typedef struct {
+  int n[3];
+  int pbc[3];
+  double a[3][3];
+  int nsub;
+  double sub_pos[SX_MAX_SUB][3];
+  double mu[SX_MAX_SUB];
+} sx_lattice;
+
+/* One unordered bond: pair energy -S_a(R)^T J S_b(R + d) for every cell R,
+ * J row-major 3x3 in meV.  It is expanded into the directed bonds
+ * (a <- b at +d, J) and (b <- a at -d, J^T) ("Spin Hamiltonian and
+ * effective fields", ordered-pair form with J_ji^{ba} = J_ij^{ab}). */
+typedef struct {
+  int a, b;
+  int d[3];
+  double J[9];
+} sx_bond;
+
+/* A directed tap of the convolution kernel K_ab(delta) for target
+ * sublattice a ("Backend representations"): b_a(R) += J S_b(R + d). */
+typedef struct {
+  int a, b;
+  int d[3];
+  double J[9];
+} sx_tap;
+
+/* Heun/LLG parameters ("Atomistic spin dynamics", "Stochastic LLG"):
+ * dt in fs, Gilbert damping alpha, temperature in K (0 = deterministic).
+ * Thermal noise eta for site i at step t comes from Philox4x32-10 with
+ * counter (i_lo, i_hi, t_lo, replica << 8) and key (seed_lo, seed_hi),
+ * mapped to (0,1) by (2*(x>>9)+1)*2^-24 and to normals by Box-Muller; the
+ * same eta serves the predictor and the corrector. */
+typedef struct {
+  double dt_fs;
+  double alpha;
+  double T_kelvin;
+  uint64_t seed;
+  uint32_t replica;
+} sx_llg_params;
+
+/* Create a context for a lattice.  Host-only: makes no CUDA call.
+ * SX_ERR_ARG for n[k] < 1, nsub outside 1..SX_MAX_SUB, a singular cell. */
+int sx_create(sx_ctx **out, const sx_lattice *lat);
+
+/* Release the context, its plan and its device workspaces (NULL is a no-op). */
+void sx_destroy(sx_ctx *ctx);
+
+/* Thread-local text of the last error in this thread. */
+const char *sx_last_error(void);
+
+/* Number of distance shells found for the lattice and the radius (nm) of
+ * shell k (1-based; shell 1 = nearest neighbours).  Shells are the distinct
+ * site-to-site distances sorted ascending, ties within 1e-9 of the cell size
+ * ("Hopfion calculation": couplings on the first neighbour shells). */
+int sx_num_shells(const sx_ctx *ctx);
+double sx_shell_radius(const sx_ctx *ctx, int shell);
+
+/* Isotropic exchange J (meV) on every bond of distance shell `shell`
+ * (1-based): J_ij = J I.  Accumulates.  SX_ERR_ARG if the shell is out of
+ * range or beyond the bond search box (|delta| <= 4 cells). */
+int sx_add_shell_exchange(sx_ctx *ctx, int shell, double J);
+
+/* DMI of strength D (meV) on the bonds of shell `shell`: interfacial
+ * D_ij = D (z x r_ij) on bonds in the xy plane, bulk D_ij = D r_ij
+ * (r_ij the unit bond vector from i to j).  Enters J_ij as the
+ * antisymmetric matrix [[0,Dz,-Dy],[-Dz,0,Dx],[Dy,-Dx,0]]
+ * ("Spin Hamiltonian and effective fields"). */
+int sx_add_dmi(sx_ctx *ctx, int shell, int kind, double D);
+
+/* General 3x3 tensors (symmetric anisotropic exchange, DMI, ...) as n
+ * unordered bonds; see sx_bond.  SX_ERR_ARG for a self bond (a == b, d = 0),
+ * a sublattice out of range or |d_k| > 4. */
+int sx_add_bonds(sx_ctx *ctx, const sx_bond *bonds, size_t n);
+
+/* Uniform external field B (tesla): H_Z = -sum_i mu_i mu_B B.S_i. */
+int sx_set_zeeman(sx_ctx *ctx, const double B[3]);
+
+/* Uniaxial anisotropy on sublattice `sub`: H_ani = -sum K (S_i.n)^2,
+ * K in meV, axis normalised by the library.  Replaces the previous value. */
+int sx_set_anisotropy(sx_ctx *ctx, int sub, double K, const double axis[3]);
+
+/* Point-dipole interaction between all moments, J_ij^dip =
+ * (mu0 mu_B^2/4pi) mu_i mu_j (3 r r - I)/r^3, evaluated in reciprocal space
+ * (FFT backend only; periodic axes use the minimum image, a separation of
+ * exactly half a period is split into its two images with weight 1/2). */
+int sx_set_dipolar(sx_ctx *ctx, int enable);
+
+/* Directed taps (the convolution kernel) of target sublattice a after the
+ * Hamiltonian is set: writes up to cap taps, returns their total count or
+ * a negative status.  Host-only. */
+int sx_get_taps(sx_ctx *ctx, int a, sx_tap *out, int cap);
+
+/* Choose backend and precision, build the device tables and workspaces on
+ * the current CUDA device.  Must follow every Hamiltonian change and precede
+ * every device call.  SX_ERR_UNSUPPORTED for a combination this build cannot
+ * serve (e.g. STENCIL with taps beyond its halo, TF32/BF16 without
+ * IGEMM_TC); SX_ERR_ARG if a periodic axis is shorter than 2*range+1. */
+int sx_plan(sx_ctx *ctx, int backend, int precision);
+
+/* Reduced effective field b = -dH/dS (meV, see "Spin Hamiltonian and
+ * effective fields") of the spin field S, written to b (device, same layout
+ * as S, FP64 whatever the plan precision).  S and b must not overlap. */
+int sx_field(sx_ctx *ctx, const double *S, double *b, void *stream);
+
+/* nsteps normalised Heun steps of the LLG equation, steps step0 ..
+ * step0+nsteps-1 (the step index is the noise counter).  S (device) holds
+ * the input and receives the result; S_scratch (device, same size, no
+ * overlap) is a caller-owned ping-pong buffer whose content is overwritten.
+ * SX_ERR_ARG for dt <= 0, alpha < 0, T < 0 or nsteps < 0. */
+int sx_llg_heun_step(sx_ctx *ctx, double *S, double *S_scratch, const sx_llg_params *p, uint64_t step0,
+                     int nsteps, void *stream);
+
+/* One normalised Heun step out of place: S_out = Heun(S_in) at step `step`.
+ * S_in and S_out are device arrays of 3*nsite doubles that must not overlap;
+ * S_in is not modified.  Same rules as sx_llg_heun_step. */
+int sx_llg_heun_step_out(sx_ctx *ctx, const double *S_in, double *S_out, const sx_llg_params *p, uint64_t step,
+                         void *stream);
+
+/* End-to-end variant on HOST memory: copies S_host to the device, runs
+ * nsteps Heun steps in library-owned device buffers and copies the result
+ * back into S_host.  Synchronises the stream.  S_host may be pinned or
+ * pageable; pinned memory gives full copy bandwidth. */
+int sx_llg_heun_host(sx_ctx *ctx, double *S_host, const sx_llg_params *p, uint64_t step0, int nsteps,
+                     void *stream);
+
+/* Total energy in meV and its parts, E_host[0] = total, [1] = bilinear
+ * (-1/2 sum S.b_bil), [2] = Zeeman, [3] = anisotropy, [4] = dipolar, reduced
+ * in FP64 in a fixed order (deterministic).  The bilinear field is evaluated
+ * in the plan precision.  Synchronises the stream. */
+int sx_energy(sx_ctx *ctx, const double *S, double *E_host, void *stream);
+
+/* max_i |S_i x b_i| in meV (the force measure of the minimisation and path
+ * methods), written to *out_host.  Synchronises the stream. */
+int sx_torque_max(sx_ctx *ctx, const double *S, double *out_host, void *stream);
+
+/* The thermal normals the Heun step draws: eta for sites site0 .. site0+n-1
+ * at step `step`, written as n x 3 floats to eta_dev (device).  The noise is
+ * a pure function of (seed, replica, site, step), see sx_llg_params. */
+int sx_thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64_t n, uint64_t step, float *eta_dev,
+                       void *stream);
+
+/* Plan facts for callers and tests: out[0] = nsite, out[1] = max taps per
+ * sublattice, out[2..4] = halo radius per axis (cells), out[5] = backend,
+ * out[6] = precision, out[7] = device kernel launches per Heun step. */
+int sx_plan_info(const sx_ctx *ctx, int64_t out[8]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SX_H */

@@ -1,6 +1,6 @@
-"""Builds oracle models from the workload descriptions (input marshalling only)."""
+"""Builds oracle models from the workload descriptions (input marshalling only; test infrastructure)."""
 import oracle
-from paper_2605_26016_gb300.workloads import WORKLOADS, cubic_cell
+from workloads import WORKLOADS, cubic_cell
 
 
 def oracle_model(name, n, pbc=None, dipolar=False, build=True, **override):

@@ -1,0 +1,381 @@
+"""Thin Python binding of the GB300 atomistic spin library (include/sx.h).
+
+Every function here only marshals arguments for the C ABI of libsx.so; all
+computation happens in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  Importing works without a GPU; the library must have been
+built (``python -m paper_2605_26016_gb300.build`` or ``__graft_entry__.build()``)
+and there is no fallback: calls fail loudly if libsx.so is missing.
+
+Spin fields are float64 CUDA tensors of shape (3, nsub, nz, ny, nx) (or any
+contiguous tensor with 3*nsite elements in that order).
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsx.so")
+
+SX_OK, SX_ERR_ARG, SX_ERR_UNSUPPORTED, SX_ERR_OOM, SX_ERR_CUDA, SX_ERR_TIMEOUT, SX_ERR_NUMERIC, SX_ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+SX_BACKEND_GATHER, SX_BACKEND_STENCIL, SX_BACKEND_IGEMM_TC, SX_BACKEND_FFT = 0, 1, 2, 3
+SX_PREC_FP64, SX_PREC_FP32, SX_PREC_TF32, SX_PREC_BF16 = 0, 1, 2, 3
+SX_DMI_INTERFACIAL, SX_DMI_BULK = 0, 1
+SX_MAX_SUB = 8
+
+BACKENDS = {"gather": SX_BACKEND_GATHER, "stencil": SX_BACKEND_STENCIL, "igemm_tc": SX_BACKEND_IGEMM_TC,
+            "fft": SX_BACKEND_FFT}
+PRECISIONS = {"fp64": SX_PREC_FP64, "fp32": SX_PREC_FP32, "tf32": SX_PREC_TF32, "bf16": SX_PREC_BF16}
+
+# names exported by libsx.so, exactly the functions declared in include/sx.h
+EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shell_radius", "sx_add_shell_exchange",
+           "sx_add_dmi", "sx_add_bonds", "sx_set_zeeman", "sx_set_anisotropy", "sx_set_dipolar", "sx_get_taps",
+           "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
+           "sx_thermal_normals", "sx_plan_info")
+
+
+class sx_lattice(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("pbc", ctypes.c_int * 3), ("a", (ctypes.c_double * 3) * 3),
+                ("nsub", ctypes.c_int), ("sub_pos", (ctypes.c_double * 3) * SX_MAX_SUB),
+                ("mu", ctypes.c_double * SX_MAX_SUB)]
+
+
+class sx_bond(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int), ("b", ctypes.c_int), ("d", ctypes.c_int * 3), ("J", ctypes.c_double * 9)]
+
+
+sx_tap = sx_bond
+
+
+class sx_llg_params(ctypes.Structure):
+    _fields_ = [("dt_fs", ctypes.c_double), ("alpha", ctypes.c_double), ("T_kelvin", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("replica", ctypes.c_uint32)]
+
+
+class SxError(RuntimeError):
+    def __init__(self, code, fn, msg):
+        super().__init__(f"{fn} failed ({code}): {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libsx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2605_26016_gb300.build`")
+        try:  # share the CUDA runtime torch already loaded
+            import torch  # noqa: F401
+        except ImportError:
+            pass
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+        sig = {
+            "sx_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(sx_lattice)]),
+            "sx_destroy": (None, [vp]),
+            "sx_last_error": (ctypes.c_char_p, []),
+            "sx_num_shells": (ctypes.c_int, [vp]),
+            "sx_shell_radius": (ctypes.c_double, [vp, ctypes.c_int]),
+            "sx_add_shell_exchange": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
+            "sx_add_dmi": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
+            "sx_add_bonds": (ctypes.c_int, [vp, ctypes.POINTER(sx_bond), ctypes.c_size_t]),
+            "sx_set_zeeman": (ctypes.c_int, [vp, dp]),
+            "sx_set_anisotropy": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, dp]),
+            "sx_set_dipolar": (ctypes.c_int, [vp, ctypes.c_int]),
+            "sx_get_taps": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(sx_tap), ctypes.c_int]),
+            "sx_plan": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+            "sx_field": (ctypes.c_int, [vp, vp, vp, vp]),
+            "sx_llg_heun_step": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_uint64,
+                                                ctypes.c_int, vp]),
+            "sx_llg_heun_step_out": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_uint64, vp]),
+            "sx_llg_heun_host": (ctypes.c_int, [vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_uint64,
+                                                ctypes.c_int, vp]),
+            "sx_energy": (ctypes.c_int, [vp, vp, dp, vp]),
+            "sx_torque_max": (ctypes.c_int, [vp, vp, dp, vp]),
+            "sx_thermal_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, i64,
+                                                  ctypes.c_uint64, vp, vp]),
+            "sx_plan_info": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error():
+    return lib().sx_last_error().decode(errors="replace")
+
+
+def _chk(rc, fn):
+    if rc != SX_OK:
+        raise SxError(rc, fn, last_error())
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, nelem, dtype_name="float64"):
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch." + dtype_name or t.numel() != nelem:
+        raise ValueError(f"expected a contiguous CUDA {dtype_name} tensor with {nelem} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dbl3(v):
+    return (ctypes.c_double * 3)(*[float(x) for x in v])
+
+
+def make_lattice(n, pbc, cell, pos, mu):
+    L = sx_lattice()
+    for k in range(3):
+        L.n[k] = int(n[k])
+        L.pbc[k] = 1 if pbc[k] else 0
+        for j in range(3):
+            L.a[k][j] = float(cell[k][j])
+    L.nsub = len(pos)
+    for s, p in enumerate(pos):
+        for j in range(3):
+            L.sub_pos[s][j] = float(p[j])
+        L.mu[s] = float(mu[s])
+    return L
+
+
+# ---------------------------------------------------------------- C-ABI mirrors
+
+def sx_create(n, pbc, cell, pos, mu):
+    h = ctypes.c_void_p()
+    L = make_lattice(n, pbc, cell, pos, mu)
+    _chk(lib().sx_create(ctypes.byref(h), ctypes.byref(L)), "sx_create")
+    return h
+
+
+def sx_destroy(ctx):
+    if ctx is not None and ctx.value:
+        lib().sx_destroy(ctx)
+
+
+def sx_num_shells(ctx):
+    return lib().sx_num_shells(ctx)
+
+
+def sx_shell_radius(ctx, shell):
+    return lib().sx_shell_radius(ctx, int(shell))
+
+
+def sx_add_shell_exchange(ctx, shell, J):
+    return _chk(lib().sx_add_shell_exchange(ctx, int(shell), float(J)), "sx_add_shell_exchange")
+
+
+def sx_add_dmi(ctx, shell, kind, D):
+    return _chk(lib().sx_add_dmi(ctx, int(shell), int(kind), float(D)), "sx_add_dmi")
+
+
+def sx_add_bonds(ctx, bonds):
+    """bonds: iterable of (a, b, (dx, dy, dz), J 3x3)."""
+    bonds = list(bonds)
+    arr = (sx_bond * max(1, len(bonds)))()
+    for i, (a, b, d, J) in enumerate(bonds):
+        arr[i].a, arr[i].b = int(a), int(b)
+        for k in range(3):
+            arr[i].d[k] = int(d[k])
+        flat = [float(x) for row in J for x in row]
+        for k in range(9):
+            arr[i].J[k] = flat[k]
+    return _chk(lib().sx_add_bonds(ctx, arr, len(bonds)), "sx_add_bonds")
+
+
+def sx_set_zeeman(ctx, B):
+    return _chk(lib().sx_set_zeeman(ctx, _dbl3(B)), "sx_set_zeeman")
+
+
+def sx_set_anisotropy(ctx, sub, K, axis):
+    return _chk(lib().sx_set_anisotropy(ctx, int(sub), float(K), _dbl3(axis)), "sx_set_anisotropy")
+
+
+def sx_set_dipolar(ctx, enable):
+    return _chk(lib().sx_set_dipolar(ctx, 1 if enable else 0), "sx_set_dipolar")
+
+
+def sx_get_taps(ctx, a):
+    n = lib().sx_get_taps(ctx, int(a), None, 0)
+    if n < 0:
+        raise SxError(n, "sx_get_taps", last_error())
+    arr = (sx_tap * max(1, n))()
+    _ = lib().sx_get_taps(ctx, int(a), arr, n)
+    return [(t.b, tuple(t.d), [list(t.J[0:3]), list(t.J[3:6]), list(t.J[6:9])]) for t in arr[:n]]
+
+
+def sx_plan(ctx, backend, precision):
+    b = BACKENDS.get(backend, backend)
+    p = PRECISIONS.get(precision, precision)
+    return _chk(lib().sx_plan(ctx, int(b), int(p)), "sx_plan")
+
+
+def sx_plan_info(ctx):
+    out = (ctypes.c_int64 * 8)()
+    _chk(lib().sx_plan_info(ctx, out), "sx_plan_info")
+    keys = ("nsite", "max_taps", "rx", "ry", "rz", "backend", "precision", "launches_per_step")
+    return dict(zip(keys, list(out)))
+
+
+def llg_params(dt_fs, alpha, T=0.0, seed=0, replica=0):
+    p = sx_llg_params()
+    p.dt_fs, p.alpha, p.T_kelvin, p.seed, p.replica = float(dt_fs), float(alpha), float(T), int(seed), int(replica)
+    return p
+
+
+def sx_field(ctx, S, b, nsite, stream=None):
+    return _chk(lib().sx_field(ctx, _dev_ptr(S, 3 * nsite), _dev_ptr(b, 3 * nsite), _stream(stream)), "sx_field")
+
+
+def sx_llg_heun_step(ctx, S, S_scratch, params, step0, nsteps, nsite, stream=None):
+    return _chk(lib().sx_llg_heun_step(ctx, _dev_ptr(S, 3 * nsite), _dev_ptr(S_scratch, 3 * nsite),
+                                       ctypes.byref(params), int(step0), int(nsteps), _stream(stream)),
+                "sx_llg_heun_step")
+
+
+def sx_llg_heun_step_out(ctx, S_in, S_out, params, step, nsite, stream=None):
+    return _chk(lib().sx_llg_heun_step_out(ctx, _dev_ptr(S_in, 3 * nsite), _dev_ptr(S_out, 3 * nsite),
+                                           ctypes.byref(params), int(step), _stream(stream)), "sx_llg_heun_step_out")
+
+
+def sx_llg_heun_host(ctx, S_host, params, step0, nsteps, nsite, stream=None):
+    """S_host: contiguous float64 CPU torch tensor (pinned for full bandwidth) or numpy array."""
+    if hasattr(S_host, "data_ptr"):
+        if S_host.is_cuda or not S_host.is_contiguous() or S_host.numel() != 3 * nsite:
+            raise ValueError("S_host must be a contiguous CPU tensor with 3*nsite elements")
+        ptr = ctypes.c_void_p(S_host.data_ptr())
+    else:
+        if S_host.size != 3 * nsite or not S_host.flags["C_CONTIGUOUS"]:
+            raise ValueError("S_host must be a contiguous array with 3*nsite elements")
+        ptr = ctypes.c_void_p(S_host.ctypes.data)
+    return _chk(lib().sx_llg_heun_host(ctx, ptr, ctypes.byref(params), int(step0), int(nsteps), _stream(stream)),
+                "sx_llg_heun_host")
+
+
+def sx_energy(ctx, S, nsite, stream=None):
+    out = (ctypes.c_double * 5)()
+    _chk(lib().sx_energy(ctx, _dev_ptr(S, 3 * nsite), out, _stream(stream)), "sx_energy")
+    return {"total": out[0], "bilinear": out[1], "zeeman": out[2], "anisotropy": out[3], "dipolar": out[4]}
+
+
+def sx_torque_max(ctx, S, nsite, stream=None):
+    out = ctypes.c_double()
+    _chk(lib().sx_torque_max(ctx, _dev_ptr(S, 3 * nsite), ctypes.byref(out), _stream(stream)), "sx_torque_max")
+    return out.value
+
+
+def sx_thermal_normals(seed, replica, site0, n, step, eta, stream=None):
+    return _chk(lib().sx_thermal_normals(int(seed), int(replica), int(site0), int(n), int(step),
+                                         _dev_ptr(eta, 3 * n, "float32"), _stream(stream)), "sx_thermal_normals")
+
+
+# ---------------------------------------------------------------- convenience
+
+class SpinSystem:
+    """Owns one context.  Convenience over the sx_* functions above."""
+
+    def __init__(self, n, pbc, cell, pos, mu):
+        self.ctx = sx_create(n, pbc, cell, pos, mu)
+        self.n = tuple(int(v) for v in n)
+        self.nsub = len(pos)
+        self.nsite = self.nsub * self.n[0] * self.n[1] * self.n[2]
+        self.shape = (3, self.nsub, self.n[2], self.n[1], self.n[0])
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            sx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_shell_exchange(self, shell, J):
+        sx_add_shell_exchange(self.ctx, shell, J)
+
+    def add_dmi(self, shell, kind, D):
+        sx_add_dmi(self.ctx, shell, kind, D)
+
+    def add_bonds(self, bonds):
+        sx_add_bonds(self.ctx, bonds)
+
+    def set_zeeman(self, B):
+        sx_set_zeeman(self.ctx, B)
+
+    def set_anisotropy(self, sub, K, axis):
+        sx_set_anisotropy(self.ctx, sub, K, axis)
+
+    def set_dipolar(self, on):
+        sx_set_dipolar(self.ctx, on)
+
+    def taps(self, a):
+        return sx_get_taps(self.ctx, a)
+
+    def plan(self, backend="stencil", precision="fp32"):
+        sx_plan(self.ctx, backend, precision)
+        return sx_plan_info(self.ctx)
+
+    def info(self):
+        return sx_plan_info(self.ctx)
+
+    def field(self, S, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(S)
+        sx_field(self.ctx, S, out, self.nsite, stream)
+        return out
+
+    def heun(self, S, scratch, dt, alpha, T=0.0, seed=0, replica=0, step0=0, nsteps=1, stream=None):
+        sx_llg_heun_step(self.ctx, S, scratch, llg_params(dt, alpha, T, seed, replica), step0, nsteps, self.nsite,
+                         stream)
+        return S
+
+    def heun_host(self, S_host, dt, alpha, T=0.0, seed=0, replica=0, step0=0, nsteps=1, stream=None):
+        sx_llg_heun_host(self.ctx, S_host, llg_params(dt, alpha, T, seed, replica), step0, nsteps, self.nsite, stream)
+        return S_host
+
+    def energy(self, S, stream=None):
+        return sx_energy(self.ctx, S, self.nsite, stream)
+
+    def torque_max(self, S, stream=None):
+        return sx_torque_max(self.ctx, S, self.nsite, stream)
+
+
+def system_from_workload(workload, n, pbc=None, cell=None, **override):
+    """SpinSystem (not yet planned) for a workload description: a dict with keys pos, mu, shells,
+    dmi, B, K, pbc (see workloads.py at the repository root), or the name of one there."""
+    if isinstance(workload, str):
+        from workloads import WORKLOADS, cubic_cell
+        w = dict(WORKLOADS[workload])
+        cell = cell or cubic_cell()
+    else:
+        w = dict(workload)
+    if cell is None:
+        raise ValueError("cell vectors are required with a workload dict")
+    w.update(override)
+    s = SpinSystem(n, pbc if pbc is not None else w["pbc"], cell, w["pos"], w["mu"])
+    for k, J in enumerate(w["shells"]):
+        if J != 0.0:
+            s.add_shell_exchange(k + 1, J)
+    if w["dmi"]:
+        shell, kind, D = w["dmi"]
+        s.add_dmi(shell, kind, D)
+    s.set_zeeman(w["B"])
+    if w["K"]:
+        K, axis = w["K"]
+        for sub in range(len(w["pos"])):
+            s.set_anisotropy(sub, K, axis)
+    return s, w

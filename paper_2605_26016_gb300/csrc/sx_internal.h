@@ -1,0 +1,131 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sx.h"
+
+namespace sx {
+
+// CODATA 2018 constants in the library's units (meV, T, fs, K).
+constexpr double kMuB = 5.7883818060e-2;     // meV / T
+constexpr double kGamma = 1.76085963023e-4;  // rad / (fs T)
+constexpr double kKB = 8.617333262e-2;       // meV / K
+constexpr int kSearch = 4;                   // bond search box: cell offsets -4..4
+constexpr int kMaxTaps = 512;                // taps per target sublattice
+
+// One directed tap of K_ab(delta) as stored on the device for the gather path.
+struct DevTap {
+  int b, dx, dy, dz;
+  int iso;  // 1: J = j I (only J[0] used)
+  int pad;
+  double J[9];
+  float Jf[9];
+  float pad2;
+};
+
+// Lattice geometry as seen by kernels.
+struct Geo {
+  int nx, ny, nz, nsub;
+  int px, py, pz;  // periodic flags
+  int pad;
+  int64_t ncell, nsite;
+};
+
+// On-site terms per sublattice: Zeeman mu mu_B B (meV), uniaxial 2K and axis,
+// 1/(mu mu_B) to turn the reduced field into tesla.
+struct OnSite {
+  double zee[SX_MAX_SUB][3];
+  double twoK[SX_MAX_SUB];
+  double axis[SX_MAX_SUB][3];
+  double inv_mm[SX_MAX_SUB];
+};
+
+// Heun step constants shared by every backend.
+struct HeunConst {
+  double dt;
+  double g;                     // -gamma / (1 + alpha^2)
+  double alpha;
+  double sigma[SX_MAX_SUB];     // thermal field amplitude (T); 0 if deterministic
+  uint64_t seed;
+  uint32_t replica;
+  int thermal;
+};
+
+struct Tap {
+  int b, d[3];
+  double J[9];
+};
+
+// Stencil-backend tables (filled by the host planner, consumed by sx_stencil.cu).
+struct StencilPlan;
+
+}  // namespace sx
+
+struct sx_ctx {
+  sx_lattice lat;
+  sx::Geo geo;
+  double shell_r[256];
+  int nshell;
+  double tol;
+  double shellJ[SX_MAX_SHELL];
+  int dmi_kind[SX_MAX_SHELL];
+  double dmiD[SX_MAX_SHELL];
+  std::vector<sx_bond> bonds;
+  double B[3];
+  double K[SX_MAX_SUB];
+  double axis[SX_MAX_SUB][3];
+  int dipolar;
+  int ham_version;
+
+  // tables built from the Hamiltonian
+  std::vector<std::vector<sx::Tap>> taps;  // per target sublattice
+  int radius[3];
+  int tables_version;
+
+  // plan
+  int planned;
+  int plan_version;
+  int backend, prec;
+  int device;
+  sx::OnSite onsite;
+  sx::DevTap *d_taps;
+  int *d_tap_off;
+  double *d_work;        // 2 x 3 nsite doubles: Heun predictor state and f0 (gather path)
+  double *d_field;       // 3 nsite doubles: field scratch for energy / torque
+  double *d_partial;     // reduction partials
+  double *d_host_S[2];   // device buffers for the host-memory entry point
+  int64_t nblock_red;
+  sx::StencilPlan *stencil;
+  int launches_per_step;
+};
+
+namespace sx {
+
+int set_error(int code, const std::string &msg);
+int cuda_error(cudaError_t e, const char *what);
+
+// gather path (sx_gather.cu)
+cudaError_t gather_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
+cudaError_t gather_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
+                             cudaStream_t st);
+cudaError_t reduce_energy(const sx_ctx *c, const double *S, const double *bbil, double *partial, int64_t nblock,
+                          double *out_dev, cudaStream_t st);
+cudaError_t reduce_torque(const sx_ctx *c, const double *S, const double *b, double *partial, int64_t nblock,
+                          double *out_dev, cudaStream_t st);
+int64_t reduce_blocks(int64_t nsite);
+cudaError_t thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64_t n, uint64_t step, float *eta,
+                            cudaStream_t st);
+
+// stencil path (sx_stencil.cu)
+int stencil_plan(sx_ctx *c);
+void stencil_free(sx_ctx *c);
+cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
+cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
+                              cudaStream_t st);
+
+}  // namespace sx

@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (normwise, max_i |b_i - b_i^ref| / max_i |b_i^ref| over site vectors):
+FP64 path 1e-12; FP32 field 1e-6.  A Heun step is compared on its increment
+S^{n+1} - S^n, normwise, with the same bounds (FP32: 1e-5, the increment
+carries the FP32 field error of both stages).  Thermal noise must agree bit
+for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2605_26016_gb300 as sx
+from oracle.models import oracle_model
+from workloads import SC_POS, cubic_cell, random_spins
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL_FIELD = {"fp64": 1e-12, "fp32": 1e-6}
+TOL_STEP = {"fp64": 1e-11, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_26016_gb300.build import build
+    build()
+    torch.cuda.init()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def normwise(got, ref):
+    got = np.asarray(got).reshape(3, -1)
+    ref = np.asarray(ref).reshape(3, -1)
+    d = np.sqrt(((got - ref) ** 2).sum(0)).max()
+    return d / max(np.sqrt((ref ** 2).sum(0)).max(), 1e-300)
+
+
+def pair(name, n, pbc=None, extra=None, **override):
+    s, w = sx.system_from_workload(name, n, pbc=pbc, **override)
+    m, _ = oracle_model(name, n, pbc=pbc, build=False, **override)
+    if extra:
+        extra(s, m)
+    m.build()
+    return s, m, w
+
+
+def _bonds_extra(s, m):
+    rng = np.random.default_rng(5)
+    J1 = rng.normal(size=(3, 3)) * 0.7
+    s.add_bonds([(0, 1, (1, 0, -1), J1)])
+    m.add_bond(0, 1, (1, 0, -1), J1)
+    s.add_dmi(2, sx.SX_DMI_BULK, 0.4)
+    m.add_dmi(2, 1, 0.4)
+
+
+CASES = [
+    ("bcc_4shell", (13, 11, 9), (1, 1, 0), None),
+    ("bcc_4shell", (10, 7, 12), (0, 1, 1), _bonds_extra),
+    ("sc_j123_dmi", (17, 12, 10), None, None),
+    ("sc_j123", (20, 9, 11), None, None),
+    ("sc_nn", (33, 5, 7), None, None),
+]
+
+
+# ---------------------------------------------------------------- noise
+
+@pytest.mark.parametrize("seed,replica,site0,n,step", [(0, 0, 0, 4096, 0), (2, 0, 123456789, 20000, 77),
+                                                       (2 ** 40 + 5, 3, 2 ** 33 - 7, 5000, 2 ** 31 + 9)])
+def test_noise_bit_equal(seed, replica, site0, n, step):
+    eta = torch.empty(n * 3, dtype=torch.float32, device="cuda")
+    sx.sx_thermal_normals(seed, replica, site0, n, step, eta)
+    torch.cuda.synchronize()
+    ref = oracle.normals(seed, replica, site0, n, step)
+    got = eta.cpu().numpy().reshape(n, 3)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+# ---------------------------------------------------------------- field / energy / torque
+
+@pytest.mark.parametrize("backend", ["gather"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_field_energy_torque(backend, prec, case):
+    name, n, pbc, extra = CASES[case]
+    s, m, w = pair(name, n, pbc, extra)
+    s.plan(backend, prec)
+    S = random_spins(s.nsub, n, 100 + case)
+    Sd = dev(S)
+    b = s.field(Sd)
+    torch.cuda.synchronize()
+    ref = m.field(S)
+    assert normwise(b.cpu().numpy(), ref) <= TOL_FIELD[prec]
+    e = s.energy(Sd)
+    e_ref, t_ref = m.energy(S, terms=True)
+    scale = np.abs(t_ref).sum()
+    bsum = 0.5 * np.sqrt((ref.reshape(3, -1) ** 2).sum(0)).sum()   # bound on sum_i |S_i.b_i| / 2
+    assert abs(e["total"] - e_ref) <= TOL_FIELD[prec] * bsum
+    assert abs(e["bilinear"] - t_ref[0]) <= TOL_FIELD[prec] * bsum
+    assert abs(e["zeeman"] - t_ref[1]) <= 1e-12 * scale
+    assert abs(e["anisotropy"] - t_ref[2]) <= 1e-12 * scale
+    tq = s.torque_max(Sd)
+    tq_ref = m.torque_max(S)
+    assert abs(tq - tq_ref) <= TOL_FIELD[prec] * max(np.sqrt((ref.reshape(3, -1) ** 2).sum(0)).max(), 1.0) * 4
+
+
+# ---------------------------------------------------------------- Heun
+
+@pytest.mark.parametrize("backend", ["gather"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", [0, 1, 2])
+@pytest.mark.parametrize("thermal", [False, True])
+def test_heun_step(backend, prec, case, thermal):
+    name, n, pbc, extra = CASES[case]
+    s, m, w = pair(name, n, pbc, extra)
+    s.plan(backend, prec)
+    S = random_spins(s.nsub, n, 200 + case)
+    T = w["T"] if thermal else 0.0
+    T = T if T > 0 else 100.0 if thermal else 0.0
+    kw = dict(dt=w["dt"], alpha=w["alpha"], T=T, seed=31 + case, replica=case, step0=1000 + case)
+    for nsteps in (1, 4):
+        Sd = dev(S)
+        scratch = torch.empty_like(Sd)
+        s.heun(Sd, scratch, nsteps=nsteps, **kw)
+        torch.cuda.synchronize()
+        got = Sd.cpu().numpy()
+        ref = m.heun(S, kw["dt"], kw["alpha"], T=T, seed=kw["seed"], replica=kw["replica"], step0=kw["step0"],
+                     nsteps=nsteps)
+        assert normwise(got - S, ref - S) <= TOL_STEP[prec] * (1 if nsteps == 1 else 4)
+        assert np.abs(np.sqrt((got.reshape(3, -1) ** 2).sum(0)) - 1).max() < 1e-13
+
+
+def test_heun_host_entry_matches_device_entry():
+    s, m, w = pair("bcc_4shell", (9, 8, 7))
+    s.plan("gather", "fp32")
+    S = random_spins(2, (9, 8, 7), 9)
+    Sd = dev(S)
+    s.heun(Sd, torch.empty_like(Sd), dt=0.1, alpha=0.05, T=300.0, seed=4, step0=5, nsteps=3)
+    Sh = torch.from_numpy(S.copy()).pin_memory()
+    s.heun_host(Sh, dt=0.1, alpha=0.05, T=300.0, seed=4, step0=5, nsteps=3)
+    torch.cuda.synchronize()
+    assert torch.equal(Sd.cpu(), Sh)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_single_spin_larmor_step():
+    s = sx.SpinSystem((1, 1, 1), (0, 0, 0), cubic_cell(), SC_POS, [1.0])
+    s.set_zeeman([0.0, 0.0, 10.0])
+    s.plan("gather", "fp64")
+    m = oracle.Model((1, 1, 1), (0, 0, 0), cubic_cell(), SC_POS, [1.0])
+    m.set_zeeman([0.0, 0.0, 10.0])
+    m.build()
+    S = np.array([math.sin(1.0), 0.0, math.cos(1.0)]).reshape(3, 1, 1, 1, 1)
+    Sd = dev(S)
+    s.heun(Sd, torch.empty_like(Sd), dt=2.0, alpha=0.1, nsteps=50)
+    ref = m.heun(S, 2.0, 0.1, nsteps=50)
+    assert np.abs(Sd.cpu().numpy() - ref).max() < 1e-13
+
+
+def test_zero_steps_is_identity_and_open_thin_lattice():
+    n = (1, 5, 3)
+    s, m, w = pair("sc_j123", n, pbc=(0, 1, 0))
+    s.plan("gather", "fp64")
+    S = random_spins(1, n, 8)
+    Sd = dev(S)
+    s.heun(Sd, torch.empty_like(Sd), dt=0.1, alpha=0.1, nsteps=0)
+    assert np.array_equal(Sd.cpu().numpy(), S)
+    b = s.field(Sd)
+    assert normwise(b.cpu().numpy(), m.field(S)) <= 1e-12
+
+
+def test_bad_arguments_on_device_calls():
+    s, m, w = pair("sc_nn", (8, 8, 8))
+    s.plan("gather", "fp32")
+    S = dev(random_spins(1, (8, 8, 8), 1))
+    with pytest.raises(ValueError):
+        s.field(S[:, :, :4].contiguous())
+    with pytest.raises(sx.SxError) as e:
+        sx.sx_llg_heun_step(s.ctx, S, S, sx.llg_params(0.1, 0.1), 0, 1, s.nsite)
+    assert e.value.code == sx.SX_ERR_ARG
+    with pytest.raises(sx.SxError) as e:
+        sx.sx_llg_heun_step(s.ctx, S, torch.empty_like(S), sx.llg_params(-0.1, 0.1), 0, 1, s.nsite)
+    assert e.value.code == sx.SX_ERR_ARG
+    s.set_zeeman([0, 0, 2.0])     # changes the Hamiltonian: the plan is stale
+    with pytest.raises(sx.SxError) as e:
+        s.field(S)
+    assert e.value.code == sx.SX_ERR_STATE
+
+
+# ---------------------------------------------------------------- full size, sampled
+
+@pytest.mark.parametrize("backend,prec", [("gather", "fp32"), ("gather", "fp64")])
+def test_full_size_bcc_sampled_field(backend, prec):
+    n = (128, 128, 128)
+    s, w = sx.system_from_workload("bcc_4shell", n)
+    s.plan(backend, prec)
+    S = random_spins(2, n, w["seed"])
+    b = s.field(dev(S)).cpu().numpy().reshape(3, -1)
+    m, _ = oracle_model("bcc_4shell", n, build=False)
+    rng = np.random.default_rng(0)
+    sites = np.concatenate([rng.choice(s.nsite, 3000, replace=False), [0, s.nsite - 1, 128 * 128 * 128 - 1]])
+    ref = m.field_sites(S, sites)
+    got = b[:, sites].T
+    assert normwise(got.T, ref.T) <= TOL_FIELD[prec]

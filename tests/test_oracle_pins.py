@@ -12,8 +12,8 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle_models import oracle_model
-from paper_2605_26016_gb300.workloads import A_NM, BCC_POS, SC_POS, cubic_cell, random_spins, uniform_spins
+from oracle.models import oracle_model
+from workloads import A_NM, BCC_POS, SC_POS, cubic_cell, random_spins, uniform_spins
 
 C = oracle.constants()
 MU_B, GAMMA, K_B = C["mu_B"], C["gamma"], C["k_B"]
