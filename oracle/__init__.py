@@ -75,6 +75,8 @@ def lib():
         L.orc_torque_max.argtypes = [ctypes.c_void_p, _dp]
         L.orc_heun.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64]
+        L.orc_heun_sites.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _i64p, ctypes.c_int64, _dp]
         L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.orc_normals_block.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                         ctypes.c_uint64, _fp]
@@ -185,6 +187,15 @@ class Model:
 
     def torque_max(self, S):
         return lib().orc_torque_max(self.h, _ptr(self._spins(S), _dp))
+
+    def heun_sites(self, S, sites, dt, alpha, T=0.0, seed=0, replica=0, step=0):
+        """One Heun step evaluated at the given sites only: (len(sites), 3)."""
+        S = self._spins(S)
+        sites = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+        out = np.empty((len(sites), 3), dtype=np.float64)
+        _check(lib().orc_heun_sites(self.h, _ptr(S, _dp), float(dt), float(alpha), float(T), int(seed), int(replica),
+                                    int(step), _ptr(sites, _i64p), len(sites), _ptr(out, _dp)), "heun_sites")
+        return out
 
     def heun(self, S, dt, alpha, T=0.0, seed=0, replica=0, step0=0, nsteps=1):
         """Return a new spin array after nsteps normalised Heun steps."""

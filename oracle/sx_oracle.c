@@ -817,6 +817,99 @@ int orc_heun(void *h, double *S, double dt, double alpha, double T, uint64_t see
   return 0;
 }
 
+/* One Heun step evaluated only at the selected sites (same arithmetic as
+ * orc_heun): the predictor is formed for each selected site and for every
+ * source of its bonds, then the corrector at the site.  For checks on large
+ * lattices where a full step on the CPU is too slow.  out[3*k + c]. */
+int orc_heun_sites(void *h, const double *S, double dt, double alpha, double T, uint64_t seed, uint32_t replica,
+                   uint64_t step, const int64_t *sites, int64_t nsel, double *out) {
+  orc_model *m = (orc_model *)h;
+  if (m->dipolar) return -1;
+  int64_t N = m->nsite;
+  int err = 0;
+#pragma omp parallel
+  {
+    int64_t *jj = (int64_t *)malloc(sizeof(int64_t) * ORC_PAIRCAP);
+    double *JJ = (double *)malloc(sizeof(double) * 9 * ORC_PAIRCAP);
+    int64_t *kk = (int64_t *)malloc(sizeof(int64_t) * ORC_PAIRCAP);
+    double *KK = (double *)malloc(sizeof(double) * 9 * ORC_PAIRCAP);
+    double *St = (double *)malloc(sizeof(double) * 3 * (ORC_PAIRCAP + 1));
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t q = 0; q < nsel; q++) {
+      int64_t i = sites[q];
+      if (i < 0 || i >= N) {
+        err = 1;
+        continue;
+      }
+      int64_t ci = site_pairs(m, i, jj, JJ, ORC_PAIRCAP);
+      if (ci > ORC_PAIRCAP) {
+        err = 1;
+        continue;
+      }
+      double f0i[3];
+      /* predictor for the site itself (slot ci) and every bond source (slots 0..ci-1) */
+      for (int64_t p = 0; p <= ci; p++) {
+        int64_t j = (p < ci) ? jj[p] : i;
+        int64_t cj = site_pairs(m, j, kk, KK, ORC_PAIRCAP);
+        double b[3] = {0, 0, 0};
+        for (int64_t r = 0; r < cj; r++) {
+          int64_t k = kk[r];
+          const double *J = KK + 9 * r;
+          double Sk[3] = {S[k], S[N + k], S[2 * N + k]};
+          for (int a = 0; a < 3; a++) b[a] += J[3 * a] * Sk[0] + J[3 * a + 1] * Sk[1] + J[3 * a + 2] * Sk[2];
+        }
+        int s, cc[3];
+        site_coords(m, j, &s, cc);
+        double Sj[3] = {S[j], S[N + j], S[2 * N + j]};
+        onsite_field(m, s, Sj, b);
+        double mm = m->mu[s] * ORC_MU_B, B[3], f[3], x[3], th[3] = {0, 0, 0};
+        if (T > 0.0) {
+          double sigma = sqrt(2.0 * alpha * ORC_K_B * T / (ORC_GAMMA * m->mu[s] * ORC_MU_B * dt));
+          float eta[3];
+          orc_normals(seed, replica, (uint64_t)j, step, eta);
+          for (int a = 0; a < 3; a++) th[a] = sigma * (double)eta[a];
+        }
+        for (int a = 0; a < 3; a++) B[a] = b[a] / mm + th[a];
+        llg_rhs(Sj, B, alpha, f);
+        for (int a = 0; a < 3; a++) x[a] = Sj[a] + dt * f[a];
+        normalise(x);
+        for (int a = 0; a < 3; a++) St[3 * p + a] = x[a];
+        if (p == ci)
+          for (int a = 0; a < 3; a++) f0i[a] = f[a];
+      }
+      /* corrector at the site from the predicted neighbours */
+      double b[3] = {0, 0, 0};
+      for (int64_t p = 0; p < ci; p++) {
+        const double *J = JJ + 9 * p;
+        const double *Sp = St + 3 * p;
+        for (int a = 0; a < 3; a++) b[a] += J[3 * a] * Sp[0] + J[3 * a + 1] * Sp[1] + J[3 * a + 2] * Sp[2];
+      }
+      int s, cc[3];
+      site_coords(m, i, &s, cc);
+      double Sti[3] = {St[3 * ci], St[3 * ci + 1], St[3 * ci + 2]};
+      onsite_field(m, s, Sti, b);
+      double mm = m->mu[s] * ORC_MU_B, B[3], f[3], x[3], th[3] = {0, 0, 0};
+      if (T > 0.0) {
+        double sigma = sqrt(2.0 * alpha * ORC_K_B * T / (ORC_GAMMA * m->mu[s] * ORC_MU_B * dt));
+        float eta[3];
+        orc_normals(seed, replica, (uint64_t)i, step, eta);
+        for (int a = 0; a < 3; a++) th[a] = sigma * (double)eta[a];
+      }
+      for (int a = 0; a < 3; a++) B[a] = b[a] / mm + th[a];
+      llg_rhs(Sti, B, alpha, f);
+      for (int a = 0; a < 3; a++) x[a] = S[a * N + i] + 0.5 * dt * (f0i[a] + f[a]);
+      normalise(x);
+      for (int a = 0; a < 3; a++) out[3 * q + a] = x[a];
+    }
+    free(jj);
+    free(JJ);
+    free(kk);
+    free(KK);
+    free(St);
+  }
+  return err ? -1 : 0;
+}
+
 int orc_num_threads(void) { return omp_get_max_threads(); }
 
 /* physical constants as used here, for tests */

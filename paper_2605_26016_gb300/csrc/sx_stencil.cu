@@ -1,16 +1,751 @@
-// Shared-memory halo stencil backend with the fused Heun step (placeholder until the kernel lands).
+// Stencil backend: the sparse-convolution realisation of the bilinear field
+//   b_a^alpha(R) = sum_b sum_delta sum_beta K_ab^{alpha beta}(delta) S_b^beta(R + delta)
+// ("Backend representations"), fused with the normalised Heun step of the
+// stochastic LLG equation ("Atomistic spin dynamics", "Stochastic LLG").
+//
+// GB300 design:
+//  * Lattice families fix the tap geometry at compile time (which (b, delta)
+//    taps exist and whether a tap is a scalar or a full 3x3 tensor); the J
+//    values are kernel parameters, so any Hamiltonian whose taps fit a family
+//    runs on it.  Families: simple cubic nearest neighbours, simple cubic
+//    3x3x3 cube (three distance shells), bcc as two sublattices with four
+//    distance shells.
+//  * A CTA owns a 32 x BY column tile and marches along z.  Each S^n plane is
+//    loaded once (FP64 from HBM, turned into FP32 with integer bit operations,
+//    staged in shared memory as float4) and every (source sublattice, dx, dy)
+//    group is read from shared memory once and pushed into per-thread register
+//    accumulators for every dz, so a site costs one LDS.128 per group instead
+//    of one per tap.
+//  * Heun fusion: the predictor runs on the tile plus an r-wide halo and keeps
+//    S~ in shared memory; the corrector runs on the interior.  HBM traffic per
+//    spin-step is one FP64 read and one FP64 write (48 B).  Thermal noise is
+//    drawn once per site and step and reused by the corrector.
+//  * Mixed precision: field, torque and predictor in FP32; the corrector's
+//    state sum S^n + dt/2 (f0 + f1) and its renormalisation in FP64 (GB300's
+//    FP64 pipe is ~1/70 of FP32, so conversions use integer bit operations and
+//    the FP64 pipe only runs the normalisation).
+#include <string.h>
+
+#include <new>
+#include <utility>
+
 #include "sx_internal.h"
+#include "sx_noise.cuh"
 
 namespace sx {
 
-int stencil_plan(sx_ctx *c) {
-  (void)c;
-  return set_error(SX_ERR_UNSUPPORTED, "stencil backend not built yet");
+// ------------------------------------------------------------------ families
+
+struct TapSpec {
+  int a, b, dx, dy, dz, tensor, coef;
+};
+
+template <int N>
+struct TapArr {
+  TapSpec t[N];
+  int n, niso, nten;
+};
+
+// Taps are ordered by (b, dy, dx, a, dz) so that one (b, dx, dy) group is one
+// shared-memory read that serves every target sublattice and every dz.
+template <int N, class Pred>
+constexpr TapArr<N> make_taps(int nsub, int R, Pred keep) {
+  TapArr<N> r{};
+  int n = 0, ni = 0, nt = 0;
+  for (int b = 0; b < nsub; ++b)
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx)
+        for (int a = 0; a < nsub; ++a)
+          for (int dz = -R; dz <= R; ++dz) {
+            const int k = keep(a, b, dx, dy, dz);  // 0: absent, 1: scalar, 2: tensor
+            if (!k) continue;
+            r.t[n] = TapSpec{a, b, dx, dy, dz, k == 2, k == 2 ? nt : ni};
+            if (k == 2)
+              ++nt;
+            else
+              ++ni;
+            ++n;
+          }
+  r.n = n;
+  r.niso = ni;
+  r.nten = nt;
+  return r;
 }
-void stencil_free(sx_ctx *c) { c->stencil = nullptr; }
-cudaError_t stencil_field(const sx_ctx *, const double *, double *, bool, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t stencil_heun_step(const sx_ctx *, const double *, double *, const HeunConst &, uint64_t, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+struct KeepSC6 {
+  int mode;
+  constexpr int operator()(int, int, int dx, int dy, int dz) const {
+    return dx * dx + dy * dy + dz * dz == 1 ? mode : 0;
+  }
+};
+struct KeepSC26 {
+  int mode;
+  constexpr int operator()(int, int, int dx, int dy, int dz) const {
+    const int d2 = dx * dx + dy * dy + dz * dz;
+    return d2 == 0 ? 0 : (d2 == 1 ? mode : 1);
+  }
+};
+// bcc conventional cell as sublattices at (0,0,0) and (1/2,1/2,1/2): squared bond
+// lengths in units of (a/2)^2 are 3, 4, 8, 11 for the first four shells
+struct KeepBCC4 {
+  constexpr int operator()(int a, int b, int dx, int dy, int dz) const {
+    const int o = b - a;
+    const int hx = 2 * dx + o, hy = 2 * dy + o, hz = 2 * dz + o;
+    const int d2 = hx * hx + hy * hy + hz * hz;
+    return (d2 == 3 || d2 == 4 || d2 == 8 || d2 == 11) ? 1 : 0;
+  }
+};
+
+enum FamilyId { FAM_SC6_ISO = 0, FAM_SC6_TEN, FAM_SC26_ISO, FAM_SC26_TEN, FAM_BCC4, FAM_COUNT };
+
+template <int ID>
+struct Family;
+template <>
+struct Family<FAM_SC6_ISO> {
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6;
+  static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC6{1});
+};
+template <>
+struct Family<FAM_SC6_TEN> {
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6;
+  static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC6{2});
+};
+template <>
+struct Family<FAM_SC26_ISO> {
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26;
+  static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{1});
+};
+template <>
+struct Family<FAM_SC26_TEN> {
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26;
+  static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{2});
+};
+template <>
+struct Family<FAM_BCC4> {
+  static constexpr int NSUB = 2, R = 2, BY = 16, NTAP = 100;
+  static constexpr TapArr<NTAP> L = make_taps<NTAP>(2, 2, KeepBCC4{});
+};
+
+constexpr int kMaxIso = 104;
+constexpr int kMaxTen = 8;
+
+// Per-launch arguments (passed by value, read from the kernel-parameter bank).
+struct StencilArgs {
+  int nx, ny, nz, px, py, pz;
+  int tz;  // output planes per CTA
+  int thermal;
+  long long nsite;
+  float Jiso[kMaxIso];
+  float Jt[kMaxTen][9];
+  float zee[2][3], twoK[2], axis[2][3], inv_mm[2], sigma[2];
+  float g, alpha, dt, hdt;
+  unsigned long long seed, step;
+  unsigned replica;
+};
+
+struct StencilPlan {
+  int family;
+  int tz;
+  StencilArgs base;
+};
+
+// ------------------------------------------------------------------ helpers
+
+template <class F, int I>
+struct TapAt {
+  static constexpr TapSpec s = F::L.t[I];
+  static constexpr TapSpec prev = F::L.t[I > 0 ? I - 1 : 0];
+  static constexpr int a = s.a, b = s.b, dx = s.dx, dy = s.dy, dz = s.dz, tensor = s.tensor, coef = s.coef;
+  static constexpr bool fresh = I == 0 || prev.b != b || prev.dx != dx || prev.dy != dy;
+};
+
+// FP64 -> FP32 by integer bit operations (round half up on the first dropped
+// bit; magnitudes below 2^-126 become zero).  Avoids the FP64 conversion pipe.
+__device__ __forceinline__ float f64_to_f32(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned a = hi & 0x7FFFFFFFu;
+  if (a < 0x38100000u) return 0.0f;
+  unsigned m = __funnelshift_l(lo, a - 0x38000000u, 3);
+  m += (lo >> 28) & 1u;
+  return __uint_as_float(m | (hi & 0x80000000u));
+}
+
+// FP32 -> FP64 by integer bit operations (exact for normal numbers; FP32
+// subnormals become zero).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned a = b & 0x7FFFFFFFu;
+  if (a < 0x00800000u) return 0.0;
+  const unsigned hi = (b & 0x80000000u) | ((a >> 3) + 0x38000000u);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+__device__ __forceinline__ int wrap_axis(int c, int n, int periodic, bool &ok) {
+  if (c >= 0 && c < n) return c;
+  if (!periodic) {
+    ok = false;
+    return 0;
+  }
+  c %= n;
+  return c < 0 ? c + n : c;
+}
+
+__device__ __forceinline__ void rhs32(const float s[3], const float B[3], float g, float alpha, float f[3]) {
+  const float t0 = s[1] * B[2] - s[2] * B[1];
+  const float t1 = s[2] * B[0] - s[0] * B[2];
+  const float t2 = s[0] * B[1] - s[1] * B[0];
+  const float u0 = s[1] * t2 - s[2] * t1;
+  const float u1 = s[2] * t0 - s[0] * t2;
+  const float u2 = s[0] * t1 - s[1] * t0;
+  f[0] = g * (t0 + alpha * u0);
+  f[1] = g * (t1 + alpha * u1);
+  f[2] = g * (t2 + alpha * u2);
+}
+
+// S' = N[S + d] in FP64 with d given in FP32.  x = S + d, eps = |x|^2 - 1,
+// c - 1 = t = eps (-1/2 + eps g(eps)) with g = 3/8 - 5/16 eps + 35/128 eps^2
+// (binomial series of (1+eps)^(-1/2)), S' = x + x t.
+__device__ __forceinline__ void renormalise64(const double S[3], const float d[3], double out[3]) {
+  const double x0 = S[0] + f32_to_f64(d[0]);
+  const double x1 = S[1] + f32_to_f64(d[1]);
+  const double x2 = S[2] + f32_to_f64(d[2]);
+  const double eps = fma(x0, x0, fma(x1, x1, fma(x2, x2, -1.0)));
+  const float e = f64_to_f32(eps);
+  const float gq = fmaf(e, fmaf(e, 0.2734375f, -0.3125f), 0.375f);
+  const double t = eps * fma(eps, f32_to_f64(gq), -0.5);
+  out[0] = fma(x0, t, x0);
+  out[1] = fma(x1, t, x1);
+  out[2] = fma(x2, t, x2);
+}
+
+// ------------------------------------------------------------------ geometry
+
+template <class F>
+struct G {
+  static constexpr int NS = F::NSUB, R = F::R, BY = F::BY;
+  static constexpr int BX = 32, NT = BX * BY, TX = BX - 2 * R, TY = BY - 2 * R;
+  static constexpr int LX = BX + 2 * R, LY = BY + 2 * R;
+  static constexpr int Q = R + 1;                   // ring depth (planes)
+  static constexpr int SN = NS * LY * LX;           // float4 per staged S^n plane
+  static constexpr int ST = NS * BY * BX;           // float4 per S~ plane
+  static constexpr int NLOAD = (SN + NT - 1) / NT;  // sites each thread stages per plane
+  static constexpr int ACC = 2 * R + 1;
+  static constexpr size_t SMEM = (size_t)Q * SN * 16 + (size_t)Q * ST * 16 + (size_t)Q * NS * NT * 24;
+};
+
+// accumulate one staged plane into acc[a][RZ - dz][c] for every tap
+template <class F, int I>
+__device__ __forceinline__ void tap_push(const StencilArgs &p, const float4 *__restrict__ base, int pitch_sub,
+                                         int pitch_row, float4 &v, float (&acc)[F::NSUB][2 * F::R + 1][3]) {
+  using t = TapAt<F, I>;
+  if constexpr (t::fresh) v = base[t::b * pitch_sub + t::dy * pitch_row + t::dx];
+  float *o = acc[t::a][F::R - t::dz];
+  if constexpr (t::tensor) {
+    const float *J = p.Jt[t::coef];
+    o[0] = fmaf(J[0], v.x, fmaf(J[1], v.y, fmaf(J[2], v.z, o[0])));
+    o[1] = fmaf(J[3], v.x, fmaf(J[4], v.y, fmaf(J[5], v.z, o[1])));
+    o[2] = fmaf(J[6], v.x, fmaf(J[7], v.y, fmaf(J[8], v.z, o[2])));
+  } else {
+    const float J = p.Jiso[t::coef];
+    o[0] = fmaf(J, v.x, o[0]);
+    o[1] = fmaf(J, v.y, o[1]);
+    o[2] = fmaf(J, v.z, o[2]);
+  }
+}
+
+template <class F, int... I>
+__device__ __forceinline__ void push_all(std::integer_sequence<int, I...>, const StencilArgs &p,
+                                         const float4 *__restrict__ base, int pitch_sub, int pitch_row,
+                                         float (&acc)[F::NSUB][2 * F::R + 1][3]) {
+  float4 v;
+  (tap_push<F, I>(p, base, pitch_sub, pitch_row, v, acc), ...);
+}
+
+template <class F>
+__device__ __forceinline__ void shift_acc(float (&acc)[F::NSUB][2 * F::R + 1][3]) {
+#pragma unroll
+  for (int a = 0; a < F::NSUB; ++a) {
+#pragma unroll
+    for (int j = 0; j < 2 * F::R; ++j) {
+      acc[a][j][0] = acc[a][j + 1][0];
+      acc[a][j][1] = acc[a][j + 1][1];
+      acc[a][j][2] = acc[a][j + 1][2];
+    }
+    acc[a][2 * F::R][0] = acc[a][2 * F::R][1] = acc[a][2 * F::R][2] = 0.0f;
+  }
+}
+
+// Stage plane q of S^n for the load region into registers (FP64), coalesced along x.
+template <class F>
+__device__ __forceinline__ void fetch_plane(const StencilArgs &p, const double *__restrict__ S, int x0, int y0,
+                                            int q, int tid, double (&pre)[G<F>::NLOAD][3]) {
+  using g = G<F>;
+  bool zok = true;
+  const int gz = wrap_axis(q, p.nz, p.pz, zok);
+#pragma unroll
+  for (int j = 0; j < g::NLOAD; ++j) {
+    const int e = tid + j * g::NT;
+    pre[j][0] = pre[j][1] = pre[j][2] = 0.0;
+    if (e < g::SN) {
+      const int s = e / (g::LX * g::LY);
+      const int r = e - s * (g::LX * g::LY);
+      const int row = r / g::LX, col = r - row * g::LX;
+      bool ok = zok;
+      const int gx = wrap_axis(x0 - 2 * g::R + col, p.nx, p.px, ok);
+      const int gy = wrap_axis(y0 - 2 * g::R + row, p.ny, p.py, ok);
+      if (ok) {
+        const long long i = (((long long)s * p.nz + gz) * p.ny + gy) * p.nx + gx;
+        pre[j][0] = __ldg(S + i);
+        pre[j][1] = __ldg(S + p.nsite + i);
+        pre[j][2] = __ldg(S + 2 * p.nsite + i);
+      }
+    }
+  }
+}
+
+template <class F>
+__device__ __forceinline__ void store_plane(float4 *__restrict__ dst, int tid, const double (&pre)[G<F>::NLOAD][3]) {
+  using g = G<F>;
+#pragma unroll
+  for (int j = 0; j < g::NLOAD; ++j) {
+    const int e = tid + j * g::NT;
+    if (e < g::SN) dst[e] = make_float4(f64_to_f32(pre[j][0]), f64_to_f32(pre[j][1]), f64_to_f32(pre[j][2]), 0.0f);
+  }
+}
+
+__device__ __forceinline__ void onsite32(const StencilArgs &p, int a, const float s[3], float b[3]) {
+  const float q = p.twoK[a] * (s[0] * p.axis[a][0] + s[1] * p.axis[a][1] + s[2] * p.axis[a][2]);
+  b[0] += p.zee[a][0] + q * p.axis[a][0];
+  b[1] += p.zee[a][1] + q * p.axis[a][1];
+  b[2] += p.zee[a][2] + q * p.axis[a][2];
+}
+
+// ------------------------------------------------------------------ fused Heun
+
+template <int FID>
+__global__ void __launch_bounds__(G<Family<FID>>::NT, 1)
+    k_heun_fused(const StencilArgs p, const double *__restrict__ Sin, double *__restrict__ Sout) {
+  using F = Family<FID>;
+  using g = G<F>;
+  constexpr int NS = F::NSUB, R = F::R, Q = g::Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *sn = reinterpret_cast<float4 *>(smem_raw);         // [Q][SN]
+  float4 *st = sn + Q * g::SN;                               // [Q][ST]
+  float *fq = reinterpret_cast<float *>(st + Q * g::ST);     // [Q][NS][6][NT]
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * g::TX, y0 = blockIdx.y * g::TY, z0 = blockIdx.z * p.tz;
+  const int tzc = min(p.tz, p.nz - z0);
+  // this thread's predictor column and whether it is an interior (output) column
+  const int cx = x0 - R + tx, cy = y0 - R + ty;
+  const bool inner = tx >= R && tx < 32 - R && ty >= R && ty < F::BY - R && cx < p.nx && cy < p.ny;
+  bool col_ok = true;
+  const int wx = wrap_axis(cx, p.nx, p.px, col_ok);
+  const int wy = wrap_axis(cy, p.ny, p.py, col_ok);
+
+  float accp[NS][2 * R + 1][3];
+  float accc[NS][2 * R + 1][3];
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int j = 0; j < 2 * R + 1; ++j) accp[a][j][0] = accp[a][j][1] = accp[a][j][2] = accc[a][j][0] =
+        accc[a][j][1] = accc[a][j][2] = 0.0f;
+
+  double pre[g::NLOAD][3];
+  double s64[NS][3];
+  const int niter = tzc + 4 * R;
+  fetch_plane<F>(p, Sin, x0, y0, z0 - 2 * R, tid, pre);
+
+  for (int k = 0; k < niter; ++k) {
+    const int q = z0 - 2 * R + k;
+    store_plane<F>(sn + (k % Q) * g::SN, tid, pre);
+    if (k + 1 < niter) fetch_plane<F>(p, Sin, x0, y0, q + 1, tid, pre);
+    const int kc = k - 4 * R;
+    const int c = z0 + kc;
+    const bool do_corr = inner && kc >= 0;
+    if (do_corr) {  // FP64 state of this corrector site (L2-resident: staged 2R planes ago)
+#pragma unroll
+      for (int a = 0; a < NS; ++a) {
+        const long long i = (((long long)a * p.nz + c) * p.ny + cy) * p.nx + cx;
+        s64[a][0] = __ldg(Sin + i);
+        s64[a][1] = __ldg(Sin + p.nsite + i);
+        s64[a][2] = __ldg(Sin + 2 * p.nsite + i);
+      }
+    }
+    __syncthreads();
+
+    // predictor field: push the staged plane q into the accumulators
+    {
+      const float4 *base = sn + (k % Q) * g::SN + (ty + R) * g::LX + (tx + R);
+      push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, g::LX * g::LY, g::LX, accp);
+    }
+    const int kp = k - 2 * R;
+    if (kp >= 0) {
+      // predictor at plane pz = q - R for every column of the 32 x BY region
+      const int pz = q - R;
+      bool ok = col_ok;
+      const int wz = wrap_axis(pz, p.nz, p.pz, ok);
+      const float4 *cen = sn + ((k - R) % Q) * g::SN + (ty + R) * g::LX + (tx + R);
+      float4 *out = st + (kp % Q) * g::ST + ty * 32 + tx;
+      float *fo = fq + (kp % Q) * (NS * 6 * g::NT) + tid;
+#pragma unroll
+      for (int a = 0; a < NS; ++a) {
+        float4 tilde = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ok) {
+          const float4 c4 = cen[a * g::LX * g::LY];
+          const float s[3] = {c4.x, c4.y, c4.z};
+          float b[3] = {accp[a][0][0], accp[a][0][1], accp[a][0][2]};
+          onsite32(p, a, s, b);
+          float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+          if (p.thermal) {
+            const unsigned long long site = (((unsigned long long)a * p.nz + wz) * p.ny + wy) * p.nx + wx;
+            normals3(p.seed, p.replica, site, p.step, e0, e1, e2);
+          }
+          const float sg = p.sigma[a], im = p.inv_mm[a];
+          const float B[3] = {fmaf(b[0], im, sg * e0), fmaf(b[1], im, sg * e1), fmaf(b[2], im, sg * e2)};
+          float f[3];
+          rhs32(s, B, p.g, p.alpha, f);
+          float x[3] = {fmaf(p.dt, f[0], s[0]), fmaf(p.dt, f[1], s[1]), fmaf(p.dt, f[2], s[2])};
+          const float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+          float r = rsqrtf(n2);
+          r = r * fmaf(-0.5f * n2, r * r, 1.5f);
+          tilde = make_float4(x[0] * r, x[1] * r, x[2] * r, 0.f);
+          if (inner) {
+            float *fa = fo + a * 6 * g::NT;
+            fa[0] = f[0];
+            fa[g::NT] = f[1];
+            fa[2 * g::NT] = f[2];
+            fa[3 * g::NT] = e0;
+            fa[4 * g::NT] = e1;
+            fa[5 * g::NT] = e2;
+          }
+        }
+        out[a * 32 * F::BY] = tilde;
+      }
+    }
+    shift_acc<F>(accp);
+    __syncthreads();
+
+    if (inner && kp >= 0) {
+      // corrector field: push the S~ plane just computed
+      const float4 *base = st + (kp % Q) * g::ST + ty * 32 + tx;
+      push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, 32 * F::BY, 32, accc);
+      if (kc >= 0 && kc < tzc) {
+        const int slot = (kc + R) % Q;
+        const float4 *cen = st + slot * g::ST + ty * 32 + tx;
+        const float *fi = fq + slot * (NS * 6 * g::NT) + tid;
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+          const float4 c4 = cen[a * 32 * F::BY];
+          const float s[3] = {c4.x, c4.y, c4.z};
+          float b[3] = {accc[a][0][0], accc[a][0][1], accc[a][0][2]};
+          onsite32(p, a, s, b);
+          const float *fa = fi + a * 6 * g::NT;
+          const float sg = p.sigma[a], im = p.inv_mm[a];
+          const float B[3] = {fmaf(b[0], im, sg * fa[3 * g::NT]), fmaf(b[1], im, sg * fa[4 * g::NT]),
+                              fmaf(b[2], im, sg * fa[5 * g::NT])};
+          float f[3];
+          rhs32(s, B, p.g, p.alpha, f);
+          const float d[3] = {p.hdt * (fa[0] + f[0]), p.hdt * (fa[g::NT] + f[1]), p.hdt * (fa[2 * g::NT] + f[2])};
+          double o[3];
+          renormalise64(s64[a], d, o);
+          const long long i = (((long long)a * p.nz + c) * p.ny + cy) * p.nx + cx;
+          Sout[i] = o[0];
+          Sout[p.nsite + i] = o[1];
+          Sout[2 * p.nsite + i] = o[2];
+        }
+      }
+      shift_acc<F>(accc);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ field only
+
+template <class F>
+struct GF {
+  static constexpr int NS = F::NSUB, R = F::R, BY = F::BY;
+  static constexpr int NT = 32 * BY, LX = 32 + 2 * R, LY = BY + 2 * R;
+  static constexpr int SN = NS * LY * LX;
+  static constexpr int NLOAD = (SN + NT - 1) / NT;
+  static constexpr size_t SMEM = 2 * (size_t)SN * 16 + (size_t)(R + 1) * NS * NT * 16;
+};
+
+// Reduced field of plane-marching tiles (32 x BY outputs); onsite adds Zeeman
+// and anisotropy.  Output FP64 (widened from the FP32 accumulators).
+template <int FID>
+__global__ void __launch_bounds__(GF<Family<FID>>::NT, 1)
+    k_field_stencil(const StencilArgs p, int onsite, const double *__restrict__ Sin, double *__restrict__ b) {
+  using F = Family<FID>;
+  using g = GF<F>;
+  constexpr int NS = F::NSUB, R = F::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *sn = reinterpret_cast<float4 *>(smem_raw);      // [2][SN]
+  float4 *cq = sn + 2 * g::SN;                            // [R+1][NS][NT] centre values
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * F::BY, z0 = blockIdx.z * p.tz;
+  const int tzc = min(p.tz, p.nz - z0);
+  const int cx = x0 + tx, cy = y0 + ty;
+  const bool mine = cx < p.nx && cy < p.ny;
+  float acc[NS][2 * R + 1][3];
+#pragma unroll
+  for (int a = 0; a < NS; ++a)
+#pragma unroll
+    for (int j = 0; j < 2 * R + 1; ++j) acc[a][j][0] = acc[a][j][1] = acc[a][j][2] = 0.0f;
+  // loads use the fused kernel's staging with the halo shifted by R
+  double pre[g::NLOAD][3];
+  auto fetch = [&](int q) {
+    bool zok = true;
+    const int gz = wrap_axis(q, p.nz, p.pz, zok);
+#pragma unroll
+    for (int j = 0; j < g::NLOAD; ++j) {
+      const int e = tid + j * g::NT;
+      pre[j][0] = pre[j][1] = pre[j][2] = 0.0;
+      if (e < g::SN) {
+        const int s = e / (g::LX * g::LY);
+        const int r = e - s * (g::LX * g::LY);
+        const int row = r / g::LX, col = r - row * g::LX;
+        bool ok = zok;
+        const int gx = wrap_axis(x0 - R + col, p.nx, p.px, ok);
+        const int gy = wrap_axis(y0 - R + row, p.ny, p.py, ok);
+        if (ok) {
+          const long long i = (((long long)s * p.nz + gz) * p.ny + gy) * p.nx + gx;
+          pre[j][0] = __ldg(Sin + i);
+          pre[j][1] = __ldg(Sin + p.nsite + i);
+          pre[j][2] = __ldg(Sin + 2 * p.nsite + i);
+        }
+      }
+    }
+  };
+  const int niter = tzc + 2 * R;
+  fetch(z0 - R);
+  for (int k = 0; k < niter; ++k) {
+    const int q = z0 - R + k;
+    float4 *buf = sn + (k & 1) * g::SN;
+#pragma unroll
+    for (int j = 0; j < g::NLOAD; ++j) {
+      const int e = tid + j * g::NT;
+      if (e < g::SN)
+        buf[e] = make_float4(f64_to_f32(pre[j][0]), f64_to_f32(pre[j][1]), f64_to_f32(pre[j][2]), 0.0f);
+    }
+    if (k + 1 < niter) fetch(q + 1);
+    __syncthreads();
+    const float4 *base = buf + (ty + R) * g::LX + (tx + R);
+    push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, g::LX * g::LY, g::LX, acc);
+    // keep this plane's centre values for the on-site terms R planes later
+#pragma unroll
+    for (int a = 0; a < NS; ++a) cq[((k % (R + 1)) * NS + a) * g::NT + tid] = base[a * g::LX * g::LY];
+    const int kc = k - 2 * R;
+    if (mine && kc >= 0) {
+      const int c = z0 + kc;
+#pragma unroll
+      for (int a = 0; a < NS; ++a) {
+        float v[3] = {acc[a][0][0], acc[a][0][1], acc[a][0][2]};
+        if (onsite) {
+          const float4 c4 = cq[(((k - R) % (R + 1)) * NS + a) * g::NT + tid];
+          const float s[3] = {c4.x, c4.y, c4.z};
+          onsite32(p, a, s, v);
+        }
+        const long long i = (((long long)a * p.nz + c) * p.ny + cy) * p.nx + cx;
+        b[i] = (double)v[0];
+        b[p.nsite + i] = (double)v[1];
+        b[2 * p.nsite + i] = (double)v[2];
+      }
+    }
+    shift_acc<F>(acc);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ planning
+
+namespace {
+
+template <int FID>
+bool match_family(const sx_ctx *c, StencilArgs &a) {
+  using F = Family<FID>;
+  if (c->lat.nsub != F::NSUB) return false;
+  for (int k = 0; k < kMaxIso; ++k) a.Jiso[k] = 0.0f;
+  for (int k = 0; k < kMaxTen; ++k)
+    for (int m = 0; m < 9; ++m) a.Jt[k][m] = 0.0f;
+  for (int s = 0; s < F::NSUB; ++s) {
+    for (const Tap &t : c->taps[s]) {
+      int hit = -1;
+      for (int i = 0; i < F::L.n; ++i) {
+        const TapSpec &f = F::L.t[i];
+        if (f.a == s && f.b == t.b && f.dx == t.d[0] && f.dy == t.d[1] && f.dz == t.d[2]) {
+          hit = i;
+          break;
+        }
+      }
+      if (hit < 0) return false;
+      const TapSpec &f = F::L.t[hit];
+      const bool iso = t.J[1] == 0.0 && t.J[2] == 0.0 && t.J[3] == 0.0 && t.J[5] == 0.0 && t.J[6] == 0.0 &&
+                       t.J[7] == 0.0 && t.J[0] == t.J[4] && t.J[4] == t.J[8];
+      if (f.tensor) {
+        for (int m = 0; m < 9; ++m) a.Jt[f.coef][m] = (float)t.J[m];
+      } else {
+        if (!iso) return false;
+        a.Jiso[f.coef] = (float)t.J[0];
+      }
+    }
+  }
+  return true;
+}
+
+template <int FID>
+cudaError_t set_smem() {
+  cudaError_t e = cudaFuncSetAttribute(k_heun_fused<FID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)G<Family<FID>>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_field_stencil<FID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)GF<Family<FID>>::SMEM);
+}
+
+template <int FID>
+cudaError_t launch_heun(const StencilPlan &sp, const StencilArgs &a, const double *src, double *dst,
+                        cudaStream_t st) {
+  using g = G<Family<FID>>;
+  const dim3 grid((a.nx + g::TX - 1) / g::TX, (a.ny + g::TY - 1) / g::TY, (a.nz + sp.tz - 1) / sp.tz);
+  k_heun_fused<FID><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, src, dst);
+  return cudaGetLastError();
+}
+
+template <int FID>
+cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &a, int onsite, const double *S, double *b,
+                         cudaStream_t st) {
+  using g = GF<Family<FID>>;
+  const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, (a.nz + sp.tz - 1) / sp.tz);
+  k_field_stencil<FID><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, onsite, S, b);
+  return cudaGetLastError();
+}
+
+template <int FID>
+int tiles_xy(const sx_ctx *c) {
+  using g = G<Family<FID>>;
+  return ((c->geo.nx + g::TX - 1) / g::TX) * ((c->geo.ny + g::TY - 1) / g::TY);
+}
+
+int family_radius(int fam) {
+  switch (fam) {
+    case FAM_BCC4: return 2;
+    default: return 1;
+  }
+}
+
+}  // namespace
+
+int stencil_plan(sx_ctx *c) {
+  if (c->prec != SX_PREC_FP32)
+    return set_error(SX_ERR_UNSUPPORTED, "the stencil backend computes the field in FP32 (use gather for FP64)");
+  StencilPlan *sp = new (std::nothrow) StencilPlan();
+  if (!sp) return set_error(SX_ERR_OOM, "host allocation failed");
+  StencilArgs &a = sp->base;
+  memset(&a, 0, sizeof(a));
+  int fam = -1;
+  if (match_family<FAM_SC6_ISO>(c, a))
+    fam = FAM_SC6_ISO;
+  else if (match_family<FAM_SC6_TEN>(c, a))
+    fam = FAM_SC6_TEN;
+  else if (match_family<FAM_SC26_ISO>(c, a))
+    fam = FAM_SC26_ISO;
+  else if (match_family<FAM_SC26_TEN>(c, a))
+    fam = FAM_SC26_TEN;
+  else if (match_family<FAM_BCC4>(c, a))
+    fam = FAM_BCC4;
+  if (fam < 0) {
+    delete sp;
+    return set_error(SX_ERR_UNSUPPORTED,
+                     "no stencil family holds these taps (families: SC nearest neighbours, SC 3x3x3 cube, bcc four "
+                     "shells); use the gather backend");
+  }
+  sp->family = fam;
+  a.nx = c->geo.nx;
+  a.ny = c->geo.ny;
+  a.nz = c->geo.nz;
+  a.px = c->geo.px;
+  a.py = c->geo.py;
+  a.pz = c->geo.pz;
+  a.nsite = c->geo.nsite;
+  for (int s = 0; s < c->lat.nsub && s < 2; ++s) {
+    for (int k = 0; k < 3; ++k) {
+      a.zee[s][k] = (float)c->onsite.zee[s][k];
+      a.axis[s][k] = (float)c->onsite.axis[s][k];
+    }
+    a.twoK[s] = (float)c->onsite.twoK[s];
+    a.inv_mm[s] = (float)c->onsite.inv_mm[s];
+  }
+  // z chunk: enough CTAs to fill the GPU a few times over, at least 8 planes
+  int txy = 0;
+  switch (fam) {
+    case FAM_SC6_ISO: txy = tiles_xy<FAM_SC6_ISO>(c); break;
+    case FAM_SC6_TEN: txy = tiles_xy<FAM_SC6_TEN>(c); break;
+    case FAM_SC26_ISO: txy = tiles_xy<FAM_SC26_ISO>(c); break;
+    case FAM_SC26_TEN: txy = tiles_xy<FAM_SC26_TEN>(c); break;
+    default: txy = tiles_xy<FAM_BCC4>(c); break;
+  }
+  const int R = family_radius(fam);
+  int nchunk = (4 * 152 + txy - 1) / txy;
+  int tz = (c->geo.nz + nchunk - 1) / nchunk;
+  if (tz < 8 * R) tz = 8 * R;
+  if (tz > c->geo.nz) tz = c->geo.nz;
+  sp->tz = tz;
+  a.tz = tz;
+  cudaError_t e;
+  switch (fam) {
+    case FAM_SC6_ISO: e = set_smem<FAM_SC6_ISO>(); break;
+    case FAM_SC6_TEN: e = set_smem<FAM_SC6_TEN>(); break;
+    case FAM_SC26_ISO: e = set_smem<FAM_SC26_ISO>(); break;
+    case FAM_SC26_TEN: e = set_smem<FAM_SC26_TEN>(); break;
+    default: e = set_smem<FAM_BCC4>(); break;
+  }
+  if (e != cudaSuccess) {
+    delete sp;
+    return cuda_error(e, "cudaFuncSetAttribute");
+  }
+  c->stencil = sp;
+  c->launches_per_step = 1;
+  return SX_OK;
+}
+
+void stencil_free(sx_ctx *c) {
+  delete c->stencil;
+  c->stencil = nullptr;
+}
+
+int stencil_family(const sx_ctx *c) { return c->stencil ? c->stencil->family : -1; }
+
+cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st) {
+  const StencilPlan &sp = *c->stencil;
+  switch (sp.family) {
+    case FAM_SC6_ISO: return launch_field<FAM_SC6_ISO>(sp, sp.base, onsite, S, b, st);
+    case FAM_SC6_TEN: return launch_field<FAM_SC6_TEN>(sp, sp.base, onsite, S, b, st);
+    case FAM_SC26_ISO: return launch_field<FAM_SC26_ISO>(sp, sp.base, onsite, S, b, st);
+    case FAM_SC26_TEN: return launch_field<FAM_SC26_TEN>(sp, sp.base, onsite, S, b, st);
+    default: return launch_field<FAM_BCC4>(sp, sp.base, onsite, S, b, st);
+  }
+}
+
+cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
+                              cudaStream_t st) {
+  const StencilPlan &sp = *c->stencil;
+  StencilArgs a = sp.base;
+  a.g = (float)h.g;
+  a.alpha = (float)h.alpha;
+  a.dt = (float)h.dt;
+  a.hdt = (float)(0.5 * h.dt);
+  a.thermal = h.thermal;
+  for (int s = 0; s < c->lat.nsub && s < 2; ++s) a.sigma[s] = (float)h.sigma[s];
+  a.seed = h.seed;
+  a.replica = h.replica;
+  a.step = step;
+  switch (sp.family) {
+    case FAM_SC6_ISO: return launch_heun<FAM_SC6_ISO>(sp, a, src, dst, st);
+    case FAM_SC6_TEN: return launch_heun<FAM_SC6_TEN>(sp, a, src, dst, st);
+    case FAM_SC26_ISO: return launch_heun<FAM_SC26_ISO>(sp, a, src, dst, st);
+    case FAM_SC26_TEN: return launch_heun<FAM_SC26_TEN>(sp, a, src, dst, st);
+    default: return launch_heun<FAM_BCC4>(sp, a, src, dst, st);
+  }
 }
 
 }  // namespace sx

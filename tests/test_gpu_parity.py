@@ -63,11 +63,21 @@ def _bonds_extra(s, m):
 
 CASES = [
     ("bcc_4shell", (13, 11, 9), (1, 1, 0), None),
-    ("bcc_4shell", (10, 7, 12), (0, 1, 1), _bonds_extra),
+    ("bcc_4shell", (10, 7, 12), (0, 1, 1), _bonds_extra),   # general tensors: no stencil family
     ("sc_j123_dmi", (17, 12, 10), None, None),
     ("sc_j123", (20, 9, 11), None, None),
     ("sc_nn", (33, 5, 7), None, None),
+    ("bcc_4shell", (40, 30, 20), (1, 0, 1), None),            # several x/y tiles and z chunks
+    ("sc_j123", (70, 40, 25), (0, 1, 1), None),
+    ("sc_j123_dmi", (31, 29, 33), (1, 1, 0), None),
 ]
+STENCIL_OK = {0, 2, 3, 4, 5, 6, 7}
+PATHS = [("gather", "fp64"), ("gather", "fp32"), ("stencil", "fp32")]
+
+
+def _skip_unsupported(backend, case):
+    if backend == "stencil" and case not in STENCIL_OK:
+        pytest.skip("Hamiltonian outside the stencil families (checked by test_stencil_rejects)")
 
 
 # ---------------------------------------------------------------- noise
@@ -85,10 +95,10 @@ def test_noise_bit_equal(seed, replica, site0, n, step):
 
 # ---------------------------------------------------------------- field / energy / torque
 
-@pytest.mark.parametrize("backend", ["gather"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("backend,prec", PATHS)
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_field_energy_torque(backend, prec, case):
+    _skip_unsupported(backend, case)
     name, n, pbc, extra = CASES[case]
     s, m, w = pair(name, n, pbc, extra)
     s.plan(backend, prec)
@@ -113,11 +123,11 @@ def test_field_energy_torque(backend, prec, case):
 
 # ---------------------------------------------------------------- Heun
 
-@pytest.mark.parametrize("backend", ["gather"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", [0, 1, 2])
+@pytest.mark.parametrize("backend,prec", PATHS)
+@pytest.mark.parametrize("case", [0, 1, 2, 4, 5, 6, 7])
 @pytest.mark.parametrize("thermal", [False, True])
 def test_heun_step(backend, prec, case, thermal):
+    _skip_unsupported(backend, case)
     name, n, pbc, extra = CASES[case]
     s, m, w = pair(name, n, pbc, extra)
     s.plan(backend, prec)
@@ -197,7 +207,39 @@ def test_bad_arguments_on_device_calls():
 
 # ---------------------------------------------------------------- full size, sampled
 
-@pytest.mark.parametrize("backend,prec", [("gather", "fp32"), ("gather", "fp64")])
+def test_stencil_rejects_what_it_cannot_hold():
+    s, m, w = pair(*CASES[1][:3], extra=CASES[1][3])
+    with pytest.raises(sx.SxError) as e:
+        s.plan("stencil", "fp32")
+    assert e.value.code == sx.SX_ERR_UNSUPPORTED
+    s2, _, _ = pair("bcc_4shell", (8, 8, 8))
+    with pytest.raises(sx.SxError) as e:
+        s2.plan("stencil", "fp64")
+    assert e.value.code == sx.SX_ERR_UNSUPPORTED
+    assert s2.plan("stencil", "fp32")["launches_per_step"] == 1
+
+
+def test_stencil_host_entry_and_in_place_entry_agree():
+    s, m, w = pair("sc_j123_dmi", (24, 20, 18))
+    s.plan("stencil", "fp32")
+    S = random_spins(1, (24, 20, 18), 19)
+    Sd = dev(S)
+    s.heun(Sd, torch.empty_like(Sd), dt=0.1, alpha=0.1, T=50.0, seed=8, step0=2, nsteps=5)
+    Sh = torch.from_numpy(S.copy()).pin_memory()
+    s.heun_host(Sh, dt=0.1, alpha=0.1, T=50.0, seed=8, step0=2, nsteps=5)
+    torch.cuda.synchronize()
+    assert torch.equal(Sd.cpu(), Sh)
+    out = torch.empty_like(Sd)
+    S0 = dev(S)
+    sx.sx_llg_heun_step_out(s.ctx, S0, out, sx.llg_params(0.1, 0.1, 50.0, 8), 2, s.nsite)
+    torch.cuda.synchronize()
+    assert torch.equal(S0.cpu(), torch.from_numpy(S))       # input untouched
+    one = dev(S)
+    s.heun(one, torch.empty_like(one), dt=0.1, alpha=0.1, T=50.0, seed=8, step0=2, nsteps=1)
+    assert torch.equal(out, one)
+
+
+@pytest.mark.parametrize("backend,prec", [("gather", "fp32"), ("gather", "fp64"), ("stencil", "fp32")])
 def test_full_size_bcc_sampled_field(backend, prec):
     n = (128, 128, 128)
     s, w = sx.system_from_workload("bcc_4shell", n)
@@ -210,3 +252,27 @@ def test_full_size_bcc_sampled_field(backend, prec):
     ref = m.field_sites(S, sites)
     got = b[:, sites].T
     assert normwise(got.T, ref.T) <= TOL_FIELD[prec]
+
+
+@pytest.mark.parametrize("name,n", [("bcc_4shell", (128, 128, 128)), ("sc_j123_dmi", (256, 256, 256))])
+def test_full_size_step_sampled_heun(name, n):
+    # the launch bench.py times (stencil, FP32 field / FP64 state, stochastic, one step out of place),
+    # checked at sampled sites against the oracle's site-by-site Heun step
+    s, w = sx.system_from_workload(name, n)
+    s.plan("stencil", "fp32")
+    S = random_spins(s.nsub, n, w["seed"])
+    Sd = dev(S)
+    out = torch.empty_like(Sd)
+    sx.sx_llg_heun_step_out(s.ctx, Sd, out, sx.llg_params(w["dt"], w["alpha"], w["T"], seed=w["seed"]), 10, s.nsite)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(3, -1)
+    m, _ = oracle_model(name, n, build=False)
+    rng = np.random.default_rng(1)
+    ncell = n[0] * n[1] * n[2]
+    sites = np.unique(np.concatenate([rng.choice(s.nsite, 600, replace=False),
+                                      [0, s.nsite - 1, ncell - 1, min(ncell, s.nsite - 1)]]))
+    ref = m.heun_sites(S, sites, w["dt"], w["alpha"], T=w["T"], seed=w["seed"], replica=0, step=10)
+    S0 = S.reshape(3, -1)[:, sites]
+    assert normwise(got[:, sites] - S0, ref.T - S0) <= TOL_STEP["fp32"]
+    norms = out.view(3, -1).pow(2).sum(0).sqrt()
+    assert (norms - 1).abs().max().item() < 1e-13

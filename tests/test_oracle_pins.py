@@ -321,6 +321,17 @@ def test_philox_words_uniform():
     assert abs(bits.mean() - 0.5) < 5 * 0.5 / math.sqrt(bits.size)
 
 
+@pytest.mark.parametrize("name,n,pbc", [("bcc_4shell", (5, 4, 6), (1, 0, 1)), ("sc_j123_dmi", (6, 5, 4), None)])
+def test_heun_at_sites_equals_full_step(name, n, pbc):
+    # the sampled-site Heun step (used for checks at full lattice size) is the same arithmetic as a full step
+    m, w = oracle_model(name, n, pbc=pbc)
+    S = random_spins(m.nsub, n, 44)
+    full = m.heun(S, w["dt"], w["alpha"], T=w["T"] or 30.0, seed=5, replica=2, step0=17, nsteps=1).reshape(3, -1)
+    sites = np.arange(m.nsite)
+    part = m.heun_sites(S, sites, w["dt"], w["alpha"], T=w["T"] or 30.0, seed=5, replica=2, step=17)
+    assert np.array_equal(part.T, full)
+
+
 def test_stochastic_step_uses_same_noise_in_both_stages():
     # with J = 0 one stochastic Heun step of a single spin equals the deterministic Heun step in the
     # constant field B_ext + sigma*eta (eta from the site/step counter), which is only true if the
