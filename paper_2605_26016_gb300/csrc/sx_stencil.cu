@@ -102,27 +102,27 @@ template <int ID>
 struct Family;
 template <>
 struct Family<FAM_SC6_ISO> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC6{1});
 };
 template <>
 struct Family<FAM_SC6_TEN> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC6{2});
 };
 template <>
 struct Family<FAM_SC26_ISO> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{1});
 };
 template <>
 struct Family<FAM_SC26_TEN> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{2});
 };
 template <>
 struct Family<FAM_BCC4> {
-  static constexpr int NSUB = 2, R = 2, BY = 16, NTAP = 100;
+  static constexpr int NSUB = 2, R = 2, BY = 16, NTAP = 100, MINB = 1;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(2, 2, KeepBCC4{});
 };
 
@@ -218,6 +218,20 @@ __device__ __forceinline__ void renormalise64(const double S[3], const float d[3
   out[2] = fma(x2, t, x2);
 }
 
+// ------------------------------------------------------------------ async copies
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// 8-byte global -> shared copy that zero-fills when !ok (no global read then)
+__device__ __forceinline__ void cp_async8(unsigned dst, const void *src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // ------------------------------------------------------------------ geometry
 
 template <class F>
@@ -226,14 +240,20 @@ struct G {
   static constexpr int BX = 32, NT = BX * BY, TX = BX - 2 * R, TY = BY - 2 * R;
   static constexpr int LX = BX + 2 * R, LY = BY + 2 * R;
   static constexpr int Q = R + 1;                   // ring depth (planes)
-  static constexpr int SN = NS * LY * LX;           // float4 per staged S^n plane
-  static constexpr int ST = NS * BY * BX;           // float4 per S~ plane
-  static constexpr int NLOAD = (SN + NT - 1) / NT;  // sites each thread stages per plane
-  static constexpr int ACC = 2 * R + 1;
-  static constexpr size_t SMEM = (size_t)Q * SN * 16 + (size_t)Q * ST * 16 + (size_t)Q * NS * NT * 24;
+  static constexpr int SN = NS * LY * LX;           // sites per staged S^n plane (load region)
+  static constexpr int ST = NS * BY * BX;           // sites per S~ plane (predictor region)
+  static constexpr int NI = TX * TY;                // interior (output) columns
+  static constexpr int NLOAD = (SN + NT - 1) / NT;  // load-region sites per thread
+  // shared memory: S^n ring (float4), S~ ring (float4), f0/eta ring, FP64 staging of the next plane, FP64
+  // state of this iteration's corrector sites
+  static constexpr size_t OFF_ST = (size_t)Q * SN * 16;
+  static constexpr size_t OFF_FQ = OFF_ST + (size_t)Q * ST * 16;
+  static constexpr size_t OFF_STAGE = OFF_FQ + (size_t)Q * NS * 6 * NI * 4;
+  static constexpr size_t OFF_S64 = OFF_STAGE + (size_t)3 * SN * 8;
+  static constexpr size_t SMEM = OFF_S64 + (size_t)NS * 3 * NI * 8;
 };
 
-// accumulate one staged plane into acc[a][RZ - dz][c] for every tap
+// accumulate one staged plane into acc[a][R - dz][c] for every tap
 template <class F, int I>
 __device__ __forceinline__ void tap_push(const StencilArgs &p, const float4 *__restrict__ base, int pitch_sub,
                                          int pitch_row, float4 &v, float (&acc)[F::NSUB][2 * F::R + 1][3]) {
@@ -275,41 +295,57 @@ __device__ __forceinline__ void shift_acc(float (&acc)[F::NSUB][2 * F::R + 1][3]
   }
 }
 
-// Stage plane q of S^n for the load region into registers (FP64), coalesced along x.
-template <class F>
-__device__ __forceinline__ void fetch_plane(const StencilArgs &p, const double *__restrict__ S, int x0, int y0,
-                                            int q, int tid, double (&pre)[G<F>::NLOAD][3]) {
-  using g = G<F>;
-  bool zok = true;
-  const int gz = wrap_axis(q, p.nz, p.pz, zok);
+// In-plane part of the global index of the load-region sites this thread stages
+// (x and y wrapped once here; the plane term is added per z step).
+template <int NLOAD, int NT, int SN, int LX, int LY>
+__device__ __forceinline__ void load_offsets(const StencilArgs &p, int xs, int ys, int tid, long long (&off)[NLOAD],
+                                             unsigned &okmask) {
+  okmask = 0u;
 #pragma unroll
-  for (int j = 0; j < g::NLOAD; ++j) {
-    const int e = tid + j * g::NT;
-    pre[j][0] = pre[j][1] = pre[j][2] = 0.0;
-    if (e < g::SN) {
-      const int s = e / (g::LX * g::LY);
-      const int r = e - s * (g::LX * g::LY);
-      const int row = r / g::LX, col = r - row * g::LX;
-      bool ok = zok;
-      const int gx = wrap_axis(x0 - 2 * g::R + col, p.nx, p.px, ok);
-      const int gy = wrap_axis(y0 - 2 * g::R + row, p.ny, p.py, ok);
-      if (ok) {
-        const long long i = (((long long)s * p.nz + gz) * p.ny + gy) * p.nx + gx;
-        pre[j][0] = __ldg(S + i);
-        pre[j][1] = __ldg(S + p.nsite + i);
-        pre[j][2] = __ldg(S + 2 * p.nsite + i);
-      }
+  for (int j = 0; j < NLOAD; ++j) {
+    const int e = tid + j * NT;
+    off[j] = 0;
+    if (e < SN) {
+      const int s = e / (LX * LY);
+      const int r = e - s * (LX * LY);
+      const int row = r / LX, col = r - row * LX;
+      bool ok = true;
+      const int gx = wrap_axis(xs + col, p.nx, p.px, ok);
+      const int gy = wrap_axis(ys + row, p.ny, p.py, ok);
+      off[j] = (long long)s * p.nz * p.ny * p.nx + (long long)gy * p.nx + gx;
+      if (ok) okmask |= 1u << j;
     }
   }
 }
 
-template <class F>
-__device__ __forceinline__ void store_plane(float4 *__restrict__ dst, int tid, const double (&pre)[G<F>::NLOAD][3]) {
-  using g = G<F>;
+// Issue the zero-filling async copies of plane q into the FP64 staging area.
+template <int NLOAD, int NT, int SN>
+__device__ __forceinline__ void issue_plane(const StencilArgs &p, const double *__restrict__ S, int q, int tid,
+                                            const long long (&off)[NLOAD], unsigned okmask, double *stage) {
+  bool zok = true;
+  const int gz = wrap_axis(q, p.nz, p.pz, zok);
+  const long long zoff = (long long)gz * p.ny * p.nx;
 #pragma unroll
-  for (int j = 0; j < g::NLOAD; ++j) {
-    const int e = tid + j * g::NT;
-    if (e < g::SN) dst[e] = make_float4(f64_to_f32(pre[j][0]), f64_to_f32(pre[j][1]), f64_to_f32(pre[j][2]), 0.0f);
+  for (int j = 0; j < NLOAD; ++j) {
+    const int e = tid + j * NT;
+    if (e < SN) {
+      const bool ok = zok && ((okmask >> j) & 1u);
+      const double *src = ok ? S + off[j] + zoff : S;
+      cp_async8(smem_addr(stage + e), src, ok);
+      cp_async8(smem_addr(stage + SN + e), ok ? src + p.nsite : S, ok);
+      cp_async8(smem_addr(stage + 2 * SN + e), ok ? src + 2 * p.nsite : S, ok);
+    }
+  }
+}
+
+// Turn this thread's staged FP64 sites into FP32 float4 (integer conversion).
+template <int NLOAD, int NT, int SN>
+__device__ __forceinline__ void convert_plane(const double *stage, float4 *dst, int tid) {
+#pragma unroll
+  for (int j = 0; j < NLOAD; ++j) {
+    const int e = tid + j * NT;
+    if (e < SN)
+      dst[e] = make_float4(f64_to_f32(stage[e]), f64_to_f32(stage[SN + e]), f64_to_f32(stage[2 * SN + e]), 0.0f);
   }
 }
 
@@ -322,56 +358,71 @@ __device__ __forceinline__ void onsite32(const StencilArgs &p, int a, const floa
 
 // ------------------------------------------------------------------ fused Heun
 
+// One normalised Heun step from Sin to Sout.  Per z iteration k (plane q = z0 - 2R + k):
+//   1. this thread's staged copy of plane q lands -> FP32 ring slot; the copies of plane q+1 and
+//      of the FP64 state of the corrector sites are issued (asynchronous, no registers held);
+//   2. plane q is pushed into the predictor accumulators; the predictor of plane q - R runs on the
+//      whole 32 x BY region (tile + halo) and writes S~ and, for interior columns, f0 and eta;
+//   3. interior columns push S~ of plane q - R into the corrector accumulators and finish the
+//      corrector of plane q - 2R in FP64.
 template <int FID>
-__global__ void __launch_bounds__(G<Family<FID>>::NT, 1)
+__global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINB)
     k_heun_fused(const StencilArgs p, const double *__restrict__ Sin, double *__restrict__ Sout) {
   using F = Family<FID>;
   using g = G<F>;
   constexpr int NS = F::NSUB, R = F::R, Q = g::Q;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *sn = reinterpret_cast<float4 *>(smem_raw);         // [Q][SN]
-  float4 *st = sn + Q * g::SN;                               // [Q][ST]
-  float *fq = reinterpret_cast<float *>(st + Q * g::ST);     // [Q][NS][6][NT]
+  float4 *sn = reinterpret_cast<float4 *>(smem_raw);                 // [Q][SN]
+  float4 *st = reinterpret_cast<float4 *>(smem_raw + g::OFF_ST);     // [Q][ST]
+  float *fq = reinterpret_cast<float *>(smem_raw + g::OFF_FQ);       // [Q][NS][6][NI]
+  double *stage = reinterpret_cast<double *>(smem_raw + g::OFF_STAGE);  // [3][SN]
+  double *s64 = reinterpret_cast<double *>(smem_raw + g::OFF_S64);   // [NS][3][NI]
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int x0 = blockIdx.x * g::TX, y0 = blockIdx.y * g::TY, z0 = blockIdx.z * p.tz;
   const int tzc = min(p.tz, p.nz - z0);
-  // this thread's predictor column and whether it is an interior (output) column
-  const int cx = x0 - R + tx, cy = y0 - R + ty;
+  const int cx = x0 - R + tx, cy = y0 - R + ty;  // this thread's predictor column
   const bool inner = tx >= R && tx < 32 - R && ty >= R && ty < F::BY - R && cx < p.nx && cy < p.ny;
+  const int ii = (ty - R) * g::TX + (tx - R);    // interior index (valid when inner)
   bool col_ok = true;
   const int wx = wrap_axis(cx, p.nx, p.px, col_ok);
   const int wy = wrap_axis(cy, p.ny, p.py, col_ok);
+  const long long plane = (long long)p.ny * p.nx, subvol = (long long)p.nz * plane;
+
+  long long off[g::NLOAD];
+  unsigned okmask;
+  load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(p, x0 - 2 * R, y0 - 2 * R, tid, off, okmask);
 
   float accp[NS][2 * R + 1][3];
   float accc[NS][2 * R + 1][3];
 #pragma unroll
   for (int a = 0; a < NS; ++a)
 #pragma unroll
-    for (int j = 0; j < 2 * R + 1; ++j) accp[a][j][0] = accp[a][j][1] = accp[a][j][2] = accc[a][j][0] =
-        accc[a][j][1] = accc[a][j][2] = 0.0f;
+    for (int j = 0; j < 2 * R + 1; ++j)
+      accp[a][j][0] = accp[a][j][1] = accp[a][j][2] = accc[a][j][0] = accc[a][j][1] = accc[a][j][2] = 0.0f;
 
-  double pre[g::NLOAD][3];
-  double s64[NS][3];
   const int niter = tzc + 4 * R;
-  fetch_plane<F>(p, Sin, x0, y0, z0 - 2 * R, tid, pre);
+  issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, z0 - 2 * R, tid, off, okmask, stage);
+  cp_commit();
 
   for (int k = 0; k < niter; ++k) {
     const int q = z0 - 2 * R + k;
-    store_plane<F>(sn + (k % Q) * g::SN, tid, pre);
-    if (k + 1 < niter) fetch_plane<F>(p, Sin, x0, y0, q + 1, tid, pre);
-    const int kc = k - 4 * R;
+    cp_wait<0>();
+    convert_plane<g::NLOAD, g::NT, g::SN>(stage, sn + (k % Q) * g::SN, tid);
+    const int kp = k - 2 * R, kc = k - 4 * R;
     const int c = z0 + kc;
-    const bool do_corr = inner && kc >= 0;
-    if (do_corr) {  // FP64 state of this corrector site (L2-resident: staged 2R planes ago)
+    if (inner && kc >= 0) {  // FP64 state of this corrector site (staged 2R planes ago: L2-resident)
 #pragma unroll
       for (int a = 0; a < NS; ++a) {
-        const long long i = (((long long)a * p.nz + c) * p.ny + cy) * p.nx + cx;
-        s64[a][0] = __ldg(Sin + i);
-        s64[a][1] = __ldg(Sin + p.nsite + i);
-        s64[a][2] = __ldg(Sin + 2 * p.nsite + i);
+        const double *src = Sin + a * subvol + c * plane + (long long)cy * p.nx + cx;
+        cp_async8(smem_addr(s64 + (a * 3 + 0) * g::NI + ii), src, true);
+        cp_async8(smem_addr(s64 + (a * 3 + 1) * g::NI + ii), src + p.nsite, true);
+        cp_async8(smem_addr(s64 + (a * 3 + 2) * g::NI + ii), src + 2 * p.nsite, true);
       }
     }
+    cp_commit();
+    if (k + 1 < niter) issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, q + 1, tid, off, okmask, stage);
+    cp_commit();
     __syncthreads();
 
     // predictor field: push the staged plane q into the accumulators
@@ -379,7 +430,6 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, 1)
       const float4 *base = sn + (k % Q) * g::SN + (ty + R) * g::LX + (tx + R);
       push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, g::LX * g::LY, g::LX, accp);
     }
-    const int kp = k - 2 * R;
     if (kp >= 0) {
       // predictor at plane pz = q - R for every column of the 32 x BY region
       const int pz = q - R;
@@ -387,7 +437,7 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, 1)
       const int wz = wrap_axis(pz, p.nz, p.pz, ok);
       const float4 *cen = sn + ((k - R) % Q) * g::SN + (ty + R) * g::LX + (tx + R);
       float4 *out = st + (kp % Q) * g::ST + ty * 32 + tx;
-      float *fo = fq + (kp % Q) * (NS * 6 * g::NT) + tid;
+      float *fo = fq + (kp % Q) * (NS * 6 * g::NI) + ii;
 #pragma unroll
       for (int a = 0; a < NS; ++a) {
         float4 tilde = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -398,26 +448,26 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, 1)
           onsite32(p, a, s, b);
           float e0 = 0.f, e1 = 0.f, e2 = 0.f;
           if (p.thermal) {
-            const unsigned long long site = (((unsigned long long)a * p.nz + wz) * p.ny + wy) * p.nx + wx;
+            const unsigned long long site = (unsigned long long)(a * subvol + wz * plane + (long long)wy * p.nx + wx);
             normals3(p.seed, p.replica, site, p.step, e0, e1, e2);
           }
           const float sg = p.sigma[a], im = p.inv_mm[a];
           const float B[3] = {fmaf(b[0], im, sg * e0), fmaf(b[1], im, sg * e1), fmaf(b[2], im, sg * e2)};
           float f[3];
           rhs32(s, B, p.g, p.alpha, f);
-          float x[3] = {fmaf(p.dt, f[0], s[0]), fmaf(p.dt, f[1], s[1]), fmaf(p.dt, f[2], s[2])};
+          const float x[3] = {fmaf(p.dt, f[0], s[0]), fmaf(p.dt, f[1], s[1]), fmaf(p.dt, f[2], s[2])};
           const float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
           float r = rsqrtf(n2);
           r = r * fmaf(-0.5f * n2, r * r, 1.5f);
           tilde = make_float4(x[0] * r, x[1] * r, x[2] * r, 0.f);
           if (inner) {
-            float *fa = fo + a * 6 * g::NT;
+            float *fa = fo + a * 6 * g::NI;
             fa[0] = f[0];
-            fa[g::NT] = f[1];
-            fa[2 * g::NT] = f[2];
-            fa[3 * g::NT] = e0;
-            fa[4 * g::NT] = e1;
-            fa[5 * g::NT] = e2;
+            fa[g::NI] = f[1];
+            fa[2 * g::NI] = f[2];
+            fa[3 * g::NI] = e0;
+            fa[4 * g::NI] = e1;
+            fa[5 * g::NI] = e2;
           }
         }
         out[a * 32 * F::BY] = tilde;
@@ -430,26 +480,29 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, 1)
       // corrector field: push the S~ plane just computed
       const float4 *base = st + (kp % Q) * g::ST + ty * 32 + tx;
       push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, 32 * F::BY, 32, accc);
-      if (kc >= 0 && kc < tzc) {
+      if (kc >= 0) {
         const int slot = (kc + R) % Q;
         const float4 *cen = st + slot * g::ST + ty * 32 + tx;
-        const float *fi = fq + slot * (NS * 6 * g::NT) + tid;
+        const float *fi = fq + slot * (NS * 6 * g::NI) + ii;
+        cp_wait<1>();  // this thread's FP64 state copies (all but the newest group)
 #pragma unroll
         for (int a = 0; a < NS; ++a) {
           const float4 c4 = cen[a * 32 * F::BY];
           const float s[3] = {c4.x, c4.y, c4.z};
           float b[3] = {accc[a][0][0], accc[a][0][1], accc[a][0][2]};
           onsite32(p, a, s, b);
-          const float *fa = fi + a * 6 * g::NT;
+          const float *fa = fi + a * 6 * g::NI;
           const float sg = p.sigma[a], im = p.inv_mm[a];
-          const float B[3] = {fmaf(b[0], im, sg * fa[3 * g::NT]), fmaf(b[1], im, sg * fa[4 * g::NT]),
-                              fmaf(b[2], im, sg * fa[5 * g::NT])};
+          const float B[3] = {fmaf(b[0], im, sg * fa[3 * g::NI]), fmaf(b[1], im, sg * fa[4 * g::NI]),
+                              fmaf(b[2], im, sg * fa[5 * g::NI])};
           float f[3];
           rhs32(s, B, p.g, p.alpha, f);
-          const float d[3] = {p.hdt * (fa[0] + f[0]), p.hdt * (fa[g::NT] + f[1]), p.hdt * (fa[2 * g::NT] + f[2])};
+          const float d[3] = {p.hdt * (fa[0] + f[0]), p.hdt * (fa[g::NI] + f[1]), p.hdt * (fa[2 * g::NI] + f[2])};
+          const double S0[3] = {s64[(a * 3 + 0) * g::NI + ii], s64[(a * 3 + 1) * g::NI + ii],
+                                s64[(a * 3 + 2) * g::NI + ii]};
           double o[3];
-          renormalise64(s64[a], d, o);
-          const long long i = (((long long)a * p.nz + c) * p.ny + cy) * p.nx + cx;
+          renormalise64(S0, d, o);
+          const long long i = a * subvol + c * plane + (long long)cy * p.nx + cx;
           Sout[i] = o[0];
           Sout[p.nsite + i] = o[1];
           Sout[2 * p.nsite + i] = o[2];
@@ -458,6 +511,7 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, 1)
       shift_acc<F>(accc);
     }
   }
+  cp_wait<0>();
 }
 
 // ------------------------------------------------------------------ field only
@@ -468,67 +522,47 @@ struct GF {
   static constexpr int NT = 32 * BY, LX = 32 + 2 * R, LY = BY + 2 * R;
   static constexpr int SN = NS * LY * LX;
   static constexpr int NLOAD = (SN + NT - 1) / NT;
-  static constexpr size_t SMEM = 2 * (size_t)SN * 16 + (size_t)(R + 1) * NS * NT * 16;
+  static constexpr size_t OFF_CQ = 2 * (size_t)SN * 16;
+  static constexpr size_t OFF_STAGE = OFF_CQ + (size_t)(R + 1) * NS * NT * 16;
+  static constexpr size_t SMEM = OFF_STAGE + (size_t)3 * SN * 8;
 };
 
 // Reduced field of plane-marching tiles (32 x BY outputs); onsite adds Zeeman
 // and anisotropy.  Output FP64 (widened from the FP32 accumulators).
 template <int FID>
-__global__ void __launch_bounds__(GF<Family<FID>>::NT, 1)
+__global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
     k_field_stencil(const StencilArgs p, int onsite, const double *__restrict__ Sin, double *__restrict__ b) {
   using F = Family<FID>;
   using g = GF<F>;
   constexpr int NS = F::NSUB, R = F::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4 *sn = reinterpret_cast<float4 *>(smem_raw);      // [2][SN]
-  float4 *cq = sn + 2 * g::SN;                            // [R+1][NS][NT] centre values
+  float4 *sn = reinterpret_cast<float4 *>(smem_raw);                    // [2][SN]
+  float4 *cq = reinterpret_cast<float4 *>(smem_raw + g::OFF_CQ);        // [R+1][NS][NT] centre values
+  double *stage = reinterpret_cast<double *>(smem_raw + g::OFF_STAGE);  // [3][SN]
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * F::BY, z0 = blockIdx.z * p.tz;
   const int tzc = min(p.tz, p.nz - z0);
   const int cx = x0 + tx, cy = y0 + ty;
   const bool mine = cx < p.nx && cy < p.ny;
+  const long long plane = (long long)p.ny * p.nx, subvol = (long long)p.nz * plane;
   float acc[NS][2 * R + 1][3];
 #pragma unroll
   for (int a = 0; a < NS; ++a)
 #pragma unroll
     for (int j = 0; j < 2 * R + 1; ++j) acc[a][j][0] = acc[a][j][1] = acc[a][j][2] = 0.0f;
-  // loads use the fused kernel's staging with the halo shifted by R
-  double pre[g::NLOAD][3];
-  auto fetch = [&](int q) {
-    bool zok = true;
-    const int gz = wrap_axis(q, p.nz, p.pz, zok);
-#pragma unroll
-    for (int j = 0; j < g::NLOAD; ++j) {
-      const int e = tid + j * g::NT;
-      pre[j][0] = pre[j][1] = pre[j][2] = 0.0;
-      if (e < g::SN) {
-        const int s = e / (g::LX * g::LY);
-        const int r = e - s * (g::LX * g::LY);
-        const int row = r / g::LX, col = r - row * g::LX;
-        bool ok = zok;
-        const int gx = wrap_axis(x0 - R + col, p.nx, p.px, ok);
-        const int gy = wrap_axis(y0 - R + row, p.ny, p.py, ok);
-        if (ok) {
-          const long long i = (((long long)s * p.nz + gz) * p.ny + gy) * p.nx + gx;
-          pre[j][0] = __ldg(Sin + i);
-          pre[j][1] = __ldg(Sin + p.nsite + i);
-          pre[j][2] = __ldg(Sin + 2 * p.nsite + i);
-        }
-      }
-    }
-  };
+  long long off[g::NLOAD];
+  unsigned okmask;
+  load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(p, x0 - R, y0 - R, tid, off, okmask);
   const int niter = tzc + 2 * R;
-  fetch(z0 - R);
+  issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, z0 - R, tid, off, okmask, stage);
+  cp_commit();
   for (int k = 0; k < niter; ++k) {
     const int q = z0 - R + k;
     float4 *buf = sn + (k & 1) * g::SN;
-#pragma unroll
-    for (int j = 0; j < g::NLOAD; ++j) {
-      const int e = tid + j * g::NT;
-      if (e < g::SN)
-        buf[e] = make_float4(f64_to_f32(pre[j][0]), f64_to_f32(pre[j][1]), f64_to_f32(pre[j][2]), 0.0f);
-    }
-    if (k + 1 < niter) fetch(q + 1);
+    cp_wait<0>();
+    convert_plane<g::NLOAD, g::NT, g::SN>(stage, buf, tid);
+    if (k + 1 < niter) issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, q + 1, tid, off, okmask, stage);
+    cp_commit();
     __syncthreads();
     const float4 *base = buf + (ty + R) * g::LX + (tx + R);
     push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, g::LX * g::LY, g::LX, acc);
@@ -546,7 +580,7 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, 1)
           const float s[3] = {c4.x, c4.y, c4.z};
           onsite32(p, a, s, v);
         }
-        const long long i = (((long long)a * p.nz + c) * p.ny + cy) * p.nx + cx;
+        const long long i = a * subvol + c * plane + (long long)cy * p.nx + cx;
         b[i] = (double)v[0];
         b[p.nsite + i] = (double)v[1];
         b[2 * p.nsite + i] = (double)v[2];
@@ -555,6 +589,7 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, 1)
     shift_acc<F>(acc);
     __syncthreads();
   }
+  cp_wait<0>();
 }
 
 // ------------------------------------------------------------------ planning
@@ -620,17 +655,34 @@ cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &a, int onsite
   return cudaGetLastError();
 }
 
+// z chunk per CTA: each chunk pays 4R warm-up planes, and the grid runs in
+// waves of (SMs x resident CTAs); pick the chunk that minimises
+// waves * (chunk + 4R), preferring longer chunks (fewer re-read planes) on ties.
 template <int FID>
-int tiles_xy(const sx_ctx *c) {
-  using g = G<Family<FID>>;
-  return ((c->geo.nx + g::TX - 1) / g::TX) * ((c->geo.ny + g::TY - 1) / g::TY);
-}
-
-int family_radius(int fam) {
-  switch (fam) {
-    case FAM_BCC4: return 2;
-    default: return 1;
+int choose_tz(const sx_ctx *c) {
+  using F = Family<FID>;
+  using g = G<F>;
+  const int txy = ((c->geo.nx + g::TX - 1) / g::TX) * ((c->geo.ny + g::TY - 1) / g::TY);
+  int nsm = 152, occ = 1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_heun_fused<FID>, g::NT, g::SMEM) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  const long long slots = (long long)nsm * occ;
+  const int nz = c->geo.nz;
+  int best_tz = nz;
+  long long best = -1;
+  for (int tz = nz; tz >= 1; --tz) {
+    const int nchunk = (nz + tz - 1) / tz;
+    if (tz != nz && (nz + nchunk - 1) / nchunk != tz) continue;  // only balanced chunk lengths
+    const long long waves = ((long long)txy * nchunk + slots - 1) / slots;
+    const long long cost = waves * (tz + 4 * F::R);
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_tz = tz;
+    }
   }
+  return best_tz;
 }
 
 }  // namespace
@@ -675,22 +727,6 @@ int stencil_plan(sx_ctx *c) {
     a.twoK[s] = (float)c->onsite.twoK[s];
     a.inv_mm[s] = (float)c->onsite.inv_mm[s];
   }
-  // z chunk: enough CTAs to fill the GPU a few times over, at least 8 planes
-  int txy = 0;
-  switch (fam) {
-    case FAM_SC6_ISO: txy = tiles_xy<FAM_SC6_ISO>(c); break;
-    case FAM_SC6_TEN: txy = tiles_xy<FAM_SC6_TEN>(c); break;
-    case FAM_SC26_ISO: txy = tiles_xy<FAM_SC26_ISO>(c); break;
-    case FAM_SC26_TEN: txy = tiles_xy<FAM_SC26_TEN>(c); break;
-    default: txy = tiles_xy<FAM_BCC4>(c); break;
-  }
-  const int R = family_radius(fam);
-  int nchunk = (4 * 152 + txy - 1) / txy;
-  int tz = (c->geo.nz + nchunk - 1) / nchunk;
-  if (tz < 8 * R) tz = 8 * R;
-  if (tz > c->geo.nz) tz = c->geo.nz;
-  sp->tz = tz;
-  a.tz = tz;
   cudaError_t e;
   switch (fam) {
     case FAM_SC6_ISO: e = set_smem<FAM_SC6_ISO>(); break;
@@ -703,6 +739,14 @@ int stencil_plan(sx_ctx *c) {
     delete sp;
     return cuda_error(e, "cudaFuncSetAttribute");
   }
+  switch (fam) {
+    case FAM_SC6_ISO: sp->tz = choose_tz<FAM_SC6_ISO>(c); break;
+    case FAM_SC6_TEN: sp->tz = choose_tz<FAM_SC6_TEN>(c); break;
+    case FAM_SC26_ISO: sp->tz = choose_tz<FAM_SC26_ISO>(c); break;
+    case FAM_SC26_TEN: sp->tz = choose_tz<FAM_SC26_TEN>(c); break;
+    default: sp->tz = choose_tz<FAM_BCC4>(c); break;
+  }
+  a.tz = sp->tz;
   c->stencil = sp;
   c->launches_per_step = 1;
   return SX_OK;
