@@ -223,6 +223,22 @@ int sx_energy(sx_ctx *ctx, const double *S, double *E_host, void *stream);
  * methods), written to *out_host.  Synchronises the stream. */
 int sx_torque_max(sx_ctx *ctx, const double *S, double *out_host, void *stream);
 
+/* max_i |S_i x b_i| of caller-provided spins S and fields b (device, layout
+ * of sx_field, 3*nsite doubles each, no overlap), written to *out_host.  The
+ * paper has no counterpart: this is a variant of sx_torque_max for callers
+ * that cannot let the library allocate device memory (an application that
+ * reserves the GPU's memory up front in its own arena, or a loop that must
+ * not absorb cudaMalloc's implicit synchronisation).  It needs no context,
+ * calls no allocating routine, and keeps its partial maxima in a fixed
+ * 9.7 KB device array in the library image that every GPU loading the
+ * library holds until exit.  The first call on a device looks up that
+ * array's address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU race; calls serialised on one stream do not.
+ * SX_ERR_ARG for null or misaligned pointers, overlap, or nsite outside
+ * 1..2^40.  Synchronises the stream. */
+int sx_torque_max_noalloc(const double *S, const double *b, int64_t nsite, double *out_host, void *stream);
+
 /* The thermal normals the Heun step draws: eta for sites site0 .. site0+n-1
  * at step `step`, written as n x 3 floats to eta_dev (device).  The noise is
  * a pure function of (seed, replica, site, step), see sx_llg_params. */

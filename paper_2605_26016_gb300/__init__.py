@@ -30,7 +30,7 @@ PRECISIONS = {"fp64": SX_PREC_FP64, "fp32": SX_PREC_FP32, "tf32": SX_PREC_TF32, 
 EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shell_radius", "sx_add_shell_exchange",
            "sx_add_dmi", "sx_add_bonds", "sx_set_zeeman", "sx_set_anisotropy", "sx_set_dipolar", "sx_get_taps",
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
-           "sx_thermal_normals", "sx_plan_info")
+           "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc")
 
 
 class sx_lattice(ctypes.Structure):
@@ -97,6 +97,7 @@ def lib():
             "sx_thermal_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, i64,
                                                   ctypes.c_uint64, vp, vp]),
             "sx_plan_info": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
+            "sx_torque_max_noalloc": (ctypes.c_int, [vp, vp, i64, dp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -272,6 +273,15 @@ def sx_energy(ctx, S, nsite, stream=None):
 def sx_torque_max(ctx, S, nsite, stream=None):
     out = ctypes.c_double()
     _chk(lib().sx_torque_max(ctx, _dev_ptr(S, 3 * nsite), ctypes.byref(out), _stream(stream)), "sx_torque_max")
+    return out.value
+
+
+def sx_torque_max_noalloc(S, b, nsite, stream=None):
+    """max_i |S_i x b_i| for caller-provided spins and fields; the library allocates nothing for it
+    (scratch lives in a fixed array in the library image)."""
+    out = ctypes.c_double()
+    _chk(lib().sx_torque_max_noalloc(_dev_ptr(S, 3 * nsite), _dev_ptr(b, 3 * nsite), int(nsite), ctypes.byref(out),
+                                     _stream(stream)), "sx_torque_max_noalloc")
     return out.value
 
 
