@@ -351,3 +351,67 @@ def test_stochastic_step_uses_same_noise_in_both_stages():
         mi.build()
         ref = mi.heun(S0[:, :, :, :, i:i + 1], dt, alpha, nsteps=1)
         assert np.abs(ref.reshape(3) - S1[:, 0, 0, 0, i]).max() < 1e-15
+
+
+# ---------------------------------------------------------------- dipolar
+
+def test_mu_b_and_dipolar_prefactor_from_first_principles():
+    # mu_B = e hbar / (2 m_e) from the exact SI e and h (hbar = h / 2 pi) and CODATA 2018 m_e (relative
+    # uncertainty 3e-10); mu0/4pi = 1e-7 T m/A to 1e-10
+    e, h, me = 1.602176634e-19, 6.62607015e-34, 9.1093837015e-31
+    mu_b_JT = e * (h / (2 * math.pi)) / (2 * me)
+    assert abs(MU_B / (mu_b_JT / e * 1e3) - 1) < 1e-9                  # meV/T
+    pref = 1e-7 * mu_b_JT ** 2 / e * 1e3 * 1e27                        # J m^3 -> meV nm^3
+    assert abs(C["dip_pref"] / pref - 1) < 2e-9
+
+
+def test_two_dipoles_textbook_field():
+    # b_1 = (mu0 mu_B^2/4pi) mu_1 mu_2 (3 (S_2.e) e - S_2) / r^3 for two moments on an open lattice
+    a = 0.3
+    m = oracle.Model((2, 1, 1), (0, 0, 0), cubic_cell(a), SC_POS, [2.0])
+    m.set_dipolar(True)
+    m.build()
+    S = np.zeros((3, 1, 1, 1, 2))
+    S[:, 0, 0, 0, 0] = [0.0, 0.6, 0.8]
+    S[:, 0, 0, 0, 1] = [0.48, 0.6, 0.64]
+    b = m.field(S)
+    ex = np.array([1.0, 0.0, 0.0])
+    S2 = S[:, 0, 0, 0, 1]
+    expect = C["dip_pref"] * 4.0 * (3 * ex * (ex @ S2) - S2) / a ** 3
+    assert np.abs(b[:, 0, 0, 0, 0] - expect).max() < 1e-14 * np.abs(expect).max() + 1e-18
+
+
+@pytest.mark.parametrize("L", [4, 5, 6])
+def test_uniform_state_zero_dipolar_field_in_periodic_cube(L):
+    # uniform magnetisation in a periodic cubic box: the minimum-image sum (with half-period images split
+    # evenly) is cubic-symmetric, so the dipolar field vanishes (sum of (3 e e - I)/r^3 is traceless and
+    # isotropic)
+    m = oracle.Model((L, L, L), (1, 1, 1), cubic_cell(), SC_POS, [2.2])
+    m.set_dipolar(True)
+    m.build()
+    d = np.array([0.3, -0.5, 0.8])
+    S = uniform_spins(1, (L, L, L), d)
+    b = m.field(S)
+    scale = C["dip_pref"] * 2.2 ** 2 / A_NM ** 3
+    assert np.abs(b).max() < 1e-12 * scale
+    # a non-uniform state does feel a dipolar field
+    S2 = random_spins(1, (L, L, L), 3)
+    assert np.abs(m.field(S2)).max() > 1e-3 * scale
+
+
+def test_dipolar_energy_gradient():
+    n = (3, 4, 2)
+    m = oracle.Model(n, (1, 0, 1), cubic_cell(), [[0, 0, 0], [0.5, 0.5, 0.5]], [2.2, 1.5])
+    m.add_shell_exchange(1, 0.3)
+    m.set_dipolar(True)
+    m.build()
+    S = random_spins(2, n, 12)
+    b = m.field(S)
+    h = 1e-5
+    rng = np.random.default_rng(2)
+    for flat in rng.choice(S.size, 12, replace=False):
+        Sp, Sm = S.copy().reshape(-1), S.copy().reshape(-1)
+        Sp[flat] += h
+        Sm[flat] -= h
+        g = (m.energy(Sp) - m.energy(Sm)) / (2 * h)
+        assert abs(-g - b.reshape(-1)[flat]) < 1e-6 * max(1.0, abs(g))
