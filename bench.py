@@ -188,6 +188,8 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     wl = WORKLOADS[args.workload]
     s, w = sx.system_from_workload(wl["name"], wl["n"])
+    if args.dipolar:
+        s.set_dipolar(True)
     info = s.plan(args.backend, args.precision)
     nsite = s.nsite
     seed = w["seed"] + 1000 * rank
@@ -268,7 +270,7 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32-field/f64-state" if args.precision == "fp32" else args.precision,
            "data": "synthetic: seeded random unit spins; every rank an independent replica",
-           "config": {"workload": args.workload, "lattice": wl["desc"], "backend": args.backend,
+           "config": {"workload": args.workload, "lattice": wl["desc"], "backend": args.backend, "dipolar": args.dipolar,
                       "precision": args.precision, "nsite_per_gpu": nsite, "parallelism": f"replicas x{world}",
                       "l2": "flushed before every timed step (256 MB write + 256 MB read)",
                       "median_step_ms": statistics.median(times), "wall_s": t_wall, "max_norm_error": norm_err},
@@ -296,6 +298,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the step kernel from an ncu capture (GB/s roofline context)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dipolar", action="store_true", help="add the point-dipole field (FFT backend)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

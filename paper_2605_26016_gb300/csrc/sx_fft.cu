@@ -1,0 +1,685 @@
+// FFT backend: the bilinear and dipolar field in reciprocal space,
+//   b^_a^alpha(q) = sum_b sum_beta K^_ab^{alpha beta}(q) S^_b^beta(q)
+// ("Backend representations": the FFT backend transforms the spin field,
+// multiplies by the precomputed kernel spectrum and transforms back; long-range
+// dipolar fields use the same reciprocal-space convolution).
+//
+// Design:
+//  * Own radix-2 FFT: each 1D pass stages W lines of length n in shared memory
+//    (bit-reversed placement, then log2 n in-place butterfly stages with a
+//    host-built twiddle table), lines grouped so that global accesses are
+//    coalesced along x.  Power-of-two axes up to 4096, FP32 or FP64 complex.
+//  * The 3*nsub real spin channels are packed two per complex field; the
+//    k-space multiply treats q and -q together, which recovers every real
+//    channel's spectrum from the packed one and writes the packed spectrum of
+//    the real field back.
+//  * The kernel matrix M(q) = sum_delta K(delta) e^{+i q.delta} over channels
+//    (a, alpha) x (b, beta) is Hermitian (reverse bonds carry the transpose,
+//    the dipolar tensor is symmetric), so only its diagonal (real) and upper
+//    triangle (complex) are stored.  It is built once per plan in FP64 from the
+//    directed taps and, when enabled, the periodic point-dipole sum (minimum
+//    image; a separation of exactly half a period split into its two images
+//    with weight 1/2).
+//  * Heun step: field(S^n) -> predictor -> field(S~) -> corrector, the state sum
+//    and renormalisation in FP64 as in the stencil backend.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "sx_device.cuh"
+#include "sx_internal.h"
+#include "sx_noise.cuh"
+
+namespace sx {
+
+template <typename R>
+struct CxT;
+template <>
+struct CxT<float> {
+  using T = float2;
+};
+template <>
+struct CxT<double> {
+  using T = double2;
+};
+
+struct FftPlan {
+  int prec;  // SX_PREC_FP32 or SX_PREC_FP64 (arithmetic of transforms and fields)
+  int n[3], logn[3], W[3];
+  int nsub, nch, nzf, noff;
+  long long N;   // cells
+  void *Z;       // [nzf][N] complex: packed spin channels, then packed fields
+  void *Md;      // [nch][N] real: diagonal of M(q)
+  void *Mo;      // [noff][N] complex: upper triangle of M(q)
+  void *tw[3];   // per axis: n/2 complex twiddles exp(-2 pi i k / n)
+  void *St, *F0, *Bf;  // Heun: predictor state, f0, field buffer; [nch][N] real each
+};
+
+namespace {
+
+constexpr int kFftThreads = 512;
+constexpr size_t kFftSmem = 200 * 1024;
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+// One 1D pass over every line of one axis.  Line group g (W lines, adjacent
+// along the grouping axis, stride gs), outer line index o (stride os), element
+// i along the transform axis (stride is); blockIdx.z selects the field.
+template <typename R>
+__global__ void __launch_bounds__(kFftThreads)
+    k_fft_pass(typename CxT<R>::T *__restrict__ data, int n, int logn, int W, int ifast, long long gs, long long os,
+               long long is, long long fstride, const typename CxT<R>::T *__restrict__ tw, int inverse) {
+  using C = typename CxT<R>::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C *sm = reinterpret_cast<C *>(smraw);
+  const int pitch = n + 1;
+  C *base = data + blockIdx.z * fstride + (long long)blockIdx.x * W * gs + (long long)blockIdx.y * os;
+  const int total = W * n;
+  for (int e = threadIdx.x; e < total; e += kFftThreads) {
+    int w, i;
+    if (ifast) {
+      w = e / n;
+      i = e - w * n;
+    } else {
+      i = e / W;
+      w = e - i * W;
+    }
+    const int r = (int)(__brev((unsigned)i) >> (32 - logn));
+    sm[w * pitch + r] = base[w * gs + i * is];
+  }
+  __syncthreads();
+  const int nh = n >> 1;
+  for (int s = 0; s < logn; ++s) {
+    const int half = 1 << s;
+    for (int t = threadIdx.x; t < W * nh; t += kFftThreads) {
+      const int w = t / nh, j = t - w * nh;
+      const int k = j & (half - 1);
+      const int i0 = ((j >> s) << (s + 1)) + k, i1 = i0 + half;
+      C f = tw[k << (logn - 1 - s)];
+      if (inverse) f.y = -f.y;
+      const C a = sm[w * pitch + i0];
+      const C b = cmul(sm[w * pitch + i1], f);
+      C u, v;
+      u.x = a.x + b.x;
+      u.y = a.y + b.y;
+      v.x = a.x - b.x;
+      v.y = a.y - b.y;
+      sm[w * pitch + i0] = u;
+      sm[w * pitch + i1] = v;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < total; e += kFftThreads) {
+    int w, i;
+    if (ifast) {
+      w = e / n;
+      i = e - w * n;
+    } else {
+      i = e / W;
+      w = e - i * W;
+    }
+    base[w * gs + i * is] = sm[w * pitch + i];
+  }
+}
+
+// real channels [nch][N] -> packed complex fields [nzf][N]
+template <typename Tin, typename R>
+__global__ void k_pack(const Tin *__restrict__ S, typename CxT<R>::T *__restrict__ Z, int nch, long long N) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int nzf = (nch + 1) / 2;
+  for (int m = 0; m < nzf; ++m) {
+    typename CxT<R>::T z;
+    z.x = (R)S[(long long)(2 * m) * N + i];
+    z.y = (2 * m + 1 < nch) ? (R)S[(long long)(2 * m + 1) * N + i] : (R)0;
+    Z[m * N + i] = z;
+  }
+}
+
+// b^(q) = M(q) S^(q) for every (q, -q) pair; channel spectra are unpacked from
+// the packed fields, the packed spectrum of the (real) field is written back.
+template <typename R, int NCH>
+__global__ void k_kmul(typename CxT<R>::T *__restrict__ Z, const R *__restrict__ Md,
+                       const typename CxT<R>::T *__restrict__ Mo, int nx, int ny, int nz, long long N) {
+  using C = typename CxT<R>::T;
+  constexpr int NZF = (NCH + 1) / 2;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  const int x = (int)(q % nx);
+  const int y = (int)((q / nx) % ny);
+  const int z = (int)(q / ((long long)nx * ny));
+  const long long mq = (long long)((nx - x) & (nx - 1)) + (long long)nx * (((ny - y) & (ny - 1)) +
+                                                                           (long long)ny * ((nz - z) & (nz - 1)));
+  if (mq < q) return;  // the partner thread handles this pair
+  C s[NCH];
+#pragma unroll
+  for (int m = 0; m < NZF; ++m) {
+    const C a = Z[m * N + q], bc = Z[m * N + mq];  // conj of bc is the spectrum at q of conj(field)
+    C u;
+    u.x = (R)0.5 * (a.x + bc.x);
+    u.y = (R)0.5 * (a.y - bc.y);
+    s[2 * m] = u;
+    if (2 * m + 1 < NCH) {
+      C v;
+      v.x = (R)0.5 * (a.y + bc.y);
+      v.y = (R)-0.5 * (a.x - bc.x);
+      s[2 * m + 1] = v;
+    }
+  }
+  C b[NCH];
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) {
+    const R d = Md[k * N + q];
+    C acc;
+    acc.x = d * s[k].x;
+    acc.y = d * s[k].y;
+#pragma unroll
+    for (int l = 0; l < NCH; ++l) {
+      if (l == k) continue;
+      const int lo = k < l ? k : l, hi = k < l ? l : k;
+      const int p = lo * NCH - lo * (lo + 1) / 2 + (hi - lo - 1);
+      C mkl = Mo[p * N + q];
+      if (k > l) mkl.y = -mkl.y;
+      const C t = cmul(mkl, s[l]);
+      acc.x += t.x;
+      acc.y += t.y;
+    }
+    b[k] = acc;
+  }
+#pragma unroll
+  for (int m = 0; m < NZF; ++m) {
+    const C e = b[2 * m];
+    C o;
+    o.x = (R)0;
+    o.y = (R)0;
+    if (2 * m + 1 < NCH) o = b[2 * m + 1];
+    C wq, wm;
+    wq.x = e.x - o.y;
+    wq.y = e.y + o.x;
+    wm.x = e.x + o.y;
+    wm.y = -e.y + o.x;
+    Z[m * N + q] = wq;
+    if (mq != q) Z[m * N + mq] = wm;
+  }
+}
+
+// packed fields -> real channels times scale, plus Zeeman and anisotropy when onsite
+template <typename R, typename Tout, typename Tspin>
+__global__ void k_unpack(const typename CxT<R>::T *__restrict__ Z, Tout *__restrict__ b, int nsub, long long N,
+                         R scale, const Tspin *__restrict__ S, OnSite os, int onsite) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int nch = 3 * nsub;
+  R v[3 * SX_MAX_SUB];
+  for (int m = 0; m < (nch + 1) / 2; ++m) {
+    const typename CxT<R>::T z = Z[m * N + i];
+    v[2 * m] = z.x * scale;
+    if (2 * m + 1 < nch) v[2 * m + 1] = z.y * scale;
+  }
+  if (onsite) {
+    for (int a = 0; a < nsub; ++a) {
+      const R s0 = (R)S[(long long)(0 * nsub + a) * N + i], s1 = (R)S[(long long)(1 * nsub + a) * N + i],
+              s2 = (R)S[(long long)(2 * nsub + a) * N + i];
+      const R p = (R)os.twoK[a] * (s0 * (R)os.axis[a][0] + s1 * (R)os.axis[a][1] + s2 * (R)os.axis[a][2]);
+      for (int c = 0; c < 3; ++c) v[c * nsub + a] += (R)os.zee[a][c] + p * (R)os.axis[a][c];
+    }
+  }
+  for (int k = 0; k < nch; ++k) b[(long long)k * N + i] = (Tout)v[k];
+}
+
+// ---------------------------------------------------------------- Heun
+
+template <typename R>
+__device__ __forceinline__ void onsite_t(const OnSite &os, int a, const R s[3], R b[3]) {
+  const R p = (R)os.twoK[a] * (s[0] * (R)os.axis[a][0] + s[1] * (R)os.axis[a][1] + s[2] * (R)os.axis[a][2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) b[c] += (R)os.zee[a][c] + p * (R)os.axis[a][c];
+}
+
+__device__ __forceinline__ void unit_t(float x[3]) {
+  const float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  float r = rsqrtf(n2);
+  r = r * fmaf(-0.5f * n2, r * r, 1.5f);
+  x[0] *= r;
+  x[1] *= r;
+  x[2] *= r;
+}
+__device__ __forceinline__ void unit_t(double x[3]) {
+  const double r = rsqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  x[0] *= r;
+  x[1] *= r;
+  x[2] *= r;
+}
+
+template <typename R>
+__device__ __forceinline__ void thermal_t(const HeunConst &h, int a, long long site, uint64_t step, R th[3]) {
+  th[0] = th[1] = th[2] = (R)0;
+  if (h.thermal) {
+    float e0, e1, e2;
+    normals3(h.seed, h.replica, (uint64_t)site, step, e0, e1, e2);
+    const R sg = (R)h.sigma[a];
+    th[0] = sg * (R)e0;
+    th[1] = sg * (R)e1;
+    th[2] = sg * (R)e2;
+  }
+}
+
+// predictor from the bilinear+dipolar field Bf of S (on-site terms added here)
+template <typename R>
+__global__ void k_fft_predict(const double *__restrict__ S, const R *__restrict__ Bf, R *__restrict__ St,
+                              R *__restrict__ F0, int nsub, long long N, OnSite os, HeunConst h, uint64_t step) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  for (int a = 0; a < nsub; ++a) {
+    R s[3], b[3], th[3], f[3];
+    for (int c = 0; c < 3; ++c) {
+      s[c] = (R)S[(long long)(c * nsub + a) * N + i];
+      b[c] = Bf[(long long)(c * nsub + a) * N + i];
+    }
+    onsite_t<R>(os, a, s, b);
+    thermal_t<R>(h, a, (long long)a * N + i, step, th);
+    const R im = (R)os.inv_mm[a];
+    const R B[3] = {b[0] * im + th[0], b[1] * im + th[1], b[2] * im + th[2]};
+    llg_rhs_t<R>(s, B, (R)h.g, (R)h.alpha, f);
+    R x[3] = {s[0] + (R)h.dt * f[0], s[1] + (R)h.dt * f[1], s[2] + (R)h.dt * f[2]};
+    unit_t(x);
+    for (int c = 0; c < 3; ++c) {
+      St[(long long)(c * nsub + a) * N + i] = x[c];
+      F0[(long long)(c * nsub + a) * N + i] = f[c];
+    }
+  }
+}
+
+__device__ __forceinline__ void correct_state(const double S[3], const float d[3], double o[3]) {
+  renormalise64(S, d, o);
+}
+__device__ __forceinline__ void correct_state(const double S[3], const double d[3], double o[3]) {
+  double x[3] = {S[0] + d[0], S[1] + d[1], S[2] + d[2]};
+  unit_t(x);
+  o[0] = x[0];
+  o[1] = x[1];
+  o[2] = x[2];
+}
+
+template <typename R>
+__global__ void k_fft_correct(const double *__restrict__ S, const R *__restrict__ St, const R *__restrict__ F0,
+                              const R *__restrict__ Bf, double *__restrict__ Snew, int nsub, long long N, OnSite os,
+                              HeunConst h, uint64_t step) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  for (int a = 0; a < nsub; ++a) {
+    R s[3], b[3], th[3], f[3], d[3];
+    double s64[3], o[3];
+    for (int c = 0; c < 3; ++c) {
+      const long long k = (long long)(c * nsub + a) * N + i;
+      s[c] = St[k];
+      b[c] = Bf[k];
+      s64[c] = S[k];
+    }
+    onsite_t<R>(os, a, s, b);
+    thermal_t<R>(h, a, (long long)a * N + i, step, th);
+    const R im = (R)os.inv_mm[a];
+    const R B[3] = {b[0] * im + th[0], b[1] * im + th[1], b[2] * im + th[2]};
+    llg_rhs_t<R>(s, B, (R)h.g, (R)h.alpha, f);
+    const R hdt = (R)(0.5 * h.dt);
+    for (int c = 0; c < 3; ++c) d[c] = hdt * (F0[(long long)(c * nsub + a) * N + i] + f[c]);
+    correct_state(s64, d, o);
+    for (int c = 0; c < 3; ++c) Snew[(long long)(c * nsub + a) * N + i] = o[c];
+  }
+}
+
+// ---------------------------------------------------------------- kernel spectrum (plan time, FP64)
+
+struct DipArgs {
+  int nx, ny, nz, nsub;
+  double A[3][3];
+  double pos[SX_MAX_SUB][3];
+  double mu[SX_MAX_SUB];
+  double pref, tol;
+  int dipolar;
+};
+
+// real-space kernel component K_{(a,alpha),(b,beta)}(delta) for every cell delta (imag = 0):
+// the periodic point-dipole sum; exchange taps are added afterwards
+__global__ void k_fill_dipolar(double2 *__restrict__ Zb, DipArgs d, int a, int al, int b, int be) {
+  const long long N = (long long)d.nx * d.ny * d.nz;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  double val = 0.0;
+  if (d.dipolar) {
+    const int cx = (int)(idx % d.nx), cy = (int)((idx / d.nx) % d.ny), cz = (int)(idx / ((long long)d.nx * d.ny));
+    const int c[3] = {cx, cy, cz};
+    const int L[3] = {d.nx, d.ny, d.nz};
+    double img[3][2], wgt[3][2];
+    int nim[3];
+    for (int k = 0; k < 3; ++k) {
+      const double f = c[k] + d.pos[b][k] - d.pos[a][k];
+      const double t = f - L[k] * floor(f / L[k] + 0.5);
+      if (fabs(fabs(t) - 0.5 * L[k]) < 1e-12) {
+        nim[k] = 2;
+        img[k][0] = -0.5 * L[k];
+        img[k][1] = 0.5 * L[k];
+        wgt[k][0] = wgt[k][1] = 0.5;
+      } else {
+        nim[k] = 1;
+        img[k][0] = t;
+        wgt[k][0] = 1.0;
+      }
+    }
+    for (int ix = 0; ix < nim[0]; ++ix)
+      for (int iy = 0; iy < nim[1]; ++iy)
+        for (int iz = 0; iz < nim[2]; ++iz) {
+          const double f[3] = {img[0][ix], img[1][iy], img[2][iz]};
+          double r[3];
+          for (int k = 0; k < 3; ++k) r[k] = f[0] * d.A[0][k] + f[1] * d.A[1][k] + f[2] * d.A[2][k];
+          const double len = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+          if (len <= d.tol) continue;
+          const double e_al = r[al] / len, e_be = r[be] / len;
+          const double w = wgt[0][ix] * wgt[1][iy] * wgt[2][iz];
+          val += w * d.pref * d.mu[a] * d.mu[b] * (3.0 * e_al * e_be - (al == be ? 1.0 : 0.0)) / (len * len * len);
+        }
+  }
+  Zb[idx] = make_double2(val, 0.0);
+}
+
+// add exchange taps of (target a, source b) to component (alpha, beta); serial, deterministic
+__global__ void k_add_taps(double2 *__restrict__ Zb, const DevTap *__restrict__ taps, int t0, int t1, int b, int al,
+                           int be, int nx, int ny, int nz) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int t = t0; t < t1; ++t) {
+    const DevTap &tp = taps[t];
+    if (tp.b != b) continue;
+    const double J = tp.iso ? (al == be ? tp.J[0] : 0.0) : tp.J[3 * al + be];
+    if (J == 0.0) continue;
+    const int x = ((tp.dx % nx) + nx) % nx, y = ((tp.dy % ny) + ny) % ny, z = ((tp.dz % nz) + nz) % nz;
+    Zb[x + (long long)nx * (y + (long long)ny * z)].x += J;
+  }
+}
+
+template <typename R>
+__global__ void k_store_diag(const double2 *__restrict__ Zb, R *__restrict__ Md, long long N) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) Md[i] = (R)Zb[i].x;
+}
+template <typename R>
+__global__ void k_store_off(const double2 *__restrict__ Zb, typename CxT<R>::T *__restrict__ Mo, long long N) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    typename CxT<R>::T v;
+    v.x = (R)Zb[i].x;
+    v.y = (R)Zb[i].y;
+    Mo[i] = v;
+  }
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+template <typename R>
+int pick_w(int n, int extent) {
+  const size_t csz = sizeof(typename CxT<R>::T);
+  int w = 16;
+  while (w > 1 && ((size_t)w * (n + 1) * csz > kFftSmem || w > extent)) w >>= 1;
+  return w;
+}
+
+// 3D transform of nfields packed fields in place (x, y, z passes; axes of length 1 skipped)
+template <typename R>
+cudaError_t fft3d(const FftPlan &fp, typename CxT<R>::T *Z, int nfields, const void *const tw[3], int inverse,
+                  cudaStream_t st) {
+  using C = typename CxT<R>::T;
+  const int nx = fp.n[0], ny = fp.n[1], nz = fp.n[2];
+  const long long N = fp.N;
+  for (int ax = 0; ax < 3; ++ax) {
+    const int n = fp.n[ax];
+    if (n < 2) continue;
+    int W;
+    dim3 grid;
+    long long gs, os, is;
+    int ifast;
+    if (ax == 0) {  // lines along x, grouped along y
+      W = pick_w<R>(n, ny);
+      grid = dim3(ny / W, nz, nfields);
+      gs = nx;
+      os = (long long)nx * ny;
+      is = 1;
+      ifast = 1;
+    } else if (ax == 1) {  // lines along y, grouped along x
+      W = pick_w<R>(n, nx);
+      grid = dim3(nx / W, nz, nfields);
+      gs = 1;
+      os = (long long)nx * ny;
+      is = nx;
+      ifast = 0;
+    } else {  // lines along z, grouped along x
+      W = pick_w<R>(n, nx);
+      grid = dim3(nx / W, ny, nfields);
+      gs = 1;
+      os = nx;
+      is = (long long)nx * ny;
+      ifast = 0;
+    }
+    const size_t smem = (size_t)W * (n + 1) * sizeof(C);
+    k_fft_pass<R><<<grid, kFftThreads, smem, st>>>(Z, n, fp.logn[ax], W, ifast, gs, os, is, N,
+                                                   static_cast<const C *>(tw[ax]), inverse);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t kmul(const FftPlan &fp, cudaStream_t st) {
+  using C = typename CxT<R>::T;
+  const unsigned g = blocks_for(fp.N, 256);
+  C *Z = static_cast<C *>(fp.Z);
+  const R *Md = static_cast<const R *>(fp.Md);
+  const C *Mo = static_cast<const C *>(fp.Mo);
+  if (fp.nch == 3)
+    k_kmul<R, 3><<<g, 256, 0, st>>>(Z, Md, Mo, fp.n[0], fp.n[1], fp.n[2], fp.N);
+  else
+    k_kmul<R, 6><<<g, 256, 0, st>>>(Z, Md, Mo, fp.n[0], fp.n[1], fp.n[2], fp.N);
+  return cudaGetLastError();
+}
+
+// field of the real channels `in` (FP64 spins or plan-precision predictor state) into `out`
+template <typename R, typename Tin, typename Tout>
+cudaError_t field_pipeline(const sx_ctx *c, const Tin *in, Tout *out, bool onsite, cudaStream_t st) {
+  const FftPlan &fp = *c->fft;
+  using C = typename CxT<R>::T;
+  C *Z = static_cast<C *>(fp.Z);
+  k_pack<Tin, R><<<blocks_for(fp.N, 256), 256, 0, st>>>(in, Z, fp.nch, fp.N);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = fft3d<R>(fp, Z, fp.nzf, fp.tw, 0, st);
+  if (e == cudaSuccess) e = kmul<R>(fp, st);
+  if (e == cudaSuccess) e = fft3d<R>(fp, Z, fp.nzf, fp.tw, 1, st);
+  if (e != cudaSuccess) return e;
+  k_unpack<R, Tout, Tin><<<blocks_for(fp.N, 256), 256, 0, st>>>(Z, out, fp.nsub, fp.N, (R)(1.0 / (double)fp.N), in,
+                                                                c->onsite, onsite ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t heun_pipeline(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
+                          cudaStream_t st) {
+  const FftPlan &fp = *c->fft;
+  R *St = static_cast<R *>(fp.St), *F0 = static_cast<R *>(fp.F0), *Bf = static_cast<R *>(fp.Bf);
+  cudaError_t e = field_pipeline<R, double, R>(c, src, Bf, false, st);
+  if (e != cudaSuccess) return e;
+  k_fft_predict<R><<<blocks_for(fp.N, 256), 256, 0, st>>>(src, Bf, St, F0, fp.nsub, fp.N, c->onsite, h, step);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = field_pipeline<R, R, R>(c, St, Bf, false, st);
+  if (e != cudaSuccess) return e;
+  k_fft_correct<R><<<blocks_for(fp.N, 256), 256, 0, st>>>(src, St, F0, Bf, dst, fp.nsub, fp.N, c->onsite, h, step);
+  return cudaGetLastError();
+}
+
+template <typename R>
+std::vector<typename CxT<R>::T> twiddles(int n) {
+  std::vector<typename CxT<R>::T> t(n / 2 > 0 ? n / 2 : 1);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < n / 2; ++k) {
+    t[k].x = (R)cos(-2.0 * pi * k / n);
+    t[k].y = (R)sin(-2.0 * pi * k / n);
+  }
+  return t;
+}
+
+template <typename R>
+cudaError_t alloc_twiddles(const FftPlan &fp, void *tw[3]) {
+  for (int ax = 0; ax < 3; ++ax) {
+    std::vector<typename CxT<R>::T> t = twiddles<R>(fp.n[ax]);
+    cudaError_t e = cudaMalloc(&tw[ax], t.size() * sizeof(t[0]));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(tw[ax], t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <typename R>
+cudaError_t set_fft_smem() {
+  return cudaFuncSetAttribute(k_fft_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFftSmem);
+}
+
+// M(q) in FP64: fill each upper-triangle component in real space, transform
+// with e^{+i q.delta}, store in the plan precision
+template <typename R>
+cudaError_t build_kernel(sx_ctx *c, FftPlan &fp) {
+  const long long N = fp.N;
+  double2 *Zb = nullptr;
+  void *tw64[3] = {nullptr, nullptr, nullptr};
+  cudaError_t e = cudaMalloc(&Zb, N * sizeof(double2));
+  if (e == cudaSuccess) e = alloc_twiddles<double>(fp, tw64);
+  if (e == cudaSuccess) e = set_fft_smem<double>();
+  DipArgs d;
+  memset(&d, 0, sizeof(d));
+  d.nx = fp.n[0];
+  d.ny = fp.n[1];
+  d.nz = fp.n[2];
+  d.nsub = fp.nsub;
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j) d.A[k][j] = c->lat.a[k][j];
+  for (int s = 0; s < fp.nsub; ++s) {
+    for (int k = 0; k < 3; ++k) d.pos[s][k] = c->lat.sub_pos[s][k];
+    d.mu[s] = c->lat.mu[s];
+  }
+  // mu0 mu_B^2 / (4 pi) in meV nm^3: 1e-7 T m/A * (9.2740100783e-24 J/T)^2, J m^3 -> meV nm^3
+  d.pref = 1e-7 * 9.2740100783e-24 * 9.2740100783e-24 * 1e27 / 1.602176634e-22;
+  d.tol = c->tol;
+  d.dipolar = c->dipolar;
+  std::vector<int> off(fp.nsub + 1, 0);
+  for (int a = 0; a < fp.nsub; ++a) off[a + 1] = off[a] + (int)c->taps[a].size();
+  int p = 0;
+  for (int ka = 0; ka < fp.nch && e == cudaSuccess; ++ka)
+    for (int kb = ka; kb < fp.nch && e == cudaSuccess; ++kb) {
+      const int a = ka % fp.nsub, al = ka / fp.nsub, b = kb % fp.nsub, be = kb / fp.nsub;
+      k_fill_dipolar<<<blocks_for(N, 256), 256>>>(Zb, d, a, al, b, be);
+      k_add_taps<<<1, 1>>>(Zb, c->d_taps, off[a], off[a + 1], b, al, be, fp.n[0], fp.n[1], fp.n[2]);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = fft3d<double>(fp, Zb, 1, tw64, 1, 0);
+      if (e != cudaSuccess) break;
+      if (ka == kb) {
+        k_store_diag<R><<<blocks_for(N, 256), 256>>>(Zb, static_cast<R *>(fp.Md) + ka * N, N);
+      } else {
+        k_store_off<R><<<blocks_for(N, 256), 256>>>(Zb, static_cast<typename CxT<R>::T *>(fp.Mo) + p * N, N);
+        ++p;
+      }
+      e = cudaGetLastError();
+    }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(Zb);
+  for (int k = 0; k < 3; ++k) cudaFree(tw64[k]);
+  return e;
+}
+
+template <typename R>
+cudaError_t alloc_plan(FftPlan &fp) {
+  using C = typename CxT<R>::T;
+  const long long N = fp.N;
+  cudaError_t e = cudaMalloc(&fp.Z, (size_t)fp.nzf * N * sizeof(C));
+  if (e == cudaSuccess) e = cudaMalloc(&fp.Md, (size_t)fp.nch * N * sizeof(R));
+  if (e == cudaSuccess && fp.noff) e = cudaMalloc(&fp.Mo, (size_t)fp.noff * N * sizeof(C));
+  if (e == cudaSuccess) e = cudaMalloc(&fp.St, (size_t)fp.nch * N * sizeof(R));
+  if (e == cudaSuccess) e = cudaMalloc(&fp.F0, (size_t)fp.nch * N * sizeof(R));
+  if (e == cudaSuccess) e = cudaMalloc(&fp.Bf, (size_t)fp.nch * N * sizeof(R));
+  if (e == cudaSuccess) e = alloc_twiddles<R>(fp, fp.tw);
+  if (e == cudaSuccess) e = set_fft_smem<R>();
+  return e;
+}
+
+}  // namespace
+
+void fft_free(sx_ctx *c) {
+  FftPlan *fp = c->fft;
+  if (!fp) return;
+  cudaFree(fp->Z);
+  cudaFree(fp->Md);
+  cudaFree(fp->Mo);
+  cudaFree(fp->St);
+  cudaFree(fp->F0);
+  cudaFree(fp->Bf);
+  for (int k = 0; k < 3; ++k) cudaFree(fp->tw[k]);
+  delete fp;
+  c->fft = nullptr;
+}
+
+int fft_plan(sx_ctx *c) {
+  if (c->prec != SX_PREC_FP32 && c->prec != SX_PREC_FP64)
+    return set_error(SX_ERR_UNSUPPORTED, "the FFT backend computes in FP32 or FP64");
+  if (c->lat.nsub > 2) return set_error(SX_ERR_UNSUPPORTED, "the FFT backend supports up to two sublattices");
+  for (int k = 0; k < 3; ++k) {
+    const int n = c->lat.n[k];
+    if (!c->lat.pbc[k]) return set_error(SX_ERR_UNSUPPORTED, "the FFT backend needs periodic boundaries on every axis");
+    if (n & (n - 1)) return set_error(SX_ERR_UNSUPPORTED, "the FFT backend needs power-of-two cell counts");
+    if (n > 4096) return set_error(SX_ERR_UNSUPPORTED, "the FFT backend supports up to 4096 cells per axis");
+  }
+  FftPlan *fp = new (std::nothrow) FftPlan();
+  if (!fp) return set_error(SX_ERR_OOM, "host allocation failed");
+  memset(fp, 0, sizeof(*fp));
+  fp->prec = c->prec;
+  for (int k = 0; k < 3; ++k) {
+    fp->n[k] = c->lat.n[k];
+    fp->logn[k] = ilog2(c->lat.n[k]);
+  }
+  fp->nsub = c->lat.nsub;
+  fp->nch = 3 * fp->nsub;
+  fp->nzf = (fp->nch + 1) / 2;
+  fp->noff = fp->nch * (fp->nch - 1) / 2;
+  fp->N = c->geo.ncell;
+  c->fft = fp;
+  cudaError_t e = (fp->prec == SX_PREC_FP32) ? alloc_plan<float>(*fp) : alloc_plan<double>(*fp);
+  if (e == cudaSuccess) e = (fp->prec == SX_PREC_FP32) ? build_kernel<float>(c, *fp) : build_kernel<double>(c, *fp);
+  if (e != cudaSuccess) {
+    fft_free(c);
+    return cuda_error(e, "FFT plan");
+  }
+  c->launches_per_step = 2 * (1 + 2 * ((fp->n[0] > 1) + (fp->n[1] > 1) + (fp->n[2] > 1)) + 1 + 1) + 2;
+  return SX_OK;
+}
+
+cudaError_t fft_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st) {
+  if (c->fft->prec == SX_PREC_FP32) return field_pipeline<float, double, double>(c, S, b, onsite, st);
+  return field_pipeline<double, double, double>(c, S, b, onsite, st);
+}
+
+cudaError_t fft_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
+                          cudaStream_t st) {
+  if (c->fft->prec == SX_PREC_FP32) return heun_pipeline<float>(c, src, dst, h, step, st);
+  return heun_pipeline<double>(c, src, dst, h, step, st);
+}
+
+}  // namespace sx

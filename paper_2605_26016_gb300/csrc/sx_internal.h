@@ -63,6 +63,8 @@ struct Tap {
 
 // Stencil-backend tables (filled by the host planner, consumed by sx_stencil.cu).
 struct StencilPlan;
+// FFT-backend buffers and kernel spectrum (sx_fft.cu).
+struct FftPlan;
 
 }  // namespace sx
 
@@ -101,6 +103,7 @@ struct sx_ctx {
   double *d_host_S[2];   // device buffers for the host-memory entry point
   int64_t nblock_red;
   sx::StencilPlan *stencil;
+  sx::FftPlan *fft;
   int launches_per_step;
 };
 
@@ -127,5 +130,12 @@ void stencil_free(sx_ctx *c);
 cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
 cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                               cudaStream_t st);
+
+// FFT path (sx_fft.cu)
+int fft_plan(sx_ctx *c);
+void fft_free(sx_ctx *c);
+cudaError_t fft_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
+cudaError_t fft_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
+                          cudaStream_t st);
 
 }  // namespace sx

@@ -29,6 +29,7 @@
 #include <new>
 #include <utility>
 
+#include "sx_device.cuh"
 #include "sx_internal.h"
 #include "sx_noise.cuh"
 
@@ -158,65 +159,6 @@ struct TapAt {
   static constexpr int a = s.a, b = s.b, dx = s.dx, dy = s.dy, dz = s.dz, tensor = s.tensor, coef = s.coef;
   static constexpr bool fresh = I == 0 || prev.b != b || prev.dx != dx || prev.dy != dy;
 };
-
-// FP64 -> FP32 by integer bit operations (round half up on the first dropped
-// bit; magnitudes below 2^-126 become zero).  Avoids the FP64 conversion pipe.
-__device__ __forceinline__ float f64_to_f32(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  const unsigned a = hi & 0x7FFFFFFFu;
-  if (a < 0x38100000u) return 0.0f;
-  unsigned m = __funnelshift_l(lo, a - 0x38000000u, 3);
-  m += (lo >> 28) & 1u;
-  return __uint_as_float(m | (hi & 0x80000000u));
-}
-
-// FP32 -> FP64 by integer bit operations (exact for normal numbers; FP32
-// subnormals become zero).
-__device__ __forceinline__ double f32_to_f64(float f) {
-  const unsigned b = __float_as_uint(f);
-  const unsigned a = b & 0x7FFFFFFFu;
-  if (a < 0x00800000u) return 0.0;
-  const unsigned hi = (b & 0x80000000u) | ((a >> 3) + 0x38000000u);
-  return __hiloint2double((int)hi, (int)(b << 29));
-}
-
-__device__ __forceinline__ int wrap_axis(int c, int n, int periodic, bool &ok) {
-  if (c >= 0 && c < n) return c;
-  if (!periodic) {
-    ok = false;
-    return 0;
-  }
-  c %= n;
-  return c < 0 ? c + n : c;
-}
-
-__device__ __forceinline__ void rhs32(const float s[3], const float B[3], float g, float alpha, float f[3]) {
-  const float t0 = s[1] * B[2] - s[2] * B[1];
-  const float t1 = s[2] * B[0] - s[0] * B[2];
-  const float t2 = s[0] * B[1] - s[1] * B[0];
-  const float u0 = s[1] * t2 - s[2] * t1;
-  const float u1 = s[2] * t0 - s[0] * t2;
-  const float u2 = s[0] * t1 - s[1] * t0;
-  f[0] = g * (t0 + alpha * u0);
-  f[1] = g * (t1 + alpha * u1);
-  f[2] = g * (t2 + alpha * u2);
-}
-
-// S' = N[S + d] in FP64 with d given in FP32.  x = S + d, eps = |x|^2 - 1,
-// c - 1 = t = eps (-1/2 + eps g(eps)) with g = 3/8 - 5/16 eps + 35/128 eps^2
-// (binomial series of (1+eps)^(-1/2)), S' = x + x t.
-__device__ __forceinline__ void renormalise64(const double S[3], const float d[3], double out[3]) {
-  const double x0 = S[0] + f32_to_f64(d[0]);
-  const double x1 = S[1] + f32_to_f64(d[1]);
-  const double x2 = S[2] + f32_to_f64(d[2]);
-  const double eps = fma(x0, x0, fma(x1, x1, fma(x2, x2, -1.0)));
-  const float e = f64_to_f32(eps);
-  const float gq = fmaf(e, fmaf(e, 0.2734375f, -0.3125f), 0.375f);
-  const double t = eps * fma(eps, f32_to_f64(gq), -0.5);
-  out[0] = fma(x0, t, x0);
-  out[1] = fma(x1, t, x1);
-  out[2] = fma(x2, t, x2);
-}
 
 // ------------------------------------------------------------------ async copies
 
