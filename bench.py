@@ -47,6 +47,24 @@ WORKLOADS = {
 }
 
 
+def replica_of(rank, base_seed):
+    """Every rank runs an independent replica: its own seed and Philox replica index."""
+    return {"seed": base_seed + 1000 * rank, "replica": rank}
+
+
+def max_over_ranks(value, dist, device):
+    """The timed region's duration, max over ranks (the slowest rank sets the whole-job time)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(world, units_per_rank, steps, total_ms):
+    """Units processed by all ranks divided by the (max-over-ranks) timed duration."""
+    return world * units_per_rank * steps / (total_ms * 1e-3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -192,11 +210,11 @@ def run_ours(args):
         s.set_dipolar(True)
     info = s.plan(args.backend, args.precision)
     nsite = s.nsite
-    seed = w["seed"] + 1000 * rank
-    S = torch.from_numpy(random_spins(s.nsub, wl["n"], seed)).to(dev)
+    rep = replica_of(rank, w["seed"])
+    S = torch.from_numpy(random_spins(s.nsub, wl["n"], rep["seed"])).to(dev)
     S2 = torch.empty_like(S)
     stream = torch.cuda.current_stream()
-    p = sx.llg_params(w["dt"], w["alpha"], w["T"], seed=seed, replica=rank)
+    p = sx.llg_params(w["dt"], w["alpha"], w["T"], seed=rep["seed"], replica=rep["replica"])
     flush_w = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     flush_r = torch.ones(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     sink = torch.zeros((), dtype=torch.float32, device=dev)
@@ -233,9 +251,7 @@ def run_ours(args):
     times = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(times)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+        total_ms = max_over_ranks(total_ms, dist, dev)
     # sanity: the state stays on the unit sphere
     Sf = bufs[step & 1]
     norm_err = (Sf.view(3, -1).pow(2).sum(0).sqrt() - 1).abs().max().item()
@@ -250,15 +266,13 @@ def run_ours(args):
         sx.sx_llg_heun_host(s.ctx, Sh, p, step + 1 + k, 1, nsite, stream)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = t.item()
+        e2e_s = max_over_ranks(e2e_s, dist, dev)
 
     if rank != 0:
         dist.destroy_process_group()
         return
     ms_per_step = total_ms / args.steps
-    value = world * nsite * args.steps / (total_ms * 1e-3)
+    value = whole_job_rate(world, nsite, args.steps, total_ms)
     hbm, peak_kind = peaks()
     launches = info["launches_per_step"]
     achieved = BYTES_PER_SPIN_STEP * nsite / (ms_per_step * 1e-3) / 1e9

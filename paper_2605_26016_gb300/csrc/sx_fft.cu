@@ -83,14 +83,15 @@ __global__ void __launch_bounds__(kFftThreads)
   const int pitch = n + 1;
   C *base = data + blockIdx.z * fstride + (long long)blockIdx.x * W * gs + (long long)blockIdx.y * os;
   const int total = W * n;
+  const int logw = 31 - __clz(W);  // W and n are powers of two
   for (int e = threadIdx.x; e < total; e += kFftThreads) {
     int w, i;
     if (ifast) {
-      w = e / n;
-      i = e - w * n;
+      w = e >> logn;
+      i = e & (n - 1);
     } else {
-      i = e / W;
-      w = e - i * W;
+      i = e >> logw;
+      w = e & (W - 1);
     }
     const int r = (int)(__brev((unsigned)i) >> (32 - logn));
     sm[w * pitch + r] = base[w * gs + i * is];
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(kFftThreads)
   for (int s = 0; s < logn; ++s) {
     const int half = 1 << s;
     for (int t = threadIdx.x; t < W * nh; t += kFftThreads) {
-      const int w = t / nh, j = t - w * nh;
+      const int w = t >> (logn - 1), j = t & (nh - 1);
       const int k = j & (half - 1);
       const int i0 = ((j >> s) << (s + 1)) + k, i1 = i0 + half;
       C f = tw[k << (logn - 1 - s)];
@@ -120,11 +121,11 @@ __global__ void __launch_bounds__(kFftThreads)
   for (int e = threadIdx.x; e < total; e += kFftThreads) {
     int w, i;
     if (ifast) {
-      w = e / n;
-      i = e - w * n;
+      w = e >> logn;
+      i = e & (n - 1);
     } else {
-      i = e / W;
-      w = e - i * W;
+      i = e >> logw;
+      w = e & (W - 1);
     }
     base[w * gs + i * is] = sm[w * pitch + i];
   }
