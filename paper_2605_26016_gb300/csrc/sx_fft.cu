@@ -672,6 +672,21 @@ int fft_plan(sx_ctx *c) {
   return SX_OK;
 }
 
+// Heun stages that take the bilinear field from a buffer (also used by the tensor-core backend)
+cudaError_t bufheun_predict(const sx_ctx *c, const double *S, const float *Bf, float *St, float *F0,
+                            const HeunConst &h, uint64_t step, cudaStream_t st) {
+  const long long N = c->geo.ncell;
+  k_fft_predict<float><<<blocks_for(N, 256), 256, 0, st>>>(S, Bf, St, F0, c->lat.nsub, N, c->onsite, h, step);
+  return cudaGetLastError();
+}
+
+cudaError_t bufheun_correct(const sx_ctx *c, const double *S, const float *St, const float *F0, const float *Bf,
+                            double *Snew, const HeunConst &h, uint64_t step, cudaStream_t st) {
+  const long long N = c->geo.ncell;
+  k_fft_correct<float><<<blocks_for(N, 256), 256, 0, st>>>(S, St, F0, Bf, Snew, c->lat.nsub, N, c->onsite, h, step);
+  return cudaGetLastError();
+}
+
 cudaError_t fft_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st) {
   if (c->fft->prec == SX_PREC_FP32) return field_pipeline<float, double, double>(c, S, b, onsite, st);
   return field_pipeline<double, double, double>(c, S, b, onsite, st);

@@ -184,6 +184,7 @@ void build_tables(sx_ctx *c) {
 void free_plan(sx_ctx *c) {
   if (c->stencil) stencil_free(c);
   if (c->fft) fft_free(c);
+  if (c->tc) tc_free(c);
   cudaFree(c->d_taps);
   cudaFree(c->d_tap_off);
   cudaFree(c->d_work);
@@ -243,6 +244,7 @@ int make_heun_const(const sx_ctx *c, const sx_llg_params *p, HeunConst &h) {
 cudaError_t backend_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st) {
   if (c->backend == SX_BACKEND_STENCIL) return stencil_field(c, S, b, onsite, st);
   if (c->backend == SX_BACKEND_FFT) return fft_field(c, S, b, onsite, st);
+  if (c->backend == SX_BACKEND_IGEMM_TC) return tc_field(c, S, b, onsite, st);
   return gather_field(c, S, b, onsite, st);
 }
 
@@ -250,6 +252,7 @@ cudaError_t backend_step(const sx_ctx *c, const double *src, double *dst, const 
                          cudaStream_t st) {
   if (c->backend == SX_BACKEND_STENCIL) return stencil_heun_step(c, src, dst, h, step, st);
   if (c->backend == SX_BACKEND_FFT) return fft_heun_step(c, src, dst, h, step, st);
+  if (c->backend == SX_BACKEND_IGEMM_TC) return tc_heun_step(c, src, dst, h, step, st);
   return gather_heun_step(c, src, dst, h, step, st);
 }
 
@@ -405,7 +408,8 @@ int sx_plan(sx_ctx *c, int backend, int prec) {
   if (prec < SX_PREC_FP64 || prec > SX_PREC_BF16) return set_error(SX_ERR_ARG, "unknown precision");
   if ((backend == SX_BACKEND_GATHER || backend == SX_BACKEND_STENCIL) && prec > SX_PREC_FP32)
     return set_error(SX_ERR_UNSUPPORTED, "TF32/BF16 fields need the tensor-core backend");
-  if (backend == SX_BACKEND_IGEMM_TC) return set_error(SX_ERR_UNSUPPORTED, "backend not available in this build");
+  if (backend == SX_BACKEND_IGEMM_TC && prec != SX_PREC_BF16 && prec != SX_PREC_TF32)
+    return set_error(SX_ERR_UNSUPPORTED, "the tensor-core backend computes the field in BF16 or TF32");
   if (c->dipolar && backend != SX_BACKEND_FFT)
     return set_error(SX_ERR_UNSUPPORTED, "the dipolar term needs the FFT backend");
   if (c->tables_version != c->ham_version) build_tables(c);
@@ -477,8 +481,8 @@ int sx_plan(sx_ctx *c, int backend, int prec) {
   SX_TRY(cudaMalloc(&c->d_field, N3 * sizeof(double)), "cudaMalloc field workspace");
   SX_TRY(cudaMalloc(&c->d_partial, (3 * c->nblock_red + 8) * sizeof(double)), "cudaMalloc reduction partials");
   c->launches_per_step = 2;
-  if (backend == SX_BACKEND_STENCIL || backend == SX_BACKEND_FFT) {
-    const int rc = backend == SX_BACKEND_STENCIL ? stencil_plan(c) : fft_plan(c);
+  if (backend != SX_BACKEND_GATHER) {
+    const int rc = backend == SX_BACKEND_STENCIL ? stencil_plan(c) : backend == SX_BACKEND_FFT ? fft_plan(c) : tc_plan(c);
     if (rc != SX_OK) {
       free_plan(c);
       return rc;

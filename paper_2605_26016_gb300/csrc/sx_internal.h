@@ -65,6 +65,8 @@ struct Tap {
 struct StencilPlan;
 // FFT-backend buffers and kernel spectrum (sx_fft.cu).
 struct FftPlan;
+// Tensor-core backend plan (sx_tc.cu).
+struct TcPlan;
 
 }  // namespace sx
 
@@ -104,6 +106,7 @@ struct sx_ctx {
   int64_t nblock_red;
   sx::StencilPlan *stencil;
   sx::FftPlan *fft;
+  sx::TcPlan *tc;
   int launches_per_step;
 };
 
@@ -137,5 +140,13 @@ void fft_free(sx_ctx *c);
 cudaError_t fft_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
 cudaError_t fft_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                           cudaStream_t st);
+
+// tensor-core path (sx_tc.cu)
+int tc_plan(sx_ctx *c);
+void tc_free(sx_ctx *c);
+cudaError_t tc_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
+cudaError_t tc_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
+                         cudaStream_t st);
+int tc_check_error(const sx_ctx *c);
 
 }  // namespace sx
