@@ -128,6 +128,25 @@ typedef struct {
   uint32_t replica;
 } sx_llg_params;
 
+/* Static minimisation on the product of unit spheres ("Static optimization
+ * and minimum-energy paths"): tangent force f_i = b_i - (b_i.S_i) S_i,
+ * exponential-map retraction R(S, u) = cos|u| S + sin|u| u/|u|.
+ *  SX_MIN_VP: velocity projection, per iteration
+ *      v <- v + dt/2 (f_prev + f), v <- max(v.f, 0)/(f.f) f (system-wide dot
+ *      products), S <- R(S, dt v + dt^2/2 f)   (dt: pseudo time, f in meV);
+ *  SX_MIN_DAMPED_LLG: normalised Heun steps of the LLG equation at T = 0,
+ *      dt in fs, damping alpha. */
+typedef enum { SX_MIN_VP = 0, SX_MIN_DAMPED_LLG = 1 } sx_min_method;
+
+typedef struct {
+  int method;       /* sx_min_method */
+  double dt;        /* VP pseudo time step, or LLG time step in fs */
+  double alpha;     /* damping of SX_MIN_DAMPED_LLG (ignored by VP) */
+  double tol;       /* stop when max_i |S_i x b_i| < tol (meV) */
+  int max_iter;     /* iteration cap */
+  int check_every;  /* iterations between convergence checks, >= 1 */
+} sx_min_params;
+
 /* Create a context for a lattice.  Host-only: makes no CUDA call.
  * SX_ERR_ARG for n[k] < 1, nsub outside 1..SX_MAX_SUB, a singular cell. */
 int sx_create(sx_ctx **out, const sx_lattice *lat);
@@ -212,6 +231,17 @@ int sx_llg_heun_step_out(sx_ctx *ctx, const double *S_in, double *S_out, const s
  * pageable; pinned memory gives full copy bandwidth. */
 int sx_llg_heun_host(sx_ctx *ctx, double *S_host, const sx_llg_params *p, uint64_t step0, int nsteps,
                      void *stream);
+
+/* Minimise the energy from S (device, in place) with the plan's field
+ * backend; S_scratch (device, same size, no overlap) is overwritten.  Stops
+ * after max_iter iterations or when max_i |S_i x b_i| < tol at a check.
+ * *iters_out receives the iterations done, *torque_out the last measured
+ * torque (meV, -1 if never measured).  The first VP call allocates a
+ * 48 B/site workspace kept until sx_destroy.  Synchronises the stream.
+ * SX_ERR_ARG for dt <= 0, tol < 0, max_iter < 0, check_every < 1 or an
+ * unknown method. */
+int sx_minimise(sx_ctx *ctx, double *S, double *S_scratch, const sx_min_params *p, int *iters_out,
+                double *torque_out, void *stream);
 
 /* Total energy in meV and its parts, E_host[0] = total, [1] = bilinear
  * (-1/2 sum S.b_bil), [2] = Zeeman, [3] = anisotropy, [4] = dipolar, reduced

@@ -77,6 +77,7 @@ def lib():
                                ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64]
         L.orc_heun_sites.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _i64p, ctypes.c_int64, _dp]
+        L.orc_vp.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int64, _dp, _dp, ctypes.c_int]
         L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.orc_normals_block.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                         ctypes.c_uint64, _fp]
@@ -196,6 +197,17 @@ class Model:
         _check(lib().orc_heun_sites(self.h, _ptr(S, _dp), float(dt), float(alpha), float(T), int(seed), int(replica),
                                     int(step), _ptr(sites, _i64p), len(sites), _ptr(out, _dp)), "heun_sites")
         return out
+
+    def vp(self, S, dt, niter, state=None):
+        """Velocity-projection minimisation; returns (S, state) where state carries (v, f_prev)."""
+        S = self._spins(S).copy()
+        first = state is None
+        if first:
+            state = (np.zeros(3 * self.nsite), np.zeros(3 * self.nsite))
+        v, fp = state
+        _check(lib().orc_vp(self.h, _ptr(S, _dp), float(dt), int(niter), _ptr(v, _dp), _ptr(fp, _dp),
+                            1 if first else 0), "vp")
+        return S.reshape(self.shape), (v, fp)
 
     def heun(self, S, dt, alpha, T=0.0, seed=0, replica=0, step0=0, nsteps=1):
         """Return a new spin array after nsteps normalised Heun steps."""

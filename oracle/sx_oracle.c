@@ -910,6 +910,71 @@ int orc_heun_sites(void *h, const double *S, double dt, double alpha, double T, 
   return err ? -1 : 0;
 }
 
+/* ------------------------------------------------------------------ minimisation */
+
+/* Exponential-map retraction ("Static optimization and minimum-energy paths"):
+ * R(S, u) = cos|u| S + sin|u| u/|u| for a tangent u (limit S for |u| = 0). */
+static void retract_exp(double S[3], const double u[3]) {
+  double a = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  if (a == 0.0) return;
+  double c = cos(a), s = sin(a) / a;
+  for (int k = 0; k < 3; k++) S[k] = c * S[k] + s * u[k];
+  normalise(S);
+}
+
+/* Velocity-projection minimisation, niter iterations, in place on S.
+ * Force f = b - (b.S) S (tangent part of -dH/dS).  Each iteration:
+ *   v <- v + dt/2 (f_prev + f)            (skipped on the first iteration: v = 0)
+ *   v <- max(v.f, 0) / (f.f) * f          (sums over the whole system)
+ *   S <- R_exp(S, dt v + dt^2/2 f)
+ * vstate (3N) and fprev (3N) carry v and f between calls; *first = 1 starts afresh. */
+int orc_vp(void *h, double *S, double dt, int64_t niter, double *vstate, double *fprev, int first) {
+  orc_model *m = (orc_model *)h;
+  if (!m->built) {
+    int e = orc_build(m);
+    if (e) return e;
+  }
+  int64_t N = m->nsite;
+  double *b = (double *)malloc(sizeof(double) * 3 * N);
+  double *f = (double *)malloc(sizeof(double) * 3 * N);
+  if (!b || !f) {
+    free(b);
+    free(f);
+    return -3;
+  }
+  for (int64_t it = 0; it < niter; it++) {
+    orc_field(m, S, b);
+    double p = 0.0, F2 = 0.0;
+    for (int64_t i = 0; i < N; i++) {
+      double Si[3] = {S[i], S[N + i], S[2 * N + i]}, bi[3] = {b[i], b[N + i], b[2 * N + i]};
+      double d = bi[0] * Si[0] + bi[1] * Si[1] + bi[2] * Si[2];
+      for (int k = 0; k < 3; k++) {
+        double fk = bi[k] - d * Si[k];
+        f[k * N + i] = fk;
+        double vk = (first && it == 0) ? 0.0 : vstate[k * N + i] + 0.5 * dt * (fprev[k * N + i] + fk);
+        vstate[k * N + i] = vk;
+        p += vk * fk;
+        F2 += fk * fk;
+      }
+    }
+    double c = (p > 0.0 && F2 > 0.0) ? p / F2 : 0.0;
+    for (int64_t i = 0; i < N; i++) {
+      double Si[3] = {S[i], S[N + i], S[2 * N + i]}, u[3];
+      for (int k = 0; k < 3; k++) {
+        double fk = f[k * N + i];
+        vstate[k * N + i] = c * fk;
+        fprev[k * N + i] = fk;
+        u[k] = dt * c * fk + 0.5 * dt * dt * fk;
+      }
+      retract_exp(Si, u);
+      for (int k = 0; k < 3; k++) S[k * N + i] = Si[k];
+    }
+  }
+  free(b);
+  free(f);
+  return 0;
+}
+
 int orc_num_threads(void) { return omp_get_max_threads(); }
 
 /* physical constants as used here, for tests */

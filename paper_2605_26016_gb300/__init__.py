@@ -30,7 +30,8 @@ PRECISIONS = {"fp64": SX_PREC_FP64, "fp32": SX_PREC_FP32, "tf32": SX_PREC_TF32, 
 EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shell_radius", "sx_add_shell_exchange",
            "sx_add_dmi", "sx_add_bonds", "sx_set_zeeman", "sx_set_anisotropy", "sx_set_dipolar", "sx_get_taps",
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
-           "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc")
+           "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise")
+SX_MIN_VP, SX_MIN_DAMPED_LLG = 0, 1
 
 
 class sx_lattice(ctypes.Structure):
@@ -49,6 +50,11 @@ sx_tap = sx_bond
 class sx_llg_params(ctypes.Structure):
     _fields_ = [("dt_fs", ctypes.c_double), ("alpha", ctypes.c_double), ("T_kelvin", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("replica", ctypes.c_uint32)]
+
+
+class sx_min_params(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("dt", ctypes.c_double), ("alpha", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
 
 
 class SxError(RuntimeError):
@@ -98,6 +104,8 @@ def lib():
                                                   ctypes.c_uint64, vp, vp]),
             "sx_plan_info": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
             "sx_torque_max_noalloc": (ctypes.c_int, [vp, vp, i64, dp, vp]),
+            "sx_minimise": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_min_params), ctypes.POINTER(ctypes.c_int),
+                                           dp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -285,6 +293,19 @@ def sx_torque_max_noalloc(S, b, nsite, stream=None):
     return out.value
 
 
+def sx_minimise(ctx, S, S_scratch, nsite, method="vp", dt=0.05, alpha=1.0, tol=1e-8, max_iter=1000, check_every=50,
+                stream=None):
+    """Minimise in place; returns (iterations, last measured max |S x b| in meV)."""
+    p = sx_min_params()
+    p.method = {"vp": SX_MIN_VP, "damped_llg": SX_MIN_DAMPED_LLG}.get(method, method)
+    p.dt, p.alpha, p.tol, p.max_iter, p.check_every = float(dt), float(alpha), float(tol), int(max_iter), int(check_every)
+    it = ctypes.c_int()
+    tq = ctypes.c_double()
+    _chk(lib().sx_minimise(ctx, _dev_ptr(S, 3 * nsite), _dev_ptr(S_scratch, 3 * nsite), ctypes.byref(p),
+                           ctypes.byref(it), ctypes.byref(tq), _stream(stream)), "sx_minimise")
+    return it.value, tq.value
+
+
 def sx_thermal_normals(seed, replica, site0, n, step, eta, stream=None):
     return _chk(lib().sx_thermal_normals(int(seed), int(replica), int(site0), int(n), int(step),
                                          _dev_ptr(eta, 3 * n, "float32"), _stream(stream)), "sx_thermal_normals")
@@ -359,6 +380,12 @@ class SpinSystem:
 
     def energy(self, S, stream=None):
         return sx_energy(self.ctx, S, self.nsite, stream)
+
+    def minimise(self, S, scratch=None, stream=None, **kw):
+        import torch
+        if scratch is None:
+            scratch = torch.empty_like(S)
+        return sx_minimise(self.ctx, S, scratch, self.nsite, stream=stream, **kw)
 
     def torque_max(self, S, stream=None):
         return sx_torque_max(self.ctx, S, self.nsite, stream)

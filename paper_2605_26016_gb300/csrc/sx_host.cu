@@ -185,6 +185,8 @@ void free_plan(sx_ctx *c) {
   if (c->stencil) stencil_free(c);
   if (c->fft) fft_free(c);
   if (c->tc) tc_free(c);
+  cudaFree(c->d_min);
+  c->d_min = nullptr;
   cudaFree(c->d_taps);
   cudaFree(c->d_tap_off);
   cudaFree(c->d_work);
@@ -564,6 +566,20 @@ int sx_llg_heun_host(sx_ctx *c, double *S_host, const sx_llg_params *p, uint64_t
     return cuda_error(e, "device to host copy");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(e, "stream synchronize");
   return SX_OK;
+}
+
+int sx_minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p, int *iters_out,
+                double *torque_out, void *stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if ((rc = check_spin_ptr(S, "S")) || (rc = check_spin_ptr(S_scratch, "S_scratch"))) return rc;
+  if (overlaps(S, S_scratch, 3 * (size_t)c->geo.nsite * sizeof(double)))
+    return set_error(SX_ERR_ARG, "S and S_scratch overlap");
+  if (!p) return set_error(SX_ERR_ARG, "null minimiser parameters");
+  if (p->method != SX_MIN_VP && p->method != SX_MIN_DAMPED_LLG) return set_error(SX_ERR_ARG, "unknown method");
+  if (!(p->dt > 0.0) || !(p->tol >= 0.0) || p->max_iter < 0 || p->check_every < 1 || !(p->alpha >= 0.0))
+    return set_error(SX_ERR_ARG, "bad minimiser parameters");
+  return minimise(c, S, S_scratch, p, iters_out, torque_out, (cudaStream_t)stream, backend_field, backend_step);
 }
 
 int sx_energy(sx_ctx *c, const double *S, double *E_host, void *stream) {

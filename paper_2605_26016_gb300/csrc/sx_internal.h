@@ -107,6 +107,7 @@ struct sx_ctx {
   sx::StencilPlan *stencil;
   sx::FftPlan *fft;
   sx::TcPlan *tc;
+  double *d_min;  // minimiser workspace (velocity, force, partials), allocated on first use
   int launches_per_step;
 };
 
@@ -140,6 +141,12 @@ void fft_free(sx_ctx *c);
 cudaError_t fft_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
 cudaError_t fft_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                           cudaStream_t st);
+
+// minimisation (sx_min.cu)
+int minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p, int *iters_out, double *torque_out,
+             cudaStream_t st, cudaError_t (*field)(const sx_ctx *, const double *, double *, bool, cudaStream_t),
+             cudaError_t (*step)(const sx_ctx *, const double *, double *, const HeunConst &, uint64_t,
+                                 cudaStream_t));
 
 // tensor-core path (sx_tc.cu)
 int tc_plan(sx_ctx *c);

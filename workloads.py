@@ -59,6 +59,33 @@ def random_spins(nsub, n, seed):
     return np.ascontiguousarray(S)
 
 
+def hopf_ansatz(n, radius, center=None):
+    """Toroidal Hopf-map texture with Hopf index 1 on a simple-cubic grid, shape (3, 1, nz, ny, nx).
+
+    A degree-1 map of space into the 3-sphere, q = (cos f(r), sin f(r) r/|r|) with
+    f = pi (1 - r/radius) inside the ball and 0 outside, composed with the Hopf
+    projection Z1 = q0 + i q3, Z2 = q1 + i q2 ->
+    S = (2 Re Z1 conj(Z2), 2 Im Z1 conj(Z2), |Z1|^2 - |Z2|^2).  S -> +z far away; the
+    preimage of -z is the ring r = radius/2 in the plane through the centre.
+    """
+    nx, ny, nz = n
+    c = np.asarray(center if center is not None else [(nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2], dtype=np.float64)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    rx, ry, rz = x - c[0], y - c[1], z - c[2]
+    r = np.sqrt(rx * rx + ry * ry + rz * rz)
+    f = np.where(r < radius, np.pi * (1.0 - r / radius), 0.0)
+    inv = np.where(r > 0, 1.0 / np.where(r > 0, r, 1.0), 0.0)
+    q0 = np.cos(f)
+    sf = np.sin(f) * inv
+    q1, q2, q3 = sf * rx, sf * ry, sf * rz
+    z1 = q0 + 1j * q3
+    z2 = q1 + 1j * q2
+    w = z1 * np.conj(z2)
+    S = np.stack([2 * w.real, 2 * w.imag, np.abs(z1) ** 2 - np.abs(z2) ** 2])
+    S /= np.sqrt((S * S).sum(0))
+    return np.ascontiguousarray(S.reshape(3, 1, nz, ny, nx))
+
+
 def uniform_spins(nsub, n, direction):
     d = np.asarray(direction, dtype=np.float64)
     d = d / np.sqrt((d * d).sum())
