@@ -78,6 +78,11 @@ def lib():
         L.orc_heun_sites.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _i64p, ctypes.c_int64, _dp]
         L.orc_vp.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int64, _dp, _dp, ctypes.c_int]
+        L.orc_geodesic.restype = ctypes.c_double
+        L.orc_geodesic.argtypes = [ctypes.c_int64, _dp, _dp]
+        L.orc_gneb.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                               ctypes.c_int64, _dp, _dp]
+        L.orc_string.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _dp, _dp]
         L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.orc_normals_block.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                         ctypes.c_uint64, _fp]
@@ -209,12 +214,46 @@ class Model:
                             1 if first else 0), "vp")
         return S.reshape(self.shape), (v, fp)
 
+    def _chain(self, images):
+        img = np.ascontiguousarray(np.asarray(images, dtype=np.float64)).copy()
+        if img.size % (3 * self.nsite) or img.size // (3 * self.nsite) < 3:
+            raise ValueError("a chain needs at least 3 images of %d spins" % self.nsite)
+        return img.reshape(-1, 3 * self.nsite)
+
+    def gneb(self, images, dt, k, niter, climbing=False):
+        """niter geodesic-NEB iterations (endpoints fixed); returns (images, energies, max force)."""
+        img = self._chain(images)
+        E = np.zeros(img.shape[0])
+        fm = ctypes.c_double(0.0)
+        _check(lib().orc_gneb(self.h, _ptr(img, _dp), img.shape[0], float(dt), float(k), 1 if climbing else 0,
+                              int(niter), _ptr(E, _dp), ctypes.byref(fm)), "gneb")
+        return img.reshape((img.shape[0],) + self.shape), E, fm.value
+
+    def string(self, images, dt, niter):
+        """niter string-method iterations (step, then equal-arc-length redistribution);
+        returns (images, energies, max force)."""
+        img = self._chain(images)
+        E = np.zeros(img.shape[0])
+        fm = ctypes.c_double(0.0)
+        _check(lib().orc_string(self.h, _ptr(img, _dp), img.shape[0], float(dt), int(niter), _ptr(E, _dp),
+                                ctypes.byref(fm)), "string")
+        return img.reshape((img.shape[0],) + self.shape), E, fm.value
+
     def heun(self, S, dt, alpha, T=0.0, seed=0, replica=0, step0=0, nsteps=1):
         """Return a new spin array after nsteps normalised Heun steps."""
         S = self._spins(S).copy()
         _check(lib().orc_heun(self.h, _ptr(S, _dp), float(dt), float(alpha), float(T), int(seed), int(replica),
                               int(step0), int(nsteps)), "heun")
         return S.reshape(self.shape)
+
+
+def geodesic(A, B):
+    """Geodesic distance between two spin fields: sqrt(sum_i arccos^2(A_i . B_i))."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).reshape(3, -1))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.float64).reshape(3, -1))
+    if A.shape != B.shape:
+        raise ValueError("spin fields differ in size")
+    return lib().orc_geodesic(A.shape[1], _ptr(A, _dp), _ptr(B, _dp))
 
 
 def philox4x32_10(ctr, key):

@@ -975,6 +975,203 @@ int orc_vp(void *h, double *S, double dt, int64_t niter, double *vstate, double 
   return 0;
 }
 
+/* ------------------------------------------------------------------ minimum-energy paths */
+
+/* geodesic distance between two spin fields ("Static optimization and
+ * minimum-energy paths"): d = [ sum_i arccos^2(S_i^(n).S_i^(m)) ]^(1/2) */
+double orc_geodesic(int64_t N, const double *A, const double *B) {
+  double s = 0.0;
+  for (int64_t i = 0; i < N; i++) {
+    double d = A[i] * B[i] + A[N + i] * B[N + i] + A[2 * N + i] * B[2 * N + i];
+    if (d > 1.0) d = 1.0;
+    if (d < -1.0) d = -1.0;
+    double a = acos(d);
+    s += a * a;
+  }
+  return sqrt(s);
+}
+
+/* tangent-space projection at S: x - (x.S) S */
+static void project(const double S[3], double x[3]) {
+  double d = x[0] * S[0] + x[1] * S[1] + x[2] * S[2];
+  for (int k = 0; k < 3; k++) x[k] -= d * S[k];
+}
+
+/* niter GNEB iterations on a chain of nimg images (img[n*3N ...]); endpoints fixed.
+ * Tangent: energy-weighted upwind combination of the projected differences
+ * t+ = P(S_{n+1} - S_n), t- = P(S_n - S_{n-1}), normalised over the image.
+ * Force on an interior image: f - (f.tau) tau + k (d_{n,n+1} - d_{n-1,n}) tau,
+ * or f - 2 (f.tau) tau for the climbing image (the highest-energy interior image
+ * when climbing != 0); f = b - (b.S) S.  Update S <- R_exp(S, dt F).
+ * E receives the image energies and *fmax_out the largest site force of the last iteration. */
+int orc_gneb(void *h, double *img, int nimg, double dt, double kspring, int climbing, int64_t niter, double *E,
+             double *fmax_out) {
+  orc_model *m = (orc_model *)h;
+  if (!m->built) {
+    int e = orc_build(m);
+    if (e) return e;
+  }
+  if (nimg < 3) return -1;
+  int64_t N = m->nsite;
+  double *b = (double *)malloc(sizeof(double) * 3 * N);
+  double *F = (double *)malloc(sizeof(double) * 3 * N * nimg);
+  if (!b || !F) {
+    free(b);
+    free(F);
+    return -3;
+  }
+  for (int64_t it = 0; it < niter; it++) {
+    for (int n = 0; n < nimg; n++) E[n] = orc_energy(m, img + (int64_t)n * 3 * N, NULL);
+    int top = 1;
+    for (int n = 1; n < nimg - 1; n++)
+      if (E[n] > E[top]) top = n;
+    double worst = 0.0;
+    for (int n = 1; n < nimg - 1; n++) {
+      double *S = img + (int64_t)n * 3 * N, *Sp = S + 3 * N, *Sm = S - 3 * N;
+      orc_field(m, S, b);
+      double a, bb;
+      double dEp = E[n + 1] - E[n], dEm = E[n - 1] - E[n];
+      if (E[n + 1] > E[n] && E[n] > E[n - 1]) {
+        a = 1.0;
+        bb = 0.0;
+      } else if (E[n + 1] < E[n] && E[n] < E[n - 1]) {
+        a = 0.0;
+        bb = 1.0;
+      } else {
+        double emax = fmax(fabs(dEp), fabs(dEm)), emin = fmin(fabs(dEp), fabs(dEm));
+        if (E[n + 1] > E[n - 1]) {
+          a = emax;
+          bb = emin;
+        } else {
+          a = emin;
+          bb = emax;
+        }
+      }
+      double tt = 0.0, ft = 0.0;
+      double *tau = F + (int64_t)n * 3 * N; /* tau stored temporarily in F */
+      for (int64_t i = 0; i < N; i++) {
+        double s[3] = {S[i], S[N + i], S[2 * N + i]}, tp[3], tm[3], bi[3] = {b[i], b[N + i], b[2 * N + i]};
+        for (int k = 0; k < 3; k++) {
+          tp[k] = Sp[k * N + i] - s[k];
+          tm[k] = s[k] - Sm[k * N + i];
+        }
+        project(s, tp);
+        project(s, tm);
+        project(s, bi);
+        for (int k = 0; k < 3; k++) {
+          double t = a * tp[k] + bb * tm[k];
+          tau[k * N + i] = t;
+          tt += t * t;
+          ft += bi[k] * t;
+        }
+      }
+      double tn = sqrt(tt);
+      double ftau = tn > 0 ? ft / tn : 0.0;
+      double dpl = orc_geodesic(N, S, Sp), dmi = orc_geodesic(N, Sm, S);
+      int ci = climbing && n == top;
+      double cf = ci ? 2.0 : 1.0, ks = ci ? 0.0 : kspring * (dpl - dmi);
+      for (int64_t i = 0; i < N; i++) {
+        double s[3] = {S[i], S[N + i], S[2 * N + i]}, bi[3] = {b[i], b[N + i], b[2 * N + i]}, f2 = 0.0;
+        project(s, bi);
+        for (int k = 0; k < 3; k++) {
+          double th = tn > 0 ? tau[k * N + i] / tn : 0.0;
+          double Fk = bi[k] - cf * ftau * th + ks * th;
+          tau[k * N + i] = Fk;
+          f2 += Fk * Fk;
+        }
+        if (sqrt(f2) > worst) worst = sqrt(f2);
+      }
+    }
+    for (int n = 1; n < nimg - 1; n++) {
+      double *S = img + (int64_t)n * 3 * N, *Fn = F + (int64_t)n * 3 * N;
+      for (int64_t i = 0; i < N; i++) {
+        double s[3] = {S[i], S[N + i], S[2 * N + i]}, u[3];
+        for (int k = 0; k < 3; k++) u[k] = dt * Fn[k * N + i];
+        retract_exp(s, u);
+        for (int k = 0; k < 3; k++) S[k * N + i] = s[k];
+      }
+    }
+    *fmax_out = worst;
+  }
+  for (int n = 0; n < nimg; n++) E[n] = orc_energy(m, img + (int64_t)n * 3 * N, NULL);
+  free(b);
+  free(F);
+  return 0;
+}
+
+/* niter string-method iterations: every interior image steps along its tangent
+ * force, S <- R_exp(S, dt f), then the images are redistributed at equal
+ * geodesic arc length by per-site spherical interpolation between neighbours.
+ * *fmax_out receives the largest site force |f| of the last iteration. */
+int orc_string(void *h, double *img, int nimg, double dt, int64_t niter, double *E, double *fmax_out) {
+  orc_model *m = (orc_model *)h;
+  if (!m->built) {
+    int e = orc_build(m);
+    if (e) return e;
+  }
+  if (nimg < 3) return -1;
+  int64_t N = m->nsite;
+  double *b = (double *)malloc(sizeof(double) * 3 * N);
+  double *old = (double *)malloc(sizeof(double) * 3 * N * nimg);
+  double *L = (double *)malloc(sizeof(double) * nimg);
+  if (!b || !old || !L) {
+    free(b);
+    free(old);
+    free(L);
+    return -3;
+  }
+  for (int64_t it = 0; it < niter; it++) {
+    double worst = 0.0;
+    for (int n = 1; n < nimg - 1; n++) {
+      double *S = img + (int64_t)n * 3 * N;
+      orc_field(m, S, b);
+      for (int64_t i = 0; i < N; i++) {
+        double s[3] = {S[i], S[N + i], S[2 * N + i]}, u[3] = {b[i], b[N + i], b[2 * N + i]};
+        project(s, u);
+        double f = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        if (f > worst) worst = f;
+        for (int k = 0; k < 3; k++) u[k] *= dt;
+        retract_exp(s, u);
+        for (int k = 0; k < 3; k++) S[k * N + i] = s[k];
+      }
+    }
+    *fmax_out = worst;
+    memcpy(old, img, sizeof(double) * 3 * N * nimg);
+    L[0] = 0.0;
+    for (int n = 1; n < nimg; n++)
+      L[n] = L[n - 1] + orc_geodesic(N, old + (int64_t)(n - 1) * 3 * N, old + (int64_t)n * 3 * N);
+    for (int n = 1; n < nimg - 1; n++) {
+      double target = L[nimg - 1] * n / (nimg - 1);
+      int j = 0;
+      while (j < nimg - 2 && L[j + 1] < target) j++;
+      double seg = L[j + 1] - L[j];
+      double w = seg > 0 ? (target - L[j]) / seg : 0.0;
+      const double *A = old + (int64_t)j * 3 * N, *B = old + (int64_t)(j + 1) * 3 * N;
+      double *S = img + (int64_t)n * 3 * N;
+      for (int64_t i = 0; i < N; i++) {
+        double a[3] = {A[i], A[N + i], A[2 * N + i]}, c[3] = {B[i], B[N + i], B[2 * N + i]}, s[3];
+        double d = a[0] * c[0] + a[1] * c[1] + a[2] * c[2];
+        if (d > 1.0) d = 1.0;
+        if (d < -1.0) d = -1.0;
+        double th = acos(d);
+        if (th < 1e-12) {
+          for (int k = 0; k < 3; k++) s[k] = a[k];
+        } else {
+          double p = sin((1.0 - w) * th) / sin(th), q = sin(w * th) / sin(th);
+          for (int k = 0; k < 3; k++) s[k] = p * a[k] + q * c[k];
+        }
+        normalise(s);
+        for (int k = 0; k < 3; k++) S[k * N + i] = s[k];
+      }
+    }
+  }
+  for (int n = 0; n < nimg; n++) E[n] = orc_energy(m, img + (int64_t)n * 3 * N, NULL);
+  free(b);
+  free(old);
+  free(L);
+  return 0;
+}
+
 int orc_num_threads(void) { return omp_get_max_threads(); }
 
 /* physical constants as used here, for tests */

@@ -94,3 +94,38 @@ def uniform_spins(nsub, n, direction):
     for c in range(3):
         S[c] = d[c]
     return S
+
+
+def polar_chain(theta_a, theta_b, nimg, phi_bulge=0.0):
+    """A chain of nimg single-spin states S = (sin t cos p, sin t sin p, cos t), shape (nimg, 3, 1, 1, 1, 1):
+    t runs linearly from theta_a to theta_b, p = phi_bulge * sin(pi s) for s = n/(nimg-1), so the
+    endpoints lie in the x-z plane and the interior bulges towards +y."""
+    s = np.linspace(0.0, 1.0, nimg)
+    t = theta_a + (theta_b - theta_a) * s
+    p = phi_bulge * np.sin(np.pi * s)
+    S = np.stack([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)], axis=1)
+    return np.ascontiguousarray(S.reshape(nimg, 3, 1, 1, 1, 1))
+
+
+def nlerp_chain(A, B, nimg, jitter=0.0, seed=0):
+    """A chain of nimg spin fields between A and B (same shape): image n is the site-wise
+    normalised linear blend (1 - s) A + s B, s = n/(nimg-1), plus optional seeded Gaussian
+    jitter on the interior images.  Endpoints are A and B unchanged.  Antiparallel site
+    pairs are tilted by a fixed small vector before normalising."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((nimg,) + A.shape)
+    tilt = np.zeros_like(A)
+    tilt[0] = 1e-3
+    for n in range(nimg):
+        s = n / (nimg - 1)
+        if n == 0:
+            out[n] = A
+            continue
+        if n == nimg - 1:
+            out[n] = B
+            continue
+        X = (1.0 - s) * A + s * B + tilt
+        if jitter:
+            X = X + jitter * rng.standard_normal(A.shape)
+        out[n] = X / np.sqrt((X * X).sum(0))
+    return np.ascontiguousarray(out)
