@@ -147,6 +147,35 @@ typedef struct {
   int check_every;  /* iterations between convergence checks, >= 1 */
 } sx_min_params;
 
+/* Minimum-energy paths ("Static optimization and minimum-energy paths"):
+ * a chain of images Y_0 .. Y_{M-1}, each a whole spin field, with fixed
+ * endpoints.  Image distance: the geodesic metric
+ * d(Y_n, Y_m) = [sum_i arccos^2(S_i^n . S_i^m)]^(1/2).  With f = b - (b.S) S
+ * the tangent force of an image, t+ = P(S_{n+1} - S_n), t- = P(S_n - S_{n-1})
+ * (P: projection on the tangent plane of each spin) and tau^ the unit path
+ * tangent of image n in image space (t+ when E_{n+1} > E_n > E_{n-1}, t- when
+ * E_{n+1} < E_n < E_{n-1}, otherwise the energy-weighted sum with the larger
+ * of |E_{n+1} - E_n|, |E_{n-1} - E_n| on the side of the higher neighbour;
+ * Henkelman and Jonsson's tangent):
+ *  SX_PATH_GNEB:    F = f - (f.tau^) tau^ + k (d(n,n+1) - d(n-1,n)) tau^;
+ *  SX_PATH_CI_GNEB: as GNEB, but the highest-energy interior image moves
+ *                   with F = f - 2 (f.tau^) tau^;
+ *  both then move every interior image by S <- R(S, dt F) (exponential map);
+ *  SX_PATH_STRING:  S <- R(S, dt f) for every interior image, then the
+ *                   interior images are re-placed at equal geodesic arc
+ *                   length along the chain by per-site spherical
+ *                   interpolation between the two neighbouring old images. */
+typedef enum { SX_PATH_STRING = 0, SX_PATH_GNEB = 1, SX_PATH_CI_GNEB = 2 } sx_path_method;
+
+typedef struct {
+  int method;       /* sx_path_method */
+  double dt;        /* step of the retraction, rad per meV of force */
+  double k_spring;  /* GNEB spring constant, meV per rad (ignored by the string method) */
+  double tol;       /* stop when the largest site force |F| is below tol (meV) at a check */
+  int max_iter;     /* iteration cap */
+  int check_every;  /* iterations between convergence checks, >= 1 */
+} sx_path_params;
+
 /* Create a context for a lattice.  Host-only: makes no CUDA call.
  * SX_ERR_ARG for n[k] < 1, nsub outside 1..SX_MAX_SUB, a singular cell. */
 int sx_create(sx_ctx **out, const sx_lattice *lat);
@@ -242,6 +271,30 @@ int sx_llg_heun_host(sx_ctx *ctx, double *S_host, const sx_llg_params *p, uint64
  * unknown method. */
 int sx_minimise(sx_ctx *ctx, double *S, double *S_scratch, const sx_min_params *p, int *iters_out,
                 double *torque_out, void *stream);
+
+/* Iterations of a path method (see sx_path_params) on a chain of nimg images
+ * (3 .. 4096) stored back to back in `images` (device, image n at
+ * images + 3*nsite*n, each in the layout of sx_field), in place; images 0 and
+ * nimg-1 are not modified.  The field of every interior image is evaluated
+ * with the plan's backend each iteration; FP64 plans do the path arithmetic
+ * in FP64, other plans in FP32 with the spins kept and renormalised in FP64.
+ * Energies and geodesic sums are reduced in FP64 in a fixed order.  Stops
+ * after max_iter iterations or when the largest site force of an iteration
+ * is below tol (measured every check_every iterations and on the last).
+ * *iters_out: iterations done; E_host (nimg doubles, may be NULL): the image
+ * energies (meV) of the final chain; *fmax_host: the largest site force |F|
+ * (meV) of the last measured iteration, -1 if none ran.  The first call
+ * allocates a workspace of one chain (24 B per site per image) plus partial
+ * sums, kept until sx_destroy and grown for a longer chain.  Synchronises
+ * the stream.  SX_ERR_ARG for nimg out of range, an unknown method, dt <= 0,
+ * k_spring < 0, tol < 0, max_iter < 0 or check_every < 1. */
+int sx_path_step(sx_ctx *ctx, double *images, int nimg, const sx_path_params *p, int *iters_out, double *E_host,
+                 double *fmax_host, void *stream);
+
+/* Geodesic distance d(A, B) = [sum_i arccos^2(A_i . B_i)]^(1/2) between two
+ * spin fields of the context's lattice (device, layout of sx_field), in FP64
+ * (per-site angle atan2(|A_i x B_i|, A_i . B_i)).  Synchronises the stream. */
+int sx_geodesic(sx_ctx *ctx, const double *A, const double *B, double *d_host, void *stream);
 
 /* Total energy in meV and its parts, E_host[0] = total, [1] = bilinear
  * (-1/2 sum S.b_bil), [2] = Zeeman, [3] = anisotropy, [4] = dipolar, reduced

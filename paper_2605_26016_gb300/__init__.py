@@ -30,8 +30,11 @@ PRECISIONS = {"fp64": SX_PREC_FP64, "fp32": SX_PREC_FP32, "tf32": SX_PREC_TF32, 
 EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shell_radius", "sx_add_shell_exchange",
            "sx_add_dmi", "sx_add_bonds", "sx_set_zeeman", "sx_set_anisotropy", "sx_set_dipolar", "sx_get_taps",
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
-           "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise")
+           "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise", "sx_path_step",
+           "sx_geodesic")
 SX_MIN_VP, SX_MIN_DAMPED_LLG = 0, 1
+SX_PATH_STRING, SX_PATH_GNEB, SX_PATH_CI_GNEB = 0, 1, 2
+PATH_METHODS = {"string": SX_PATH_STRING, "gneb": SX_PATH_GNEB, "ci_gneb": SX_PATH_CI_GNEB}
 
 
 class sx_lattice(ctypes.Structure):
@@ -55,6 +58,11 @@ class sx_llg_params(ctypes.Structure):
 class sx_min_params(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("dt", ctypes.c_double), ("alpha", ctypes.c_double), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class sx_path_params(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("dt", ctypes.c_double), ("k_spring", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
 
 
 class SxError(RuntimeError):
@@ -106,6 +114,9 @@ def lib():
             "sx_torque_max_noalloc": (ctypes.c_int, [vp, vp, i64, dp, vp]),
             "sx_minimise": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_min_params), ctypes.POINTER(ctypes.c_int),
                                            dp, vp]),
+            "sx_path_step": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(sx_path_params),
+                                            ctypes.POINTER(ctypes.c_int), dp, dp, vp]),
+            "sx_geodesic": (ctypes.c_int, [vp, vp, vp, dp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -306,6 +317,31 @@ def sx_minimise(ctx, S, S_scratch, nsite, method="vp", dt=0.05, alpha=1.0, tol=1
     return it.value, tq.value
 
 
+def sx_path_step(ctx, images, nimg, nsite, method="gneb", dt=0.05, k_spring=1.0, tol=0.0, max_iter=100,
+                 check_every=50, stream=None):
+    """Path-method iterations on a chain (nimg images back to back, in place; endpoints fixed).
+    Returns (iterations, image energies in meV as a list, largest site force of the last measured
+    iteration in meV)."""
+    p = sx_path_params()
+    p.method = PATH_METHODS.get(method, method)
+    p.dt, p.k_spring, p.tol = float(dt), float(k_spring), float(tol)
+    p.max_iter, p.check_every = int(max_iter), int(check_every)
+    it = ctypes.c_int()
+    E = (ctypes.c_double * max(1, int(nimg)))()
+    fm = ctypes.c_double()
+    _chk(lib().sx_path_step(ctx, _dev_ptr(images, 3 * nsite * int(nimg)), int(nimg), ctypes.byref(p),
+                            ctypes.byref(it), E, ctypes.byref(fm), _stream(stream)), "sx_path_step")
+    return it.value, [E[i] for i in range(int(nimg))], fm.value
+
+
+def sx_geodesic(ctx, A, B, nsite, stream=None):
+    """Geodesic distance between two spin fields (FP64)."""
+    out = ctypes.c_double()
+    _chk(lib().sx_geodesic(ctx, _dev_ptr(A, 3 * nsite), _dev_ptr(B, 3 * nsite), ctypes.byref(out),
+                           _stream(stream)), "sx_geodesic")
+    return out.value
+
+
 def sx_thermal_normals(seed, replica, site0, n, step, eta, stream=None):
     return _chk(lib().sx_thermal_normals(int(seed), int(replica), int(site0), int(n), int(step),
                                          _dev_ptr(eta, 3 * n, "float32"), _stream(stream)), "sx_thermal_normals")
@@ -389,6 +425,13 @@ class SpinSystem:
 
     def torque_max(self, S, stream=None):
         return sx_torque_max(self.ctx, S, self.nsite, stream)
+
+    def path(self, images, method="gneb", stream=None, **kw):
+        """Path-method iterations on a chain tensor of shape (nimg, 3, nsub, nz, ny, nx), in place."""
+        return sx_path_step(self.ctx, images, images.shape[0], self.nsite, method=method, stream=stream, **kw)
+
+    def geodesic(self, A, B, stream=None):
+        return sx_geodesic(self.ctx, A, B, self.nsite, stream)
 
 
 def system_from_workload(workload, n, pbc=None, cell=None, **override):

@@ -187,6 +187,9 @@ void free_plan(sx_ctx *c) {
   if (c->tc) tc_free(c);
   cudaFree(c->d_min);
   c->d_min = nullptr;
+  cudaFree(c->d_path);
+  c->d_path = nullptr;
+  c->path_bytes = 0;
   cudaFree(c->d_taps);
   cudaFree(c->d_tap_off);
   cudaFree(c->d_work);
@@ -580,6 +583,32 @@ int sx_minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p,
   if (!(p->dt > 0.0) || !(p->tol >= 0.0) || p->max_iter < 0 || p->check_every < 1 || !(p->alpha >= 0.0))
     return set_error(SX_ERR_ARG, "bad minimiser parameters");
   return minimise(c, S, S_scratch, p, iters_out, torque_out, (cudaStream_t)stream, backend_field, backend_step);
+}
+
+int sx_path_step(sx_ctx *c, double *images, int nimg, const sx_path_params *p, int *iters_out, double *E_host,
+                 double *fmax_host, void *stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if ((rc = check_spin_ptr(images, "images"))) return rc;
+  if (!p) return set_error(SX_ERR_ARG, "null path parameters");
+  if (nimg < 3 || nimg > path_max_images())
+    return set_error(SX_ERR_ARG, "a chain needs 3 .. " + std::to_string(path_max_images()) + " images");
+  if (p->method != SX_PATH_STRING && p->method != SX_PATH_GNEB && p->method != SX_PATH_CI_GNEB)
+    return set_error(SX_ERR_ARG, "unknown path method");
+  if (!(p->dt > 0.0) || !isfinite(p->dt) || !(p->k_spring >= 0.0) || !isfinite(p->k_spring) || !(p->tol >= 0.0) ||
+      p->max_iter < 0 || p->check_every < 1)
+    return set_error(SX_ERR_ARG, "bad path parameters");
+  cudaError_t e = path_run(c, images, nimg, p, iters_out, E_host, fmax_host, (cudaStream_t)stream, backend_field);
+  return e == cudaSuccess ? SX_OK : cuda_error(e, "path step");
+}
+
+int sx_geodesic(sx_ctx *c, const double *A, const double *B, double *d_host, void *stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if ((rc = check_spin_ptr(A, "A")) || (rc = check_spin_ptr(B, "B"))) return rc;
+  if (!d_host) return set_error(SX_ERR_ARG, "d_host is null");
+  cudaError_t e = geodesic(c, A, B, d_host, (cudaStream_t)stream);
+  return e == cudaSuccess ? SX_OK : cuda_error(e, "geodesic");
 }
 
 int sx_energy(sx_ctx *c, const double *S, double *E_host, void *stream) {

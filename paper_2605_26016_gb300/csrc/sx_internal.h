@@ -108,6 +108,8 @@ struct sx_ctx {
   sx::FftPlan *fft;
   sx::TcPlan *tc;
   double *d_min;  // minimiser workspace (velocity, force, partials), allocated on first use
+  double *d_path;     // path-method workspace (second chain, partial sums), allocated on first use
+  size_t path_bytes;  // its size
   int launches_per_step;
 };
 
@@ -141,6 +143,14 @@ void fft_free(sx_ctx *c);
 cudaError_t fft_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
 cudaError_t fft_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                           cudaStream_t st);
+
+typedef cudaError_t (*FieldFn)(const sx_ctx *, const double *, double *, bool, cudaStream_t);
+
+// minimum-energy paths (sx_path.cu)
+int path_max_images();
+cudaError_t path_run(sx_ctx *c, double *img, int nimg, const sx_path_params *p, int *iters_out, double *E_host,
+                     double *fmax_host, cudaStream_t st, FieldFn field);
+cudaError_t geodesic(const sx_ctx *c, const double *A, const double *B, double *out_host, cudaStream_t st);
 
 // minimisation (sx_min.cu)
 int minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p, int *iters_out, double *torque_out,

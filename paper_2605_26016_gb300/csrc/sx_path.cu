@@ -1,0 +1,586 @@
+// Minimum-energy paths ("Static optimization and minimum-energy paths"), batched
+// over the images of a chain.  An image is a whole spin field; the chain is
+// nimg images back to back, image n at X + 3 N n.  Endpoints stay fixed.
+//
+// Geodesic image distance d(Y_n, Y_m) = [sum_i arccos^2(S_i^n . S_i^m)]^(1/2);
+// the per-site angle is taken as atan2(|S x T|, S . T), which equals arccos(S.T)
+// for unit vectors and stays accurate for nearly parallel spins.
+//
+// GNEB (Bessarab et al., geodesic NEB): with f = b - (b.S) S the tangent force
+// and t+ = P(S_{n+1} - S_n), t- = P(S_n - S_{n-1}) the projected differences,
+// the path tangent is tau = a t+ + c t- (energy-weighted upwind choice of
+// Henkelman and Jonsson) normalised over the whole image, and
+//   F = f - (f.tau^) tau^ + k (d_{n,n+1} - d_{n-1,n}) tau^      (GNEB)
+//   F = f - 2 (f.tau^) tau^                                     (climbing image)
+// followed by S <- R_exp(S, dt F).  Because tau is linear in t+ and t-, one
+// pass over the chain reduces the five inner products t+.t+, t+.t-, t-.t-,
+// f.t+, f.t- per image (together with the image energy and the geodesic
+// distance to the next image); a one-thread kernel then turns them into two
+// coefficients per image, F = f + A t+ + C t-, and a second pass moves the
+// images.  No host synchronisation inside an iteration.
+//
+// String method: every interior image steps S <- R_exp(S, dt f); then the
+// images are placed at equal geodesic arc length by per-site spherical
+// interpolation between the two neighbouring old images.
+//
+// Buffers: the caller's chain X and a library chain W alternate.  The fields of
+// the interior images of X are written into the interior slots of the other
+// chain, and each update thread overwrites the field values it has just read
+// at its own site with the new spins, so one extra chain suffices.
+//
+// Precision: FP64 plans do every step in FP64 (libm-style trig).  Other plans
+// (FP32 field) do the path arithmetic in FP32 on FP32-rounded spins with the
+// state kept in FP64: the update S + d is formed and renormalised in FP64, the
+// energies are summed in FP64.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "sx_device.cuh"
+#include "sx_internal.h"
+
+namespace sx {
+
+namespace {
+
+constexpr int kPT = 256;     // threads per block
+constexpr int kNS = 8;       // partial sums per (image, block)
+constexpr int kMaxImg = 4096;
+
+// partial slots: 0 energy, 1 t+.t+, 2 t+.t-, 3 t-.t-, 4 f.t+, 5 f.t-, 6 theta^2 to the next image
+enum { P_E = 0, P_PP, P_PM, P_MM, P_FP, P_FM, P_D2 };
+
+__device__ __forceinline__ double block_sum(double v, double *sm) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kPT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double *sm) {
+  sm[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kPT / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const double r = sm[0];
+  __syncthreads();
+  return r;
+}
+
+template <typename R>
+__device__ __forceinline__ R to_r(double v);
+template <>
+__device__ __forceinline__ double to_r<double>(double v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float to_r<float>(double v) {
+  return f64_to_f32(v);
+}
+
+template <typename R>
+__device__ __forceinline__ void load3(const double *__restrict__ p, long long N, long long i, R s[3]) {
+  s[0] = to_r<R>(p[i]);
+  s[1] = to_r<R>(p[N + i]);
+  s[2] = to_r<R>(p[2 * N + i]);
+}
+
+template <typename R>
+__device__ __forceinline__ R dot3(const R a[3], const R b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// x <- x - (x.s) s
+template <typename R>
+__device__ __forceinline__ void project(const R s[3], R x[3]) {
+  const R d = dot3(x, s);
+  x[0] -= d * s[0];
+  x[1] -= d * s[1];
+  x[2] -= d * s[2];
+}
+
+__device__ __forceinline__ double r_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float r_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double r_sin(double x) { return sin(x); }
+__device__ __forceinline__ float r_sin(float x) { return sinf(x); }
+
+// angle between unit vectors s and t = s + dl: |s x t| = |s x dl|, s.t = 1 - |dl|^2/2
+template <typename R>
+__device__ __forceinline__ R site_angle(const R s[3], const R dl[3]) {
+  const R c0 = s[1] * dl[2] - s[2] * dl[1];
+  const R c1 = s[2] * dl[0] - s[0] * dl[2];
+  const R c2 = s[0] * dl[1] - s[1] * dl[0];
+  return r_atan2(r_sqrt(c0 * c0 + c1 * c1 + c2 * c2), R(1) - R(0.5) * dot3(dl, dl));
+}
+
+// S <- R_exp(S, u) for a tangent u; s64 is the FP64 state, sr its copy in R.
+__device__ __forceinline__ void retract(const double s64[3], const double sr[3], const double u[3], double out[3]) {
+  (void)sr;
+  const double a = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  if (a == 0.0) {
+    out[0] = s64[0];
+    out[1] = s64[1];
+    out[2] = s64[2];
+    return;
+  }
+  const double c = cos(a), sn = sin(a) / a;
+  double x[3];
+  for (int k = 0; k < 3; ++k) x[k] = c * s64[k] + sn * u[k];
+  const double r = 1.0 / sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  for (int k = 0; k < 3; ++k) out[k] = x[k] * r;
+}
+
+// FP32 arithmetic, FP64 state: d = (cos a - 1) s + (sin a / a) u with
+// cos a - 1 = -2 sin^2(a/2), then S' = N[S + d] in FP64.
+__device__ __forceinline__ void retract(const double s64[3], const float sr[3], const float u[3], double out[3]) {
+  const float a = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const float h = sinf(0.5f * a);
+  const float c1 = -2.0f * h * h;
+  const float sc = a > 0.0f ? sinf(a) / a : 1.0f;
+  const float d[3] = {c1 * sr[0] + sc * u[0], c1 * sr[1] + sc * u[1], c1 * sr[2] + sc * u[2]};
+  renormalise64(s64, d, out);
+}
+
+// Per (image, block) partial sums.  blockIdx.y = n in 0 .. nimg-2: the
+// geodesic angle to image n+1, and for n >= 1 (FULL) the energy and the five
+// tangent inner products of interior image n.  B holds the field of image n
+// in slot n.
+template <typename R, bool FULL>
+__global__ void __launch_bounds__(kPT) k_path_reduce(const double *__restrict__ X, const double *__restrict__ B,
+                                                     long long N, long long ncell, OnSite os,
+                                                     double *__restrict__ partial) {
+  __shared__ double sm[kPT];
+  const int n = blockIdx.y;
+  const double *S = X + 3 * N * (long long)n;
+  const double *Sp = S + 3 * N;
+  R acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  double e = 0.0;
+  const bool interior = FULL && n >= 1;
+  for (long long i = (long long)blockIdx.x * kPT + threadIdx.x; i < N; i += (long long)gridDim.x * kPT) {
+    R s[3], sp[3];
+    load3<R>(S, N, i, s);
+    load3<R>(Sp, N, i, sp);
+    R tp[3] = {sp[0] - s[0], sp[1] - s[1], sp[2] - s[2]};
+    const R th = site_angle<R>(s, tp);
+    acc[P_D2] += th * th;
+    if (interior) {
+      const double *Sm = S - 3 * N, *b = B + 3 * N * (long long)n;
+      R sm_[3], br[3];
+      load3<R>(Sm, N, i, sm_);
+      const double b0 = b[i], b1 = b[N + i], b2 = b[2 * N + i];
+      const double s0 = S[i], s1 = S[N + i], s2 = S[2 * N + i];
+      const int a = (int)(i / ncell);
+      e += -0.5 * (s0 * (b0 + os.zee[a][0]) + s1 * (b1 + os.zee[a][1]) + s2 * (b2 + os.zee[a][2]));
+      br[0] = to_r<R>(b0);
+      br[1] = to_r<R>(b1);
+      br[2] = to_r<R>(b2);
+      R tm[3] = {s[0] - sm_[0], s[1] - sm_[1], s[2] - sm_[2]};
+      project<R>(s, tp);
+      project<R>(s, tm);
+      project<R>(s, br);
+      acc[P_PP] += dot3(tp, tp);
+      acc[P_PM] += dot3(tp, tm);
+      acc[P_MM] += dot3(tm, tm);
+      acc[P_FP] += dot3(br, tp);
+      acc[P_FM] += dot3(br, tm);
+    }
+  }
+  double *out = partial + ((long long)n * gridDim.x + blockIdx.x) * kNS;
+  const double d2 = block_sum((double)acc[P_D2], sm);
+  if (threadIdx.x == 0) out[P_D2] = d2;
+  if (interior) {
+    const double v0 = block_sum(e, sm);
+    double v[5];
+    for (int k = 0; k < 5; ++k) v[k] = block_sum((double)acc[P_PP + k], sm);
+    if (threadIdx.x == 0) {
+      out[P_E] = v0;
+      for (int k = 0; k < 5; ++k) out[P_PP + k] = v[k];
+    }
+  }
+}
+
+// sums[n][k] = sum over blocks, one block per image slot n (fixed order: deterministic)
+__global__ void __launch_bounds__(kPT) k_path_sum(const double *__restrict__ partial, int nb, int full,
+                                                  double *__restrict__ sums) {
+  __shared__ double sm[kPT];
+  const int n = blockIdx.x;
+  const double *p = partial + (long long)n * nb * kNS;
+  for (int k = 0; k < 7; ++k) {
+    if (k != P_D2 && !(full && n >= 1)) {
+      if (threadIdx.x == 0) sums[n * kNS + k] = 0.0;
+      continue;
+    }
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < nb; j += kPT) acc += p[(long long)j * kNS + k];
+    acc = block_sum(acc, sm);
+    if (threadIdx.x == 0) sums[n * kNS + k] = acc;
+  }
+}
+
+// Per-image coefficients (one thread; nimg <= kMaxImg).
+//  GNEB / CI: coef[n] = {A, C, 0, 0} with F = f + A t+ + C t-.
+//  string:    coef[n] = {0, 0, j, w}: image n becomes slerp(old_j, old_j+1; w).
+// E[n] receives the image energies (endpoints from eend[0] and eend[5]).
+__global__ void k_path_coef(const double *__restrict__ sums, const double *__restrict__ eend, int nimg, int method,
+                            double kspring, double *__restrict__ coef, double *__restrict__ E,
+                            double *__restrict__ L) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int M = nimg;
+  E[0] = eend[0];
+  E[M - 1] = eend[5];
+  for (int n = 1; n < M - 1; ++n) E[n] = sums[n * kNS + P_E];
+  if (method == SX_PATH_STRING) {
+    L[0] = 0.0;
+    for (int n = 0; n < M - 1; ++n) L[n + 1] = L[n] + sqrt(sums[n * kNS + P_D2]);
+    for (int n = 1; n < M - 1; ++n) {
+      const double target = L[M - 1] * n / (M - 1);
+      int j = 0;
+      while (j < M - 2 && L[j + 1] < target) ++j;
+      const double seg = L[j + 1] - L[j];
+      coef[4 * n + 0] = 0.0;
+      coef[4 * n + 1] = 0.0;
+      coef[4 * n + 2] = (double)j;
+      coef[4 * n + 3] = seg > 0.0 ? (target - L[j]) / seg : 0.0;
+    }
+    return;
+  }
+  int top = 1;
+  for (int n = 2; n < M - 1; ++n)
+    if (E[n] > E[top]) top = n;
+  for (int n = 1; n < M - 1; ++n) {
+    const double *s = sums + n * kNS;
+    const double dEp = E[n + 1] - E[n], dEm = E[n - 1] - E[n];
+    double a, c;
+    if (E[n + 1] > E[n] && E[n] > E[n - 1]) {
+      a = 1.0;
+      c = 0.0;
+    } else if (E[n + 1] < E[n] && E[n] < E[n - 1]) {
+      a = 0.0;
+      c = 1.0;
+    } else {
+      const double hi = fmax(fabs(dEp), fabs(dEm)), lo = fmin(fabs(dEp), fabs(dEm));
+      if (E[n + 1] > E[n - 1]) {
+        a = hi;
+        c = lo;
+      } else {
+        a = lo;
+        c = hi;
+      }
+    }
+    const double tt = a * a * s[P_PP] + 2.0 * a * c * s[P_PM] + c * c * s[P_MM];
+    const double tn = sqrt(fmax(tt, 0.0));
+    const double ftau = tn > 0.0 ? (a * s[P_FP] + c * s[P_FM]) / tn : 0.0;
+    const bool ci = method == SX_PATH_CI_GNEB && n == top;
+    const double dplus = sqrt(sums[n * kNS + P_D2]), dminus = sqrt(sums[(n - 1) * kNS + P_D2]);
+    const double ks = ci ? 0.0 : kspring * (dplus - dminus);
+    const double cc = tn > 0.0 ? (ks - (ci ? 2.0 : 1.0) * ftau) / tn : 0.0;
+    coef[4 * n + 0] = cc * a;
+    coef[4 * n + 1] = cc * c;
+    coef[4 * n + 2] = 0.0;
+    coef[4 * n + 3] = 0.0;
+  }
+}
+
+__device__ __forceinline__ void record_max(double v, double *sm, unsigned long long *slot) {
+  v = block_max(v, sm);
+  // non-negative doubles order like their bit patterns
+  if (threadIdx.x == 0 && slot) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+// GNEB / CI-GNEB update of interior image n = blockIdx.y + 1: reads the chain X
+// and the field of image n in slot n of Y, writes the new image into slot n of Y.
+template <typename R>
+__global__ void __launch_bounds__(kPT) k_gneb_update(const double *__restrict__ X, double *__restrict__ Y, long long N,
+                                                     const double *__restrict__ coef, double dt,
+                                                     unsigned long long *__restrict__ fmax_slot) {
+  __shared__ double sm[kPT];
+  const int n = blockIdx.y + 1;
+  const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
+  double fm = 0.0;
+  if (i < N) {
+    const double *S = X + 3 * N * (long long)n;
+    double *Yn = Y + 3 * N * (long long)n;
+    R s[3], sp[3], smn[3], b[3];
+    load3<R>(S, N, i, s);
+    load3<R>(S + 3 * N, N, i, sp);
+    load3<R>(S - 3 * N, N, i, smn);
+    load3<R>(Yn, N, i, b);
+    const double s64[3] = {S[i], S[N + i], S[2 * N + i]};
+    R tp[3] = {sp[0] - s[0], sp[1] - s[1], sp[2] - s[2]};
+    R tm[3] = {s[0] - smn[0], s[1] - smn[1], s[2] - smn[2]};
+    project<R>(s, tp);
+    project<R>(s, tm);
+    project<R>(s, b);
+    const R A = (R)coef[4 * n], C = (R)coef[4 * n + 1], h = (R)dt;
+    R u[3];
+    for (int k = 0; k < 3; ++k) {
+      const R F = b[k] + A * tp[k] + C * tm[k];
+      u[k] = F;
+    }
+    fm = (double)r_sqrt(dot3(u, u));
+    for (int k = 0; k < 3; ++k) u[k] *= h;
+    double out[3];
+    retract(s64, s, u, out);
+    Yn[i] = out[0];
+    Yn[N + i] = out[1];
+    Yn[2 * N + i] = out[2];
+  }
+  record_max(fm, sm, fmax_slot);
+}
+
+// string step, in place on interior image n = blockIdx.y + 1 of X (field in slot n of Y)
+template <typename R>
+__global__ void __launch_bounds__(kPT) k_string_step(double *__restrict__ X, const double *__restrict__ Y, long long N,
+                                                     double dt, unsigned long long *__restrict__ fmax_slot) {
+  __shared__ double sm[kPT];
+  const int n = blockIdx.y + 1;
+  const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
+  double fm = 0.0;
+  if (i < N) {
+    double *S = X + 3 * N * (long long)n;
+    R s[3], b[3];
+    load3<R>(S, N, i, s);
+    load3<R>(Y + 3 * N * (long long)n, N, i, b);
+    const double s64[3] = {S[i], S[N + i], S[2 * N + i]};
+    project<R>(s, b);
+    fm = (double)r_sqrt(dot3(b, b));
+    const R h = (R)dt;
+    R u[3] = {h * b[0], h * b[1], h * b[2]};
+    double out[3];
+    retract(s64, s, u, out);
+    S[i] = out[0];
+    S[N + i] = out[1];
+    S[2 * N + i] = out[2];
+  }
+  record_max(fm, sm, fmax_slot);
+}
+
+// slerp(a, c; w) on one site, FP64
+__device__ __forceinline__ void slerp_site(const double a[3], const double c[3], double w, double out[3]) {
+  const double c0 = a[1] * c[2] - a[2] * c[1], c1 = a[2] * c[0] - a[0] * c[2], c2 = a[0] * c[1] - a[1] * c[0];
+  const double th = atan2(sqrt(c0 * c0 + c1 * c1 + c2 * c2), a[0] * c[0] + a[1] * c[1] + a[2] * c[2]);
+  double x[3];
+  if (th < 1e-12) {
+    for (int k = 0; k < 3; ++k) x[k] = a[k];
+  } else {
+    const double st = sin(th), p = sin((1.0 - w) * th) / st, q = sin(w * th) / st;
+    for (int k = 0; k < 3; ++k) x[k] = p * a[k] + q * c[k];
+  }
+  const double r = 1.0 / sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  for (int k = 0; k < 3; ++k) out[k] = x[k] * r;
+}
+
+// FP32 arithmetic, FP64 state: out = N[a + d], d = (p + q - 1) a + q (c - a)
+__device__ __forceinline__ void slerp_site_f(const double a64[3], const float a[3], const float c[3], float w,
+                                             double out[3]) {
+  const float dl[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  const float th = site_angle<float>(a, dl);
+  float pq1, q;
+  if (th < 1e-6f) {
+    pq1 = 0.0f;
+    q = w;
+  } else {
+    const float st = sinf(th);
+    const float p = sinf((1.0f - w) * th) / st;
+    q = sinf(w * th) / st;
+    pq1 = (p - 1.0f) + q;
+  }
+  const float d[3] = {pq1 * a[0] + q * dl[0], pq1 * a[1] + q * dl[1], pq1 * a[2] + q * dl[2]};
+  renormalise64(a64, d, out);
+}
+
+// string redistribution: interior image n = blockIdx.y + 1 of Y from images j, j+1 of X
+template <typename R>
+__global__ void __launch_bounds__(kPT) k_string_redistribute(const double *__restrict__ X, double *__restrict__ Y,
+                                                             long long N, const double *__restrict__ coef) {
+  const int n = blockIdx.y + 1;
+  const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (i >= N) return;
+  const int j = (int)coef[4 * n + 2];
+  const double w = coef[4 * n + 3];
+  const double *A = X + 3 * N * (long long)j, *Cn = A + 3 * N;
+  const double a64[3] = {A[i], A[N + i], A[2 * N + i]};
+  double out[3];
+  if (sizeof(R) == 8) {
+    const double c64[3] = {Cn[i], Cn[N + i], Cn[2 * N + i]};
+    slerp_site(a64, c64, w, out);
+  } else {
+    float a[3], c[3];
+    load3<float>(A, N, i, a);
+    load3<float>(Cn, N, i, c);
+    slerp_site_f(a64, a, c, (float)w, out);
+  }
+  double *Yn = Y + 3 * N * (long long)n;
+  Yn[i] = out[0];
+  Yn[N + i] = out[1];
+  Yn[2 * N + i] = out[2];
+}
+
+// geodesic distance squared between two fields, per-block partials (FP64)
+__global__ void __launch_bounds__(kPT) k_geo_pair(const double *__restrict__ A, const double *__restrict__ B,
+                                                  long long N, double *__restrict__ partial) {
+  __shared__ double sm[kPT];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * kPT + threadIdx.x; i < N; i += (long long)gridDim.x * kPT) {
+    const double s[3] = {A[i], A[N + i], A[2 * N + i]};
+    const double d[3] = {B[i] - s[0], B[N + i] - s[1], B[2 * N + i] - s[2]};
+    const double th = site_angle<double>(s, d);
+    acc += th * th;
+  }
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kPT) k_geo_final(const double *__restrict__ partial, int nb,
+                                                   double *__restrict__ out) {
+  __shared__ double sm[kPT];
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < nb; j += kPT) acc += partial[j];
+  acc = block_sum(acc, sm);
+  if (threadIdx.x == 0) out[0] = sqrt(acc);
+}
+
+int reduce_grid(long long N) {
+  const long long per = (long long)kPT * 4;
+  return (int)std::max(1LL, std::min(2048LL, (N + per - 1) / per));
+}
+
+struct PathLayout {
+  double *W, *partial, *sums, *coef, *E, *L, *eend;
+  unsigned long long *fmax;
+  size_t bytes;
+};
+
+PathLayout layout(double *base, long long N, int nimg, int nb) {
+  PathLayout l;
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    double *p = base ? base + off : nullptr;
+    off += (n + 31) & ~(size_t)31;  // 256-byte aligned slices
+    return p;
+  };
+  l.W = take(3 * (size_t)N * nimg);
+  l.partial = take((size_t)(nimg - 1) * nb * kNS);
+  l.sums = take((size_t)nimg * kNS);
+  l.coef = take(4 * (size_t)nimg);
+  l.E = take((size_t)nimg);
+  l.L = take((size_t)nimg);
+  l.eend = take(10);
+  l.fmax = (unsigned long long *)take(1);
+  l.bytes = off * sizeof(double);
+  return l;
+}
+
+template <typename R>
+cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int *iters_out, double *E_host,
+                     double *fmax_host, cudaStream_t st, FieldFn field) {
+  const long long N = c->geo.nsite, stride = 3 * N;
+  const int nb = reduce_grid(N);
+  const unsigned nbu = (unsigned)((N + kPT - 1) / kPT);
+  PathLayout l = layout(nullptr, N, M, nb);
+  cudaError_t e;
+  if (c->path_bytes < l.bytes) {
+    cudaFree(c->d_path);
+    c->d_path = nullptr;
+    c->path_bytes = 0;
+    if ((e = cudaMalloc(&c->d_path, l.bytes)) != cudaSuccess) return e;
+    c->path_bytes = l.bytes;
+  }
+  l = layout(c->d_path, N, M, nb);
+  const size_t ibytes = (size_t)stride * sizeof(double);
+  // endpoints into the library chain, endpoint energies (fixed for the whole call)
+  if ((e = cudaMemcpyAsync(l.W, img, ibytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(l.W + stride * (M - 1), img + stride * (M - 1), ibytes, cudaMemcpyDeviceToDevice,
+                           st)) != cudaSuccess)
+    return e;
+  for (int k = 0; k < 2; ++k) {
+    const double *Sk = img + stride * (k ? M - 1 : 0);
+    if ((e = field(c, Sk, c->d_field, false, st)) != cudaSuccess) return e;
+    if ((e = reduce_energy(c, Sk, c->d_field, c->d_partial, c->nblock_red, l.eend + 5 * k, st)) != cudaSuccess)
+      return e;
+  }
+  const bool string = p->method == SX_PATH_STRING;
+  double *X = img, *Y = l.W;
+  const dim3 gred((unsigned)nb, (unsigned)(M - 1)), gupd(nbu, (unsigned)(M - 2));
+  int it = 0;
+  double fmax = -1.0;
+  while (it < p->max_iter) {
+    const bool measure = (it + 1) % p->check_every == 0 || it + 1 == p->max_iter;
+    unsigned long long *slot = measure ? l.fmax : nullptr;
+    if (measure && (e = cudaMemsetAsync(l.fmax, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    for (int n = 1; n < M - 1; ++n)
+      if ((e = field(c, X + stride * n, Y + stride * n, true, st)) != cudaSuccess) return e;
+    if (string) {
+      k_string_step<R><<<gupd, kPT, 0, st>>>(X, Y, N, p->dt, slot);
+      k_path_reduce<R, false><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, c->onsite, l.partial);
+      k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 0, l.sums);
+      k_path_coef<<<1, 32, 0, st>>>(l.sums, l.eend, M, p->method, p->k_spring, l.coef, l.E, l.L);
+      k_string_redistribute<R><<<gupd, kPT, 0, st>>>(X, Y, N, l.coef);
+    } else {
+      k_path_reduce<R, true><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, c->onsite, l.partial);
+      k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 1, l.sums);
+      k_path_coef<<<1, 32, 0, st>>>(l.sums, l.eend, M, p->method, p->k_spring, l.coef, l.E, l.L);
+      k_gneb_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, l.coef, p->dt, slot);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::swap(X, Y);
+    ++it;
+    if (measure) {
+      unsigned long long bits = 0;
+      if ((e = cudaMemcpyAsync(&bits, l.fmax, sizeof(bits), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+      memcpy(&fmax, &bits, sizeof(fmax));
+      if (fmax < p->tol) break;
+    }
+  }
+  // energies of the final chain (the tangent sums computed alongside are unused)
+  for (int n = 1; n < M - 1; ++n)
+    if ((e = field(c, X + stride * n, Y + stride * n, true, st)) != cudaSuccess) return e;
+  k_path_reduce<R, true><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, c->onsite, l.partial);
+  k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 1, l.sums);
+  k_path_coef<<<1, 32, 0, st>>>(l.sums, l.eend, M, SX_PATH_GNEB, 0.0, l.coef, l.E, l.L);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (X != img &&
+      (e = cudaMemcpyAsync(img + stride, X + stride, ibytes * (M - 2), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  if (E_host && (e = cudaMemcpyAsync(E_host, l.E, sizeof(double) * M, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  if (iters_out) *iters_out = it;
+  if (fmax_host) *fmax_host = fmax;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int path_max_images() { return kMaxImg; }
+
+cudaError_t path_run(sx_ctx *c, double *img, int nimg, const sx_path_params *p, int *iters_out, double *E_host,
+                     double *fmax_host, cudaStream_t st, FieldFn field) {
+  if (c->prec == SX_PREC_FP64) return run_path<double>(c, img, nimg, p, iters_out, E_host, fmax_host, st, field);
+  return run_path<float>(c, img, nimg, p, iters_out, E_host, fmax_host, st, field);
+}
+
+cudaError_t geodesic(const sx_ctx *c, const double *A, const double *B, double *out_host, cudaStream_t st) {
+  const long long N = c->geo.nsite;
+  const int nb = (int)std::min<long long>(c->nblock_red, reduce_grid(N));
+  double *out = c->d_partial + 3 * c->nblock_red;
+  k_geo_pair<<<nb, kPT, 0, st>>>(A, B, N, c->d_partial);
+  k_geo_final<<<1, kPT, 0, st>>>(c->d_partial, nb, out);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, out, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+}  // namespace sx
