@@ -253,6 +253,16 @@ cudaError_t backend_field(const sx_ctx *c, const double *S, double *b, bool onsi
   return gather_field(c, S, b, onsite, st);
 }
 
+cudaError_t backend_field_batch(const sx_ctx *c, const double *S, double *b, int count, long long stride,
+                                bool onsite, cudaStream_t st) {
+  if (c->backend == SX_BACKEND_STENCIL) return stencil_field_batch(c, S, b, count, stride, onsite, st);
+  for (int k = 0; k < count; ++k) {
+    cudaError_t e = backend_field(c, S + stride * k, b + stride * k, onsite, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t backend_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                          cudaStream_t st) {
   if (c->backend == SX_BACKEND_STENCIL) return stencil_heun_step(c, src, dst, h, step, st);
@@ -598,7 +608,8 @@ int sx_path_step(sx_ctx *c, double *images, int nimg, const sx_path_params *p, i
   if (!(p->dt > 0.0) || !isfinite(p->dt) || !(p->k_spring >= 0.0) || !isfinite(p->k_spring) || !(p->tol >= 0.0) ||
       p->max_iter < 0 || p->check_every < 1)
     return set_error(SX_ERR_ARG, "bad path parameters");
-  cudaError_t e = path_run(c, images, nimg, p, iters_out, E_host, fmax_host, (cudaStream_t)stream, backend_field);
+  cudaError_t e =
+      path_run(c, images, nimg, p, iters_out, E_host, fmax_host, (cudaStream_t)stream, backend_field_batch);
   return e == cudaSuccess ? SX_OK : cuda_error(e, "path step");
 }
 

@@ -134,6 +134,9 @@ cudaError_t thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int
 int stencil_plan(sx_ctx *c);
 void stencil_free(sx_ctx *c);
 cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
+// fields of `count` spin fields stride doubles apart (S, S + stride, ...) into b, b + stride, ... in one launch
+cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int count, long long stride,
+                                bool onsite, cudaStream_t st);
 cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                               cudaStream_t st);
 
@@ -145,11 +148,13 @@ cudaError_t fft_heun_step(const sx_ctx *c, const double *src, double *dst, const
                           cudaStream_t st);
 
 typedef cudaError_t (*FieldFn)(const sx_ctx *, const double *, double *, bool, cudaStream_t);
+// fields of count spin fields stride doubles apart, written stride doubles apart
+typedef cudaError_t (*FieldBatchFn)(const sx_ctx *, const double *, double *, int, long long, bool, cudaStream_t);
 
 // minimum-energy paths (sx_path.cu)
 int path_max_images();
 cudaError_t path_run(sx_ctx *c, double *img, int nimg, const sx_path_params *p, int *iters_out, double *E_host,
-                     double *fmax_host, cudaStream_t st, FieldFn field);
+                     double *fmax_host, cudaStream_t st, FieldBatchFn field);
 cudaError_t geodesic(const sx_ctx *c, const double *A, const double *B, double *out_host, cudaStream_t st);
 
 // minimisation (sx_min.cu)

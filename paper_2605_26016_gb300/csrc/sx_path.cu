@@ -15,9 +15,10 @@
 // followed by S <- R_exp(S, dt F).  Because tau is linear in t+ and t-, one
 // pass over the chain reduces the five inner products t+.t+, t+.t-, t-.t-,
 // f.t+, f.t- per image (together with the image energy and the geodesic
-// distance to the next image); a one-thread kernel then turns them into two
+// distance to the next image); a one-block kernel then turns them into two
 // coefficients per image, F = f + A t+ + C t-, and a second pass moves the
-// images.  No host synchronisation inside an iteration.
+// images.  The fields of all interior images come from one batched launch
+// where the backend has one.  No host synchronisation inside an iteration.
 //
 // String method: every interior image steps S <- R_exp(S, dt f); then the
 // images are placed at equal geodesic arc length by per-site spherical
@@ -63,18 +64,6 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
   return r;
 }
 
-__device__ __forceinline__ double block_max(double v, double *sm) {
-  sm[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = kPT / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
-    __syncthreads();
-  }
-  const double r = sm[0];
-  __syncthreads();
-  return r;
-}
-
 template <typename R>
 __device__ __forceinline__ R to_r(double v);
 template <>
@@ -84,6 +73,16 @@ __device__ __forceinline__ double to_r<double>(double v) {
 template <>
 __device__ __forceinline__ float to_r<float>(double v) {
   return f64_to_f32(v);
+}
+
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return f32_to_f64(v); }
+
+// sublattice of site i (sites are sublattice-major, ncell sites each; nsub <= 8)
+__device__ __forceinline__ int sublattice(long long i, long long ncell, int nsub) {
+  int a = 0;
+  while (a + 1 < nsub && i >= (a + 1) * ncell) ++a;
+  return a;
 }
 
 template <typename R>
@@ -111,8 +110,6 @@ __device__ __forceinline__ double r_atan2(double y, double x) { return atan2(y, 
 __device__ __forceinline__ float r_atan2(float y, float x) { return atan2f(y, x); }
 __device__ __forceinline__ double r_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float r_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double r_sin(double x) { return sin(x); }
-__device__ __forceinline__ float r_sin(float x) { return sinf(x); }
 
 // angle between unit vectors s and t = s + dl: |s x t| = |s x dl|, s.t = 1 - |dl|^2/2
 template <typename R>
@@ -151,113 +148,171 @@ __device__ __forceinline__ void retract(const double s64[3], const float sr[3], 
   renormalise64(s64, d, out);
 }
 
-// Per (image, block) partial sums.  blockIdx.y = n in 0 .. nimg-2: the
-// geodesic angle to image n+1, and for n >= 1 (FULL) the energy and the five
-// tangent inner products of interior image n.  B holds the field of image n
-// in slot n.
-template <typename R, bool FULL>
-__global__ void __launch_bounds__(kPT) k_path_reduce(const double *__restrict__ X, const double *__restrict__ B,
-                                                     long long N, long long ncell, OnSite os,
-                                                     double *__restrict__ partial) {
-  __shared__ double sm[kPT];
-  const int n = blockIdx.y;
-  const double *S = X + 3 * N * (long long)n;
-  const double *Sp = S + 3 * N;
-  R acc[7] = {0, 0, 0, 0, 0, 0, 0};
-  double e = 0.0;
-  const bool interior = FULL && n >= 1;
-  for (long long i = (long long)blockIdx.x * kPT + threadIdx.x; i < N; i += (long long)gridDim.x * kPT) {
-    R s[3], sp[3];
-    load3<R>(S, N, i, s);
-    load3<R>(Sp, N, i, sp);
-    R tp[3] = {sp[0] - s[0], sp[1] - s[1], sp[2] - s[2]};
-    const R th = site_angle<R>(s, tp);
-    acc[P_D2] += th * th;
-    if (interior) {
-      const double *Sm = S - 3 * N, *b = B + 3 * N * (long long)n;
-      R sm_[3], br[3];
-      load3<R>(Sm, N, i, sm_);
-      const double b0 = b[i], b1 = b[N + i], b2 = b[2 * N + i];
-      const double s0 = S[i], s1 = S[N + i], s2 = S[2 * N + i];
-      const int a = (int)(i / ncell);
-      e += -0.5 * (s0 * (b0 + os.zee[a][0]) + s1 * (b1 + os.zee[a][1]) + s2 * (b2 + os.zee[a][2]));
-      br[0] = to_r<R>(b0);
-      br[1] = to_r<R>(b1);
-      br[2] = to_r<R>(b2);
-      R tm[3] = {s[0] - sm_[0], s[1] - sm_[1], s[2] - sm_[2]};
-      project<R>(s, tp);
-      project<R>(s, tm);
-      project<R>(s, br);
-      acc[P_PP] += dot3(tp, tp);
-      acc[P_PM] += dot3(tp, tm);
-      acc[P_MM] += dot3(tm, tm);
-      acc[P_FP] += dot3(br, tp);
-      acc[P_FM] += dot3(br, tm);
-    }
+// Zeeman term mu mu_B B per sublattice in the arithmetic type of the path kernels
+template <typename R>
+struct ZeeR {
+  R z[SX_MAX_SUB][3];
+};
+
+// Sum NV per-thread values of type R over the block: a shuffle tree in R inside
+// each warp, then the warp sums widened and added in FP64 by thread 0, which
+// writes out[slot[k]].  All threads must call it.
+template <typename R, int NV>
+__device__ __forceinline__ void block_reduce_store(R (&v)[NV], const int (&slot)[NV], double *__restrict__ out) {
+  __shared__ R red[NV][kPT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    R x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[k][warp] = x;
   }
-  double *out = partial + ((long long)n * gridDim.x + blockIdx.x) * kNS;
-  const double d2 = block_sum((double)acc[P_D2], sm);
-  if (threadIdx.x == 0) out[P_D2] = d2;
-  if (interior) {
-    const double v0 = block_sum(e, sm);
-    double v[5];
-    for (int k = 0; k < 5; ++k) v[k] = block_sum((double)acc[P_PP + k], sm);
-    if (threadIdx.x == 0) {
-      out[P_E] = v0;
-      for (int k = 0; k < 5; ++k) out[P_PP + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double acc = 0.0;
+      for (int w = 0; w < kPT / 32; ++w) acc += to_d(red[k][w]);
+      out[slot[k]] = acc;
     }
   }
 }
 
-// sums[n][k] = sum over blocks, one block per image slot n (fixed order: deterministic)
-__global__ void __launch_bounds__(kPT) k_path_sum(const double *__restrict__ partial, int nb, int full,
+enum { MODE_GEO = 0, MODE_FULL = 1, MODE_ENERGY = 2 };
+
+// Per (image slot, block) partial sums; image n = n0 + blockIdx.y * nstep.
+//  MODE_GEO:    theta^2 to image n+1 (n in 0 .. nimg-2);
+//  MODE_FULL:   as MODE_GEO, and for n >= 1 the energy sum S.(b + zee) and the
+//               five tangent inner products of image n;
+//  MODE_ENERGY: the energy sum of image n only.
+// B holds the field of image n in slot n.  Slot layout: partial[(y nb + block) kNS + k].
+template <typename R, int MODE>
+__global__ void __launch_bounds__(kPT) k_path_reduce(const double *__restrict__ X, const double *__restrict__ B,
+                                                     long long N, long long ncell, int nsub, ZeeR<R> zee, int n0,
+                                                     int nstep, double *__restrict__ partial) {
+  const int n = n0 + blockIdx.y * nstep;
+  const double *S = X + 3 * N * (long long)n;
+  const double *Sp = S + 3 * N;
+  R acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  const bool geo = MODE != MODE_ENERGY;
+  const bool tangent = MODE == MODE_FULL && n >= 1;
+  const bool energy = MODE == MODE_ENERGY || tangent;
+  for (long long i = (long long)blockIdx.x * kPT + threadIdx.x; i < N; i += (long long)gridDim.x * kPT) {
+    R s[3];
+    load3<R>(S, N, i, s);
+    R tp[3];
+    if (geo) {
+      R sp[3];
+      load3<R>(Sp, N, i, sp);
+      tp[0] = sp[0] - s[0];
+      tp[1] = sp[1] - s[1];
+      tp[2] = sp[2] - s[2];
+      const R th = site_angle<R>(s, tp);
+      acc[P_D2] += th * th;
+    }
+    if (energy) {
+      R br[3];
+      load3<R>(B + 3 * N * (long long)n, N, i, br);
+      const int a = sublattice(i, ncell, nsub);
+      acc[P_E] += s[0] * (br[0] + zee.z[a][0]) + s[1] * (br[1] + zee.z[a][1]) + s[2] * (br[2] + zee.z[a][2]);
+      if (tangent) {
+        R sm_[3];
+        load3<R>(S - 3 * N, N, i, sm_);
+        R tm[3] = {s[0] - sm_[0], s[1] - sm_[1], s[2] - sm_[2]};
+        project<R>(s, tp);
+        project<R>(s, tm);
+        project<R>(s, br);
+        acc[P_PP] += dot3(tp, tp);
+        acc[P_PM] += dot3(tp, tm);
+        acc[P_MM] += dot3(tm, tm);
+        acc[P_FP] += dot3(br, tp);
+        acc[P_FM] += dot3(br, tm);
+      }
+    }
+  }
+  double *out = partial + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * kNS;
+  if (MODE == MODE_GEO) {
+    R v[1] = {acc[P_D2]};
+    const int sl[1] = {P_D2};
+    block_reduce_store<R, 1>(v, sl, out);
+  } else if (MODE == MODE_ENERGY) {
+    R v[1] = {acc[P_E]};
+    const int sl[1] = {P_E};
+    block_reduce_store<R, 1>(v, sl, out);
+  } else {
+    const int sl[7] = {0, 1, 2, 3, 4, 5, 6};
+    block_reduce_store<R, 7>(acc, sl, out);  // slot 0 etc. hold zeros for n = 0
+  }
+}
+
+// sums[y][k] = sum over the blocks of image slot y (fixed order: deterministic);
+// the energy slot is scaled by -1/2 (E = -1/2 sum S.(b + zee)).  nv: the
+// number of leading slots to reduce (7, or 1 for energies only); with
+// geo_only only the geodesic slot is reduced and the others are set to 0.
+__global__ void __launch_bounds__(kPT) k_path_sum(const double *__restrict__ partial, int nb, int geo_only,
                                                   double *__restrict__ sums) {
   __shared__ double sm[kPT];
-  const int n = blockIdx.x;
-  const double *p = partial + (long long)n * nb * kNS;
+  const int y = blockIdx.x;
+  const double *p = partial + (long long)y * nb * kNS;
   for (int k = 0; k < 7; ++k) {
-    if (k != P_D2 && !(full && n >= 1)) {
-      if (threadIdx.x == 0) sums[n * kNS + k] = 0.0;
+    if (geo_only && k != P_D2) {
+      if (threadIdx.x == 0) sums[y * kNS + k] = 0.0;
       continue;
     }
     double acc = 0.0;
     for (int j = threadIdx.x; j < nb; j += kPT) acc += p[(long long)j * kNS + k];
     acc = block_sum(acc, sm);
-    if (threadIdx.x == 0) sums[n * kNS + k] = acc;
+    if (threadIdx.x == 0) sums[y * kNS + k] = k == P_E ? -0.5 * acc : acc;
   }
 }
 
-// Per-image coefficients (one thread; nimg <= kMaxImg).
+// Per-image coefficients (one block; nimg <= kMaxImg).
 //  GNEB / CI: coef[n] = {A, C, 0, 0} with F = f + A t+ + C t-.
 //  string:    coef[n] = {0, 0, j, w}: image n becomes slerp(old_j, old_j+1; w).
-// E[n] receives the image energies (endpoints from eend[0] and eend[5]).
-__global__ void k_path_coef(const double *__restrict__ sums, const double *__restrict__ eend, int nimg, int method,
-                            double kspring, double *__restrict__ coef, double *__restrict__ E,
-                            double *__restrict__ L) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// coeff holds the same numbers in FP32.  E[n] receives the image energies
+// (endpoints from the energy slots of eend[0 .. kNS) and eend[kNS .. 2 kNS)).
+__global__ void __launch_bounds__(kPT) k_path_coef(const double *__restrict__ sums, const double *__restrict__ eend,
+                                                   int nimg, int method, double kspring, double *__restrict__ coef,
+                                                   float *__restrict__ coeff, double *__restrict__ E,
+                                                   double *__restrict__ L) {
+  __shared__ int top_s;
   const int M = nimg;
-  E[0] = eend[0];
-  E[M - 1] = eend[5];
-  for (int n = 1; n < M - 1; ++n) E[n] = sums[n * kNS + P_E];
+  for (int n = threadIdx.x; n < M; n += blockDim.x)
+    E[n] = n == 0 ? eend[P_E] : n == M - 1 ? eend[kNS + P_E] : sums[n * kNS + P_E];
+  __syncthreads();
   if (method == SX_PATH_STRING) {
-    L[0] = 0.0;
-    for (int n = 0; n < M - 1; ++n) L[n + 1] = L[n] + sqrt(sums[n * kNS + P_D2]);
-    for (int n = 1; n < M - 1; ++n) {
+    if (threadIdx.x == 0) {
+      L[0] = 0.0;
+      for (int n = 0; n < M - 1; ++n) L[n + 1] = L[n] + sqrt(sums[n * kNS + P_D2]);
+    }
+    __syncthreads();
+    for (int n = 1 + threadIdx.x; n < M - 1; n += blockDim.x) {
       const double target = L[M - 1] * n / (M - 1);
       int j = 0;
       while (j < M - 2 && L[j + 1] < target) ++j;
       const double seg = L[j + 1] - L[j];
+      const double w = seg > 0.0 ? (target - L[j]) / seg : 0.0;
       coef[4 * n + 0] = 0.0;
       coef[4 * n + 1] = 0.0;
       coef[4 * n + 2] = (double)j;
-      coef[4 * n + 3] = seg > 0.0 ? (target - L[j]) / seg : 0.0;
+      coef[4 * n + 3] = w;
+      coeff[4 * n + 0] = 0.0f;
+      coeff[4 * n + 1] = 0.0f;
+      coeff[4 * n + 2] = (float)j;
+      coeff[4 * n + 3] = (float)w;
     }
     return;
   }
-  int top = 1;
-  for (int n = 2; n < M - 1; ++n)
-    if (E[n] > E[top]) top = n;
-  for (int n = 1; n < M - 1; ++n) {
+  if (threadIdx.x == 0) {
+    int top = 1;
+    for (int n = 2; n < M - 1; ++n)
+      if (E[n] > E[top]) top = n;
+    top_s = top;
+  }
+  __syncthreads();
+  const int top = top_s;
+  for (int n = 1 + threadIdx.x; n < M - 1; n += blockDim.x) {
     const double *s = sums + n * kNS;
     const double dEp = E[n + 1] - E[n], dEm = E[n - 1] - E[n];
     double a, c;
@@ -288,25 +343,36 @@ __global__ void k_path_coef(const double *__restrict__ sums, const double *__res
     coef[4 * n + 1] = cc * c;
     coef[4 * n + 2] = 0.0;
     coef[4 * n + 3] = 0.0;
+    coeff[4 * n + 0] = (float)(cc * a);
+    coeff[4 * n + 1] = (float)(cc * c);
+    coeff[4 * n + 2] = 0.0f;
+    coeff[4 * n + 3] = 0.0f;
   }
 }
 
-__device__ __forceinline__ void record_max(double v, double *sm, unsigned long long *slot) {
-  v = block_max(v, sm);
-  // non-negative doubles order like their bit patterns
-  if (threadIdx.x == 0 && slot) atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+template <typename R>
+__device__ __forceinline__ void record_max(R v, unsigned long long *slot) {
+  __shared__ R red[kPT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0 && slot) {
+    for (int w = 1; w < kPT / 32; ++w) v = max(v, red[w]);
+    // non-negative doubles order like their bit patterns
+    atomicMax(slot, (unsigned long long)__double_as_longlong(to_d(v)));
+  }
 }
 
 // GNEB / CI-GNEB update of interior image n = blockIdx.y + 1: reads the chain X
 // and the field of image n in slot n of Y, writes the new image into slot n of Y.
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_gneb_update(const double *__restrict__ X, double *__restrict__ Y, long long N,
-                                                     const double *__restrict__ coef, double dt,
+                                                     const R *__restrict__ coef, R dt,
                                                      unsigned long long *__restrict__ fmax_slot) {
-  __shared__ double sm[kPT];
   const int n = blockIdx.y + 1;
   const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
-  double fm = 0.0;
+  R fm = 0;
   if (i < N) {
     const double *S = X + 3 * N * (long long)n;
     double *Yn = Y + 3 * N * (long long)n;
@@ -321,31 +387,27 @@ __global__ void __launch_bounds__(kPT) k_gneb_update(const double *__restrict__ 
     project<R>(s, tp);
     project<R>(s, tm);
     project<R>(s, b);
-    const R A = (R)coef[4 * n], C = (R)coef[4 * n + 1], h = (R)dt;
+    const R A = coef[4 * n], C = coef[4 * n + 1];
     R u[3];
-    for (int k = 0; k < 3; ++k) {
-      const R F = b[k] + A * tp[k] + C * tm[k];
-      u[k] = F;
-    }
-    fm = (double)r_sqrt(dot3(u, u));
-    for (int k = 0; k < 3; ++k) u[k] *= h;
+    for (int k = 0; k < 3; ++k) u[k] = b[k] + A * tp[k] + C * tm[k];
+    fm = r_sqrt(dot3(u, u));
+    for (int k = 0; k < 3; ++k) u[k] *= dt;
     double out[3];
     retract(s64, s, u, out);
     Yn[i] = out[0];
     Yn[N + i] = out[1];
     Yn[2 * N + i] = out[2];
   }
-  record_max(fm, sm, fmax_slot);
+  record_max<R>(fm, fmax_slot);
 }
 
 // string step, in place on interior image n = blockIdx.y + 1 of X (field in slot n of Y)
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_string_step(double *__restrict__ X, const double *__restrict__ Y, long long N,
-                                                     double dt, unsigned long long *__restrict__ fmax_slot) {
-  __shared__ double sm[kPT];
+                                                     R dt, unsigned long long *__restrict__ fmax_slot) {
   const int n = blockIdx.y + 1;
   const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
-  double fm = 0.0;
+  R fm = 0;
   if (i < N) {
     double *S = X + 3 * N * (long long)n;
     R s[3], b[3];
@@ -353,16 +415,15 @@ __global__ void __launch_bounds__(kPT) k_string_step(double *__restrict__ X, con
     load3<R>(Y + 3 * N * (long long)n, N, i, b);
     const double s64[3] = {S[i], S[N + i], S[2 * N + i]};
     project<R>(s, b);
-    fm = (double)r_sqrt(dot3(b, b));
-    const R h = (R)dt;
-    R u[3] = {h * b[0], h * b[1], h * b[2]};
+    fm = r_sqrt(dot3(b, b));
+    R u[3] = {dt * b[0], dt * b[1], dt * b[2]};
     double out[3];
     retract(s64, s, u, out);
     S[i] = out[0];
     S[N + i] = out[1];
     S[2 * N + i] = out[2];
   }
-  record_max(fm, sm, fmax_slot);
+  record_max<R>(fm, fmax_slot);
 }
 
 // slerp(a, c; w) on one site, FP64
@@ -402,23 +463,23 @@ __device__ __forceinline__ void slerp_site_f(const double a64[3], const float a[
 // string redistribution: interior image n = blockIdx.y + 1 of Y from images j, j+1 of X
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_string_redistribute(const double *__restrict__ X, double *__restrict__ Y,
-                                                             long long N, const double *__restrict__ coef) {
+                                                             long long N, const R *__restrict__ coef) {
   const int n = blockIdx.y + 1;
   const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
   if (i >= N) return;
   const int j = (int)coef[4 * n + 2];
-  const double w = coef[4 * n + 3];
+  const R w = coef[4 * n + 3];
   const double *A = X + 3 * N * (long long)j, *Cn = A + 3 * N;
   const double a64[3] = {A[i], A[N + i], A[2 * N + i]};
   double out[3];
-  if (sizeof(R) == 8) {
+  if constexpr (sizeof(R) == 8) {
     const double c64[3] = {Cn[i], Cn[N + i], Cn[2 * N + i]};
     slerp_site(a64, c64, w, out);
   } else {
     float a[3], c[3];
     load3<float>(A, N, i, a);
     load3<float>(Cn, N, i, c);
-    slerp_site_f(a64, a, c, (float)w, out);
+    slerp_site_f(a64, a, c, w, out);
   }
   double *Yn = Y + 3 * N * (long long)n;
   Yn[i] = out[0];
@@ -457,6 +518,7 @@ int reduce_grid(long long N) {
 
 struct PathLayout {
   double *W, *partial, *sums, *coef, *E, *L, *eend;
+  float *coeff;
   unsigned long long *fmax;
   size_t bytes;
 };
@@ -473,9 +535,10 @@ PathLayout layout(double *base, long long N, int nimg, int nb) {
   l.partial = take((size_t)(nimg - 1) * nb * kNS);
   l.sums = take((size_t)nimg * kNS);
   l.coef = take(4 * (size_t)nimg);
+  l.coeff = (float *)take(2 * (size_t)nimg);
   l.E = take((size_t)nimg);
   l.L = take((size_t)nimg);
-  l.eend = take(10);
+  l.eend = take(2 * kNS);
   l.fmax = (unsigned long long *)take(1);
   l.bytes = off * sizeof(double);
   return l;
@@ -483,7 +546,7 @@ PathLayout layout(double *base, long long N, int nimg, int nb) {
 
 template <typename R>
 cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int *iters_out, double *E_host,
-                     double *fmax_host, cudaStream_t st, FieldFn field) {
+                     double *fmax_host, cudaStream_t st, FieldBatchFn field) {
   const long long N = c->geo.nsite, stride = 3 * N;
   const int nb = reduce_grid(N);
   const unsigned nbu = (unsigned)((N + kPT - 1) / kPT);
@@ -498,18 +561,25 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
   }
   l = layout(c->d_path, N, M, nb);
   const size_t ibytes = (size_t)stride * sizeof(double);
-  // endpoints into the library chain, endpoint energies (fixed for the whole call)
+  ZeeR<R> zr;
+  for (int a = 0; a < SX_MAX_SUB; ++a)
+    for (int k = 0; k < 3; ++k) zr.z[a][k] = (R)c->onsite.zee[a][k];
+  const int nsub = c->lat.nsub;
+  // endpoint energies (fixed for the whole call), with the same arithmetic as
+  // the interior images: fields of images 0 and M-1 into slots 0 and M-1 of W
+  if ((e = field(c, img, l.W, 2, stride * (M - 1), true, st)) != cudaSuccess) return e;
+  k_path_reduce<R, MODE_ENERGY><<<dim3((unsigned)nb, 2), kPT, 0, st>>>(img, l.W, N, c->geo.ncell, nsub, zr, 0, M - 1,
+                                                                        l.partial);
+  k_path_sum<<<2, kPT, 0, st>>>(l.partial, nb, 0, l.eend);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // then the endpoint spins into the library chain
   if ((e = cudaMemcpyAsync(l.W, img, ibytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(l.W + stride * (M - 1), img + stride * (M - 1), ibytes, cudaMemcpyDeviceToDevice,
                            st)) != cudaSuccess)
     return e;
-  for (int k = 0; k < 2; ++k) {
-    const double *Sk = img + stride * (k ? M - 1 : 0);
-    if ((e = field(c, Sk, c->d_field, false, st)) != cudaSuccess) return e;
-    if ((e = reduce_energy(c, Sk, c->d_field, c->d_partial, c->nblock_red, l.eend + 5 * k, st)) != cudaSuccess)
-      return e;
-  }
   const bool string = p->method == SX_PATH_STRING;
+  const R dt = (R)p->dt;
+  const R *coefR = sizeof(R) == 8 ? (const R *)l.coef : (const R *)l.coeff;
   double *X = img, *Y = l.W;
   const dim3 gred((unsigned)nb, (unsigned)(M - 1)), gupd(nbu, (unsigned)(M - 2));
   int it = 0;
@@ -518,19 +588,18 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
     const bool measure = (it + 1) % p->check_every == 0 || it + 1 == p->max_iter;
     unsigned long long *slot = measure ? l.fmax : nullptr;
     if (measure && (e = cudaMemsetAsync(l.fmax, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    for (int n = 1; n < M - 1; ++n)
-      if ((e = field(c, X + stride * n, Y + stride * n, true, st)) != cudaSuccess) return e;
+    if ((e = field(c, X + stride, Y + stride, M - 2, stride, true, st)) != cudaSuccess) return e;
     if (string) {
-      k_string_step<R><<<gupd, kPT, 0, st>>>(X, Y, N, p->dt, slot);
-      k_path_reduce<R, false><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, c->onsite, l.partial);
-      k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 0, l.sums);
-      k_path_coef<<<1, 32, 0, st>>>(l.sums, l.eend, M, p->method, p->k_spring, l.coef, l.E, l.L);
-      k_string_redistribute<R><<<gupd, kPT, 0, st>>>(X, Y, N, l.coef);
-    } else {
-      k_path_reduce<R, true><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, c->onsite, l.partial);
+      k_string_step<R><<<gupd, kPT, 0, st>>>(X, Y, N, dt, slot);
+      k_path_reduce<R, MODE_GEO><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, nsub, zr, 0, 1, l.partial);
       k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 1, l.sums);
-      k_path_coef<<<1, 32, 0, st>>>(l.sums, l.eend, M, p->method, p->k_spring, l.coef, l.E, l.L);
-      k_gneb_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, l.coef, p->dt, slot);
+      k_path_coef<<<1, kPT, 0, st>>>(l.sums, l.eend, M, p->method, p->k_spring, l.coef, l.coeff, l.E, l.L);
+      k_string_redistribute<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR);
+    } else {
+      k_path_reduce<R, MODE_FULL><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, nsub, zr, 0, 1, l.partial);
+      k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 0, l.sums);
+      k_path_coef<<<1, kPT, 0, st>>>(l.sums, l.eend, M, p->method, p->k_spring, l.coef, l.coeff, l.E, l.L);
+      k_gneb_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, slot);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(X, Y);
@@ -544,11 +613,10 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
     }
   }
   // energies of the final chain (the tangent sums computed alongside are unused)
-  for (int n = 1; n < M - 1; ++n)
-    if ((e = field(c, X + stride * n, Y + stride * n, true, st)) != cudaSuccess) return e;
-  k_path_reduce<R, true><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, c->onsite, l.partial);
-  k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 1, l.sums);
-  k_path_coef<<<1, 32, 0, st>>>(l.sums, l.eend, M, SX_PATH_GNEB, 0.0, l.coef, l.E, l.L);
+  if ((e = field(c, X + stride, Y + stride, M - 2, stride, true, st)) != cudaSuccess) return e;
+  k_path_reduce<R, MODE_FULL><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, nsub, zr, 0, 1, l.partial);
+  k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 0, l.sums);
+  k_path_coef<<<1, kPT, 0, st>>>(l.sums, l.eend, M, SX_PATH_GNEB, 0.0, l.coef, l.coeff, l.E, l.L);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (X != img &&
       (e = cudaMemcpyAsync(img + stride, X + stride, ibytes * (M - 2), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
@@ -566,7 +634,7 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
 int path_max_images() { return kMaxImg; }
 
 cudaError_t path_run(sx_ctx *c, double *img, int nimg, const sx_path_params *p, int *iters_out, double *E_host,
-                     double *fmax_host, cudaStream_t st, FieldFn field) {
+                     double *fmax_host, cudaStream_t st, FieldBatchFn field) {
   if (c->prec == SX_PREC_FP64) return run_path<double>(c, img, nimg, p, iters_out, E_host, fmax_host, st, field);
   return run_path<float>(c, img, nimg, p, iters_out, E_host, fmax_host, st, field);
 }

@@ -146,7 +146,9 @@ struct StencilArgs {
 
 struct StencilPlan {
   int family;
-  int tz;
+  int tz;           // z chunk of the fused Heun step (and of single-image field launches)
+  int nsm;          // SMs of the device
+  int occ_field;    // resident CTAs per SM of the field kernel
   StencilArgs base;
 };
 
@@ -473,7 +475,8 @@ struct GF {
 // and anisotropy.  Output FP64 (widened from the FP32 accumulators).
 template <int FID>
 __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
-    k_field_stencil(const StencilArgs p, int onsite, const double *__restrict__ Sin, double *__restrict__ b) {
+    k_field_stencil(const StencilArgs p, int onsite, const double *__restrict__ Sin, double *__restrict__ b,
+                    int nzc, long long istride) {
   using F = Family<FID>;
   using g = GF<F>;
   constexpr int NS = F::NSUB, R = F::R;
@@ -482,7 +485,11 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
   float4 *cq = reinterpret_cast<float4 *>(smem_raw + g::OFF_CQ);        // [R+1][NS][NT] centre values
   double *stage = reinterpret_cast<double *>(smem_raw + g::OFF_STAGE);  // [3][SN]
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * F::BY, z0 = blockIdx.z * p.tz;
+  // blockIdx.z = image * nzc + z chunk (several spin fields istride doubles apart in one launch)
+  const int img = blockIdx.z / nzc, zc = blockIdx.z - img * nzc;
+  Sin += img * istride;
+  b += img * istride;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * F::BY, z0 = zc * p.tz;
   const int tzc = min(p.tz, p.nz - z0);
   const int cx = x0 + tx, cy = y0 + ty;
   const bool mine = cx < p.nx && cy < p.ny;
@@ -588,12 +595,38 @@ cudaError_t launch_heun(const StencilPlan &sp, const StencilArgs &a, const doubl
   return cudaGetLastError();
 }
 
+// z chunk of a field launch over `count` images: minimise waves * (chunk + 2R)
+// (the field kernel pays 2R warm-up planes per chunk), balanced chunks only.
 template <int FID>
-cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &a, int onsite, const double *S, double *b,
-                         cudaStream_t st) {
+int field_tz(const StencilPlan &sp, const StencilArgs &a, int count) {
+  const long long txy = (long long)((a.nx + 31) / 32) * ((a.ny + Family<FID>::BY - 1) / Family<FID>::BY) * count;
+  const long long slots = (long long)sp.nsm * sp.occ_field;
+  int best_tz = a.nz;
+  long long best = -1;
+  for (int tz = a.nz; tz >= 1; --tz) {
+    const int nchunk = (a.nz + tz - 1) / tz;
+    if (tz != a.nz && (a.nz + nchunk - 1) / nchunk != tz) continue;
+    if ((long long)nchunk * count > 65535) break;
+    const long long waves = (txy * nchunk + slots - 1) / slots;
+    const long long cost = waves * (tz + 2 * Family<FID>::R);
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_tz = tz;
+    }
+  }
+  return best_tz;
+}
+
+template <int FID>
+cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &base, int onsite, const double *S, double *b,
+                         int count, long long stride, cudaStream_t st) {
   using g = GF<Family<FID>>;
-  const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, (a.nz + sp.tz - 1) / sp.tz);
-  k_field_stencil<FID><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, onsite, S, b);
+  StencilArgs a = base;
+  a.tz = count == 1 ? sp.tz : field_tz<FID>(sp, a, count);
+  const int nzc = (a.nz + a.tz - 1) / a.tz;
+  if ((long long)nzc * count > 65535) return cudaErrorInvalidConfiguration;
+  const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, nzc * count);
+  k_field_stencil<FID><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, onsite, S, b, nzc, stride);
   return cudaGetLastError();
 }
 
@@ -625,6 +658,16 @@ int choose_tz(const sx_ctx *c) {
     }
   }
   return best_tz;
+}
+
+template <int FID>
+int field_occupancy() {
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_field_stencil<FID>, GF<Family<FID>>::NT,
+                                                    GF<Family<FID>>::SMEM) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  return occ;
 }
 
 }  // namespace
@@ -689,6 +732,15 @@ int stencil_plan(sx_ctx *c) {
     default: sp->tz = choose_tz<FAM_BCC4>(c); break;
   }
   a.tz = sp->tz;
+  sp->nsm = 152;
+  cudaDeviceGetAttribute(&sp->nsm, cudaDevAttrMultiProcessorCount, c->device);
+  switch (fam) {
+    case FAM_SC6_ISO: sp->occ_field = field_occupancy<FAM_SC6_ISO>(); break;
+    case FAM_SC6_TEN: sp->occ_field = field_occupancy<FAM_SC6_TEN>(); break;
+    case FAM_SC26_ISO: sp->occ_field = field_occupancy<FAM_SC26_ISO>(); break;
+    case FAM_SC26_TEN: sp->occ_field = field_occupancy<FAM_SC26_TEN>(); break;
+    default: sp->occ_field = field_occupancy<FAM_BCC4>(); break;
+  }
   c->stencil = sp;
   c->launches_per_step = 1;
   return SX_OK;
@@ -701,15 +753,20 @@ void stencil_free(sx_ctx *c) {
 
 int stencil_family(const sx_ctx *c) { return c->stencil ? c->stencil->family : -1; }
 
-cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st) {
+cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int count, long long stride,
+                                bool onsite, cudaStream_t st) {
   const StencilPlan &sp = *c->stencil;
   switch (sp.family) {
-    case FAM_SC6_ISO: return launch_field<FAM_SC6_ISO>(sp, sp.base, onsite, S, b, st);
-    case FAM_SC6_TEN: return launch_field<FAM_SC6_TEN>(sp, sp.base, onsite, S, b, st);
-    case FAM_SC26_ISO: return launch_field<FAM_SC26_ISO>(sp, sp.base, onsite, S, b, st);
-    case FAM_SC26_TEN: return launch_field<FAM_SC26_TEN>(sp, sp.base, onsite, S, b, st);
-    default: return launch_field<FAM_BCC4>(sp, sp.base, onsite, S, b, st);
+    case FAM_SC6_ISO: return launch_field<FAM_SC6_ISO>(sp, sp.base, onsite, S, b, count, stride, st);
+    case FAM_SC6_TEN: return launch_field<FAM_SC6_TEN>(sp, sp.base, onsite, S, b, count, stride, st);
+    case FAM_SC26_ISO: return launch_field<FAM_SC26_ISO>(sp, sp.base, onsite, S, b, count, stride, st);
+    case FAM_SC26_TEN: return launch_field<FAM_SC26_TEN>(sp, sp.base, onsite, S, b, count, stride, st);
+    default: return launch_field<FAM_BCC4>(sp, sp.base, onsite, S, b, count, stride, st);
   }
+}
+
+cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st) {
+  return stencil_field_batch(c, S, b, 1, 0, onsite, st);
 }
 
 cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
