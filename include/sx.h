@@ -83,6 +83,18 @@ typedef enum {
 
 typedef enum { SX_DMI_INTERFACIAL = 0, SX_DMI_BULK = 1 } sx_dmi_kind;
 
+/* How the STENCIL backend runs a Heun step.  Both give bit-identical results
+ * (the same FP32 field sums in the same order, the same noise, the same FP64
+ * renormalisation).
+ *  SX_STENCIL_FUSED:    one launch; the predictor runs on the tile plus a halo
+ *                       and keeps S~ in shared memory (48 B of HBM traffic per
+ *                       spin-step, more arithmetic per site);
+ *  SX_STENCIL_TWO_PASS: a predictor pass writes S~ and f0 as FP32 planes, a
+ *                       corrector pass reads them (120 B per spin-step, no
+ *                       halo recomputation); needs a 24 B per site workspace;
+ *  SX_STENCIL_AUTO:     two-pass when its workspace can be allocated. */
+typedef enum { SX_STENCIL_AUTO = 0, SX_STENCIL_FUSED = 1, SX_STENCIL_TWO_PASS = 2 } sx_stencil_scheme;
+
 /* Crystal.  Cell vectors a[k] are rows in nm; sub_pos are fractional
  * coordinates; mu[s] is the moment of sublattice s in Bohr magnetons
  * ("Spin Hamiltonian and effective fields": mu_i = mu_i mu_B S_i).
@@ -234,6 +246,23 @@ int sx_get_taps(sx_ctx *ctx, int a, sx_tap *out, int cap);
  * serve (e.g. STENCIL with taps beyond its halo, TF32/BF16 without
  * IGEMM_TC); SX_ERR_ARG if a periodic axis is shorter than 2*range+1. */
 int sx_plan(sx_ctx *ctx, int backend, int precision);
+
+/* Choose the STENCIL Heun scheme (sx_stencil_scheme) for this and later
+ * plans of the context.  On a planned STENCIL context it takes effect at once
+ * (allocating or freeing the two-pass workspace); otherwise it is kept for
+ * the next sx_plan.  SX_ERR_ARG for an unknown scheme, SX_ERR_OOM when the
+ * two-pass workspace cannot be allocated (the plan is left unchanged). */
+int sx_set_stencil_scheme(sx_ctx *ctx, int scheme);
+
+/* Time the candidate Heun schemes of the plan on the caller's data and keep
+ * the fastest: each runs `steps` (>= 1) out-of-place steps S -> S_scratch
+ * (S is not modified; S_scratch is overwritten) after one warm-up step.
+ * times_ms (may be NULL) receives the mean step time of SX_STENCIL_FUSED and
+ * SX_STENCIL_TWO_PASS (-1 when a scheme was not timed).  Returns the chosen
+ * scheme (> 0) or a negative status.  Plans other than STENCIL have a single
+ * scheme and return SX_STENCIL_FUSED untimed.  Synchronises the stream. */
+int sx_autotune(sx_ctx *ctx, const double *S, double *S_scratch, const sx_llg_params *p, int steps,
+                double times_ms[2], void *stream);
 
 /* Reduced effective field b = -dH/dS (meV, see "Spin Hamiltonian and
  * effective fields") of the spin field S, written to b (device, same layout

@@ -31,7 +31,9 @@ EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shel
            "sx_add_dmi", "sx_add_bonds", "sx_set_zeeman", "sx_set_anisotropy", "sx_set_dipolar", "sx_get_taps",
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
            "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise", "sx_path_step",
-           "sx_geodesic")
+           "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune")
+SX_STENCIL_AUTO, SX_STENCIL_FUSED, SX_STENCIL_TWO_PASS = 0, 1, 2
+STENCIL_SCHEMES = {"auto": SX_STENCIL_AUTO, "fused": SX_STENCIL_FUSED, "two_pass": SX_STENCIL_TWO_PASS}
 SX_MIN_VP, SX_MIN_DAMPED_LLG = 0, 1
 SX_PATH_STRING, SX_PATH_GNEB, SX_PATH_CI_GNEB = 0, 1, 2
 PATH_METHODS = {"string": SX_PATH_STRING, "gneb": SX_PATH_GNEB, "ci_gneb": SX_PATH_CI_GNEB}
@@ -117,6 +119,8 @@ def lib():
             "sx_path_step": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(sx_path_params),
                                             ctypes.POINTER(ctypes.c_int), dp, dp, vp]),
             "sx_geodesic": (ctypes.c_int, [vp, vp, vp, dp, vp]),
+            "sx_set_stencil_scheme": (ctypes.c_int, [vp, ctypes.c_int]),
+            "sx_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_int, dp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -340,6 +344,23 @@ def sx_geodesic(ctx, A, B, nsite, stream=None):
     _chk(lib().sx_geodesic(ctx, _dev_ptr(A, 3 * nsite), _dev_ptr(B, 3 * nsite), ctypes.byref(out),
                            _stream(stream)), "sx_geodesic")
     return out.value
+
+
+def sx_set_stencil_scheme(ctx, scheme):
+    """Choose the stencil Heun scheme ("auto", "fused" or "two_pass")."""
+    return _chk(lib().sx_set_stencil_scheme(ctx, STENCIL_SCHEMES.get(scheme, scheme)), "sx_set_stencil_scheme")
+
+
+def sx_autotune(ctx, S, S_scratch, p, nsite, steps=5, stream=None):
+    """Time the stencil Heun schemes on S (unchanged) and keep the fastest; returns
+    (chosen scheme name, {"fused": ms, "two_pass": ms})."""
+    t = (ctypes.c_double * 2)()
+    rc = lib().sx_autotune(ctx, _dev_ptr(S, 3 * nsite), _dev_ptr(S_scratch, 3 * nsite), ctypes.byref(p), int(steps),
+                           t, _stream(stream))
+    if rc < 0:
+        _chk(rc, "sx_autotune")
+    name = {v: k for k, v in STENCIL_SCHEMES.items()}[rc]
+    return name, {"fused": t[0], "two_pass": t[1]}
 
 
 def sx_thermal_normals(seed, replica, site0, n, step, eta, stream=None):

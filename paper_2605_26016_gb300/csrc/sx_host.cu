@@ -509,6 +509,75 @@ int sx_plan(sx_ctx *c, int backend, int prec) {
   return SX_OK;
 }
 
+int sx_set_stencil_scheme(sx_ctx *c, int scheme) {
+  if (!c) return set_error(SX_ERR_ARG, "null context");
+  if (scheme != SX_STENCIL_AUTO && scheme != SX_STENCIL_FUSED && scheme != SX_STENCIL_TWO_PASS)
+    return set_error(SX_ERR_ARG, "unknown stencil scheme");
+  if (c->planned && c->backend == SX_BACKEND_STENCIL) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(c->device);
+    const int old = c->opt_scheme, old_eff = stencil_scheme(c);
+    c->opt_scheme = scheme;
+    int rc = stencil_set_scheme(c, scheme);
+    if (rc != SX_OK) {
+      c->opt_scheme = old;
+      stencil_set_scheme(c, old_eff);
+    }
+    cudaSetDevice(cur);
+    return rc;
+  }
+  c->opt_scheme = scheme;
+  return SX_OK;
+}
+
+int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_params *p, int steps, double times_ms[2],
+                void *stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if ((rc = check_spin_ptr(S, "S")) || (rc = check_spin_ptr(S_scratch, "S_scratch"))) return rc;
+  if (overlaps(S, S_scratch, 3 * (size_t)c->geo.nsite * sizeof(double)))
+    return set_error(SX_ERR_ARG, "S and S_scratch overlap");
+  if (steps < 1) return set_error(SX_ERR_ARG, "steps must be >= 1");
+  HeunConst h;
+  if ((rc = make_heun_const(c, p, h))) return rc;
+  if (times_ms) times_ms[0] = times_ms[1] = -1.0;
+  if (c->backend != SX_BACKEND_STENCIL) return SX_STENCIL_FUSED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int keep = c->opt_scheme;
+  double best = -1.0;
+  int best_scheme = stencil_scheme(c);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int scheme = SX_STENCIL_FUSED; scheme <= SX_STENCIL_TWO_PASS && e == cudaSuccess; ++scheme) {
+    if (stencil_set_scheme(c, scheme) != SX_OK || stencil_scheme(c) != scheme) continue;  // no workspace
+    if ((e = backend_step(c, S, S_scratch, h, 0, st)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = backend_step(c, S, S_scratch, h, (uint64_t)k, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    const double t = ms / steps;
+    if (times_ms) times_ms[scheme - 1] = t;
+    if (best < 0.0 || t < best) {
+      best = t;
+      best_scheme = scheme;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    stencil_set_scheme(c, keep);
+    return cuda_error(e, "autotune");
+  }
+  c->opt_scheme = best_scheme;
+  if ((rc = stencil_set_scheme(c, best_scheme)) != SX_OK) return rc;
+  return best_scheme;
+}
+
 int sx_field(sx_ctx *c, const double *S, double *b, void *stream) {
   int rc = check_ready(c);
   if (rc) return rc;

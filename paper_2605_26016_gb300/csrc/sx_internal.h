@@ -108,6 +108,7 @@ struct sx_ctx {
   sx::FftPlan *fft;
   sx::TcPlan *tc;
   double *d_min;  // minimiser workspace (velocity, force, partials), allocated on first use
+  int opt_scheme;     // stencil Heun scheme requested for the next plan (sx_stencil_scheme)
   double *d_path;     // path-method workspace (second chain, partial sums), allocated on first use
   size_t path_bytes;  // its size
   int launches_per_step;
@@ -133,6 +134,8 @@ cudaError_t thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int
 // stencil path (sx_stencil.cu)
 int stencil_plan(sx_ctx *c);
 void stencil_free(sx_ctx *c);
+int stencil_set_scheme(sx_ctx *c, int scheme);  // SX_STENCIL_*, on a planned stencil context
+int stencil_scheme(const sx_ctx *c);
 cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
 // fields of `count` spin fields stride doubles apart (S, S + stride, ...) into b, b + stride, ... in one launch
 cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int count, long long stride,

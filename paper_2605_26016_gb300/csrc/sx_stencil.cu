@@ -147,8 +147,12 @@ struct StencilArgs {
 struct StencilPlan {
   int family;
   int tz;           // z chunk of the fused Heun step (and of single-image field launches)
+  int tz2;          // z chunk of the two-pass Heun passes
   int nsm;          // SMs of the device
   int occ_field;    // resident CTAs per SM of the field kernel
+  int scheme;       // SX_STENCIL_FUSED or SX_STENCIL_TWO_PASS
+  float *d_St;      // two-pass workspace: S~ (3 nsite floats)
+  float *d_f0;      // two-pass workspace: f0 (3 nsite floats)
   StencilArgs base;
 };
 
@@ -471,24 +475,70 @@ struct GF {
   static constexpr size_t SMEM = OFF_STAGE + (size_t)3 * SN * 8;
 };
 
-// Reduced field of plane-marching tiles (32 x BY outputs); onsite adds Zeeman
-// and anisotropy.  Output FP64 (widened from the FP32 accumulators).
-template <int FID>
+// One plane-marching pass over 32 x BY output columns: the field of an input
+// spin field plus an epilogue per output site.
+//  PASS_FIELD: b = field (+ Zeeman and anisotropy when onsite), FP64 out;
+//  PASS_PRED:  Heun predictor from S^n (FP64 in): f0 = f(S^n, B), S~ = N[S^n + dt f0],
+//              S~ and f0 written as FP32 planes;
+//  PASS_CORR:  Heun corrector from S~ (FP32 in): f1 = f(S~, B~),
+//              S^{n+1} = N[S^n + dt/2 (f0 + f1)] in FP64 (S^n and f0 read at the site).
+// PASS_PRED followed by PASS_CORR is the two-pass form of the fused Heun step:
+// the same FP32 field sums in the same order, the same noise (drawn again from
+// its counter in the corrector), the same FP64 renormalisation.
+enum PassMode { PASS_FIELD = 0, PASS_PRED = 1, PASS_CORR = 2 };
+
+struct PassIO {
+  const double *S;   // FIELD, PRED: input spins; CORR: the FP64 state S^n
+  const float *St;   // CORR: S~ (three FP32 planes)
+  double *b;         // FIELD: output field
+  float *St_out;     // PRED: S~
+  float *f0;         // PRED: written; CORR: read
+  double *Sout;      // CORR: S^{n+1}
+  int nzc;           // z chunks per image (blockIdx.z = image * nzc + chunk)
+  long long istride; // doubles between images (FIELD)
+};
+
+// FP32 planes of S~ straight into the float4 ring (4-byte zero-filling copies)
+template <int NLOAD, int NT, int SN>
+__device__ __forceinline__ void issue_plane_f32(const StencilArgs &p, const float *__restrict__ S, int q, int tid,
+                                                const long long (&off)[NLOAD], unsigned okmask, float4 *dst) {
+  bool zok = true;
+  const int gz = wrap_axis(q, p.nz, p.pz, zok);
+  const long long zoff = (long long)gz * p.ny * p.nx;
+#pragma unroll
+  for (int j = 0; j < NLOAD; ++j) {
+    const int e = tid + j * NT;
+    if (e < SN) {
+      const bool ok = zok && ((okmask >> j) & 1u);
+      const float *src = ok ? S + off[j] + zoff : S;
+      float *d = reinterpret_cast<float *>(dst + e);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(d)), "l"(src),
+                   "r"(ok ? 4 : 0)
+                   : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(d + 1)),
+                   "l"(ok ? src + p.nsite : S), "r"(ok ? 4 : 0)
+                   : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(d + 2)),
+                   "l"(ok ? src + 2 * p.nsite : S), "r"(ok ? 4 : 0)
+                   : "memory");
+    }
+  }
+}
+
+template <int FID, int MODE>
 __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
-    k_field_stencil(const StencilArgs p, int onsite, const double *__restrict__ Sin, double *__restrict__ b,
-                    int nzc, long long istride) {
+    k_stencil_pass(const StencilArgs p, int onsite, const PassIO io) {
   using F = Family<FID>;
   using g = GF<F>;
   constexpr int NS = F::NSUB, R = F::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *sn = reinterpret_cast<float4 *>(smem_raw);                    // [2][SN]
   float4 *cq = reinterpret_cast<float4 *>(smem_raw + g::OFF_CQ);        // [R+1][NS][NT] centre values
-  double *stage = reinterpret_cast<double *>(smem_raw + g::OFF_STAGE);  // [3][SN]
+  double *stage = reinterpret_cast<double *>(smem_raw + g::OFF_STAGE);  // [3][SN] (FP64 input)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  // blockIdx.z = image * nzc + z chunk (several spin fields istride doubles apart in one launch)
-  const int img = blockIdx.z / nzc, zc = blockIdx.z - img * nzc;
-  Sin += img * istride;
-  b += img * istride;
+  const int img = blockIdx.z / io.nzc, zc = blockIdx.z - img * io.nzc;
+  const double *Sin = io.S + img * io.istride;
+  double *bout = io.b + img * io.istride;
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * F::BY, z0 = zc * p.tz;
   const int tzc = min(p.tz, p.nz - z0);
   const int cx = x0 + tx, cy = y0 + ty;
@@ -503,19 +553,28 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
   unsigned okmask;
   load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(p, x0 - R, y0 - R, tid, off, okmask);
   const int niter = tzc + 2 * R;
-  issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, z0 - R, tid, off, okmask, stage);
+  if constexpr (MODE == PASS_CORR)
+    issue_plane_f32<g::NLOAD, g::NT, g::SN>(p, io.St, z0 - R, tid, off, okmask, sn);
+  else
+    issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, z0 - R, tid, off, okmask, stage);
   cp_commit();
   for (int k = 0; k < niter; ++k) {
     const int q = z0 - R + k;
     float4 *buf = sn + (k & 1) * g::SN;
     cp_wait<0>();
-    convert_plane<g::NLOAD, g::NT, g::SN>(stage, buf, tid);
-    if (k + 1 < niter) issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, q + 1, tid, off, okmask, stage);
+    if constexpr (MODE == PASS_CORR) {
+      __syncthreads();  // every thread's copies of plane q have landed
+      if (k + 1 < niter)
+        issue_plane_f32<g::NLOAD, g::NT, g::SN>(p, io.St, q + 1, tid, off, okmask, sn + ((k + 1) & 1) * g::SN);
+    } else {
+      convert_plane<g::NLOAD, g::NT, g::SN>(stage, buf, tid);
+      if (k + 1 < niter) issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, q + 1, tid, off, okmask, stage);
+    }
     cp_commit();
-    __syncthreads();
+    if constexpr (MODE != PASS_CORR) __syncthreads();
     const float4 *base = buf + (ty + R) * g::LX + (tx + R);
     push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, g::LX * g::LY, g::LX, acc);
-    // keep this plane's centre values for the on-site terms R planes later
+    // keep this plane's centre values for the epilogue R planes later
 #pragma unroll
     for (int a = 0; a < NS; ++a) cq[((k % (R + 1)) * NS + a) * g::NT + tid] = base[a * g::LX * g::LY];
     const int kc = k - 2 * R;
@@ -524,15 +583,44 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
 #pragma unroll
       for (int a = 0; a < NS; ++a) {
         float v[3] = {acc[a][0][0], acc[a][0][1], acc[a][0][2]};
-        if (onsite) {
-          const float4 c4 = cq[(((k - R) % (R + 1)) * NS + a) * g::NT + tid];
-          const float s[3] = {c4.x, c4.y, c4.z};
-          onsite32(p, a, s, v);
-        }
+        const float4 c4 = cq[(((k - R) % (R + 1)) * NS + a) * g::NT + tid];
+        const float s[3] = {c4.x, c4.y, c4.z};
         const long long i = a * subvol + c * plane + (long long)cy * p.nx + cx;
-        b[i] = (double)v[0];
-        b[p.nsite + i] = (double)v[1];
-        b[2 * p.nsite + i] = (double)v[2];
+        if constexpr (MODE == PASS_FIELD) {
+          if (onsite) onsite32(p, a, s, v);
+          bout[i] = (double)v[0];
+          bout[p.nsite + i] = (double)v[1];
+          bout[2 * p.nsite + i] = (double)v[2];
+        } else {
+          onsite32(p, a, s, v);
+          float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+          if (p.thermal) normals3(p.seed, p.replica, (unsigned long long)i, p.step, e0, e1, e2);
+          const float sg = p.sigma[a], im = p.inv_mm[a];
+          const float B[3] = {fmaf(v[0], im, sg * e0), fmaf(v[1], im, sg * e1), fmaf(v[2], im, sg * e2)};
+          float f[3];
+          rhs32(s, B, p.g, p.alpha, f);
+          if constexpr (MODE == PASS_PRED) {
+            const float x[3] = {fmaf(p.dt, f[0], s[0]), fmaf(p.dt, f[1], s[1]), fmaf(p.dt, f[2], s[2])};
+            const float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            float r = rsqrtf(n2);
+            r = r * fmaf(-0.5f * n2, r * r, 1.5f);
+            io.St_out[i] = x[0] * r;
+            io.St_out[p.nsite + i] = x[1] * r;
+            io.St_out[2 * p.nsite + i] = x[2] * r;
+            io.f0[i] = f[0];
+            io.f0[p.nsite + i] = f[1];
+            io.f0[2 * p.nsite + i] = f[2];
+          } else {
+            const float d[3] = {p.hdt * (io.f0[i] + f[0]), p.hdt * (io.f0[p.nsite + i] + f[1]),
+                                p.hdt * (io.f0[2 * p.nsite + i] + f[2])};
+            const double S0[3] = {io.S[i], io.S[p.nsite + i], io.S[2 * p.nsite + i]};
+            double o[3];
+            renormalise64(S0, d, o);
+            io.Sout[i] = o[0];
+            io.Sout[p.nsite + i] = o[1];
+            io.Sout[2 * p.nsite + i] = o[2];
+          }
+        }
       }
     }
     shift_acc<F>(acc);
@@ -582,8 +670,11 @@ cudaError_t set_smem() {
   cudaError_t e = cudaFuncSetAttribute(k_heun_fused<FID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)G<Family<FID>>::SMEM);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_field_stencil<FID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)GF<Family<FID>>::SMEM);
+  for (auto fn : {k_stencil_pass<FID, PASS_FIELD>, k_stencil_pass<FID, PASS_PRED>, k_stencil_pass<FID, PASS_CORR>}) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GF<Family<FID>>::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <int FID>
@@ -623,10 +714,35 @@ cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &base, int ons
   using g = GF<Family<FID>>;
   StencilArgs a = base;
   a.tz = count == 1 ? sp.tz : field_tz<FID>(sp, a, count);
-  const int nzc = (a.nz + a.tz - 1) / a.tz;
-  if ((long long)nzc * count > 65535) return cudaErrorInvalidConfiguration;
-  const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, nzc * count);
-  k_field_stencil<FID><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, onsite, S, b, nzc, stride);
+  PassIO io;
+  memset(&io, 0, sizeof(io));
+  io.S = S;
+  io.b = b;
+  io.nzc = (a.nz + a.tz - 1) / a.tz;
+  io.istride = stride;
+  if ((long long)io.nzc * count > 65535) return cudaErrorInvalidConfiguration;
+  const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc * count);
+  k_stencil_pass<FID, PASS_FIELD><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, onsite, io);
+  return cudaGetLastError();
+}
+
+// two-pass Heun step: predictor pass into the S~ / f0 workspace, corrector pass into dst
+template <int FID>
+cudaError_t launch_heun2(const StencilPlan &sp, StencilArgs a, const double *src, double *dst, cudaStream_t st) {
+  using g = GF<Family<FID>>;
+  a.tz = sp.tz2;
+  PassIO io;
+  memset(&io, 0, sizeof(io));
+  io.S = src;
+  io.St = sp.d_St;
+  io.St_out = sp.d_St;
+  io.f0 = sp.d_f0;
+  io.Sout = dst;
+  io.nzc = (a.nz + a.tz - 1) / a.tz;
+  io.b = nullptr;
+  const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc);
+  k_stencil_pass<FID, PASS_PRED><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, 1, io);
+  k_stencil_pass<FID, PASS_CORR><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, 1, io);
   return cudaGetLastError();
 }
 
@@ -663,7 +779,7 @@ int choose_tz(const sx_ctx *c) {
 template <int FID>
 int field_occupancy() {
   int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_field_stencil<FID>, GF<Family<FID>>::NT,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stencil_pass<FID, PASS_CORR>, GF<Family<FID>>::NT,
                                                     GF<Family<FID>>::SMEM) != cudaSuccess ||
       occ < 1)
     occ = 1;
@@ -741,12 +857,54 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC26_TEN: sp->occ_field = field_occupancy<FAM_SC26_TEN>(); break;
     default: sp->occ_field = field_occupancy<FAM_BCC4>(); break;
   }
+  switch (fam) {
+    case FAM_SC6_ISO: sp->tz2 = field_tz<FAM_SC6_ISO>(*sp, a, 1); break;
+    case FAM_SC6_TEN: sp->tz2 = field_tz<FAM_SC6_TEN>(*sp, a, 1); break;
+    case FAM_SC26_ISO: sp->tz2 = field_tz<FAM_SC26_ISO>(*sp, a, 1); break;
+    case FAM_SC26_TEN: sp->tz2 = field_tz<FAM_SC26_TEN>(*sp, a, 1); break;
+    default: sp->tz2 = field_tz<FAM_BCC4>(*sp, a, 1); break;
+  }
   c->stencil = sp;
-  c->launches_per_step = 1;
+  const int rc = stencil_set_scheme(c, c->opt_scheme);
+  if (rc != SX_OK) {
+    stencil_free(c);
+    return rc;
+  }
   return SX_OK;
 }
 
+int stencil_set_scheme(sx_ctx *c, int scheme) {
+  StencilPlan *sp = c->stencil;
+  if (scheme == SX_STENCIL_AUTO) scheme = SX_STENCIL_TWO_PASS;
+  if (scheme == SX_STENCIL_TWO_PASS && !sp->d_St) {
+    const size_t bytes = 3 * (size_t)c->geo.nsite * sizeof(float);
+    if (cudaMalloc(&sp->d_St, bytes) != cudaSuccess || cudaMalloc(&sp->d_f0, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(sp->d_St);
+      sp->d_St = nullptr;
+      sp->d_f0 = nullptr;
+      if (c->opt_scheme == SX_STENCIL_TWO_PASS)
+        return set_error(SX_ERR_OOM, "two-pass stencil workspace (24 B per site): out of device memory");
+      scheme = SX_STENCIL_FUSED;
+    }
+  }
+  if (scheme == SX_STENCIL_FUSED && sp->d_St) {
+    cudaFree(sp->d_St);
+    cudaFree(sp->d_f0);
+    sp->d_St = sp->d_f0 = nullptr;
+  }
+  sp->scheme = scheme;
+  c->launches_per_step = scheme == SX_STENCIL_TWO_PASS ? 2 : 1;
+  return SX_OK;
+}
+
+int stencil_scheme(const sx_ctx *c) { return c->stencil ? c->stencil->scheme : -1; }
+
 void stencil_free(sx_ctx *c) {
+  if (c->stencil) {
+    cudaFree(c->stencil->d_St);
+    cudaFree(c->stencil->d_f0);
+  }
   delete c->stencil;
   c->stencil = nullptr;
 }
@@ -782,6 +940,15 @@ cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, c
   a.seed = h.seed;
   a.replica = h.replica;
   a.step = step;
+  if (sp.scheme == SX_STENCIL_TWO_PASS) {
+    switch (sp.family) {
+      case FAM_SC6_ISO: return launch_heun2<FAM_SC6_ISO>(sp, a, src, dst, st);
+      case FAM_SC6_TEN: return launch_heun2<FAM_SC6_TEN>(sp, a, src, dst, st);
+      case FAM_SC26_ISO: return launch_heun2<FAM_SC26_ISO>(sp, a, src, dst, st);
+      case FAM_SC26_TEN: return launch_heun2<FAM_SC26_TEN>(sp, a, src, dst, st);
+      default: return launch_heun2<FAM_BCC4>(sp, a, src, dst, st);
+    }
+  }
   switch (sp.family) {
     case FAM_SC6_ISO: return launch_heun<FAM_SC6_ISO>(sp, a, src, dst, st);
     case FAM_SC6_TEN: return launch_heun<FAM_SC6_TEN>(sp, a, src, dst, st);

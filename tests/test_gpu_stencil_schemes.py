@@ -1,0 +1,72 @@
+"""The two STENCIL Heun schemes (fused single launch, two-pass predictor/corrector) give bit-identical
+steps; the autotuner picks one of them without touching the input."""
+import numpy as np
+import pytest
+
+import paper_2605_26016_gb300 as sx
+from workloads import random_spins
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_26016_gb300.build import build
+    build()
+
+
+CASES = [
+    ("bcc_4shell", (13, 11, 9), (1, 1, 0)),
+    ("bcc_4shell", (40, 30, 20), (1, 0, 1)),
+    ("sc_j123_dmi", (17, 12, 10), (1, 1, 1)),
+    ("sc_j123_dmi", (31, 29, 33), (1, 1, 0)),
+    ("sc_j123", (70, 40, 25), (0, 1, 1)),
+    ("sc_nn", (33, 5, 7), (1, 1, 1)),
+    ("sc_nn", (64, 48, 40), (0, 0, 0)),
+]
+
+
+@pytest.mark.parametrize("thermal", [False, True])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_fused_and_two_pass_steps_are_bit_identical(case, thermal):
+    name, n, pbc = CASES[case]
+    s, w = sx.system_from_workload(name, n, pbc=pbc)
+    S0 = torch.from_numpy(random_spins(s.nsub, n, 300 + case)).cuda()
+    T = 120.0 if thermal else 0.0
+    out = {}
+    for scheme, launches in (("fused", 1), ("two_pass", 2)):
+        sx.sx_set_stencil_scheme(s.ctx, scheme)
+        info = s.plan("stencil", "fp32")
+        assert info["launches_per_step"] == launches
+        S = S0.clone()
+        s.heun(S, torch.empty_like(S), dt=w["dt"], alpha=w["alpha"], T=T, seed=9, replica=2, step0=17, nsteps=3)
+        torch.cuda.synchronize()
+        out[scheme] = S.cpu().numpy()
+    assert np.array_equal(out["fused"].view(np.uint64), out["two_pass"].view(np.uint64))
+
+
+def test_scheme_switch_on_a_planned_context_and_autotune():
+    n = (48, 40, 36)
+    s, w = sx.system_from_workload("bcc_4shell", n)
+    assert s.plan("stencil", "fp32")["launches_per_step"] == 2  # auto: two-pass
+    sx.sx_set_stencil_scheme(s.ctx, "fused")
+    assert s.info()["launches_per_step"] == 1
+    with pytest.raises(sx.SxError):
+        sx.sx_set_stencil_scheme(s.ctx, 9)
+    assert s.info()["launches_per_step"] == 1
+    S = torch.from_numpy(random_spins(2, n, 5)).cuda()
+    keep = S.clone()
+    p = sx.llg_params(w["dt"], w["alpha"], w["T"], seed=1)
+    name, t = sx.sx_autotune(s.ctx, S, torch.empty_like(S), p, s.nsite, steps=3)
+    assert name in ("fused", "two_pass")
+    assert t["fused"] > 0 and t["two_pass"] > 0
+    assert torch.equal(S, keep)
+    assert s.info()["launches_per_step"] == (1 if name == "fused" else 2)
+    # the gather backend has one scheme
+    g, _ = sx.system_from_workload("bcc_4shell", (8, 8, 8))
+    g.plan("gather", "fp32")
+    S8 = torch.from_numpy(random_spins(2, (8, 8, 8), 5)).cuda()
+    assert sx.sx_autotune(g.ctx, S8, torch.empty_like(S8), p, g.nsite)[0] == "fused"
