@@ -89,9 +89,10 @@ typedef enum { SX_DMI_INTERFACIAL = 0, SX_DMI_BULK = 1 } sx_dmi_kind;
  *  SX_STENCIL_FUSED:    one launch; the predictor runs on the tile plus a halo
  *                       and keeps S~ in shared memory (48 B of HBM traffic per
  *                       spin-step, more arithmetic per site);
- *  SX_STENCIL_TWO_PASS: a predictor pass writes S~ and f0 as FP32 planes, a
- *                       corrector pass reads them (120 B per spin-step, no
- *                       halo recomputation); needs a 24 B per site workspace;
+ *  SX_STENCIL_TWO_PASS: a predictor pass writes S~, f0 and (thermal steps)
+ *                       the normals as FP32 planes, a corrector pass reads
+ *                       them (120 B per spin-step, 144 B with noise; no halo
+ *                       recomputation); needs a 36 B per site workspace;
  *  SX_STENCIL_AUTO:     two-pass when its workspace can be allocated. */
 typedef enum { SX_STENCIL_AUTO = 0, SX_STENCIL_FUSED = 1, SX_STENCIL_TWO_PASS = 2 } sx_stencil_scheme;
 

@@ -153,6 +153,7 @@ struct StencilPlan {
   int scheme;       // SX_STENCIL_FUSED or SX_STENCIL_TWO_PASS
   float *d_St;      // two-pass workspace: S~ (3 nsite floats)
   float *d_f0;      // two-pass workspace: f0 (3 nsite floats)
+  float *d_eta;     // two-pass workspace: thermal normals (3 nsite floats)
   StencilArgs base;
 };
 
@@ -481,10 +482,11 @@ struct GF {
 //  PASS_PRED:  Heun predictor from S^n (FP64 in): f0 = f(S^n, B), S~ = N[S^n + dt f0],
 //              S~ and f0 written as FP32 planes;
 //  PASS_CORR:  Heun corrector from S~ (FP32 in): f1 = f(S~, B~),
-//              S^{n+1} = N[S^n + dt/2 (f0 + f1)] in FP64 (S^n and f0 read at the site).
+//              S^{n+1} = N[S^n + dt/2 (f0 + f1)] in FP64 (S^n, f0 and, for a
+//              thermal step, the predictor's normals read at the site).
 // PASS_PRED followed by PASS_CORR is the two-pass form of the fused Heun step:
-// the same FP32 field sums in the same order, the same noise (drawn again from
-// its counter in the corrector), the same FP64 renormalisation.
+// the same FP32 field sums in the same order, the same noise, the same FP64
+// renormalisation.
 enum PassMode { PASS_FIELD = 0, PASS_PRED = 1, PASS_CORR = 2 };
 
 struct PassIO {
@@ -493,6 +495,7 @@ struct PassIO {
   double *b;         // FIELD: output field
   float *St_out;     // PRED: S~
   float *f0;         // PRED: written; CORR: read
+  float *eta;        // thermal steps: the normals, written by PRED and read by CORR
   double *Sout;      // CORR: S^{n+1}
   int nzc;           // z chunks per image (blockIdx.z = image * nzc + chunk)
   long long istride; // doubles between images (FIELD)
@@ -553,6 +556,27 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
   unsigned okmask;
   load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(p, x0 - R, y0 - R, tid, off, okmask);
   const int niter = tzc + 2 * R;
+  // corrector: S^n and f0 of the next output plane, loaded one plane ahead so the
+  // global-load latency hides behind a plane of field work
+  double nS[NS][3];
+  float nf[NS][3], ne[NS][3];
+  auto prefetch = [&](int cz) {
+    if constexpr (MODE == PASS_CORR) {
+      if (mine && cz < z0 + tzc) {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+          const long long i = a * subvol + cz * plane + (long long)cy * p.nx + cx;
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            nS[a][m] = io.S[m * p.nsite + i];
+            nf[a][m] = io.f0[m * p.nsite + i];
+            ne[a][m] = p.thermal ? io.eta[m * p.nsite + i] : 0.0f;
+          }
+        }
+      }
+    }
+  };
+  prefetch(z0);
   if constexpr (MODE == PASS_CORR)
     issue_plane_f32<g::NLOAD, g::NT, g::SN>(p, io.St, z0 - R, tid, off, okmask, sn);
   else
@@ -594,7 +618,18 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
         } else {
           onsite32(p, a, s, v);
           float e0 = 0.f, e1 = 0.f, e2 = 0.f;
-          if (p.thermal) normals3(p.seed, p.replica, (unsigned long long)i, p.step, e0, e1, e2);
+          if constexpr (MODE == PASS_PRED) {
+            if (p.thermal) {
+              normals3(p.seed, p.replica, (unsigned long long)i, p.step, e0, e1, e2);
+              io.eta[i] = e0;
+              io.eta[p.nsite + i] = e1;
+              io.eta[2 * p.nsite + i] = e2;
+            }
+          } else {
+            e0 = ne[a][0];
+            e1 = ne[a][1];
+            e2 = ne[a][2];
+          }
           const float sg = p.sigma[a], im = p.inv_mm[a];
           const float B[3] = {fmaf(v[0], im, sg * e0), fmaf(v[1], im, sg * e1), fmaf(v[2], im, sg * e2)};
           float f[3];
@@ -611,17 +646,16 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
             io.f0[p.nsite + i] = f[1];
             io.f0[2 * p.nsite + i] = f[2];
           } else {
-            const float d[3] = {p.hdt * (io.f0[i] + f[0]), p.hdt * (io.f0[p.nsite + i] + f[1]),
-                                p.hdt * (io.f0[2 * p.nsite + i] + f[2])};
-            const double S0[3] = {io.S[i], io.S[p.nsite + i], io.S[2 * p.nsite + i]};
+            const float d[3] = {p.hdt * (nf[a][0] + f[0]), p.hdt * (nf[a][1] + f[1]), p.hdt * (nf[a][2] + f[2])};
             double o[3];
-            renormalise64(S0, d, o);
+            renormalise64(nS[a], d, o);
             io.Sout[i] = o[0];
             io.Sout[p.nsite + i] = o[1];
             io.Sout[2 * p.nsite + i] = o[2];
           }
         }
       }
+      prefetch(c + 1);
     }
     shift_acc<F>(acc);
     __syncthreads();
@@ -737,6 +771,7 @@ cudaError_t launch_heun2(const StencilPlan &sp, StencilArgs a, const double *src
   io.St = sp.d_St;
   io.St_out = sp.d_St;
   io.f0 = sp.d_f0;
+  io.eta = sp.d_eta;
   io.Sout = dst;
   io.nzc = (a.nz + a.tz - 1) / a.tz;
   io.b = nullptr;
@@ -878,20 +913,22 @@ int stencil_set_scheme(sx_ctx *c, int scheme) {
   if (scheme == SX_STENCIL_AUTO) scheme = SX_STENCIL_TWO_PASS;
   if (scheme == SX_STENCIL_TWO_PASS && !sp->d_St) {
     const size_t bytes = 3 * (size_t)c->geo.nsite * sizeof(float);
-    if (cudaMalloc(&sp->d_St, bytes) != cudaSuccess || cudaMalloc(&sp->d_f0, bytes) != cudaSuccess) {
+    if (cudaMalloc(&sp->d_St, bytes) != cudaSuccess || cudaMalloc(&sp->d_f0, bytes) != cudaSuccess ||
+        cudaMalloc(&sp->d_eta, bytes) != cudaSuccess) {
       cudaGetLastError();
       cudaFree(sp->d_St);
-      sp->d_St = nullptr;
-      sp->d_f0 = nullptr;
+      cudaFree(sp->d_f0);
+      sp->d_St = sp->d_f0 = sp->d_eta = nullptr;
       if (c->opt_scheme == SX_STENCIL_TWO_PASS)
-        return set_error(SX_ERR_OOM, "two-pass stencil workspace (24 B per site): out of device memory");
+        return set_error(SX_ERR_OOM, "two-pass stencil workspace (36 B per site): out of device memory");
       scheme = SX_STENCIL_FUSED;
     }
   }
   if (scheme == SX_STENCIL_FUSED && sp->d_St) {
     cudaFree(sp->d_St);
     cudaFree(sp->d_f0);
-    sp->d_St = sp->d_f0 = nullptr;
+    cudaFree(sp->d_eta);
+    sp->d_St = sp->d_f0 = sp->d_eta = nullptr;
   }
   sp->scheme = scheme;
   c->launches_per_step = scheme == SX_STENCIL_TWO_PASS ? 2 : 1;
@@ -904,6 +941,7 @@ void stencil_free(sx_ctx *c) {
   if (c->stencil) {
     cudaFree(c->stencil->d_St);
     cudaFree(c->stencil->d_f0);
+    cudaFree(c->stencil->d_eta);
   }
   delete c->stencil;
   c->stencil = nullptr;
