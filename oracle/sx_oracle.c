@@ -644,7 +644,8 @@ static float u01(uint32_t x) { return (float)(2u * (x >> 9) + 1u) * 5.9604644775
 /* natural log of u in (0,1) by u = m 2^e, m in [sqrt(1/2), sqrt(2)],
  * ln m = 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9), s = (m-1)/(m+1).
  * Every step is one correctly rounded FP32 operation (built without FP
- * contraction), so the result is reproducible bit for bit. */
+ * contraction; each Horner step is one fused multiply-add, fmaf, which IEEE 754
+ * also rounds once), so the result is reproducible bit for bit. */
 static float bm_log(float u) {
   uint32_t bits;
   memcpy(&bits, &u, 4);
@@ -658,41 +659,41 @@ static float bm_log(float u) {
   }
   float s = (mm - 1.0f) / (mm + 1.0f);
   float s2 = s * s;
-  float p = 0.111111111f;     /* 1/9 */
-  p = p * s2 + 0.142857143f;  /* 1/7 */
-  p = p * s2 + 0.2f;          /* 1/5 */
-  p = p * s2 + 0.333333333f;  /* 1/3 */
-  p = p * s2 + 1.0f;
+  float p = 0.111111111f;            /* 1/9 */
+  p = fmaf(p, s2, 0.142857143f);     /* 1/7 */
+  p = fmaf(p, s2, 0.2f);             /* 1/5 */
+  p = fmaf(p, s2, 0.333333333f);     /* 1/3 */
+  p = fmaf(p, s2, 1.0f);
   float lnm = (2.0f * s) * p;
-  return (float)e * 0.693147181f + lnm;
+  return fmaf((float)e, 0.693147181f, lnm);
 }
 
 /* cos and sin of 2 pi u for u in (0,1): quadrant q = floor(4u) (exact),
  * x = (4u - q) pi/2 in [0, pi/2), Taylor series of sin (to x^15) and cos
- * (to x^14) in Horner form, then the quadrant map. */
+ * (to x^14) in Horner form with one fmaf per step, then the quadrant map. */
 static void bm_sincos2pi(float u, float *cs, float *sn) {
   float t = 4.0f * u;
   int q = (int)t;
   float r = t - (float)q;
   float x = r * 1.57079633f;
   float x2 = x * x;
-  float sp = -7.64716373e-13f;        /* -1/15! */
-  sp = sp * x2 + 1.60590438e-10f;     /* 1/13! */
-  sp = sp * x2 + -2.50521084e-8f;     /* -1/11! */
-  sp = sp * x2 + 2.75573192e-6f;      /* 1/9! */
-  sp = sp * x2 + -1.98412698e-4f;     /* -1/7! */
-  sp = sp * x2 + 8.33333333e-3f;      /* 1/5! */
-  sp = sp * x2 + -1.66666667e-1f;     /* -1/3! */
-  sp = sp * x2 + 1.0f;
+  float sp = -7.64716373e-13f;            /* -1/15! */
+  sp = fmaf(sp, x2, 1.60590438e-10f);     /* 1/13! */
+  sp = fmaf(sp, x2, -2.50521084e-8f);     /* -1/11! */
+  sp = fmaf(sp, x2, 2.75573192e-6f);      /* 1/9! */
+  sp = fmaf(sp, x2, -1.98412698e-4f);     /* -1/7! */
+  sp = fmaf(sp, x2, 8.33333333e-3f);      /* 1/5! */
+  sp = fmaf(sp, x2, -1.66666667e-1f);     /* -1/3! */
+  sp = fmaf(sp, x2, 1.0f);
   float sx = sp * x;
-  float cp = -1.14707456e-11f;        /* -1/14! */
-  cp = cp * x2 + 2.08767570e-9f;      /* 1/12! */
-  cp = cp * x2 + -2.75573192e-7f;     /* -1/10! */
-  cp = cp * x2 + 2.48015873e-5f;      /* 1/8! */
-  cp = cp * x2 + -1.38888889e-3f;     /* -1/6! */
-  cp = cp * x2 + 4.16666667e-2f;      /* 1/4! */
-  cp = cp * x2 + -0.5f;               /* -1/2! */
-  cp = cp * x2 + 1.0f;
+  float cp = -1.14707456e-11f;            /* -1/14! */
+  cp = fmaf(cp, x2, 2.08767570e-9f);      /* 1/12! */
+  cp = fmaf(cp, x2, -2.75573192e-7f);     /* -1/10! */
+  cp = fmaf(cp, x2, 2.48015873e-5f);      /* 1/8! */
+  cp = fmaf(cp, x2, -1.38888889e-3f);     /* -1/6! */
+  cp = fmaf(cp, x2, 4.16666667e-2f);      /* 1/4! */
+  cp = fmaf(cp, x2, -0.5f);               /* -1/2! */
+  cp = fmaf(cp, x2, 1.0f);
   float cx = cp;
   switch (q & 3) {
     case 0: *cs = cx; *sn = sx; break;

@@ -12,8 +12,10 @@
 // sqrt(-2 ln u0) (cos, sin)(2 pi u1), eta2 = sqrt(-2 ln u2) cos(2 pi u3).
 // ln and sincos are short polynomial evaluations in which every operation is
 // a single correctly rounded FP32 operation (explicit _rn intrinsics, so the
-// compiler cannot fuse them), which makes the normals reproducible bit for
-// bit on any IEEE machine that performs the same operation sequence:
+// compiler cannot fuse or split them; each Horner step is one fused
+// multiply-add, rounded once as IEEE 754 specifies), which makes the normals
+// reproducible bit for bit on any IEEE machine that performs the same
+// operation sequence:
 //   ln u:  u = m 2^e with m in [sqrt(1/2), sqrt(2)], s = (m-1)/(m+1),
 //          ln u = e ln2 + 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9);
 //   2 pi u: q = floor(4u), x = (4u - q) pi/2, Taylor sin to x^15 and cos to
@@ -55,11 +57,11 @@ __device__ __forceinline__ float ln_open(float u) {
   const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
   const float s2 = __fmul_rn(s, s);
   float p = 0.111111111f;
-  p = __fadd_rn(__fmul_rn(p, s2), 0.142857143f);
-  p = __fadd_rn(__fmul_rn(p, s2), 0.2f);
-  p = __fadd_rn(__fmul_rn(p, s2), 0.333333333f);
-  p = __fadd_rn(__fmul_rn(p, s2), 1.0f);
-  return __fadd_rn(__fmul_rn(__int2float_rn(e), 0.693147181f), __fmul_rn(__fmul_rn(2.0f, s), p));
+  p = __fmaf_rn(p, s2, 0.142857143f);
+  p = __fmaf_rn(p, s2, 0.2f);
+  p = __fmaf_rn(p, s2, 0.333333333f);
+  p = __fmaf_rn(p, s2, 1.0f);
+  return __fmaf_rn(__int2float_rn(e), 0.693147181f, __fmul_rn(__fmul_rn(2.0f, s), p));
 }
 
 __device__ __forceinline__ void cos_sin_2pi(float u, float &cs, float &sn) {
@@ -68,22 +70,22 @@ __device__ __forceinline__ void cos_sin_2pi(float u, float &cs, float &sn) {
   const float x = __fmul_rn(__fsub_rn(t, __int2float_rn(q)), 1.57079633f);
   const float x2 = __fmul_rn(x, x);
   float ps = -7.64716373e-13f;
-  ps = __fadd_rn(__fmul_rn(ps, x2), 1.60590438e-10f);
-  ps = __fadd_rn(__fmul_rn(ps, x2), -2.50521084e-8f);
-  ps = __fadd_rn(__fmul_rn(ps, x2), 2.75573192e-6f);
-  ps = __fadd_rn(__fmul_rn(ps, x2), -1.98412698e-4f);
-  ps = __fadd_rn(__fmul_rn(ps, x2), 8.33333333e-3f);
-  ps = __fadd_rn(__fmul_rn(ps, x2), -1.66666667e-1f);
-  ps = __fadd_rn(__fmul_rn(ps, x2), 1.0f);
+  ps = __fmaf_rn(ps, x2, 1.60590438e-10f);
+  ps = __fmaf_rn(ps, x2, -2.50521084e-8f);
+  ps = __fmaf_rn(ps, x2, 2.75573192e-6f);
+  ps = __fmaf_rn(ps, x2, -1.98412698e-4f);
+  ps = __fmaf_rn(ps, x2, 8.33333333e-3f);
+  ps = __fmaf_rn(ps, x2, -1.66666667e-1f);
+  ps = __fmaf_rn(ps, x2, 1.0f);
   const float sx = __fmul_rn(ps, x);
   float pc = -1.14707456e-11f;
-  pc = __fadd_rn(__fmul_rn(pc, x2), 2.08767570e-9f);
-  pc = __fadd_rn(__fmul_rn(pc, x2), -2.75573192e-7f);
-  pc = __fadd_rn(__fmul_rn(pc, x2), 2.48015873e-5f);
-  pc = __fadd_rn(__fmul_rn(pc, x2), -1.38888889e-3f);
-  pc = __fadd_rn(__fmul_rn(pc, x2), 4.16666667e-2f);
-  pc = __fadd_rn(__fmul_rn(pc, x2), -0.5f);
-  pc = __fadd_rn(__fmul_rn(pc, x2), 1.0f);
+  pc = __fmaf_rn(pc, x2, 2.08767570e-9f);
+  pc = __fmaf_rn(pc, x2, -2.75573192e-7f);
+  pc = __fmaf_rn(pc, x2, 2.48015873e-5f);
+  pc = __fmaf_rn(pc, x2, -1.38888889e-3f);
+  pc = __fmaf_rn(pc, x2, 4.16666667e-2f);
+  pc = __fmaf_rn(pc, x2, -0.5f);
+  pc = __fmaf_rn(pc, x2, 1.0f);
   const float cx = pc;
   switch (q & 3) {
     case 0: cs = cx; sn = sx; break;

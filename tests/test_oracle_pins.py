@@ -302,6 +302,21 @@ def test_normal_noise_statistics():
     assert np.abs(cc - np.eye(3)).max() < 5 / math.sqrt(eta.shape[0])
 
 
+def test_box_muller_transform_is_accurate():
+    # the FP32 normals equal the Box-Muller transform of the same Philox words evaluated in FP64 with
+    # libm's log, cos and sin, to a few FP32 ulps: pins the project-written log and sincos
+    rng = np.random.default_rng(3)
+    for site in rng.integers(0, 2 ** 40, size=4000):
+        site = int(site)
+        x = oracle.philox4x32_10((site & 0xFFFFFFFF, site >> 32, 11, 2 << 8), (77, 0))
+        u = [(2 * (w >> 9) + 1) * 2.0 ** -24 for w in x]
+        r0, r1 = math.sqrt(-2 * math.log(u[0])), math.sqrt(-2 * math.log(u[2]))
+        ref = np.array([r0 * math.cos(2 * math.pi * u[1]), r0 * math.sin(2 * math.pi * u[1]),
+                        r1 * math.cos(2 * math.pi * u[3])])
+        got = oracle.normals(77, 2, site, 1, 11)[0].astype(np.float64)
+        assert np.abs(got - ref).max() <= 4e-7 * max(1.0, np.abs(ref).max())
+
+
 def test_noise_is_counter_based():
     a = oracle.normals(7, 0, 50, 10, 3)
     b = oracle.normals(7, 0, 55, 5, 3)
