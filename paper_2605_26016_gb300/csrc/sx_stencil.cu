@@ -202,45 +202,61 @@ struct G {
   static constexpr size_t SMEM = OFF_S64 + (size_t)NS * 3 * NI * 8;
 };
 
-// accumulate one staged plane into acc[a][R - dz][c] for every tap
+// Per-thread accumulator of one output site and one dz: (x, y) packed for the
+// f32x2 FMA pipe path, z alone.  Each lane of __ffma2_rn is one fused
+// multiply-add, so the sums equal scalar fmaf sums taken in the same order.
+struct Acc3 {
+  float2 xy;
+  float z;
+};
+
+// accumulate one staged plane into acc[a][R - dz] for every tap
 template <class F, int I>
 __device__ __forceinline__ void tap_push(const StencilArgs &p, const float4 *__restrict__ base, int pitch_sub,
-                                         int pitch_row, float4 &v, float (&acc)[F::NSUB][2 * F::R + 1][3]) {
+                                         int pitch_row, float4 &v, Acc3 (&acc)[F::NSUB][2 * F::R + 1]) {
   using t = TapAt<F, I>;
   if constexpr (t::fresh) v = base[t::b * pitch_sub + t::dy * pitch_row + t::dx];
-  float *o = acc[t::a][F::R - t::dz];
+  Acc3 &o = acc[t::a][F::R - t::dz];
   if constexpr (t::tensor) {
     const float *J = p.Jt[t::coef];
-    o[0] = fmaf(J[0], v.x, fmaf(J[1], v.y, fmaf(J[2], v.z, o[0])));
-    o[1] = fmaf(J[3], v.x, fmaf(J[4], v.y, fmaf(J[5], v.z, o[1])));
-    o[2] = fmaf(J[6], v.x, fmaf(J[7], v.y, fmaf(J[8], v.z, o[2])));
+    o.xy = __ffma2_rn(make_float2(J[2], J[5]), make_float2(v.z, v.z), o.xy);
+    o.xy = __ffma2_rn(make_float2(J[1], J[4]), make_float2(v.y, v.y), o.xy);
+    o.xy = __ffma2_rn(make_float2(J[0], J[3]), make_float2(v.x, v.x), o.xy);
+    o.z = fmaf(J[6], v.x, fmaf(J[7], v.y, fmaf(J[8], v.z, o.z)));
   } else {
     const float J = p.Jiso[t::coef];
-    o[0] = fmaf(J, v.x, o[0]);
-    o[1] = fmaf(J, v.y, o[1]);
-    o[2] = fmaf(J, v.z, o[2]);
+    o.xy = __ffma2_rn(make_float2(J, J), make_float2(v.x, v.y), o.xy);
+    o.z = fmaf(J, v.z, o.z);
   }
 }
 
 template <class F, int... I>
 __device__ __forceinline__ void push_all(std::integer_sequence<int, I...>, const StencilArgs &p,
                                          const float4 *__restrict__ base, int pitch_sub, int pitch_row,
-                                         float (&acc)[F::NSUB][2 * F::R + 1][3]) {
+                                         Acc3 (&acc)[F::NSUB][2 * F::R + 1]) {
   float4 v;
   (tap_push<F, I>(p, base, pitch_sub, pitch_row, v, acc), ...);
 }
 
 template <class F>
-__device__ __forceinline__ void shift_acc(float (&acc)[F::NSUB][2 * F::R + 1][3]) {
+__device__ __forceinline__ void zero_acc(Acc3 (&acc)[F::NSUB][2 * F::R + 1]) {
+#pragma unroll
+  for (int a = 0; a < F::NSUB; ++a)
+#pragma unroll
+    for (int j = 0; j < 2 * F::R + 1; ++j) {
+      acc[a][j].xy = make_float2(0.0f, 0.0f);
+      acc[a][j].z = 0.0f;
+    }
+}
+
+template <class F>
+__device__ __forceinline__ void shift_acc(Acc3 (&acc)[F::NSUB][2 * F::R + 1]) {
 #pragma unroll
   for (int a = 0; a < F::NSUB; ++a) {
 #pragma unroll
-    for (int j = 0; j < 2 * F::R; ++j) {
-      acc[a][j][0] = acc[a][j + 1][0];
-      acc[a][j][1] = acc[a][j + 1][1];
-      acc[a][j][2] = acc[a][j + 1][2];
-    }
-    acc[a][2 * F::R][0] = acc[a][2 * F::R][1] = acc[a][2 * F::R][2] = 0.0f;
+    for (int j = 0; j < 2 * F::R; ++j) acc[a][j] = acc[a][j + 1];
+    acc[a][2 * F::R].xy = make_float2(0.0f, 0.0f);
+    acc[a][2 * F::R].z = 0.0f;
   }
 }
 
@@ -342,13 +358,10 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINB)
   unsigned okmask;
   load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(p, x0 - 2 * R, y0 - 2 * R, tid, off, okmask);
 
-  float accp[NS][2 * R + 1][3];
-  float accc[NS][2 * R + 1][3];
-#pragma unroll
-  for (int a = 0; a < NS; ++a)
-#pragma unroll
-    for (int j = 0; j < 2 * R + 1; ++j)
-      accp[a][j][0] = accp[a][j][1] = accp[a][j][2] = accc[a][j][0] = accc[a][j][1] = accc[a][j][2] = 0.0f;
+  Acc3 accp[NS][2 * R + 1];
+  Acc3 accc[NS][2 * R + 1];
+  zero_acc<F>(accp);
+  zero_acc<F>(accc);
 
   const int niter = tzc + 4 * R;
   issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, z0 - 2 * R, tid, off, okmask, stage);
@@ -393,7 +406,7 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINB)
         if (ok) {
           const float4 c4 = cen[a * g::LX * g::LY];
           const float s[3] = {c4.x, c4.y, c4.z};
-          float b[3] = {accp[a][0][0], accp[a][0][1], accp[a][0][2]};
+          float b[3] = {accp[a][0].xy.x, accp[a][0].xy.y, accp[a][0].z};
           onsite32(p, a, s, b);
           float e0 = 0.f, e1 = 0.f, e2 = 0.f;
           if (p.thermal) {
@@ -438,7 +451,7 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINB)
         for (int a = 0; a < NS; ++a) {
           const float4 c4 = cen[a * 32 * F::BY];
           const float s[3] = {c4.x, c4.y, c4.z};
-          float b[3] = {accc[a][0][0], accc[a][0][1], accc[a][0][2]};
+          float b[3] = {accc[a][0].xy.x, accc[a][0].xy.y, accc[a][0].z};
           onsite32(p, a, s, b);
           const float *fa = fi + a * 6 * g::NI;
           const float sg = p.sigma[a], im = p.inv_mm[a];
@@ -547,11 +560,8 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
   const int cx = x0 + tx, cy = y0 + ty;
   const bool mine = cx < p.nx && cy < p.ny;
   const long long plane = (long long)p.ny * p.nx, subvol = (long long)p.nz * plane;
-  float acc[NS][2 * R + 1][3];
-#pragma unroll
-  for (int a = 0; a < NS; ++a)
-#pragma unroll
-    for (int j = 0; j < 2 * R + 1; ++j) acc[a][j][0] = acc[a][j][1] = acc[a][j][2] = 0.0f;
+  Acc3 acc[NS][2 * R + 1];
+  zero_acc<F>(acc);
   long long off[g::NLOAD];
   unsigned okmask;
   load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(p, x0 - R, y0 - R, tid, off, okmask);
@@ -606,7 +616,7 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
       const int c = z0 + kc;
 #pragma unroll
       for (int a = 0; a < NS; ++a) {
-        float v[3] = {acc[a][0][0], acc[a][0][1], acc[a][0][2]};
+        float v[3] = {acc[a][0].xy.x, acc[a][0].xy.y, acc[a][0].z};
         const float4 c4 = cq[(((k - R) % (R + 1)) * NS + a) * g::NT + tid];
         const float s[3] = {c4.x, c4.y, c4.z};
         const long long i = a * subvol + c * plane + (long long)cy * p.nx + cx;
