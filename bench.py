@@ -134,7 +134,7 @@ def cpu_oracle_rate(wl, budget_s=15.0, cells=None, steps=None, seed=7):
     from workloads import WORKLOADS as W, random_spins
     from oracle.models import oracle_model
     w = W[wl["name"]]
-    ncell = cells or min(32, wl["n"][0])
+    ncell = cells or min(64, wl["n"][0])
     n = (ncell, ncell, ncell)
     m, _ = oracle_model(wl["name"], n)
     S = random_spins(len(w["pos"]), n, seed)
@@ -142,7 +142,7 @@ def cpu_oracle_rate(wl, budget_s=15.0, cells=None, steps=None, seed=7):
     t0 = time.perf_counter()
     S = m.heun(S, w["dt"], w["alpha"], T=T, seed=seed, step0=0, nsteps=1)
     one = time.perf_counter() - t0
-    k = steps or max(1, min(200, int(budget_s / max(one, 1e-6))))
+    k = steps or max(1, min(10000, int(budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
     m.heun(S, w["dt"], w["alpha"], T=T, seed=seed, step0=1, nsteps=k)
     dt = time.perf_counter() - t0
