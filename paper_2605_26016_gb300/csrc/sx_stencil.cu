@@ -26,8 +26,10 @@
 //    the FP64 pipe only runs the normalisation).
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <utility>
+#include <vector>
 
 #include "sx_device.cuh"
 #include "sx_internal.h"
@@ -154,6 +156,8 @@ struct StencilPlan {
   float *d_St;      // two-pass workspace: S~ (3 nsite floats)
   float *d_f0;      // two-pass workspace: f0 (3 nsite floats)
   float *d_eta;     // two-pass workspace: thermal normals (3 nsite floats)
+  int2 *d_sched;    // balanced schedule of the two-pass kernels (nsched CTAs)
+  int nsched;
   StencilArgs base;
 };
 
@@ -512,6 +516,8 @@ struct PassIO {
   double *Sout;      // CORR: S^{n+1}
   int nzc;           // z chunks per image (blockIdx.z = image * nzc + chunk)
   long long istride; // doubles between images (FIELD)
+  const int2 *sched; // balanced schedule (one image): CTA k owns column-plane units
+                     // [sched[k].x, sched[k].x + sched[k].y) of u = column * nz + z; null: the grid tiles
 };
 
 // FP32 planes of S~ straight into the float4 ring (4-byte zero-filling copies)
@@ -541,22 +547,20 @@ __device__ __forceinline__ void issue_plane_f32(const StencilArgs &p, const floa
   }
 }
 
+// One segment: the output columns of the 32 x BY tile at (x0, y0), planes z0 .. z0 + tzc - 1,
+// of image img.
 template <int FID, int MODE>
-__global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
-    k_stencil_pass(const StencilArgs p, int onsite, const PassIO io) {
+__device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, const PassIO &io,
+                                             unsigned char *smem_raw, int img, int x0, int y0, int z0, int tzc) {
   using F = Family<FID>;
   using g = GF<F>;
   constexpr int NS = F::NSUB, R = F::R;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *sn = reinterpret_cast<float4 *>(smem_raw);                    // [2][SN]
   float4 *cq = reinterpret_cast<float4 *>(smem_raw + g::OFF_CQ);        // [R+1][NS][NT] centre values
   double *stage = reinterpret_cast<double *>(smem_raw + g::OFF_STAGE);  // [3][SN] (FP64 input)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-  const int img = blockIdx.z / io.nzc, zc = blockIdx.z - img * io.nzc;
   const double *Sin = io.S + img * io.istride;
   double *bout = io.b + img * io.istride;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * F::BY, z0 = zc * p.tz;
-  const int tzc = min(p.tz, p.nz - z0);
   const int cx = x0 + tx, cy = y0 + ty;
   const bool mine = cx < p.nx && cy < p.ny;
   const long long plane = (long long)p.ny * p.nx, subvol = (long long)p.nz * plane;
@@ -673,6 +677,31 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
   cp_wait<0>();
 }
 
+template <int FID, int MODE>
+__global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
+    k_stencil_pass(const StencilArgs p, int onsite, const PassIO io) {
+  using F = Family<FID>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (io.sched) {
+    const int2 e = io.sched[blockIdx.x];
+    const int ncx = (p.nx + 31) / 32;
+    long long u = e.x;
+    const long long uend = (long long)e.x + e.y;
+    while (u < uend) {  // uniform over the block
+      const int col = (int)(u / p.nz), z = (int)(u - (long long)col * p.nz);
+      const int len = (int)min((long long)(p.nz - z), uend - u);
+      pass_segment<FID, MODE>(p, onsite, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+      u += len;
+      __syncthreads();  // shared memory is reused by the next segment
+    }
+  } else {
+    const int img = blockIdx.z / io.nzc, zc = blockIdx.z - img * io.nzc;
+    const int z0 = zc * p.tz;
+    pass_segment<FID, MODE>(p, onsite, io, smem_raw, img, blockIdx.x * 32, blockIdx.y * F::BY, z0,
+                            min(p.tz, p.nz - z0));
+  }
+}
+
 // ------------------------------------------------------------------ planning
 
 namespace {
@@ -783,12 +812,53 @@ cudaError_t launch_heun2(const StencilPlan &sp, StencilArgs a, const double *src
   io.f0 = sp.d_f0;
   io.eta = sp.d_eta;
   io.Sout = dst;
-  io.nzc = (a.nz + a.tz - 1) / a.tz;
   io.b = nullptr;
-  const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc);
+  io.sched = sp.d_sched;
+  io.nzc = (a.nz + a.tz - 1) / a.tz;
+  const dim3 grid = sp.d_sched ? dim3(sp.nsched)
+                               : dim3((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc);
   k_stencil_pass<FID, PASS_PRED><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, 1, io);
   k_stencil_pass<FID, PASS_CORR><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, 1, io);
   return cudaGetLastError();
+}
+
+// Balanced schedule of a one-image pass over `slots` resident CTAs: the column-plane
+// units u = column * nz + z are cut into contiguous ranges, one per CTA, so that the
+// largest cost (planes + 2R warm-up planes per column segment) is as small as the
+// greedy packing allows.
+std::vector<int2> balanced_schedule(long long ncol, int nz, int R, long long slots) {
+  const long long U = ncol * nz, w = 2LL * R;
+  auto pack = [&](long long B, std::vector<int2> *out) {
+    long long u = 0, n = 0;
+    while (u < U) {
+      const long long u0 = u;
+      long long cost = 0;
+      while (u < U) {
+        const long long avail = nz - u % nz;
+        if (cost + w + 1 > B) break;
+        const long long t = std::min(avail, B - cost - w);
+        cost += w + t;
+        u += t;
+        if (t < avail) break;
+      }
+      if (out) out->push_back(make_int2((int)u0, (int)(u - u0)));
+      ++n;
+    }
+    return n;
+  };
+  // hi: whole columns, ceil(ncol / slots) of them per CTA, always fits
+  long long lo = std::max<long long>(w + 1, (U + slots - 1) / slots + w);
+  long long hi = std::max(lo, ((ncol + slots - 1) / slots) * (nz + w));
+  while (lo < hi) {
+    const long long mid = (lo + hi) / 2;
+    if (pack(mid, nullptr) <= slots)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  std::vector<int2> out;
+  pack(lo, &out);
+  return out;
 }
 
 // z chunk per CTA: each chunk pays 4R warm-up planes, and the grid runs in
@@ -909,6 +979,29 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC26_TEN: sp->tz2 = field_tz<FAM_SC26_TEN>(*sp, a, 1); break;
     default: sp->tz2 = field_tz<FAM_BCC4>(*sp, a, 1); break;
   }
+  {
+    // every family uses 32-wide tiles; R and BY per family
+    const int R = fam == FAM_BCC4 ? Family<FAM_BCC4>::R : Family<FAM_SC6_ISO>::R;
+    const int BY = fam == FAM_BCC4 ? Family<FAM_BCC4>::BY : Family<FAM_SC6_ISO>::BY;
+    const long long ncol = (long long)((a.nx + 31) / 32) * ((a.ny + BY - 1) / BY);
+    // Only when the columns are fewer than the resident CTA slots: then the z-chunked grid
+    // leaves SMs idle (e.g. 128 CTAs for 152 SMs) and the balanced schedule fills them.
+    // With many columns the hardware's dynamic CTA scheduling balances equal columns
+    // well and keeps neighbouring columns (which share halo planes) concurrent in L2.
+    const long long slots = (long long)sp->nsm * sp->occ_field;
+    std::vector<int2> sch;
+    if (ncol < slots && ncol * a.nz < (1LL << 31)) sch = balanced_schedule(ncol, a.nz, R, slots);
+    sp->nsched = (int)sch.size();
+    if (sch.empty()) {
+      sp->d_sched = nullptr;
+    } else if (cudaMalloc(&sp->d_sched, sch.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMemcpy(sp->d_sched, sch.data(), sch.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(sp->d_sched);
+      delete sp;
+      return set_error(SX_ERR_OOM, "stencil schedule: device allocation failed");
+    }
+  }
   c->stencil = sp;
   const int rc = stencil_set_scheme(c, c->opt_scheme);
   if (rc != SX_OK) {
@@ -952,6 +1045,7 @@ void stencil_free(sx_ctx *c) {
     cudaFree(c->stencil->d_St);
     cudaFree(c->stencil->d_f0);
     cudaFree(c->stencil->d_eta);
+    cudaFree(c->stencil->d_sched);
   }
   delete c->stencil;
   c->stencil = nullptr;

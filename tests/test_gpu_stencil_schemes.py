@@ -26,6 +26,10 @@ CASES = [
     ("sc_j123", (70, 40, 25), (0, 1, 1)),
     ("sc_nn", (33, 5, 7), (1, 1, 1)),
     ("sc_nn", (64, 48, 40), (0, 0, 0)),
+    # more tile columns than resident CTAs: the two-pass kernels run on the z-chunked grid
+    # instead of the balanced column-plane schedule
+    ("sc_j123_dmi", (640, 256, 6), (1, 1, 1)),
+    ("bcc_4shell", (512, 256, 5), (1, 1, 1)),
 ]
 
 
