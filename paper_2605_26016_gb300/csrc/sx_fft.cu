@@ -70,9 +70,100 @@ __device__ __forceinline__ C cmul(C a, C b) {
   return r;
 }
 
+// a <- a + w b, b <- a - w b
+template <typename C>
+__device__ __forceinline__ void bfly(C &a, C &b, const C &w) {
+  const C t = cmul(b, w);
+  b.x = a.x - t.x;
+  b.y = a.y - t.y;
+  a.x += t.x;
+  a.y += t.y;
+}
+
+// w times -i (forward) or +i (inverse)
+template <typename C>
+__device__ __forceinline__ C rot_quarter(C w, int inverse) {
+  C r;
+  if (inverse) {
+    r.x = -w.y;
+    r.y = w.x;
+  } else {
+    r.x = w.y;
+    r.y = -w.x;
+  }
+  return r;
+}
+
+// w times exp(-i pi/4) (forward) or exp(+i pi/4) (inverse)
+template <typename C, typename R>
+__device__ __forceinline__ C rot_eighth(C w, int inverse) {
+  const R h = (R)0.70710678118654752440;
+  C r;
+  if (inverse) {
+    r.x = h * (w.x - w.y);
+    r.y = h * (w.x + w.y);
+  } else {
+    r.x = h * (w.x + w.y);
+    r.y = h * (w.y - w.x);
+  }
+  return r;
+}
+
+// LR consecutive radix-2 decimation-in-time stages s .. s + LR - 1 in registers.  Stage s
+// pairs elements h = 2^s apart with twiddle w_{2h}^k; the 2^LR elements i0 + m h
+// (i0 = block * 2^LR h + k) only meet each other in these stages, so one thread
+// takes them through all LR stages and writes them back in place: stage s+1 uses
+// w_{4h}^{k + (m&1) h} = w_{4h}^k (-i)^(m&1), stage s+2 w_{8h}^{k + m h} = w_{8h}^k w_8^m.
+template <typename R, int LR>
+__device__ __forceinline__ void dit_stages(typename CxT<R>::T *sm, int pitch, int W, int logn, int s,
+                                           const typename CxT<R>::T *__restrict__ tw, int inverse) {
+  using C = typename CxT<R>::T;
+  constexpr int RAD = 1 << LR;
+  const int h = 1 << s;
+  const int logng = logn - LR;
+  const int total = W << logng;
+  for (int t = threadIdx.x; t < total; t += kFftThreads) {
+    const int w = t >> logng, j = t & ((1 << logng) - 1);
+    const int k = j & (h - 1);
+    C *line = sm + w * pitch + ((j >> s) << (s + LR)) + k;
+    C v[RAD];
+#pragma unroll
+    for (int m = 0; m < RAD; ++m) v[m] = line[m * h];
+    C t1 = tw[k << (logn - 1 - s)];
+    if (inverse) t1.y = -t1.y;
+#pragma unroll
+    for (int m = 0; m < RAD; m += 2) bfly(v[m], v[m + 1], t1);
+    if constexpr (LR >= 2) {
+      C t2 = tw[k << (logn - 2 - s)];
+      if (inverse) t2.y = -t2.y;
+      const C t2b = rot_quarter(t2, inverse);
+#pragma unroll
+      for (int m = 0; m < RAD; m += 4) {
+        bfly(v[m], v[m + 2], t2);
+        bfly(v[m + 1], v[m + 3], t2b);
+      }
+    }
+    if constexpr (LR >= 3) {
+      C t3 = tw[k << (logn - 3 - s)];
+      if (inverse) t3.y = -t3.y;
+      const C t31 = rot_eighth<C, R>(t3, inverse);
+      const C t32 = rot_quarter(t3, inverse);
+      const C t33 = rot_eighth<C, R>(t32, inverse);
+      bfly(v[0], v[4], t3);
+      bfly(v[1], v[5], t31);
+      bfly(v[2], v[6], t32);
+      bfly(v[3], v[7], t33);
+    }
+#pragma unroll
+    for (int m = 0; m < RAD; ++m) line[m * h] = v[m];
+  }
+}
+
 // One 1D pass over every line of one axis.  Line group g (W lines, adjacent
 // along the grouping axis, stride gs), outer line index o (stride os), element
-// i along the transform axis (stride is); blockIdx.z selects the field.
+// i along the transform axis (stride is); blockIdx.z selects the field.  The
+// lines are staged bit-reversed in shared memory and transformed in place by
+// radix-2 DIT stages taken three (then two, then one) at a time in registers.
 template <typename R>
 __global__ void __launch_bounds__(kFftThreads)
     k_fft_pass(typename CxT<R>::T *__restrict__ data, int n, int logn, int W, int ifast, long long gs, long long os,
@@ -97,24 +188,17 @@ __global__ void __launch_bounds__(kFftThreads)
     sm[w * pitch + r] = base[w * gs + i * is];
   }
   __syncthreads();
-  const int nh = n >> 1;
-  for (int s = 0; s < logn; ++s) {
-    const int half = 1 << s;
-    for (int t = threadIdx.x; t < W * nh; t += kFftThreads) {
-      const int w = t >> (logn - 1), j = t & (nh - 1);
-      const int k = j & (half - 1);
-      const int i0 = ((j >> s) << (s + 1)) + k, i1 = i0 + half;
-      C f = tw[k << (logn - 1 - s)];
-      if (inverse) f.y = -f.y;
-      const C a = sm[w * pitch + i0];
-      const C b = cmul(sm[w * pitch + i1], f);
-      C u, v;
-      u.x = a.x + b.x;
-      u.y = a.y + b.y;
-      v.x = a.x - b.x;
-      v.y = a.y - b.y;
-      sm[w * pitch + i0] = u;
-      sm[w * pitch + i1] = v;
+  for (int s = 0; s < logn;) {
+    const int rem = logn - s;
+    if (rem >= 3) {
+      dit_stages<R, 3>(sm, pitch, W, logn, s, tw, inverse);
+      s += 3;
+    } else if (rem == 2) {
+      dit_stages<R, 2>(sm, pitch, W, logn, s, tw, inverse);
+      s += 2;
+    } else {
+      dit_stages<R, 1>(sm, pitch, W, logn, s, tw, inverse);
+      s += 1;
     }
     __syncthreads();
   }
