@@ -55,6 +55,7 @@ struct FftPlan {
   void *Mo;      // [noff][N] complex: upper triangle of M(q)
   void *tw[3];   // per axis: n/2 complex twiddles exp(-2 pi i k / n)
   void *St, *F0, *Bf;  // Heun: predictor state, f0, field buffer; [nch][N] real each
+  void *Th;            // Heun: thermal field of the step, [nch][N] real
 };
 
 namespace {
@@ -69,6 +70,13 @@ __device__ __forceinline__ C cmul(C a, C b) {
   r.y = a.x * b.y + a.y * b.x;
   return r;
 }
+
+// Shared-memory slot of element i of a staged line: one padding slot after every
+// eight elements, so that the strided element patterns of the early fused stages
+// and the bit-reversed staging spread over the banks.  The line pitch
+// fft_pitch(n) is odd, so equal elements of adjacent lines fall in different banks.
+__host__ __device__ __forceinline__ int fft_slot(int i) { return i + (i >> 3); }
+__host__ __device__ __forceinline__ int fft_pitch(int n) { return n + (n >> 3) + 1; }
 
 // a <- a + w b, b <- a - w b
 template <typename C>
@@ -125,10 +133,11 @@ __device__ __forceinline__ void dit_stages(typename CxT<R>::T *sm, int pitch, in
   for (int t = threadIdx.x; t < total; t += kFftThreads) {
     const int w = t >> logng, j = t & ((1 << logng) - 1);
     const int k = j & (h - 1);
-    C *line = sm + w * pitch + ((j >> s) << (s + LR)) + k;
+    C *line = sm + w * pitch;
+    const int i0 = ((j >> s) << (s + LR)) + k;
     C v[RAD];
 #pragma unroll
-    for (int m = 0; m < RAD; ++m) v[m] = line[m * h];
+    for (int m = 0; m < RAD; ++m) v[m] = line[fft_slot(i0 + m * h)];
     C t1 = tw[k << (logn - 1 - s)];
     if (inverse) t1.y = -t1.y;
 #pragma unroll
@@ -155,7 +164,7 @@ __device__ __forceinline__ void dit_stages(typename CxT<R>::T *sm, int pitch, in
       bfly(v[3], v[7], t33);
     }
 #pragma unroll
-    for (int m = 0; m < RAD; ++m) line[m * h] = v[m];
+    for (int m = 0; m < RAD; ++m) line[fft_slot(i0 + m * h)] = v[m];
   }
 }
 
@@ -171,7 +180,7 @@ __global__ void __launch_bounds__(kFftThreads)
   using C = typename CxT<R>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
   C *sm = reinterpret_cast<C *>(smraw);
-  const int pitch = n + 1;
+  const int pitch = fft_pitch(n);
   C *base = data + blockIdx.z * fstride + (long long)blockIdx.x * W * gs + (long long)blockIdx.y * os;
   const int total = W * n;
   const int logw = 31 - __clz(W);  // W and n are powers of two
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__(kFftThreads)
       w = e & (W - 1);
     }
     const int r = (int)(__brev((unsigned)i) >> (32 - logn));
-    sm[w * pitch + r] = base[w * gs + i * is];
+    sm[w * pitch + fft_slot(r)] = base[w * gs + i * is];
   }
   __syncthreads();
   for (int s = 0; s < logn;) {
@@ -211,8 +220,65 @@ __global__ void __launch_bounds__(kFftThreads)
       i = e >> logw;
       w = e & (W - 1);
     }
-    base[w * gs + i * is] = sm[w * pitch + i];
+    base[w * gs + i * is] = sm[w * pitch + fft_slot(i)];
   }
+}
+
+// Conversions between the state (FP64) and the arithmetic type without the FP64
+// conversion pipe (integer bit operations, see sx_device.cuh).
+template <typename To, typename From>
+__device__ __forceinline__ To cvt(From v) {
+  if constexpr (sizeof(To) == sizeof(From))
+    return v;
+  else if constexpr (sizeof(To) == 4)
+    return f64_to_f32(v);
+  else
+    return f32_to_f64(v);
+}
+
+// On-site and Heun constants in the arithmetic type R, converted once on the host.
+template <typename R>
+struct OnSiteT {
+  R zee[SX_MAX_SUB][3];
+  R twoK[SX_MAX_SUB];
+  R axis[SX_MAX_SUB][3];
+  R inv_mm[SX_MAX_SUB];
+};
+template <typename R>
+struct HeunT {
+  R dt, hdt, g, alpha;
+  R sigma[SX_MAX_SUB];
+  uint64_t seed;
+  uint32_t replica;
+  int thermal;
+};
+
+template <typename R>
+OnSiteT<R> onsite_cast(const OnSite &o) {
+  OnSiteT<R> r;
+  for (int a = 0; a < SX_MAX_SUB; ++a) {
+    for (int c = 0; c < 3; ++c) {
+      r.zee[a][c] = (R)o.zee[a][c];
+      r.axis[a][c] = (R)o.axis[a][c];
+    }
+    r.twoK[a] = (R)o.twoK[a];
+    r.inv_mm[a] = (R)o.inv_mm[a];
+  }
+  return r;
+}
+
+template <typename R>
+HeunT<R> heun_cast(const HeunConst &h) {
+  HeunT<R> r;
+  r.dt = (R)h.dt;
+  r.hdt = (R)(0.5 * h.dt);
+  r.g = (R)h.g;
+  r.alpha = (R)h.alpha;
+  for (int a = 0; a < SX_MAX_SUB; ++a) r.sigma[a] = (R)h.sigma[a];
+  r.seed = h.seed;
+  r.replica = h.replica;
+  r.thermal = h.thermal;
+  return r;
 }
 
 // real channels [nch][N] -> packed complex fields [nzf][N]
@@ -223,8 +289,8 @@ __global__ void k_pack(const Tin *__restrict__ S, typename CxT<R>::T *__restrict
   const int nzf = (nch + 1) / 2;
   for (int m = 0; m < nzf; ++m) {
     typename CxT<R>::T z;
-    z.x = (R)S[(long long)(2 * m) * N + i];
-    z.y = (2 * m + 1 < nch) ? (R)S[(long long)(2 * m + 1) * N + i] : (R)0;
+    z.x = cvt<R>(S[(long long)(2 * m) * N + i]);
+    z.y = (2 * m + 1 < nch) ? cvt<R>(S[(long long)(2 * m + 1) * N + i]) : (R)0;
     Z[m * N + i] = z;
   }
 }
@@ -299,7 +365,7 @@ __global__ void k_kmul(typename CxT<R>::T *__restrict__ Z, const R *__restrict__
 // packed fields -> real channels times scale, plus Zeeman and anisotropy when onsite
 template <typename R, typename Tout, typename Tspin>
 __global__ void k_unpack(const typename CxT<R>::T *__restrict__ Z, Tout *__restrict__ b, int nsub, long long N,
-                         R scale, const Tspin *__restrict__ S, OnSite os, int onsite) {
+                         R scale, const Tspin *__restrict__ S, OnSiteT<R> os, int onsite) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int nch = 3 * nsub;
@@ -311,22 +377,22 @@ __global__ void k_unpack(const typename CxT<R>::T *__restrict__ Z, Tout *__restr
   }
   if (onsite) {
     for (int a = 0; a < nsub; ++a) {
-      const R s0 = (R)S[(long long)(0 * nsub + a) * N + i], s1 = (R)S[(long long)(1 * nsub + a) * N + i],
-              s2 = (R)S[(long long)(2 * nsub + a) * N + i];
-      const R p = (R)os.twoK[a] * (s0 * (R)os.axis[a][0] + s1 * (R)os.axis[a][1] + s2 * (R)os.axis[a][2]);
-      for (int c = 0; c < 3; ++c) v[c * nsub + a] += (R)os.zee[a][c] + p * (R)os.axis[a][c];
+      const R s0 = cvt<R>(S[(long long)(0 * nsub + a) * N + i]), s1 = cvt<R>(S[(long long)(1 * nsub + a) * N + i]),
+              s2 = cvt<R>(S[(long long)(2 * nsub + a) * N + i]);
+      const R p = os.twoK[a] * (s0 * os.axis[a][0] + s1 * os.axis[a][1] + s2 * os.axis[a][2]);
+      for (int c = 0; c < 3; ++c) v[c * nsub + a] += os.zee[a][c] + p * os.axis[a][c];
     }
   }
-  for (int k = 0; k < nch; ++k) b[(long long)k * N + i] = (Tout)v[k];
+  for (int k = 0; k < nch; ++k) b[(long long)k * N + i] = cvt<Tout>(v[k]);
 }
 
 // ---------------------------------------------------------------- Heun
 
 template <typename R>
-__device__ __forceinline__ void onsite_t(const OnSite &os, int a, const R s[3], R b[3]) {
-  const R p = (R)os.twoK[a] * (s[0] * (R)os.axis[a][0] + s[1] * (R)os.axis[a][1] + s[2] * (R)os.axis[a][2]);
+__device__ __forceinline__ void onsite_t(const OnSiteT<R> &os, int a, const R s[3], R b[3]) {
+  const R p = os.twoK[a] * (s[0] * os.axis[a][0] + s[1] * os.axis[a][1] + s[2] * os.axis[a][2]);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) b[c] += (R)os.zee[a][c] + p * (R)os.axis[a][c];
+  for (int c = 0; c < 3; ++c) b[c] += os.zee[a][c] + p * os.axis[a][c];
 }
 
 __device__ __forceinline__ void unit_t(float x[3]) {
@@ -345,36 +411,40 @@ __device__ __forceinline__ void unit_t(double x[3]) {
 }
 
 template <typename R>
-__device__ __forceinline__ void thermal_t(const HeunConst &h, int a, long long site, uint64_t step, R th[3]) {
+__device__ __forceinline__ void thermal_t(const HeunT<R> &h, int a, long long site, uint64_t step, R th[3]) {
   th[0] = th[1] = th[2] = (R)0;
   if (h.thermal) {
     float e0, e1, e2;
     normals3(h.seed, h.replica, (uint64_t)site, step, e0, e1, e2);
-    const R sg = (R)h.sigma[a];
-    th[0] = sg * (R)e0;
-    th[1] = sg * (R)e1;
-    th[2] = sg * (R)e2;
+    const R sg = h.sigma[a];
+    th[0] = sg * cvt<R>(e0);
+    th[1] = sg * cvt<R>(e1);
+    th[2] = sg * cvt<R>(e2);
   }
 }
 
 // predictor from the bilinear+dipolar field Bf of S (on-site terms added here)
+// (a thermal step also stores the thermal field sigma eta in Th for the corrector)
 template <typename R>
 __global__ void k_fft_predict(const double *__restrict__ S, const R *__restrict__ Bf, R *__restrict__ St,
-                              R *__restrict__ F0, int nsub, long long N, OnSite os, HeunConst h, uint64_t step) {
+                              R *__restrict__ F0, R *__restrict__ Th, int nsub, long long N, OnSiteT<R> os,
+                              HeunT<R> h, uint64_t step) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   for (int a = 0; a < nsub; ++a) {
     R s[3], b[3], th[3], f[3];
     for (int c = 0; c < 3; ++c) {
-      s[c] = (R)S[(long long)(c * nsub + a) * N + i];
+      s[c] = cvt<R>(S[(long long)(c * nsub + a) * N + i]);
       b[c] = Bf[(long long)(c * nsub + a) * N + i];
     }
     onsite_t<R>(os, a, s, b);
     thermal_t<R>(h, a, (long long)a * N + i, step, th);
-    const R im = (R)os.inv_mm[a];
+    if (h.thermal)
+      for (int c = 0; c < 3; ++c) Th[(long long)(c * nsub + a) * N + i] = th[c];
+    const R im = os.inv_mm[a];
     const R B[3] = {b[0] * im + th[0], b[1] * im + th[1], b[2] * im + th[2]};
-    llg_rhs_t<R>(s, B, (R)h.g, (R)h.alpha, f);
-    R x[3] = {s[0] + (R)h.dt * f[0], s[1] + (R)h.dt * f[1], s[2] + (R)h.dt * f[2]};
+    llg_rhs_t<R>(s, B, h.g, h.alpha, f);
+    R x[3] = {s[0] + h.dt * f[0], s[1] + h.dt * f[1], s[2] + h.dt * f[2]};
     unit_t(x);
     for (int c = 0; c < 3; ++c) {
       St[(long long)(c * nsub + a) * N + i] = x[c];
@@ -396,8 +466,8 @@ __device__ __forceinline__ void correct_state(const double S[3], const double d[
 
 template <typename R>
 __global__ void k_fft_correct(const double *__restrict__ S, const R *__restrict__ St, const R *__restrict__ F0,
-                              const R *__restrict__ Bf, double *__restrict__ Snew, int nsub, long long N, OnSite os,
-                              HeunConst h, uint64_t step) {
+                              const R *__restrict__ Bf, const R *__restrict__ Th, double *__restrict__ Snew, int nsub,
+                              long long N, OnSiteT<R> os, HeunT<R> h) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   for (int a = 0; a < nsub; ++a) {
@@ -410,11 +480,11 @@ __global__ void k_fft_correct(const double *__restrict__ S, const R *__restrict_
       s64[c] = S[k];
     }
     onsite_t<R>(os, a, s, b);
-    thermal_t<R>(h, a, (long long)a * N + i, step, th);
-    const R im = (R)os.inv_mm[a];
+    for (int c = 0; c < 3; ++c) th[c] = h.thermal ? Th[(long long)(c * nsub + a) * N + i] : (R)0;
+    const R im = os.inv_mm[a];
     const R B[3] = {b[0] * im + th[0], b[1] * im + th[1], b[2] * im + th[2]};
-    llg_rhs_t<R>(s, B, (R)h.g, (R)h.alpha, f);
-    const R hdt = (R)(0.5 * h.dt);
+    llg_rhs_t<R>(s, B, h.g, h.alpha, f);
+    const R hdt = h.hdt;
     for (int c = 0; c < 3; ++c) d[c] = hdt * (F0[(long long)(c * nsub + a) * N + i] + f[c]);
     correct_state(s64, d, o);
     for (int c = 0; c < 3; ++c) Snew[(long long)(c * nsub + a) * N + i] = o[c];
@@ -517,7 +587,7 @@ template <typename R>
 int pick_w(int n, int extent) {
   const size_t csz = sizeof(typename CxT<R>::T);
   int w = 16;
-  while (w > 1 && ((size_t)w * (n + 1) * csz > kFftSmem || w > extent)) w >>= 1;
+  while (w > 1 && ((size_t)w * fft_pitch(n) * csz > kFftSmem || w > extent)) w >>= 1;
   return w;
 }
 
@@ -557,7 +627,7 @@ cudaError_t fft3d(const FftPlan &fp, typename CxT<R>::T *Z, int nfields, const v
       is = (long long)nx * ny;
       ifast = 0;
     }
-    const size_t smem = (size_t)W * (n + 1) * sizeof(C);
+    const size_t smem = (size_t)W * fft_pitch(n) * sizeof(C);
     k_fft_pass<R><<<grid, kFftThreads, smem, st>>>(Z, n, fp.logn[ax], W, ifast, gs, os, is, N,
                                                    static_cast<const C *>(tw[ax]), inverse);
     cudaError_t e = cudaGetLastError();
@@ -593,7 +663,7 @@ cudaError_t field_pipeline(const sx_ctx *c, const Tin *in, Tout *out, bool onsit
   if (e == cudaSuccess) e = fft3d<R>(fp, Z, fp.nzf, fp.tw, 1, st);
   if (e != cudaSuccess) return e;
   k_unpack<R, Tout, Tin><<<blocks_for(fp.N, 256), 256, 0, st>>>(Z, out, fp.nsub, fp.N, (R)(1.0 / (double)fp.N), in,
-                                                                c->onsite, onsite ? 1 : 0);
+                                                                onsite_cast<R>(c->onsite), onsite ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -602,13 +672,16 @@ cudaError_t heun_pipeline(const sx_ctx *c, const double *src, double *dst, const
                           cudaStream_t st) {
   const FftPlan &fp = *c->fft;
   R *St = static_cast<R *>(fp.St), *F0 = static_cast<R *>(fp.F0), *Bf = static_cast<R *>(fp.Bf);
+  R *Th = static_cast<R *>(fp.Th);
   cudaError_t e = field_pipeline<R, double, R>(c, src, Bf, false, st);
   if (e != cudaSuccess) return e;
-  k_fft_predict<R><<<blocks_for(fp.N, 256), 256, 0, st>>>(src, Bf, St, F0, fp.nsub, fp.N, c->onsite, h, step);
+  k_fft_predict<R><<<blocks_for(fp.N, 256), 256, 0, st>>>(src, Bf, St, F0, Th, fp.nsub, fp.N, onsite_cast<R>(c->onsite),
+                                                          heun_cast<R>(h), step);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   e = field_pipeline<R, R, R>(c, St, Bf, false, st);
   if (e != cudaSuccess) return e;
-  k_fft_correct<R><<<blocks_for(fp.N, 256), 256, 0, st>>>(src, St, F0, Bf, dst, fp.nsub, fp.N, c->onsite, h, step);
+  k_fft_correct<R><<<blocks_for(fp.N, 256), 256, 0, st>>>(src, St, F0, Bf, Th, dst, fp.nsub, fp.N,
+                                                          onsite_cast<R>(c->onsite), heun_cast<R>(h));
   return cudaGetLastError();
 }
 
@@ -701,6 +774,7 @@ cudaError_t alloc_plan(FftPlan &fp) {
   if (e == cudaSuccess) e = cudaMalloc(&fp.St, (size_t)fp.nch * N * sizeof(R));
   if (e == cudaSuccess) e = cudaMalloc(&fp.F0, (size_t)fp.nch * N * sizeof(R));
   if (e == cudaSuccess) e = cudaMalloc(&fp.Bf, (size_t)fp.nch * N * sizeof(R));
+  if (e == cudaSuccess) e = cudaMalloc(&fp.Th, (size_t)fp.nch * N * sizeof(R));
   if (e == cudaSuccess) e = alloc_twiddles<R>(fp, fp.tw);
   if (e == cudaSuccess) e = set_fft_smem<R>();
   return e;
@@ -717,6 +791,7 @@ void fft_free(sx_ctx *c) {
   cudaFree(fp->St);
   cudaFree(fp->F0);
   cudaFree(fp->Bf);
+  cudaFree(fp->Th);
   for (int k = 0; k < 3; ++k) cudaFree(fp->tw[k]);
   delete fp;
   c->fft = nullptr;
@@ -757,17 +832,19 @@ int fft_plan(sx_ctx *c) {
 }
 
 // Heun stages that take the bilinear field from a buffer (also used by the tensor-core backend)
-cudaError_t bufheun_predict(const sx_ctx *c, const double *S, const float *Bf, float *St, float *F0,
+cudaError_t bufheun_predict(const sx_ctx *c, const double *S, const float *Bf, float *St, float *F0, float *Th,
                             const HeunConst &h, uint64_t step, cudaStream_t st) {
   const long long N = c->geo.ncell;
-  k_fft_predict<float><<<blocks_for(N, 256), 256, 0, st>>>(S, Bf, St, F0, c->lat.nsub, N, c->onsite, h, step);
+  k_fft_predict<float><<<blocks_for(N, 256), 256, 0, st>>>(S, Bf, St, F0, Th, c->lat.nsub, N,
+                                                           onsite_cast<float>(c->onsite), heun_cast<float>(h), step);
   return cudaGetLastError();
 }
 
 cudaError_t bufheun_correct(const sx_ctx *c, const double *S, const float *St, const float *F0, const float *Bf,
-                            double *Snew, const HeunConst &h, uint64_t step, cudaStream_t st) {
+                            const float *Th, double *Snew, const HeunConst &h, cudaStream_t st) {
   const long long N = c->geo.ncell;
-  k_fft_correct<float><<<blocks_for(N, 256), 256, 0, st>>>(S, St, F0, Bf, Snew, c->lat.nsub, N, c->onsite, h, step);
+  k_fft_correct<float><<<blocks_for(N, 256), 256, 0, st>>>(S, St, F0, Bf, Th, Snew, c->lat.nsub, N,
+                                                           onsite_cast<float>(c->onsite), heun_cast<float>(h));
   return cudaGetLastError();
 }
 

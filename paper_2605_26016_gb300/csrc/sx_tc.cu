@@ -40,10 +40,10 @@
 namespace sx {
 
 // buffer-based Heun stages shared with the FFT backend (sx_fft.cu)
-cudaError_t bufheun_predict(const sx_ctx *c, const double *S, const float *Bf, float *St, float *F0,
+cudaError_t bufheun_predict(const sx_ctx *c, const double *S, const float *Bf, float *St, float *F0, float *Th,
                             const HeunConst &h, uint64_t step, cudaStream_t st);
 cudaError_t bufheun_correct(const sx_ctx *c, const double *S, const float *St, const float *F0, const float *Bf,
-                            double *Snew, const HeunConst &h, uint64_t step, cudaStream_t st);
+                            const float *Th, double *Snew, const HeunConst &h, cudaStream_t st);
 
 constexpr int kTcM = 128;      // output x per CTA (MMA M)
 constexpr int kTcYB = 8;       // output y per CTA (one core-matrix row group)
@@ -68,6 +68,7 @@ struct TcPlan {
   int tf32;
   TcArgs base;
   float *St, *F0, *Bf;  // Heun workspaces [3][ncell]
+  float *Th;            // thermal field of the step [3][ncell]
   int *err;
 };
 
@@ -374,6 +375,7 @@ int tc_plan(sx_ctx *c) {
   cudaError_t e = cudaMalloc(&tp->St, n3 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&tp->F0, n3 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&tp->Bf, n3 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&tp->Th, n3 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&tp->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(tp->err, 0, sizeof(int));
   if (e == cudaSuccess) e = tp->tf32 ? set_tc_smem<true>() : set_tc_smem<false>();
@@ -393,6 +395,7 @@ void tc_free(sx_ctx *c) {
   cudaFree(tp->St);
   cudaFree(tp->F0);
   cudaFree(tp->Bf);
+  cudaFree(tp->Th);
   cudaFree(tp->err);
   delete tp;
   c->tc = nullptr;
@@ -411,11 +414,11 @@ cudaError_t tc_heun_step(const sx_ctx *c, const double *src, double *dst, const 
   a.onsite = 0;
   cudaError_t e = tp.tf32 ? launch_tc<true, double, float>(c, a, src, tp.Bf, st)
                           : launch_tc<false, double, float>(c, a, src, tp.Bf, st);
-  if (e == cudaSuccess) e = bufheun_predict(c, src, tp.Bf, tp.St, tp.F0, h, step, st);
+  if (e == cudaSuccess) e = bufheun_predict(c, src, tp.Bf, tp.St, tp.F0, tp.Th, h, step, st);
   if (e == cudaSuccess)
     e = tp.tf32 ? launch_tc<true, float, float>(c, a, tp.St, tp.Bf, st)
                 : launch_tc<false, float, float>(c, a, tp.St, tp.Bf, st);
-  if (e == cudaSuccess) e = bufheun_correct(c, src, tp.St, tp.F0, tp.Bf, dst, h, step, st);
+  if (e == cudaSuccess) e = bufheun_correct(c, src, tp.St, tp.F0, tp.Bf, tp.Th, dst, h, st);
   return e;
 }
 
