@@ -26,6 +26,18 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __hiloint2double((int)hi, (int)(b << 29));
 }
 
+// Conversion between FP64 and the arithmetic type R of a kernel through the
+// integer-bit helpers above (identity when the types agree).
+template <typename To, typename From>
+__device__ __forceinline__ To cvt(From v) {
+  if constexpr (sizeof(To) == sizeof(From))
+    return v;
+  else if constexpr (sizeof(To) == 4)
+    return f64_to_f32(v);
+  else
+    return f32_to_f64(v);
+}
+
 __device__ __forceinline__ int wrap_axis(int c, int n, int periodic, bool &ok) {
   if (c >= 0 && c < n) return c;
   if (!periodic) {

@@ -224,63 +224,6 @@ __global__ void __launch_bounds__(kFftThreads)
   }
 }
 
-// Conversions between the state (FP64) and the arithmetic type without the FP64
-// conversion pipe (integer bit operations, see sx_device.cuh).
-template <typename To, typename From>
-__device__ __forceinline__ To cvt(From v) {
-  if constexpr (sizeof(To) == sizeof(From))
-    return v;
-  else if constexpr (sizeof(To) == 4)
-    return f64_to_f32(v);
-  else
-    return f32_to_f64(v);
-}
-
-// On-site and Heun constants in the arithmetic type R, converted once on the host.
-template <typename R>
-struct OnSiteT {
-  R zee[SX_MAX_SUB][3];
-  R twoK[SX_MAX_SUB];
-  R axis[SX_MAX_SUB][3];
-  R inv_mm[SX_MAX_SUB];
-};
-template <typename R>
-struct HeunT {
-  R dt, hdt, g, alpha;
-  R sigma[SX_MAX_SUB];
-  uint64_t seed;
-  uint32_t replica;
-  int thermal;
-};
-
-template <typename R>
-OnSiteT<R> onsite_cast(const OnSite &o) {
-  OnSiteT<R> r;
-  for (int a = 0; a < SX_MAX_SUB; ++a) {
-    for (int c = 0; c < 3; ++c) {
-      r.zee[a][c] = (R)o.zee[a][c];
-      r.axis[a][c] = (R)o.axis[a][c];
-    }
-    r.twoK[a] = (R)o.twoK[a];
-    r.inv_mm[a] = (R)o.inv_mm[a];
-  }
-  return r;
-}
-
-template <typename R>
-HeunT<R> heun_cast(const HeunConst &h) {
-  HeunT<R> r;
-  r.dt = (R)h.dt;
-  r.hdt = (R)(0.5 * h.dt);
-  r.g = (R)h.g;
-  r.alpha = (R)h.alpha;
-  for (int a = 0; a < SX_MAX_SUB; ++a) r.sigma[a] = (R)h.sigma[a];
-  r.seed = h.seed;
-  r.replica = h.replica;
-  r.thermal = h.thermal;
-  return r;
-}
-
 // real channels [nch][N] -> packed complex fields [nzf][N]
 template <typename Tin, typename R>
 __global__ void k_pack(const Tin *__restrict__ S, typename CxT<R>::T *__restrict__ Z, int nch, long long N) {

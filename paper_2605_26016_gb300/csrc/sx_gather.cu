@@ -8,6 +8,7 @@
 // (predictor, corrector) with the predictor state in a workspace.
 //
 // Also here: the FP64 energy and torque reductions and the noise probe.
+#include "sx_device.cuh"
 #include "sx_internal.h"
 #include "sx_noise.cuh"
 
@@ -58,7 +59,7 @@ __device__ __forceinline__ void bilinear(const Geo &g, const DevTap *__restrict_
     const int zz = wrap(z + tp.dz, g.nz, g.pz);
     if ((xx | yy | zz) < 0) continue;
     const int64_t j = (((int64_t)tp.b * g.nz + zz) * g.ny + yy) * g.nx + xx;
-    const R s0 = (R)S[j], s1 = (R)S[g.nsite + j], s2 = (R)S[2 * g.nsite + j];
+    const R s0 = cvt<R>(S[j]), s1 = cvt<R>(S[g.nsite + j]), s2 = cvt<R>(S[2 * g.nsite + j]);
     if (tp.iso) {
       const R J = tapJ<R>(tp, 0);
       acc[0] += J * s0;
@@ -74,12 +75,12 @@ __device__ __forceinline__ void bilinear(const Geo &g, const DevTap *__restrict_
 
 // Zeeman mu mu_B B and anisotropy 2K (S.n) n, added in precision R
 template <typename R>
-__device__ __forceinline__ void onsite_add(const OnSite &os, int a, const R s[3], R b[3]) {
-  const R n0 = (R)os.axis[a][0], n1 = (R)os.axis[a][1], n2 = (R)os.axis[a][2];
-  const R p = (R)os.twoK[a] * (s[0] * n0 + s[1] * n1 + s[2] * n2);
-  b[0] += (R)os.zee[a][0] + p * n0;
-  b[1] += (R)os.zee[a][1] + p * n1;
-  b[2] += (R)os.zee[a][2] + p * n2;
+__device__ __forceinline__ void onsite_add(const OnSiteT<R> &os, int a, const R s[3], R b[3]) {
+  const R n0 = os.axis[a][0], n1 = os.axis[a][1], n2 = os.axis[a][2];
+  const R p = os.twoK[a] * (s[0] * n0 + s[1] * n1 + s[2] * n2);
+  b[0] += os.zee[a][0] + p * n0;
+  b[1] += os.zee[a][1] + p * n1;
+  b[2] += os.zee[a][2] + p * n2;
 }
 
 // LLG right-hand side f = g [S x B + alpha S x (S x B)], g = -gamma/(1+alpha^2)
@@ -113,7 +114,7 @@ __device__ __forceinline__ void unit(double x[3]) {
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_field(Geo g, const DevTap *__restrict__ taps,
-                                                    const int *__restrict__ off, OnSite os, int onsite,
+                                                    const int *__restrict__ off, OnSiteT<R> os, int onsite,
                                                     const double *__restrict__ S, double *__restrict__ b) {
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i >= g.nsite) return;
@@ -122,31 +123,31 @@ __global__ void __launch_bounds__(kThreads) k_field(Geo g, const DevTap *__restr
   R acc[3];
   bilinear<R>(g, taps, off, S, x, y, z, a, acc);
   if (onsite) {
-    const R s[3] = {(R)S[i], (R)S[g.nsite + i], (R)S[2 * g.nsite + i]};
+    const R s[3] = {cvt<R>(S[i]), cvt<R>(S[g.nsite + i]), cvt<R>(S[2 * g.nsite + i])};
     onsite_add<R>(os, a, s, acc);
   }
-  b[i] = (double)acc[0];
-  b[g.nsite + i] = (double)acc[1];
-  b[2 * g.nsite + i] = (double)acc[2];
+  b[i] = cvt<double>(acc[0]);
+  b[g.nsite + i] = cvt<double>(acc[1]);
+  b[2 * g.nsite + i] = cvt<double>(acc[2]);
 }
 
 template <typename R>
-__device__ __forceinline__ void thermal(const HeunConst &h, int a, int64_t i, uint64_t step, R th[3]) {
+__device__ __forceinline__ void thermal(const HeunT<R> &h, int a, int64_t i, uint64_t step, R th[3]) {
   th[0] = th[1] = th[2] = R(0);
   if (h.thermal) {
     float e0, e1, e2;
     normals3(h.seed, h.replica, (uint64_t)i, step, e0, e1, e2);
-    const R sg = (R)h.sigma[a];
-    th[0] = sg * (R)e0;
-    th[1] = sg * (R)e1;
-    th[2] = sg * (R)e2;
+    const R sg = h.sigma[a];
+    th[0] = sg * cvt<R>(e0);
+    th[1] = sg * cvt<R>(e1);
+    th[2] = sg * cvt<R>(e2);
   }
 }
 
 // Predictor: S~ = N[S + dt f(S)], f0 kept for the corrector.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_predict(Geo g, const DevTap *__restrict__ taps,
-                                                      const int *__restrict__ off, OnSite os, HeunConst h,
+                                                      const int *__restrict__ off, OnSiteT<R> os, HeunT<R> h,
                                                       uint64_t step, const double *__restrict__ S,
                                                       double *__restrict__ St, double *__restrict__ F0) {
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -155,27 +156,27 @@ __global__ void __launch_bounds__(kThreads) k_predict(Geo g, const DevTap *__res
   site_of(g, i, x, y, z, a);
   R b[3];
   bilinear<R>(g, taps, off, S, x, y, z, a, b);
-  const R s[3] = {(R)S[i], (R)S[g.nsite + i], (R)S[2 * g.nsite + i]};
+  const R s[3] = {cvt<R>(S[i]), cvt<R>(S[g.nsite + i]), cvt<R>(S[2 * g.nsite + i])};
   onsite_add<R>(os, a, s, b);
   R th[3];
   thermal<R>(h, a, i, step, th);
-  const R im = (R)os.inv_mm[a];
+  const R im = os.inv_mm[a];
   const R B[3] = {b[0] * im + th[0], b[1] * im + th[1], b[2] * im + th[2]};
   R f[3];
-  llg_rhs<R>(s, B, (R)h.g, (R)h.alpha, f);
-  const R dt = (R)h.dt;
+  llg_rhs<R>(s, B, h.g, h.alpha, f);
+  const R dt = h.dt;
   R xn[3] = {s[0] + dt * f[0], s[1] + dt * f[1], s[2] + dt * f[2]};
   unit(xn);
   for (int k = 0; k < 3; ++k) {
-    St[k * g.nsite + i] = (double)xn[k];
-    F0[k * g.nsite + i] = (double)f[k];
+    St[k * g.nsite + i] = cvt<double>(xn[k]);
+    F0[k * g.nsite + i] = cvt<double>(f[k]);
   }
 }
 
 // Corrector: S' = N[S + dt/2 (f(S) + f(S~))]; the state sum and N[.] in FP64.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_correct(Geo g, const DevTap *__restrict__ taps,
-                                                      const int *__restrict__ off, OnSite os, HeunConst h,
+                                                      const int *__restrict__ off, OnSiteT<R> os, HeunT<R> h,
                                                       uint64_t step, const double *__restrict__ S,
                                                       const double *__restrict__ St, const double *__restrict__ F0,
                                                       double *__restrict__ Snew) {
@@ -185,19 +186,19 @@ __global__ void __launch_bounds__(kThreads) k_correct(Geo g, const DevTap *__res
   site_of(g, i, x, y, z, a);
   R b[3];
   bilinear<R>(g, taps, off, St, x, y, z, a, b);
-  const R s[3] = {(R)St[i], (R)St[g.nsite + i], (R)St[2 * g.nsite + i]};
+  const R s[3] = {cvt<R>(St[i]), cvt<R>(St[g.nsite + i]), cvt<R>(St[2 * g.nsite + i])};
   onsite_add<R>(os, a, s, b);
   R th[3];
   thermal<R>(h, a, i, step, th);
-  const R im = (R)os.inv_mm[a];
+  const R im = os.inv_mm[a];
   const R B[3] = {b[0] * im + th[0], b[1] * im + th[1], b[2] * im + th[2]};
   R f[3];
-  llg_rhs<R>(s, B, (R)h.g, (R)h.alpha, f);
-  const R hdt = (R)(0.5 * h.dt);
+  llg_rhs<R>(s, B, h.g, h.alpha, f);
+  const R hdt = h.hdt;
   double xn[3];
   for (int k = 0; k < 3; ++k) {
-    const R d = hdt * ((R)F0[k * g.nsite + i] + f[k]);
-    xn[k] = S[k * g.nsite + i] + (double)d;
+    const R d = hdt * (cvt<R>(F0[k * g.nsite + i]) + f[k]);
+    xn[k] = S[k * g.nsite + i] + cvt<double>(d);
   }
   unit(xn);
   for (int k = 0; k < 3; ++k) Snew[k * g.nsite + i] = xn[k];
@@ -322,9 +323,11 @@ int64_t reduce_blocks(int64_t nsite) {
 cudaError_t gather_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st) {
   const Geo &g = c->geo;
   if (c->prec == SX_PREC_FP64)
-    k_field<double><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, c->onsite, onsite, S, b);
+    k_field<double><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, onsite_cast<double>(c->onsite),
+                                                            onsite, S, b);
   else
-    k_field<float><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, c->onsite, onsite, S, b);
+    k_field<float><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, onsite_cast<float>(c->onsite),
+                                                           onsite, S, b);
   return cudaGetLastError();
 }
 
@@ -334,14 +337,18 @@ cudaError_t gather_heun_step(const sx_ctx *c, const double *src, double *dst, co
   double *St = c->d_work;
   double *F0 = c->d_work + 3 * g.nsite;
   if (c->prec == SX_PREC_FP64) {
-    k_predict<double><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, c->onsite, h, step, src,
+    k_predict<double><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, onsite_cast<double>(c->onsite),
+                                                              heun_cast<double>(h), step, src,
                                                               St, F0);
-    k_correct<double><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, c->onsite, h, step, src,
+    k_correct<double><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, onsite_cast<double>(c->onsite),
+                                                              heun_cast<double>(h), step, src,
                                                               St, F0, dst);
   } else {
-    k_predict<float><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, c->onsite, h, step, src,
+    k_predict<float><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, onsite_cast<float>(c->onsite),
+                                                              heun_cast<float>(h), step, src,
                                                              St, F0);
-    k_correct<float><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, c->onsite, h, step, src,
+    k_correct<float><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, onsite_cast<float>(c->onsite),
+                                                              heun_cast<float>(h), step, src,
                                                              St, F0, dst);
   }
   return cudaGetLastError();

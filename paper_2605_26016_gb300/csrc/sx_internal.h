@@ -61,6 +61,52 @@ struct Tap {
   double J[9];
 };
 
+// On-site and Heun constants in a kernel's arithmetic type R, converted once on
+// the host so that no kernel spends FP64 conversions on them per site.
+template <typename R>
+struct OnSiteT {
+  R zee[SX_MAX_SUB][3];
+  R twoK[SX_MAX_SUB];
+  R axis[SX_MAX_SUB][3];
+  R inv_mm[SX_MAX_SUB];
+};
+template <typename R>
+struct HeunT {
+  R dt, hdt, g, alpha;
+  R sigma[SX_MAX_SUB];
+  uint64_t seed;
+  uint32_t replica;
+  int thermal;
+};
+
+template <typename R>
+inline OnSiteT<R> onsite_cast(const OnSite &o) {
+  OnSiteT<R> r;
+  for (int a = 0; a < SX_MAX_SUB; ++a) {
+    for (int c = 0; c < 3; ++c) {
+      r.zee[a][c] = (R)o.zee[a][c];
+      r.axis[a][c] = (R)o.axis[a][c];
+    }
+    r.twoK[a] = (R)o.twoK[a];
+    r.inv_mm[a] = (R)o.inv_mm[a];
+  }
+  return r;
+}
+
+template <typename R>
+inline HeunT<R> heun_cast(const HeunConst &h) {
+  HeunT<R> r;
+  r.dt = (R)h.dt;
+  r.hdt = (R)(0.5 * h.dt);
+  r.g = (R)h.g;
+  r.alpha = (R)h.alpha;
+  for (int a = 0; a < SX_MAX_SUB; ++a) r.sigma[a] = (R)h.sigma[a];
+  r.seed = h.seed;
+  r.replica = h.replica;
+  r.thermal = h.thermal;
+  return r;
+}
+
 // Stencil-backend tables (filled by the host planner, consumed by sx_stencil.cu).
 struct StencilPlan;
 // FFT-backend buffers and kernel spectrum (sx_fft.cu).
