@@ -18,8 +18,10 @@
 //    (144 x (8+2R) x (8+2R)) in the canonical no-swizzle K-major layout with
 //    8 consecutive y rows per core matrix, so the operand of plane (dy, dz) is
 //    the same tile seen from a different start address (16-byte rows).
-//  * A is generated in shared memory from the tap values for each non-zero
-//    plane (planes whose taps are all zero are skipped).
+//  * A of every non-zero plane (planes whose taps are all zero are skipped) is
+//    built once per plan in global memory, already in the shared-memory
+//    operand layout; the kernel streams the planes into a double buffer with
+//    16-byte cp.async copies, the copy of plane p+1 overlapping the MMAs of p.
 //  * One elected thread issues tcgen05.mma (kind::f16 for BF16, kind::tf32 for
 //    TF32), tcgen05.commit arrives on an mbarrier; waits are bounded and set an
 //    error flag instead of hanging.  The epilogue reads TMEM with tcgen05.ld.
@@ -62,10 +64,15 @@ struct TcArgs {
   float zee[3], twoK, axis[3];
   int onsite;
   int *err;          // set to 1 if a bounded wait gave up
+  const unsigned char *A;  // Toeplitz operands of the planes, built once per plan in the
+                           // shared-memory layout (tc_a_stride bytes per plane)
+  int nabuf;               // shared-memory A buffers: 2 (copy of plane p+1 overlaps the MMAs of p) or 1
+  unsigned smem;           // dynamic shared memory of the launch
 };
 
 struct TcPlan {
   int tf32;
+  unsigned char *A;     // Toeplitz operands, nplanes x tc_a_stride bytes
   TcArgs base;
   float *St, *F0, *Bf;  // Heun workspaces [3][ncell]
   float *Th;            // thermal field of the step [3][ncell]
@@ -126,6 +133,48 @@ __device__ __forceinline__ bool wait_parity(uint64_t *mbar, uint32_t parity, int
   return false;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit_tc() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_tc() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// bytes of one plane's A operand (TF32: one copy; BF16: hi and lo copies)
+template <bool TF32>
+constexpr size_t tc_a_stride() {
+  return (TF32 ? 1 : 2) * (size_t)kTcM * kTcKP * (TF32 ? 4 : 2);
+}
+
+// bytes of one copy of the resident input window for halo R: K chunks x (8+2R) x (8+2R) rows of 16 bytes
+template <bool TF32>
+__host__ __device__ constexpr size_t tc_b_copy(int R) {
+  return (size_t)(kTcKP / (16 / (TF32 ? 4 : 2))) * (kTcZB + 2 * R) * (kTcYB + 2 * R) * 16;
+}
+
+// dynamic shared memory of a launch with nabuf A buffers
+template <bool TF32>
+constexpr size_t tc_smem_bytes(int R, int nabuf) {
+  return (TF32 ? 1 : 2) * tc_b_copy<TF32>(R) + (size_t)nabuf * tc_a_stride<TF32>() + 64;
+}
+
+// Toeplitz A[m][k] = J(k - R - m, dy, dz) of plane blockIdx.x, in the canonical K-major
+// no-swizzle layout the kernel hands to tcgen05.mma (plan time)
+template <bool TF32>
+__global__ void k_build_a(const TcArgs p, unsigned char *__restrict__ A) {
+  constexpr int ESZ = TF32 ? 4 : 2;
+  constexpr int EPC = 16 / ESZ;
+  constexpr size_t A_COPY = (size_t)kTcM * kTcKP * ESZ;
+  const int pl = blockIdx.x, dy = p.plane_dy[pl], dz = p.plane_dz[pl];
+  unsigned char *dst = A + (size_t)pl * tc_a_stride<TF32>();
+  for (int e = threadIdx.x; e < kTcM * kTcKP; e += blockDim.x) {
+    const int k = e % kTcKP, m = e / kTcKP;
+    const int dx = k - p.R - m;
+    const float v = (dx >= -p.R && dx <= p.R) ? p.J[dz + 3][dy + 3][dx + 3] : 0.0f;
+    put_elem<TF32>(dst, A_COPY, ((size_t)(k / EPC) * (kTcM / 8) + m / 8) * 128 + (size_t)(m % 8) * 16 + (size_t)(k % EPC) * ESZ,
+                   v);
+  }
+}
+
 // Field of one spin field (FP64 spins or FP32 predictor state) into out (FP64 or FP32),
 // optional on-site terms.  Grid: (ceil(nx/128), ceil(ny/8), ceil(nz/8)), 128 threads.
 template <bool TF32, typename Tin, typename Tout>
@@ -142,11 +191,12 @@ __global__ void __launch_bounds__(kTcThreads) k_field_tc(const TcArgs p, const T
   const uint32_t LBO_A = (kTcM / 8) * 128u, SBO_A = 128u;
   // operand copies: TF32 one, BF16 two (hi, lo); each B copy spans CHUNKS * ZR * YR * 16 bytes
   constexpr int NCOPY = TF32 ? 1 : 2;
-  constexpr size_t B_COPY = (size_t)CHUNKS * (kTcZB + 2 * kTcRMax) * (kTcYB + 2 * kTcRMax) * 16;
+  const size_t B_COPY = tc_b_copy<TF32>(R);
   constexpr size_t A_COPY = (size_t)kTcM * kTcKP * ESZ;
+  constexpr size_t A_STRIDE = tc_a_stride<TF32>();
   unsigned char *sB = smem;
-  unsigned char *sA = smem + NCOPY * B_COPY;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(sA + NCOPY * A_COPY);
+  unsigned char *sAbuf = smem + NCOPY * B_COPY;  // nabuf plane buffers of A_STRIDE bytes
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sAbuf + p.nabuf * A_STRIDE);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * kTcM, y0 = blockIdx.y * kTcYB, z0 = blockIdx.z * kTcZB;
@@ -184,16 +234,18 @@ __global__ void __launch_bounds__(kTcThreads) k_field_tc(const TcArgs p, const T
       put_elem<TF32>(sB, B_COPY, ((size_t)(k / EPC) * ZR + zg) * YR * 16 + (size_t)yrow * 16 + (size_t)(k % EPC) * ESZ,
                      v);
     }
+    // A of plane pl into buffer pl % nabuf (16-byte copies from the L2-resident plan operands)
+    auto copy_a = [&](int pl) {
+      const unsigned char *src = p.A + (size_t)pl * A_STRIDE;
+      unsigned char *dst = sAbuf + (size_t)(pl % p.nabuf) * A_STRIDE;
+      for (int e = tid; e < (int)(A_STRIDE / 16); e += kTcThreads) cp_async16(saddr(dst + 16 * e), src + 16 * e);
+      cp_commit_tc();
+    };
+    if (p.nplanes > 0) copy_a(0);
     for (int pl = 0; pl < p.nplanes && alive; ++pl) {
       const int dy = p.plane_dy[pl], dz = p.plane_dz[pl];
-      // Toeplitz A[m][k] = J(k - R - m, dy, dz)
-      for (int e = tid; e < kTcM * kTcKP; e += kTcThreads) {
-        const int k = e % kTcKP, m = e / kTcKP;
-        const int dx = k - R - m;
-        const float v = (dx >= -R && dx <= R) ? p.J[dz + 3][dy + 3][dx + 3] : 0.0f;
-        put_elem<TF32>(sA, A_COPY,
-                       ((size_t)(k / EPC) * (kTcM / 8) + m / 8) * 128 + (size_t)(m % 8) * 16 + (size_t)(k % EPC) * ESZ, v);
-      }
+      unsigned char *sA = sAbuf + (size_t)(pl % p.nabuf) * A_STRIDE;
+      cp_wait_all_tc();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
@@ -225,11 +277,14 @@ __global__ void __launch_bounds__(kTcThreads) k_field_tc(const TcArgs p, const T
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar))
                      : "memory");
       }
-      // every thread waits for this plane's MMAs before A (and, after the last plane, B) is rewritten
+      // with two buffers the other one was read by the MMAs of plane pl - 1, which have completed
+      if (p.nabuf == 2 && pl + 1 < p.nplanes) copy_a(pl + 1);
+      // every thread waits for this plane's MMAs before its A buffer (and, after the last plane, B) is rewritten
       alive = wait_parity(mbar, phase, p.err);
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       __syncthreads();
+      if (p.nabuf == 1 && pl + 1 < p.nplanes && alive) copy_a(pl + 1);
     }
   }
 
@@ -293,25 +348,18 @@ __global__ void __launch_bounds__(kTcThreads) k_field_tc(const TcArgs p, const T
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
 }
 
-template <bool TF32>
-constexpr size_t tc_smem() {
-  constexpr int ESZ = TF32 ? 4 : 2;
-  constexpr size_t ncopy = TF32 ? 1 : 2;
-  return ncopy * ((size_t)(kTcKP / (16 / ESZ)) * (kTcZB + 2 * kTcRMax) * (kTcYB + 2 * kTcRMax) * 16 +
-                  (size_t)kTcM * kTcKP * ESZ) +
-         64;
-}
+constexpr size_t kTcSmemMax = 227 * 1024;
 
 template <bool TF32, typename Tin, typename Tout>
 cudaError_t launch_tc(const sx_ctx *c, const TcArgs &a, const Tin *S, Tout *out, cudaStream_t st) {
   const dim3 grid((c->geo.nx + kTcM - 1) / kTcM, (c->geo.ny + kTcYB - 1) / kTcYB, (c->geo.nz + kTcZB - 1) / kTcZB);
-  k_field_tc<TF32, Tin, Tout><<<grid, kTcThreads, tc_smem<TF32>(), st>>>(a, S, out);
+  k_field_tc<TF32, Tin, Tout><<<grid, kTcThreads, a.smem, st>>>(a, S, out);
   return cudaGetLastError();
 }
 
 template <bool TF32>
 cudaError_t set_tc_smem() {
-  const int s = (int)tc_smem<TF32>();
+  const int s = (int)kTcSmemMax;
   cudaError_t e = cudaFuncSetAttribute(k_field_tc<TF32, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_field_tc<TF32, double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
@@ -379,6 +427,20 @@ int tc_plan(sx_ctx *c) {
   if (e == cudaSuccess) e = cudaMalloc(&tp->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(tp->err, 0, sizeof(int));
   if (e == cudaSuccess) e = tp->tf32 ? set_tc_smem<true>() : set_tc_smem<false>();
+  const size_t astride = tp->tf32 ? tc_a_stride<true>() : tc_a_stride<false>();
+  const size_t sm2 = tp->tf32 ? tc_smem_bytes<true>(R, 2) : tc_smem_bytes<false>(R, 2);
+  a.nabuf = sm2 <= kTcSmemMax ? 2 : 1;
+  a.smem = (unsigned)(tp->tf32 ? tc_smem_bytes<true>(R, a.nabuf) : tc_smem_bytes<false>(R, a.nabuf));
+  if (e == cudaSuccess && a.nplanes > 0) e = cudaMalloc(&tp->A, (size_t)a.nplanes * astride);
+  if (e == cudaSuccess && a.nplanes > 0) {
+    if (tp->tf32)
+      k_build_a<true><<<a.nplanes, 256>>>(a, tp->A);
+    else
+      k_build_a<false><<<a.nplanes, 256>>>(a, tp->A);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  a.A = tp->A;
   a.err = tp->err;
   c->tc = tp;
   if (e != cudaSuccess) {
@@ -396,6 +458,7 @@ void tc_free(sx_ctx *c) {
   cudaFree(tp->F0);
   cudaFree(tp->Bf);
   cudaFree(tp->Th);
+  cudaFree(tp->A);
   cudaFree(tp->err);
   delete tp;
   c->tc = nullptr;
