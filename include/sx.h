@@ -265,6 +265,14 @@ int sx_set_stencil_scheme(sx_ctx *ctx, int scheme);
 int sx_autotune(sx_ctx *ctx, const double *S, double *S_scratch, const sx_llg_params *p, int steps,
                 double times_ms[2], void *stream);
 
+/* Synchronise the stream and report whether a bounded device wait of this
+ * context's kernels gave up since the last check (tensor-core MMA waits, the
+ * grid barrier of the persistent multi-step stencil launch): SX_ERR_TIMEOUT
+ * then, and the results of the calls since the last check are invalid; the
+ * flag is cleared.  No kernel of the library traps or spins without bound:
+ * such a wait sets the flag and returns instead. */
+int sx_device_status(sx_ctx *ctx, void *stream);
+
 /* Reduced effective field b = -dH/dS (meV, see "Spin Hamiltonian and
  * effective fields") of the spin field S, written to b (device, same layout
  * as S, FP64 whatever the plan precision).  S and b must not overlap. */
@@ -274,6 +282,10 @@ int sx_field(sx_ctx *ctx, const double *S, double *b, void *stream);
  * step0+nsteps-1 (the step index is the noise counter).  S (device) holds
  * the input and receives the result; S_scratch (device, same size, no
  * overlap) is a caller-owned ping-pong buffer whose content is overwritten.
+ * On a STENCIL two-pass plan of a lattice with fewer tile columns than
+ * resident CTAs, nsteps >= 2 run in one cooperative launch with a bounded
+ * grid barrier between the passes (bit-identical to separate launches;
+ * sx_device_status reports a barrier that gave up).
  * SX_ERR_ARG for dt <= 0, alpha < 0, T < 0 or nsteps < 0. */
 int sx_llg_heun_step(sx_ctx *ctx, double *S, double *S_scratch, const sx_llg_params *p, uint64_t step0,
                      int nsteps, void *stream);

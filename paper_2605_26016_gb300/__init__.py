@@ -31,7 +31,7 @@ EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shel
            "sx_add_dmi", "sx_add_bonds", "sx_set_zeeman", "sx_set_anisotropy", "sx_set_dipolar", "sx_get_taps",
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
            "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise", "sx_path_step",
-           "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune")
+           "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune", "sx_device_status")
 SX_STENCIL_AUTO, SX_STENCIL_FUSED, SX_STENCIL_TWO_PASS = 0, 1, 2
 STENCIL_SCHEMES = {"auto": SX_STENCIL_AUTO, "fused": SX_STENCIL_FUSED, "two_pass": SX_STENCIL_TWO_PASS}
 SX_MIN_VP, SX_MIN_DAMPED_LLG = 0, 1
@@ -120,6 +120,7 @@ def lib():
                                             ctypes.POINTER(ctypes.c_int), dp, dp, vp]),
             "sx_geodesic": (ctypes.c_int, [vp, vp, vp, dp, vp]),
             "sx_set_stencil_scheme": (ctypes.c_int, [vp, ctypes.c_int]),
+            "sx_device_status": (ctypes.c_int, [vp, vp]),
             "sx_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_int, dp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -344,6 +345,11 @@ def sx_geodesic(ctx, A, B, nsite, stream=None):
     _chk(lib().sx_geodesic(ctx, _dev_ptr(A, 3 * nsite), _dev_ptr(B, 3 * nsite), ctypes.byref(out),
                            _stream(stream)), "sx_geodesic")
     return out.value
+
+
+def sx_device_status(ctx, stream=None):
+    """Synchronise and raise SxError(SX_ERR_TIMEOUT) if a bounded device wait gave up since the last check."""
+    return _chk(lib().sx_device_status(ctx, _stream(stream)), "sx_device_status")
 
 
 def sx_set_stencil_scheme(ctx, scheme):

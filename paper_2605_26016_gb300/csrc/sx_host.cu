@@ -578,6 +578,18 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
   return best_scheme;
 }
 
+int sx_device_status(sx_ctx *c, void *stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "device status");
+  int timed_out = 0;
+  if (c->backend == SX_BACKEND_STENCIL) timed_out |= stencil_check_error(c);
+  if (c->backend == SX_BACKEND_IGEMM_TC) timed_out |= tc_check_error(c);
+  if (timed_out) return set_error(SX_ERR_TIMEOUT, "a bounded device wait gave up; results of that call are invalid");
+  return SX_OK;
+}
+
 int sx_field(sx_ctx *c, const double *S, double *b, void *stream) {
   int rc = check_ready(c);
   if (rc) return rc;
@@ -599,9 +611,15 @@ int sx_llg_heun_step(sx_ctx *c, double *S, double *S_scratch, const sx_llg_param
   if ((rc = make_heun_const(c, p, h))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   double *buf[2] = {S, S_scratch};
-  for (int k = 0; k < nsteps; ++k) {
-    cudaError_t e = backend_step(c, buf[k & 1], buf[(k + 1) & 1], h, step0 + (uint64_t)k, st);
-    if (e != cudaSuccess) return cuda_error(e, "Heun step launch");
+  if (nsteps >= 2 && c->backend == SX_BACKEND_STENCIL && stencil_persistent_ok(c)) {
+    // small lattices: all steps in one cooperative launch
+    cudaError_t e = stencil_heun_steps_persistent(c, S, S_scratch, h, step0, nsteps, st);
+    if (e != cudaSuccess) return cuda_error(e, "persistent Heun launch");
+  } else {
+    for (int k = 0; k < nsteps; ++k) {
+      cudaError_t e = backend_step(c, buf[k & 1], buf[(k + 1) & 1], h, step0 + (uint64_t)k, st);
+      if (e != cudaSuccess) return cuda_error(e, "Heun step launch");
+    }
   }
   if (nsteps & 1) {
     cudaError_t e = cudaMemcpyAsync(S, S_scratch, bytes, cudaMemcpyDeviceToDevice, st);

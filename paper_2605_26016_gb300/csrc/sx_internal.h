@@ -182,6 +182,11 @@ int stencil_plan(sx_ctx *c);
 void stencil_free(sx_ctx *c);
 int stencil_set_scheme(sx_ctx *c, int scheme);  // SX_STENCIL_*, on a planned stencil context
 int stencil_scheme(const sx_ctx *c);
+// the two-pass scheme's persistent multi-step launch (lattices with fewer tile columns than CTA slots)
+bool stencil_persistent_ok(const sx_ctx *c);
+cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S1, const HeunConst &h,
+                                          uint64_t step0, int nsteps, cudaStream_t st);
+int stencil_check_error(const sx_ctx *c);
 cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
 // fields of `count` spin fields stride doubles apart (S, S + stride, ...) into b, b + stride, ... in one launch
 cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int count, long long stride,

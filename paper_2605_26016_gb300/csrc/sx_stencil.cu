@@ -146,6 +146,8 @@ struct StencilArgs {
   unsigned replica;
 };
 
+struct GridBar;
+
 struct StencilPlan {
   int family;
   int tz;           // z chunk of the fused Heun step (and of single-image field launches)
@@ -158,6 +160,8 @@ struct StencilPlan {
   float *d_eta;     // two-pass workspace: thermal normals (3 nsite floats)
   int2 *d_sched;    // balanced schedule of the two-pass kernels (nsched CTAs)
   int nsched;
+  GridBar *d_bar;   // grid barrier and error word of the persistent multi-step kernel
+  int persistent;   // 1: nsched CTAs of the persistent kernel fit on the device at once
   StencilArgs base;
 };
 
@@ -516,6 +520,7 @@ struct PassIO {
   double *Sout;      // CORR: S^{n+1}
   int nzc;           // z chunks per image (blockIdx.z = image * nzc + chunk)
   long long istride; // doubles between images (FIELD)
+  unsigned long long step;  // noise counter of the step (PRED)
   const int2 *sched; // balanced schedule (one image): CTA k owns column-plane units
                      // [sched[k].x, sched[k].x + sched[k].y) of u = column * nz + z; null: the grid tiles
 };
@@ -634,7 +639,7 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, c
           float e0 = 0.f, e1 = 0.f, e2 = 0.f;
           if constexpr (MODE == PASS_PRED) {
             if (p.thermal) {
-              normals3(p.seed, p.replica, (unsigned long long)i, p.step, e0, e1, e2);
+              normals3(p.seed, p.replica, (unsigned long long)i, io.step, e0, e1, e2);
               io.eta[i] = e0;
               io.eta[p.nsite + i] = e1;
               io.eta[2 * p.nsite + i] = e2;
@@ -677,28 +682,94 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, c
   cp_wait<0>();
 }
 
+// The column-plane units of schedule entry k, segment by segment.
+template <int FID, int MODE>
+__device__ __forceinline__ void run_scheduled(const StencilArgs &p, int onsite, const PassIO &io,
+                                              unsigned char *smem_raw, int k) {
+  using F = Family<FID>;
+  const int2 e = io.sched[k];
+  const int ncx = (p.nx + 31) / 32;
+  long long u = e.x;
+  const long long uend = (long long)e.x + e.y;
+  while (u < uend) {  // uniform over the block
+    const int col = (int)(u / p.nz), z = (int)(u - (long long)col * p.nz);
+    const int len = (int)min((long long)(p.nz - z), uend - u);
+    pass_segment<FID, MODE>(p, onsite, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+    u += len;
+    __syncthreads();  // shared memory is reused by the next segment
+  }
+}
+
 template <int FID, int MODE>
 __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
     k_stencil_pass(const StencilArgs p, int onsite, const PassIO io) {
   using F = Family<FID>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (io.sched) {
-    const int2 e = io.sched[blockIdx.x];
-    const int ncx = (p.nx + 31) / 32;
-    long long u = e.x;
-    const long long uend = (long long)e.x + e.y;
-    while (u < uend) {  // uniform over the block
-      const int col = (int)(u / p.nz), z = (int)(u - (long long)col * p.nz);
-      const int len = (int)min((long long)(p.nz - z), uend - u);
-      pass_segment<FID, MODE>(p, onsite, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
-      u += len;
-      __syncthreads();  // shared memory is reused by the next segment
-    }
+    run_scheduled<FID, MODE>(p, onsite, io, smem_raw, blockIdx.x);
   } else {
     const int img = blockIdx.z / io.nzc, zc = blockIdx.z - img * io.nzc;
     const int z0 = zc * p.tz;
     pass_segment<FID, MODE>(p, onsite, io, smem_raw, img, blockIdx.x * 32, blockIdx.y * F::BY, z0,
                             min(p.tz, p.nz - z0));
+  }
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident): arrive on a
+// counter, the last arrival resets it and advances the generation; the others
+// wait for the generation to change.  The wait is bounded: after about two
+// seconds it sets the error word and gives up, and every CTA then leaves the
+// step loop at its next barrier.  Returns false once the error word is set.
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+  int err;
+  int pad;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBar *gb, unsigned nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    volatile unsigned *vgen = &gb->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      for (long it = 0; *vgen == g; ++it) {
+        if (it > (1L << 25)) {
+          atomicExch(&gb->err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int *)&gb->err == 0;
+}
+
+// nsteps two-pass Heun steps in one cooperative launch (lattices with few tile
+// columns, where per-step launches would dominate): step k runs the predictor
+// over every CTA's scheduled units, a grid barrier, the corrector, a barrier.
+// The state alternates between S0 and S1 (step k reads S_{k mod 2}).  Same
+// per-site arithmetic as the separate pass launches, so bit-identical to them.
+template <int FID>
+__global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
+    k_heun_persistent(const StencilArgs p, PassIO io, double *S0, double *S1, int nsteps,
+                      unsigned long long step0, GridBar *gb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int k = 0; k < nsteps; ++k) {
+    io.S = (k & 1) ? S1 : S0;
+    io.Sout = (k & 1) ? S0 : S1;
+    io.step = step0 + (unsigned long long)k;
+    run_scheduled<FID, PASS_PRED>(p, 1, io, smem_raw, blockIdx.x);
+    if (!grid_sync(gb, gridDim.x)) return;
+    run_scheduled<FID, PASS_CORR>(p, 1, io, smem_raw, blockIdx.x);
+    if (!grid_sync(gb, gridDim.x)) return;
   }
 }
 
@@ -814,12 +885,34 @@ cudaError_t launch_heun2(const StencilPlan &sp, StencilArgs a, const double *src
   io.Sout = dst;
   io.b = nullptr;
   io.sched = sp.d_sched;
+  io.step = a.step;
   io.nzc = (a.nz + a.tz - 1) / a.tz;
   const dim3 grid = sp.d_sched ? dim3(sp.nsched)
                                : dim3((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc);
   k_stencil_pass<FID, PASS_PRED><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, 1, io);
   k_stencil_pass<FID, PASS_CORR><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, 1, io);
   return cudaGetLastError();
+}
+
+template <int FID>
+cudaError_t launch_persistent(const StencilPlan &sp, const StencilArgs &a, double *S0, double *S1, int nsteps,
+                              unsigned long long step0, cudaStream_t st) {
+  using g = GF<Family<FID>>;
+  PassIO io;
+  memset(&io, 0, sizeof(io));
+  io.St = sp.d_St;
+  io.St_out = sp.d_St;
+  io.f0 = sp.d_f0;
+  io.eta = sp.d_eta;
+  io.sched = sp.d_sched;
+  io.nzc = 1;
+  StencilArgs pa = a;
+  GridBar *gb = sp.d_bar;
+  void *args[] = {(void *)&pa, (void *)&io, (void *)&S0, (void *)&S1, (void *)&nsteps, (void *)&step0, (void *)&gb};
+  cudaError_t e = cudaMemsetAsync(sp.d_bar, 0, 2 * sizeof(unsigned), st);  // count, gen (err is sticky)
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel((const void *)k_heun_persistent<FID>, dim3(sp.nsched),
+                                     dim3(32, Family<FID>::BY), args, g::SMEM, st);
 }
 
 // Balanced schedule of a one-image pass over `slots` resident CTAs: the column-plane
@@ -889,6 +982,15 @@ int choose_tz(const sx_ctx *c) {
     }
   }
   return best_tz;
+}
+
+template <int FID>
+cudaError_t persistent_occupancy(int *occ) {
+  cudaError_t e = cudaFuncSetAttribute(k_heun_persistent<FID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)GF<Family<FID>>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_heun_persistent<FID>, GF<Family<FID>>::NT,
+                                                       GF<Family<FID>>::SMEM);
 }
 
 template <int FID>
@@ -1002,6 +1104,25 @@ int stencil_plan(sx_ctx *c) {
       return set_error(SX_ERR_OOM, "stencil schedule: device allocation failed");
     }
   }
+  if (sp->d_sched) {
+    int occ = 0;
+    cudaError_t e2 = cudaMalloc(&sp->d_bar, sizeof(GridBar));
+    if (e2 == cudaSuccess) e2 = cudaMemset(sp->d_bar, 0, sizeof(GridBar));
+    if (e2 == cudaSuccess) {
+      switch (fam) {
+        case FAM_SC6_ISO: e2 = persistent_occupancy<FAM_SC6_ISO>(&occ); break;
+        case FAM_SC6_TEN: e2 = persistent_occupancy<FAM_SC6_TEN>(&occ); break;
+        case FAM_SC26_ISO: e2 = persistent_occupancy<FAM_SC26_ISO>(&occ); break;
+        case FAM_SC26_TEN: e2 = persistent_occupancy<FAM_SC26_TEN>(&occ); break;
+        default: e2 = persistent_occupancy<FAM_BCC4>(&occ); break;
+      }
+    }
+    if (e2 != cudaSuccess) {
+      cudaGetLastError();
+      occ = 0;
+    }
+    sp->persistent = sp->d_bar && (long long)occ * sp->nsm >= sp->nsched ? 1 : 0;
+  }
   c->stencil = sp;
   const int rc = stencil_set_scheme(c, c->opt_scheme);
   if (rc != SX_OK) {
@@ -1040,12 +1161,26 @@ int stencil_set_scheme(sx_ctx *c, int scheme) {
 
 int stencil_scheme(const sx_ctx *c) { return c->stencil ? c->stencil->scheme : -1; }
 
+bool stencil_persistent_ok(const sx_ctx *c) {
+  return c->stencil && c->stencil->scheme == SX_STENCIL_TWO_PASS && c->stencil->persistent;
+}
+
+// 1 if a bounded wait of the persistent kernel gave up since the last check (clears it)
+int stencil_check_error(const sx_ctx *c) {
+  if (!c->stencil || !c->stencil->d_bar) return 0;
+  GridBar h;
+  if (cudaMemcpy(&h, c->stencil->d_bar, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+  if (h.err) cudaMemset(c->stencil->d_bar, 0, sizeof(GridBar));
+  return h.err;
+}
+
 void stencil_free(sx_ctx *c) {
   if (c->stencil) {
     cudaFree(c->stencil->d_St);
     cudaFree(c->stencil->d_f0);
     cudaFree(c->stencil->d_eta);
     cudaFree(c->stencil->d_sched);
+    cudaFree(c->stencil->d_bar);
   }
   delete c->stencil;
   c->stencil = nullptr;
@@ -1067,6 +1202,37 @@ cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int
 
 cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st) {
   return stencil_field_batch(c, S, b, 1, 0, onsite, st);
+}
+
+namespace {
+StencilArgs heun_args(const sx_ctx *c, const HeunConst &h, uint64_t step) {
+  StencilArgs a = c->stencil->base;
+  a.g = (float)h.g;
+  a.alpha = (float)h.alpha;
+  a.dt = (float)h.dt;
+  a.hdt = (float)(0.5 * h.dt);
+  a.thermal = h.thermal;
+  for (int s = 0; s < c->lat.nsub && s < 2; ++s) a.sigma[s] = (float)h.sigma[s];
+  a.seed = h.seed;
+  a.replica = h.replica;
+  a.step = step;
+  return a;
+}
+}  // namespace
+
+// nsteps steps in one persistent launch, S0 -> S1 -> S0 ...; the result is in S_{nsteps mod 2}
+cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S1, const HeunConst &h,
+                                          uint64_t step0, int nsteps, cudaStream_t st) {
+  const StencilPlan &sp = *c->stencil;
+  StencilArgs a = heun_args(c, h, step0);
+  a.tz = sp.tz2;
+  switch (sp.family) {
+    case FAM_SC6_ISO: return launch_persistent<FAM_SC6_ISO>(sp, a, S0, S1, nsteps, step0, st);
+    case FAM_SC6_TEN: return launch_persistent<FAM_SC6_TEN>(sp, a, S0, S1, nsteps, step0, st);
+    case FAM_SC26_ISO: return launch_persistent<FAM_SC26_ISO>(sp, a, S0, S1, nsteps, step0, st);
+    case FAM_SC26_TEN: return launch_persistent<FAM_SC26_TEN>(sp, a, S0, S1, nsteps, step0, st);
+    default: return launch_persistent<FAM_BCC4>(sp, a, S0, S1, nsteps, step0, st);
+  }
 }
 
 cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,

@@ -485,9 +485,11 @@ cudaError_t tc_heun_step(const sx_ctx *c, const double *src, double *dst, const 
   return e;
 }
 
+// 1 if a bounded wait of the tensor-core kernel gave up since the last check (clears it)
 int tc_check_error(const sx_ctx *c) {
   int h = 0;
   if (!c->tc || cudaMemcpy(&h, c->tc->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+  if (h) cudaMemset(c->tc->err, 0, sizeof(int));
   return h;
 }
 

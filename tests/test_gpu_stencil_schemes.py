@@ -74,3 +74,26 @@ def test_scheme_switch_on_a_planned_context_and_autotune():
     g.plan("gather", "fp32")
     S8 = torch.from_numpy(random_spins(2, (8, 8, 8), 5)).cuda()
     assert sx.sx_autotune(g.ctx, S8, torch.empty_like(S8), p, g.nsite)[0] == "fused"
+
+
+@pytest.mark.parametrize("thermal", [False, True])
+@pytest.mark.parametrize("name,n,pbc", [("sc_nn", (32, 32, 32), (1, 1, 1)), ("bcc_4shell", (13, 11, 9), (1, 1, 0)),
+                                        ("sc_j123_dmi", (17, 12, 10), (1, 1, 1)), ("bcc_4shell", (40, 30, 20), (1, 0, 1))])
+def test_persistent_multi_step_launch_equals_separate_steps(name, n, pbc, thermal):
+    # on these few-column lattices sx_llg_heun_step runs all steps in one cooperative launch with a grid
+    # barrier between the passes; sx_llg_heun_step_out launches each step's two passes separately
+    s, w = sx.system_from_workload(name, n, pbc=pbc)
+    sx.sx_set_stencil_scheme(s.ctx, "two_pass")
+    s.plan("stencil", "fp32")
+    S0 = torch.from_numpy(random_spins(s.nsub, n, 77)).cuda()
+    T = 150.0 if thermal else 0.0
+    p = sx.llg_params(w["dt"], w["alpha"], T, seed=4, replica=1)
+    for nsteps in (2, 5):
+        A = S0.clone()
+        s.heun(A, torch.empty_like(A), dt=w["dt"], alpha=w["alpha"], T=T, seed=4, replica=1, step0=11, nsteps=nsteps)
+        bufs = [S0.clone(), torch.empty_like(S0)]
+        for k in range(nsteps):
+            sx.sx_llg_heun_step_out(s.ctx, bufs[k & 1], bufs[(k + 1) & 1], p, 11 + k, s.nsite)
+        torch.cuda.synchronize()
+        sx.sx_device_status(s.ctx)
+        assert torch.equal(A, bufs[nsteps & 1])
