@@ -265,6 +265,27 @@ int sx_set_stencil_scheme(sx_ctx *ctx, int scheme);
 int sx_autotune(sx_ctx *ctx, const double *S, double *S_scratch, const sx_llg_params *p, int steps,
                 double times_ms[2], void *stream);
 
+/* A batch of independent replicas that share one Hamiltonian: planned STENCIL
+ * contexts with the same lattice family and identical couplings, on-site
+ * terms and moments, but their own lattice sizes and boundaries (e.g. an
+ * ensemble of cubes of different edge).  One predictor and one corrector
+ * launch advance every replica: the CTAs walk a balanced schedule over all
+ * replicas' column-plane units.  sx_batch_create switches the contexts to
+ * the two-pass scheme; they must outlive the batch and not be re-planned
+ * (SX_ERR_STATE).  SX_ERR_ARG for differing couplings, a repeated context or
+ * nrep outside 1..65536; SX_ERR_UNSUPPORTED for non-STENCIL plans. */
+typedef struct sx_batch sx_batch;
+int sx_batch_create(sx_batch **out, sx_ctx *const *ctxs, int nrep);
+void sx_batch_destroy(sx_batch *b);
+
+/* One Heun step at `step` for every replica r of the batch: S_out[r] =
+ * Heun(S_in[r]) (host arrays of nrep device pointers; S_in[r] and S_out[r]
+ * must not overlap).  Replica r draws its noise with replica index
+ * p->replica + r; otherwise bit-identical to sx_llg_heun_step_out on its
+ * context. */
+int sx_batch_heun_step(sx_batch *b, const double *const *S_in, double *const *S_out, const sx_llg_params *p,
+                       uint64_t step, void *stream);
+
 /* Synchronise the stream and report whether a bounded device wait of this
  * context's kernels gave up since the last check (tensor-core MMA waits, the
  * grid barrier of the persistent multi-step stencil launch): SX_ERR_TIMEOUT

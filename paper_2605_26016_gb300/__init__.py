@@ -31,7 +31,8 @@ EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shel
            "sx_add_dmi", "sx_add_bonds", "sx_set_zeeman", "sx_set_anisotropy", "sx_set_dipolar", "sx_get_taps",
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
            "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise", "sx_path_step",
-           "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune", "sx_device_status")
+           "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune", "sx_device_status",
+           "sx_batch_create", "sx_batch_destroy", "sx_batch_heun_step")
 SX_STENCIL_AUTO, SX_STENCIL_FUSED, SX_STENCIL_TWO_PASS = 0, 1, 2
 STENCIL_SCHEMES = {"auto": SX_STENCIL_AUTO, "fused": SX_STENCIL_FUSED, "two_pass": SX_STENCIL_TWO_PASS}
 SX_MIN_VP, SX_MIN_DAMPED_LLG = 0, 1
@@ -121,6 +122,10 @@ def lib():
             "sx_geodesic": (ctypes.c_int, [vp, vp, vp, dp, vp]),
             "sx_set_stencil_scheme": (ctypes.c_int, [vp, ctypes.c_int]),
             "sx_device_status": (ctypes.c_int, [vp, vp]),
+            "sx_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int]),
+            "sx_batch_destroy": (None, [vp]),
+            "sx_batch_heun_step": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                  ctypes.POINTER(sx_llg_params), ctypes.c_uint64, vp]),
             "sx_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_int, dp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -345,6 +350,36 @@ def sx_geodesic(ctx, A, B, nsite, stream=None):
     _chk(lib().sx_geodesic(ctx, _dev_ptr(A, 3 * nsite), _dev_ptr(B, 3 * nsite), ctypes.byref(out),
                            _stream(stream)), "sx_geodesic")
     return out.value
+
+
+class Batch:
+    """Replicas sharing one Hamiltonian (SpinSystem objects with stencil plans), advanced together by
+    sx_batch_heun_step.  Keeps the systems alive while it exists."""
+
+    def __init__(self, systems):
+        self.systems = list(systems)
+        arr = (ctypes.c_void_p * len(self.systems))(*[s.ctx for s in self.systems])
+        h = ctypes.c_void_p()
+        _chk(lib().sx_batch_create(ctypes.byref(h), arr, len(self.systems)), "sx_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sx_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def heun_step(self, S_in, S_out, params, step, stream=None):
+        n = len(self.systems)
+        a = (ctypes.c_void_p * n)(*[_dev_ptr(x, 3 * s.nsite).value for x, s in zip(S_in, self.systems)])
+        b = (ctypes.c_void_p * n)(*[_dev_ptr(x, 3 * s.nsite).value for x, s in zip(S_out, self.systems)])
+        return _chk(lib().sx_batch_heun_step(self.h, a, b, ctypes.byref(params), int(step), _stream(stream)),
+                    "sx_batch_heun_step")
 
 
 def sx_device_status(ctx, stream=None):

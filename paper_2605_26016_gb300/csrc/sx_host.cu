@@ -506,6 +506,7 @@ int sx_plan(sx_ctx *c, int backend, int prec) {
 #undef SX_TRY
   c->planned = 1;
   c->plan_version = c->ham_version;
+  ++c->plan_gen;
   return SX_OK;
 }
 
@@ -576,6 +577,79 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
   c->opt_scheme = best_scheme;
   if ((rc = stencil_set_scheme(c, best_scheme)) != SX_OK) return rc;
   return best_scheme;
+}
+
+struct sx_batch {
+  sx::StencilBatch *sb;
+  std::vector<sx_ctx *> ctxs;
+  std::vector<int> plan_gens;
+};
+
+int sx_batch_create(sx_batch **out, sx_ctx *const *ctxs, int nrep) {
+  if (!out) return set_error(SX_ERR_ARG, "null output");
+  *out = nullptr;
+  if (!ctxs || nrep < 1 || nrep > 65536) return set_error(SX_ERR_ARG, "a batch needs 1 .. 65536 contexts");
+  for (int r = 0; r < nrep; ++r) {
+    int rc = check_ready(ctxs[r]);
+    if (rc) return rc;
+    if (ctxs[r]->backend != SX_BACKEND_STENCIL)
+      return set_error(SX_ERR_UNSUPPORTED, "batched steps run on STENCIL plans only");
+    for (int q = 0; q < r; ++q)
+      if (ctxs[q] == ctxs[r]) return set_error(SX_ERR_ARG, "a context appears twice in the batch");
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(ctxs[0]->device);
+  for (int r = 0; r < nrep; ++r) {
+    if (stencil_scheme(ctxs[r]) != SX_STENCIL_TWO_PASS) {
+      const int rc = stencil_set_scheme(ctxs[r], SX_STENCIL_TWO_PASS);
+      if (rc != SX_OK || stencil_scheme(ctxs[r]) != SX_STENCIL_TWO_PASS) {
+        cudaSetDevice(cur);
+        return rc != SX_OK ? rc : set_error(SX_ERR_OOM, "two-pass workspace of a batched context");
+      }
+    }
+  }
+  sx::StencilBatch *sb = nullptr;
+  const int rc = stencil_batch_create(&sb, ctxs, nrep);
+  cudaSetDevice(cur);
+  if (rc != SX_OK) return rc;
+  sx_batch *b = new (std::nothrow) sx_batch();
+  if (!b) {
+    stencil_batch_free(sb);
+    return set_error(SX_ERR_OOM, "host allocation failed");
+  }
+  b->sb = sb;
+  b->ctxs.assign(ctxs, ctxs + nrep);
+  for (int r = 0; r < nrep; ++r) b->plan_gens.push_back(ctxs[r]->plan_gen);
+  *out = b;
+  return SX_OK;
+}
+
+void sx_batch_destroy(sx_batch *b) {
+  if (!b) return;
+  stencil_batch_free(b->sb);
+  delete b;
+}
+
+int sx_batch_heun_step(sx_batch *b, const double *const *S_in, double *const *S_out, const sx_llg_params *p,
+                       uint64_t step, void *stream) {
+  if (!b || !S_in || !S_out) return set_error(SX_ERR_ARG, "null argument");
+  const int nrep = (int)b->ctxs.size();
+  for (int r = 0; r < nrep; ++r) {
+    const sx_ctx *c = b->ctxs[r];
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (c->plan_gen != b->plan_gens[r] || stencil_scheme(c) != SX_STENCIL_TWO_PASS)
+      return set_error(SX_ERR_STATE, "a batched context was re-planned: create the batch again");
+    if ((rc = check_spin_ptr(S_in[r], "S_in")) || (rc = check_spin_ptr(S_out[r], "S_out"))) return rc;
+    if (overlaps(S_in[r], S_out[r], 3 * (size_t)c->geo.nsite * sizeof(double)))
+      return set_error(SX_ERR_ARG, "S_in and S_out of a replica overlap");
+  }
+  HeunConst h;
+  int rc = make_heun_const(b->ctxs[0], p, h);
+  if (rc) return rc;
+  cudaError_t e = stencil_batch_step(b->sb, S_in, S_out, h, step, (cudaStream_t)stream);
+  return e == cudaSuccess ? SX_OK : cuda_error(e, "batched Heun step");
 }
 
 int sx_device_status(sx_ctx *c, void *stream) {

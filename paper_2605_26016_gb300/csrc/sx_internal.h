@@ -140,6 +140,7 @@ struct sx_ctx {
   // plan
   int planned;
   int plan_version;
+  int plan_gen;  // incremented by every plan and every workspace change (stale-pointer guard)
   int backend, prec;
   int device;
   sx::OnSite onsite;
@@ -187,6 +188,12 @@ bool stencil_persistent_ok(const sx_ctx *c);
 cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S1, const HeunConst &h,
                                           uint64_t step0, int nsteps, cudaStream_t st);
 int stencil_check_error(const sx_ctx *c);
+// batches of replicas sharing one coupling table (two-pass stencil plans)
+struct StencilBatch;
+int stencil_batch_create(StencilBatch **out, sx_ctx *const *ctxs, int nrep);
+void stencil_batch_free(StencilBatch *b);
+cudaError_t stencil_batch_step(StencilBatch *b, const double *const *S_in, double *const *S_out, const HeunConst &h,
+                               uint64_t step, cudaStream_t st);
 cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
 // fields of `count` spin fields stride doubles apart (S, S + stride, ...) into b, b + stride, ... in one launch
 cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int count, long long stride,

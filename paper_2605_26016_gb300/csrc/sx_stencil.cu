@@ -270,8 +270,8 @@ __device__ __forceinline__ void shift_acc(Acc3 (&acc)[F::NSUB][2 * F::R + 1]) {
 
 // In-plane part of the global index of the load-region sites this thread stages
 // (x and y wrapped once here; the plane term is added per z step).
-template <int NLOAD, int NT, int SN, int LX, int LY>
-__device__ __forceinline__ void load_offsets(const StencilArgs &p, int xs, int ys, int tid, long long (&off)[NLOAD],
+template <int NLOAD, int NT, int SN, int LX, int LY, class GEO>
+__device__ __forceinline__ void load_offsets(const GEO &p, int xs, int ys, int tid, long long (&off)[NLOAD],
                                              unsigned &okmask) {
   okmask = 0u;
 #pragma unroll
@@ -292,8 +292,8 @@ __device__ __forceinline__ void load_offsets(const StencilArgs &p, int xs, int y
 }
 
 // Issue the zero-filling async copies of plane q into the FP64 staging area.
-template <int NLOAD, int NT, int SN>
-__device__ __forceinline__ void issue_plane(const StencilArgs &p, const double *__restrict__ S, int q, int tid,
+template <int NLOAD, int NT, int SN, class GEO>
+__device__ __forceinline__ void issue_plane(const GEO &p, const double *__restrict__ S, int q, int tid,
                                             const long long (&off)[NLOAD], unsigned okmask, double *stage) {
   bool zok = true;
   const int gz = wrap_axis(q, p.nz, p.pz, zok);
@@ -526,8 +526,8 @@ struct PassIO {
 };
 
 // FP32 planes of S~ straight into the float4 ring (4-byte zero-filling copies)
-template <int NLOAD, int NT, int SN>
-__device__ __forceinline__ void issue_plane_f32(const StencilArgs &p, const float *__restrict__ S, int q, int tid,
+template <int NLOAD, int NT, int SN, class GEO>
+__device__ __forceinline__ void issue_plane_f32(const GEO &p, const float *__restrict__ S, int q, int tid,
                                                 const long long (&off)[NLOAD], unsigned okmask, float4 *dst) {
   bool zok = true;
   const int gz = wrap_axis(q, p.nz, p.pz, zok);
@@ -553,9 +553,11 @@ __device__ __forceinline__ void issue_plane_f32(const StencilArgs &p, const floa
 }
 
 // One segment: the output columns of the 32 x BY tile at (x0, y0), planes z0 .. z0 + tzc - 1,
-// of image img.
-template <int FID, int MODE>
-__device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, const PassIO &io,
+// of image img.  p carries the couplings and constants, gg the lattice geometry (nx .. pz,
+// nsite) and the noise replica index: the launch arguments themselves for one system, a
+// per-replica record in a batch.
+template <int FID, int MODE, class GEO>
+__device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg, int onsite, const PassIO &io,
                                              unsigned char *smem_raw, int img, int x0, int y0, int z0, int tzc) {
   using F = Family<FID>;
   using g = GF<F>;
@@ -567,13 +569,13 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, c
   const double *Sin = io.S + img * io.istride;
   double *bout = io.b + img * io.istride;
   const int cx = x0 + tx, cy = y0 + ty;
-  const bool mine = cx < p.nx && cy < p.ny;
-  const long long plane = (long long)p.ny * p.nx, subvol = (long long)p.nz * plane;
+  const bool mine = cx < gg.nx && cy < gg.ny;
+  const long long plane = (long long)gg.ny * gg.nx, subvol = (long long)gg.nz * plane;
   Acc3 acc[NS][2 * R + 1];
   zero_acc<F>(acc);
   long long off[g::NLOAD];
   unsigned okmask;
-  load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(p, x0 - R, y0 - R, tid, off, okmask);
+  load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(gg, x0 - R, y0 - R, tid, off, okmask);
   const int niter = tzc + 2 * R;
   // corrector: S^n and f0 of the next output plane, loaded one plane ahead so the
   // global-load latency hides behind a plane of field work
@@ -584,12 +586,12 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, c
       if (mine && cz < z0 + tzc) {
 #pragma unroll
         for (int a = 0; a < NS; ++a) {
-          const long long i = a * subvol + cz * plane + (long long)cy * p.nx + cx;
+          const long long i = a * subvol + cz * plane + (long long)cy * gg.nx + cx;
 #pragma unroll
           for (int m = 0; m < 3; ++m) {
-            nS[a][m] = io.S[m * p.nsite + i];
-            nf[a][m] = io.f0[m * p.nsite + i];
-            ne[a][m] = p.thermal ? io.eta[m * p.nsite + i] : 0.0f;
+            nS[a][m] = io.S[m * gg.nsite + i];
+            nf[a][m] = io.f0[m * gg.nsite + i];
+            ne[a][m] = p.thermal ? io.eta[m * gg.nsite + i] : 0.0f;
           }
         }
       }
@@ -597,9 +599,9 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, c
   };
   prefetch(z0);
   if constexpr (MODE == PASS_CORR)
-    issue_plane_f32<g::NLOAD, g::NT, g::SN>(p, io.St, z0 - R, tid, off, okmask, sn);
+    issue_plane_f32<g::NLOAD, g::NT, g::SN>(gg, io.St, z0 - R, tid, off, okmask, sn);
   else
-    issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, z0 - R, tid, off, okmask, stage);
+    issue_plane<g::NLOAD, g::NT, g::SN>(gg, Sin, z0 - R, tid, off, okmask, stage);
   cp_commit();
   for (int k = 0; k < niter; ++k) {
     const int q = z0 - R + k;
@@ -608,10 +610,10 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, c
     if constexpr (MODE == PASS_CORR) {
       __syncthreads();  // every thread's copies of plane q have landed
       if (k + 1 < niter)
-        issue_plane_f32<g::NLOAD, g::NT, g::SN>(p, io.St, q + 1, tid, off, okmask, sn + ((k + 1) & 1) * g::SN);
+        issue_plane_f32<g::NLOAD, g::NT, g::SN>(gg, io.St, q + 1, tid, off, okmask, sn + ((k + 1) & 1) * g::SN);
     } else {
       convert_plane<g::NLOAD, g::NT, g::SN>(stage, buf, tid);
-      if (k + 1 < niter) issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, q + 1, tid, off, okmask, stage);
+      if (k + 1 < niter) issue_plane<g::NLOAD, g::NT, g::SN>(gg, Sin, q + 1, tid, off, okmask, stage);
     }
     cp_commit();
     if constexpr (MODE != PASS_CORR) __syncthreads();
@@ -628,21 +630,21 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, c
         float v[3] = {acc[a][0].xy.x, acc[a][0].xy.y, acc[a][0].z};
         const float4 c4 = cq[(((k - R) % (R + 1)) * NS + a) * g::NT + tid];
         const float s[3] = {c4.x, c4.y, c4.z};
-        const long long i = a * subvol + c * plane + (long long)cy * p.nx + cx;
+        const long long i = a * subvol + c * plane + (long long)cy * gg.nx + cx;
         if constexpr (MODE == PASS_FIELD) {
           if (onsite) onsite32(p, a, s, v);
           bout[i] = (double)v[0];
-          bout[p.nsite + i] = (double)v[1];
-          bout[2 * p.nsite + i] = (double)v[2];
+          bout[gg.nsite + i] = (double)v[1];
+          bout[2 * gg.nsite + i] = (double)v[2];
         } else {
           onsite32(p, a, s, v);
           float e0 = 0.f, e1 = 0.f, e2 = 0.f;
           if constexpr (MODE == PASS_PRED) {
             if (p.thermal) {
-              normals3(p.seed, p.replica, (unsigned long long)i, io.step, e0, e1, e2);
+              normals3(p.seed, gg.replica, (unsigned long long)i, io.step, e0, e1, e2);
               io.eta[i] = e0;
-              io.eta[p.nsite + i] = e1;
-              io.eta[2 * p.nsite + i] = e2;
+              io.eta[gg.nsite + i] = e1;
+              io.eta[2 * gg.nsite + i] = e2;
             }
           } else {
             e0 = ne[a][0];
@@ -659,18 +661,18 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, int onsite, c
             float r = rsqrtf(n2);
             r = r * fmaf(-0.5f * n2, r * r, 1.5f);
             io.St_out[i] = x[0] * r;
-            io.St_out[p.nsite + i] = x[1] * r;
-            io.St_out[2 * p.nsite + i] = x[2] * r;
+            io.St_out[gg.nsite + i] = x[1] * r;
+            io.St_out[2 * gg.nsite + i] = x[2] * r;
             io.f0[i] = f[0];
-            io.f0[p.nsite + i] = f[1];
-            io.f0[2 * p.nsite + i] = f[2];
+            io.f0[gg.nsite + i] = f[1];
+            io.f0[2 * gg.nsite + i] = f[2];
           } else {
             const float d[3] = {p.hdt * (nf[a][0] + f[0]), p.hdt * (nf[a][1] + f[1]), p.hdt * (nf[a][2] + f[2])};
             double o[3];
             renormalise64(nS[a], d, o);
             io.Sout[i] = o[0];
-            io.Sout[p.nsite + i] = o[1];
-            io.Sout[2 * p.nsite + i] = o[2];
+            io.Sout[gg.nsite + i] = o[1];
+            io.Sout[2 * gg.nsite + i] = o[2];
           }
         }
       }
@@ -694,7 +696,7 @@ __device__ __forceinline__ void run_scheduled(const StencilArgs &p, int onsite, 
   while (u < uend) {  // uniform over the block
     const int col = (int)(u / p.nz), z = (int)(u - (long long)col * p.nz);
     const int len = (int)min((long long)(p.nz - z), uend - u);
-    pass_segment<FID, MODE>(p, onsite, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+    pass_segment<FID, MODE>(p, p, onsite, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
     u += len;
     __syncthreads();  // shared memory is reused by the next segment
   }
@@ -710,7 +712,7 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
   } else {
     const int img = blockIdx.z / io.nzc, zc = blockIdx.z - img * io.nzc;
     const int z0 = zc * p.tz;
-    pass_segment<FID, MODE>(p, onsite, io, smem_raw, img, blockIdx.x * 32, blockIdx.y * F::BY, z0,
+    pass_segment<FID, MODE>(p, p, onsite, io, smem_raw, img, blockIdx.x * 32, blockIdx.y * F::BY, z0,
                             min(p.tz, p.nz - z0));
   }
 }
@@ -773,6 +775,69 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
   }
 }
 
+// ------------------------------------------------------------------ batches of replicas
+
+// One replica of a batch: its geometry, its noise replica index, the first global
+// column-plane unit it owns, and its state and two-pass workspace.
+struct SGeo {
+  int nx, ny, nz, px, py, pz;
+  long long nsite;
+  unsigned replica;
+};
+struct BatchRep {
+  SGeo g;
+  long long u0;
+  const double *S;
+  double *Sout;
+  float *St, *f0, *eta;
+};
+
+// One two-pass stage over a batch of replicas that share the couplings in p: CTA k
+// walks the global column-plane units of schedule entry k, which may span replicas
+// (units are replica-major; within a replica u = column * nz + z).
+template <int FID, int MODE>
+__global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
+    k_batch_pass(const StencilArgs p, const BatchRep *__restrict__ reps, int nrep, const int2 *__restrict__ sched,
+                 unsigned long long step) {
+  using F = Family<FID>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 e = sched[blockIdx.x];
+  long long u = e.x;
+  const long long uend = (long long)e.x + e.y;
+  int lo = 0, hi = nrep - 1;  // last replica with u0 <= u
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (reps[mid].u0 <= u)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  int r = lo;
+  while (u < uend) {  // uniform over the block
+    while (r + 1 < nrep && reps[r + 1].u0 <= u) ++r;
+    const SGeo gg = reps[r].g;
+    PassIO io;
+    io.S = reps[r].S;
+    io.St = reps[r].St;
+    io.St_out = reps[r].St;
+    io.b = nullptr;
+    io.f0 = reps[r].f0;
+    io.eta = reps[r].eta;
+    io.Sout = reps[r].Sout;
+    io.nzc = 1;
+    io.istride = 0;
+    io.step = step;
+    io.sched = nullptr;
+    const long long ul = u - reps[r].u0;
+    const int ncx = (gg.nx + 31) / 32;
+    const int col = (int)(ul / gg.nz), z = (int)(ul - (long long)col * gg.nz);
+    const int len = (int)min((long long)(gg.nz - z), uend - u);
+    pass_segment<FID, MODE>(p, gg, 1, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+    u += len;
+    __syncthreads();  // shared memory is reused by the next segment
+  }
+}
+
 // ------------------------------------------------------------------ planning
 
 namespace {
@@ -815,6 +880,10 @@ cudaError_t set_smem() {
                                        (int)G<Family<FID>>::SMEM);
   if (e != cudaSuccess) return e;
   for (auto fn : {k_stencil_pass<FID, PASS_FIELD>, k_stencil_pass<FID, PASS_PRED>, k_stencil_pass<FID, PASS_CORR>}) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GF<Family<FID>>::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  for (auto fn : {k_batch_pass<FID, PASS_PRED>, k_batch_pass<FID, PASS_CORR>}) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GF<Family<FID>>::SMEM);
     if (e != cudaSuccess) return e;
   }
@@ -919,6 +988,50 @@ cudaError_t launch_persistent(const StencilPlan &sp, const StencilArgs &a, doubl
 // units u = column * nz + z are cut into contiguous ranges, one per CTA, so that the
 // largest cost (planes + 2R warm-up planes per column segment) is as small as the
 // greedy packing allows.
+// Same packing over several replicas whose units follow each other (replica r: ncol[r]
+// columns of nz[r] planes each, starting at global unit off[r]).
+std::vector<int2> balanced_schedule_multi(const std::vector<long long> &ncol, const std::vector<int> &nz, int R,
+                                          long long slots) {
+  const int nr = (int)ncol.size();
+  std::vector<long long> off(nr + 1, 0);
+  for (int r = 0; r < nr; ++r) off[r + 1] = off[r] + ncol[r] * nz[r];
+  const long long U = off[nr], w = 2LL * R;
+  long long colsum = 0;
+  for (int r = 0; r < nr; ++r) colsum += ncol[r];
+  auto pack = [&](long long B, std::vector<int2> *out) {
+    long long u = 0, n = 0;
+    int r = 0;
+    while (u < U) {
+      const long long u0 = u;
+      long long cost = 0;
+      while (u < U) {
+        while (u >= off[r + 1]) ++r;
+        const long long avail = nz[r] - (u - off[r]) % nz[r];
+        if (cost + w + 1 > B) break;
+        const long long t = std::min(avail, B - cost - w);
+        cost += w + t;
+        u += t;
+        if (t < avail) break;
+      }
+      if (out) out->push_back(make_int2((int)u0, (int)(u - u0)));
+      ++n;
+    }
+    return n;
+  };
+  long long lo = std::max<long long>(w + 1, (U + slots - 1) / slots + w);
+  long long hi = std::max(lo, U + w * colsum);  // one CTA taking everything always fits
+  while (lo < hi) {
+    const long long mid = (lo + hi) / 2;
+    if (pack(mid, nullptr) <= slots)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  std::vector<int2> out;
+  pack(lo, &out);
+  return out;
+}
+
 std::vector<int2> balanced_schedule(long long ncol, int nz, int R, long long slots) {
   const long long U = ncol * nz, w = 2LL * R;
   auto pack = [&](long long B, std::vector<int2> *out) {
@@ -1154,6 +1267,7 @@ int stencil_set_scheme(sx_ctx *c, int scheme) {
     cudaFree(sp->d_eta);
     sp->d_St = sp->d_f0 = sp->d_eta = nullptr;
   }
+  if (sp->scheme != scheme) ++c->plan_gen;  // workspace allocated or freed
   sp->scheme = scheme;
   c->launches_per_step = scheme == SX_STENCIL_TWO_PASS ? 2 : 1;
   return SX_OK;
@@ -1232,6 +1346,119 @@ cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S
     case FAM_SC26_ISO: return launch_persistent<FAM_SC26_ISO>(sp, a, S0, S1, nsteps, step0, st);
     case FAM_SC26_TEN: return launch_persistent<FAM_SC26_TEN>(sp, a, S0, S1, nsteps, step0, st);
     default: return launch_persistent<FAM_BCC4>(sp, a, S0, S1, nsteps, step0, st);
+  }
+}
+
+// ------------------------------------------------------------------ batches (host)
+
+struct StencilBatch {
+  int nrep = 0, family = -1;
+  const sx_ctx *proto = nullptr;
+  std::vector<BatchRep> h_reps;
+  BatchRep *d_reps = nullptr;
+  int2 *d_sched = nullptr;
+  int nsched = 0;
+};
+
+namespace {
+bool same_couplings(const StencilArgs &a, const StencilArgs &b) {
+  return memcmp(a.Jiso, b.Jiso, sizeof(a.Jiso)) == 0 && memcmp(a.Jt, b.Jt, sizeof(a.Jt)) == 0 &&
+         memcmp(a.zee, b.zee, sizeof(a.zee)) == 0 && memcmp(a.twoK, b.twoK, sizeof(a.twoK)) == 0 &&
+         memcmp(a.axis, b.axis, sizeof(a.axis)) == 0 && memcmp(a.inv_mm, b.inv_mm, sizeof(a.inv_mm)) == 0;
+}
+
+template <int FID>
+cudaError_t launch_batch(const StencilBatch &b, const StencilArgs &a, unsigned long long step, cudaStream_t st) {
+  using g = GF<Family<FID>>;
+  const dim3 grid(b.nsched), block(32, Family<FID>::BY);
+  k_batch_pass<FID, PASS_PRED><<<grid, block, g::SMEM, st>>>(a, b.d_reps, b.nrep, b.d_sched, step);
+  k_batch_pass<FID, PASS_CORR><<<grid, block, g::SMEM, st>>>(a, b.d_reps, b.nrep, b.d_sched, step);
+  return cudaGetLastError();
+}
+}  // namespace
+
+int stencil_batch_create(StencilBatch **out, sx_ctx *const *ctxs, int nrep) {
+  StencilBatch *b = new (std::nothrow) StencilBatch();
+  if (!b) return set_error(SX_ERR_OOM, "host allocation failed");
+  b->nrep = nrep;
+  b->proto = ctxs[0];
+  b->family = ctxs[0]->stencil->family;
+  std::vector<long long> ncol(nrep);
+  std::vector<int> nz(nrep);
+  long long u0 = 0;
+  const int BY = b->family == FAM_BCC4 ? Family<FAM_BCC4>::BY : Family<FAM_SC6_ISO>::BY;
+  const int R = b->family == FAM_BCC4 ? Family<FAM_BCC4>::R : Family<FAM_SC6_ISO>::R;
+  for (int r = 0; r < nrep; ++r) {
+    const sx_ctx *c = ctxs[r];
+    if (c->stencil->family != b->family || !same_couplings(c->stencil->base, ctxs[0]->stencil->base)) {
+      delete b;
+      return set_error(SX_ERR_ARG, "batched replicas must share the lattice family and every coupling");
+    }
+    if (c->device != ctxs[0]->device) {
+      delete b;
+      return set_error(SX_ERR_ARG, "batched replicas must be planned on one device");
+    }
+    BatchRep rep;
+    memset(&rep, 0, sizeof(rep));
+    rep.g.nx = c->geo.nx;
+    rep.g.ny = c->geo.ny;
+    rep.g.nz = c->geo.nz;
+    rep.g.px = c->geo.px;
+    rep.g.py = c->geo.py;
+    rep.g.pz = c->geo.pz;
+    rep.g.nsite = c->geo.nsite;
+    rep.u0 = u0;
+    rep.St = c->stencil->d_St;
+    rep.f0 = c->stencil->d_f0;
+    rep.eta = c->stencil->d_eta;
+    ncol[r] = (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY);
+    nz[r] = c->geo.nz;
+    u0 += ncol[r] * nz[r];
+    b->h_reps.push_back(rep);
+  }
+  if (u0 >= (1LL << 31)) {
+    delete b;
+    return set_error(SX_ERR_UNSUPPORTED, "batch too large for one schedule (2^31 column-plane units)");
+  }
+  const StencilPlan &sp0 = *ctxs[0]->stencil;
+  std::vector<int2> sch = balanced_schedule_multi(ncol, nz, R, (long long)sp0.nsm * sp0.occ_field);
+  b->nsched = (int)sch.size();
+  cudaError_t e = cudaMalloc(&b->d_reps, nrep * sizeof(BatchRep));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_sched, sch.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_sched, sch.data(), sch.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    stencil_batch_free(b);
+    return cuda_error(e, "batch plan");
+  }
+  *out = b;
+  return SX_OK;
+}
+
+void stencil_batch_free(StencilBatch *b) {
+  if (!b) return;
+  cudaFree(b->d_reps);
+  cudaFree(b->d_sched);
+  delete b;
+}
+
+cudaError_t stencil_batch_step(StencilBatch *b, const double *const *S_in, double *const *S_out, const HeunConst &h,
+                               uint64_t step, cudaStream_t st) {
+  for (int r = 0; r < b->nrep; ++r) {
+    b->h_reps[r].S = S_in[r];
+    b->h_reps[r].Sout = S_out[r];
+    b->h_reps[r].g.replica = h.replica + (uint32_t)r;
+  }
+  // pageable source: staged by the driver before this call returns, ordered on the stream
+  cudaError_t e =
+      cudaMemcpyAsync(b->d_reps, b->h_reps.data(), b->nrep * sizeof(BatchRep), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  const StencilArgs a = heun_args(b->proto, h, step);
+  switch (b->family) {
+    case FAM_SC6_ISO: return launch_batch<FAM_SC6_ISO>(*b, a, step, st);
+    case FAM_SC6_TEN: return launch_batch<FAM_SC6_TEN>(*b, a, step, st);
+    case FAM_SC26_ISO: return launch_batch<FAM_SC26_ISO>(*b, a, step, st);
+    case FAM_SC26_TEN: return launch_batch<FAM_SC26_TEN>(*b, a, step, st);
+    default: return launch_batch<FAM_BCC4>(*b, a, step, st);
   }
 }
 

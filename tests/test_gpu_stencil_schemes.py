@@ -97,3 +97,36 @@ def test_persistent_multi_step_launch_equals_separate_steps(name, n, pbc, therma
         torch.cuda.synchronize()
         sx.sx_device_status(s.ctx)
         assert torch.equal(A, bufs[nsteps & 1])
+
+
+@pytest.mark.parametrize("scheme", ["fused", "two_pass"])
+def test_heun_step_out_is_cuda_graph_capturable(scheme):
+    # sx_llg_heun_step_out only enqueues kernels on the given stream (no synchronisation, no allocation
+    # after planning), so a loop of steps can be captured once and replayed; the replay equals eager steps
+    n = (48, 40, 36)
+    s, w = sx.system_from_workload("sc_j123_dmi", n)
+    sx.sx_set_stencil_scheme(s.ctx, scheme)
+    s.plan("stencil", "fp32")
+    S0 = torch.from_numpy(random_spins(1, n, 12)).cuda()
+    A, B = S0.clone(), torch.empty_like(S0)
+    p = sx.llg_params(w["dt"], w["alpha"], 0.0)
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        sx.sx_llg_heun_step_out(s.ctx, A, B, p, 0, s.nsite, stream=stream)  # warm-up outside capture
+        sx.sx_llg_heun_step_out(s.ctx, B, A, p, 1, s.nsite, stream=stream)
+    stream.synchronize()
+    A.copy_(S0)
+    with torch.cuda.graph(g, stream=stream):
+        sx.sx_llg_heun_step_out(s.ctx, A, B, p, 0, s.nsite, stream=stream)
+        sx.sx_llg_heun_step_out(s.ctx, B, A, p, 1, s.nsite, stream=stream)
+    A.copy_(S0)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    ref, tmp = S0.clone(), torch.empty_like(S0)
+    for _ in range(3):
+        sx.sx_llg_heun_step_out(s.ctx, ref, tmp, p, 0, s.nsite)
+        sx.sx_llg_heun_step_out(s.ctx, tmp, ref, p, 1, s.nsite)
+    torch.cuda.synchronize()
+    assert torch.equal(A, ref)
