@@ -14,7 +14,7 @@ import pytest
 import oracle
 import paper_2605_26016_gb300 as sx
 from oracle.models import oracle_model
-from workloads import SC_POS, cubic_cell, random_spins
+from workloads import SC_POS, cubic_cell, random_spins, random_spins_torch
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -276,3 +276,31 @@ def test_full_size_step_sampled_heun(name, n):
     assert normwise(got[:, sites] - S0, ref.T - S0) <= TOL_STEP["fp32"]
     norms = out.view(3, -1).pow(2).sum(0).sqrt()
     assert (norms - 1).abs().max().item() < 1e-13
+
+
+def test_full_size_sc_1024_step_sampled_heun():
+    # the billion-spin configuration (SC 1024^3, J1-J3 + interfacial DMI, T = 50 K) in the launch
+    # bench.py times for it (stencil, two-pass scheme, one stochastic step out of place), checked at
+    # sampled sites against the oracle's site-by-site Heun step; the input comes from a seeded
+    # device generator (1.07e9 spins)
+    n = (1024, 1024, 1024)
+    free = torch.cuda.mem_get_info()[0]
+    if free < 120 * 2 ** 30:
+        pytest.skip("needs ~120 GB of free device memory")
+    s, w = sx.system_from_workload("sc_j123_dmi", n)
+    sx.sx_set_stencil_scheme(s.ctx, "two_pass")
+    s.plan("stencil", "fp32")
+    Sd = random_spins_torch(1, n, w["seed"])
+    out = torch.empty_like(Sd)
+    sx.sx_llg_heun_step_out(s.ctx, Sd, out, sx.llg_params(w["dt"], w["alpha"], w["T"], seed=w["seed"]), 3, s.nsite)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(2)
+    sites = np.unique(np.concatenate([rng.choice(s.nsite, 400, replace=False), [0, s.nsite - 1, 1023, 1024 ** 2]]))
+    idx = torch.from_numpy(sites).cuda()
+    got = out.view(3, -1)[:, idx].cpu().numpy()
+    S = Sd.cpu().numpy()
+    del out
+    m, _ = oracle_model("sc_j123_dmi", n, build=False)
+    ref = m.heun_sites(S, sites, w["dt"], w["alpha"], T=w["T"], seed=w["seed"], replica=0, step=3)
+    S0 = S.reshape(3, -1)[:, sites]
+    assert normwise(got - S0, ref.T - S0) <= TOL_STEP["fp32"]

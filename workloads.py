@@ -129,3 +129,26 @@ def nlerp_chain(A, B, nimg, jitter=0.0, seed=0):
             X = X + jitter * rng.standard_normal(A.shape)
         out[n] = X / np.sqrt((X * X).sum(0))
     return np.ascontiguousarray(out)
+
+
+def random_spins_torch(nsub, n, seed, device="cuda"):
+    """Uniform random unit spins generated on a torch device (for lattices too large to generate in
+    numpy in reasonable time), shape (3, nsub, nz, ny, nx), float64: z = 2u - 1, phi = 2 pi v with u, v
+    from torch's seeded Philox generator of that device.  Not the same numbers as random_spins."""
+    import torch
+    nx, ny, nz = n
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    m = nsub * nx * ny * nz
+    S = torch.empty((3, m), dtype=torch.float64, device=device)
+    u = torch.rand(m, generator=g, device=device, dtype=torch.float64)
+    S[2] = 2.0 * u - 1.0
+    r = torch.sqrt(torch.clamp(1.0 - S[2] * S[2], min=0.0))
+    u = torch.rand(m, generator=g, device=device, dtype=torch.float64)
+    u.mul_(2.0 * np.pi)
+    torch.cos(u, out=S[0])
+    S[0].mul_(r)
+    torch.sin(u, out=S[1])
+    S[1].mul_(r)
+    del u, r
+    return S.view(3, nsub, nz, ny, nx)
