@@ -8,12 +8,16 @@
 //   v <- max(v.f, 0) / (f.f) f          (dot products over the whole system)
 //   S <- R_exp(S, dt v + dt^2/2 f)
 // The two global sums are reduced on the device and the step coefficient stays
-// on the device, so an iteration needs no host synchronisation.
+// on the device, so an iteration needs no host synchronisation.  FP64 plans do
+// every step in FP64; FP32-field plans keep v and f in FP32, reduce in FP32
+// per warp and FP64 per block, and apply the retraction in FP32 with the state
+// sum and renormalisation in FP64.
 // Damped LLG: normalised Heun steps at T = 0 with the given damping.
 // Convergence: max_i |S_i x b_i| below tol, checked every check_every iterations.
 #include <math.h>
 #include <string.h>
 
+#include "sx_device.cuh"
 #include "sx_internal.h"
 
 namespace sx {
@@ -34,34 +38,55 @@ __device__ __forceinline__ double block_sum_d(double v, double *sm) {
   return r;
 }
 
-// tangent force, velocity half-update and per-block partial sums of v.f and f.f
+// Sum of two per-thread values of type R over the block: shuffle trees in R,
+// warp sums widened and added in FP64 by thread 0 (written to out[0], out[1]).
+template <typename R>
+__device__ __forceinline__ void block_sum2(R a, R b, double *out) {
+  __shared__ double red[2][kMinThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = cvt<double>(a);
+    red[1][threadIdx.x >> 5] = cvt<double>(b);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int w = 0; w < kMinThreads / 32; ++w) {
+      x += red[0][w];
+      y += red[1][w];
+    }
+    out[0] = x;
+    out[1] = y;
+  }
+}
+
+// tangent force, velocity half-update and per-block partial sums of v.f and f.f.
+// R: arithmetic and storage type of v and f (FP64 plans: double; FP32-field plans: float).
+template <typename R>
 __global__ void __launch_bounds__(kMinThreads) k_vp_force(const double *__restrict__ S, const double *__restrict__ b,
-                                                          double *__restrict__ v, double *__restrict__ fprev,
-                                                          int first, double dt, long long N,
-                                                          double *__restrict__ partial) {
-  __shared__ double sm[kMinThreads];
-  double p = 0.0, F2 = 0.0;
+                                                          R *__restrict__ v, R *__restrict__ fprev, int first, R hdt,
+                                                          long long N, double *__restrict__ partial) {
+  R p = 0, F2 = 0;
   for (long long i = (long long)blockIdx.x * kMinThreads + threadIdx.x; i < N;
        i += (long long)gridDim.x * kMinThreads) {
-    const double s0 = S[i], s1 = S[N + i], s2 = S[2 * N + i];
-    const double b0 = b[i], b1 = b[N + i], b2 = b[2 * N + i];
-    const double d = b0 * s0 + b1 * s1 + b2 * s2;
-    const double f[3] = {b0 - d * s0, b1 - d * s1, b2 - d * s2};
+    const R s0 = cvt<R>(S[i]), s1 = cvt<R>(S[N + i]), s2 = cvt<R>(S[2 * N + i]);
+    const R b0 = cvt<R>(b[i]), b1 = cvt<R>(b[N + i]), b2 = cvt<R>(b[2 * N + i]);
+    const R d = b0 * s0 + b1 * s1 + b2 * s2;
+    const R f[3] = {b0 - d * s0, b1 - d * s1, b2 - d * s2};
     for (int k = 0; k < 3; ++k) {
       const long long j = k * N + i;
-      const double vk = first ? 0.0 : v[j] + 0.5 * dt * (fprev[j] + f[k]);
+      const R vk = first ? (R)0 : v[j] + hdt * (fprev[j] + f[k]);
       v[j] = vk;
       fprev[j] = f[k];
       p += vk * f[k];
       F2 += f[k] * f[k];
     }
   }
-  p = block_sum_d(p, sm);
-  F2 = block_sum_d(F2, sm);
-  if (threadIdx.x == 0) {
-    partial[2 * blockIdx.x] = p;
-    partial[2 * blockIdx.x + 1] = F2;
-  }
+  block_sum2<R>(p, F2, partial + 2 * blockIdx.x);
 }
 
 __global__ void __launch_bounds__(kMinThreads) k_vp_coef(const double *__restrict__ partial, int nb,
@@ -74,29 +99,70 @@ __global__ void __launch_bounds__(kMinThreads) k_vp_coef(const double *__restric
   }
   p = block_sum_d(p, sm);
   F2 = block_sum_d(F2, sm);
-  if (threadIdx.x == 0) coef[0] = (p > 0.0 && F2 > 0.0) ? p / F2 : 0.0;
+  if (threadIdx.x == 0) {
+    const double c = (p > 0.0 && F2 > 0.0) ? p / F2 : 0.0;
+    coef[0] = c;
+    reinterpret_cast<float *>(coef + 1)[0] = (float)c;  // the same coefficient for FP32 plans
+  }
 }
 
-__global__ void __launch_bounds__(kMinThreads) k_vp_update(double *__restrict__ S, double *__restrict__ v,
-                                                           const double *__restrict__ f,
-                                                           const double *__restrict__ coef, double dt,
-                                                           long long N) {
-  const long long i = (long long)blockIdx.x * kMinThreads + threadIdx.x;
-  if (i >= N) return;
-  const double c = coef[0];
-  double u[3], s[3] = {S[i], S[N + i], S[2 * N + i]};
-  for (int k = 0; k < 3; ++k) {
-    const double fk = f[k * N + i];
-    v[k * N + i] = c * fk;
-    u[k] = dt * c * fk + 0.5 * dt * dt * fk;
-  }
+// S <- R_exp(S, u), u tangent: FP64 plans in FP64 (libm cos, sin)
+__device__ __forceinline__ void vp_retract(double s[3], const double u[3]) {
   const double a = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   if (a > 0.0) {
     const double cs = cos(a), sn = sin(a) / a;
     for (int k = 0; k < 3; ++k) s[k] = cs * s[k] + sn * u[k];
     const double r = rsqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
-    for (int k = 0; k < 3; ++k) S[k * N + i] = s[k] * r;
+    for (int k = 0; k < 3; ++k) s[k] *= r;
   }
+}
+
+// FP32 arithmetic, FP64 state: d = (cos a - 1) s + (sin a / a) u with cos a - 1 = -2 sin^2(a/2),
+// S' = N[S + d] in FP64
+__device__ __forceinline__ void vp_retract(double s[3], const float u[3]) {
+  const float a = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  if (a > 0.0f) {
+    const float sf[3] = {f64_to_f32(s[0]), f64_to_f32(s[1]), f64_to_f32(s[2])};
+    const float h = sinf(0.5f * a);
+    const float c1 = -2.0f * h * h, sc = sinf(a) / a;
+    const float d[3] = {c1 * sf[0] + sc * u[0], c1 * sf[1] + sc * u[1], c1 * sf[2] + sc * u[2]};
+    const double s0[3] = {s[0], s[1], s[2]};
+    renormalise64(s0, d, s);
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kMinThreads) k_vp_update(double *__restrict__ S, R *__restrict__ v,
+                                                           const R *__restrict__ f, const double *__restrict__ coef,
+                                                           R dt, long long N) {
+  const long long i = (long long)blockIdx.x * kMinThreads + threadIdx.x;
+  if (i >= N) return;
+  R c;
+  if constexpr (sizeof(R) == 8)
+    c = coef[0];
+  else
+    c = reinterpret_cast<const float *>(coef + 1)[0];
+  const R hdt2 = (R)0.5 * dt * dt;
+  R u[3];
+  double s[3] = {S[i], S[N + i], S[2 * N + i]};
+  for (int k = 0; k < 3; ++k) {
+    const R fk = f[k * N + i];
+    v[k * N + i] = c * fk;
+    u[k] = dt * c * fk + hdt2 * fk;
+  }
+  vp_retract(s, u);
+  for (int k = 0; k < 3; ++k) S[k * N + i] = s[k];
+}
+
+template <typename R>
+cudaError_t vp_iteration(const sx_ctx *c, double *S, double *ws, int first, double dt, int nb, cudaStream_t st) {
+  const long long N = c->geo.nsite;
+  R *v = reinterpret_cast<R *>(ws), *fp = v + 3 * N;
+  double *part = ws + 6 * N, *coef = part + 2 * nb;
+  k_vp_force<R><<<nb, kMinThreads, 0, st>>>(S, c->d_field, v, fp, first, (R)(0.5 * dt), N, part);
+  k_vp_coef<<<1, kMinThreads, 0, st>>>(part, nb, coef);
+  k_vp_update<R><<<(unsigned)((N + kMinThreads - 1) / kMinThreads), kMinThreads, 0, st>>>(S, v, fp, coef, (R)dt, N);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -113,8 +179,6 @@ int minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p, in
     e = cudaMalloc(&c->d_min, (6 * (size_t)N + 2 * (size_t)nb + 8) * sizeof(double));
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc minimiser workspace");
   }
-  double *v = c->d_min, *fp = c->d_min ? c->d_min + 3 * N : nullptr;
-  double *part = c->d_min ? c->d_min + 6 * N : nullptr, *coef = part ? part + 2 * nb : nullptr;
   HeunConst h;
   memset(&h, 0, sizeof(h));
   h.dt = p->dt;
@@ -127,11 +191,8 @@ int minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p, in
     if (p->method == SX_MIN_VP) {
       e = field(c, cur, c->d_field, true, st);
       if (e != cudaSuccess) break;
-      k_vp_force<<<nb, kMinThreads, 0, st>>>(cur, c->d_field, v, fp, it == 0 ? 1 : 0, p->dt, N, part);
-      k_vp_coef<<<1, kMinThreads, 0, st>>>(part, nb, coef);
-      k_vp_update<<<(unsigned)((N + kMinThreads - 1) / kMinThreads), kMinThreads, 0, st>>>(cur, v, fp, coef, p->dt,
-                                                                                        N);
-      e = cudaGetLastError();
+      e = c->prec == SX_PREC_FP64 ? vp_iteration<double>(c, cur, c->d_min, it == 0 ? 1 : 0, p->dt, nb, st)
+                                  : vp_iteration<float>(c, cur, c->d_min, it == 0 ? 1 : 0, p->dt, nb, st);
     } else {
       e = step(c, cur, other, h, (uint64_t)it, st);
       double *t = cur;
