@@ -152,3 +152,21 @@ def random_spins_torch(nsub, n, seed, device="cuda"):
     S[1].mul_(r)
     del u, r
     return S.view(3, nsub, nz, ny, nx)
+
+
+CNN_CHANNELS = (10, 16, 16, 16, 3)
+
+
+def cnn_init_params(seed, channels=CNN_CHANNELS):
+    """Initial weights of the path proposer's four 3x3x3 convolutions: He-normal (std sqrt(2 / (27 c_in)))
+    from numpy's PCG64 seeded generator, the last layer scaled by 0.1 so that the untrained proposer stays
+    close to the interpolation; zero biases.  List of (w [out][in][3][3][3], b [out]) in float64."""
+    rng = np.random.default_rng(seed)
+    params = []
+    for l in range(len(channels) - 1):
+        ci, co = channels[l], channels[l + 1]
+        w = rng.standard_normal((co, ci, 3, 3, 3)) * np.sqrt(2.0 / (27 * ci))
+        if l == len(channels) - 2:
+            w *= 0.1
+        params.append((w, np.zeros(co)))
+    return params
