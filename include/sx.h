@@ -396,6 +396,103 @@ int sx_thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64_t 
  * out[6] = precision, out[7] = device kernel launches per Heun step. */
 int sx_plan_info(const sx_ctx *ctx, int64_t out[8]);
 
+/* ---------------------------------------------------------------------------
+ * Convolutional proposer of path chains.
+ *
+ * The string and GNEB methods ("Static optimization and minimum-energy
+ * paths") start from a chain of images between two endpoint states; the
+ * usual first chain is the site-wise geodesic interpolation.  The proposer is
+ * a small learned map that turns such an interpolated image into a better
+ * first guess of the converged image, trained on paths the path method has
+ * converged.  It is not part of the paper's method; the paper's geodesic
+ * interpolation stays the fallback (sx_cnn_interpolate).
+ *
+ * Model, for one sublattice on an n[0] x n[1] x n[2] grid with zero padding
+ * outside it: per site the input has 10 channels (interpolated image I,
+ * endpoint A, endpoint B, path coordinate s); four 3x3x3 convolutions with
+ * bias map 10 -> 16 -> 16 -> 16 -> 3 channels, ReLU after the first three;
+ * the proposal is P = N[I + Y] per site (Y the last convolution's output) and
+ * the training loss is L = mean over samples and sites of (1 - P . T), T the
+ * converged image.  Parameters (sx_cnn_num_params() = 19,491 FP32 values):
+ * per layer the weights [out][in][dz][dy][dx] (dz, dy, dx = -1, 0, 1 at index
+ * 0, 1, 2) then the biases, layers in order.  Inputs and hidden activations
+ * are stored in BF16 (round to nearest even of the FP32 value), weights are
+ * rounded to BF16 for the tensor-core convolutions, sums are FP32; the
+ * normalisation and the loss are FP64.
+ *
+ * Image layout: a sample is 3 planes of ncell doubles, [c][z][y][x], x
+ * fastest (the layout of sx_field for nsub = 1).  Packed inputs X are BF16
+ * bit patterns, [sample][z][y][x][16] (32 bytes per site, 16-byte aligned).
+ * All arrays are device memory owned by the caller unless stated.
+ * ------------------------------------------------------------------------- */
+typedef struct sx_cnn sx_cnn;
+
+typedef struct {
+  double lr;     /* step size */
+  double beta1;  /* first-moment decay, in [0, 1) */
+  double beta2;  /* second-moment decay, in [0, 1) */
+  double eps;    /* denominator offset, > 0 */
+} sx_adam_params;
+
+/* Number of parameters of the proposer (19,491). */
+int64_t sx_cnn_num_params(void);
+
+/* Create a proposer for grids of n[0] x n[1] x n[2] sites and batches of up to
+ * max_batch samples.  Allocates the parameters (zero), Adam moments,
+ * activations (96 B per site of max_batch samples), activation gradients
+ * (128 B per site), a packed-input buffer (32 B per site) and weight-gradient
+ * partials (about 110 KB per 16 x 16 x 8 block of sites); synchronises the
+ * device.  SX_ERR_ARG for n[k] outside 1..4096 or max_batch < 1. */
+int sx_cnn_create(sx_cnn **out, const int n[3], int max_batch);
+
+/* Release the proposer and its device memory (NULL is a no-op). */
+void sx_cnn_destroy(sx_cnn *h);
+
+/* Copy sx_cnn_num_params() parameters from host memory, reset the Adam state
+ * and rebuild the tensor-core operands.  Synchronises the device. */
+int sx_cnn_set_params(sx_cnn *h, const float *params_host);
+
+/* Copy the parameters to host memory.  Synchronises the device. */
+int sx_cnn_get_params(sx_cnn *h, float *params_host);
+
+/* Pack nb samples into X: sample b reads I + b*i_stride, A + b*ab_stride,
+ * B + b*ab_stride (each 3*ncell doubles; ab_stride = 0 shares one pair of
+ * endpoints) and s[b] (device array of nb doubles).  Strides count doubles;
+ * i_stride >= 3*ncell, ab_stride >= 0.  Asynchronous.  SX_ERR_ARG for null or
+ * misaligned pointers, nb outside 1..max_batch or bad strides. */
+int sx_cnn_pack(sx_cnn *h, const double *I, int64_t i_stride, const double *A, const double *B, int64_t ab_stride,
+                const double *s, int nb, uint16_t *X, void *stream);
+
+/* Proposals P (nb x 3 x ncell doubles, may equal I) of nb packed samples X
+ * with interpolated images I (nb x 3 x ncell).  Synchronises the stream;
+ * SX_ERR_TIMEOUT if a bounded tensor-core wait gave up. */
+int sx_cnn_forward(sx_cnn *h, const uint16_t *X, const double *I, int nb, double *P, void *stream);
+
+/* Loss of nb packed samples X with interpolated images I and targets T (each
+ * nb x 3 x ncell doubles) and its gradient with respect to every parameter:
+ * grad (device, sx_cnn_num_params() floats; NULL keeps it in the proposer for
+ * sx_cnn_adam_step) and *loss_host (may be NULL).  Weight gradients are
+ * reduced in FP64 in a fixed order (deterministic).  Synchronises the stream. */
+int sx_cnn_loss_grad(sx_cnn *h, const uint16_t *X, const double *I, const double *T, int nb, float *grad,
+                     double *loss_host, void *stream);
+
+/* One Adam update (Kingma and Ba) of the parameters with gradient grad
+ * (device; NULL = the proposer's own, from sx_cnn_loss_grad with grad NULL);
+ * rebuilds the tensor-core operands.  Asynchronous. */
+int sx_cnn_adam_step(sx_cnn *h, const float *grad, const sx_adam_params *p, void *stream);
+
+/* Geodesic interpolation of a chain (nimg x 3 x ncell doubles, in place):
+ * interior image k becomes, site by site, the point at s = k/(nimg-1) of the
+ * shorter great-circle arc from image 0 to image nimg-1; parallel pairs blend
+ * linearly, antiparallel pairs turn through the part of x-hat (y-hat where
+ * |A_x| >= 0.9) orthogonal to A.  Asynchronous.  SX_ERR_ARG for nimg < 3 or
+ * nimg - 2 > max_batch. */
+int sx_cnn_interpolate(sx_cnn *h, double *chain, int nimg, void *stream);
+
+/* sx_cnn_interpolate, then every interior image replaced by the proposer's
+ * output for it (in place).  Synchronises the stream. */
+int sx_cnn_propose(sx_cnn *h, double *chain, int nimg, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

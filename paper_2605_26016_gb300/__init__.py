@@ -32,7 +32,10 @@ EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shel
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
            "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise", "sx_path_step",
            "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune", "sx_device_status",
-           "sx_batch_create", "sx_batch_destroy", "sx_batch_heun_step")
+           "sx_batch_create", "sx_batch_destroy", "sx_batch_heun_step",
+           "sx_cnn_num_params", "sx_cnn_create", "sx_cnn_destroy", "sx_cnn_set_params", "sx_cnn_get_params",
+           "sx_cnn_pack", "sx_cnn_forward", "sx_cnn_loss_grad", "sx_cnn_adam_step", "sx_cnn_interpolate",
+           "sx_cnn_propose")
 SX_STENCIL_AUTO, SX_STENCIL_FUSED, SX_STENCIL_TWO_PASS = 0, 1, 2
 STENCIL_SCHEMES = {"auto": SX_STENCIL_AUTO, "fused": SX_STENCIL_FUSED, "two_pass": SX_STENCIL_TWO_PASS}
 SX_MIN_VP, SX_MIN_DAMPED_LLG = 0, 1
@@ -66,6 +69,11 @@ class sx_min_params(ctypes.Structure):
 class sx_path_params(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("dt", ctypes.c_double), ("k_spring", ctypes.c_double),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class sx_adam_params(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
 
 
 class SxError(RuntimeError):
@@ -127,6 +135,17 @@ def lib():
             "sx_batch_heun_step": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                   ctypes.POINTER(sx_llg_params), ctypes.c_uint64, vp]),
             "sx_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_int, dp, vp]),
+            "sx_cnn_num_params": (i64, []),
+            "sx_cnn_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+            "sx_cnn_destroy": (None, [vp]),
+            "sx_cnn_set_params": (ctypes.c_int, [vp, vp]),
+            "sx_cnn_get_params": (ctypes.c_int, [vp, vp]),
+            "sx_cnn_pack": (ctypes.c_int, [vp, vp, i64, vp, vp, i64, vp, ctypes.c_int, vp, vp]),
+            "sx_cnn_forward": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp, vp]),
+            "sx_cnn_loss_grad": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_int, vp, dp, vp]),
+            "sx_cnn_adam_step": (ctypes.c_int, [vp, vp, ctypes.POINTER(sx_adam_params), vp]),
+            "sx_cnn_interpolate": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
+            "sx_cnn_propose": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -407,6 +426,90 @@ def sx_autotune(ctx, S, S_scratch, p, nsite, steps=5, stream=None):
 def sx_thermal_normals(seed, replica, site0, n, step, eta, stream=None):
     return _chk(lib().sx_thermal_normals(int(seed), int(replica), int(site0), int(n), int(step),
                                          _dev_ptr(eta, 3 * n, "float32"), _stream(stream)), "sx_thermal_normals")
+
+
+class Proposer:
+    """The convolutional chain proposer of include/sx.h (sx_cnn_*) for grids n = (nx, ny, nz) and batches of
+    up to max_batch samples.  Images are float64 CUDA tensors with 3*ncell elements per sample ([c][z][y][x]);
+    packed inputs are int16 CUDA tensors (BF16 bit patterns) of shape (nb, ncell, 16)."""
+
+    def __init__(self, n, max_batch):
+        self.n = tuple(int(v) for v in n)
+        self.ncell = self.n[0] * self.n[1] * self.n[2]
+        self.max_batch = int(max_batch)
+        self.nparams = int(lib().sx_cnn_num_params())
+        h = ctypes.c_void_p()
+        _chk(lib().sx_cnn_create(ctypes.byref(h), (ctypes.c_int * 3)(*self.n), self.max_batch), "sx_cnn_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().sx_cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        if a.size != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters")
+        return _chk(lib().sx_cnn_set_params(self.h, a.ctypes.data_as(ctypes.c_void_p)), "sx_cnn_set_params")
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.nparams, dtype=np.float32)
+        _chk(lib().sx_cnn_get_params(self.h, a.ctypes.data_as(ctypes.c_void_p)), "sx_cnn_get_params")
+        return a
+
+    def new_packed(self, nb):
+        import torch
+        return torch.empty((nb, self.ncell, 16), dtype=torch.int16, device="cuda")
+
+    def pack(self, I, A, B, s, X, shared_endpoints=False, stream=None):
+        """X <- packed samples (I[b], A[b], B[b], s[b]); with shared_endpoints A and B are single images."""
+        nb = X.shape[0]
+        m = 3 * self.ncell
+        ab = m if not shared_endpoints else 0
+        return _chk(lib().sx_cnn_pack(self.h, _dev_ptr(I, nb * m), m, _dev_ptr(A, m if shared_endpoints else nb * m),
+                                      _dev_ptr(B, m if shared_endpoints else nb * m), ab, _dev_ptr(s, nb),
+                                      nb, _dev_ptr(X, nb * self.ncell * 16, "int16"), _stream(stream)), "sx_cnn_pack")
+
+    def forward(self, X, I, P, stream=None):
+        nb = X.shape[0]
+        m = 3 * self.ncell
+        return _chk(lib().sx_cnn_forward(self.h, _dev_ptr(X, nb * self.ncell * 16, "int16"), _dev_ptr(I, nb * m), nb,
+                                         _dev_ptr(P, nb * m), _stream(stream)), "sx_cnn_forward")
+
+    def loss_grad(self, X, I, T, grad=None, stream=None):
+        """Returns the loss; the gradient goes to grad (float32 CUDA tensor) or stays in the proposer."""
+        nb = X.shape[0]
+        m = 3 * self.ncell
+        loss = ctypes.c_double()
+        g = _dev_ptr(grad, self.nparams, "float32") if grad is not None else None
+        _chk(lib().sx_cnn_loss_grad(self.h, _dev_ptr(X, nb * self.ncell * 16, "int16"), _dev_ptr(I, nb * m),
+                                    _dev_ptr(T, nb * m), nb, g, ctypes.byref(loss), _stream(stream)),
+             "sx_cnn_loss_grad")
+        return loss.value
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, grad=None, stream=None):
+        p = sx_adam_params(lr, beta1, beta2, eps)
+        g = _dev_ptr(grad, self.nparams, "float32") if grad is not None else None
+        return _chk(lib().sx_cnn_adam_step(self.h, g, ctypes.byref(p), _stream(stream)), "sx_cnn_adam_step")
+
+    def interpolate(self, chain, stream=None):
+        nimg = chain.shape[0]
+        return _chk(lib().sx_cnn_interpolate(self.h, _dev_ptr(chain, nimg * 3 * self.ncell), nimg, _stream(stream)),
+                    "sx_cnn_interpolate")
+
+    def propose(self, chain, stream=None):
+        nimg = chain.shape[0]
+        return _chk(lib().sx_cnn_propose(self.h, _dev_ptr(chain, nimg * 3 * self.ncell), nimg, _stream(stream)),
+                    "sx_cnn_propose")
 
 
 # ---------------------------------------------------------------- convenience

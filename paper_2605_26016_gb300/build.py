@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsx.so")
 
 SOURCES = ["sx_host.cu", "sx_gather.cu", "sx_stencil.cu", "sx_noalloc.cu", "sx_fft.cu", "sx_tc.cu", "sx_min.cu",
-           "sx_path.cu"]
+           "sx_path.cu", "sx_cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-warn-spills",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

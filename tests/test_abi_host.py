@@ -142,3 +142,15 @@ def test_tap_counts():
     assert len(s2.taps(0)) == 26
     s3, _ = sx.system_from_workload("sc_j123_dmi", (8, 8, 8))
     assert len(s3.taps(0)) == 26
+
+
+def test_proposer_size_and_argument_checks():
+    L = sx.lib()
+    assert L.sx_cnn_num_params() == 19491
+    h = ctypes.c_void_p()
+    for n, mb in (((0, 4, 4), 1), ((4, 4, 5000), 1), ((4, 4, 4), 0)):
+        rc = L.sx_cnn_create(ctypes.byref(h), (ctypes.c_int * 3)(*n), mb)
+        assert rc == sx.SX_ERR_ARG and not h.value
+    assert L.sx_cnn_adam_step(None, None, None, None) == sx.SX_ERR_ARG
+    assert L.sx_cnn_interpolate(None, None, 5, None) == sx.SX_ERR_ARG
+    L.sx_cnn_destroy(None)

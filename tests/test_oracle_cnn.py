@@ -92,3 +92,48 @@ def test_loss_vanishes_on_the_target_and_is_bounded():
     assert np.abs(P - I).max() < 1e-15 and loss == pytest.approx(0.0, abs=1e-15)
     _, loss2, _ = cnn.forward(params, X, I, -I)
     assert loss2 == pytest.approx(2.0)
+
+
+def test_interpolation_is_constant_speed_on_the_great_circle():
+    rng = np.random.default_rng(6)
+    A = _unit(rng.standard_normal((1, 3, 5, 4, 3)))[0]
+    B = _unit(rng.standard_normal((1, 3, 5, 4, 3)))[0]
+    B[:, 0, 0, 0] = -A[:, 0, 0, 0]          # antiparallel site
+    B[:, 1, 0, 0] = A[:, 1, 0, 0]           # parallel site
+    ang = lambda X, Y: np.arctan2(np.sqrt((np.cross(X, Y, axis=0) ** 2).sum(0)), (X * Y).sum(0))
+    th = ang(A, B)
+    assert np.abs(cnn.interpolate(A, B, 0.0) - A).max() < 1e-15
+    assert np.abs(cnn.interpolate(A, B, 1.0)[:, 1:] - B[:, 1:]).max() < 1e-12
+    for s in (0.2, 0.5, 0.85):
+        I = cnn.interpolate(A, B, s)
+        assert np.abs((I * I).sum(0) - 1).max() < 1e-14
+        # angle from A is s * theta, from B (1 - s) * theta: I lies on the shorter arc
+        assert np.abs(ang(A, I) - s * th).max() < 1e-9
+        assert np.abs(ang(I, B) - (1 - s) * th)[1:].max() < 1e-9
+        # in the plane of A and B (generic sites)
+        n = np.cross(A, B, axis=0)
+        assert np.abs((n * I).sum(0)[1:]).max() < 1e-12
+        # antiparallel site: quarter turns through the x-hat direction orthogonal to A
+        a = A[:, 0, 0, 0]
+        u = np.array([1.0, 0.0, 0.0]) - a[0] * a
+        u /= np.linalg.norm(u)
+        assert np.abs(I[:, 0, 0, 0] - (np.cos(np.pi * s) * a + np.sin(np.pi * s) * u)).max() < 1e-14
+
+
+def test_flatten_round_trip_and_size():
+    p = cnn_init_params(3)
+    f = cnn.flatten(p)
+    assert f.size == 19491
+    q = cnn.unflatten(f)
+    assert all(np.array_equal(a, c) and np.array_equal(b, d) for (a, b), (c, d) in zip(p, q))
+
+
+def test_adam_constant_gradient_moves_by_lr_times_sign():
+    # with bias correction, a constant gradient gives mhat = g and vhat = g^2 at every step, so each update
+    # is lr g / (|g| + eps)
+    g = np.array([3.0, -0.5, 1e-3, 0.0])
+    th, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in (1, 2, 3):
+        prev = th
+        th, m, v = cnn.adam_step(th, m, v, g, t, lr=0.01)
+        assert np.abs((th - prev) - (-0.01 * g / (np.abs(g) + 1e-8))).max() < 1e-15

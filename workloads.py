@@ -170,3 +170,10 @@ def cnn_init_params(seed, channels=CNN_CHANNELS):
             w *= 0.1
         params.append((w, np.zeros(co)))
     return params
+
+
+def cnn_init_flat(seed, channels=CNN_CHANNELS):
+    """cnn_init_params as one float32 vector in the proposer's parameter order (per layer the weights, then the
+    biases, layers in order)."""
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in cnn_init_params(seed, channels)]).astype(
+        np.float32)
