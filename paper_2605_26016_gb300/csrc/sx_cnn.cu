@@ -281,8 +281,8 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs p) {
         double Z[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) Z[k] = p.I[i0 + k * p.ncell] + (double)(__uint_as_float(r[k]) + bias[k]);
-        const double nrm = sqrt(Z[0] * Z[0] + Z[1] * Z[1] + Z[2] * Z[2]);
-        const double P0 = Z[0] / nrm, P1 = Z[1] / nrm, P2 = Z[2] / nrm;
+        const double rn = 1.0 / sqrt(Z[0] * Z[0] + Z[1] * Z[1] + Z[2] * Z[2]);
+        const double P0 = Z[0] * rn, P1 = Z[1] * rn, P2 = Z[2] * rn;
         if (p.P) {
           p.P[i0] = P0;
           p.P[i0 + p.ncell] = P1;
@@ -296,8 +296,8 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs p) {
           const double g0 = -T0 * p.inv_m, g1 = -T1 * p.inv_m, g2 = -T2 * p.inv_m;
           const double gp = g0 * P0 + g1 * P1 + g2 * P2;
           float4 *dst = reinterpret_cast<float4 *>(p.g_out + site * kC);
-          dst[0] = make_float4((float)((g0 - gp * P0) / nrm), (float)((g1 - gp * P1) / nrm),
-                               (float)((g2 - gp * P2) / nrm), 0.0f);
+          dst[0] = make_float4((float)((g0 - gp * P0) * rn), (float)((g1 - gp * P1) * rn),
+                               (float)((g2 - gp * P2) * rn), 0.0f);
           const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
           dst[1] = zero;
           dst[2] = zero;
@@ -422,8 +422,10 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const WgradArgs p) {
   if (task < 16) out[kTaps * 256 + task] = gb;
 }
 
-// grad[i] for every parameter: the FP64 sum over the partials of its layer, in partial order; block 0 also
-// reduces the loss partials.
+// grad for every parameter: the FP64 sum over the partials of its layer.  Block (x, l) with 32 x 8 threads
+// reduces partial entries q = 32 x + lane of layer l: warp w sums slots w, w + 8, ... (coalesced across lanes),
+// the eight warp sums combine in a fixed tree, and the entry is scattered to its parameter.  Row l = kLayers
+// reduces the loss partials the same way.  The order depends only on the sizes (deterministic).
 struct ReduceArgs {
   const float *part[kLayers];
   long long nslot;       // partials per layer
@@ -434,29 +436,41 @@ struct ReduceArgs {
   double *loss;          // device scalar
 };
 
-__global__ void k_grad_reduce(const ReduceArgs p) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && p.loss) {
-    double s = 0.0;
-    for (long long k = 0; k < p.nloss; ++k) s += p.loss_part[k];
-    *p.loss = s * p.inv_m;
-  }
-  if (i >= kNParam) return;
-  int l = 0;
-  while (l + 1 < kLayers && i >= wofs(l + 1)) ++l;
-  const int j = i - wofs(l);
-  const int ci = cin_of(l), co = cout_of(l);
-  int idx;
-  if (j < co * ci * kTaps) {
-    const int o = j / (ci * kTaps), c = (j / kTaps) % ci, t = j % kTaps;
-    idx = t * 256 + o * 16 + c;
-  } else {
-    idx = kTaps * 256 + (j - co * ci * kTaps);
-  }
-  const float *src = p.part[l] + idx;
+__global__ void __launch_bounds__(256) k_grad_reduce(const ReduceArgs p) {
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x, w = threadIdx.y, l = blockIdx.y;
+  const int q = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (long long k = 0; k < p.nslot; ++k) s += (double)src[(size_t)k * kPart];
-  p.grad[i] = (float)s;
+  if (l == kLayers) {
+    if (blockIdx.x == 0)
+      for (long long k = w * 32 + lane; k < p.nloss; k += 256) s += p.loss_part[k];
+  } else if (q < kPart) {
+    const float *src = p.part[l] + q;
+    for (long long k = w; k < p.nslot; k += 8) s += (double)src[(size_t)k * kPart];
+  }
+  red[w][lane] = s;
+  __syncthreads();
+  if (w != 0) return;
+  const double t = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                   ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+  if (l == kLayers) {
+    if (blockIdx.x != 0) return;
+    double v = t;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, off);
+    if (lane == 0 && p.loss) *p.loss = v * p.inv_m;
+    return;
+  }
+  if (q >= kPart) return;
+  const int ci = cin_of(l), co = cout_of(l);
+  int j = -1;
+  if (q < kTaps * 256) {
+    const int tap = q >> 8, o = (q >> 4) & 15, c = q & 15;
+    if (o < co && c < ci) j = (o * ci + c) * kTaps + tap;
+  } else if (q - kTaps * 256 < co) {
+    j = co * ci * kTaps + (q - kTaps * 256);
+  }
+  if (j >= 0) p.grad[wofs(l) + j] = (float)t;
 }
 
 // Writes the BF16 operands of parameter i (a weight) into the forward and input-gradient operands of its layer.
@@ -833,7 +847,7 @@ int sx_cnn_loss_grad(sx_cnn *h, const uint16_t *X, const double *I, const double
     r.nloss = head_blocks(h, nb);
     r.inv_m = 1.0 / ((double)nb * (double)h->ncell);
     r.loss = h->loss;
-    k_grad_reduce<<<(kNParam + 255) / 256, 256, 0, st>>>(r);
+    k_grad_reduce<<<dim3((kPart + 31) / 32, kLayers + 1), dim3(32, 8), 0, st>>>(r);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return cuda_error(e, "sx_cnn_loss_grad");

@@ -1,0 +1,260 @@
+"""Learned chain proposals for the string method: generate converged paths, train the proposer, compare.
+
+    python -m paper_2605_26016_gb300.proposer_workflow [L] [ntrain] [ntest] [train_seconds] [eval_iters] [params.npy]
+
+Defaults: L = 32 (simple cubic L^3, open boundaries), 200 training paths, 12 test paths, 150 s of training,
+30000 string iterations per evaluation arm.
+
+Hamiltonian family: the four-shell frustrated exchange of the hopfion calculation (J1 = 1 meV, J2/J1 = 0.188,
+J3/J1 = -0.274, J4/J1 = -0.161), with J2..J4 scaled by seeded factors in [0.97, 1.03] and a Zeeman field
+B_z in [0, 0.04] T per path (stronger fields or larger changes shrink the barrier to nothing).  Endpoint
+A is a hopfion (Hopf ansatz of seeded radius 8..10 and centre offset +-2 sites, relaxed by velocity
+projection); endpoint B is the ferromagnet along +z.  A path is the string
+method's chain of 16 images from the geodesic interpolation of A and B, run for a fixed number of iterations
+(dt = 0.05 rad/meV); its interior images are the training targets.  Paths are generated on 8 CUDA streams
+from 8 host threads (distinct contexts are independent).
+
+The proposer (include/sx.h, sx_cnn_*) is trained with Adam on (interpolated image, A, B, s) -> converged
+image over all interior images of the training paths, batches of 28 samples, cosine learning-rate decay.
+
+Evaluation on held-out Hamiltonians: each test path is run twice on one stream, from the geodesic
+interpolation (plain) and from the proposer's chain (learned), in calls of 100 iterations, recording the
+wall-clock time and the barrier max_k E_k - E_0 after each call.  The reference barrier is the lower of the
+two arms' final barriers (a converged string is a minimum-energy path, whose saddle is the lowest maximum
+along paths); an arm has reached it at the first call after which its barrier stays within 1e-3 of the
+hopfion energy scale E(A) - E(B).  For the first three test paths the plain arm then continues to three
+times the iterations, to show whether it reaches the lower barrier at all.  Prints one JSON line per stage
+and a summary.
+"""
+import json
+import os
+import sys
+import threading
+import time
+
+
+def main(argv):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import numpy as np
+    import torch
+    import paper_2605_26016_gb300 as sx
+    from workloads import cnn_init_flat, cubic_cell, hopf_ansatz, uniform_spins
+
+    L = int(argv[0]) if len(argv) > 0 else 32
+    ntrain = int(argv[1]) if len(argv) > 1 else 200
+    ntest = int(argv[2]) if len(argv) > 2 else 12
+    train_s = float(argv[3]) if len(argv) > 3 else 150.0
+    eval_iters = int(argv[4]) if len(argv) > 4 else 30000
+    gen_iters = 15000
+    nimg, dt = 16, 0.05
+    n = (L, L, L)
+    ncell = L ** 3
+    shells = (1.0, 0.188, -0.274, -0.161)
+
+    def system(h):
+        s = sx.SpinSystem(n, (0, 0, 0), cubic_cell(), [[0, 0, 0]], [1.0])
+        for k, J in enumerate(shells):
+            s.add_shell_exchange(k + 1, J * (h["f"][k - 1] if k > 0 else 1.0))
+        s.set_zeeman([0.0, 0.0, h["B"]])
+        s.plan("gather", "fp32")
+        return s
+
+    rng = np.random.default_rng(2605)
+    hams = [dict(f=rng.uniform(0.97, 1.03, 3).tolist(), B=float(rng.uniform(0.0, 0.04)), R=float(rng.uniform(8, 10)),
+                 c=(rng.uniform(-2, 2, 3) + (L - 1) / 2).tolist()) for _ in range(ntrain + ntest)]
+    FM = torch.from_numpy(uniform_spins(1, n, [0.0, 0.0, 1.0])).cuda()
+    helper = sx.Proposer(n, nimg - 2)
+
+    def geodesic_chain(A, stream=None):
+        chain = torch.empty((nimg, 3, ncell), dtype=torch.float64, device="cuda")
+        chain[0].copy_(A.view(3, ncell))
+        chain[-1].copy_(FM.view(3, ncell))
+        helper.interpolate(chain, stream=stream)
+        return chain
+
+    # ------------------------------------------------------------ converged paths
+    def make_path(h, stream):
+        with torch.cuda.stream(stream):
+            s = system(h)
+            A = torch.from_numpy(hopf_ansatz(n, h["R"], h["c"])).cuda()
+            s.minimise(A, method="vp", dt=0.1, tol=1e-4, max_iter=6000, check_every=1000, stream=stream)
+            zmin = A[2].min().item()
+            if zmin > -0.5:
+                s.close()
+                return None
+            chain = torch.empty((nimg, 3, ncell), dtype=torch.float64, device="cuda")
+            chain[0].copy_(A.view(3, ncell))
+            chain[-1].copy_(FM.view(3, ncell))
+            prop = sx.Proposer(n, nimg - 2)
+            prop.interpolate(chain, stream=stream)
+            prop.close()
+            it, E, fm = s.path(chain, method="string", dt=dt, tol=0.0,
+                               max_iter=gen_iters, check_every=gen_iters, stream=stream)
+            stream.synchronize()
+            s.close()
+            return dict(A=A, chain=chain, barrier=max(E) - E[0], scale=E[0] - E[-1], fmax=fm)
+
+    t0 = time.time()
+    paths = [None] * len(hams)
+    nthreads = 8
+    lock = threading.Lock()
+    todo = list(range(len(hams)))
+
+    def worker():
+        st = torch.cuda.Stream()
+        while True:
+            with lock:
+                if not todo:
+                    return
+                i = todo.pop(0)
+            paths[i] = make_path(hams[i], st)
+
+    th = [threading.Thread(target=worker) for _ in range(nthreads)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    train_ids = [i for i in range(ntrain) if paths[i] is not None]
+    test_ids = [i for i in range(ntrain, ntrain + ntest) if paths[i] is not None]
+    print(json.dumps({"stage": "paths", "lattice": list(n), "images": nimg, "string_iterations": gen_iters,
+                      "train_paths": len(train_ids), "test_paths": len(test_ids),
+                      "collapsed": sum(p is None for p in paths), "seconds": gen_s,
+                      "barrier_range": [min(paths[i]["barrier"] for i in train_ids),
+                                        max(paths[i]["barrier"] for i in train_ids)]}), flush=True)
+
+    # ------------------------------------------------------------ training set
+    nint = nimg - 2
+    ns = len(train_ids) * nint
+    X = torch.empty((ns, ncell, 16), dtype=torch.int16, device="cuda")
+    I = torch.empty((ns, 3, ncell), dtype=torch.float64, device="cuda")
+    T = torch.empty((ns, 3, ncell), dtype=torch.float64, device="cuda")
+    svals = torch.tensor([k / (nimg - 1) for k in range(1, nimg - 1)], dtype=torch.float64, device="cuda")
+    for j, i in enumerate(train_ids):
+        g = geodesic_chain(paths[i]["A"])
+        sl = slice(j * nint, (j + 1) * nint)
+        I[sl].copy_(g[1:-1])
+        T[sl].copy_(paths[i]["chain"][1:-1])
+        helper.pack(I[sl], paths[i]["A"], FM, svals, X[sl], shared_endpoints=True)
+    batch = 2 * nint
+    model = sx.Proposer(n, batch)
+    model.set_params(cnn_init_flat(7))
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    lr0, lr1 = 2e-3, 5e-5
+    steps, losses = 0, []
+    t0 = time.time()
+    est_steps = None
+    while True:
+        perm = torch.randperm(ns, generator=gen).cuda()
+        for b0 in range(0, ns - batch + 1, batch):
+            idx = perm[b0:b0 + batch]
+            Xb, Ib, Tb = X.index_select(0, idx), I.index_select(0, idx), T.index_select(0, idx)
+            loss = model.loss_grad(Xb, Ib, Tb)
+            el = time.time() - t0
+            if est_steps is None and steps == 20:
+                est_steps = int(20 * train_s / max(el, 1e-6))
+            frac = min(1.0, steps / est_steps) if est_steps else 0.0
+            lr = lr1 + 0.5 * (lr0 - lr1) * (1 + np.cos(np.pi * frac))
+            model.adam_step(lr)
+            losses.append(loss)
+            steps += 1
+            if el > train_s:
+                break
+        if time.time() - t0 > train_s:
+            break
+    torch.cuda.synchronize()
+    train_time = time.time() - t0
+    if len(argv) > 5:
+        np.save(argv[5], model.get_params())
+
+    def angles(P, Tt):
+        d = (P * Tt).sum(1).clamp(-1, 1)
+        return torch.rad2deg(torch.acos(d)).mean().item()
+
+    # held-out error of the proposals against the converged images
+    err = {"interp_deg": [], "proposal_deg": []}
+    for i in test_ids:
+        g = geodesic_chain(paths[i]["A"])
+        c = g.clone()
+        model.propose(c)
+        err["interp_deg"].append(angles(g[1:-1], paths[i]["chain"][1:-1]))
+        err["proposal_deg"].append(angles(c[1:-1], paths[i]["chain"][1:-1]))
+    print(json.dumps({"stage": "train", "samples": ns, "batch": batch, "steps": steps, "seconds": train_time,
+                      "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:])),
+                      "test_mean_angle_interp_deg": float(np.mean(err["interp_deg"])),
+                      "test_mean_angle_proposal_deg": float(np.mean(err["proposal_deg"]))}), flush=True)
+
+    # ------------------------------------------------------------ evaluation
+    chunk = 100
+    results = []
+    for i in test_ids:
+        h = hams[i]
+        s = system(h)
+        arms = {}
+        for arm in ("plain", "learned"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c = geodesic_chain(paths[i]["A"])
+            if arm == "learned":
+                model.propose(c)
+            torch.cuda.synchronize()
+            t_init = time.perf_counter() - t0
+            hist = []
+            done = 0
+            while done < eval_iters:
+                it, E, fm = s.path(c, method="string", dt=dt, tol=0.0, max_iter=chunk,
+                                   check_every=chunk)
+                done += it
+                hist.append((done, time.perf_counter() - t0, max(E) - E[0], fm, E[0] - E[-1]))
+            arms[arm] = dict(hist=hist, t_init=t_init, chain=c)
+        ref = min(arms["plain"]["hist"][-1][2], arms["learned"]["hist"][-1][2])
+        scale = arms["plain"]["hist"][-1][4]
+        tol = 1e-3 * abs(scale)
+        row = dict(path=i, B=h["B"], f=h["f"], barrier_ref=ref, scale=scale, tol=tol)
+        for arm, a in arms.items():
+            hs = a["hist"]
+            k = len(hs)
+            while k > 0 and abs(hs[k - 1][2] - ref) <= tol:
+                k -= 1
+            row[arm] = dict(reached=k < len(hs), t_init=a["t_init"], first_barrier=hs[0][2],
+                            final_barrier=hs[-1][2], final_fmax=hs[-1][3])
+            if k < len(hs):
+                row[arm].update(iterations=hs[k][0], seconds=hs[k][1])
+        if len(results) < 3:
+            # the plain arm continued: does it reach the lower barrier later?
+            c_more = []
+            t0 = time.perf_counter()
+            done = 0
+            while done < 2 * eval_iters:
+                it, E, fm = s.path(arms["plain"]["chain"], method="string", dt=dt, tol=0.0, max_iter=chunk,
+                                   check_every=chunk)
+                done += it
+                if done % eval_iters == 0:
+                    c_more.append((eval_iters + done, max(E) - E[0], fm))
+            row["plain_continued"] = c_more
+        results.append(row)
+        print(json.dumps({"stage": "eval", **row}), flush=True)
+        s.close()
+    both = [r for r in results if r["plain"]["reached"] and r["learned"]["reached"]]
+    sp = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in both]
+    print(json.dumps({"stage": "summary", "test_paths": len(results), "both_reached": len(both),
+                      "plain_reached": sum(r["plain"]["reached"] for r in results),
+                      "learned_reached": sum(r["learned"]["reached"] for r in results),
+                      "lower_final_barrier": {"learned": sum(r["learned"]["final_barrier"] < r["plain"]["final_barrier"]
+                                                             for r in results),
+                                              "plain": sum(r["plain"]["final_barrier"] < r["learned"]["final_barrier"]
+                                                           for r in results)},
+                      "only_learned_reached": sum(r["learned"]["reached"] and not r["plain"]["reached"] for r in results),
+                      "only_plain_reached": sum(r["plain"]["reached"] and not r["learned"]["reached"] for r in results),
+                      "median_speedup_wall": float(np.median(sp)) if sp else None,
+                      "learned_faster": sum(r["learned"]["seconds"] < r["plain"]["seconds"] for r in both),
+                      "median_plain_s": float(np.median([r["plain"]["seconds"] for r in both])) if both else None,
+                      "median_learned_s": float(np.median([r["learned"]["seconds"] for r in both])) if both else None,
+                      "generation_s": gen_s, "training_s": train_time}), flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
