@@ -82,6 +82,8 @@ def lib():
         L.orc_geodesic.argtypes = [ctypes.c_int64, _dp, _dp]
         L.orc_gneb.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                ctypes.c_int64, _dp, _dp]
+        L.orc_gneb_vp.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int]
         L.orc_string.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int64, _dp, _dp]
         L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.orc_normals_block.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
@@ -228,6 +230,20 @@ class Model:
         _check(lib().orc_gneb(self.h, _ptr(img, _dp), img.shape[0], float(dt), float(k), 1 if climbing else 0,
                               int(niter), _ptr(E, _dp), ctypes.byref(fm)), "gneb")
         return img.reshape((img.shape[0],) + self.shape), E, fm.value
+
+    def gneb_vp(self, images, dt, k, niter, climbing=False, state=None):
+        """niter geodesic-NEB iterations with velocity projection on the chain's force; returns (images,
+        energies, max force, state); pass the returned state back to continue with the same velocity."""
+        img = self._chain(images)
+        E = np.zeros(img.shape[0])
+        fm = ctypes.c_double(0.0)
+        first = state is None
+        if first:
+            state = (np.zeros(img.shape), np.zeros(img.shape))
+        _check(lib().orc_gneb_vp(self.h, _ptr(img, _dp), img.shape[0], float(dt), float(k), 1 if climbing else 0,
+                                 int(niter), _ptr(E, _dp), ctypes.byref(fm), _ptr(state[0], _dp),
+                                 _ptr(state[1], _dp), 1 if first else 0), "gneb_vp")
+        return img.reshape((img.shape[0],) + self.shape), E, fm.value, state
 
     def string(self, images, dt, niter):
         """niter string-method iterations (step, then equal-arc-length redistribution);

@@ -1005,6 +1005,82 @@ static void project(const double S[3], double x[3]) {
  * or f - 2 (f.tau) tau for the climbing image (the highest-energy interior image
  * when climbing != 0); f = b - (b.S) S.  Update S <- R_exp(S, dt F).
  * E receives the image energies and *fmax_out the largest site force of the last iteration. */
+/* GNEB / CI-GNEB forces of every interior image of a chain: E receives the image
+ * energies, F (nimg x 3N, interior slots) the forces, *worst the largest site |F|. */
+static void gneb_forces(orc_model *m, const double *img, int nimg, double kspring, int climbing, double *E,
+                        double *F, double *b, double *worst_out) {
+  int64_t N = m->nsite;
+  for (int n = 0; n < nimg; n++) E[n] = orc_energy(m, img + (int64_t)n * 3 * N, NULL);
+  int top = 1;
+  for (int n = 1; n < nimg - 1; n++)
+    if (E[n] > E[top]) top = n;
+  double worst = 0.0;
+  for (int n = 1; n < nimg - 1; n++) {
+    const double *S = img + (int64_t)n * 3 * N, *Sp = S + 3 * N, *Sm = S - 3 * N;
+    orc_field(m, S, b);
+    double a, bb;
+    double dEp = E[n + 1] - E[n], dEm = E[n - 1] - E[n];
+    if (E[n + 1] > E[n] && E[n] > E[n - 1]) {
+      a = 1.0;
+      bb = 0.0;
+    } else if (E[n + 1] < E[n] && E[n] < E[n - 1]) {
+      a = 0.0;
+      bb = 1.0;
+    } else {
+      double emax = fmax(fabs(dEp), fabs(dEm)), emin = fmin(fabs(dEp), fabs(dEm));
+      if (E[n + 1] > E[n - 1]) {
+        a = emax;
+        bb = emin;
+      } else {
+        a = emin;
+        bb = emax;
+      }
+    }
+    double tt = 0.0, ft = 0.0;
+    double *tau = F + (int64_t)n * 3 * N; /* tau stored temporarily in F */
+    for (int64_t i = 0; i < N; i++) {
+      double s[3] = {S[i], S[N + i], S[2 * N + i]}, tp[3], tm[3], bi[3] = {b[i], b[N + i], b[2 * N + i]};
+      for (int k = 0; k < 3; k++) {
+        tp[k] = Sp[k * N + i] - s[k];
+        tm[k] = s[k] - Sm[k * N + i];
+      }
+      project(s, tp);
+      project(s, tm);
+      project(s, bi);
+      for (int k = 0; k < 3; k++) {
+        double t = a * tp[k] + bb * tm[k];
+        tau[k * N + i] = t;
+        tt += t * t;
+        ft += bi[k] * t;
+      }
+    }
+    double tn = sqrt(tt);
+    double ftau = tn > 0 ? ft / tn : 0.0;
+    double dpl = orc_geodesic(N, S, Sp), dmi = orc_geodesic(N, Sm, S);
+    int ci = climbing && n == top;
+    double cf = ci ? 2.0 : 1.0, ks = ci ? 0.0 : kspring * (dpl - dmi);
+    for (int64_t i = 0; i < N; i++) {
+      double s[3] = {S[i], S[N + i], S[2 * N + i]}, bi[3] = {b[i], b[N + i], b[2 * N + i]}, f2 = 0.0;
+      project(s, bi);
+      for (int k = 0; k < 3; k++) {
+        double th = tn > 0 ? tau[k * N + i] / tn : 0.0;
+        double Fk = bi[k] - cf * ftau * th + ks * th;
+        tau[k * N + i] = Fk;
+        f2 += Fk * Fk;
+      }
+      if (sqrt(f2) > worst) worst = sqrt(f2);
+    }
+  }
+  *worst_out = worst;
+}
+
+/* niter GNEB iterations on a chain of nimg images (img[n*3N ...]); endpoints fixed.
+ * Tangent: energy-weighted upwind combination of the projected differences
+ * t+ = P(S_{n+1} - S_n), t- = P(S_n - S_{n-1}), normalised over the image.
+ * Force on an interior image: f - (f.tau) tau + k (d_{n,n+1} - d_{n-1,n}) tau,
+ * or f - 2 (f.tau) tau for the climbing image (the highest-energy interior image
+ * when climbing != 0); f = b - (b.S) S.  Update S <- R_exp(S, dt F).
+ * E receives the image energies and *fmax_out the largest site force of the last iteration. */
 int orc_gneb(void *h, double *img, int nimg, double dt, double kspring, int climbing, int64_t niter, double *E,
              double *fmax_out) {
   orc_model *m = (orc_model *)h;
@@ -1022,72 +1098,72 @@ int orc_gneb(void *h, double *img, int nimg, double dt, double kspring, int clim
     return -3;
   }
   for (int64_t it = 0; it < niter; it++) {
-    for (int n = 0; n < nimg; n++) E[n] = orc_energy(m, img + (int64_t)n * 3 * N, NULL);
-    int top = 1;
-    for (int n = 1; n < nimg - 1; n++)
-      if (E[n] > E[top]) top = n;
-    double worst = 0.0;
-    for (int n = 1; n < nimg - 1; n++) {
-      double *S = img + (int64_t)n * 3 * N, *Sp = S + 3 * N, *Sm = S - 3 * N;
-      orc_field(m, S, b);
-      double a, bb;
-      double dEp = E[n + 1] - E[n], dEm = E[n - 1] - E[n];
-      if (E[n + 1] > E[n] && E[n] > E[n - 1]) {
-        a = 1.0;
-        bb = 0.0;
-      } else if (E[n + 1] < E[n] && E[n] < E[n - 1]) {
-        a = 0.0;
-        bb = 1.0;
-      } else {
-        double emax = fmax(fabs(dEp), fabs(dEm)), emin = fmin(fabs(dEp), fabs(dEm));
-        if (E[n + 1] > E[n - 1]) {
-          a = emax;
-          bb = emin;
-        } else {
-          a = emin;
-          bb = emax;
-        }
-      }
-      double tt = 0.0, ft = 0.0;
-      double *tau = F + (int64_t)n * 3 * N; /* tau stored temporarily in F */
-      for (int64_t i = 0; i < N; i++) {
-        double s[3] = {S[i], S[N + i], S[2 * N + i]}, tp[3], tm[3], bi[3] = {b[i], b[N + i], b[2 * N + i]};
-        for (int k = 0; k < 3; k++) {
-          tp[k] = Sp[k * N + i] - s[k];
-          tm[k] = s[k] - Sm[k * N + i];
-        }
-        project(s, tp);
-        project(s, tm);
-        project(s, bi);
-        for (int k = 0; k < 3; k++) {
-          double t = a * tp[k] + bb * tm[k];
-          tau[k * N + i] = t;
-          tt += t * t;
-          ft += bi[k] * t;
-        }
-      }
-      double tn = sqrt(tt);
-      double ftau = tn > 0 ? ft / tn : 0.0;
-      double dpl = orc_geodesic(N, S, Sp), dmi = orc_geodesic(N, Sm, S);
-      int ci = climbing && n == top;
-      double cf = ci ? 2.0 : 1.0, ks = ci ? 0.0 : kspring * (dpl - dmi);
-      for (int64_t i = 0; i < N; i++) {
-        double s[3] = {S[i], S[N + i], S[2 * N + i]}, bi[3] = {b[i], b[N + i], b[2 * N + i]}, f2 = 0.0;
-        project(s, bi);
-        for (int k = 0; k < 3; k++) {
-          double th = tn > 0 ? tau[k * N + i] / tn : 0.0;
-          double Fk = bi[k] - cf * ftau * th + ks * th;
-          tau[k * N + i] = Fk;
-          f2 += Fk * Fk;
-        }
-        if (sqrt(f2) > worst) worst = sqrt(f2);
-      }
-    }
+    double worst;
+    gneb_forces(m, img, nimg, kspring, climbing, E, F, b, &worst);
     for (int n = 1; n < nimg - 1; n++) {
       double *S = img + (int64_t)n * 3 * N, *Fn = F + (int64_t)n * 3 * N;
       for (int64_t i = 0; i < N; i++) {
         double s[3] = {S[i], S[N + i], S[2 * N + i]}, u[3];
         for (int k = 0; k < 3; k++) u[k] = dt * Fn[k * N + i];
+        retract_exp(s, u);
+        for (int k = 0; k < 3; k++) S[k * N + i] = s[k];
+      }
+    }
+    *fmax_out = worst;
+  }
+  for (int n = 0; n < nimg; n++) E[n] = orc_energy(m, img + (int64_t)n * 3 * N, NULL);
+  free(b);
+  free(F);
+  return 0;
+}
+
+/* niter GNEB iterations with velocity projection ("Static optimization and
+ * minimum-energy paths": velocity projection, Bitzek et al.) on the GNEB force
+ * F of all interior images taken as one vector: v' = v + dt/2 (F_prev + F)
+ * (v' = 0 on the first iteration when first != 0), c = max(v'.F, 0) / (F.F)
+ * with the dot products over every interior image and site, v <- c F,
+ * S <- R_exp(S, dt c F + dt^2/2 F), F_prev <- F.  vstate and fprev hold
+ * nimg x 3N doubles (interior slots used) and carry the velocity between calls. */
+int orc_gneb_vp(void *h, double *img, int nimg, double dt, double kspring, int climbing, int64_t niter, double *E,
+                double *fmax_out, double *vstate, double *fprev, int first) {
+  orc_model *m = (orc_model *)h;
+  if (!m->built) {
+    int e = orc_build(m);
+    if (e) return e;
+  }
+  if (nimg < 3) return -1;
+  int64_t N = m->nsite;
+  double *b = (double *)malloc(sizeof(double) * 3 * N);
+  double *F = (double *)malloc(sizeof(double) * 3 * N * nimg);
+  if (!b || !F) {
+    free(b);
+    free(F);
+    return -3;
+  }
+  for (int64_t it = 0; it < niter; it++) {
+    double worst;
+    gneb_forces(m, img, nimg, kspring, climbing, E, F, b, &worst);
+    double p = 0.0, F2 = 0.0;
+    for (int n = 1; n < nimg - 1; n++) {
+      double *Fn = F + (int64_t)n * 3 * N, *vn = vstate + (int64_t)n * 3 * N, *pn = fprev + (int64_t)n * 3 * N;
+      for (int64_t j = 0; j < 3 * N; j++) {
+        double vk = (first && it == 0) ? 0.0 : vn[j] + 0.5 * dt * (pn[j] + Fn[j]);
+        p += vk * Fn[j];
+        F2 += Fn[j] * Fn[j];
+      }
+    }
+    double c = (p > 0.0 && F2 > 0.0) ? p / F2 : 0.0;
+    for (int n = 1; n < nimg - 1; n++) {
+      double *S = img + (int64_t)n * 3 * N, *Fn = F + (int64_t)n * 3 * N;
+      double *vn = vstate + (int64_t)n * 3 * N, *pn = fprev + (int64_t)n * 3 * N;
+      for (int64_t i = 0; i < N; i++) {
+        double s[3] = {S[i], S[N + i], S[2 * N + i]}, u[3];
+        for (int k = 0; k < 3; k++) {
+          double fk = Fn[k * N + i];
+          vn[k * N + i] = c * fk;
+          pn[k * N + i] = fk;
+          u[k] = dt * c * fk + 0.5 * dt * dt * fk;
+        }
         retract_exp(s, u);
         for (int k = 0; k < 3; k++) S[k * N + i] = s[k];
       }

@@ -192,3 +192,35 @@ def test_gneb_tangent_is_continuous_across_an_energy_extremum():
     ang = lambda x, y: np.arccos(min(1.0, abs(np.dot(x, y)) / (np.linalg.norm(x) * np.linalg.norm(y))))
     assert ang(tp, tm) > 0.2
     assert ang(G, tp) < 1e-3
+
+
+def test_vp_ci_gneb_finds_the_same_stoner_wohlfarth_saddle_faster():
+    m = macrospin()
+    chain = polar_chain(THETA0, np.pi - THETA0, 9, phi_bulge=0.8)
+    img, E, fmax, state = m.gneb_vp(chain, dt=0.1, k=1.0, niter=400, climbing=True)
+    S = img.reshape(9, 3)
+    assert fmax < 1e-12
+    top = int(np.argmax(E[1:-1])) + 1
+    assert np.abs(S[top] - [1.0, 0.0, 0.0]).max() < 1e-8
+    assert E[top] - E[0] == pytest.approx(K * (1 - H / (2 * K)) ** 2, abs=1e-12)
+    assert np.abs(S[:, 1]).max() < 1e-8
+    # after 100 iterations steepest descent with the same step is still far behind
+    _, _, f100, _ = m.gneb_vp(chain, dt=0.1, k=1.0, niter=100, climbing=True)
+    _, _, fsd = m.gneb(chain, dt=0.1, k=1.0, niter=100, climbing=True)
+    assert f100 < 1e-5 and fsd > 100 * f100
+
+
+def test_vp_gneb_first_iteration_is_the_half_dt_squared_step_and_state_carries_over():
+    m = macrospin()
+    chain = polar_chain(THETA0, np.pi - THETA0, 7, phi_bulge=0.6)
+    dt = 0.05
+    one, _, _, st1 = m.gneb_vp(chain, dt=dt, k=1.0, niter=1)
+    # v = 0 on the first iteration, so the move is R_exp(S, dt^2/2 F): the same as a steepest-descent step of
+    # dt^2/2
+    sd, _, _ = m.gneb(chain, dt=0.5 * dt * dt, k=1.0, niter=1)
+    assert np.abs(one - sd).max() < 1e-15
+    # two calls of 5 with the carried state equal one call of 10
+    a, _, _, st = m.gneb_vp(chain, dt=dt, k=1.0, niter=5)
+    a, _, _, st = m.gneb_vp(a, dt=dt, k=1.0, niter=5, state=st)
+    b, _, _, _ = m.gneb_vp(chain, dt=dt, k=1.0, niter=10)
+    assert np.abs(a - b).max() < 1e-15
