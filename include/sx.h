@@ -180,6 +180,13 @@ typedef struct {
  *                   interpolation between the two neighbouring old images. */
 typedef enum { SX_PATH_STRING = 0, SX_PATH_GNEB = 1, SX_PATH_CI_GNEB = 2 } sx_path_method;
 
+/* Update rule of the GNEB and CI-GNEB iterations.  SX_PATH_STEEPEST: S <- R(S, dt F).  SX_PATH_VP: velocity
+ * projection (the minimisation section lists it among the optimisers; the update of sx_minimise) on the force
+ * F of all interior images taken as one vector: v' = v + dt/2 (F_prev + F) (0 on the first iteration from
+ * rest), v = max(v'.F, 0)/(F.F) F with the dot products over every interior site, S <- R(S, dt v + dt^2/2 F).
+ * The velocity and previous force live in the path workspace (another 2 chains). */
+typedef enum { SX_PATH_STEEPEST = 0, SX_PATH_VP = 1 } sx_path_optimizer;
+
 typedef struct {
   int method;       /* sx_path_method */
   double dt;        /* step of the retraction, rad per meV of force */
@@ -187,6 +194,9 @@ typedef struct {
   double tol;       /* stop when the largest site force |F| is below tol (meV) at a check */
   int max_iter;     /* iteration cap */
   int check_every;  /* iterations between convergence checks, >= 1 */
+  int optimizer;    /* sx_path_optimizer: SX_PATH_STEEPEST or SX_PATH_VP (GNEB and CI-GNEB only) */
+  int keep_velocity; /* SX_PATH_VP: 1 = continue from the velocity the previous call on this context left
+                        (a VP call on a chain of the same number of images), 0 = start at rest */
 } sx_path_params;
 
 /* Create a context for a lattice.  Host-only: makes no CUDA call.

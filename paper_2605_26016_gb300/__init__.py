@@ -41,6 +41,8 @@ STENCIL_SCHEMES = {"auto": SX_STENCIL_AUTO, "fused": SX_STENCIL_FUSED, "two_pass
 SX_MIN_VP, SX_MIN_DAMPED_LLG = 0, 1
 SX_PATH_STRING, SX_PATH_GNEB, SX_PATH_CI_GNEB = 0, 1, 2
 PATH_METHODS = {"string": SX_PATH_STRING, "gneb": SX_PATH_GNEB, "ci_gneb": SX_PATH_CI_GNEB}
+SX_PATH_STEEPEST, SX_PATH_VP = 0, 1
+PATH_OPTIMIZERS = {"steepest": SX_PATH_STEEPEST, "vp": SX_PATH_VP}
 
 
 class sx_lattice(ctypes.Structure):
@@ -68,7 +70,8 @@ class sx_min_params(ctypes.Structure):
 
 class sx_path_params(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("dt", ctypes.c_double), ("k_spring", ctypes.c_double),
-                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("optimizer", ctypes.c_int), ("keep_velocity", ctypes.c_int)]
 
 
 class sx_adam_params(ctypes.Structure):
@@ -347,7 +350,7 @@ def sx_minimise(ctx, S, S_scratch, nsite, method="vp", dt=0.05, alpha=1.0, tol=1
 
 
 def sx_path_step(ctx, images, nimg, nsite, method="gneb", dt=0.05, k_spring=1.0, tol=0.0, max_iter=100,
-                 check_every=50, stream=None):
+                 check_every=50, optimizer="steepest", keep_velocity=False, stream=None):
     """Path-method iterations on a chain (nimg images back to back, in place; endpoints fixed).
     Returns (iterations, image energies in meV as a list, largest site force of the last measured
     iteration in meV)."""
@@ -355,6 +358,8 @@ def sx_path_step(ctx, images, nimg, nsite, method="gneb", dt=0.05, k_spring=1.0,
     p.method = PATH_METHODS.get(method, method)
     p.dt, p.k_spring, p.tol = float(dt), float(k_spring), float(tol)
     p.max_iter, p.check_every = int(max_iter), int(check_every)
+    p.optimizer = PATH_OPTIMIZERS.get(optimizer, optimizer)
+    p.keep_velocity = 1 if keep_velocity else 0
     it = ctypes.c_int()
     E = (ctypes.c_double * max(1, int(nimg)))()
     fm = ctypes.c_double()

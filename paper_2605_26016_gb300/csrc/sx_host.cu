@@ -190,6 +190,7 @@ void free_plan(sx_ctx *c) {
   cudaFree(c->d_path);
   c->d_path = nullptr;
   c->path_bytes = 0;
+  c->path_vp_nimg = 0;
   cudaFree(c->d_taps);
   cudaFree(c->d_tap_off);
   cudaFree(c->d_work);
@@ -769,6 +770,10 @@ int sx_path_step(sx_ctx *c, double *images, int nimg, const sx_path_params *p, i
   if (!(p->dt > 0.0) || !isfinite(p->dt) || !(p->k_spring >= 0.0) || !isfinite(p->k_spring) || !(p->tol >= 0.0) ||
       p->max_iter < 0 || p->check_every < 1)
     return set_error(SX_ERR_ARG, "bad path parameters");
+  if (p->optimizer != SX_PATH_STEEPEST && p->optimizer != SX_PATH_VP)
+    return set_error(SX_ERR_ARG, "unknown path optimizer");
+  if (p->optimizer == SX_PATH_VP && p->method == SX_PATH_STRING)
+    return set_error(SX_ERR_UNSUPPORTED, "velocity projection applies to GNEB and CI-GNEB, not the string method");
   cudaError_t e =
       path_run(c, images, nimg, p, iters_out, E_host, fmax_host, (cudaStream_t)stream, backend_field_batch);
   return e == cudaSuccess ? SX_OK : cuda_error(e, "path step");

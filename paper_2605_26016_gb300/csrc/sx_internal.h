@@ -158,6 +158,7 @@ struct sx_ctx {
   int opt_scheme;     // stencil Heun scheme requested for the next plan (sx_stencil_scheme)
   double *d_path;     // path-method workspace (second chain, partial sums), allocated on first use
   size_t path_bytes;  // its size
+  int path_vp_nimg;   // chain length whose VP velocity the workspace holds (0: none)
   int launches_per_step;
 };
 

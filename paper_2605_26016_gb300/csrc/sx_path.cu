@@ -401,6 +401,104 @@ __global__ void __launch_bounds__(kPT) k_gneb_update(const double *__restrict__ 
   record_max<R>(fm, fmax_slot);
 }
 
+// Velocity projection on the GNEB force, pass 1: the force F of interior image n = blockIdx.y + 1 at every
+// site (as k_gneb_update forms it), v' = v + dt/2 (F_prev + F) (0 when first), per-block FP64 sums of v'.F and
+// F.F into partial[2 * (blockIdx.y * gridDim.x + blockIdx.x) + {0, 1}], and F stored over F_prev.
+template <typename R>
+__global__ void __launch_bounds__(kPT) k_gneb_vp_force(const double *__restrict__ X, const double *__restrict__ Y,
+                                                       long long N, const R *__restrict__ coef, R dt,
+                                                       const R *__restrict__ V, R *__restrict__ Fp, int first,
+                                                       double *__restrict__ partial,
+                                                       unsigned long long *__restrict__ fmax_slot) {
+  __shared__ double sm[kPT];
+  const int n = blockIdx.y + 1;
+  const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
+  R fm = 0;
+  double pv = 0.0, ff = 0.0;
+  if (i < N) {
+    const double *S = X + 3 * N * (long long)n;
+    R s[3], sp[3], smn[3], b[3];
+    load3<R>(S, N, i, s);
+    load3<R>(S + 3 * N, N, i, sp);
+    load3<R>(S - 3 * N, N, i, smn);
+    load3<R>(Y + 3 * N * (long long)n, N, i, b);
+    R tp[3] = {sp[0] - s[0], sp[1] - s[1], sp[2] - s[2]};
+    R tm[3] = {s[0] - smn[0], s[1] - smn[1], s[2] - smn[2]};
+    project<R>(s, tp);
+    project<R>(s, tm);
+    project<R>(s, b);
+    const R A = coef[4 * n], C = coef[4 * n + 1];
+    R F[3];
+    for (int k = 0; k < 3; ++k) F[k] = b[k] + A * tp[k] + C * tm[k];
+    fm = r_sqrt(dot3(F, F));
+    const long long base = 3 * N * (long long)n + i;
+    R pr = 0, fr = 0;
+    for (int k = 0; k < 3; ++k) {
+      const R v = first ? (R)0 : V[base + k * N] + (R)0.5 * dt * (Fp[base + k * N] + F[k]);
+      pr += v * F[k];
+      fr += F[k] * F[k];
+      Fp[base + k * N] = F[k];
+    }
+    pv = (double)pr;
+    ff = (double)fr;
+  }
+  record_max<R>(fm, fmax_slot);
+  pv = block_sum(pv, sm);
+  ff = block_sum(ff, sm);
+  if (threadIdx.x == 0) {
+    const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    partial[2 * blk] = pv;
+    partial[2 * blk + 1] = ff;
+  }
+}
+
+// pass 2: c = max(sum v'.F, 0) / sum F.F over all blocks (fixed order), as cvp[0] (FP64) and cvp[1] (FP32 bits)
+__global__ void __launch_bounds__(kPT) k_gneb_vp_coef(const double *__restrict__ partial, long long nblk,
+                                                      double *__restrict__ cvp) {
+  __shared__ double sm[kPT];
+  double pv = 0.0, ff = 0.0;
+  for (long long j = threadIdx.x; j < nblk; j += kPT) {
+    pv += partial[2 * j];
+    ff += partial[2 * j + 1];
+  }
+  pv = block_sum(pv, sm);
+  ff = block_sum(ff, sm);
+  if (threadIdx.x == 0) {
+    const double c = (pv > 0.0 && ff > 0.0) ? pv / ff : 0.0;
+    cvp[0] = c;
+    reinterpret_cast<float *>(cvp + 1)[0] = (float)c;
+  }
+}
+
+// pass 3: v = c F, S <- R_exp(S, dt c F + dt^2/2 F) from slot n of X into slot n of Y
+template <typename R>
+__global__ void __launch_bounds__(kPT) k_gneb_vp_update(const double *__restrict__ X, double *__restrict__ Y,
+                                                        long long N, const R *__restrict__ Fp, R *__restrict__ V,
+                                                        const double *__restrict__ cvp, R dt) {
+  const int n = blockIdx.y + 1;
+  const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (i >= N) return;
+  const R c = sizeof(R) == 8 ? (R)cvp[0] : (R)reinterpret_cast<const float *>(cvp + 1)[0];
+  const double *S = X + 3 * N * (long long)n;
+  double *Yn = Y + 3 * N * (long long)n;
+  R s[3];
+  load3<R>(S, N, i, s);
+  const double s64[3] = {S[i], S[N + i], S[2 * N + i]};
+  const long long base = 3 * N * (long long)n + i;
+  R u[3];
+  const R h = (R)0.5 * dt * dt;
+  for (int k = 0; k < 3; ++k) {
+    const R f = Fp[base + k * N];
+    V[base + k * N] = c * f;
+    u[k] = dt * c * f + h * f;
+  }
+  double out[3];
+  retract(s64, s, u, out);
+  Yn[i] = out[0];
+  Yn[N + i] = out[1];
+  Yn[2 * N + i] = out[2];
+}
+
 // string step, in place on interior image n = blockIdx.y + 1 of X (field in slot n of Y)
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_string_step(double *__restrict__ X, const double *__restrict__ Y, long long N,
@@ -518,6 +616,7 @@ int reduce_grid(long long N) {
 
 struct PathLayout {
   double *W, *partial, *sums, *coef, *E, *L, *eend;
+  double *V, *Fp, *vp_partial, *cvp;  // velocity projection: velocity, previous force, block sums, coefficient
   float *coeff;
   unsigned long long *fmax;
   size_t bytes;
@@ -540,6 +639,10 @@ PathLayout layout(double *base, long long N, int nimg, int nb) {
   l.L = take((size_t)nimg);
   l.eend = take(2 * kNS);
   l.fmax = (unsigned long long *)take(1);
+  l.V = take(3 * (size_t)N * nimg);
+  l.Fp = take(3 * (size_t)N * nimg);
+  l.vp_partial = take(2 * (size_t)((N + kPT - 1) / kPT) * (nimg > 2 ? nimg - 2 : 1));
+  l.cvp = take(2);
   l.bytes = off * sizeof(double);
   return l;
 }
@@ -556,9 +659,13 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
     cudaFree(c->d_path);
     c->d_path = nullptr;
     c->path_bytes = 0;
+    c->path_vp_nimg = 0;
     if ((e = cudaMalloc(&c->d_path, l.bytes)) != cudaSuccess) return e;
     c->path_bytes = l.bytes;
   }
+  const bool vp = p->optimizer == SX_PATH_VP && p->method != SX_PATH_STRING;
+  int vp_first = !(vp && p->keep_velocity && c->path_vp_nimg == M);
+  c->path_vp_nimg = 0;
   l = layout(c->d_path, N, M, nb);
   const size_t ibytes = (size_t)stride * sizeof(double);
   ZeeR<R> zr;
@@ -599,7 +706,15 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
       k_path_reduce<R, MODE_FULL><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, nsub, zr, 0, 1, l.partial);
       k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 0, l.sums);
       k_path_coef<<<1, kPT, 0, st>>>(l.sums, l.eend, M, p->method, p->k_spring, l.coef, l.coeff, l.E, l.L);
-      k_gneb_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, slot);
+      if (vp) {
+        R *Vr = reinterpret_cast<R *>(l.V), *Fr = reinterpret_cast<R *>(l.Fp);
+        k_gneb_vp_force<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, Vr, Fr, vp_first, l.vp_partial, slot);
+        k_gneb_vp_coef<<<1, kPT, 0, st>>>(l.vp_partial, (long long)nbu * (M - 2), l.cvp);
+        k_gneb_vp_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, Fr, Vr, l.cvp, dt);
+        vp_first = 0;
+      } else {
+        k_gneb_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, slot);
+      }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(X, Y);
@@ -624,6 +739,7 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
   if (E_host && (e = cudaMemcpyAsync(E_host, l.E, sizeof(double) * M, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return e;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  if (vp) c->path_vp_nimg = M;
   if (iters_out) *iters_out = it;
   if (fmax_host) *fmax_host = fmax;
   return cudaSuccess;

@@ -1,30 +1,30 @@
-"""Learned chain proposals for the string method: generate converged paths, train the proposer, compare.
+"""Learned chain proposals for minimum-energy paths: generate converged paths, train the proposer, compare.
 
-    python -m paper_2605_26016_gb300.proposer_workflow [L] [ntrain] [ntest] [train_seconds] [eval_iters] [params.npy]
+    python -m paper_2605_26016_gb300.proposer_workflow [L] [ntrain] [ntest] [train_seconds] [max_iters] [params.npy]
 
-Defaults: L = 32 (simple cubic L^3, open boundaries), 200 training paths, 12 test paths, 150 s of training,
-30000 string iterations per evaluation arm.
+Defaults: L = 32 (simple cubic L^3, open boundaries), 200 training paths, 12 test paths, 200 s of training,
+at most 20000 path iterations per run.
 
 Hamiltonian family: the four-shell frustrated exchange of the hopfion calculation (J1 = 1 meV, J2/J1 = 0.188,
 J3/J1 = -0.274, J4/J1 = -0.161), with J2..J4 scaled by seeded factors in [0.97, 1.03] and a Zeeman field
 B_z in [0, 0.04] T per path (stronger fields or larger changes shrink the barrier to nothing).  Endpoint
 A is a hopfion (Hopf ansatz of seeded radius 8..10 and centre offset +-2 sites, relaxed by velocity
-projection); endpoint B is the ferromagnet along +z.  A path is the string
-method's chain of 16 images from the geodesic interpolation of A and B, run for a fixed number of iterations
-(dt = 0.05 rad/meV); its interior images are the training targets.  Paths are generated on 8 CUDA streams
-from 8 host threads (distinct contexts are independent).
+projection); endpoint B is the ferromagnet along +z.
+
+A path is a chain of 16 images relaxed by climbing-image GNEB with velocity projection (dt = 0.05,
+k = 1 meV/rad) until the largest site force is below 1e-3 meV (J1 = 1 meV; the paper keeps the path force
+below about 1e-3 J1), in calls of 1000 iterations that carry the velocity.  Training paths start from the
+geodesic interpolation; only converged paths with a barrier between 0 and E(A) - E(B) are kept.  Paths are
+generated on 8 CUDA streams from 8 host threads (distinct contexts are independent).
 
 The proposer (include/sx.h, sx_cnn_*) is trained with Adam on (interpolated image, A, B, s) -> converged
 image over all interior images of the training paths, batches of 28 samples, cosine learning-rate decay.
 
-Evaluation on held-out Hamiltonians: each test path is run twice on one stream, from the geodesic
-interpolation (plain) and from the proposer's chain (learned), in calls of 100 iterations, recording the
-wall-clock time and the barrier max_k E_k - E_0 after each call.  The reference barrier is the lower of the
-two arms' final barriers (a converged string is a minimum-energy path, whose saddle is the lowest maximum
-along paths); an arm has reached it at the first call after which its barrier stays within 1e-3 of the
-hopfion energy scale E(A) - E(B).  For the first three test paths the plain arm then continues to three
-times the iterations, to show whether it reaches the lower barrier at all.  Prints one JSON line per stage
-and a summary.
+Evaluation on held-out Hamiltonians: each test path is relaxed twice on one stream, from the geodesic
+interpolation (plain) and from the proposer's chain (learned), recording wall-clock seconds (proposal
+included), iterations, the converged barrier (climbing-image energy minus E(A)) and the force.  Two
+converged barriers are the same when they differ by at most 1e-3 of the hopfion energy scale E(A) - E(B);
+otherwise the runs found different annihilation channels.  Prints one JSON line per stage and a summary.
 """
 import json
 import os
@@ -45,9 +45,9 @@ def main(argv):
     L = int(argv[0]) if len(argv) > 0 else 32
     ntrain = int(argv[1]) if len(argv) > 1 else 200
     ntest = int(argv[2]) if len(argv) > 2 else 12
-    train_s = float(argv[3]) if len(argv) > 3 else 150.0
-    eval_iters = int(argv[4]) if len(argv) > 4 else 30000
-    gen_iters = 15000
+    train_s = float(argv[3]) if len(argv) > 3 else 200.0
+    max_iters = int(argv[4]) if len(argv) > 4 else 20000
+    ftol, chunk = 1e-3, 1000
     nimg, dt = 16, 0.05
     n = (L, L, L)
     ncell = L ** 3
@@ -75,7 +75,19 @@ def main(argv):
         return chain
 
     # ------------------------------------------------------------ converged paths
-    def make_path(h, stream):
+    def relax(s, chain, t0, stream=None):
+        """VP CI-GNEB in calls of `chunk` iterations until the force is below ftol; returns the history."""
+        hist, done = [], 0
+        while done < max_iters:
+            it, E, fm = s.path(chain, method="ci_gneb", dt=dt, k_spring=1.0, tol=ftol, max_iter=chunk,
+                               check_every=50, optimizer="vp", keep_velocity=done > 0, stream=stream)
+            done += it
+            hist.append((done, time.perf_counter() - t0, max(E) - E[0], fm, E[0] - E[-1]))
+            if fm < ftol:
+                break
+        return hist
+
+    def make_path(h, stream, prop):
         with torch.cuda.stream(stream):
             s = system(h)
             A = torch.from_numpy(hopf_ansatz(n, h["R"], h["c"])).cuda()
@@ -87,14 +99,13 @@ def main(argv):
             chain = torch.empty((nimg, 3, ncell), dtype=torch.float64, device="cuda")
             chain[0].copy_(A.view(3, ncell))
             chain[-1].copy_(FM.view(3, ncell))
-            prop = sx.Proposer(n, nimg - 2)
             prop.interpolate(chain, stream=stream)
-            prop.close()
-            it, E, fm = s.path(chain, method="string", dt=dt, tol=0.0,
-                               max_iter=gen_iters, check_every=gen_iters, stream=stream)
+            hist = relax(s, chain, time.perf_counter(), stream)
             stream.synchronize()
             s.close()
-            return dict(A=A, chain=chain, barrier=max(E) - E[0], scale=E[0] - E[-1], fmax=fm)
+            done, _, barrier, fm, scale = hist[-1]
+            ok = fm < ftol and 0.0 < barrier < scale
+            return dict(A=A, chain=chain, barrier=barrier, scale=scale, fmax=fm, iters=done, ok=ok)
 
     t0 = time.time()
     paths = [None] * len(hams)
@@ -104,12 +115,14 @@ def main(argv):
 
     def worker():
         st = torch.cuda.Stream()
+        prop = sx.Proposer(n, nimg - 2)
         while True:
             with lock:
                 if not todo:
+                    prop.close()
                     return
                 i = todo.pop(0)
-            paths[i] = make_path(hams[i], st)
+            paths[i] = make_path(hams[i], st, prop)
 
     th = [threading.Thread(target=worker) for _ in range(nthreads)]
     for t in th:
@@ -118,11 +131,13 @@ def main(argv):
         t.join()
     torch.cuda.synchronize()
     gen_s = time.time() - t0
-    train_ids = [i for i in range(ntrain) if paths[i] is not None]
-    test_ids = [i for i in range(ntrain, ntrain + ntest) if paths[i] is not None]
-    print(json.dumps({"stage": "paths", "lattice": list(n), "images": nimg, "string_iterations": gen_iters,
-                      "train_paths": len(train_ids), "test_paths": len(test_ids),
-                      "collapsed": sum(p is None for p in paths), "seconds": gen_s,
+    train_ids = [i for i in range(ntrain) if paths[i] is not None and paths[i]["ok"]]
+    test_ids = [i for i in range(ntrain, ntrain + ntest) if paths[i] is not None and paths[i]["ok"]]
+    print(json.dumps({"stage": "paths", "lattice": list(n), "images": nimg, "method": "ci_gneb+vp",
+                      "force_tol": ftol, "train_paths": len(train_ids), "test_paths": len(test_ids),
+                      "collapsed": sum(p is None for p in paths),
+                      "unconverged": sum(p is not None and not p["ok"] for p in paths), "seconds": gen_s,
+                      "median_iterations": float(np.median([paths[i]["iters"] for i in train_ids])),
                       "barrier_range": [min(paths[i]["barrier"] for i in train_ids),
                                         max(paths[i]["barrier"] for i in train_ids)]}), flush=True)
 
@@ -188,12 +203,11 @@ def main(argv):
                       "test_mean_angle_proposal_deg": float(np.mean(err["proposal_deg"]))}), flush=True)
 
     # ------------------------------------------------------------ evaluation
-    chunk = 100
     results = []
     for i in test_ids:
         h = hams[i]
         s = system(h)
-        arms = {}
+        row = dict(path=i, B=h["B"], f=h["f"])
         for arm in ("plain", "learned"):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -202,57 +216,30 @@ def main(argv):
                 model.propose(c)
             torch.cuda.synchronize()
             t_init = time.perf_counter() - t0
-            hist = []
-            done = 0
-            while done < eval_iters:
-                it, E, fm = s.path(c, method="string", dt=dt, tol=0.0, max_iter=chunk,
-                                   check_every=chunk)
-                done += it
-                hist.append((done, time.perf_counter() - t0, max(E) - E[0], fm, E[0] - E[-1]))
-            arms[arm] = dict(hist=hist, t_init=t_init, chain=c)
-        ref = min(arms["plain"]["hist"][-1][2], arms["learned"]["hist"][-1][2])
-        scale = arms["plain"]["hist"][-1][4]
-        tol = 1e-3 * abs(scale)
-        row = dict(path=i, B=h["B"], f=h["f"], barrier_ref=ref, scale=scale, tol=tol)
-        for arm, a in arms.items():
-            hs = a["hist"]
-            k = len(hs)
-            while k > 0 and abs(hs[k - 1][2] - ref) <= tol:
-                k -= 1
-            row[arm] = dict(reached=k < len(hs), t_init=a["t_init"], first_barrier=hs[0][2],
-                            final_barrier=hs[-1][2], final_fmax=hs[-1][3])
-            if k < len(hs):
-                row[arm].update(iterations=hs[k][0], seconds=hs[k][1])
-        if len(results) < 3:
-            # the plain arm continued: does it reach the lower barrier later?
-            c_more = []
-            t0 = time.perf_counter()
-            done = 0
-            while done < 2 * eval_iters:
-                it, E, fm = s.path(arms["plain"]["chain"], method="string", dt=dt, tol=0.0, max_iter=chunk,
-                                   check_every=chunk)
-                done += it
-                if done % eval_iters == 0:
-                    c_more.append((eval_iters + done, max(E) - E[0], fm))
-            row["plain_continued"] = c_more
+            hist = relax(s, c, t0)
+            done, sec, barrier, fm, scale = hist[-1]
+            row[arm] = dict(converged=fm < ftol, iterations=done, seconds=sec, t_init=t_init, barrier=barrier,
+                            fmax=fm, first_barrier=hist[0][2])
+            row["scale"] = scale
+        row["same_barrier"] = abs(row["plain"]["barrier"] - row["learned"]["barrier"]) <= 1e-3 * abs(row["scale"])
         results.append(row)
         print(json.dumps({"stage": "eval", **row}), flush=True)
         s.close()
-    both = [r for r in results if r["plain"]["reached"] and r["learned"]["reached"]]
-    sp = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in both]
-    print(json.dumps({"stage": "summary", "test_paths": len(results), "both_reached": len(both),
-                      "plain_reached": sum(r["plain"]["reached"] for r in results),
-                      "learned_reached": sum(r["learned"]["reached"] for r in results),
-                      "lower_final_barrier": {"learned": sum(r["learned"]["final_barrier"] < r["plain"]["final_barrier"]
-                                                             for r in results),
-                                              "plain": sum(r["plain"]["final_barrier"] < r["learned"]["final_barrier"]
-                                                           for r in results)},
-                      "only_learned_reached": sum(r["learned"]["reached"] and not r["plain"]["reached"] for r in results),
-                      "only_plain_reached": sum(r["plain"]["reached"] and not r["learned"]["reached"] for r in results),
-                      "median_speedup_wall": float(np.median(sp)) if sp else None,
-                      "learned_faster": sum(r["learned"]["seconds"] < r["plain"]["seconds"] for r in both),
-                      "median_plain_s": float(np.median([r["plain"]["seconds"] for r in both])) if both else None,
-                      "median_learned_s": float(np.median([r["learned"]["seconds"] for r in both])) if both else None,
+    conv = [r for r in results if r["plain"]["converged"] and r["learned"]["converged"]]
+    same = [r for r in conv if r["same_barrier"]]
+    sp_all = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in conv]
+    sp_same = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in same]
+    print(json.dumps({"stage": "summary", "test_paths": len(results), "both_converged": len(conv),
+                      "same_barrier": len(same),
+                      "lower_barrier": {"learned": sum(r["learned"]["barrier"] < r["plain"]["barrier"] -
+                                                       1e-3 * abs(r["scale"]) for r in conv),
+                                        "plain": sum(r["plain"]["barrier"] < r["learned"]["barrier"] -
+                                                     1e-3 * abs(r["scale"]) for r in conv)},
+                      "learned_faster": sum(r["learned"]["seconds"] < r["plain"]["seconds"] for r in conv),
+                      "median_speedup_all": float(np.median(sp_all)) if sp_all else None,
+                      "median_speedup_same_barrier": float(np.median(sp_same)) if sp_same else None,
+                      "median_plain_s": float(np.median([r["plain"]["seconds"] for r in conv])) if conv else None,
+                      "median_learned_s": float(np.median([r["learned"]["seconds"] for r in conv])) if conv else None,
                       "generation_s": gen_s, "training_s": train_time}), flush=True)
 
 

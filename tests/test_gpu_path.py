@@ -180,3 +180,49 @@ def test_full_size_ci_gneb_iteration_bcc_64_32_images():
     assert np.abs(d.cpu().numpy() - ref).max() < 2e-5
     assert np.abs(np.array(E) - Er).max() < 1e-5 * np.abs(Er).max()
     assert fm == pytest.approx(fr, rel=1e-4)
+
+
+@pytest.mark.parametrize("method", ["gneb", "ci_gneb"])
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_vp_chain_iterations_match_oracle_and_carry_velocity(case, method):
+    name, n, pbc, backend, prec, tol, dt = CASES[case]
+    s, m, chain = chain_case(name, n, pbc, 7, 40 + case, B=[0.0, 0.4, 0.8])
+    s.plan(backend, prec)
+    d = dev(chain)
+    kw = dict(method=method, dt=dt, k_spring=0.5, optimizer="vp", check_every=3)
+    it, E, fm = s.path(d, max_iter=3, **kw)
+    it2, E2, fm2 = s.path(d, max_iter=3, keep_velocity=True, **kw)
+    assert it == 3 and it2 == 3
+    ref, Er, fr, st = m.gneb_vp(chain, dt=dt, k=0.5, niter=3, climbing=method == "ci_gneb")
+    ref, Er, fr, st = m.gneb_vp(ref, dt=dt, k=0.5, niter=3, climbing=method == "ci_gneb", state=st)
+    got = d.cpu().numpy()
+    assert np.array_equal(got[0], chain[0]) and np.array_equal(got[-1], chain[-1])
+    assert np.abs(got - ref).max() < tol
+    scale = max(1.0, np.abs(Er).max())
+    assert np.abs(np.array(E2) - Er).max() < (1e-11 if prec == "fp64" else 1e-5) * scale
+    assert fm2 == pytest.approx(fr, rel=1e-9 if prec == "fp64" else 1e-4)
+    # without keep_velocity the second call starts at rest: a different chain
+    d2 = dev(chain)
+    s.path(d2, max_iter=3, **kw)
+    s.path(d2, max_iter=3, **kw)
+    rest, _, _, _ = m.gneb_vp(m.gneb_vp(chain, dt=dt, k=0.5, niter=3, climbing=method == "ci_gneb")[0], dt=dt,
+                                k=0.5, niter=3, climbing=method == "ci_gneb")
+    assert np.abs(d2.cpu().numpy() - rest).max() < tol
+    assert np.abs(rest - ref).max() > 5 * tol
+
+
+def test_vp_ci_gneb_converges_macrospin_faster():
+    s, m = macrospin_pair()
+    s.plan("gather", "fp64")
+    chain = polar_chain(THETA0, np.pi - THETA0, 9, phi_bulge=0.8)
+    d = dev(chain)
+    it, E, fm = s.path(d, method="ci_gneb", dt=0.1, k_spring=1.0, tol=1e-10, max_iter=6000, check_every=10,
+                       optimizer="vp")
+    d2 = dev(chain)
+    it_sd, _, _ = s.path(d2, method="ci_gneb", dt=0.1, k_spring=1.0, tol=1e-10, max_iter=6000, check_every=10)
+    assert fm < 1e-10 and it < it_sd / 2
+    top = int(np.argmax(E[1:-1])) + 1
+    assert E[top] - E[0] == pytest.approx(K * (1 - H / (2 * K)) ** 2, abs=1e-12)
+    with pytest.raises(sx.SxError) as e:
+        s.path(d, method="string", optimizer="vp", max_iter=1)
+    assert e.value.code == sx.SX_ERR_UNSUPPORTED
