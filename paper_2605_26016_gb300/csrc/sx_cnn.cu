@@ -36,17 +36,19 @@
 // (kind::f16) and tcgen05.commit; every wait is bounded and sets an error flag
 // instead of hanging.  Epilogues read TMEM with tcgen05.ld and fuse bias and
 // ReLU (forward), the normalisation, loss and loss gradient (last layer), or
-// the ReLU mask (input gradient).
+// the ReLU mask (input gradient).  The head forms the proposal in FP64 and the
+// training loss and dL/dZ in FP32.
 //
-// Weight gradients sum g_out[s][o] x act[s + tap][c] over all sites: CUDA-core
-// FMAs on a shared-memory window, per-CTA partial sums in FP32 reduced over
-// CTAs in FP64 in a fixed order (deterministic).
+// Weight gradients sum g_out[s][o] x act[s + tap][c] over all sites: an
+// im2col GEMM on the tensor cores with the sites as K, per-CTA partial sums
+// reduced over CTAs in FP64 in a fixed order (deterministic).
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
 
 #include <new>
 
+#include "sx_device.cuh"
 #include "sx_internal.h"
 
 struct sx_cnn;
@@ -76,7 +78,6 @@ constexpr int kBZF = 4;               // output z planes per CTA, forward
 constexpr int kBZD = 2;               // output z planes per CTA, input gradient
 constexpr int kZW = 8;                // z planes per weight-gradient CTA (two at a time)
 constexpr int kPart = kTaps * 256 + 16;  // one partial: gw[tap][o][c] then gb[o]
-constexpr int kWgThreads = 216;          // 2 halves x 27 taps x 4 input-channel quads
 
 enum Mode { FWD = 0, HEAD = 1, DGRAD = 2 };
 
@@ -140,7 +141,7 @@ struct ConvArgs {
   const double *I;            // HEAD: interpolated images [nb][3][ncell]
   const double *T;            // HEAD: targets [nb][3][ncell] or null
   double *P;                  // HEAD: proposals [nb][3][ncell] or null (may equal I)
-  double inv_m;               // HEAD: 1 / (nb ncell)
+  float inv_mf;               // HEAD: 1 / (nb ncell)
   double *loss_part;          // HEAD: per-CTA sums of (1 - P.T)
   int *err;
 };
@@ -278,26 +279,43 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs p) {
         dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
       } else if (MODE == HEAD) {
         const long long i0 = (long long)blockIdx.z * 3 * p.ncell + cell;
-        double Z[3];
+        float Y[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) Z[k] = p.I[i0 + k * p.ncell] + (double)(__uint_as_float(r[k]) + bias[k]);
-        const double rn = 1.0 / sqrt(Z[0] * Z[0] + Z[1] * Z[1] + Z[2] * Z[2]);
-        const double P0 = Z[0] * rn, P1 = Z[1] * rn, P2 = Z[2] * rn;
+        for (int k = 0; k < 3; ++k) Y[k] = __uint_as_float(r[k]) + bias[k];
         if (p.P) {
-          p.P[i0] = P0;
-          p.P[i0 + p.ncell] = P1;
-          p.P[i0 + 2 * p.ncell] = P2;
+          // P = Z / |Z| in FP64: 1/|Z| from an FP32 estimate and two Newton steps (FP64 division and square
+          // root run on the FP64 pipe, 1/70 of the FP32 rate on this part)
+          double Z[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) Z[k] = p.I[i0 + k * p.ncell] + f32_to_f64(Y[k]);
+          const double z2 = Z[0] * Z[0] + Z[1] * Z[1] + Z[2] * Z[2];
+          double rn = f32_to_f64(rsqrtf(f64_to_f32(z2)));
+          rn = rn * (1.5 - 0.5 * z2 * rn * rn);
+          rn = rn * (1.5 - 0.5 * z2 * rn * rn);
+          p.P[i0] = Z[0] * rn;
+          p.P[i0 + p.ncell] = Z[1] * rn;
+          p.P[i0 + 2 * p.ncell] = Z[2] * rn;
         }
         if (p.T) {
-          const double T0 = p.T[i0], T1 = p.T[i0 + p.ncell], T2 = p.T[i0 + 2 * p.ncell];
-          const double dot = P0 * T0 + P1 * T1 + P2 * T2;
-          lsum += 1.0 - dot;
-          // dL/dP = -T / m; dL/dZ = (dL/dP - (dL/dP . P) P) / |Z|
-          const double g0 = -T0 * p.inv_m, g1 = -T1 * p.inv_m, g2 = -T2 * p.inv_m;
-          const double gp = g0 * P0 + g1 * P1 + g2 * P2;
+          // loss term and dL/dZ in FP32 (dL/dZ is stored in FP32): P = Z / |Z|, 1 - P.T = |P - T|^2 / 2 for
+          // unit P and T, dL/dP = -T / m, dL/dZ = (dL/dP - (dL/dP . P) P) / |Z|
+          float Zf[3], Tf[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            Zf[k] = f64_to_f32(p.I[i0 + k * p.ncell]) + Y[k];
+            Tf[k] = f64_to_f32(p.T[i0 + k * p.ncell]);
+          }
+          const float z2 = Zf[0] * Zf[0] + Zf[1] * Zf[1] + Zf[2] * Zf[2];
+          float rn = rsqrtf(z2);
+          rn = rn * (1.5f - 0.5f * z2 * rn * rn);
+          const float P0 = Zf[0] * rn, P1 = Zf[1] * rn, P2 = Zf[2] * rn;
+          const float d0 = P0 - Tf[0], d1 = P1 - Tf[1], d2 = P2 - Tf[2];
+          lsum += (double)(0.5f * (d0 * d0 + d1 * d1 + d2 * d2));
+          const float im = p.inv_mf;
+          const float g0 = -Tf[0] * im, g1 = -Tf[1] * im, g2 = -Tf[2] * im;
+          const float gp = g0 * P0 + g1 * P1 + g2 * P2;
           float4 *dst = reinterpret_cast<float4 *>(p.g_out + site * kC);
-          dst[0] = make_float4((float)((g0 - gp * P0) * rn), (float)((g1 - gp * P1) * rn),
-                               (float)((g2 - gp * P2) * rn), 0.0f);
+          dst[0] = make_float4((g0 - gp * P0) * rn, (g1 - gp * P1) * rn, (g2 - gp * P2) * rn, 0.0f);
           const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
           dst[1] = zero;
           dst[2] = zero;
@@ -333,40 +351,65 @@ __global__ void __launch_bounds__(kThreads) k_conv(const ConvArgs p) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TCOLS));
 }
 
-// Weight and bias gradients of one layer: per CTA a 16 x 16 x kZW block of sites of one sample, processed two
-// z planes at a time.  Thread (half, tap, quad) accumulates gw[tap][o][4 quad .. 4 quad + 3] for all 16 o over
-// the sites of z plane `half` of each pair; threads with (tap, quad) index < 16 also sum gb[o].  Each half writes
-// its own partial (2 per CTA).
+// Weight and bias gradients of one layer on the tensor cores.  gw[tap][o][c] = sum_s act[s + tap][c] g[s][o]
+// is a GEMM with the sites as K: D[(tap, c)][o] += A[(tap, c)][s] B[s][o].  A CTA owns a 16 x 16 x kZW block of
+// sites of one sample and walks it in K blocks of 64 sites (4 y rows x 16 x of one z plane):
+//  * the channels-last input window of a z pair (18 x 18 x 4 sites, zero outside the lattice) is staged in
+//    shared memory;
+//  * per K block the im2col operand A is gathered from the window: rows (tap, c) in four M = 128 groups of
+//    eight taps (taps 27..31 of the last group are never written and their rows of D are not read), eight
+//    consecutive x sites per 16-byte core-matrix row;
+//  * B holds g of the 64 sites split into BF16 hi and lo parts as N = 32 columns (o hi, o lo), so one
+//    128 x 32 x 16 MMA per group and K step accumulates both parts, summed in the epilogue;
+//  * one thread issues the 16 MMAs of a K block and commits; all threads wait (bounded) before the operands
+//    are rebuilt.
+// Each CTA writes one partial gw[tap][o][c], gb[o]; gb is summed on the CUDA cores from the same g values.
 struct WgradArgs {
   int nx, ny, nz, tiles_x;
   long long ncell;
   const float *g;          // gradient of the layer output [nb][ncell][16]
   const uint16_t *act;     // layer input [nb][ncell][16] BF16
-  float *part;             // [2 * nblocks][kPart]
+  float *part;             // [nblocks][kPart]
+  int *err;
 };
 
-constexpr int kWgRows = kWX * kWY * 4;  // window of a z pair: 18 x 18 x 4 sites
-constexpr size_t kWgSmem = (size_t)kWgRows * 32 + (size_t)2 * kBX * kBY * kC * 4;
+constexpr int kWgThreads = 256;
+constexpr int kWgRows = kWX * kWY * 4;              // window of a z pair: 18 x 18 x 4 sites
+constexpr uint32_t kWgAGroup = 128 * 64 * 2;        // one M group of A: 128 rows x 64 sites BF16
+constexpr uint32_t kWgA = 4 * kWgAGroup;
+constexpr uint32_t kWgB = 32 * 64 * 2;
+constexpr size_t kWgSmem = (size_t)kWgRows * 32 + kWgA + kWgB + 128 * 4 + 64;
 
 __global__ void __launch_bounds__(kWgThreads) k_wgrad(const WgradArgs p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint16_t *sA = reinterpret_cast<uint16_t *>(smem);                   // [row][16] BF16
-  float *sG = reinterpret_cast<float *>(smem + (size_t)kWgRows * 32);  // [zl][y][x][16]
-  const int tid = threadIdx.x;
-  const int half = tid / 108, task = tid % 108;
-  const int tap = task >> 2, quad = task & 3;
-  const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+  uint16_t *sWin = reinterpret_cast<uint16_t *>(smem);  // [row][16] BF16
+  unsigned char *sA = smem + (size_t)kWgRows * 32;
+  unsigned char *sB = sA + kWgA;
+  float *sGb = reinterpret_cast<float *>(sB + kWgB);  // [8][16] bias partials
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(sGb + 128);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int bxy = blockIdx.x;
   const int x0 = (bxy % p.tiles_x) * kBX, y0 = (bxy / p.tiles_x) * kBY, zb = blockIdx.y * kZW;
   const long long sbase = (long long)blockIdx.z * p.ncell;
-  float acc[16][4];
-#pragma unroll
-  for (int o = 0; o < 16; ++o)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[o][c] = 0.0f;
-  float gb = 0.0f;
-  for (int z0 = zb; z0 < zb + kZW && z0 < p.nz; z0 += 2) {
-    __syncthreads();
+
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(mbar)));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(saddr(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  // kind::f16: D FP32, A and B BF16, both K-major, N = 32, M = 128
+  constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(32 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  float gbacc = 0.0f;
+  uint32_t phase = 0;
+  bool alive = true;
+  int kblk = 0;
+  for (int z0 = zb; z0 < zb + kZW && z0 < p.nz && alive; z0 += 2) {
+    // window rows (zw, yw, xw) of z planes z0 - 1 .. z0 + 2 (the previous K block's MMAs have completed)
     for (int e = tid; e < kWgRows * 2; e += kWgThreads) {
       const int ch = e & 1, r = e >> 1;
       const int xw = r % kWX, q = r / kWX, yw = q % kWY, zw = q / kWY;
@@ -374,52 +417,109 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const WgradArgs p) {
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       if (gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny && gz >= 0 && gz < p.nz)
         v = __ldg(reinterpret_cast<const uint4 *>(p.act + (sbase + ((long long)gz * p.ny + gy) * p.nx + gx) * kC) + ch);
-      reinterpret_cast<uint4 *>(sA)[2 * r + ch] = v;
+      reinterpret_cast<uint4 *>(sWin)[2 * r + ch] = v;
     }
-    for (int e = tid; e < 2 * kBX * kBY * 4; e += kWgThreads) {
-      const int q4 = e & 3, s = e >> 2;
-      const int xl = s % kBX, yl = (s / kBX) % kBY, zl = s / (kBX * kBY);
-      const int gx = x0 + xl, gy = y0 + yl, gz = z0 + zl;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gx < p.nx && gy < p.ny && gz < p.nz)
-        v = __ldg(reinterpret_cast<const float4 *>(p.g + (sbase + ((long long)gz * p.ny + gy) * p.nx + gx) * kC) + q4);
-      reinterpret_cast<float4 *>(sG)[4 * s + q4] = v;
-    }
-    __syncthreads();
-    const float4 *gp = reinterpret_cast<const float4 *>(sG) + (size_t)half * kBX * kBY * 4;
-    for (int yl = 0; yl < kBY; ++yl) {
-      const int rowb = ((half + 1 + dz) * kWY + (yl + 1 + dy)) * kWX + 1 + dx;
-#pragma unroll 2
-      for (int xl = 0; xl < kBX; ++xl) {
-        const uint2 av = *reinterpret_cast<const uint2 *>(sA + (rowb + xl) * kC + 4 * quad);
-        const float a0 = bf16_lo(av.x), a1 = bf16_hi(av.x), a2 = bf16_lo(av.y), a3 = bf16_hi(av.y);
-        const float4 *gs = gp + (yl * kBX + xl) * 4;
+    for (int zl = 0; zl < 2 && alive; ++zl) {
+      for (int yq = 0; yq < 4 && alive; ++yq) {
+        __syncthreads();  // window staged; previous operands consumed
+        if (tid < 128) {
+          // B: sites k = 8 kc + j (y = 4 yq + kc / 2, x = 8 (kc % 2) + j), column o (hi) and 16 + o (lo)
+          const int kc = tid >> 4, o = tid & 15;
+          const int gy = y0 + 4 * yq + (kc >> 1), gz = z0 + zl, gx0 = x0 + 8 * (kc & 1);
+          float v[8];
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          const float4 g = gs[q4];
-          const float gv[4] = {g.x, g.y, g.z, g.w};
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            acc[4 * q4 + j][0] = fmaf(gv[j], a0, acc[4 * q4 + j][0]);
-            acc[4 * q4 + j][1] = fmaf(gv[j], a1, acc[4 * q4 + j][1]);
-            acc[4 * q4 + j][2] = fmaf(gv[j], a2, acc[4 * q4 + j][2]);
-            acc[4 * q4 + j][3] = fmaf(gv[j], a3, acc[4 * q4 + j][3]);
+          for (int j = 0; j < 8; ++j) {
+            const int gx = gx0 + j;
+            v[j] = (gx < p.nx && gy < p.ny && gz < p.nz)
+                       ? __ldg(p.g + (sbase + ((long long)gz * p.ny + gy) * p.nx + gx) * kC + o)
+                       : 0.0f;
+            gbacc += v[j];
           }
+          uint4 hi, lo;
+          split_bf16(v[0], v[1], hi.x, lo.x);
+          split_bf16(v[2], v[3], hi.y, lo.y);
+          split_bf16(v[4], v[5], hi.z, lo.z);
+          split_bf16(v[6], v[7], hi.w, lo.w);
+          *reinterpret_cast<uint4 *>(sB + kc * 512 + (o >> 3) * 128 + (o & 7) * 16) = hi;
+          *reinterpret_cast<uint4 *>(sB + kc * 512 + ((16 + o) >> 3) * 128 + (o & 7) * 16) = lo;
         }
+        // A: row m = 16 (tap % 8) + c of group tap / 8, 16-byte chunk of sites 8 kc .. 8 kc + 7
+        for (int e = tid; e < kTaps * 16 * 8; e += kWgThreads) {
+          const int c = e & 15, kc = (e >> 4) & 7, t = e >> 7;
+          const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+          const int row = ((zl + 1 + dz) * kWY + (4 * yq + (kc >> 1) + 1 + dy)) * kWX + 8 * (kc & 1) + 1 + dx;
+          const uint16_t *src = sWin + row * kC + c;
+          uint4 w;
+          w.x = (uint32_t)src[0] | ((uint32_t)src[kC] << 16);
+          w.y = (uint32_t)src[2 * kC] | ((uint32_t)src[3 * kC] << 16);
+          w.z = (uint32_t)src[4 * kC] | ((uint32_t)src[5 * kC] << 16);
+          w.w = (uint32_t)src[6 * kC] | ((uint32_t)src[7 * kC] << 16);
+          const int m = 16 * (t & 7) + c;
+          *reinterpret_cast<uint4 *>(sA + (t >> 3) * kWgAGroup + kc * 2048 + (m >> 3) * 128 + (m & 7) * 16) = w;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int G = 0; G < 4; ++G) {
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t ad = smem_desc(saddr(sA) + G * kWgAGroup + ks * 2 * 2048, 2048u, 128u);
+              const uint64_t bd = smem_desc(saddr(sB) + ks * 2 * 512, 512u, 128u);
+              const uint32_t acc = (kblk > 0 || ks > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n.reg .pred q;\nsetp.ne.u32 q, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(
+                      tmem + (uint32_t)(G * 32)),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar))
+                       : "memory");
+        }
+        alive = __syncthreads_and(wait_parity(mbar, phase, p.err) ? 1 : 0) != 0;
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        ++kblk;
       }
     }
-    if (task < 16) {
-      const float *gsum = sG + (size_t)half * kBX * kBY * kC + task;
-      for (int s = 0; s < kBX * kBY; ++s) gb += gsum[(size_t)s * kC];
-    }
+    __syncthreads();
   }
+  if (tid < 128) sGb[tid] = gbacc;
+  __syncthreads();
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  float *out = p.part + (size_t)(2 * blk + half) * kPart;
+  float *out = p.part + (size_t)blk * kPart;
+  if (tid < 16) {
+    float sgb = 0.0f;
+    for (int k = 0; k < 8; ++k) sgb += sGb[k * 16 + tid];
+    out[kTaps * 256 + tid] = sgb;
+  }
+  if (alive && kblk > 0) {
+    // row m = 32 (warp % 4) + lane of groups warp / 4 and warp / 4 + 2: tap 8 G + m / 16, channel m % 16
+    const int q = warp & 3;
+    for (int G = warp >> 2; G < 4; G += 2) {
+      uint32_t r[32];
+      const uint32_t a = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(G * 32);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+          "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(a));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int m = q * 32 + lane, t = 8 * G + (m >> 4), c = m & 15;
+      if (t < kTaps) {
 #pragma unroll
-  for (int o = 0; o < 16; ++o)
-    *reinterpret_cast<float4 *>(out + tap * 256 + o * 16 + 4 * quad) =
-        make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
-  if (task < 16) out[kTaps * 256 + task] = gb;
+        for (int o = 0; o < 16; ++o) out[t * 256 + o * 16 + c] = __uint_as_float(r[o]) + __uint_as_float(r[16 + o]);
+      }
+    }
+  } else {
+    // no K block ran (or a wait gave up): zero weight partials
+    for (int e = tid; e < kTaps * 256; e += kWgThreads) out[e] = 0.0f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
 // grad for every parameter: the FP64 sum over the partials of its layer.  Block (x, l) with 32 x 8 threads
@@ -655,13 +755,14 @@ cudaError_t launch_wgrad(const sx_cnn *h, int nb, const float *g, const uint16_t
   a.g = g;
   a.act = act;
   a.part = part;
+  a.err = h->err;
   const dim3 grid((unsigned)(h->tiles_x * h->tiles_y), (unsigned)((h->n[2] + kZW - 1) / kZW), (unsigned)nb);
   k_wgrad<<<grid, kWgThreads, kWgSmem, st>>>(a);
   return cudaGetLastError();
 }
 
 long long wgrad_slots(const sx_cnn *h, int nb) {
-  return 2LL * h->tiles_x * h->tiles_y * ((h->n[2] + kZW - 1) / kZW) * nb;
+  return 1LL * h->tiles_x * h->tiles_y * ((h->n[2] + kZW - 1) / kZW) * nb;
 }
 long long head_blocks(const sx_cnn *h, int nb) {
   return (long long)h->tiles_x * h->tiles_y * ((h->n[2] + kBZF - 1) / kBZF) * nb;
@@ -690,7 +791,7 @@ cudaError_t forward(sx_cnn *h, const uint16_t *X, const double *I, const double 
   a.I = I;
   a.T = T;
   a.P = P;
-  a.inv_m = 1.0 / ((double)nb * (double)h->ncell);
+  a.inv_mf = (float)(1.0 / ((double)nb * (double)h->ncell));
   a.g_out = h->g[0];
   a.loss_part = h->loss_part;
   return launch_conv<HEAD, kBZF>(h, nb, a, st);

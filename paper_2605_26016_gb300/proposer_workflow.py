@@ -1,6 +1,7 @@
 """Learned chain proposals for minimum-energy paths: generate converged paths, train the proposer, compare.
 
-    python -m paper_2605_26016_gb300.proposer_workflow [L] [ntrain] [ntest] [train_seconds] [max_iters] [params.npy]
+    python -m paper_2605_26016_gb300.proposer_workflow [L] [ntrain] [ntest] [train_seconds] [max_iters] \
+        [params_out.npy] [params_in.npy]
 
 Defaults: L = 32 (simple cubic L^3, open boundaries), 200 training paths, 12 test paths, 200 s of training,
 at most 20000 path iterations per run.
@@ -11,9 +12,12 @@ B_z in [0, 0.04] T per path (stronger fields or larger changes shrink the barrie
 A is a hopfion (Hopf ansatz of seeded radius 8..10 and centre offset +-2 sites, relaxed by velocity
 projection); endpoint B is the ferromagnet along +z.
 
-A path is a chain of 16 images relaxed by climbing-image GNEB with velocity projection (dt = 0.05,
-k = 1 meV/rad) until the largest site force is below 1e-3 meV (J1 = 1 meV; the paper keeps the path force
-below about 1e-3 J1), in calls of 1000 iterations that carry the velocity.  Training paths start from the
+A path is a chain of 16 images relaxed with velocity projection (dt = 0.05, k = 1 meV/rad, calls of 1000
+iterations that carry the velocity) in two stages, as GNEB refinement is followed by climbing-image
+refinement in the paper: GNEB until the largest site force is below 1e-2 meV, then CI-GNEB from rest until
+it is below 1e-3 meV (J1 = 1 meV; the paper keeps the path force below about 1e-3 J1), at most max_iters
+iterations in all.  A run whose barrier exceeds the hopfion energy scale E(A) - E(B) has left the basin of
+the path and is stopped as diverged.  Training paths start from the
 geodesic interpolation; only converged paths with a barrier between 0 and E(A) - E(B) are kept.  Paths are
 generated on 8 CUDA streams from 8 host threads (distinct contexts are independent).
 
@@ -21,8 +25,10 @@ The proposer (include/sx.h, sx_cnn_*) is trained with Adam on (interpolated imag
 image over all interior images of the training paths, batches of 28 samples, cosine learning-rate decay.
 
 Evaluation on held-out Hamiltonians: each test path is relaxed twice on one stream, from the geodesic
-interpolation (plain) and from the proposer's chain (learned), recording wall-clock seconds (proposal
-included), iterations, the converged barrier (climbing-image energy minus E(A)) and the force.  Two
+interpolation (plain) and from the proposer's chain (learned, falling back to the geodesic interpolation
+when its run diverges, the fallback's time included), recording wall-clock seconds (proposal included),
+iterations, the converged barrier (climbing-image energy minus E(A)) and the force.  With params_in the
+training paths and the training are skipped and the proposer's parameters are read from that file.  Two
 converged barriers are the same when they differ by at most 1e-3 of the hopfion energy scale E(A) - E(B);
 otherwise the runs found different annihilation channels.  Prints one JSON line per stage and a summary.
 """
@@ -76,16 +82,21 @@ def main(argv):
 
     # ------------------------------------------------------------ converged paths
     def relax(s, chain, t0, stream=None):
-        """VP CI-GNEB in calls of `chunk` iterations until the force is below ftol; returns the history."""
+        """Two-stage VP relaxation (GNEB to 1e-2 meV, then CI-GNEB from rest to ftol); returns (history,
+        converged, diverged)."""
         hist, done = [], 0
-        while done < max_iters:
-            it, E, fm = s.path(chain, method="ci_gneb", dt=dt, k_spring=1.0, tol=ftol, max_iter=chunk,
-                               check_every=50, optimizer="vp", keep_velocity=done > 0, stream=stream)
-            done += it
-            hist.append((done, time.perf_counter() - t0, max(E) - E[0], fm, E[0] - E[-1]))
-            if fm < ftol:
-                break
-        return hist
+        for method, tol, cap in (("gneb", 1e-2, max_iters // 2), ("ci_gneb", ftol, max_iters)):
+            start = done
+            while done < cap:
+                it, E, fm = s.path(chain, method=method, dt=dt, k_spring=1.0, tol=tol, max_iter=chunk,
+                                   check_every=50, optimizer="vp", keep_velocity=done > start, stream=stream)
+                done += it
+                hist.append((done, time.perf_counter() - t0, max(E) - E[0], fm, E[0] - E[-1]))
+                if max(E) - E[0] > E[0] - E[-1]:
+                    return hist, False, True
+                if fm < tol:
+                    break
+        return hist, hist[-1][3] < ftol, False
 
     def make_path(h, stream, prop):
         with torch.cuda.stream(stream):
@@ -100,18 +111,19 @@ def main(argv):
             chain[0].copy_(A.view(3, ncell))
             chain[-1].copy_(FM.view(3, ncell))
             prop.interpolate(chain, stream=stream)
-            hist = relax(s, chain, time.perf_counter(), stream)
+            hist, conv, _ = relax(s, chain, time.perf_counter(), stream)
             stream.synchronize()
             s.close()
             done, _, barrier, fm, scale = hist[-1]
-            ok = fm < ftol and 0.0 < barrier < scale
+            ok = conv and 0.0 < barrier < scale
             return dict(A=A, chain=chain, barrier=barrier, scale=scale, fmax=fm, iters=done, ok=ok)
 
+    params_in = argv[6] if len(argv) > 6 else None
     t0 = time.time()
     paths = [None] * len(hams)
     nthreads = 8
     lock = threading.Lock()
-    todo = list(range(len(hams)))
+    todo = list(range(ntrain if params_in else 0, len(hams)))
 
     def worker():
         st = torch.cuda.Stream()
@@ -132,58 +144,63 @@ def main(argv):
     torch.cuda.synchronize()
     gen_s = time.time() - t0
     train_ids = [i for i in range(ntrain) if paths[i] is not None and paths[i]["ok"]]
+    train_ids = train_ids if not params_in else []
     test_ids = [i for i in range(ntrain, ntrain + ntest) if paths[i] is not None and paths[i]["ok"]]
     print(json.dumps({"stage": "paths", "lattice": list(n), "images": nimg, "method": "ci_gneb+vp",
                       "force_tol": ftol, "train_paths": len(train_ids), "test_paths": len(test_ids),
-                      "collapsed": sum(p is None for p in paths),
+                      "collapsed": sum(paths[i] is None for i in range(ntrain if params_in else 0, len(hams))),
                       "unconverged": sum(p is not None and not p["ok"] for p in paths), "seconds": gen_s,
-                      "median_iterations": float(np.median([paths[i]["iters"] for i in train_ids])),
-                      "barrier_range": [min(paths[i]["barrier"] for i in train_ids),
-                                        max(paths[i]["barrier"] for i in train_ids)]}), flush=True)
+                      "median_iterations": float(np.median([paths[i]["iters"] for i in train_ids + test_ids])),
+                      "barrier_range": [min(paths[i]["barrier"] for i in train_ids + test_ids),
+                                        max(paths[i]["barrier"] for i in train_ids + test_ids)]}), flush=True)
 
     # ------------------------------------------------------------ training set
-    nint = nimg - 2
-    ns = len(train_ids) * nint
-    X = torch.empty((ns, ncell, 16), dtype=torch.int16, device="cuda")
-    I = torch.empty((ns, 3, ncell), dtype=torch.float64, device="cuda")
-    T = torch.empty((ns, 3, ncell), dtype=torch.float64, device="cuda")
-    svals = torch.tensor([k / (nimg - 1) for k in range(1, nimg - 1)], dtype=torch.float64, device="cuda")
-    for j, i in enumerate(train_ids):
-        g = geodesic_chain(paths[i]["A"])
-        sl = slice(j * nint, (j + 1) * nint)
-        I[sl].copy_(g[1:-1])
-        T[sl].copy_(paths[i]["chain"][1:-1])
-        helper.pack(I[sl], paths[i]["A"], FM, svals, X[sl], shared_endpoints=True)
-    batch = 2 * nint
+    batch = 2 * (nimg - 2)
     model = sx.Proposer(n, batch)
-    model.set_params(cnn_init_flat(7))
-    gen = torch.Generator(device="cpu").manual_seed(11)
-    lr0, lr1 = 2e-3, 5e-5
-    steps, losses = 0, []
-    t0 = time.time()
-    est_steps = None
-    while True:
-        perm = torch.randperm(ns, generator=gen).cuda()
-        for b0 in range(0, ns - batch + 1, batch):
-            idx = perm[b0:b0 + batch]
-            Xb, Ib, Tb = X.index_select(0, idx), I.index_select(0, idx), T.index_select(0, idx)
-            loss = model.loss_grad(Xb, Ib, Tb)
-            el = time.time() - t0
-            if est_steps is None and steps == 20:
-                est_steps = int(20 * train_s / max(el, 1e-6))
-            frac = min(1.0, steps / est_steps) if est_steps else 0.0
-            lr = lr1 + 0.5 * (lr0 - lr1) * (1 + np.cos(np.pi * frac))
-            model.adam_step(lr)
-            losses.append(loss)
-            steps += 1
-            if el > train_s:
+    ns, steps, losses, train_time = 0, 0, [float("nan")], 0.0
+    if params_in:
+        model.set_params(np.load(params_in))
+    else:
+        nint = nimg - 2
+        ns = len(train_ids) * nint
+        X = torch.empty((ns, ncell, 16), dtype=torch.int16, device="cuda")
+        I = torch.empty((ns, 3, ncell), dtype=torch.float64, device="cuda")
+        T = torch.empty((ns, 3, ncell), dtype=torch.float64, device="cuda")
+        svals = torch.tensor([k / (nimg - 1) for k in range(1, nimg - 1)], dtype=torch.float64, device="cuda")
+        for j, i in enumerate(train_ids):
+            g = geodesic_chain(paths[i]["A"])
+            sl = slice(j * nint, (j + 1) * nint)
+            I[sl].copy_(g[1:-1])
+            T[sl].copy_(paths[i]["chain"][1:-1])
+            helper.pack(I[sl], paths[i]["A"], FM, svals, X[sl], shared_endpoints=True)
+        model.set_params(cnn_init_flat(7))
+        gen = torch.Generator(device="cpu").manual_seed(11)
+        lr0, lr1 = 2e-3, 5e-5
+        steps, losses = 0, []
+        t0 = time.time()
+        est_steps = None
+        while True:
+            perm = torch.randperm(ns, generator=gen).cuda()
+            for b0 in range(0, ns - batch + 1, batch):
+                idx = perm[b0:b0 + batch]
+                Xb, Ib, Tb = X.index_select(0, idx), I.index_select(0, idx), T.index_select(0, idx)
+                loss = model.loss_grad(Xb, Ib, Tb)
+                el = time.time() - t0
+                if est_steps is None and steps == 20:
+                    est_steps = int(20 * train_s / max(el, 1e-6))
+                frac = min(1.0, steps / est_steps) if est_steps else 0.0
+                lr = lr1 + 0.5 * (lr0 - lr1) * (1 + np.cos(np.pi * frac))
+                model.adam_step(lr)
+                losses.append(loss)
+                steps += 1
+                if el > train_s:
+                    break
+            if time.time() - t0 > train_s:
                 break
-        if time.time() - t0 > train_s:
-            break
-    torch.cuda.synchronize()
-    train_time = time.time() - t0
-    if len(argv) > 5:
-        np.save(argv[5], model.get_params())
+        torch.cuda.synchronize()
+        train_time = time.time() - t0
+        if len(argv) > 5:
+            np.save(argv[5], model.get_params())
 
     def angles(P, Tt):
         d = (P * Tt).sum(1).clamp(-1, 1)
@@ -216,10 +233,18 @@ def main(argv):
                 model.propose(c)
             torch.cuda.synchronize()
             t_init = time.perf_counter() - t0
-            hist = relax(s, c, t0)
+            hist, conv, div = relax(s, c, t0)
+            fallback = False
+            if arm == "learned" and div:
+                # the geodesic interpolation as fallback, after the diverged run
+                spent = hist[-1][0]
+                c = geodesic_chain(paths[i]["A"])
+                hist, conv, div = relax(s, c, t0)
+                hist = [(h_[0] + spent,) + tuple(h_[1:]) for h_ in hist]
+                fallback = True
             done, sec, barrier, fm, scale = hist[-1]
-            row[arm] = dict(converged=fm < ftol, iterations=done, seconds=sec, t_init=t_init, barrier=barrier,
-                            fmax=fm, first_barrier=hist[0][2])
+            row[arm] = dict(converged=conv, diverged=div, fallback=fallback, iterations=done, seconds=sec,
+                            t_init=t_init, barrier=barrier, fmax=fm, first_barrier=hist[0][2])
             row["scale"] = scale
         row["same_barrier"] = abs(row["plain"]["barrier"] - row["learned"]["barrier"]) <= 1e-3 * abs(row["scale"])
         results.append(row)
@@ -229,7 +254,10 @@ def main(argv):
     same = [r for r in conv if r["same_barrier"]]
     sp_all = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in conv]
     sp_same = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in same]
+    direct = [r for r in conv if not r["learned"]["fallback"]]
+    sp_direct = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in direct]
     print(json.dumps({"stage": "summary", "test_paths": len(results), "both_converged": len(conv),
+                      "learned_fallbacks": sum(r["learned"]["fallback"] for r in results),
                       "same_barrier": len(same),
                       "lower_barrier": {"learned": sum(r["learned"]["barrier"] < r["plain"]["barrier"] -
                                                        1e-3 * abs(r["scale"]) for r in conv),
@@ -238,6 +266,7 @@ def main(argv):
                       "learned_faster": sum(r["learned"]["seconds"] < r["plain"]["seconds"] for r in conv),
                       "median_speedup_all": float(np.median(sp_all)) if sp_all else None,
                       "median_speedup_same_barrier": float(np.median(sp_same)) if sp_same else None,
+                      "median_speedup_without_fallback": float(np.median(sp_direct)) if sp_direct else None,
                       "median_plain_s": float(np.median([r["plain"]["seconds"] for r in conv])) if conv else None,
                       "median_learned_s": float(np.median([r["learned"]["seconds"] for r in conv])) if conv else None,
                       "generation_s": gen_s, "training_s": train_time}), flush=True)
