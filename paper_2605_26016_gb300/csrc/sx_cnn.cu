@@ -443,19 +443,30 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad(const WgradArgs p) {
           *reinterpret_cast<uint4 *>(sB + kc * 512 + (o >> 3) * 128 + (o & 7) * 16) = hi;
           *reinterpret_cast<uint4 *>(sB + kc * 512 + ((16 + o) >> 3) * 128 + (o & 7) * 16) = lo;
         }
-        // A: row m = 16 (tap % 8) + c of group tap / 8, 16-byte chunk of sites 8 kc .. 8 kc + 7
-        for (int e = tid; e < kTaps * 16 * 8; e += kWgThreads) {
-          const int c = e & 15, kc = (e >> 4) & 7, t = e >> 7;
+        // A: row m = 16 (tap % 8) + c of group tap / 8, 16-byte chunk of sites 8 kc .. 8 kc + 7.  A task takes
+        // the channel pair (2 cp, 2 cp + 1) of one tap and chunk: eight 4-byte reads of the window give both
+        // rows.  Groups of eight lanes take neighbouring taps (window rows one site apart).
+        for (int e = tid; e < kTaps * 8 * 8; e += kWgThreads) {
+          const int cp = e & 7, tk = e >> 3, t = tk % kTaps, kc = tk / kTaps;
           const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
           const int row = ((zl + 1 + dz) * kWY + (4 * yq + (kc >> 1) + 1 + dy)) * kWX + 8 * (kc & 1) + 1 + dx;
-          const uint16_t *src = sWin + row * kC + c;
-          uint4 w;
-          w.x = (uint32_t)src[0] | ((uint32_t)src[kC] << 16);
-          w.y = (uint32_t)src[2 * kC] | ((uint32_t)src[3 * kC] << 16);
-          w.z = (uint32_t)src[4 * kC] | ((uint32_t)src[5 * kC] << 16);
-          w.w = (uint32_t)src[6 * kC] | ((uint32_t)src[7 * kC] << 16);
-          const int m = 16 * (t & 7) + c;
-          *reinterpret_cast<uint4 *>(sA + (t >> 3) * kWgAGroup + kc * 2048 + (m >> 3) * 128 + (m & 7) * 16) = w;
+          const uint32_t *src = reinterpret_cast<const uint32_t *>(sWin + row * kC) + cp;
+          uint32_t v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) v[j] = src[j * (kC / 2)];
+          uint4 we, wo;
+          we.x = __byte_perm(v[0], v[1], 0x5410);
+          wo.x = __byte_perm(v[0], v[1], 0x7632);
+          we.y = __byte_perm(v[2], v[3], 0x5410);
+          wo.y = __byte_perm(v[2], v[3], 0x7632);
+          we.z = __byte_perm(v[4], v[5], 0x5410);
+          wo.z = __byte_perm(v[4], v[5], 0x7632);
+          we.w = __byte_perm(v[6], v[7], 0x5410);
+          wo.w = __byte_perm(v[6], v[7], 0x7632);
+          const int m = 16 * (t & 7) + 2 * cp;
+          unsigned char *dst = sA + (t >> 3) * kWgAGroup + kc * 2048 + (m >> 3) * 128 + (m & 7) * 16;
+          *reinterpret_cast<uint4 *>(dst) = we;
+          *reinterpret_cast<uint4 *>(dst + 16) = wo;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
