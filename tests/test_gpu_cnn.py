@@ -241,3 +241,64 @@ def test_batch_and_argument_errors():
     with pytest.raises(sx().SxError):
         Pr.adam_step(-1.0)
     Pr.close()
+
+
+def _crop(n, z, y, x, r=4):
+    """Slices of a crop of radius r around (z, y, x) inside a grid n = (nx, ny, nz): four 3x3x3 layers see r = 4
+    sites away, so the crop's own zero padding lies only where the lattice has none or beyond the receptive
+    field of the centre."""
+    z0, y0, x0 = max(0, z - r), max(0, y - r), max(0, x - r)
+    sl = (slice(z0, min(n[2], z + r + 1)), slice(y0, min(n[1], y + r + 1)), slice(x0, min(n[0], x + r + 1)))
+    return sl, (z - z0, y - y0, x - x0)
+
+
+def test_full_size_proposals_on_sampled_sites_and_batch_additivity():
+    # the proposer at the chain size of the batched-path workload: 64^3 sites, 30 interior images
+    n, nb = (64, 64, 64), 30
+    rng = np.random.default_rng(11)
+    shape = (3, n[2], n[1], n[0])
+    A = unit(rng.standard_normal((1,) + shape))[0]
+    B = unit(rng.standard_normal((1,) + shape))[0]
+    s = (np.arange(nb) + 1) / (nb + 1)
+    flat32, params = strong_params(11)
+    Pr = sx().Proposer(n, nb)
+    Pr.set_params(flat32)
+    Ad, Bd = dev(A), dev(B)
+    chain = torch.empty((nb + 2, 3, n[0] * n[1] * n[2]), dtype=torch.float64, device="cuda")
+    chain[0].copy_(Ad.view(3, -1))
+    chain[-1].copy_(Bd.view(3, -1))
+    Pr.interpolate(chain)
+    I = chain[1:-1].clone()
+    X = Pr.new_packed(nb)
+    Pr.pack(I, Ad, Bd, dev(s), X, shared_endpoints=True)
+    P = torch.empty_like(I)
+    Pr.forward(X, I, P)
+    Pn = P.cpu().numpy().reshape((nb,) + shape)
+    In = I.cpu().numpy().reshape((nb,) + shape)
+    # sampled sites: corners, faces, interior, every image
+    picks = [(b, int(rng.integers(0, n[2])), int(rng.integers(0, n[1])), int(rng.integers(0, n[0]))) for b in range(nb)]
+    picks += [(0, 0, 0, 0), (nb - 1, n[2] - 1, n[1] - 1, n[0] - 1), (5, 0, 31, 63), (7, 63, 0, 17)]
+    dev_ = []
+    for b, z, y, x in picks:
+        sl, c = _crop(n, z, y, x)
+        Ac, Bc = A[(slice(None),) + sl], B[(slice(None),) + sl]
+        Ic = cnn.interpolate(Ac, Bc, s[b])  # the oracle's own interpolation of the crop
+        assert np.abs(In[b][(slice(None),) + sl] - Ic).max() < 1e-12
+        ref, _, _ = cnn.forward(params, cnn.make_input(Ic[None], Ac[None], Bc[None], [s[b]]), Ic[None])
+        dev_.append(np.abs(Pn[b][:, z, y, x] - ref[0][:, c[0], c[1], c[2]]).max())
+    dev_ = np.array(dev_)
+    assert np.median(dev_) < 1e-6 and dev_.max() < 2e-3, (np.median(dev_), dev_.max())
+    assert np.abs((Pn * Pn).sum(1) - 1).max() < 1e-14
+    # the loss gradient of the whole batch is the mean of the gradients of its two halves: the per-CTA
+    # partials and their reduction over 7,680 blocks add up
+    T = torch.from_numpy(unit(rng.standard_normal((nb,) + shape))).cuda().view(nb, 3, -1)
+    g_all = torch.empty(Pr.nparams, dtype=torch.float32, device="cuda")
+    g_a, g_b = torch.empty_like(g_all), torch.empty_like(g_all)
+    L = Pr.loss_grad(X, I, T, g_all)
+    h = nb // 2
+    La = Pr.loss_grad(X[:h].contiguous(), I[:h].contiguous(), T[:h].contiguous(), g_a)
+    Lb = Pr.loss_grad(X[h:].contiguous(), I[h:].contiguous(), T[h:].contiguous(), g_b)
+    assert L == pytest.approx(0.5 * (La + Lb), rel=1e-12)
+    ga, gb_, gall = g_a.cpu().numpy(), g_b.cpu().numpy(), g_all.cpu().numpy()
+    assert np.linalg.norm(gall - 0.5 * (ga + gb_)) < 1e-5 * np.linalg.norm(gall)
+    Pr.close()
