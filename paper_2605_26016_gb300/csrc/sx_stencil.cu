@@ -88,6 +88,14 @@ struct KeepSC26 {
     return d2 == 0 ? 0 : (d2 == 1 ? mode : 1);
   }
 };
+// simple cubic, four distance shells (100), (110), (111), (200): the frustrated
+// exchange of the hopfion calculation
+struct KeepSC32 {
+  constexpr int operator()(int, int, int dx, int dy, int dz) const {
+    const int d2 = dx * dx + dy * dy + dz * dz;
+    return (d2 >= 1 && d2 <= 4) ? 1 : 0;
+  }
+};
 // bcc conventional cell as sublattices at (0,0,0) and (1/2,1/2,1/2): squared bond
 // lengths in units of (a/2)^2 are 3, 4, 8, 11 for the first four shells
 struct KeepBCC4 {
@@ -99,7 +107,7 @@ struct KeepBCC4 {
   }
 };
 
-enum FamilyId { FAM_SC6_ISO = 0, FAM_SC6_TEN, FAM_SC26_ISO, FAM_SC26_TEN, FAM_BCC4, FAM_COUNT };
+enum FamilyId { FAM_SC6_ISO = 0, FAM_SC6_TEN, FAM_SC26_ISO, FAM_SC26_TEN, FAM_SC32_ISO, FAM_BCC4, FAM_COUNT };
 
 template <int ID>
 struct Family;
@@ -124,10 +132,23 @@ struct Family<FAM_SC26_TEN> {
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{2});
 };
 template <>
+struct Family<FAM_SC32_ISO> {
+  static constexpr int NSUB = 1, R = 2, BY = 16, NTAP = 32, MINB = 1;
+  static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 2, KeepSC32{});
+};
+template <>
 struct Family<FAM_BCC4> {
   static constexpr int NSUB = 2, R = 2, BY = 16, NTAP = 100, MINB = 1;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(2, 2, KeepBCC4{});
 };
+
+constexpr int family_r(int fam) {
+  return fam == FAM_BCC4 ? Family<FAM_BCC4>::R : fam == FAM_SC32_ISO ? Family<FAM_SC32_ISO>::R : Family<FAM_SC6_ISO>::R;
+}
+constexpr int family_by(int fam) {
+  return fam == FAM_BCC4 ? Family<FAM_BCC4>::BY : fam == FAM_SC32_ISO ? Family<FAM_SC32_ISO>::BY
+                                                                      : Family<FAM_SC6_ISO>::BY;
+}
 
 constexpr int kMaxIso = 104;
 constexpr int kMaxTen = 8;
@@ -1134,12 +1155,14 @@ int stencil_plan(sx_ctx *c) {
     fam = FAM_SC26_ISO;
   else if (match_family<FAM_SC26_TEN>(c, a))
     fam = FAM_SC26_TEN;
+  else if (match_family<FAM_SC32_ISO>(c, a))
+    fam = FAM_SC32_ISO;
   else if (match_family<FAM_BCC4>(c, a))
     fam = FAM_BCC4;
   if (fam < 0) {
     delete sp;
     return set_error(SX_ERR_UNSUPPORTED,
-                     "no stencil family holds these taps (families: SC nearest neighbours, SC 3x3x3 cube, bcc four "
+                     "no stencil family holds these taps (families: SC nearest neighbours, SC 3x3x3 cube, SC four shells, bcc four "
                      "shells); use the gather backend");
   }
   sp->family = fam;
@@ -1164,6 +1187,7 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC6_TEN: e = set_smem<FAM_SC6_TEN>(); break;
     case FAM_SC26_ISO: e = set_smem<FAM_SC26_ISO>(); break;
     case FAM_SC26_TEN: e = set_smem<FAM_SC26_TEN>(); break;
+    case FAM_SC32_ISO: e = set_smem<FAM_SC32_ISO>(); break;
     default: e = set_smem<FAM_BCC4>(); break;
   }
   if (e != cudaSuccess) {
@@ -1175,6 +1199,7 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC6_TEN: sp->tz = choose_tz<FAM_SC6_TEN>(c); break;
     case FAM_SC26_ISO: sp->tz = choose_tz<FAM_SC26_ISO>(c); break;
     case FAM_SC26_TEN: sp->tz = choose_tz<FAM_SC26_TEN>(c); break;
+    case FAM_SC32_ISO: sp->tz = choose_tz<FAM_SC32_ISO>(c); break;
     default: sp->tz = choose_tz<FAM_BCC4>(c); break;
   }
   a.tz = sp->tz;
@@ -1185,6 +1210,7 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC6_TEN: sp->occ_field = field_occupancy<FAM_SC6_TEN>(); break;
     case FAM_SC26_ISO: sp->occ_field = field_occupancy<FAM_SC26_ISO>(); break;
     case FAM_SC26_TEN: sp->occ_field = field_occupancy<FAM_SC26_TEN>(); break;
+    case FAM_SC32_ISO: sp->occ_field = field_occupancy<FAM_SC32_ISO>(); break;
     default: sp->occ_field = field_occupancy<FAM_BCC4>(); break;
   }
   switch (fam) {
@@ -1192,12 +1218,12 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC6_TEN: sp->tz2 = field_tz<FAM_SC6_TEN>(*sp, a, 1); break;
     case FAM_SC26_ISO: sp->tz2 = field_tz<FAM_SC26_ISO>(*sp, a, 1); break;
     case FAM_SC26_TEN: sp->tz2 = field_tz<FAM_SC26_TEN>(*sp, a, 1); break;
+    case FAM_SC32_ISO: sp->tz2 = field_tz<FAM_SC32_ISO>(*sp, a, 1); break;
     default: sp->tz2 = field_tz<FAM_BCC4>(*sp, a, 1); break;
   }
   {
     // every family uses 32-wide tiles; R and BY per family
-    const int R = fam == FAM_BCC4 ? Family<FAM_BCC4>::R : Family<FAM_SC6_ISO>::R;
-    const int BY = fam == FAM_BCC4 ? Family<FAM_BCC4>::BY : Family<FAM_SC6_ISO>::BY;
+    const int R = family_r(fam), BY = family_by(fam);
     const long long ncol = (long long)((a.nx + 31) / 32) * ((a.ny + BY - 1) / BY);
     // Only when the columns are fewer than the resident CTA slots: then the z-chunked grid
     // leaves SMs idle (e.g. 128 CTAs for 152 SMs) and the balanced schedule fills them.
@@ -1227,6 +1253,7 @@ int stencil_plan(sx_ctx *c) {
         case FAM_SC6_TEN: e2 = persistent_occupancy<FAM_SC6_TEN>(&occ); break;
         case FAM_SC26_ISO: e2 = persistent_occupancy<FAM_SC26_ISO>(&occ); break;
         case FAM_SC26_TEN: e2 = persistent_occupancy<FAM_SC26_TEN>(&occ); break;
+        case FAM_SC32_ISO: e2 = persistent_occupancy<FAM_SC32_ISO>(&occ); break;
         default: e2 = persistent_occupancy<FAM_BCC4>(&occ); break;
       }
     }
@@ -1310,6 +1337,7 @@ cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int
     case FAM_SC6_TEN: return launch_field<FAM_SC6_TEN>(sp, sp.base, onsite, S, b, count, stride, st);
     case FAM_SC26_ISO: return launch_field<FAM_SC26_ISO>(sp, sp.base, onsite, S, b, count, stride, st);
     case FAM_SC26_TEN: return launch_field<FAM_SC26_TEN>(sp, sp.base, onsite, S, b, count, stride, st);
+    case FAM_SC32_ISO: return launch_field<FAM_SC32_ISO>(sp, sp.base, onsite, S, b, count, stride, st);
     default: return launch_field<FAM_BCC4>(sp, sp.base, onsite, S, b, count, stride, st);
   }
 }
@@ -1345,6 +1373,7 @@ cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S
     case FAM_SC6_TEN: return launch_persistent<FAM_SC6_TEN>(sp, a, S0, S1, nsteps, step0, st);
     case FAM_SC26_ISO: return launch_persistent<FAM_SC26_ISO>(sp, a, S0, S1, nsteps, step0, st);
     case FAM_SC26_TEN: return launch_persistent<FAM_SC26_TEN>(sp, a, S0, S1, nsteps, step0, st);
+    case FAM_SC32_ISO: return launch_persistent<FAM_SC32_ISO>(sp, a, S0, S1, nsteps, step0, st);
     default: return launch_persistent<FAM_BCC4>(sp, a, S0, S1, nsteps, step0, st);
   }
 }
@@ -1386,8 +1415,7 @@ int stencil_batch_create(StencilBatch **out, sx_ctx *const *ctxs, int nrep) {
   std::vector<long long> ncol(nrep);
   std::vector<int> nz(nrep);
   long long u0 = 0;
-  const int BY = b->family == FAM_BCC4 ? Family<FAM_BCC4>::BY : Family<FAM_SC6_ISO>::BY;
-  const int R = b->family == FAM_BCC4 ? Family<FAM_BCC4>::R : Family<FAM_SC6_ISO>::R;
+  const int BY = family_by(b->family), R = family_r(b->family);
   for (int r = 0; r < nrep; ++r) {
     const sx_ctx *c = ctxs[r];
     if (c->stencil->family != b->family || !same_couplings(c->stencil->base, ctxs[0]->stencil->base)) {
@@ -1458,6 +1486,7 @@ cudaError_t stencil_batch_step(StencilBatch *b, const double *const *S_in, doubl
     case FAM_SC6_TEN: return launch_batch<FAM_SC6_TEN>(*b, a, step, st);
     case FAM_SC26_ISO: return launch_batch<FAM_SC26_ISO>(*b, a, step, st);
     case FAM_SC26_TEN: return launch_batch<FAM_SC26_TEN>(*b, a, step, st);
+    case FAM_SC32_ISO: return launch_batch<FAM_SC32_ISO>(*b, a, step, st);
     default: return launch_batch<FAM_BCC4>(*b, a, step, st);
   }
 }
@@ -1481,6 +1510,7 @@ cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, c
       case FAM_SC6_TEN: return launch_heun2<FAM_SC6_TEN>(sp, a, src, dst, st);
       case FAM_SC26_ISO: return launch_heun2<FAM_SC26_ISO>(sp, a, src, dst, st);
       case FAM_SC26_TEN: return launch_heun2<FAM_SC26_TEN>(sp, a, src, dst, st);
+      case FAM_SC32_ISO: return launch_heun2<FAM_SC32_ISO>(sp, a, src, dst, st);
       default: return launch_heun2<FAM_BCC4>(sp, a, src, dst, st);
     }
   }
@@ -1489,6 +1519,7 @@ cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, c
     case FAM_SC6_TEN: return launch_heun<FAM_SC6_TEN>(sp, a, src, dst, st);
     case FAM_SC26_ISO: return launch_heun<FAM_SC26_ISO>(sp, a, src, dst, st);
     case FAM_SC26_TEN: return launch_heun<FAM_SC26_TEN>(sp, a, src, dst, st);
+    case FAM_SC32_ISO: return launch_heun<FAM_SC32_ISO>(sp, a, src, dst, st);
     default: return launch_heun<FAM_BCC4>(sp, a, src, dst, st);
   }
 }

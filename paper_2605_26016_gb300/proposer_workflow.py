@@ -12,7 +12,8 @@ B_z in [0, 0.04] T per path (stronger fields or larger changes shrink the barrie
 A is a hopfion (Hopf ansatz of seeded radius 8..10 and centre offset +-2 sites, relaxed by velocity
 projection); endpoint B is the ferromagnet along +z.
 
-A path is a chain of 16 images relaxed with velocity projection (dt = 0.05, k = 1 meV/rad, calls of 1000
+Fields come from the stencil backend's four-shell family (FP32 field, FP64 state).  A path is a chain of
+16 images relaxed with velocity projection (dt = 0.05, k = 1 meV/rad, calls of 1000
 iterations that carry the velocity) in two stages, as GNEB refinement is followed by climbing-image
 refinement in the paper: GNEB until the largest site force is below 1e-2 meV, then CI-GNEB from rest until
 it is below 1e-3 meV (J1 = 1 meV; the paper keeps the path force below about 1e-3 J1), at most max_iters
@@ -64,7 +65,7 @@ def main(argv):
         for k, J in enumerate(shells):
             s.add_shell_exchange(k + 1, J * (h["f"][k - 1] if k > 0 else 1.0))
         s.set_zeeman([0.0, 0.0, h["B"]])
-        s.plan("gather", "fp32")
+        s.plan("stencil", "fp32")
         return s
 
     rng = np.random.default_rng(2605)

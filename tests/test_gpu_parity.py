@@ -70,8 +70,10 @@ CASES = [
     ("bcc_4shell", (40, 30, 20), (1, 0, 1), None),            # several x/y tiles and z chunks
     ("sc_j123", (70, 40, 25), (0, 1, 1), None),
     ("sc_j123_dmi", (31, 29, 33), (1, 1, 0), None),
+    ("sc_4shell", (21, 19, 13), None, None),                 # four shells, R = 2, open boundaries
+    ("sc_4shell", (40, 35, 18), (1, 1, 0), None),
 ]
-STENCIL_OK = {0, 2, 3, 4, 5, 6, 7}
+STENCIL_OK = {0, 2, 3, 4, 5, 6, 7, 8, 9}
 PATHS = [("gather", "fp64"), ("gather", "fp32"), ("stencil", "fp32")]
 
 

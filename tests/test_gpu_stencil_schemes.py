@@ -24,6 +24,8 @@ CASES = [
     ("sc_j123_dmi", (17, 12, 10), (1, 1, 1)),
     ("sc_j123_dmi", (31, 29, 33), (1, 1, 0)),
     ("sc_j123", (70, 40, 25), (0, 1, 1)),
+    ("sc_4shell", (37, 21, 15), (0, 0, 0)),
+    ("sc_4shell", (40, 35, 18), (1, 1, 0)),
     ("sc_nn", (33, 5, 7), (1, 1, 1)),
     ("sc_nn", (64, 48, 40), (0, 0, 0)),
     # more tile columns than resident CTAs: the two-pass kernels run on the z-chunked grid

@@ -15,6 +15,9 @@ Workloads (all synthetic; the paper's benchmark lattices are synthetic too):
                  shells, periodic in x, y and open in z, mu = 1 mu_B.
 * ``sc_j123_dmi`` simple cubic, J1..J3 as above plus interfacial DMI D = 0.1 meV
                  on the first shell, mu = 2.2 mu_B, alpha = 0.1, T = 50 K, periodic.
+* ``sc_4shell``  simple cubic, the frustrated four-shell exchange of the hopfion
+                 calculation (J1 = 1 meV, J2/J1 = 0.188, J3/J1 = -0.274, J4/J1 = -0.161),
+                 open boundaries, mu = 1 mu_B, alpha = 0.1, T = 10 K.
 
 Spins are float64 arrays of shape (3, nsub, nz, ny, nx): three component planes,
 sublattice-major, x fastest.  Random spins are uniform on the sphere:
@@ -42,6 +45,8 @@ WORKLOADS = {
                     alpha=0.1, T=0.0, dt=0.1, pbc=(1, 1, 0), seed=3),
     "sc_j123_dmi": dict(pos=SC_POS, mu=[2.2], shells=[1.0, -0.164, -0.082], dmi=(1, 0, 0.1), B=[0.0, 0.0, 0.0],
                         K=None, alpha=0.1, T=50.0, dt=0.1, pbc=(1, 1, 1), seed=5),
+    "sc_4shell": dict(pos=SC_POS, mu=[1.0], shells=[1.0, 0.188, -0.274, -0.161], dmi=None, B=[0.0, 0.0, 0.0],
+                      K=None, alpha=0.1, T=10.0, dt=0.1, pbc=(0, 0, 0), seed=7),
 }
 
 
