@@ -46,6 +46,10 @@ WORKLOADS = {
                                 "mu = 2.2, K = 0.005 meV || z, T = 300 K, alpha = 0.05, dt = 0.1 fs, periodic"),
     "sc_nn_32": dict(name="sc_nn", n=(32, 32, 32),
                      desc="simple cubic 32^3 (32,768 spins), NN J = 1 meV, B = 1 T || z, alpha = 0.1, dt = 0.1 fs"),
+    "sc_4shell_256": dict(name="sc_4shell", n=(256, 256, 256),
+                          desc="simple cubic 256^3 (16.8M spins), four-shell frustrated exchange J1..J4 = 1, 0.188, "
+                               "-0.274, -0.161 meV (the hopfion Hamiltonian), open boundaries, T = 10 K, "
+                               "alpha = 0.1, dt = 0.1 fs"),
     "sc_j123_dmi_1024": dict(name="sc_j123_dmi", n=(1024, 1024, 1024),
                              desc="simple cubic 1024^3 (1.07e9 spins), J1..J3 = 1,-0.164,-0.082 meV + interfacial "
                                   "DMI 0.1 meV, mu = 2.2, T = 50 K, alpha = 0.1, dt = 0.1 fs, periodic"),
