@@ -452,7 +452,7 @@ int64_t sx_cnn_num_params(void);
  * activations (96 B per site of max_batch samples), activation gradients
  * (128 B per site), a packed-input buffer (32 B per site) and weight-gradient
  * partials (about 110 KB per 16 x 16 x 8 block of sites); synchronises the
- * device.  SX_ERR_ARG for n[k] outside 1..4096 or max_batch < 1. */
+ * device.  SX_ERR_ARG for n[k] outside 1..4096 or max_batch outside 1..65535. */
 int sx_cnn_create(sx_cnn **out, const int n[3], int max_batch);
 
 /* Release the proposer and its device memory (NULL is a no-op). */

@@ -845,7 +845,7 @@ int sx_cnn_create(sx_cnn **out, const int n[3], int max_batch) {
   *out = nullptr;
   for (int k = 0; k < 3; ++k)
     if (n[k] < 1 || n[k] > 4096) return set_error(SX_ERR_ARG, "every n[k] must be in 1..4096");
-  if (max_batch < 1) return set_error(SX_ERR_ARG, "max_batch must be >= 1");
+  if (max_batch < 1 || max_batch > 65535) return set_error(SX_ERR_ARG, "max_batch must be in 1..65535");
   const long long ncell = (long long)n[0] * n[1] * n[2];
   if (ncell * max_batch > (1LL << 34)) return set_error(SX_ERR_ARG, "max_batch x sites too large");
   sx_cnn *h = new (std::nothrow) sx_cnn();

@@ -148,7 +148,7 @@ def test_proposer_size_and_argument_checks():
     L = sx.lib()
     assert L.sx_cnn_num_params() == 19491
     h = ctypes.c_void_p()
-    for n, mb in (((0, 4, 4), 1), ((4, 4, 5000), 1), ((4, 4, 4), 0)):
+    for n, mb in (((0, 4, 4), 1), ((4, 4, 5000), 1), ((4, 4, 4), 0), ((4, 4, 4), 65536)):
         rc = L.sx_cnn_create(ctypes.byref(h), (ctypes.c_int * 3)(*n), mb)
         assert rc == sx.SX_ERR_ARG and not h.value
     assert L.sx_cnn_adam_step(None, None, None, None) == sx.SX_ERR_ARG
