@@ -4,8 +4,9 @@
         [backend] [precision] [method] [optimizer]
 
 Defaults: bcc_4shell, 64,64,64 (524,288 spins per image), 32 images, 50 iterations, stencil, fp32,
-ci_gneb, steepest (or vp: velocity projection, GNEB and CI-GNEB only).  The chain runs from the uniform state along +z to a seeded random state, interior
-images the site-wise normalised blend with 2% seeded jitter.  Prints one JSON line: image-site
+ci_gneb, steepest (or vp: velocity projection, GNEB and CI-GNEB only).  The chain runs from the
+uniform state along +z to a seeded random state, interior images the site-wise normalised blend
+with 2% seeded jitter.  Prints one JSON line: image-site
 iterations per second (interior images x sites x iterations / time), the time per iteration
 from CUDA events around one call of all timed iterations, and the HBM roofline of the
 iteration at 48 algorithmic bytes per image-site (read S, write S').
