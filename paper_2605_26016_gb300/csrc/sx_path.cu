@@ -410,11 +410,10 @@ __global__ void __launch_bounds__(kPT) k_gneb_vp_force(const double *__restrict_
                                                        const R *__restrict__ V, R *__restrict__ Fp, int first,
                                                        double *__restrict__ partial,
                                                        unsigned long long *__restrict__ fmax_slot) {
-  __shared__ double sm[kPT];
   const int n = blockIdx.y + 1;
   const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
   R fm = 0;
-  double pv = 0.0, ff = 0.0;
+  R vf[2] = {0, 0};  // v'.F and F.F of this thread's site
   if (i < N) {
     const double *S = X + 3 * N * (long long)n;
     R s[3], sp[3], smn[3], b[3];
@@ -432,24 +431,17 @@ __global__ void __launch_bounds__(kPT) k_gneb_vp_force(const double *__restrict_
     for (int k = 0; k < 3; ++k) F[k] = b[k] + A * tp[k] + C * tm[k];
     fm = r_sqrt(dot3(F, F));
     const long long base = 3 * N * (long long)n + i;
-    R pr = 0, fr = 0;
     for (int k = 0; k < 3; ++k) {
       const R v = first ? (R)0 : V[base + k * N] + (R)0.5 * dt * (Fp[base + k * N] + F[k]);
-      pr += v * F[k];
-      fr += F[k] * F[k];
+      vf[0] += v * F[k];
+      vf[1] += F[k] * F[k];
       Fp[base + k * N] = F[k];
     }
-    pv = (double)pr;
-    ff = (double)fr;
   }
   record_max<R>(fm, fmax_slot);
-  pv = block_sum(pv, sm);
-  ff = block_sum(ff, sm);
-  if (threadIdx.x == 0) {
-    const long long blk = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-    partial[2 * blk] = pv;
-    partial[2 * blk + 1] = ff;
-  }
+  // warp sums in R, the block's eight warp sums in FP64 (as the other path reductions)
+  const int sl[2] = {0, 1};
+  block_reduce_store<R, 2>(vf, sl, partial + 2 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
 // pass 2: c = max(sum v'.F, 0) / sum F.F over all blocks (fixed order), as cvp[0] (FP64) and cvp[1] (FP32 bits)
