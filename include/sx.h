@@ -184,7 +184,7 @@ typedef enum { SX_PATH_STRING = 0, SX_PATH_GNEB = 1, SX_PATH_CI_GNEB = 2 } sx_pa
  * projection (the minimisation section lists it among the optimisers; the update of sx_minimise) on the force
  * F of all interior images taken as one vector: v' = v + dt/2 (F_prev + F) (0 on the first iteration from
  * rest), v = max(v'.F, 0)/(F.F) F with the dot products over every interior site, S <- R(S, dt v + dt^2/2 F).
- * The velocity and previous force live in the path workspace (another 2 chains). */
+ * The velocity is kept as c and the previous force (another chain in the path workspace). */
 typedef enum { SX_PATH_STEEPEST = 0, SX_PATH_VP = 1 } sx_path_optimizer;
 
 typedef struct {

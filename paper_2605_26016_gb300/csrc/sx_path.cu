@@ -402,12 +402,13 @@ __global__ void __launch_bounds__(kPT) k_gneb_update(const double *__restrict__ 
 }
 
 // Velocity projection on the GNEB force, pass 1: the force F of interior image n = blockIdx.y + 1 at every
-// site (as k_gneb_update forms it), v' = v + dt/2 (F_prev + F) (0 when first), per-block FP64 sums of v'.F and
-// F.F into partial[2 * (blockIdx.y * gridDim.x + blockIdx.x) + {0, 1}], and F stored over F_prev.
+// site (as k_gneb_update forms it), v' = v + dt/2 (F_prev + F) (0 when first) with the velocity of the previous
+// update v = c_prev F_prev (c_prev still in cvp, F_prev in Fp), per-block sums of v'.F and F.F into
+// partial[2 * (blockIdx.y * gridDim.x + blockIdx.x) + {0, 1}], and F stored over F_prev.
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_gneb_vp_force(const double *__restrict__ X, const double *__restrict__ Y,
                                                        long long N, const R *__restrict__ coef, R dt,
-                                                       const R *__restrict__ V, R *__restrict__ Fp, int first,
+                                                       const double *__restrict__ cvp, R *__restrict__ Fp, int first,
                                                        double *__restrict__ partial,
                                                        unsigned long long *__restrict__ fmax_slot) {
   const int n = blockIdx.y + 1;
@@ -431,12 +432,19 @@ __global__ void __launch_bounds__(kPT) k_gneb_vp_force(const double *__restrict_
     for (int k = 0; k < 3; ++k) F[k] = b[k] + A * tp[k] + C * tm[k];
     fm = r_sqrt(dot3(F, F));
     const long long base = 3 * N * (long long)n + i;
+    // the velocity left by the previous update is c_prev F_prev, F_prev the force stored in Fp
+    const R cprev = sizeof(R) == 8 ? (R)cvp[0] : (R)reinterpret_cast<const float *>(cvp + 1)[0];
+    // all three loads before the stores: F_prev is overwritten through the same pointer, and interleaved
+    // loads and stores would have to wait on one another
+    R fp[3] = {0, 0, 0};
+    if (!first)
+      for (int k = 0; k < 3; ++k) fp[k] = Fp[base + k * N];
     for (int k = 0; k < 3; ++k) {
-      const R v = first ? (R)0 : V[base + k * N] + (R)0.5 * dt * (Fp[base + k * N] + F[k]);
+      const R v = first ? (R)0 : cprev * fp[k] + (R)0.5 * dt * (fp[k] + F[k]);
       vf[0] += v * F[k];
       vf[1] += F[k] * F[k];
-      Fp[base + k * N] = F[k];
     }
+    for (int k = 0; k < 3; ++k) Fp[base + k * N] = F[k];
   }
   record_max<R>(fm, fmax_slot);
   // warp sums in R, the block's eight warp sums in FP64 (as the other path reductions)
@@ -462,10 +470,11 @@ __global__ void __launch_bounds__(kPT) k_gneb_vp_coef(const double *__restrict__
   }
 }
 
-// pass 3: v = c F, S <- R_exp(S, dt c F + dt^2/2 F) from slot n of X into slot n of Y
+// pass 3: S <- R_exp(S, dt c F + dt^2/2 F) from slot n of X into slot n of Y (the velocity c F is kept as c and
+// F, which the next force pass reads)
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_gneb_vp_update(const double *__restrict__ X, double *__restrict__ Y,
-                                                        long long N, const R *__restrict__ Fp, R *__restrict__ V,
+                                                        long long N, const R *__restrict__ Fp,
                                                         const double *__restrict__ cvp, R dt) {
   const int n = blockIdx.y + 1;
   const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
@@ -481,7 +490,6 @@ __global__ void __launch_bounds__(kPT) k_gneb_vp_update(const double *__restrict
   const R h = (R)0.5 * dt * dt;
   for (int k = 0; k < 3; ++k) {
     const R f = Fp[base + k * N];
-    V[base + k * N] = c * f;
     u[k] = dt * c * f + h * f;
   }
   double out[3];
@@ -608,7 +616,7 @@ int reduce_grid(long long N) {
 
 struct PathLayout {
   double *W, *partial, *sums, *coef, *E, *L, *eend;
-  double *V, *Fp, *vp_partial, *cvp;  // velocity projection: velocity, previous force, block sums, coefficient
+  double *Fp, *vp_partial, *cvp;  // velocity projection: previous force, block sums, coefficient (v = c F_prev)
   float *coeff;
   unsigned long long *fmax;
   size_t bytes;
@@ -631,7 +639,6 @@ PathLayout layout(double *base, long long N, int nimg, int nb) {
   l.L = take((size_t)nimg);
   l.eend = take(2 * kNS);
   l.fmax = (unsigned long long *)take(1);
-  l.V = take(3 * (size_t)N * nimg);
   l.Fp = take(3 * (size_t)N * nimg);
   l.vp_partial = take(2 * (size_t)((N + kPT - 1) / kPT) * (nimg > 2 ? nimg - 2 : 1));
   l.cvp = take(2);
@@ -699,10 +706,10 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
       k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 0, l.sums);
       k_path_coef<<<1, kPT, 0, st>>>(l.sums, l.eend, M, p->method, p->k_spring, l.coef, l.coeff, l.E, l.L);
       if (vp) {
-        R *Vr = reinterpret_cast<R *>(l.V), *Fr = reinterpret_cast<R *>(l.Fp);
-        k_gneb_vp_force<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, Vr, Fr, vp_first, l.vp_partial, slot);
+        R *Fr = reinterpret_cast<R *>(l.Fp);
+        k_gneb_vp_force<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, l.cvp, Fr, vp_first, l.vp_partial, slot);
         k_gneb_vp_coef<<<1, kPT, 0, st>>>(l.vp_partial, (long long)nbu * (M - 2), l.cvp);
-        k_gneb_vp_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, Fr, Vr, l.cvp, dt);
+        k_gneb_vp_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, Fr, l.cvp, dt);
         vp_first = 0;
       } else {
         k_gneb_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, slot);
