@@ -77,11 +77,17 @@ __global__ void __launch_bounds__(kMinThreads) k_vp_force(const double *__restri
     const R b0 = cvt<R>(b[i]), b1 = cvt<R>(b[N + i]), b2 = cvt<R>(b[2 * N + i]);
     const R d = b0 * s0 + b1 * s1 + b2 * s2;
     const R f[3] = {b0 - d * s0, b1 - d * s1, b2 - d * s2};
+    // loads of all three components before the stores through the same pointers
+    R vo[3] = {0, 0, 0}, fo[3] = {0, 0, 0};
+    if (!first)
+      for (int k = 0; k < 3; ++k) {
+        vo[k] = v[k * N + i];
+        fo[k] = fprev[k * N + i];
+      }
     for (int k = 0; k < 3; ++k) {
-      const long long j = k * N + i;
-      const R vk = first ? (R)0 : v[j] + hdt * (fprev[j] + f[k]);
-      v[j] = vk;
-      fprev[j] = f[k];
+      const R vk = first ? (R)0 : vo[k] + hdt * (fo[k] + f[k]);
+      v[k * N + i] = vk;
+      fprev[k * N + i] = f[k];
       p += vk * f[k];
       F2 += f[k] * f[k];
     }
