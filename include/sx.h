@@ -59,7 +59,7 @@ typedef struct sx_ctx sx_ctx;
 typedef enum {
   SX_OK = 0,
   SX_ERR_ARG = -1,         /* bad argument, size or layout */
-  SX_ERR_UNSUPPORTED = -2, /* valid request this build or plan cannot serve */
+  SX_ERR_UNSUPPORTED = -2, /* valid request the library or the plan cannot serve */
   SX_ERR_OOM = -3,         /* device or host allocation failed */
   SX_ERR_CUDA = -4,        /* a CUDA runtime call failed */
   SX_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
@@ -253,7 +253,7 @@ int sx_get_taps(sx_ctx *ctx, int a, sx_tap *out, int cap);
 
 /* Choose backend and precision, build the device tables and workspaces on
  * the current CUDA device.  Must follow every Hamiltonian change and precede
- * every device call.  SX_ERR_UNSUPPORTED for a combination this build cannot
+ * every device call.  SX_ERR_UNSUPPORTED for a combination the library cannot
  * serve (e.g. STENCIL with taps beyond its halo, TF32/BF16 without
  * IGEMM_TC); SX_ERR_ARG if a periodic axis is shorter than 2*range+1. */
 int sx_plan(sx_ctx *ctx, int backend, int precision);

@@ -1476,7 +1476,7 @@ cudaError_t stencil_batch_step(StencilBatch *b, const double *const *S_in, doubl
     b->h_reps[r].Sout = S_out[r];
     b->h_reps[r].g.replica = h.replica + (uint32_t)r;
   }
-  // pageable source: staged by the driver before this call returns, ordered on the stream
+  // pageable source: staged by the CUDA driver before this call returns, ordered on the stream
   cudaError_t e =
       cudaMemcpyAsync(b->d_reps, b->h_reps.data(), b->nrep * sizeof(BatchRep), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
