@@ -336,6 +336,21 @@ def test_philox_words_uniform():
     assert abs(bits.mean() - 0.5) < 5 * 0.5 / math.sqrt(bits.size)
 
 
+def test_philox_known_answer_vectors():
+    # tests/golden/philox4x32_10_kat.txt: the generator's published known-answer vectors
+    # (Salmon et al., SC'11, Random123 kat_vectors); a wrong multiplier, Weyl constant,
+    # round count or word permutation changes every output word
+    rows = []
+    with open(__file__.replace("test_oracle_pins.py", "golden/philox4x32_10_kat.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append([int(v, 16) for v in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        assert oracle.philox4x32_10(r[0:4], r[4:6]) == r[6:10]
+
+
 @pytest.mark.parametrize("name,n,pbc", [("bcc_4shell", (5, 4, 6), (1, 0, 1)), ("sc_j123_dmi", (6, 5, 4), None)])
 def test_heun_at_sites_equals_full_step(name, n, pbc):
     # the sampled-site Heun step (used for checks at full lattice size) is the same arithmetic as a full step
@@ -345,6 +360,64 @@ def test_heun_at_sites_equals_full_step(name, n, pbc):
     sites = np.arange(m.nsite)
     part = m.heun_sites(S, sites, w["dt"], w["alpha"], T=w["T"] or 30.0, seed=5, replica=2, step=17)
     assert np.array_equal(part.T, full)
+
+
+@pytest.mark.parametrize("name,n,pbc,dipolar", [("bcc_4shell", (5, 4, 6), (1, 0, 1), False),
+                                                 ("sc_j123_dmi", (6, 5, 4), None, False),
+                                                 ("sc_j123_dmi", (4, 4, 4), (1, 1, 1), True),
+                                                 ("sc_nn", (4, 3, 5), (0, 0, 0), True)])
+def test_field_at_sites_equals_full_field(name, n, pbc, dipolar):
+    # the sampled-site field (used for checks at full lattice size, dipolar included) is the full field
+    # restricted to those sites, on periodic, mixed and open faces
+    m, w = oracle_model(name, n, pbc=pbc, dipolar=dipolar)
+    S = random_spins(m.nsub, n, 45)
+    full = m.field(S).reshape(3, -1)
+    sites = np.arange(m.nsite)[::-1].copy()
+    part = m.field_sites(S, sites)
+    assert np.abs(part.T - full[:, sites]).max() <= 1e-14 * np.abs(full).max()
+
+
+def _single_spins(theta, phi):
+    return np.stack([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)]).reshape(
+        3, 1, 1, 1, len(theta))
+
+
+def test_torque_max_single_spins_closed_form():
+    # uncoupled spins (open chain, no bonds) at polar angles theta: in B || z the torque is
+    # |S x b| = mu mu_B B sin(theta); with uniaxial K along z it is 2K |cos(theta)| sin(theta)
+    theta = np.array([0.3, 1.1, 2.9, 0.7, 1.9])
+    phi = np.array([0.0, 2.0, -1.0, 0.5, 4.0])
+    n = (len(theta), 1, 1)
+    S = _single_spins(theta, phi)
+    mu, B = 2.0, 1.5
+    m = oracle.Model(n, (0, 0, 0), cubic_cell(), SC_POS, [mu])
+    m.set_zeeman([0.0, 0.0, B])
+    m.build()
+    expect = mu * MU_B * B * np.sin(theta).max()       # the last site, sin(1.9)
+    assert abs(m.torque_max(S) - expect) < 1e-15
+    K = 0.25
+    m = oracle.Model(n, (0, 0, 0), cubic_cell(), SC_POS, [mu])
+    m.set_anisotropy(0, K, [0.0, 0.0, 1.0])
+    m.build()
+    expect = (2 * K * np.abs(np.cos(theta)) * np.sin(theta)).max()   # the fourth site, theta = 0.7
+    assert abs(m.torque_max(S) - expect) < 1e-15
+
+
+def test_torque_max_cycloid_in_field():
+    # interfacial-DMI cycloid S = (sin qx, 0, cos qx) with exchange and DMI has b_bil = lambda S (no
+    # bilinear torque); adding B || z leaves |S x b| = mu mu_B B |sin qx|, largest over the sites
+    n = (16, 4, 4)
+    J1, D, B = 1.3, 0.4, 0.8
+    m = oracle.Model(n, (1, 1, 1), cubic_cell(), SC_POS, [1.0])
+    m.add_shell_exchange(1, J1)
+    m.add_dmi(1, 0, D)
+    m.set_zeeman([0.0, 0.0, B])
+    m.build()
+    q = 2 * np.pi * 3 / 16
+    x = np.arange(16)[None, None, :] * np.ones((4, 4, 1))
+    S = np.stack([np.sin(q * x), np.zeros_like(x), np.cos(q * x)])[:, None]
+    expect = MU_B * B * np.abs(np.sin(q * np.arange(16))).max()
+    assert abs(m.torque_max(S) - expect) < 1e-13
 
 
 def test_stochastic_step_uses_same_noise_in_both_stages():
