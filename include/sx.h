@@ -306,8 +306,12 @@ int sx_device_status(sx_ctx *ctx, void *stream);
 
 /* Reduced effective field b = -dH/dS (meV, see "Spin Hamiltonian and
  * effective fields") of the spin field S, written to b (device, same layout
- * as S, FP64 whatever the plan precision).  S and b must not overlap. */
-int sx_field(sx_ctx *ctx, const double *S, double *b, void *stream);
+ * as S).  out_prec selects the element type of b: SX_PREC_FP64 (3*nsite
+ * doubles) or SX_PREC_FP32 (3*nsite floats, for field-only callers; the
+ * stencil backend writes it from its FP32 sums directly, the others round
+ * their field to FP32).  The values are those of the plan precision either
+ * way.  S and b must not overlap.  SX_ERR_ARG for another out_prec. */
+int sx_field(sx_ctx *ctx, const double *S, void *b, int out_prec, void *stream);
 
 /* nsteps normalised Heun steps of the LLG equation, steps step0 ..
  * step0+nsteps-1 (the step index is the noise counter).  S (device) holds
@@ -376,7 +380,9 @@ int sx_geodesic(sx_ctx *ctx, const double *A, const double *B, double *d_host, v
 int sx_energy(sx_ctx *ctx, const double *S, double *E_host, void *stream);
 
 /* max_i |S_i x b_i| in meV (the force measure of the minimisation and path
- * methods), written to *out_host.  Synchronises the stream. */
+ * methods), written to *out_host.  SX_ERR_NUMERIC when a spin or field value
+ * is not finite (the maximum propagates NaN instead of skipping it).
+ * Synchronises the stream. */
 int sx_torque_max(sx_ctx *ctx, const double *S, double *out_host, void *stream);
 
 /* max_i |S_i x b_i| of caller-provided spins S and fields b (device, layout
@@ -387,12 +393,17 @@ int sx_torque_max(sx_ctx *ctx, const double *S, double *out_host, void *stream);
  * not absorb cudaMalloc's implicit synchronisation).  It needs no context,
  * calls no allocating routine, and keeps its partial maxima in a fixed
  * 9.7 KB device array in the library image that every GPU loading the
- * library holds until exit.  The first call on a device looks up that
- * array's address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  All calls share the array, so calls
- * that overlap on the GPU race; calls serialised on one stream do not.
- * SX_ERR_ARG for null or misaligned pointers, overlap, or nsite outside
- * 1..2^40.  Synchronises the stream. */
+ * library holds until exit.  Each call looks up that array's address
+ * (cudaGetSymbolAddress) in the device and context current at the call.
+ * Loading: the CUDA driver loads the library's device code into a context on
+ * its first use there (lazy module loading) and reserves device memory for
+ * it then; a caller that reserves all remaining device memory for its own
+ * arena should make one call of this function (or any library call) on each
+ * device first.  All calls share the array, so calls that overlap on the GPU
+ * race; calls serialised on one stream do not.  SX_ERR_ARG for null or
+ * misaligned pointers, overlap, or nsite outside 1..2^40; SX_ERR_NUMERIC when
+ * a spin or field value is not finite (the maximum propagates NaN).
+ * Synchronises the stream. */
 int sx_torque_max_noalloc(const double *S, const double *b, int64_t nsite, double *out_host, void *stream);
 
 /* The thermal normals the Heun step draws: eta for sites site0 .. site0+n-1

@@ -114,7 +114,7 @@ def lib():
             "sx_set_dipolar": (ctypes.c_int, [vp, ctypes.c_int]),
             "sx_get_taps": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(sx_tap), ctypes.c_int]),
             "sx_plan": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
-            "sx_field": (ctypes.c_int, [vp, vp, vp, vp]),
+            "sx_field": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, vp]),
             "sx_llg_heun_step": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_uint64,
                                                 ctypes.c_int, vp]),
             "sx_llg_heun_step_out": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_uint64, vp]),
@@ -287,7 +287,10 @@ def llg_params(dt_fs, alpha, T=0.0, seed=0, replica=0):
 
 
 def sx_field(ctx, S, b, nsite, stream=None):
-    return _chk(lib().sx_field(ctx, _dev_ptr(S, 3 * nsite), _dev_ptr(b, 3 * nsite), _stream(stream)), "sx_field")
+    """The field of S into b: a float64 tensor (FP64 output) or a float32 tensor (FP32 output)."""
+    fp32 = str(b.dtype) == "torch.float32"
+    return _chk(lib().sx_field(ctx, _dev_ptr(S, 3 * nsite), _dev_ptr(b, 3 * nsite, "float32" if fp32 else "float64"),
+                               SX_PREC_FP32 if fp32 else SX_PREC_FP64, _stream(stream)), "sx_field")
 
 
 def sx_llg_heun_step(ctx, S, S_scratch, params, step0, nsteps, nsite, stream=None):
@@ -568,10 +571,11 @@ class SpinSystem:
     def info(self):
         return sx_plan_info(self.ctx)
 
-    def field(self, S, out=None, stream=None):
+    def field(self, S, out=None, stream=None, dtype=None):
+        """The field of S: into `out` (float64 or float32), else a new tensor of `dtype` (default float64)."""
         import torch
         if out is None:
-            out = torch.empty_like(S)
+            out = torch.empty_like(S, dtype=dtype or torch.float64)
         sx_field(self.ctx, S, out, self.nsite, stream)
         return out
 

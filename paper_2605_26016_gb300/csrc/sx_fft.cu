@@ -396,21 +396,20 @@ __global__ void k_fft_predict(const double *__restrict__ S, const R *__restrict_
   }
 }
 
-__device__ __forceinline__ void correct_state(const double S[3], const float d[3], double o[3]) {
-  renormalise64(S, d, o);
+__device__ __forceinline__ bool correct_state(const double S[3], const float d[3], double o[3]) {
+  return renormalise64(S, d, o);
 }
-__device__ __forceinline__ void correct_state(const double S[3], const double d[3], double o[3]) {
-  double x[3] = {S[0] + d[0], S[1] + d[1], S[2] + d[2]};
-  unit_t(x);
-  o[0] = x[0];
-  o[1] = x[1];
-  o[2] = x[2];
+__device__ __forceinline__ bool correct_state(const double S[3], const double d[3], double o[3]) {
+  o[0] = S[0] + d[0];
+  o[1] = S[1] + d[1];
+  o[2] = S[2] + d[2];
+  return unit64_checked(o);
 }
 
 template <typename R>
 __global__ void k_fft_correct(const double *__restrict__ S, const R *__restrict__ St, const R *__restrict__ F0,
                               const R *__restrict__ Bf, const R *__restrict__ Th, double *__restrict__ Snew, int nsub,
-                              long long N, OnSiteT<R> os, HeunT<R> h) {
+                              long long N, OnSiteT<R> os, HeunT<R> h, int *__restrict__ status) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   for (int a = 0; a < nsub; ++a) {
@@ -429,7 +428,7 @@ __global__ void k_fft_correct(const double *__restrict__ S, const R *__restrict_
     llg_rhs_t<R>(s, B, h.g, h.alpha, f);
     const R hdt = h.hdt;
     for (int c = 0; c < 3; ++c) d[c] = hdt * (F0[(long long)(c * nsub + a) * N + i] + f[c]);
-    correct_state(s64, d, o);
+    report_numeric(status, correct_state(s64, d, o));
     for (int c = 0; c < 3; ++c) Snew[(long long)(c * nsub + a) * N + i] = o[c];
   }
 }
@@ -624,7 +623,7 @@ cudaError_t heun_pipeline(const sx_ctx *c, const double *src, double *dst, const
   e = field_pipeline<R, R, R>(c, St, Bf, false, st);
   if (e != cudaSuccess) return e;
   k_fft_correct<R><<<blocks_for(fp.N, 256), 256, 0, st>>>(src, St, F0, Bf, Th, dst, fp.nsub, fp.N,
-                                                          onsite_cast<R>(c->onsite), heun_cast<R>(h));
+                                                          onsite_cast<R>(c->onsite), heun_cast<R>(h), c->d_status);
   return cudaGetLastError();
 }
 
@@ -787,7 +786,8 @@ cudaError_t bufheun_correct(const sx_ctx *c, const double *S, const float *St, c
                             const float *Th, double *Snew, const HeunConst &h, cudaStream_t st) {
   const long long N = c->geo.ncell;
   k_fft_correct<float><<<blocks_for(N, 256), 256, 0, st>>>(S, St, F0, Bf, Th, Snew, c->lat.nsub, N,
-                                                           onsite_cast<float>(c->onsite), heun_cast<float>(h));
+                                                           onsite_cast<float>(c->onsite), heun_cast<float>(h),
+                                                           c->d_status);
   return cudaGetLastError();
 }
 

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_correct(Geo g, const DevTap *__res
                                                       const int *__restrict__ off, OnSiteT<R> os, HeunT<R> h,
                                                       uint64_t step, const double *__restrict__ S,
                                                       const double *__restrict__ St, const double *__restrict__ F0,
-                                                      double *__restrict__ Snew) {
+                                                      double *__restrict__ Snew, int *__restrict__ status) {
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (i >= g.nsite) return;
   int x, y, z, a;
@@ -195,12 +195,18 @@ __global__ void __launch_bounds__(kThreads) k_correct(Geo g, const DevTap *__res
   R f[3];
   llg_rhs<R>(s, B, h.g, h.alpha, f);
   const R hdt = h.hdt;
-  double xn[3];
+  R d[3];
+  double s64[3], xn[3];
   for (int k = 0; k < 3; ++k) {
-    const R d = hdt * (cvt<R>(F0[k * g.nsite + i]) + f[k]);
-    xn[k] = S[k * g.nsite + i] + cvt<double>(d);
+    d[k] = hdt * (cvt<R>(F0[k * g.nsite + i]) + f[k]);
+    s64[k] = S[k * g.nsite + i];
   }
-  unit(xn);
+  if constexpr (sizeof(R) == 4) {
+    report_numeric(status, renormalise64(s64, d, xn));
+  } else {
+    for (int k = 0; k < 3; ++k) xn[k] = s64[k] + d[k];
+    report_numeric(status, unit64_checked(xn));
+  }
   for (int k = 0; k < 3; ++k) Snew[k * g.nsite + i] = xn[k];
 }
 
@@ -211,18 +217,6 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
   __syncthreads();
   for (int s = kThreads / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = sm[0];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ double block_max(double v, double *sm) {
-  sm[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = kThreads / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
     __syncthreads();
   }
   const double r = sm[0];
@@ -279,15 +273,7 @@ __global__ void __launch_bounds__(kThreads) k_torque_partial(Geo g, const double
                                                              const double *__restrict__ b,
                                                              double *__restrict__ partial) {
   __shared__ double sm[kThreads];
-  double best = 0.0;
-  const int64_t N = g.nsite;
-  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < N; i += (int64_t)gridDim.x * kThreads) {
-    const double s0 = S[i], s1 = S[N + i], s2 = S[2 * N + i];
-    const double b0 = b[i], b1 = b[N + i], b2 = b[2 * N + i];
-    const double t0 = s1 * b2 - s2 * b1, t1 = s2 * b0 - s0 * b2, t2 = s0 * b1 - s1 * b0;
-    best = fmax(best, sqrt(t0 * t0 + t1 * t1 + t2 * t2));
-  }
-  best = block_max(best, sm);
+  const double best = block_torque_max<kThreads>(S, b, g.nsite, sm);
   if (threadIdx.x == 0) partial[blockIdx.x] = best;
 }
 
@@ -295,8 +281,8 @@ __global__ void __launch_bounds__(kThreads) k_torque_final(const double *__restr
                                                            double *__restrict__ out) {
   __shared__ double sm[kThreads];
   double best = 0.0;
-  for (int64_t j = threadIdx.x; j < nb; j += kThreads) best = fmax(best, partial[j]);
-  best = block_max(best, sm);
+  for (int64_t j = threadIdx.x; j < nb; j += kThreads) best = max_nan(best, partial[j]);
+  best = block_max_nan<kThreads>(best, sm);
   if (threadIdx.x == 0) out[0] = best;
 }
 
@@ -312,6 +298,13 @@ __global__ void k_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64
 }
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// out[i] = (float)in[i], round to nearest (IEEE conversion)
+__global__ void __launch_bounds__(kThreads) k_to_f32(const double *__restrict__ in, float *__restrict__ out,
+                                                     int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    out[i] = __double2float_rn(in[i]);
+}
 
 }  // namespace
 
@@ -342,14 +335,14 @@ cudaError_t gather_heun_step(const sx_ctx *c, const double *src, double *dst, co
                                                               St, F0);
     k_correct<double><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, onsite_cast<double>(c->onsite),
                                                               heun_cast<double>(h), step, src,
-                                                              St, F0, dst);
+                                                              St, F0, dst, c->d_status);
   } else {
     k_predict<float><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, onsite_cast<float>(c->onsite),
                                                               heun_cast<float>(h), step, src,
                                                              St, F0);
     k_correct<float><<<grid_for(g.nsite), kThreads, 0, st>>>(g, c->d_taps, c->d_tap_off, onsite_cast<float>(c->onsite),
                                                               heun_cast<float>(h), step, src,
-                                                             St, F0, dst);
+                                                             St, F0, dst, c->d_status);
   }
   return cudaGetLastError();
 }
@@ -365,6 +358,13 @@ cudaError_t reduce_torque(const sx_ctx *c, const double *S, const double *b, dou
                           double *out_dev, cudaStream_t st) {
   k_torque_partial<<<(unsigned)nblock, kThreads, 0, st>>>(c->geo, S, b, partial);
   k_torque_final<<<1, kThreads, 0, st>>>(partial, nblock, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t to_f32(const double *in, float *out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t nb = std::min<int64_t>(grid_for(n), 152 * 16);
+  k_to_f32<<<(unsigned)nb, kThreads, 0, st>>>(in, out, n);
   return cudaGetLastError();
 }
 

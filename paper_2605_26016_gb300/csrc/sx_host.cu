@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 
 #include "sx_internal.h"
@@ -25,6 +26,20 @@ int set_error(int code, const std::string &msg) {
 int cuda_error(cudaError_t e, const char *what) {
   return set_error(e == cudaErrorMemoryAllocation ? SX_ERR_OOM : SX_ERR_CUDA,
                    std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int take_status(sx_ctx *c, cudaStream_t st) {
+  if (!c->d_status) return SX_OK;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "status read");
+  if (!(h & kStatusNumeric)) return SX_OK;
+  e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "status reset");
+  return set_error(SX_ERR_NUMERIC,
+                   "a spin update met a non-finite or zero-length spin since the last check: the state is invalid");
 }
 
 namespace {
@@ -196,6 +211,8 @@ void free_plan(sx_ctx *c) {
   cudaFree(c->d_work);
   cudaFree(c->d_field);
   cudaFree(c->d_partial);
+  cudaFree(c->d_status);
+  c->d_status = nullptr;
   cudaFree(c->d_host_S[0]);
   cudaFree(c->d_host_S[1]);
   c->d_taps = nullptr;
@@ -496,6 +513,8 @@ int sx_plan(sx_ctx *c, int backend, int prec) {
   if (backend == SX_BACKEND_GATHER) SX_TRY(cudaMalloc(&c->d_work, 2 * N3 * sizeof(double)), "cudaMalloc Heun workspace");
   SX_TRY(cudaMalloc(&c->d_field, N3 * sizeof(double)), "cudaMalloc field workspace");
   SX_TRY(cudaMalloc(&c->d_partial, (3 * c->nblock_red + 8) * sizeof(double)), "cudaMalloc reduction partials");
+  SX_TRY(cudaMalloc(&c->d_status, sizeof(int)), "cudaMalloc status word");
+  SX_TRY(cudaMemset(c->d_status, 0, sizeof(int)), "clear status word");
   c->launches_per_step = 2;
   if (backend != SX_BACKEND_GATHER) {
     const int rc = backend == SX_BACKEND_STENCIL ? stencil_plan(c) : backend == SX_BACKEND_FFT ? fft_plan(c) : tc_plan(c);
@@ -662,15 +681,29 @@ int sx_device_status(sx_ctx *c, void *stream) {
   if (c->backend == SX_BACKEND_STENCIL) timed_out |= stencil_check_error(c);
   if (c->backend == SX_BACKEND_IGEMM_TC) timed_out |= tc_check_error(c);
   if (timed_out) return set_error(SX_ERR_TIMEOUT, "a bounded device wait gave up; results of that call are invalid");
-  return SX_OK;
+  return take_status(c, (cudaStream_t)stream);
 }
 
-int sx_field(sx_ctx *c, const double *S, double *b, void *stream) {
+int sx_field(sx_ctx *c, const double *S, void *b, int out_prec, void *stream) {
   int rc = check_ready(c);
   if (rc) return rc;
-  if ((rc = check_spin_ptr(S, "S")) || (rc = check_spin_ptr(b, "b"))) return rc;
-  if (overlaps(S, b, 3 * (size_t)c->geo.nsite * sizeof(double))) return set_error(SX_ERR_ARG, "S and b overlap");
-  cudaError_t e = backend_field(c, S, b, true, (cudaStream_t)stream);
+  if (out_prec != SX_PREC_FP64 && out_prec != SX_PREC_FP32)
+    return set_error(SX_ERR_ARG, "out_prec must be SX_PREC_FP64 or SX_PREC_FP32");
+  if ((rc = check_spin_ptr(S, "S"))) return rc;
+  if (!b) return set_error(SX_ERR_ARG, "b is null");
+  const size_t n3 = 3 * (size_t)c->geo.nsite;
+  if (((uintptr_t)b) & (out_prec == SX_PREC_FP64 ? 7u : 3u)) return set_error(SX_ERR_ARG, "b is misaligned");
+  if (overlaps(S, b, n3 * sizeof(double))) return set_error(SX_ERR_ARG, "S and b overlap");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (out_prec == SX_PREC_FP64) {
+    e = backend_field(c, S, static_cast<double *>(b), true, st);
+  } else if (c->backend == SX_BACKEND_STENCIL) {
+    e = stencil_field_f32(c, S, static_cast<float *>(b), true, st);
+  } else {
+    e = backend_field(c, S, c->d_field, true, st);
+    if (e == cudaSuccess) e = to_f32(c->d_field, static_cast<float *>(b), (int64_t)n3, st);
+  }
   return e == cudaSuccess ? SX_OK : cuda_error(e, "field launch");
 }
 
@@ -740,7 +773,7 @@ int sx_llg_heun_host(sx_ctx *c, double *S_host, const sx_llg_params *p, uint64_t
   if ((e = cudaMemcpyAsync(S_host, c->d_host_S[nsteps & 1], bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_error(e, "device to host copy");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(e, "stream synchronize");
-  return SX_OK;
+  return take_status(c, st);
 }
 
 int sx_minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p, int *iters_out,
@@ -774,9 +807,17 @@ int sx_path_step(sx_ctx *c, double *images, int nimg, const sx_path_params *p, i
     return set_error(SX_ERR_ARG, "unknown path optimizer");
   if (p->optimizer == SX_PATH_VP && p->method == SX_PATH_STRING)
     return set_error(SX_ERR_UNSUPPORTED, "velocity projection applies to GNEB and CI-GNEB, not the string method");
+  double fmax = -1.0;
+  std::vector<double> E(nimg);
   cudaError_t e =
-      path_run(c, images, nimg, p, iters_out, E_host, fmax_host, (cudaStream_t)stream, backend_field_batch);
-  return e == cudaSuccess ? SX_OK : cuda_error(e, "path step");
+      path_run(c, images, nimg, p, iters_out, E.data(), &fmax, (cudaStream_t)stream, backend_field_batch);
+  if (e != cudaSuccess) return cuda_error(e, "path step");
+  if (E_host) std::copy(E.begin(), E.end(), E_host);
+  if (fmax_host) *fmax_host = fmax;
+  bool finite = fmax == -1.0 || std::isfinite(fmax);
+  for (double v : E) finite = finite && std::isfinite(v);
+  if (!finite) return set_error(SX_ERR_NUMERIC, "a path image holds a non-finite spin (non-finite force or energy)");
+  return take_status(c, (cudaStream_t)stream);
 }
 
 int sx_geodesic(sx_ctx *c, const double *A, const double *B, double *d_host, void *stream) {
@@ -799,7 +840,9 @@ int sx_energy(sx_ctx *c, const double *S, double *E_host, void *stream) {
   if (e == cudaSuccess) e = reduce_energy(c, S, c->d_field, c->d_partial, c->nblock_red, out, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(E_host, out, 5 * sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return e == cudaSuccess ? SX_OK : cuda_error(e, "energy");
+  if (e != cudaSuccess) return cuda_error(e, "energy");
+  if (!std::isfinite(E_host[0])) return set_error(SX_ERR_NUMERIC, "the energy is not finite: a spin is not finite");
+  return SX_OK;
 }
 
 int sx_torque_max(sx_ctx *c, const double *S, double *out_host, void *stream) {
@@ -813,7 +856,10 @@ int sx_torque_max(sx_ctx *c, const double *S, double *out_host, void *stream) {
   if (e == cudaSuccess) e = reduce_torque(c, S, c->d_field, c->d_partial, c->nblock_red, out, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, out, sizeof(double), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return e == cudaSuccess ? SX_OK : cuda_error(e, "torque");
+  if (e != cudaSuccess) return cuda_error(e, "torque");
+  if (!std::isfinite(*out_host))
+    return set_error(SX_ERR_NUMERIC, "the torque maximum is not finite: a spin or field value is not finite");
+  return SX_OK;
 }
 
 int sx_thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64_t n, uint64_t step, float *eta_dev,

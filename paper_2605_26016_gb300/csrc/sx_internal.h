@@ -17,6 +17,7 @@ constexpr double kGamma = 1.76085963023e-4;  // rad / (fs T)
 constexpr double kKB = 8.617333262e-2;       // meV / K
 constexpr int kSearch = 4;                   // bond search box: cell offsets -4..4
 constexpr int kMaxTaps = 512;                // taps per target sublattice
+constexpr int kStatusNumeric = 1;            // status-word bit: a state update met a non-finite or zero-length spin
 
 // One directed tap of K_ab(delta) as stored on the device for the gather path.
 struct DevTap {
@@ -149,6 +150,7 @@ struct sx_ctx {
   double *d_work;        // 2 x 3 nsite doubles: Heun predictor state and f0 (gather path)
   double *d_field;       // 3 nsite doubles: field scratch for energy / torque
   double *d_partial;     // reduction partials
+  int *d_status;         // status word set by kernels (kStatusNumeric), read and cleared by the host
   double *d_host_S[2];   // device buffers for the host-memory entry point
   int64_t nblock_red;
   sx::StencilPlan *stencil;
@@ -166,6 +168,9 @@ namespace sx {
 
 int set_error(int code, const std::string &msg);
 int cuda_error(cudaError_t e, const char *what);
+// Reads the context's status word after the stream's queued work (synchronises the stream) and clears it:
+// SX_ERR_NUMERIC when a state update met a non-finite or zero-length spin since the last check.
+int take_status(sx_ctx *c, cudaStream_t st);
 
 // gather path (sx_gather.cu)
 cudaError_t gather_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
@@ -178,6 +183,8 @@ cudaError_t reduce_torque(const sx_ctx *c, const double *S, const double *b, dou
 int64_t reduce_blocks(int64_t nsite);
 cudaError_t thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64_t n, uint64_t step, float *eta,
                             cudaStream_t st);
+// out[i] = in[i] rounded to FP32, i < n
+cudaError_t to_f32(const double *in, float *out, int64_t n, cudaStream_t st);
 
 // stencil path (sx_stencil.cu)
 int stencil_plan(sx_ctx *c);
@@ -196,6 +203,8 @@ void stencil_batch_free(StencilBatch *b);
 cudaError_t stencil_batch_step(StencilBatch *b, const double *const *S_in, double *const *S_out, const HeunConst &h,
                                uint64_t step, cudaStream_t st);
 cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
+// the field written as FP32 by the field pass itself
+cudaError_t stencil_field_f32(const sx_ctx *c, const double *S, float *b, bool onsite, cudaStream_t st);
 // fields of `count` spin fields stride doubles apart (S, S + stride, ...) into b, b + stride, ... in one launch
 cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int count, long long stride,
                                 bool onsite, cudaStream_t st);

@@ -17,6 +17,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <cmath>
+
 #include "sx_device.cuh"
 #include "sx_internal.h"
 
@@ -112,20 +114,21 @@ __global__ void __launch_bounds__(kMinThreads) k_vp_coef(const double *__restric
   }
 }
 
-// S <- R_exp(S, u), u tangent: FP64 plans in FP64 (libm cos, sin)
-__device__ __forceinline__ void vp_retract(double s[3], const double u[3]) {
+// S <- R_exp(S, u), u tangent: FP64 plans in FP64 (libm cos, sin).  Returns true
+// when the result is not finite or has zero length (a numeric error).
+__device__ __forceinline__ bool vp_retract(double s[3], const double u[3]) {
   const double a = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   if (a > 0.0) {
     const double cs = cos(a), sn = sin(a) / a;
     for (int k = 0; k < 3; ++k) s[k] = cs * s[k] + sn * u[k];
-    const double r = rsqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
-    for (int k = 0; k < 3; ++k) s[k] *= r;
+    return unit64_checked(s);
   }
+  return !(a == 0.0);  // NaN step
 }
 
 // FP32 arithmetic, FP64 state: d = (cos a - 1) s + (sin a / a) u with cos a - 1 = -2 sin^2(a/2),
 // S' = N[S + d] in FP64
-__device__ __forceinline__ void vp_retract(double s[3], const float u[3]) {
+__device__ __forceinline__ bool vp_retract(double s[3], const float u[3]) {
   const float a = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   if (a > 0.0f) {
     const float sf[3] = {f64_to_f32(s[0]), f64_to_f32(s[1]), f64_to_f32(s[2])};
@@ -133,14 +136,15 @@ __device__ __forceinline__ void vp_retract(double s[3], const float u[3]) {
     const float c1 = -2.0f * h * h, sc = sinf(a) / a;
     const float d[3] = {c1 * sf[0] + sc * u[0], c1 * sf[1] + sc * u[1], c1 * sf[2] + sc * u[2]};
     const double s0[3] = {s[0], s[1], s[2]};
-    renormalise64(s0, d, s);
+    return renormalise64(s0, d, s);
   }
+  return !(a == 0.0f);  // NaN step
 }
 
 template <typename R>
 __global__ void __launch_bounds__(kMinThreads) k_vp_update(double *__restrict__ S, R *__restrict__ v,
                                                            const R *__restrict__ f, const double *__restrict__ coef,
-                                                           R dt, long long N) {
+                                                           R dt, long long N, int *__restrict__ status) {
   const long long i = (long long)blockIdx.x * kMinThreads + threadIdx.x;
   if (i >= N) return;
   R c;
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(kMinThreads) k_vp_update(double *__restrict__ 
     v[k * N + i] = c * fk;
     u[k] = dt * c * fk + hdt2 * fk;
   }
-  vp_retract(s, u);
+  report_numeric(status, vp_retract(s, u));
   for (int k = 0; k < 3; ++k) S[k * N + i] = s[k];
 }
 
@@ -167,7 +171,8 @@ cudaError_t vp_iteration(const sx_ctx *c, double *S, double *ws, int first, doub
   double *part = ws + 6 * N, *coef = part + 2 * nb;
   k_vp_force<R><<<nb, kMinThreads, 0, st>>>(S, c->d_field, v, fp, first, (R)(0.5 * dt), N, part);
   k_vp_coef<<<1, kMinThreads, 0, st>>>(part, nb, coef);
-  k_vp_update<R><<<(unsigned)((N + kMinThreads - 1) / kMinThreads), kMinThreads, 0, st>>>(S, v, fp, coef, (R)dt, N);
+  k_vp_update<R><<<(unsigned)((N + kMinThreads - 1) / kMinThreads), kMinThreads, 0, st>>>(S, v, fp, coef, (R)dt, N,
+                                                                                              c->d_status);
   return cudaGetLastError();
 }
 
@@ -212,7 +217,7 @@ int minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p, in
       if (e == cudaSuccess) e = reduce_torque(c, cur, c->d_field, c->d_partial, c->nblock_red, out_dev, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(&torque, out_dev, sizeof(double), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess || torque < p->tol) break;
+      if (e != cudaSuccess || torque < p->tol || !(torque == torque)) break;
     }
   }
   if (e == cudaSuccess && cur != S)
@@ -221,6 +226,10 @@ int minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p, in
   if (e != cudaSuccess) return cuda_error(e, "minimise");
   if (iters_out) *iters_out = it;
   if (torque_out) *torque_out = torque;
+  const int rc = take_status(c, st);
+  if (rc != SX_OK) return rc;
+  if (!std::isfinite(torque) && torque != -1.0)
+    return set_error(SX_ERR_NUMERIC, "the torque maximum is not finite: the spin state holds a non-finite value");
   return SX_OK;
 }
 

@@ -12,45 +12,34 @@
 // The array, g_torque_partials, is kStaticBlocks + 1 doubles (9.7 KB).  Every
 // GPU on which the library is loaded holds it until the process exits.  Host
 // code may not pass the array's name to a kernel: on the host that name is only
-// a stand-in, not a device address.  Its device address is looked up once per
-// device with cudaGetSymbolAddress, on the first call made with that device
-// current, and cached.
-#include <mutex>
+// a stand-in, not a device address.  Every call looks the device address up
+// with cudaGetSymbolAddress for the device and context current at the call, so
+// an address never outlives the context it belongs to (after cudaDeviceReset,
+// or with another context current on the same device, the lookup returns the
+// array of the module loaded in the context now current).
+//
+// The reduction body (per-site torque, NaN-propagating block maximum) is the
+// one sx_torque_max uses (sx_device.cuh); only the scratch location differs.
+#include <cmath>
 
+#include "sx_device.cuh"
 #include "sx_internal.h"
 
 namespace {
 
 constexpr int kStaticThreads = 256;
 constexpr int kStaticBlocks = 1216;               // grid cap: 152 SMs x 8 resident blocks
-constexpr int kMaxDevices = 64;
 constexpr int64_t kMaxSites = (int64_t)1 << 40;  // the library's lattice limit
 
 // slots 0 .. kStaticBlocks-1: per-block partial maxima; slot kStaticBlocks: the result
 static __device__ __align__(256) double g_torque_partials[kStaticBlocks + 1];
 
-std::mutex g_mu;
-double *g_dev_addr[kMaxDevices];
-
 __global__ void __launch_bounds__(kStaticThreads) k_torque_partial_static(const double *__restrict__ S,
                                                                           const double *__restrict__ b, int64_t n,
                                                                           double *__restrict__ partial) {
   __shared__ double sm[kStaticThreads];
-  double best = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * kStaticThreads + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * kStaticThreads) {
-    const double s0 = S[i], s1 = S[n + i], s2 = S[2 * n + i];
-    const double b0 = b[i], b1 = b[n + i], b2 = b[2 * n + i];
-    const double t0 = s1 * b2 - s2 * b1, t1 = s2 * b0 - s0 * b2, t2 = s0 * b1 - s1 * b0;
-    best = fmax(best, sqrt(t0 * t0 + t1 * t1 + t2 * t2));
-  }
-  sm[threadIdx.x] = best;
-  __syncthreads();
-  for (int s = kStaticThreads / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+  const double best = sx::block_torque_max<kStaticThreads>(S, b, n, sm);
+  if (threadIdx.x == 0) partial[blockIdx.x] = best;
 }
 
 // reads exactly the nb slots the partial kernel of the same call wrote, so no
@@ -58,30 +47,17 @@ __global__ void __launch_bounds__(kStaticThreads) k_torque_partial_static(const 
 __global__ void __launch_bounds__(kStaticThreads) k_torque_final_static(double *__restrict__ partial, int nb) {
   __shared__ double sm[kStaticThreads];
   double best = 0.0;
-  for (int j = threadIdx.x; j < nb; j += kStaticThreads) best = fmax(best, partial[j]);
-  sm[threadIdx.x] = best;
-  __syncthreads();
-  for (int s = kStaticThreads / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + s]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) partial[kStaticBlocks] = sm[0];
+  for (int j = threadIdx.x; j < nb; j += kStaticThreads) best = sx::max_nan(best, partial[j]);
+  best = sx::block_max_nan<kStaticThreads>(best, sm);
+  if (threadIdx.x == 0) partial[kStaticBlocks] = best;
 }
 
-// device address of the static array for the current device (set up on first use)
+// device address of the static array in the context current now
 int scratch_address(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return sx::cuda_error(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return sx::set_error(SX_ERR_UNSUPPORTED, "device ordinal beyond 63");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_dev_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_torque_partials);
-    if (e != cudaSuccess) return sx::cuda_error(e, "cudaGetSymbolAddress");
-    g_dev_addr[dev] = static_cast<double *>(p);
-  }
-  *out = g_dev_addr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_torque_partials);
+  if (e != cudaSuccess) return sx::cuda_error(e, "cudaGetSymbolAddress");
+  *out = static_cast<double *>(p);
   return SX_OK;
 }
 
@@ -108,5 +84,7 @@ extern "C" int sx_torque_max_noalloc(const double *S, const double *b, int64_t n
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, scratch + kStaticBlocks, sizeof(double),
                                             cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return e == cudaSuccess ? SX_OK : sx::cuda_error(e, "sx_torque_max_noalloc");
+  if (e != cudaSuccess) return sx::cuda_error(e, "sx_torque_max_noalloc");
+  if (!std::isfinite(*out_host)) return sx::set_error(SX_ERR_NUMERIC, "non-finite spin or field value");
+  return SX_OK;
 }

@@ -42,8 +42,43 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
   }
 }
 
+// Philox4x32-10 with the round keys precomputed (k0[r] = seed_lo + r 0x9E3779B9,
+// k1[r] = seed_hi + r 0xBB67AE85): the same ten rounds as philox4x32_10, with
+// the key schedule taken from kernel parameters instead of recomputed per site.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+
+inline PhiloxKeys philox_keys(uint64_t seed) {
+  PhiloxKeys k;
+  uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    k.k0[r] = a;
+    k.k1[r] = b;
+    a += 0x9E3779B9u;
+    b += 0xBB67AE85u;
+  }
+  return k;
+}
+
+__device__ __forceinline__ void philox4x32_10_rk(uint32_t c[4], const PhiloxKeys &K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t a = c[0], b = c[2];
+    const uint32_t h0 = __umulhi(0xD2511F53u, a), l0 = 0xD2511F53u * a;
+    const uint32_t h1 = __umulhi(0xCD9E8D57u, b), l1 = 0xCD9E8D57u * b;
+    c[0] = h1 ^ c[1] ^ K.k0[r];
+    c[1] = l1;
+    c[2] = h0 ^ c[3] ^ K.k1[r];
+    c[3] = l0;
+  }
+}
+
+// u = (2 (x >> 9) + 1) 2^-24: the float 1 + (x >> 9) 2^-23 built from its bits,
+// minus 1 - 2^-24.  Both operands and the difference are exact FP32 values, so
+// the subtraction is exact and u equals the value of the formula.
 __device__ __forceinline__ float unit_open(uint32_t x) {
-  return __fmul_rn(__uint2float_rn(((x >> 9) << 1) | 1u), 5.9604644775390625e-8f);
+  return __fsub_rn(__uint_as_float(0x3F800000u | (x >> 9)), 0.99999994039535522f);
 }
 
 __device__ __forceinline__ float ln_open(float u) {
@@ -87,19 +122,16 @@ __device__ __forceinline__ void cos_sin_2pi(float u, float &cs, float &sn) {
   pc = __fmaf_rn(pc, x2, -0.5f);
   pc = __fmaf_rn(pc, x2, 1.0f);
   const float cx = pc;
-  switch (q & 3) {
-    case 0: cs = cx; sn = sx; break;
-    case 1: cs = -sx; sn = cx; break;
-    case 2: cs = -cx; sn = -sx; break;
-    default: cs = sx; sn = -cx; break;
-  }
+  // quadrant rotation by q = 0..3: (cos, sin) = (c, s), (-s, c), (-c, -s), (s, -c); negation flips the sign
+  // bit, which is exact, so the selects equal the case analysis
+  const bool odd = (q & 1) != 0;
+  const float a = odd ? sx : cx, b = odd ? cx : sx;
+  cs = __uint_as_float(__float_as_uint(a) ^ ((unsigned)((q + 1) & 2) << 30));
+  sn = __uint_as_float(__float_as_uint(b) ^ ((unsigned)(q & 2) << 30));
 }
 
-// Three standard normals for (seed, replica, site, step).
-__device__ __forceinline__ void normals3(uint64_t seed, uint32_t replica, uint64_t site, uint64_t step, float &e0,
-                                         float &e1, float &e2) {
-  uint32_t c[4] = {(uint32_t)site, (uint32_t)(site >> 32), (uint32_t)step, replica << 8};
-  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+// Box-Muller on the four Philox words c: eta0, eta1 from (c0, c1), eta2 from (c2, c3).
+__device__ __forceinline__ void box_muller3(const uint32_t c[4], float &e0, float &e1, float &e2) {
   const float r0 = __fsqrt_rn(__fmul_rn(-2.0f, ln_open(unit_open(c[0]))));
   float cs, sn, cs2, sn2;
   cos_sin_2pi(unit_open(c[1]), cs, sn);
@@ -108,6 +140,22 @@ __device__ __forceinline__ void normals3(uint64_t seed, uint32_t replica, uint64
   e0 = __fmul_rn(r0, cs);
   e1 = __fmul_rn(r0, sn);
   e2 = __fmul_rn(r1, cs2);
+}
+
+// Three standard normals for (seed, replica, site, step).
+__device__ __forceinline__ void normals3(uint64_t seed, uint32_t replica, uint64_t site, uint64_t step, float &e0,
+                                         float &e1, float &e2) {
+  uint32_t c[4] = {(uint32_t)site, (uint32_t)(site >> 32), (uint32_t)step, replica << 8};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  box_muller3(c, e0, e1, e2);
+}
+
+// The same normals with the round keys of the seed precomputed (philox_keys).
+__device__ __forceinline__ void normals3(const PhiloxKeys &K, uint32_t replica, uint64_t site, uint64_t step,
+                                         float &e0, float &e1, float &e2) {
+  uint32_t c[4] = {(uint32_t)site, (uint32_t)(site >> 32), (uint32_t)step, replica << 8};
+  philox4x32_10_rk(c, K);
+  box_muller3(c, e0, e1, e2);
 }
 
 }  // namespace sx

@@ -120,32 +120,31 @@ __device__ __forceinline__ R site_angle(const R s[3], const R dl[3]) {
   return r_atan2(r_sqrt(c0 * c0 + c1 * c1 + c2 * c2), R(1) - R(0.5) * dot3(dl, dl));
 }
 
-// S <- R_exp(S, u) for a tangent u; s64 is the FP64 state, sr its copy in R.
-__device__ __forceinline__ void retract(const double s64[3], const double sr[3], const double u[3], double out[3]) {
+// S <- R_exp(S, u) for a tangent u; s64 is the FP64 state, sr its copy in R.  Returns true when
+// the result is not finite or has zero length (a numeric error).
+__device__ __forceinline__ bool retract(const double s64[3], const double sr[3], const double u[3], double out[3]) {
   (void)sr;
   const double a = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   if (a == 0.0) {
     out[0] = s64[0];
     out[1] = s64[1];
     out[2] = s64[2];
-    return;
+    return !(fabs(s64[0]) + fabs(s64[1]) + fabs(s64[2]) < 1e300);
   }
   const double c = cos(a), sn = sin(a) / a;
-  double x[3];
-  for (int k = 0; k < 3; ++k) x[k] = c * s64[k] + sn * u[k];
-  const double r = 1.0 / sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-  for (int k = 0; k < 3; ++k) out[k] = x[k] * r;
+  for (int k = 0; k < 3; ++k) out[k] = c * s64[k] + sn * u[k];
+  return unit64_checked(out);
 }
 
 // FP32 arithmetic, FP64 state: d = (cos a - 1) s + (sin a / a) u with
 // cos a - 1 = -2 sin^2(a/2), then S' = N[S + d] in FP64.
-__device__ __forceinline__ void retract(const double s64[3], const float sr[3], const float u[3], double out[3]) {
+__device__ __forceinline__ bool retract(const double s64[3], const float sr[3], const float u[3], double out[3]) {
   const float a = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   const float h = sinf(0.5f * a);
   const float c1 = -2.0f * h * h;
   const float sc = a > 0.0f ? sinf(a) / a : 1.0f;
   const float d[3] = {c1 * sr[0] + sc * u[0], c1 * sr[1] + sc * u[1], c1 * sr[2] + sc * u[2]};
-  renormalise64(s64, d, out);
+  return renormalise64(s64, d, out);
 }
 
 // Zeeman term mu mu_B B per sublattice in the arithmetic type of the path kernels
@@ -350,17 +349,25 @@ __global__ void __launch_bounds__(kPT) k_path_coef(const double *__restrict__ su
   }
 }
 
+// larger of two non-negative values, NaN from either operand kept (a non-finite force must not read as converged)
+template <typename R>
+__device__ __forceinline__ R max_keep_nan(R a, R b) {
+  return (a > b || a != a) ? a : b;
+}
+
 template <typename R>
 __device__ __forceinline__ void record_max(R v, unsigned long long *slot) {
   __shared__ R red[kPT / 32];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = max_keep_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0 && slot) {
-    for (int w = 1; w < kPT / 32; ++w) v = max(v, red[w]);
-    // non-negative doubles order like their bit patterns
-    atomicMax(slot, (unsigned long long)__double_as_longlong(to_d(v)));
+    for (int w = 1; w < kPT / 32; ++w) v = max_keep_nan(v, red[w]);
+    // non-negative doubles order like their bit patterns; a positive NaN orders above every finite value
+    double d = to_d(v);
+    if (d != d) d = __longlong_as_double(0x7FF8000000000000ll);
+    atomicMax(slot, (unsigned long long)__double_as_longlong(d));
   }
 }
 
@@ -369,7 +376,8 @@ __device__ __forceinline__ void record_max(R v, unsigned long long *slot) {
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_gneb_update(const double *__restrict__ X, double *__restrict__ Y, long long N,
                                                      const R *__restrict__ coef, R dt,
-                                                     unsigned long long *__restrict__ fmax_slot) {
+                                                     unsigned long long *__restrict__ fmax_slot,
+                                                     int *__restrict__ status) {
   const int n = blockIdx.y + 1;
   const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
   R fm = 0;
@@ -393,7 +401,7 @@ __global__ void __launch_bounds__(kPT) k_gneb_update(const double *__restrict__ 
     fm = r_sqrt(dot3(u, u));
     for (int k = 0; k < 3; ++k) u[k] *= dt;
     double out[3];
-    retract(s64, s, u, out);
+    report_numeric(status, retract(s64, s, u, out));
     Yn[i] = out[0];
     Yn[N + i] = out[1];
     Yn[2 * N + i] = out[2];
@@ -475,7 +483,8 @@ __global__ void __launch_bounds__(kPT) k_gneb_vp_coef(const double *__restrict__
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_gneb_vp_update(const double *__restrict__ X, double *__restrict__ Y,
                                                         long long N, const R *__restrict__ Fp,
-                                                        const double *__restrict__ cvp, R dt) {
+                                                        const double *__restrict__ cvp, R dt,
+                                                        int *__restrict__ status) {
   const int n = blockIdx.y + 1;
   const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
   if (i >= N) return;
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(kPT) k_gneb_vp_update(const double *__restrict
     u[k] = dt * c * f + h * f;
   }
   double out[3];
-  retract(s64, s, u, out);
+  report_numeric(status, retract(s64, s, u, out));
   Yn[i] = out[0];
   Yn[N + i] = out[1];
   Yn[2 * N + i] = out[2];
@@ -502,7 +511,8 @@ __global__ void __launch_bounds__(kPT) k_gneb_vp_update(const double *__restrict
 // string step, in place on interior image n = blockIdx.y + 1 of X (field in slot n of Y)
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_string_step(double *__restrict__ X, const double *__restrict__ Y, long long N,
-                                                     R dt, unsigned long long *__restrict__ fmax_slot) {
+                                                     R dt, unsigned long long *__restrict__ fmax_slot,
+                                                     int *__restrict__ status) {
   const int n = blockIdx.y + 1;
   const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
   R fm = 0;
@@ -516,7 +526,7 @@ __global__ void __launch_bounds__(kPT) k_string_step(double *__restrict__ X, con
     fm = r_sqrt(dot3(b, b));
     R u[3] = {dt * b[0], dt * b[1], dt * b[2]};
     double out[3];
-    retract(s64, s, u, out);
+    report_numeric(status, retract(s64, s, u, out));
     S[i] = out[0];
     S[N + i] = out[1];
     S[2 * N + i] = out[2];
@@ -525,7 +535,7 @@ __global__ void __launch_bounds__(kPT) k_string_step(double *__restrict__ X, con
 }
 
 // slerp(a, c; w) on one site, FP64
-__device__ __forceinline__ void slerp_site(const double a[3], const double c[3], double w, double out[3]) {
+__device__ __forceinline__ bool slerp_site(const double a[3], const double c[3], double w, double out[3]) {
   const double c0 = a[1] * c[2] - a[2] * c[1], c1 = a[2] * c[0] - a[0] * c[2], c2 = a[0] * c[1] - a[1] * c[0];
   const double th = atan2(sqrt(c0 * c0 + c1 * c1 + c2 * c2), a[0] * c[0] + a[1] * c[1] + a[2] * c[2]);
   double x[3];
@@ -535,12 +545,12 @@ __device__ __forceinline__ void slerp_site(const double a[3], const double c[3],
     const double st = sin(th), p = sin((1.0 - w) * th) / st, q = sin(w * th) / st;
     for (int k = 0; k < 3; ++k) x[k] = p * a[k] + q * c[k];
   }
-  const double r = 1.0 / sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-  for (int k = 0; k < 3; ++k) out[k] = x[k] * r;
+  for (int k = 0; k < 3; ++k) out[k] = x[k];
+  return unit64_checked(out);
 }
 
 // FP32 arithmetic, FP64 state: out = N[a + d], d = (p + q - 1) a + q (c - a)
-__device__ __forceinline__ void slerp_site_f(const double a64[3], const float a[3], const float c[3], float w,
+__device__ __forceinline__ bool slerp_site_f(const double a64[3], const float a[3], const float c[3], float w,
                                              double out[3]) {
   const float dl[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
   const float th = site_angle<float>(a, dl);
@@ -555,13 +565,14 @@ __device__ __forceinline__ void slerp_site_f(const double a64[3], const float a[
     pq1 = (p - 1.0f) + q;
   }
   const float d[3] = {pq1 * a[0] + q * dl[0], pq1 * a[1] + q * dl[1], pq1 * a[2] + q * dl[2]};
-  renormalise64(a64, d, out);
+  return renormalise64(a64, d, out);
 }
 
 // string redistribution: interior image n = blockIdx.y + 1 of Y from images j, j+1 of X
 template <typename R>
 __global__ void __launch_bounds__(kPT) k_string_redistribute(const double *__restrict__ X, double *__restrict__ Y,
-                                                             long long N, const R *__restrict__ coef) {
+                                                             long long N, const R *__restrict__ coef,
+                                                             int *__restrict__ status) {
   const int n = blockIdx.y + 1;
   const long long i = (long long)blockIdx.x * kPT + threadIdx.x;
   if (i >= N) return;
@@ -572,12 +583,12 @@ __global__ void __launch_bounds__(kPT) k_string_redistribute(const double *__res
   double out[3];
   if constexpr (sizeof(R) == 8) {
     const double c64[3] = {Cn[i], Cn[N + i], Cn[2 * N + i]};
-    slerp_site(a64, c64, w, out);
+    report_numeric(status, slerp_site(a64, c64, w, out));
   } else {
     float a[3], c[3];
     load3<float>(A, N, i, a);
     load3<float>(Cn, N, i, c);
-    slerp_site_f(a64, a, c, w, out);
+    report_numeric(status, slerp_site_f(a64, a, c, w, out));
   }
   double *Yn = Y + 3 * N * (long long)n;
   Yn[i] = out[0];
@@ -696,11 +707,11 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
     if (measure && (e = cudaMemsetAsync(l.fmax, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     if ((e = field(c, X + stride, Y + stride, M - 2, stride, true, st)) != cudaSuccess) return e;
     if (string) {
-      k_string_step<R><<<gupd, kPT, 0, st>>>(X, Y, N, dt, slot);
+      k_string_step<R><<<gupd, kPT, 0, st>>>(X, Y, N, dt, slot, c->d_status);
       k_path_reduce<R, MODE_GEO><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, nsub, zr, 0, 1, l.partial);
       k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 1, l.sums);
       k_path_coef<<<1, kPT, 0, st>>>(l.sums, l.eend, M, p->method, p->k_spring, l.coef, l.coeff, l.E, l.L);
-      k_string_redistribute<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR);
+      k_string_redistribute<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, c->d_status);
     } else {
       k_path_reduce<R, MODE_FULL><<<gred, kPT, 0, st>>>(X, Y, N, c->geo.ncell, nsub, zr, 0, 1, l.partial);
       k_path_sum<<<M - 1, kPT, 0, st>>>(l.partial, nb, 0, l.sums);
@@ -709,10 +720,10 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
         R *Fr = reinterpret_cast<R *>(l.Fp);
         k_gneb_vp_force<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, l.cvp, Fr, vp_first, l.vp_partial, slot);
         k_gneb_vp_coef<<<1, kPT, 0, st>>>(l.vp_partial, (long long)nbu * (M - 2), l.cvp);
-        k_gneb_vp_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, Fr, l.cvp, dt);
+        k_gneb_vp_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, Fr, l.cvp, dt, c->d_status);
         vp_first = 0;
       } else {
-        k_gneb_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, slot);
+        k_gneb_update<R><<<gupd, kPT, 0, st>>>(X, Y, N, coefR, dt, slot, c->d_status);
       }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -723,7 +734,7 @@ cudaError_t run_path(sx_ctx *c, double *img, int M, const sx_path_params *p, int
       if ((e = cudaMemcpyAsync(&bits, l.fmax, sizeof(bits), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
       if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
       memcpy(&fmax, &bits, sizeof(fmax));
-      if (fmax < p->tol) break;
+      if (fmax < p->tol || !(fmax == fmax)) break;
     }
   }
   // energies of the final chain (the tangent sums computed alongside are unused)

@@ -107,38 +107,57 @@ struct KeepBCC4 {
   }
 };
 
-enum FamilyId { FAM_SC6_ISO = 0, FAM_SC6_TEN, FAM_SC26_ISO, FAM_SC26_TEN, FAM_SC32_ISO, FAM_BCC4, FAM_COUNT };
+enum FamilyId {
+  FAM_SC6_ISO = 0,
+  FAM_SC6_TEN,
+  FAM_SC26_ISO,
+  FAM_SC26_TEN,
+  FAM_SC32_ISO,
+  FAM_BCC4,
+  FAM_SC26_SHELL,
+  FAM_COUNT
+};
 
 template <int ID>
 struct Family;
 template <>
 struct Family<FAM_SC6_ISO> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC6{1});
 };
 template <>
 struct Family<FAM_SC6_TEN> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC6{2});
 };
 template <>
 struct Family<FAM_SC26_ISO> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{1});
 };
 template <>
 struct Family<FAM_SC26_TEN> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{2});
+};
+// simple cubic 3x3x3 cube with one exchange constant per distance shell (100), (110), (111) and, on
+// the in-plane nearest-neighbour bonds, the off-diagonal entries of interfacial DMI (xz, zx on x bonds,
+// yz, zy on y bonds).  The field of a plane is summed by shells (push_shell26): in-plane edge and
+// corner sums E and K of the plane, then J1 C + J2 E + J3 K for the outputs one plane away and
+// J1 E + J2 K (+ DMI) for the outputs in the plane -- about half the arithmetic of 26 separate taps.
+template <>
+struct Family<FAM_SC26_SHELL> {
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 1;
+  static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{1});
 };
 template <>
 struct Family<FAM_SC32_ISO> {
-  static constexpr int NSUB = 1, R = 2, BY = 16, NTAP = 32, MINB = 1;
+  static constexpr int NSUB = 1, R = 2, BY = 16, NTAP = 32, MINB = 1, RYF = 1, TYF = 16, MINBF = 1, SHELL = 0;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 2, KeepSC32{});
 };
 template <>
 struct Family<FAM_BCC4> {
-  static constexpr int NSUB = 2, R = 2, BY = 16, NTAP = 100, MINB = 1;
+  static constexpr int NSUB = 2, R = 2, BY = 16, NTAP = 100, MINB = 1, RYF = 1, TYF = 16, MINBF = 1, SHELL = 0;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(2, 2, KeepBCC4{});
 };
 
@@ -165,6 +184,8 @@ struct StencilArgs {
   float g, alpha, dt, hdt;
   unsigned long long seed, step;
   unsigned replica;
+  int *status;      // the context's status word (numeric errors of the state update)
+  PhiloxKeys keys;  // round keys of seed
 };
 
 struct GridBar;
@@ -212,10 +233,13 @@ __device__ __forceinline__ void cp_wait() {
 
 // ------------------------------------------------------------------ geometry
 
+// Fused-kernel geometry: a CTA of 32 x TYF threads owns a 32 x BY predictor
+// region (BY = RYF * TYF rows; each thread RYF adjacent rows of one column),
+// whose interior TX x TY columns are its outputs.
 template <class F>
 struct G {
-  static constexpr int NS = F::NSUB, R = F::R, BY = F::BY;
-  static constexpr int BX = 32, NT = BX * BY, TX = BX - 2 * R, TY = BY - 2 * R;
+  static constexpr int NS = F::NSUB, R = F::R, RY = F::RYF, TYT = F::TYF, BY = RY * TYT;
+  static constexpr int BX = 32, NT = BX * TYT, TX = BX - 2 * R, TY = BY - 2 * R;
   static constexpr int LX = BX + 2 * R, LY = BY + 2 * R;
   static constexpr int Q = R + 1;                   // ring depth (planes)
   static constexpr int SN = NS * LY * LX;           // sites per staged S^n plane (load region)
@@ -265,6 +289,52 @@ __device__ __forceinline__ void push_all(std::integer_sequence<int, I...>, const
                                          Acc3 (&acc)[F::NSUB][2 * F::R + 1]) {
   float4 v;
   (tap_push<F, I>(p, base, pitch_sub, pitch_row, v, acc), ...);
+}
+
+// Field of one staged plane by distance shells (FAM_SC26_SHELL): p.Jiso[0..2] = J1..J3, p.Jt[0..3] the
+// in-plane nearest-neighbour bonds (dx, dy) = (-1, 0), (1, 0), (0, -1), (0, 1) (only their DMI entries
+// [2], [6] (x bonds) and [5], [7] (y bonds) are read).  acc[0][0] collects the outputs one plane below
+// the staged plane, acc[0][1] those in it, acc[0][2] those one plane above.
+__device__ __forceinline__ void push_shell26(const StencilArgs &p, const float4 *__restrict__ base, int pitch_row,
+                                             Acc3 (&acc)[1][3]) {
+  const float4 c = base[0];
+  const float4 w = base[-1], e = base[1];
+  const float4 n = base[-pitch_row], s = base[pitch_row];
+  const float4 nw = base[-pitch_row - 1], ne = base[-pitch_row + 1];
+  const float4 sw = base[pitch_row - 1], se = base[pitch_row + 1];
+  const float2 Exy = __fadd2_rn(__fadd2_rn(make_float2(w.x, w.y), make_float2(e.x, e.y)),
+                                __fadd2_rn(make_float2(n.x, n.y), make_float2(s.x, s.y)));
+  const float Ez = (w.z + e.z) + (n.z + s.z);
+  const float2 Kxy = __fadd2_rn(__fadd2_rn(make_float2(nw.x, nw.y), make_float2(ne.x, ne.y)),
+                                __fadd2_rn(make_float2(sw.x, sw.y), make_float2(se.x, se.y)));
+  const float Kz = (nw.z + ne.z) + (sw.z + se.z);
+  const float J1 = p.Jiso[0], J2 = p.Jiso[1], J3 = p.Jiso[2];
+  // outputs one plane away: J1 C + J2 E + J3 K
+  const float2 Txy = __ffma2_rn(make_float2(J3, J3), Kxy,
+                                __ffma2_rn(make_float2(J2, J2), Exy, __fmul2_rn(make_float2(J1, J1), make_float2(c.x, c.y))));
+  const float Tz = fmaf(J3, Kz, fmaf(J2, Ez, J1 * c.z));
+  acc[0][0].xy = __fadd2_rn(acc[0][0].xy, Txy);
+  acc[0][0].z += Tz;
+  acc[0][2].xy = __fadd2_rn(acc[0][2].xy, Txy);
+  acc[0][2].z += Tz;
+  // outputs in the plane: J1 E + J2 K and the DMI entries of the four in-plane bonds
+  float2 Mxy = __ffma2_rn(make_float2(J2, J2), Kxy, __fmul2_rn(make_float2(J1, J1), Exy));
+  float Mz = fmaf(J2, Kz, J1 * Ez);
+  Mxy.x = fmaf(p.Jt[1][2], e.z, fmaf(p.Jt[0][2], w.z, Mxy.x));
+  Mxy.y = fmaf(p.Jt[3][5], s.z, fmaf(p.Jt[2][5], n.z, Mxy.y));
+  Mz = fmaf(p.Jt[3][7], s.y, fmaf(p.Jt[2][7], n.y, fmaf(p.Jt[1][6], e.x, fmaf(p.Jt[0][6], w.x, Mz))));
+  acc[0][1].xy = __fadd2_rn(acc[0][1].xy, Mxy);
+  acc[0][1].z += Mz;
+}
+
+// Field of one staged plane into the accumulators: shell sums for FAM_SC26_SHELL, the tap list otherwise.
+template <class F>
+__device__ __forceinline__ void push_plane(const StencilArgs &p, const float4 *__restrict__ base, int pitch_sub,
+                                           int pitch_row, Acc3 (&acc)[F::NSUB][2 * F::R + 1]) {
+  if constexpr (F::SHELL)
+    push_shell26(p, base, pitch_row, acc);
+  else
+    push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, pitch_sub, pitch_row, acc);
 }
 
 template <class F>
@@ -355,16 +425,19 @@ __device__ __forceinline__ void onsite32(const StencilArgs &p, int a, const floa
 // One normalised Heun step from Sin to Sout.  Per z iteration k (plane q = z0 - 2R + k):
 //   1. this thread's staged copy of plane q lands -> FP32 ring slot; the copies of plane q+1 and
 //      of the FP64 state of the corrector sites are issued (asynchronous, no registers held);
-//   2. plane q is pushed into the predictor accumulators; the predictor of plane q - R runs on the
-//      whole 32 x BY region (tile + halo) and writes S~ and, for interior columns, f0 and eta;
-//   3. interior columns push S~ of plane q - R into the corrector accumulators and finish the
+//   2. plane q is pushed into the predictor accumulators of the thread's RY rows; the predictor of
+//      plane q - R runs on the whole 32 x BY region (tile + halo) and writes S~ and, for interior
+//      columns, f0 and eta;
+//   3. interior rows push S~ of plane q - R into the corrector accumulators and finish the
 //      corrector of plane q - 2R in FP64.
+// Rows of one thread share the column's bookkeeping and, where their neighbourhoods overlap, the
+// shared-memory reads of the field push; each row's tap order is that of the pass kernels.
 template <int FID>
-__global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINB)
+__global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINBF)
     k_heun_fused(const StencilArgs p, const double *__restrict__ Sin, double *__restrict__ Sout) {
   using F = Family<FID>;
   using g = G<F>;
-  constexpr int NS = F::NSUB, R = F::R, Q = g::Q;
+  constexpr int NS = F::NSUB, R = F::R, Q = g::Q, RY = g::RY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *sn = reinterpret_cast<float4 *>(smem_raw);                 // [Q][SN]
   float4 *st = reinterpret_cast<float4 *>(smem_raw + g::OFF_ST);     // [Q][ST]
@@ -375,22 +448,35 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINB)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   const int x0 = blockIdx.x * g::TX, y0 = blockIdx.y * g::TY, z0 = blockIdx.z * p.tz;
   const int tzc = min(p.tz, p.nz - z0);
-  const int cx = x0 - R + tx, cy = y0 - R + ty;  // this thread's predictor column
-  const bool inner = tx >= R && tx < 32 - R && ty >= R && ty < F::BY - R && cx < p.nx && cy < p.ny;
-  const int ii = (ty - R) * g::TX + (tx - R);    // interior index (valid when inner)
-  bool col_ok = true;
-  const int wx = wrap_axis(cx, p.nx, p.px, col_ok);
-  const int wy = wrap_axis(cy, p.ny, p.py, col_ok);
+  const int ry0 = ty * RY;                       // first region row of this thread
+  const int cx = x0 - R + tx;                    // this thread's predictor column
+  bool xok = true;
+  const int wx = wrap_axis(cx, p.nx, p.px, xok);
+  const bool xin = tx >= R && tx < 32 - R && cx < p.nx;
   const long long plane = (long long)p.ny * p.nx, subvol = (long long)p.nz * plane;
+  bool col_ok[RY], rin[RY], inner[RY];
+  int wy[RY], cy[RY], ii[RY];
+#pragma unroll
+  for (int j = 0; j < RY; ++j) {
+    cy[j] = y0 - R + ry0 + j;
+    col_ok[j] = xok;
+    wy[j] = wrap_axis(cy[j], p.ny, p.py, col_ok[j]);
+    rin[j] = ry0 + j >= R && ry0 + j < g::BY - R;  // interior row (the same for the whole warp)
+    inner[j] = rin[j] && xin && cy[j] < p.ny;
+    ii[j] = (ry0 + j - R) * g::TX + (tx - R);      // interior index (valid when inner)
+  }
 
   long long off[g::NLOAD];
   unsigned okmask;
   load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(p, x0 - 2 * R, y0 - 2 * R, tid, off, okmask);
 
-  Acc3 accp[NS][2 * R + 1];
-  Acc3 accc[NS][2 * R + 1];
-  zero_acc<F>(accp);
-  zero_acc<F>(accc);
+  Acc3 accp[RY][NS][2 * R + 1];
+  Acc3 accc[RY][NS][2 * R + 1];
+#pragma unroll
+  for (int j = 0; j < RY; ++j) {
+    zero_acc<F>(accp[j]);
+    zero_acc<F>(accc[j]);
+  }
 
   const int niter = tzc + 4 * R;
   issue_plane<g::NLOAD, g::NT, g::SN>(p, Sin, z0 - 2 * R, tid, off, okmask, stage);
@@ -402,13 +488,18 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINB)
     convert_plane<g::NLOAD, g::NT, g::SN>(stage, sn + (k % Q) * g::SN, tid);
     const int kp = k - 2 * R, kc = k - 4 * R;
     const int c = z0 + kc;
-    if (inner && kc >= 0) {  // FP64 state of this corrector site (staged 2R planes ago: L2-resident)
+    if (kc >= 0) {  // FP64 state of this iteration's corrector sites (staged 2R planes ago: L2-resident)
 #pragma unroll
-      for (int a = 0; a < NS; ++a) {
-        const double *src = Sin + a * subvol + c * plane + (long long)cy * p.nx + cx;
-        cp_async8(smem_addr(s64 + (a * 3 + 0) * g::NI + ii), src, true);
-        cp_async8(smem_addr(s64 + (a * 3 + 1) * g::NI + ii), src + p.nsite, true);
-        cp_async8(smem_addr(s64 + (a * 3 + 2) * g::NI + ii), src + 2 * p.nsite, true);
+      for (int j = 0; j < RY; ++j) {
+        if (inner[j]) {
+#pragma unroll
+          for (int a = 0; a < NS; ++a) {
+            const double *src = Sin + a * subvol + c * plane + (long long)cy[j] * p.nx + cx;
+            cp_async8(smem_addr(s64 + (a * 3 + 0) * g::NI + ii[j]), src, true);
+            cp_async8(smem_addr(s64 + (a * 3 + 1) * g::NI + ii[j]), src + p.nsite, true);
+            cp_async8(smem_addr(s64 + (a * 3 + 2) * g::NI + ii[j]), src + 2 * p.nsite, true);
+          }
+        }
       }
     }
     cp_commit();
@@ -416,90 +507,105 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINB)
     cp_commit();
     __syncthreads();
 
-    // predictor field: push the staged plane q into the accumulators
+    // predictor field: push the staged plane q into the accumulators of every row
     {
-      const float4 *base = sn + (k % Q) * g::SN + (ty + R) * g::LX + (tx + R);
-      push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, g::LX * g::LY, g::LX, accp);
+      const float4 *base = sn + (k % Q) * g::SN + (ry0 + R) * g::LX + (tx + R);
+#pragma unroll
+      for (int j = 0; j < RY; ++j)
+        push_plane<F>(p, base + j * g::LX, g::LX * g::LY, g::LX, accp[j]);
     }
     if (kp >= 0) {
       // predictor at plane pz = q - R for every column of the 32 x BY region
       const int pz = q - R;
-      bool ok = col_ok;
-      const int wz = wrap_axis(pz, p.nz, p.pz, ok);
-      const float4 *cen = sn + ((k - R) % Q) * g::SN + (ty + R) * g::LX + (tx + R);
-      float4 *out = st + (kp % Q) * g::ST + ty * 32 + tx;
-      float *fo = fq + (kp % Q) * (NS * 6 * g::NI) + ii;
+      bool zok = true;
+      const int wz = wrap_axis(pz, p.nz, p.pz, zok);
+      const float4 *cen = sn + ((k - R) % Q) * g::SN + (ry0 + R) * g::LX + (tx + R);
+      float4 *out = st + (kp % Q) * g::ST + ry0 * 32 + tx;
+      float *fo = fq + (kp % Q) * (NS * 6 * g::NI);
 #pragma unroll
-      for (int a = 0; a < NS; ++a) {
-        float4 tilde = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ok) {
-          const float4 c4 = cen[a * g::LX * g::LY];
-          const float s[3] = {c4.x, c4.y, c4.z};
-          float b[3] = {accp[a][0].xy.x, accp[a][0].xy.y, accp[a][0].z};
-          onsite32(p, a, s, b);
-          float e0 = 0.f, e1 = 0.f, e2 = 0.f;
-          if (p.thermal) {
-            const unsigned long long site = (unsigned long long)(a * subvol + wz * plane + (long long)wy * p.nx + wx);
-            normals3(p.seed, p.replica, site, p.step, e0, e1, e2);
-          }
-          const float sg = p.sigma[a], im = p.inv_mm[a];
-          const float B[3] = {fmaf(b[0], im, sg * e0), fmaf(b[1], im, sg * e1), fmaf(b[2], im, sg * e2)};
-          float f[3];
-          rhs32(s, B, p.g, p.alpha, f);
-          const float x[3] = {fmaf(p.dt, f[0], s[0]), fmaf(p.dt, f[1], s[1]), fmaf(p.dt, f[2], s[2])};
-          const float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-          float r = rsqrtf(n2);
-          r = r * fmaf(-0.5f * n2, r * r, 1.5f);
-          tilde = make_float4(x[0] * r, x[1] * r, x[2] * r, 0.f);
-          if (inner) {
-            float *fa = fo + a * 6 * g::NI;
-            fa[0] = f[0];
-            fa[g::NI] = f[1];
-            fa[2 * g::NI] = f[2];
-            fa[3 * g::NI] = e0;
-            fa[4 * g::NI] = e1;
-            fa[5 * g::NI] = e2;
-          }
-        }
-        out[a * 32 * F::BY] = tilde;
-      }
-    }
-    shift_acc<F>(accp);
-    __syncthreads();
-
-    if (inner && kp >= 0) {
-      // corrector field: push the S~ plane just computed
-      const float4 *base = st + (kp % Q) * g::ST + ty * 32 + tx;
-      push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, 32 * F::BY, 32, accc);
-      if (kc >= 0) {
-        const int slot = (kc + R) % Q;
-        const float4 *cen = st + slot * g::ST + ty * 32 + tx;
-        const float *fi = fq + slot * (NS * 6 * g::NI) + ii;
-        cp_wait<1>();  // this thread's FP64 state copies (all but the newest group)
+      for (int j = 0; j < RY; ++j) {
 #pragma unroll
         for (int a = 0; a < NS; ++a) {
-          const float4 c4 = cen[a * 32 * F::BY];
-          const float s[3] = {c4.x, c4.y, c4.z};
-          float b[3] = {accc[a][0].xy.x, accc[a][0].xy.y, accc[a][0].z};
-          onsite32(p, a, s, b);
-          const float *fa = fi + a * 6 * g::NI;
-          const float sg = p.sigma[a], im = p.inv_mm[a];
-          const float B[3] = {fmaf(b[0], im, sg * fa[3 * g::NI]), fmaf(b[1], im, sg * fa[4 * g::NI]),
-                              fmaf(b[2], im, sg * fa[5 * g::NI])};
-          float f[3];
-          rhs32(s, B, p.g, p.alpha, f);
-          const float d[3] = {p.hdt * (fa[0] + f[0]), p.hdt * (fa[g::NI] + f[1]), p.hdt * (fa[2 * g::NI] + f[2])};
-          const double S0[3] = {s64[(a * 3 + 0) * g::NI + ii], s64[(a * 3 + 1) * g::NI + ii],
-                                s64[(a * 3 + 2) * g::NI + ii]};
-          double o[3];
-          renormalise64(S0, d, o);
-          const long long i = a * subvol + c * plane + (long long)cy * p.nx + cx;
-          Sout[i] = o[0];
-          Sout[p.nsite + i] = o[1];
-          Sout[2 * p.nsite + i] = o[2];
+          float4 tilde = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (zok && col_ok[j]) {
+            const float4 c4 = cen[j * g::LX + a * g::LX * g::LY];
+            const float s[3] = {c4.x, c4.y, c4.z};
+            float b[3] = {accp[j][a][0].xy.x, accp[j][a][0].xy.y, accp[j][a][0].z};
+            onsite32(p, a, s, b);
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            if (p.thermal) {
+              const unsigned long long site =
+                  (unsigned long long)(a * subvol + wz * plane + (long long)wy[j] * p.nx + wx);
+              normals3(p.keys, p.replica, site, p.step, e0, e1, e2);
+            }
+            const float sg = p.sigma[a], im = p.inv_mm[a];
+            const float B[3] = {fmaf(b[0], im, sg * e0), fmaf(b[1], im, sg * e1), fmaf(b[2], im, sg * e2)};
+            float f[3];
+            rhs32(s, B, p.g, p.alpha, f);
+            const float x[3] = {fmaf(p.dt, f[0], s[0]), fmaf(p.dt, f[1], s[1]), fmaf(p.dt, f[2], s[2])};
+            const float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            float r = rsqrtf(n2);
+            r = r * fmaf(-0.5f * n2, r * r, 1.5f);
+            tilde = make_float4(x[0] * r, x[1] * r, x[2] * r, 0.f);
+            if (inner[j]) {
+              float *fa = fo + a * 6 * g::NI + ii[j];
+              fa[0] = f[0];
+              fa[g::NI] = f[1];
+              fa[2 * g::NI] = f[2];
+              fa[3 * g::NI] = e0;
+              fa[4 * g::NI] = e1;
+              fa[5 * g::NI] = e2;
+            }
+          }
+          out[j * 32 + a * 32 * g::BY] = tilde;
         }
       }
-      shift_acc<F>(accc);
+    }
+#pragma unroll
+    for (int j = 0; j < RY; ++j) shift_acc<F>(accp[j]);
+    __syncthreads();
+
+    if (kp >= 0) {
+      // corrector field: push the S~ plane just computed (interior rows)
+      const float4 *base = st + (kp % Q) * g::ST + ry0 * 32 + tx;
+#pragma unroll
+      for (int j = 0; j < RY; ++j)
+        if (rin[j])
+          push_plane<F>(p, base + j * 32, 32 * g::BY, 32, accc[j]);
+      if (kc >= 0) {
+        const int slot = (kc + R) % Q;
+        const float4 *cen = st + slot * g::ST + ry0 * 32 + tx;
+        const float *fi = fq + slot * (NS * 6 * g::NI);
+        cp_wait<1>();  // this thread's FP64 state copies (all but the newest group)
+#pragma unroll
+        for (int j = 0; j < RY; ++j) {
+          if (!inner[j]) continue;
+#pragma unroll
+          for (int a = 0; a < NS; ++a) {
+            const float4 c4 = cen[j * 32 + a * 32 * g::BY];
+            const float s[3] = {c4.x, c4.y, c4.z};
+            float b[3] = {accc[j][a][0].xy.x, accc[j][a][0].xy.y, accc[j][a][0].z};
+            onsite32(p, a, s, b);
+            const float *fa = fi + a * 6 * g::NI + ii[j];
+            const float sg = p.sigma[a], im = p.inv_mm[a];
+            const float B[3] = {fmaf(b[0], im, sg * fa[3 * g::NI]), fmaf(b[1], im, sg * fa[4 * g::NI]),
+                                fmaf(b[2], im, sg * fa[5 * g::NI])};
+            float f[3];
+            rhs32(s, B, p.g, p.alpha, f);
+            const float d[3] = {p.hdt * (fa[0] + f[0]), p.hdt * (fa[g::NI] + f[1]), p.hdt * (fa[2 * g::NI] + f[2])};
+            const double S0[3] = {s64[(a * 3 + 0) * g::NI + ii[j]], s64[(a * 3 + 1) * g::NI + ii[j]],
+                                  s64[(a * 3 + 2) * g::NI + ii[j]]};
+            double o[3];
+            report_numeric(p.status, renormalise64(S0, d, o));
+            const long long i = a * subvol + c * plane + (long long)cy[j] * p.nx + cx;
+            Sout[i] = o[0];
+            Sout[p.nsite + i] = o[1];
+            Sout[2 * p.nsite + i] = o[2];
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RY; ++j) shift_acc<F>(accc[j]);
     }
   }
   cp_wait<0>();
@@ -534,7 +640,8 @@ enum PassMode { PASS_FIELD = 0, PASS_PRED = 1, PASS_CORR = 2 };
 struct PassIO {
   const double *S;   // FIELD, PRED: input spins; CORR: the FP64 state S^n
   const float *St;   // CORR: S~ (three FP32 planes)
-  double *b;         // FIELD: output field
+  double *b;         // FIELD: output field (FP64)
+  float *bf;         // FIELD: output field in FP32 instead, when set
   float *St_out;     // PRED: S~
   float *f0;         // PRED: written; CORR: read
   float *eta;        // thermal steps: the normals, written by PRED and read by CORR
@@ -639,7 +746,7 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
     cp_commit();
     if constexpr (MODE != PASS_CORR) __syncthreads();
     const float4 *base = buf + (ty + R) * g::LX + (tx + R);
-    push_all<F>(std::make_integer_sequence<int, F::NTAP>{}, p, base, g::LX * g::LY, g::LX, acc);
+    push_plane<F>(p, base, g::LX * g::LY, g::LX, acc);
     // keep this plane's centre values for the epilogue R planes later
 #pragma unroll
     for (int a = 0; a < NS; ++a) cq[((k % (R + 1)) * NS + a) * g::NT + tid] = base[a * g::LX * g::LY];
@@ -654,15 +761,21 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
         const long long i = a * subvol + c * plane + (long long)cy * gg.nx + cx;
         if constexpr (MODE == PASS_FIELD) {
           if (onsite) onsite32(p, a, s, v);
-          bout[i] = (double)v[0];
-          bout[gg.nsite + i] = (double)v[1];
-          bout[2 * gg.nsite + i] = (double)v[2];
+          if (io.bf) {
+            io.bf[i] = v[0];
+            io.bf[gg.nsite + i] = v[1];
+            io.bf[2 * gg.nsite + i] = v[2];
+          } else {
+            bout[i] = (double)v[0];
+            bout[gg.nsite + i] = (double)v[1];
+            bout[2 * gg.nsite + i] = (double)v[2];
+          }
         } else {
           onsite32(p, a, s, v);
           float e0 = 0.f, e1 = 0.f, e2 = 0.f;
           if constexpr (MODE == PASS_PRED) {
             if (p.thermal) {
-              normals3(p.seed, gg.replica, (unsigned long long)i, io.step, e0, e1, e2);
+              normals3(p.keys, gg.replica, (unsigned long long)i, io.step, e0, e1, e2);
               io.eta[i] = e0;
               io.eta[gg.nsite + i] = e1;
               io.eta[2 * gg.nsite + i] = e2;
@@ -690,7 +803,7 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
           } else {
             const float d[3] = {p.hdt * (nf[a][0] + f[0]), p.hdt * (nf[a][1] + f[1]), p.hdt * (nf[a][2] + f[2])};
             double o[3];
-            renormalise64(nS[a], d, o);
+            report_numeric(p.status, renormalise64(nS[a], d, o));
             io.Sout[i] = o[0];
             io.Sout[gg.nsite + i] = o[1];
             io.Sout[2 * gg.nsite + i] = o[2];
@@ -863,6 +976,50 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
 
 namespace {
 
+// FAM_SC26_SHELL: taps inside the 3x3x3 cube, each distance shell complete (6, 12, 8 taps) or absent,
+// diagonal J equal within a shell, off-diagonal entries only the interfacial-DMI ones of the in-plane
+// nearest-neighbour bonds.  An absent shell gets J = 0.
+bool match_shell26(const sx_ctx *c, StencilArgs &a) {
+  if (c->lat.nsub != 1) return false;
+  for (int k = 0; k < kMaxIso; ++k) a.Jiso[k] = 0.0f;
+  for (int k = 0; k < kMaxTen; ++k)
+    for (int m = 0; m < 9; ++m) a.Jt[k][m] = 0.0f;
+  double Js[3] = {0.0, 0.0, 0.0};
+  int count[3] = {0, 0, 0};
+  for (const Tap &t : c->taps[0]) {
+    const int dx = t.d[0], dy = t.d[1], dz = t.d[2];
+    if (t.b != 0 || dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return false;
+    const int d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 == 0) return false;
+    if (t.J[0] != t.J[4] || t.J[4] != t.J[8]) return false;
+    if (count[d2 - 1] > 0 && Js[d2 - 1] != t.J[0]) return false;
+    Js[d2 - 1] = t.J[0];
+    ++count[d2 - 1];
+    // permitted off-diagonal entries: xz, zx on (+-1, 0, 0); yz, zy on (0, +-1, 0)
+    bool allow[9] = {false, false, false, false, false, false, false, false, false};
+    int slot = -1;
+    if (d2 == 1 && dz == 0) {
+      if (dy == 0) {
+        allow[2] = allow[6] = true;
+        slot = dx < 0 ? 0 : 1;
+      } else {
+        allow[5] = allow[7] = true;
+        slot = dy < 0 ? 2 : 3;
+      }
+    }
+    for (int m : {1, 2, 3, 5, 6, 7})
+      if (!allow[m] && t.J[m] != 0.0) return false;
+    if (slot >= 0)
+      for (int m = 0; m < 9; ++m) a.Jt[slot][m] = m == 0 || m == 4 || m == 8 ? 0.0f : (float)t.J[m];
+  }
+  const int full[3] = {6, 12, 8};
+  for (int k = 0; k < 3; ++k)
+    if (count[k] != 0 && count[k] != full[k]) return false;
+  if (count[1] == 0 && count[2] == 0) return false;  // nearest neighbours only: the SC6 families are cheaper
+  for (int k = 0; k < 3; ++k) a.Jiso[k] = (float)Js[k];
+  return true;
+}
+
 template <int FID>
 bool match_family(const sx_ctx *c, StencilArgs &a) {
   using F = Family<FID>;
@@ -916,7 +1073,7 @@ cudaError_t launch_heun(const StencilPlan &sp, const StencilArgs &a, const doubl
                         cudaStream_t st) {
   using g = G<Family<FID>>;
   const dim3 grid((a.nx + g::TX - 1) / g::TX, (a.ny + g::TY - 1) / g::TY, (a.nz + sp.tz - 1) / sp.tz);
-  k_heun_fused<FID><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, src, dst);
+  k_heun_fused<FID><<<grid, dim3(32, g::TYT), g::SMEM, st>>>(a, src, dst);
   return cudaGetLastError();
 }
 
@@ -944,7 +1101,7 @@ int field_tz(const StencilPlan &sp, const StencilArgs &a, int count) {
 
 template <int FID>
 cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &base, int onsite, const double *S, double *b,
-                         int count, long long stride, cudaStream_t st) {
+                         int count, long long stride, cudaStream_t st, float *bf = nullptr) {
   using g = GF<Family<FID>>;
   StencilArgs a = base;
   a.tz = count == 1 ? sp.tz : field_tz<FID>(sp, a, count);
@@ -952,6 +1109,7 @@ cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &base, int ons
   memset(&io, 0, sizeof(io));
   io.S = S;
   io.b = b;
+  io.bf = bf;
   io.nzc = (a.nz + a.tz - 1) / a.tz;
   io.istride = stride;
   if ((long long)io.nzc * count > 65535) return cudaErrorInvalidConfiguration;
@@ -1151,6 +1309,8 @@ int stencil_plan(sx_ctx *c) {
     fam = FAM_SC6_ISO;
   else if (match_family<FAM_SC6_TEN>(c, a))
     fam = FAM_SC6_TEN;
+  else if (match_shell26(c, a))
+    fam = FAM_SC26_SHELL;
   else if (match_family<FAM_SC26_ISO>(c, a))
     fam = FAM_SC26_ISO;
   else if (match_family<FAM_SC26_TEN>(c, a))
@@ -1187,6 +1347,7 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC6_TEN: e = set_smem<FAM_SC6_TEN>(); break;
     case FAM_SC26_ISO: e = set_smem<FAM_SC26_ISO>(); break;
     case FAM_SC26_TEN: e = set_smem<FAM_SC26_TEN>(); break;
+    case FAM_SC26_SHELL: e = set_smem<FAM_SC26_SHELL>(); break;
     case FAM_SC32_ISO: e = set_smem<FAM_SC32_ISO>(); break;
     default: e = set_smem<FAM_BCC4>(); break;
   }
@@ -1199,6 +1360,7 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC6_TEN: sp->tz = choose_tz<FAM_SC6_TEN>(c); break;
     case FAM_SC26_ISO: sp->tz = choose_tz<FAM_SC26_ISO>(c); break;
     case FAM_SC26_TEN: sp->tz = choose_tz<FAM_SC26_TEN>(c); break;
+    case FAM_SC26_SHELL: sp->tz = choose_tz<FAM_SC26_SHELL>(c); break;
     case FAM_SC32_ISO: sp->tz = choose_tz<FAM_SC32_ISO>(c); break;
     default: sp->tz = choose_tz<FAM_BCC4>(c); break;
   }
@@ -1210,6 +1372,7 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC6_TEN: sp->occ_field = field_occupancy<FAM_SC6_TEN>(); break;
     case FAM_SC26_ISO: sp->occ_field = field_occupancy<FAM_SC26_ISO>(); break;
     case FAM_SC26_TEN: sp->occ_field = field_occupancy<FAM_SC26_TEN>(); break;
+    case FAM_SC26_SHELL: sp->occ_field = field_occupancy<FAM_SC26_SHELL>(); break;
     case FAM_SC32_ISO: sp->occ_field = field_occupancy<FAM_SC32_ISO>(); break;
     default: sp->occ_field = field_occupancy<FAM_BCC4>(); break;
   }
@@ -1218,6 +1381,7 @@ int stencil_plan(sx_ctx *c) {
     case FAM_SC6_TEN: sp->tz2 = field_tz<FAM_SC6_TEN>(*sp, a, 1); break;
     case FAM_SC26_ISO: sp->tz2 = field_tz<FAM_SC26_ISO>(*sp, a, 1); break;
     case FAM_SC26_TEN: sp->tz2 = field_tz<FAM_SC26_TEN>(*sp, a, 1); break;
+    case FAM_SC26_SHELL: sp->tz2 = field_tz<FAM_SC26_SHELL>(*sp, a, 1); break;
     case FAM_SC32_ISO: sp->tz2 = field_tz<FAM_SC32_ISO>(*sp, a, 1); break;
     default: sp->tz2 = field_tz<FAM_BCC4>(*sp, a, 1); break;
   }
@@ -1253,6 +1417,7 @@ int stencil_plan(sx_ctx *c) {
         case FAM_SC6_TEN: e2 = persistent_occupancy<FAM_SC6_TEN>(&occ); break;
         case FAM_SC26_ISO: e2 = persistent_occupancy<FAM_SC26_ISO>(&occ); break;
         case FAM_SC26_TEN: e2 = persistent_occupancy<FAM_SC26_TEN>(&occ); break;
+        case FAM_SC26_SHELL: e2 = persistent_occupancy<FAM_SC26_SHELL>(&occ); break;
         case FAM_SC32_ISO: e2 = persistent_occupancy<FAM_SC32_ISO>(&occ); break;
         default: e2 = persistent_occupancy<FAM_BCC4>(&occ); break;
       }
@@ -1337,6 +1502,7 @@ cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int
     case FAM_SC6_TEN: return launch_field<FAM_SC6_TEN>(sp, sp.base, onsite, S, b, count, stride, st);
     case FAM_SC26_ISO: return launch_field<FAM_SC26_ISO>(sp, sp.base, onsite, S, b, count, stride, st);
     case FAM_SC26_TEN: return launch_field<FAM_SC26_TEN>(sp, sp.base, onsite, S, b, count, stride, st);
+    case FAM_SC26_SHELL: return launch_field<FAM_SC26_SHELL>(sp, sp.base, onsite, S, b, count, stride, st);
     case FAM_SC32_ISO: return launch_field<FAM_SC32_ISO>(sp, sp.base, onsite, S, b, count, stride, st);
     default: return launch_field<FAM_BCC4>(sp, sp.base, onsite, S, b, count, stride, st);
   }
@@ -1344,6 +1510,20 @@ cudaError_t stencil_field_batch(const sx_ctx *c, const double *S, double *b, int
 
 cudaError_t stencil_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st) {
   return stencil_field_batch(c, S, b, 1, 0, onsite, st);
+}
+
+cudaError_t stencil_field_f32(const sx_ctx *c, const double *S, float *b, bool onsite, cudaStream_t st) {
+  const StencilPlan &sp = *c->stencil;
+  const int on = onsite ? 1 : 0;
+  switch (sp.family) {
+    case FAM_SC6_ISO: return launch_field<FAM_SC6_ISO>(sp, sp.base, on, S, nullptr, 1, 0, st, b);
+    case FAM_SC6_TEN: return launch_field<FAM_SC6_TEN>(sp, sp.base, on, S, nullptr, 1, 0, st, b);
+    case FAM_SC26_ISO: return launch_field<FAM_SC26_ISO>(sp, sp.base, on, S, nullptr, 1, 0, st, b);
+    case FAM_SC26_TEN: return launch_field<FAM_SC26_TEN>(sp, sp.base, on, S, nullptr, 1, 0, st, b);
+    case FAM_SC26_SHELL: return launch_field<FAM_SC26_SHELL>(sp, sp.base, on, S, nullptr, 1, 0, st, b);
+    case FAM_SC32_ISO: return launch_field<FAM_SC32_ISO>(sp, sp.base, on, S, nullptr, 1, 0, st, b);
+    default: return launch_field<FAM_BCC4>(sp, sp.base, on, S, nullptr, 1, 0, st, b);
+  }
 }
 
 namespace {
@@ -1356,8 +1536,10 @@ StencilArgs heun_args(const sx_ctx *c, const HeunConst &h, uint64_t step) {
   a.thermal = h.thermal;
   for (int s = 0; s < c->lat.nsub && s < 2; ++s) a.sigma[s] = (float)h.sigma[s];
   a.seed = h.seed;
+  a.keys = philox_keys(h.seed);
   a.replica = h.replica;
   a.step = step;
+  a.status = c->d_status;
   return a;
 }
 }  // namespace
@@ -1373,6 +1555,7 @@ cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S
     case FAM_SC6_TEN: return launch_persistent<FAM_SC6_TEN>(sp, a, S0, S1, nsteps, step0, st);
     case FAM_SC26_ISO: return launch_persistent<FAM_SC26_ISO>(sp, a, S0, S1, nsteps, step0, st);
     case FAM_SC26_TEN: return launch_persistent<FAM_SC26_TEN>(sp, a, S0, S1, nsteps, step0, st);
+    case FAM_SC26_SHELL: return launch_persistent<FAM_SC26_SHELL>(sp, a, S0, S1, nsteps, step0, st);
     case FAM_SC32_ISO: return launch_persistent<FAM_SC32_ISO>(sp, a, S0, S1, nsteps, step0, st);
     default: return launch_persistent<FAM_BCC4>(sp, a, S0, S1, nsteps, step0, st);
   }
@@ -1486,6 +1669,7 @@ cudaError_t stencil_batch_step(StencilBatch *b, const double *const *S_in, doubl
     case FAM_SC6_TEN: return launch_batch<FAM_SC6_TEN>(*b, a, step, st);
     case FAM_SC26_ISO: return launch_batch<FAM_SC26_ISO>(*b, a, step, st);
     case FAM_SC26_TEN: return launch_batch<FAM_SC26_TEN>(*b, a, step, st);
+    case FAM_SC26_SHELL: return launch_batch<FAM_SC26_SHELL>(*b, a, step, st);
     case FAM_SC32_ISO: return launch_batch<FAM_SC32_ISO>(*b, a, step, st);
     default: return launch_batch<FAM_BCC4>(*b, a, step, st);
   }
@@ -1494,22 +1678,14 @@ cudaError_t stencil_batch_step(StencilBatch *b, const double *const *S_in, doubl
 cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                               cudaStream_t st) {
   const StencilPlan &sp = *c->stencil;
-  StencilArgs a = sp.base;
-  a.g = (float)h.g;
-  a.alpha = (float)h.alpha;
-  a.dt = (float)h.dt;
-  a.hdt = (float)(0.5 * h.dt);
-  a.thermal = h.thermal;
-  for (int s = 0; s < c->lat.nsub && s < 2; ++s) a.sigma[s] = (float)h.sigma[s];
-  a.seed = h.seed;
-  a.replica = h.replica;
-  a.step = step;
+  const StencilArgs a = heun_args(c, h, step);
   if (sp.scheme == SX_STENCIL_TWO_PASS) {
     switch (sp.family) {
       case FAM_SC6_ISO: return launch_heun2<FAM_SC6_ISO>(sp, a, src, dst, st);
       case FAM_SC6_TEN: return launch_heun2<FAM_SC6_TEN>(sp, a, src, dst, st);
       case FAM_SC26_ISO: return launch_heun2<FAM_SC26_ISO>(sp, a, src, dst, st);
       case FAM_SC26_TEN: return launch_heun2<FAM_SC26_TEN>(sp, a, src, dst, st);
+      case FAM_SC26_SHELL: return launch_heun2<FAM_SC26_SHELL>(sp, a, src, dst, st);
       case FAM_SC32_ISO: return launch_heun2<FAM_SC32_ISO>(sp, a, src, dst, st);
       default: return launch_heun2<FAM_BCC4>(sp, a, src, dst, st);
     }
@@ -1519,6 +1695,7 @@ cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, c
     case FAM_SC6_TEN: return launch_heun<FAM_SC6_TEN>(sp, a, src, dst, st);
     case FAM_SC26_ISO: return launch_heun<FAM_SC26_ISO>(sp, a, src, dst, st);
     case FAM_SC26_TEN: return launch_heun<FAM_SC26_TEN>(sp, a, src, dst, st);
+    case FAM_SC26_SHELL: return launch_heun<FAM_SC26_SHELL>(sp, a, src, dst, st);
     case FAM_SC32_ISO: return launch_heun<FAM_SC32_ISO>(sp, a, src, dst, st);
     default: return launch_heun<FAM_BCC4>(sp, a, src, dst, st);
   }

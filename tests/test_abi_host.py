@@ -64,7 +64,7 @@ def test_hamiltonian_argument_checks():
                 bad()
             assert e.value.code == sx.SX_ERR_ARG
         # device calls before a plan are refused without touching the GPU
-        assert sx.lib().sx_field(c, None, None, None) == sx.SX_ERR_STATE
+        assert sx.lib().sx_field(c, None, None, sx.SX_PREC_FP64, None) == sx.SX_ERR_STATE
         assert sx.lib().sx_energy(c, None, None, None) == sx.SX_ERR_STATE
         # unsupported combinations are refused before any CUDA call
         with pytest.raises(sx.SxError) as e:

@@ -1,0 +1,110 @@
+"""Numeric-error reporting (SX_ERR_NUMERIC) through the C ABI.
+
+A host-made spin field with one non-finite or zero-length site is an ordinary
+input, not a device fault: the state update flags it in the context's status
+word, the torque and energy reductions propagate NaN instead of skipping it,
+and no call reports convergence on such a state."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2605_26016_gb300 as sx
+from workloads import nlerp_chain, random_spins, uniform_spins
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_26016_gb300.build import build
+    build()
+
+
+N = (12, 10, 9)
+
+
+def _bad_spins(nsub, kind, site=37):
+    S = random_spins(nsub, N, 5).reshape(3, -1)
+    if kind == "nan":
+        S[1, site] = math.nan
+    elif kind == "inf":
+        S[0, site] = math.inf
+    else:
+        S[:, site] = 0.0
+    return torch.from_numpy(S.reshape(3, nsub, N[2], N[1], N[0]).copy()).cuda()
+
+
+def _expect_numeric(fn, *a, **kw):
+    with pytest.raises(sx.SxError) as e:
+        fn(*a, **kw)
+    assert e.value.code == sx.SX_ERR_NUMERIC, str(e.value)
+
+
+CASES = [("sc_j123_dmi", "stencil", "fp32", "two_pass"), ("sc_j123_dmi", "stencil", "fp32", "fused"),
+         ("bcc_4shell", "stencil", "fp32", "two_pass"), ("bcc_4shell", "gather", "fp32", None),
+         ("bcc_4shell", "gather", "fp64", None)]
+
+
+@pytest.mark.parametrize("name,backend,prec,scheme", CASES)
+@pytest.mark.parametrize("kind", ["nan", "inf", "zero"])
+def test_heun_step_flags_bad_site(name, backend, prec, scheme, kind):
+    s, w = sx.system_from_workload(name, N)
+    if scheme:
+        sx.sx_set_stencil_scheme(s.ctx, scheme)
+    s.plan(backend, prec)
+    S = _bad_spins(s.nsub, kind)
+    s.heun(S, torch.empty_like(S), dt=w["dt"], alpha=w["alpha"], T=w["T"], seed=3, nsteps=2)  # asynchronous: no error
+    _expect_numeric(sx.sx_device_status, s.ctx)
+    sx.sx_device_status(s.ctx)  # reading the status clears it
+    good = torch.from_numpy(random_spins(s.nsub, N, 6)).cuda()
+    s.heun(good, torch.empty_like(good), dt=w["dt"], alpha=w["alpha"], T=w["T"], seed=3, nsteps=2)
+    sx.sx_device_status(s.ctx)
+    n = good.view(3, -1).pow(2).sum(0).sqrt()
+    assert (n - 1).abs().max().item() < 1e-13
+
+
+def test_host_entry_reports_bad_site():
+    s, w = sx.system_from_workload("sc_j123_dmi", N)
+    s.plan("stencil", "fp32")
+    Sh = _bad_spins(1, "nan").cpu()
+    _expect_numeric(s.heun_host, Sh, dt=w["dt"], alpha=w["alpha"], T=w["T"], seed=3, nsteps=1)
+
+
+@pytest.mark.parametrize("backend,prec", [("stencil", "fp32"), ("gather", "fp64")])
+def test_torque_and_energy_propagate_nan(backend, prec):
+    s, w = sx.system_from_workload("sc_j123_dmi", N)
+    s.plan(backend, prec)
+    S = _bad_spins(1, "nan")
+    _expect_numeric(s.torque_max, S)
+    _expect_numeric(s.energy, S)
+    good = torch.from_numpy(random_spins(1, N, 7)).cuda()
+    b = s.field(good)
+    b.view(3, -1)[2, 101] = math.nan
+    _expect_numeric(sx.sx_torque_max_noalloc, good, b, s.nsite)
+    assert s.torque_max(good) > 0.0
+
+
+@pytest.mark.parametrize("method", ["vp", "damped_llg"])
+def test_minimise_does_not_converge_on_nan(method):
+    s, w = sx.system_from_workload("sc_j123_dmi", N)
+    s.plan("stencil", "fp32")
+    S = _bad_spins(1, "nan")
+    # a huge tolerance would be met at once if the NaN site read as zero torque
+    _expect_numeric(s.minimise, S, method=method, dt=0.05, tol=1e30, max_iter=20, check_every=5)
+
+
+@pytest.mark.parametrize("method,optimizer", [("gneb", "steepest"), ("ci_gneb", "vp"), ("string", "steepest")])
+def test_path_step_does_not_converge_on_nan(method, optimizer):
+    n = (10, 9, 8)
+    s, w = sx.system_from_workload("sc_4shell", n)
+    s.plan("stencil", "fp32")
+    A = uniform_spins(1, n, [0, 0, 1.0])
+    B = random_spins(1, n, 3)
+    chain = nlerp_chain(A, B, 6, jitter=0.02, seed=1)
+    chain[3].reshape(3, -1)[0, 17] = math.nan
+    X = torch.from_numpy(np.ascontiguousarray(chain)).cuda()
+    _expect_numeric(s.path, X, method=method, optimizer=optimizer, dt=0.01, tol=1e30, max_iter=10, check_every=1)

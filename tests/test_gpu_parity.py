@@ -123,6 +123,23 @@ def test_field_energy_torque(backend, prec, case):
     assert abs(tq - tq_ref) <= TOL_FIELD[prec] * max(np.sqrt((ref.reshape(3, -1) ** 2).sum(0)).max(), 1.0) * 4
 
 
+@pytest.mark.parametrize("backend,prec", PATHS)
+@pytest.mark.parametrize("case", [0, 2, 3, 5])
+def test_field_fp32_output(backend, prec, case):
+    # out_prec = FP32: the FP64 output rounded to FP32 (the stencil pass writes its FP32 sums, which the FP64
+    # output holds exactly), oracle-checked through the FP64 output above
+    _skip_unsupported(backend, case)
+    name, n, pbc, extra = CASES[case]
+    s, m, w = pair(name, n, pbc, extra)
+    s.plan(backend, prec)
+    Sd = dev(random_spins(s.nsub, n, 300 + case))
+    b64 = s.field(Sd)
+    b32 = s.field(Sd, dtype=torch.float32)
+    torch.cuda.synchronize()
+    assert b32.dtype == torch.float32
+    assert torch.equal(b32, b64.float())
+
+
 # ---------------------------------------------------------------- Heun
 
 @pytest.mark.parametrize("backend,prec", PATHS)

@@ -35,6 +35,19 @@ def test_noalloc_torque_matches_regular_entry(name, n, backend):
         assert abs(got - ref) <= 1e-12 * ref, (call, got, ref)
 
 
+@pytest.mark.parametrize("nsite", [1, 255, 256, 257])
+def test_noalloc_single_block_lattices(nsite):
+    # one block (nsite < 256: most threads see no site, the final pass reads one slot) and its edges,
+    # against max |S x b| formed on the host; two calls in a row
+    rng = np.random.default_rng(nsite)
+    for call in range(2):
+        S = rng.standard_normal((3, nsite))
+        b = rng.standard_normal((3, nsite)) * (call + 1)
+        ref = np.sqrt((np.cross(S.T, b.T) ** 2).sum(1)).max()
+        got = sx.sx_torque_max_noalloc(torch.from_numpy(S).cuda(), torch.from_numpy(b).cuda(), nsite)
+        assert abs(got - ref) <= 1e-14 * ref, (nsite, call, got, ref)
+
+
 def test_noalloc_rejects_bad_sizes():
     buf = torch.zeros(6, dtype=torch.float64, device="cuda")
     S, b = sx.ctypes.c_void_p(buf.data_ptr()), sx.ctypes.c_void_p(buf.data_ptr() + 24)
