@@ -359,12 +359,15 @@ __device__ __forceinline__ void shift_acc(Acc3 (&acc)[F::NSUB][2 * F::R + 1]) {
   }
 }
 
-// In-plane part of the global index of the load-region sites this thread stages
-// (x and y wrapped once here; the plane term is added per z step).
+// Site index (within one component array; the stencil backend requires nsite < 2^32) of the
+// load-region sites this thread stages, without the plane term, which is added per z step; x and
+// y are wrapped once here.  A site outside an open face gets index 0 (a valid address that the
+// zero-filling copy does not read).
 template <int NLOAD, int NT, int SN, int LX, int LY, class GEO>
-__device__ __forceinline__ void load_offsets(const GEO &p, int xs, int ys, int tid, long long (&off)[NLOAD],
+__device__ __forceinline__ void load_offsets(const GEO &p, int xs, int ys, int tid, uint32_t (&off)[NLOAD],
                                              unsigned &okmask) {
   okmask = 0u;
+  const uint32_t subvol = (uint32_t)p.nz * (uint32_t)p.ny * (uint32_t)p.nx;
 #pragma unroll
   for (int j = 0; j < NLOAD; ++j) {
     const int e = tid + j * NT;
@@ -376,7 +379,7 @@ __device__ __forceinline__ void load_offsets(const GEO &p, int xs, int ys, int t
       bool ok = true;
       const int gx = wrap_axis(xs + col, p.nx, p.px, ok);
       const int gy = wrap_axis(ys + row, p.ny, p.py, ok);
-      off[j] = (long long)s * p.nz * p.ny * p.nx + (long long)gy * p.nx + gx;
+      off[j] = (uint32_t)s * subvol + (uint32_t)gy * (uint32_t)p.nx + (uint32_t)gx;
       if (ok) okmask |= 1u << j;
     }
   }
@@ -385,19 +388,20 @@ __device__ __forceinline__ void load_offsets(const GEO &p, int xs, int ys, int t
 // Issue the zero-filling async copies of plane q into the FP64 staging area.
 template <int NLOAD, int NT, int SN, class GEO>
 __device__ __forceinline__ void issue_plane(const GEO &p, const double *__restrict__ S, int q, int tid,
-                                            const long long (&off)[NLOAD], unsigned okmask, double *stage) {
+                                            const uint32_t (&off)[NLOAD], unsigned okmask, double *stage) {
   bool zok = true;
   const int gz = wrap_axis(q, p.nz, p.pz, zok);
-  const long long zoff = (long long)gz * p.ny * p.nx;
+  const uint32_t zoff = (uint32_t)gz * (uint32_t)p.ny * (uint32_t)p.nx;
+  const double *S1 = S + p.nsite, *S2 = S + 2 * p.nsite;
 #pragma unroll
   for (int j = 0; j < NLOAD; ++j) {
     const int e = tid + j * NT;
     if (e < SN) {
       const bool ok = zok && ((okmask >> j) & 1u);
-      const double *src = ok ? S + off[j] + zoff : S;
-      cp_async8(smem_addr(stage + e), src, ok);
-      cp_async8(smem_addr(stage + SN + e), ok ? src + p.nsite : S, ok);
-      cp_async8(smem_addr(stage + 2 * SN + e), ok ? src + 2 * p.nsite : S, ok);
+      const uint32_t i = off[j] + zoff;
+      cp_async8(smem_addr(stage + e), S + i, ok);
+      cp_async8(smem_addr(stage + SN + e), S1 + i, ok);
+      cp_async8(smem_addr(stage + 2 * SN + e), S2 + i, ok);
     }
   }
 }
@@ -453,7 +457,9 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINBF)
   bool xok = true;
   const int wx = wrap_axis(cx, p.nx, p.px, xok);
   const bool xin = tx >= R && tx < 32 - R && cx < p.nx;
-  const long long plane = (long long)p.ny * p.nx, subvol = (long long)p.nz * plane;
+  const uint32_t plane = (uint32_t)p.ny * (uint32_t)p.nx, subvol = (uint32_t)p.nz * plane;
+  const double *Sin1 = Sin + p.nsite, *Sin2 = Sin + 2 * p.nsite;
+  double *Sout1 = Sout + p.nsite, *Sout2 = Sout + 2 * p.nsite;
   bool col_ok[RY], rin[RY], inner[RY];
   int wy[RY], cy[RY], ii[RY];
 #pragma unroll
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINBF)
     ii[j] = (ry0 + j - R) * g::TX + (tx - R);      // interior index (valid when inner)
   }
 
-  long long off[g::NLOAD];
+  uint32_t off[g::NLOAD];
   unsigned okmask;
   load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(p, x0 - 2 * R, y0 - 2 * R, tid, off, okmask);
 
@@ -494,10 +500,10 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINBF)
         if (inner[j]) {
 #pragma unroll
           for (int a = 0; a < NS; ++a) {
-            const double *src = Sin + a * subvol + c * plane + (long long)cy[j] * p.nx + cx;
-            cp_async8(smem_addr(s64 + (a * 3 + 0) * g::NI + ii[j]), src, true);
-            cp_async8(smem_addr(s64 + (a * 3 + 1) * g::NI + ii[j]), src + p.nsite, true);
-            cp_async8(smem_addr(s64 + (a * 3 + 2) * g::NI + ii[j]), src + 2 * p.nsite, true);
+            const uint32_t i = a * subvol + (uint32_t)c * plane + (uint32_t)cy[j] * (uint32_t)p.nx + (uint32_t)cx;
+            cp_async8(smem_addr(s64 + (a * 3 + 0) * g::NI + ii[j]), Sin + i, true);
+            cp_async8(smem_addr(s64 + (a * 3 + 1) * g::NI + ii[j]), Sin1 + i, true);
+            cp_async8(smem_addr(s64 + (a * 3 + 2) * g::NI + ii[j]), Sin2 + i, true);
           }
         }
       }
@@ -535,7 +541,7 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINBF)
             float e0 = 0.f, e1 = 0.f, e2 = 0.f;
             if (p.thermal) {
               const unsigned long long site =
-                  (unsigned long long)(a * subvol + wz * plane + (long long)wy[j] * p.nx + wx);
+                  a * subvol + (uint32_t)wz * plane + (uint32_t)wy[j] * (uint32_t)p.nx + (uint32_t)wx;
               normals3(p.keys, p.replica, site, p.step, e0, e1, e2);
             }
             const float sg = p.sigma[a], im = p.inv_mm[a];
@@ -597,10 +603,10 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINBF)
                                   s64[(a * 3 + 2) * g::NI + ii[j]]};
             double o[3];
             report_numeric(p.status, renormalise64(S0, d, o));
-            const long long i = a * subvol + c * plane + (long long)cy[j] * p.nx + cx;
+            const uint32_t i = a * subvol + (uint32_t)c * plane + (uint32_t)cy[j] * (uint32_t)p.nx + (uint32_t)cx;
             Sout[i] = o[0];
-            Sout[p.nsite + i] = o[1];
-            Sout[2 * p.nsite + i] = o[2];
+            Sout1[i] = o[1];
+            Sout2[i] = o[2];
           }
         }
       }
@@ -653,29 +659,28 @@ struct PassIO {
                      // [sched[k].x, sched[k].x + sched[k].y) of u = column * nz + z; null: the grid tiles
 };
 
+__device__ __forceinline__ void cp_async4(unsigned dst, const void *src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+
 // FP32 planes of S~ straight into the float4 ring (4-byte zero-filling copies)
 template <int NLOAD, int NT, int SN, class GEO>
 __device__ __forceinline__ void issue_plane_f32(const GEO &p, const float *__restrict__ S, int q, int tid,
-                                                const long long (&off)[NLOAD], unsigned okmask, float4 *dst) {
+                                                const uint32_t (&off)[NLOAD], unsigned okmask, float4 *dst) {
   bool zok = true;
   const int gz = wrap_axis(q, p.nz, p.pz, zok);
-  const long long zoff = (long long)gz * p.ny * p.nx;
+  const uint32_t zoff = (uint32_t)gz * (uint32_t)p.ny * (uint32_t)p.nx;
+  const float *S1 = S + p.nsite, *S2 = S + 2 * p.nsite;
 #pragma unroll
   for (int j = 0; j < NLOAD; ++j) {
     const int e = tid + j * NT;
     if (e < SN) {
       const bool ok = zok && ((okmask >> j) & 1u);
-      const float *src = ok ? S + off[j] + zoff : S;
-      float *d = reinterpret_cast<float *>(dst + e);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(d)), "l"(src),
-                   "r"(ok ? 4 : 0)
-                   : "memory");
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(d + 1)),
-                   "l"(ok ? src + p.nsite : S), "r"(ok ? 4 : 0)
-                   : "memory");
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(d + 2)),
-                   "l"(ok ? src + 2 * p.nsite : S), "r"(ok ? 4 : 0)
-                   : "memory");
+      const uint32_t i = off[j] + zoff;
+      const unsigned d = smem_addr(dst + e);
+      cp_async4(d, S + i, ok);
+      cp_async4(d + 4, S1 + i, ok);
+      cp_async4(d + 8, S2 + i, ok);
     }
   }
 }
@@ -698,10 +703,12 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
   double *bout = io.b + img * io.istride;
   const int cx = x0 + tx, cy = y0 + ty;
   const bool mine = cx < gg.nx && cy < gg.ny;
-  const long long plane = (long long)gg.ny * gg.nx, subvol = (long long)gg.nz * plane;
+  const uint32_t plane = (uint32_t)gg.ny * (uint32_t)gg.nx, subvol = (uint32_t)gg.nz * plane;
+  const uint32_t icol = (uint32_t)cy * (uint32_t)gg.nx + (uint32_t)cx;  // this thread's column in a plane
+  const long long N = gg.nsite;
   Acc3 acc[NS][2 * R + 1];
   zero_acc<F>(acc);
-  long long off[g::NLOAD];
+  uint32_t off[g::NLOAD];
   unsigned okmask;
   load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(gg, x0 - R, y0 - R, tid, off, okmask);
   const int niter = tzc + 2 * R;
@@ -714,12 +721,12 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
       if (mine && cz < z0 + tzc) {
 #pragma unroll
         for (int a = 0; a < NS; ++a) {
-          const long long i = a * subvol + cz * plane + (long long)cy * gg.nx + cx;
+          const uint32_t i = a * subvol + (uint32_t)cz * plane + icol;
 #pragma unroll
           for (int m = 0; m < 3; ++m) {
-            nS[a][m] = io.S[m * gg.nsite + i];
-            nf[a][m] = io.f0[m * gg.nsite + i];
-            ne[a][m] = p.thermal ? io.eta[m * gg.nsite + i] : 0.0f;
+            nS[a][m] = (io.S + m * N)[i];
+            nf[a][m] = (io.f0 + m * N)[i];
+            ne[a][m] = p.thermal ? (io.eta + m * N)[i] : 0.0f;
           }
         }
       }
@@ -758,17 +765,17 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
         float v[3] = {acc[a][0].xy.x, acc[a][0].xy.y, acc[a][0].z};
         const float4 c4 = cq[(((k - R) % (R + 1)) * NS + a) * g::NT + tid];
         const float s[3] = {c4.x, c4.y, c4.z};
-        const long long i = a * subvol + c * plane + (long long)cy * gg.nx + cx;
+        const uint32_t i = a * subvol + (uint32_t)c * plane + icol;
         if constexpr (MODE == PASS_FIELD) {
           if (onsite) onsite32(p, a, s, v);
           if (io.bf) {
             io.bf[i] = v[0];
-            io.bf[gg.nsite + i] = v[1];
-            io.bf[2 * gg.nsite + i] = v[2];
+            (io.bf + N)[i] = v[1];
+            (io.bf + 2 * N)[i] = v[2];
           } else {
             bout[i] = (double)v[0];
-            bout[gg.nsite + i] = (double)v[1];
-            bout[2 * gg.nsite + i] = (double)v[2];
+            (bout + N)[i] = (double)v[1];
+            (bout + 2 * N)[i] = (double)v[2];
           }
         } else {
           onsite32(p, a, s, v);
@@ -777,8 +784,8 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
             if (p.thermal) {
               normals3(p.keys, gg.replica, (unsigned long long)i, io.step, e0, e1, e2);
               io.eta[i] = e0;
-              io.eta[gg.nsite + i] = e1;
-              io.eta[2 * gg.nsite + i] = e2;
+              (io.eta + N)[i] = e1;
+              (io.eta + 2 * N)[i] = e2;
             }
           } else {
             e0 = ne[a][0];
@@ -795,25 +802,28 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
             float r = rsqrtf(n2);
             r = r * fmaf(-0.5f * n2, r * r, 1.5f);
             io.St_out[i] = x[0] * r;
-            io.St_out[gg.nsite + i] = x[1] * r;
-            io.St_out[2 * gg.nsite + i] = x[2] * r;
+            (io.St_out + N)[i] = x[1] * r;
+            (io.St_out + 2 * N)[i] = x[2] * r;
             io.f0[i] = f[0];
-            io.f0[gg.nsite + i] = f[1];
-            io.f0[2 * gg.nsite + i] = f[2];
+            (io.f0 + N)[i] = f[1];
+            (io.f0 + 2 * N)[i] = f[2];
           } else {
             const float d[3] = {p.hdt * (nf[a][0] + f[0]), p.hdt * (nf[a][1] + f[1]), p.hdt * (nf[a][2] + f[2])};
             double o[3];
             report_numeric(p.status, renormalise64(nS[a], d, o));
             io.Sout[i] = o[0];
-            io.Sout[gg.nsite + i] = o[1];
-            io.Sout[2 * gg.nsite + i] = o[2];
+            (io.Sout + N)[i] = o[1];
+            (io.Sout + 2 * N)[i] = o[2];
           }
         }
       }
       prefetch(c + 1);
     }
     shift_acc<F>(acc);
-    __syncthreads();
+    // One barrier per plane suffices: the ring slot that iteration k + 1 refills (FP32 conversion of
+    // FIELD / PRED, or the S~ copies of CORR issued after that iteration's barrier) was last read in
+    // iteration k - 1, which every thread finished before arriving at iteration k's barrier; the
+    // staging area and the centre ring are written and read by one thread only.
   }
   cp_wait<0>();
 }
@@ -1300,6 +1310,8 @@ int field_occupancy() {
 int stencil_plan(sx_ctx *c) {
   if (c->prec != SX_PREC_FP32)
     return set_error(SX_ERR_UNSUPPORTED, "the stencil backend computes the field in FP32 (use gather for FP64)");
+  if (c->geo.nsite >= (1LL << 32))
+    return set_error(SX_ERR_UNSUPPORTED, "the stencil backend indexes sites with 32 bits: nsite must be below 2^32");
   StencilPlan *sp = new (std::nothrow) StencilPlan();
   if (!sp) return set_error(SX_ERR_OOM, "host allocation failed");
   StencilArgs &a = sp->base;
