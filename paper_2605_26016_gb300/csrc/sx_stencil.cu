@@ -122,22 +122,22 @@ template <int ID>
 struct Family;
 template <>
 struct Family<FAM_SC6_ISO> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0, TYP = 16;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC6{1});
 };
 template <>
 struct Family<FAM_SC6_TEN> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 6, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0, TYP = 16;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC6{2});
 };
 template <>
 struct Family<FAM_SC26_ISO> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0, TYP = 16;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{1});
 };
 template <>
 struct Family<FAM_SC26_TEN> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 0, TYP = 16;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{2});
 };
 // simple cubic 3x3x3 cube with one exchange constant per distance shell (100), (110), (111) and, on
@@ -147,17 +147,17 @@ struct Family<FAM_SC26_TEN> {
 // J1 E + J2 K (+ DMI) for the outputs in the plane -- about half the arithmetic of 26 separate taps.
 template <>
 struct Family<FAM_SC26_SHELL> {
-  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 1;
+  static constexpr int NSUB = 1, R = 1, BY = 16, NTAP = 26, MINB = 2, RYF = 2, TYF = 8, MINBF = 2, SHELL = 1, TYP = 16;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 1, KeepSC26{1});
 };
 template <>
 struct Family<FAM_SC32_ISO> {
-  static constexpr int NSUB = 1, R = 2, BY = 16, NTAP = 32, MINB = 1, RYF = 1, TYF = 16, MINBF = 1, SHELL = 0;
+  static constexpr int NSUB = 1, R = 2, BY = 16, NTAP = 32, MINB = 1, RYF = 1, TYF = 16, MINBF = 1, SHELL = 0, TYP = 16;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(1, 2, KeepSC32{});
 };
 template <>
 struct Family<FAM_BCC4> {
-  static constexpr int NSUB = 2, R = 2, BY = 16, NTAP = 100, MINB = 1, RYF = 1, TYF = 16, MINBF = 1, SHELL = 0;
+  static constexpr int NSUB = 2, R = 2, BY = 16, NTAP = 100, MINB = 1, RYF = 1, TYF = 16, MINBF = 1, SHELL = 0, TYP = 16;
   static constexpr TapArr<NTAP> L = make_taps<NTAP>(2, 2, KeepBCC4{});
 };
 
@@ -619,14 +619,17 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINBF)
 
 // ------------------------------------------------------------------ field only
 
+// Pass-kernel geometry: a CTA of 32 x TYT threads owns a 32 x BY column tile, each thread RY = BY / TYT
+// adjacent rows of one column.
 template <class F>
 struct GF {
-  static constexpr int NS = F::NSUB, R = F::R, BY = F::BY;
-  static constexpr int NT = 32 * BY, LX = 32 + 2 * R, LY = BY + 2 * R;
+  static constexpr int NS = F::NSUB, R = F::R, BY = F::BY, TYT = F::TYP, RY = BY / TYT;
+  static_assert(RY * TYT == BY, "the tile rows must split evenly over the thread rows");
+  static constexpr int NT = 32 * TYT, LX = 32 + 2 * R, LY = BY + 2 * R;
   static constexpr int SN = NS * LY * LX;
   static constexpr int NLOAD = (SN + NT - 1) / NT;
   static constexpr size_t OFF_CQ = 2 * (size_t)SN * 16;
-  static constexpr size_t OFF_STAGE = OFF_CQ + (size_t)(R + 1) * NS * NT * 16;
+  static constexpr size_t OFF_STAGE = OFF_CQ + (size_t)(R + 1) * NS * RY * NT * 16;
   static constexpr size_t SMEM = OFF_STAGE + (size_t)3 * SN * 8;
 };
 
@@ -694,39 +697,51 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
                                              unsigned char *smem_raw, int img, int x0, int y0, int z0, int tzc) {
   using F = Family<FID>;
   using g = GF<F>;
-  constexpr int NS = F::NSUB, R = F::R;
+  constexpr int NS = F::NSUB, R = F::R, RY = g::RY;
   float4 *sn = reinterpret_cast<float4 *>(smem_raw);                    // [2][SN]
-  float4 *cq = reinterpret_cast<float4 *>(smem_raw + g::OFF_CQ);        // [R+1][NS][NT] centre values
+  float4 *cq = reinterpret_cast<float4 *>(smem_raw + g::OFF_CQ);        // [R+1][NS][RY][NT] centre values
   double *stage = reinterpret_cast<double *>(smem_raw + g::OFF_STAGE);  // [3][SN] (FP64 input)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int ry0 = ty * RY;  // first tile row of this thread
   const double *Sin = io.S + img * io.istride;
   double *bout = io.b + img * io.istride;
-  const int cx = x0 + tx, cy = y0 + ty;
-  const bool mine = cx < gg.nx && cy < gg.ny;
+  const int cx = x0 + tx;
   const uint32_t plane = (uint32_t)gg.ny * (uint32_t)gg.nx, subvol = (uint32_t)gg.nz * plane;
-  const uint32_t icol = (uint32_t)cy * (uint32_t)gg.nx + (uint32_t)cx;  // this thread's column in a plane
+  bool mine[RY];
+  uint32_t icol[RY];  // this thread's columns in a plane
+#pragma unroll
+  for (int j = 0; j < RY; ++j) {
+    const int cy = y0 + ry0 + j;
+    mine[j] = cx < gg.nx && cy < gg.ny;
+    icol[j] = (uint32_t)cy * (uint32_t)gg.nx + (uint32_t)cx;
+  }
   const long long N = gg.nsite;
-  Acc3 acc[NS][2 * R + 1];
-  zero_acc<F>(acc);
+  Acc3 acc[RY][NS][2 * R + 1];
+#pragma unroll
+  for (int j = 0; j < RY; ++j) zero_acc<F>(acc[j]);
   uint32_t off[g::NLOAD];
   unsigned okmask;
   load_offsets<g::NLOAD, g::NT, g::SN, g::LX, g::LY>(gg, x0 - R, y0 - R, tid, off, okmask);
   const int niter = tzc + 2 * R;
   // corrector: S^n and f0 of the next output plane, loaded one plane ahead so the
   // global-load latency hides behind a plane of field work
-  double nS[NS][3];
-  float nf[NS][3], ne[NS][3];
+  double nS[RY][NS][3];
+  float nf[RY][NS][3], ne[RY][NS][3];
   auto prefetch = [&](int cz) {
     if constexpr (MODE == PASS_CORR) {
-      if (mine && cz < z0 + tzc) {
+      if (cz < z0 + tzc) {
 #pragma unroll
-        for (int a = 0; a < NS; ++a) {
-          const uint32_t i = a * subvol + (uint32_t)cz * plane + icol;
+        for (int j = 0; j < RY; ++j) {
+          if (!mine[j]) continue;
 #pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            nS[a][m] = (io.S + m * N)[i];
-            nf[a][m] = (io.f0 + m * N)[i];
-            ne[a][m] = p.thermal ? (io.eta + m * N)[i] : 0.0f;
+          for (int a = 0; a < NS; ++a) {
+            const uint32_t i = a * subvol + (uint32_t)cz * plane + icol[j];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+              nS[j][a][m] = (io.S + m * N)[i];
+              nf[j][a][m] = (io.f0 + m * N)[i];
+              ne[j][a][m] = p.thermal ? (io.eta + m * N)[i] : 0.0f;
+            }
           }
         }
       }
@@ -752,74 +767,84 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
     }
     cp_commit();
     if constexpr (MODE != PASS_CORR) __syncthreads();
-    const float4 *base = buf + (ty + R) * g::LX + (tx + R);
-    push_plane<F>(p, base, g::LX * g::LY, g::LX, acc);
+    const float4 *base = buf + (ry0 + R) * g::LX + (tx + R);
+#pragma unroll
+    for (int j = 0; j < RY; ++j) push_plane<F>(p, base + j * g::LX, g::LX * g::LY, g::LX, acc[j]);
     // keep this plane's centre values for the epilogue R planes later
 #pragma unroll
-    for (int a = 0; a < NS; ++a) cq[((k % (R + 1)) * NS + a) * g::NT + tid] = base[a * g::LX * g::LY];
+    for (int j = 0; j < RY; ++j)
+#pragma unroll
+      for (int a = 0; a < NS; ++a)
+        cq[(((k % (R + 1)) * NS + a) * RY + j) * g::NT + tid] = base[j * g::LX + a * g::LX * g::LY];
     const int kc = k - 2 * R;
-    if (mine && kc >= 0) {
+    if (kc >= 0) {
       const int c = z0 + kc;
 #pragma unroll
-      for (int a = 0; a < NS; ++a) {
-        float v[3] = {acc[a][0].xy.x, acc[a][0].xy.y, acc[a][0].z};
-        const float4 c4 = cq[(((k - R) % (R + 1)) * NS + a) * g::NT + tid];
-        const float s[3] = {c4.x, c4.y, c4.z};
-        const uint32_t i = a * subvol + (uint32_t)c * plane + icol;
-        if constexpr (MODE == PASS_FIELD) {
-          if (onsite) onsite32(p, a, s, v);
-          if (io.bf) {
-            io.bf[i] = v[0];
-            (io.bf + N)[i] = v[1];
-            (io.bf + 2 * N)[i] = v[2];
-          } else {
-            bout[i] = (double)v[0];
-            (bout + N)[i] = (double)v[1];
-            (bout + 2 * N)[i] = (double)v[2];
-          }
-        } else {
-          onsite32(p, a, s, v);
-          float e0 = 0.f, e1 = 0.f, e2 = 0.f;
-          if constexpr (MODE == PASS_PRED) {
-            if (p.thermal) {
-              normals3(p.keys, gg.replica, (unsigned long long)i, io.step, e0, e1, e2);
-              io.eta[i] = e0;
-              (io.eta + N)[i] = e1;
-              (io.eta + 2 * N)[i] = e2;
+      for (int j = 0; j < RY; ++j) {
+        if (!mine[j]) continue;
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+          float v[3] = {acc[j][a][0].xy.x, acc[j][a][0].xy.y, acc[j][a][0].z};
+          const float4 c4 = cq[((((k - R) % (R + 1)) * NS + a) * RY + j) * g::NT + tid];
+          const float s[3] = {c4.x, c4.y, c4.z};
+          const uint32_t i = a * subvol + (uint32_t)c * plane + icol[j];
+          if constexpr (MODE == PASS_FIELD) {
+            if (onsite) onsite32(p, a, s, v);
+            if (io.bf) {
+              io.bf[i] = v[0];
+              (io.bf + N)[i] = v[1];
+              (io.bf + 2 * N)[i] = v[2];
+            } else {
+              bout[i] = (double)v[0];
+              (bout + N)[i] = (double)v[1];
+              (bout + 2 * N)[i] = (double)v[2];
             }
           } else {
-            e0 = ne[a][0];
-            e1 = ne[a][1];
-            e2 = ne[a][2];
-          }
-          const float sg = p.sigma[a], im = p.inv_mm[a];
-          const float B[3] = {fmaf(v[0], im, sg * e0), fmaf(v[1], im, sg * e1), fmaf(v[2], im, sg * e2)};
-          float f[3];
-          rhs32(s, B, p.g, p.alpha, f);
-          if constexpr (MODE == PASS_PRED) {
-            const float x[3] = {fmaf(p.dt, f[0], s[0]), fmaf(p.dt, f[1], s[1]), fmaf(p.dt, f[2], s[2])};
-            const float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-            float r = rsqrtf(n2);
-            r = r * fmaf(-0.5f * n2, r * r, 1.5f);
-            io.St_out[i] = x[0] * r;
-            (io.St_out + N)[i] = x[1] * r;
-            (io.St_out + 2 * N)[i] = x[2] * r;
-            io.f0[i] = f[0];
-            (io.f0 + N)[i] = f[1];
-            (io.f0 + 2 * N)[i] = f[2];
-          } else {
-            const float d[3] = {p.hdt * (nf[a][0] + f[0]), p.hdt * (nf[a][1] + f[1]), p.hdt * (nf[a][2] + f[2])};
-            double o[3];
-            report_numeric(p.status, renormalise64(nS[a], d, o));
-            io.Sout[i] = o[0];
-            (io.Sout + N)[i] = o[1];
-            (io.Sout + 2 * N)[i] = o[2];
+            onsite32(p, a, s, v);
+            float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+            if constexpr (MODE == PASS_PRED) {
+              if (p.thermal) {
+                normals3(p.keys, gg.replica, (unsigned long long)i, io.step, e0, e1, e2);
+                io.eta[i] = e0;
+                (io.eta + N)[i] = e1;
+                (io.eta + 2 * N)[i] = e2;
+              }
+            } else {
+              e0 = ne[j][a][0];
+              e1 = ne[j][a][1];
+              e2 = ne[j][a][2];
+            }
+            const float sg = p.sigma[a], im = p.inv_mm[a];
+            const float B[3] = {fmaf(v[0], im, sg * e0), fmaf(v[1], im, sg * e1), fmaf(v[2], im, sg * e2)};
+            float f[3];
+            rhs32(s, B, p.g, p.alpha, f);
+            if constexpr (MODE == PASS_PRED) {
+              const float x[3] = {fmaf(p.dt, f[0], s[0]), fmaf(p.dt, f[1], s[1]), fmaf(p.dt, f[2], s[2])};
+              const float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+              float r = rsqrtf(n2);
+              r = r * fmaf(-0.5f * n2, r * r, 1.5f);
+              io.St_out[i] = x[0] * r;
+              (io.St_out + N)[i] = x[1] * r;
+              (io.St_out + 2 * N)[i] = x[2] * r;
+              io.f0[i] = f[0];
+              (io.f0 + N)[i] = f[1];
+              (io.f0 + 2 * N)[i] = f[2];
+            } else {
+              const float d[3] = {p.hdt * (nf[j][a][0] + f[0]), p.hdt * (nf[j][a][1] + f[1]),
+                                  p.hdt * (nf[j][a][2] + f[2])};
+              double o[3];
+              report_numeric(p.status, renormalise64(nS[j][a], d, o));
+              io.Sout[i] = o[0];
+              (io.Sout + N)[i] = o[1];
+              (io.Sout + 2 * N)[i] = o[2];
+            }
           }
         }
       }
       prefetch(c + 1);
     }
-    shift_acc<F>(acc);
+#pragma unroll
+    for (int j = 0; j < RY; ++j) shift_acc<F>(acc[j]);
     // One barrier per plane suffices: the ring slot that iteration k + 1 refills (FP32 conversion of
     // FIELD / PRED, or the S~ copies of CORR issued after that iteration's barrier) was last read in
     // iteration k - 1, which every thread finished before arriving at iteration k's barrier; the
@@ -1124,7 +1149,7 @@ cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &base, int ons
   io.istride = stride;
   if ((long long)io.nzc * count > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc * count);
-  k_stencil_pass<FID, PASS_FIELD><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, onsite, io);
+  k_stencil_pass<FID, PASS_FIELD><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, onsite, io);
   return cudaGetLastError();
 }
 
@@ -1147,8 +1172,8 @@ cudaError_t launch_heun2(const StencilPlan &sp, StencilArgs a, const double *src
   io.nzc = (a.nz + a.tz - 1) / a.tz;
   const dim3 grid = sp.d_sched ? dim3(sp.nsched)
                                : dim3((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc);
-  k_stencil_pass<FID, PASS_PRED><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, 1, io);
-  k_stencil_pass<FID, PASS_CORR><<<grid, dim3(32, Family<FID>::BY), g::SMEM, st>>>(a, 1, io);
+  k_stencil_pass<FID, PASS_PRED><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io);
+  k_stencil_pass<FID, PASS_CORR><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io);
   return cudaGetLastError();
 }
 
@@ -1170,7 +1195,7 @@ cudaError_t launch_persistent(const StencilPlan &sp, const StencilArgs &a, doubl
   cudaError_t e = cudaMemsetAsync(sp.d_bar, 0, 2 * sizeof(unsigned), st);  // count, gen (err is sticky)
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel((const void *)k_heun_persistent<FID>, dim3(sp.nsched),
-                                     dim3(32, Family<FID>::BY), args, g::SMEM, st);
+                                     dim3(32, GF<Family<FID>>::TYT), args, g::SMEM, st);
 }
 
 // Balanced schedule of a one-image pass over `slots` resident CTAs: the column-plane
@@ -1594,7 +1619,7 @@ bool same_couplings(const StencilArgs &a, const StencilArgs &b) {
 template <int FID>
 cudaError_t launch_batch(const StencilBatch &b, const StencilArgs &a, unsigned long long step, cudaStream_t st) {
   using g = GF<Family<FID>>;
-  const dim3 grid(b.nsched), block(32, Family<FID>::BY);
+  const dim3 grid(b.nsched), block(32, GF<Family<FID>>::TYT);
   k_batch_pass<FID, PASS_PRED><<<grid, block, g::SMEM, st>>>(a, b.d_reps, b.nrep, b.d_sched, step);
   k_batch_pass<FID, PASS_CORR><<<grid, block, g::SMEM, st>>>(a, b.d_reps, b.nrep, b.d_sched, step);
   return cudaGetLastError();
