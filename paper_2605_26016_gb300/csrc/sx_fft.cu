@@ -47,15 +47,19 @@ struct CxT<double> {
 
 struct FftPlan {
   int prec;  // SX_PREC_FP32 or SX_PREC_FP64 (arithmetic of transforms and fields)
-  int n[3], logn[3], W[3];
-  int nsub, nch, nzf, noff;
+  int n[3], logn[3];
+  int nsub, nch, noff;
   long long N;   // cells
-  void *Z;       // [nzf][N] complex: packed spin channels, then packed fields
-  void *Md;      // [nch][N] real: diagonal of M(q)
-  void *Mo;      // [noff][N] complex: upper triangle of M(q)
-  void *tw[3];   // per axis: n/2 complex twiddles exp(-2 pi i k / n)
-  void *St, *F0, *Bf;  // Heun: predictor state, f0, field buffer; [nch][N] real each
-  void *Th;            // Heun: thermal field of the step, [nch][N] real
+  long long Nh;  // half-spectrum points (nx/2 + 1) ny nz
+  void *Z;       // [nch][Nh] complex: half spectra of the channels
+  void *Md;      // [nch][Nh] real: diagonal of M(q)
+  void *Mo;      // [noff][Nh] complex: upper triangle of M(q)
+  void *tw[3];   // per axis: n/2 complex twiddles exp(-2 pi i k / n) (full-length transforms)
+  void *twm;     // nx/4 twiddles of the nx/2-point transform of the x pass
+  void *twr;     // nx/2 + 1 split factors exp(-2 pi i q / nx) of the real-to-complex x pass
+  void *St, *F0;  // Heun: predictor state and f0, [nch][N] real each
+  void *Th;       // Heun: thermal field of the step, [nch][N] real
+  int wx, wy, wz, wc;  // lines per CTA of the x (r2c), y, z (with the kernel multiply) and x (c2r) passes
 };
 
 namespace {
@@ -224,54 +228,126 @@ __global__ void __launch_bounds__(kFftThreads)
   }
 }
 
-// real channels [nch][N] -> packed complex fields [nzf][N]
-template <typename Tin, typename R>
-__global__ void k_pack(const Tin *__restrict__ S, typename CxT<R>::T *__restrict__ Z, int nch, long long N) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int nzf = (nch + 1) / 2;
-  for (int m = 0; m < nzf; ++m) {
-    typename CxT<R>::T z;
-    z.x = cvt<R>(S[(long long)(2 * m) * N + i]);
-    z.y = (2 * m + 1 < nch) ? cvt<R>(S[(long long)(2 * m + 1) * N + i]) : (R)0;
-    Z[m * N + i] = z;
+// ---------------------------------------------------------------- real-to-complex pipeline
+//
+// The spin channels and fields are real, so only the half spectrum qx = 0 .. nx/2 (nh = nx/2 + 1
+// values) is kept, one complex spectrum per real channel k = c * nsub + a:
+//   Zh[k * Nh + (qz * ny + qy) * nh + qx],  Nh = nh * ny * nz.
+// One field evaluation is five passes over it:
+//   k_xr2c   x lines of every channel, real to complex: the nx/2-point complex transform of the
+//            (even, odd) sample pairs, then its split into the half spectrum;
+//   k_hpass  y lines, forward;
+//   k_zkz    z lines: forward transform, b^(q) = M(q) s^(q) over the channels, inverse transform,
+//            all in shared memory;
+//   k_hpass  y lines, inverse;
+//   k_xc2r   x lines of every channel, complex to real (times 1/N), followed on the cells of those
+//            lines by the field output, the Heun predictor or the Heun corrector.
+
+struct FftGeo {
+  int nx, ny, nz, nh, m, logm, logx;
+  long long N, Nh;
+};
+
+__device__ __forceinline__ int brev_n(int i, int logn) {
+  return logn ? (int)(__brev((unsigned)i) >> (32 - logn)) : 0;
+}
+
+// every radix-2 DIT stage of nlines staged lines of length 2^logn (bit-reversed input, natural output)
+template <typename R>
+__device__ __forceinline__ void fft_stages(typename CxT<R>::T *sm, int pitch, int nlines, int logn,
+                                           const typename CxT<R>::T *__restrict__ tw, int inverse) {
+  for (int s = 0; s < logn;) {
+    const int rem = logn - s;
+    if (rem >= 3) {
+      dit_stages<R, 3>(sm, pitch, nlines, logn, s, tw, inverse);
+      s += 3;
+    } else if (rem == 2) {
+      dit_stages<R, 2>(sm, pitch, nlines, logn, s, tw, inverse);
+      s += 2;
+    } else {
+      dit_stages<R, 1>(sm, pitch, nlines, logn, s, tw, inverse);
+      s += 1;
+    }
+    __syncthreads();
   }
 }
 
-// b^(q) = M(q) S^(q) for every (q, -q) pair; channel spectra are unpacked from
-// the packed fields, the packed spectrum of the (real) field is written back.
-template <typename R, int NCH>
-__global__ void k_kmul(typename CxT<R>::T *__restrict__ Z, const R *__restrict__ Md,
-                       const typename CxT<R>::T *__restrict__ Mo, int nx, int ny, int nz, long long N) {
+// x lines y0 .. y0 + W - 1 of plane z, every channel: real samples src[k][cell] -> half spectrum.
+// z_j = x_2j + i x_2j+1 (j < m = nx/2), Z = FFT_m(z); X_q = E_q + w^q O_q for q = 0 .. m with
+// E_q = (Z_q + conj Z_{m-q}) / 2, O_q = (Z_q - conj Z_{m-q}) / (2i), w = exp(-2 pi i / nx), Z_m = Z_0.
+template <typename R, typename Tin>
+__global__ void __launch_bounds__(kFftThreads)
+    k_xr2c(const Tin *__restrict__ src, typename CxT<R>::T *__restrict__ Zh, FftGeo g, int nch, int W,
+           const typename CxT<R>::T *__restrict__ twm, const typename CxT<R>::T *__restrict__ twr) {
   using C = typename CxT<R>::T;
-  constexpr int NZF = (NCH + 1) / 2;
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= N) return;
-  const int x = (int)(q % nx);
-  const int y = (int)((q / nx) % ny);
-  const int z = (int)(q / ((long long)nx * ny));
-  const long long mq = (long long)((nx - x) & (nx - 1)) + (long long)nx * (((ny - y) & (ny - 1)) +
-                                                                           (long long)ny * ((nz - z) & (nz - 1)));
-  if (mq < q) return;  // the partner thread handles this pair
-  C s[NCH];
-#pragma unroll
-  for (int m = 0; m < NZF; ++m) {
-    const C a = Z[m * N + q], bc = Z[m * N + mq];  // conj of bc is the spectrum at q of conj(field)
-    C u;
-    u.x = (R)0.5 * (a.x + bc.x);
-    u.y = (R)0.5 * (a.y - bc.y);
-    s[2 * m] = u;
-    if (2 * m + 1 < NCH) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C *sm = reinterpret_cast<C *>(smraw);
+  const int m = g.m, logm = g.logm, pitch = fft_pitch(m);
+  const int y0 = blockIdx.x * W, z = blockIdx.y;
+  const int nw = min(W, g.ny - y0);
+  for (int k = 0; k < nch; ++k) {
+    const Tin *in = src + (long long)k * g.N + ((long long)z * g.ny + y0) * g.nx;
+    for (int e = threadIdx.x; e < nw * m; e += kFftThreads) {
+      const int w = e >> logm, j = e & (m - 1);
+      const Tin *pq = in + (long long)w * g.nx + 2 * j;
       C v;
-      v.x = (R)0.5 * (a.y + bc.y);
-      v.y = (R)-0.5 * (a.x - bc.x);
-      s[2 * m + 1] = v;
+      v.x = cvt<R>(pq[0]);
+      v.y = cvt<R>(pq[1]);
+      sm[w * pitch + fft_slot(brev_n(j, logm))] = v;
     }
+    __syncthreads();
+    fft_stages<R>(sm, pitch, nw, logm, twm, 0);
+    C *dst = Zh + (long long)k * g.Nh + ((long long)z * g.ny + y0) * g.nh;
+    for (int e = threadIdx.x; e < nw * (m + 1); e += kFftThreads) {
+      const int w = e / (m + 1), q = e - w * (m + 1);
+      const C a = sm[w * pitch + fft_slot(q & (m - 1))];
+      const C b = sm[w * pitch + fft_slot((m - q) & (m - 1))];
+      const R ex = (R)0.5 * (a.x + b.x), ey = (R)0.5 * (a.y - b.y);
+      const R ox = (R)0.5 * (a.y + b.y), oy = (R)-0.5 * (a.x - b.x);
+      const C t = twr[q];
+      C X;
+      X.x = ex + (t.x * ox - t.y * oy);
+      X.y = ey + (t.x * oy + t.y * ox);
+      dst[(long long)w * g.nh + q] = X;
+    }
+    __syncthreads();
   }
-  C b[NCH];
+}
+
+// One pass of complex transforms on the half spectrum: lines of length 2^logn (element stride is),
+// W lines adjacent along the contiguous qx axis (ngroup = nh lines in all, the last group partial),
+// outer index blockIdx.y (stride os), channel blockIdx.z (stride fs).
+template <typename R>
+__global__ void __launch_bounds__(kFftThreads)
+    k_hpass(typename CxT<R>::T *__restrict__ data, int logn, int W, int ngroup, long long os, long long is,
+            long long fs, const typename CxT<R>::T *__restrict__ tw, int inverse) {
+  using C = typename CxT<R>::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C *sm = reinterpret_cast<C *>(smraw);
+  const int n = 1 << logn, pitch = fft_pitch(n);
+  const int g0 = blockIdx.x * W, nw = min(W, ngroup - g0);
+  C *base = data + blockIdx.z * fs + g0 + (long long)blockIdx.y * os;
+  for (int e = threadIdx.x; e < nw * n; e += kFftThreads) {
+    const int i = e / nw, w = e - i * nw;
+    sm[w * pitch + fft_slot(brev_n(i, logn))] = base[w + i * is];
+  }
+  __syncthreads();
+  fft_stages<R>(sm, pitch, nw, logn, tw, inverse);
+  for (int e = threadIdx.x; e < nw * n; e += kFftThreads) {
+    const int i = e / nw, w = e - i * nw;
+    base[w + i * is] = sm[w * pitch + fft_slot(i)];
+  }
+}
+
+// b = M(q) s at one wave vector (half-spectrum index q): diagonal Md, upper triangle Mo (Hermitian)
+template <typename R, int NCH>
+__device__ __forceinline__ void kmul_point(const R *__restrict__ Md, const typename CxT<R>::T *__restrict__ Mo,
+                                           long long Nh, long long q, const typename CxT<R>::T (&s)[NCH],
+                                           typename CxT<R>::T (&b)[NCH]) {
+  using C = typename CxT<R>::T;
 #pragma unroll
   for (int k = 0; k < NCH; ++k) {
-    const R d = Md[k * N + q];
+    const R d = Md[k * Nh + q];
     C acc;
     acc.x = d * s[k].x;
     acc.y = d * s[k].y;
@@ -280,7 +356,7 @@ __global__ void k_kmul(typename CxT<R>::T *__restrict__ Z, const R *__restrict__
       if (l == k) continue;
       const int lo = k < l ? k : l, hi = k < l ? l : k;
       const int p = lo * NCH - lo * (lo + 1) / 2 + (hi - lo - 1);
-      C mkl = Mo[p * N + q];
+      C mkl = Mo[p * Nh + q];
       if (k > l) mkl.y = -mkl.y;
       const C t = cmul(mkl, s[l]);
       acc.x += t.x;
@@ -288,45 +364,218 @@ __global__ void k_kmul(typename CxT<R>::T *__restrict__ Z, const R *__restrict__
     }
     b[k] = acc;
   }
+}
+
+// z lines of qx0 .. qx0 + W - 1 at qy = blockIdx.y, every channel: forward transform, kernel multiply,
+// inverse transform.  After the forward DIT the spectrum is in natural order; the multiply writes each
+// result to the bit-reversed position of its wave vector (pairs i <-> brev(i) are handled by one
+// thread), which is the input order of the inverse DIT.
+template <typename R, int NCH>
+__global__ void __launch_bounds__(kFftThreads)
+    k_zkz(typename CxT<R>::T *__restrict__ Zh, const R *__restrict__ Md, const typename CxT<R>::T *__restrict__ Mo,
+          FftGeo g, int logz, int W, const typename CxT<R>::T *__restrict__ tw) {
+  using C = typename CxT<R>::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C *sm = reinterpret_cast<C *>(smraw);
+  const int n = 1 << logz, pitch = fft_pitch(n);
+  const int qx0 = blockIdx.x * W, qy = blockIdx.y, nw = min(W, g.nh - qx0);
+  const long long zs = (long long)g.ny * g.nh;  // stride between z planes
+  C *base = Zh + (long long)qy * g.nh + qx0;
+  for (int e = threadIdx.x; e < NCH * nw * n; e += kFftThreads) {
+    const int k = e / (nw * n), r2 = e - k * nw * n, i = r2 / nw, w = r2 - i * nw;
+    sm[(k * W + w) * pitch + fft_slot(brev_n(i, logz))] = base[k * g.Nh + i * zs + w];
+  }
+  __syncthreads();
+  fft_stages<R>(sm, pitch, NCH * W, logz, tw, 0);
+  for (int e = threadIdx.x; e < nw * n; e += kFftThreads) {
+    const int i = e / nw, w = e - i * nw, r = brev_n(i, logz);
+    if (r < i) continue;
+    C si[NCH], bi[NCH];
 #pragma unroll
-  for (int m = 0; m < NZF; ++m) {
-    const C e = b[2 * m];
-    C o;
-    o.x = (R)0;
-    o.y = (R)0;
-    if (2 * m + 1 < NCH) o = b[2 * m + 1];
-    C wq, wm;
-    wq.x = e.x - o.y;
-    wq.y = e.y + o.x;
-    wm.x = e.x + o.y;
-    wm.y = -e.y + o.x;
-    Z[m * N + q] = wq;
-    if (mq != q) Z[m * N + mq] = wm;
+    for (int k = 0; k < NCH; ++k) si[k] = sm[(k * W + w) * pitch + fft_slot(i)];
+    const long long q0 = (long long)qy * g.nh + qx0 + w;
+    kmul_point<R, NCH>(Md, Mo, g.Nh, q0 + i * zs, si, bi);
+    if (r == i) {
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) sm[(k * W + w) * pitch + fft_slot(i)] = bi[k];
+    } else {
+      C sr[NCH], br[NCH];
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) sr[k] = sm[(k * W + w) * pitch + fft_slot(r)];
+      kmul_point<R, NCH>(Md, Mo, g.Nh, q0 + r * zs, sr, br);
+#pragma unroll
+      for (int k = 0; k < NCH; ++k) {
+        sm[(k * W + w) * pitch + fft_slot(r)] = bi[k];
+        sm[(k * W + w) * pitch + fft_slot(i)] = br[k];
+      }
+    }
+  }
+  __syncthreads();
+  fft_stages<R>(sm, pitch, NCH * W, logz, tw, 1);
+  for (int e = threadIdx.x; e < NCH * nw * n; e += kFftThreads) {
+    const int k = e / (nw * n), r2 = e - k * nw * n, i = r2 / nw, w = r2 - i * nw;
+    base[k * g.Nh + i * zs + w] = sm[(k * W + w) * pitch + fft_slot(i)];
   }
 }
 
-// packed fields -> real channels times scale, plus Zeeman and anisotropy when onsite
-template <typename R, typename Tout, typename Tspin>
-__global__ void k_unpack(const typename CxT<R>::T *__restrict__ Z, Tout *__restrict__ b, int nsub, long long N,
-                         R scale, const Tspin *__restrict__ S, OnSiteT<R> os, int onsite) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int nch = 3 * nsub;
-  R v[3 * SX_MAX_SUB];
-  for (int m = 0; m < (nch + 1) / 2; ++m) {
-    const typename CxT<R>::T z = Z[m * N + i];
-    v[2 * m] = z.x * scale;
-    if (2 * m + 1 < nch) v[2 * m + 1] = z.y * scale;
+enum XEpilogue { XE_FIELD = 0, XE_PRED = 1, XE_CORR = 2 };
+
+// Arguments of the complex-to-real x pass and its epilogue
+template <typename R, typename Tout>
+struct XArgs {
+  const double *S;  // FIELD: spins of the on-site terms (may be the predictor state, then Sr); PRED, CORR: S^n
+  const R *Sr;      // FIELD: spins in R instead of S when set; CORR: S~
+  Tout *out;        // FIELD: the field
+  R *St, *F0, *Th;  // PRED: written; CORR: F0, Th read
+  double *Snew;     // CORR: S^{n+1}
+  int *status;
+  OnSiteT<R> os;
+  HeunT<R> h;
+  unsigned long long step;
+  int onsite;
+};
+
+template <typename R>
+__device__ __forceinline__ void onsite_r(const OnSiteT<R> &os, int a, const R s[3], R b[3]) {
+  const R p = os.twoK[a] * (s[0] * os.axis[a][0] + s[1] * os.axis[a][1] + s[2] * os.axis[a][2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) b[c] += os.zee[a][c] + p * os.axis[a][c];
+}
+
+__device__ __forceinline__ void unit_r(float x[3]) {
+  const float n2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  float r = rsqrtf(n2);
+  r = r * fmaf(-0.5f * n2, r * r, 1.5f);
+  x[0] *= r;
+  x[1] *= r;
+  x[2] *= r;
+}
+__device__ __forceinline__ void unit_r(double x[3]) {
+  const double r = rsqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  x[0] *= r;
+  x[1] *= r;
+  x[2] *= r;
+}
+__device__ __forceinline__ bool correct_r(const double S[3], const float d[3], double o[3]) {
+  return renormalise64(S, d, o);
+}
+__device__ __forceinline__ bool correct_r(const double S[3], const double d[3], double o[3]) {
+  o[0] = S[0] + d[0];
+  o[1] = S[1] + d[1];
+  o[2] = S[2] + d[2];
+  return unit64_checked(o);
+}
+
+// x lines y0 .. y0 + W - 1 of plane z, every channel: half spectrum -> real samples times 1/N, then the
+// epilogue on those cells.  Inverse of k_xr2c: Z'_q = E'_q + i O'_q (q < m) with E'_q = X_q + conj X_{m-q},
+// O'_q = (X_q - conj X_{m-q}) conj(w^q); the unnormalised inverse m-point transform of Z' holds
+// (x_2j, x_2j+1) times N of the 3D transform.
+template <typename R, int MODE, typename Tout, int NSUB>
+__global__ void __launch_bounds__(kFftThreads)
+    k_xc2r(const typename CxT<R>::T *__restrict__ Zh, FftGeo g, int W, const typename CxT<R>::T *__restrict__ twm,
+           const typename CxT<R>::T *__restrict__ twr, XArgs<R, Tout> xa) {
+  using C = typename CxT<R>::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C *sm = reinterpret_cast<C *>(smraw);
+  constexpr int nsub = NSUB, nch = 3 * NSUB;
+  const int m = g.m, logm = g.logm, pitch = fft_pitch(m);
+  const int y0 = blockIdx.x * W, z = blockIdx.y;
+  const int nw = min(W, g.ny - y0);
+  for (int e = threadIdx.x; e < nch * nw * m; e += kFftThreads) {
+    const int k = e / (nw * m), r2 = e - k * nw * m, w = r2 >> logm, q = r2 & (m - 1);
+    const C *row = Zh + (long long)k * g.Nh + ((long long)z * g.ny + y0 + w) * g.nh;
+    const C x = row[q], y = row[m - q];
+    const R ex = x.x + y.x, ey = x.y - y.y, dx = x.x - y.x, dy = x.y + y.y;
+    const C t = twr[q];
+    const R ox = dx * t.x + dy * t.y, oy = dy * t.x - dx * t.y;  // (d) conj(t)
+    C v;
+    v.x = ex - oy;
+    v.y = ey + ox;
+    sm[(k * W + w) * pitch + fft_slot(brev_n(q, logm))] = v;
   }
-  if (onsite) {
+  __syncthreads();
+  fft_stages<R>(sm, pitch, nch * W, logm, twm, 1);
+  const R scale = (R)(1.0 / (double)g.N);
+  for (int e = threadIdx.x; e < nw * g.nx; e += kFftThreads) {
+    const int w = e >> g.logx, x = e & (g.nx - 1);
+    const long long cell = ((long long)z * g.ny + y0 + w) * g.nx + x;
+    R v[nch];
+#pragma unroll
+    for (int k = 0; k < nch; ++k) {
+      const C c = sm[(k * W + w) * pitch + fft_slot(x >> 1)];
+      v[k] = ((x & 1) ? c.y : c.x) * scale;
+    }
+#pragma unroll
     for (int a = 0; a < nsub; ++a) {
-      const R s0 = cvt<R>(S[(long long)(0 * nsub + a) * N + i]), s1 = cvt<R>(S[(long long)(1 * nsub + a) * N + i]),
-              s2 = cvt<R>(S[(long long)(2 * nsub + a) * N + i]);
-      const R p = os.twoK[a] * (s0 * os.axis[a][0] + s1 * os.axis[a][1] + s2 * os.axis[a][2]);
-      for (int c = 0; c < 3; ++c) v[c * nsub + a] += os.zee[a][c] + p * os.axis[a][c];
+      R b[3] = {v[a], v[nsub + a], v[2 * nsub + a]};
+      const long long i0 = (long long)a * g.N + cell;  // channel c of sublattice a at (c nsub + a) N + cell
+      if constexpr (MODE == XE_FIELD) {
+        if (xa.onsite) {
+          R s[3];
+          for (int c = 0; c < 3; ++c)
+            s[c] = xa.Sr ? xa.Sr[(long long)c * nsub * g.N + i0] : cvt<R>(xa.S[(long long)c * nsub * g.N + i0]);
+          onsite_r<R>(xa.os, a, s, b);
+        }
+        for (int c = 0; c < 3; ++c) xa.out[(long long)c * nsub * g.N + i0] = cvt<Tout>(b[c]);
+      } else if constexpr (MODE == XE_PRED) {
+        R s[3], th[3] = {(R)0, (R)0, (R)0}, f[3];
+        for (int c = 0; c < 3; ++c) s[c] = cvt<R>(xa.S[(long long)c * nsub * g.N + i0]);
+        onsite_r<R>(xa.os, a, s, b);
+        if (xa.h.thermal) {
+          float e0, e1, e2;
+          normals3(xa.h.seed, xa.h.replica, (uint64_t)i0, xa.step, e0, e1, e2);
+          const R sg = xa.h.sigma[a];
+          th[0] = sg * cvt<R>(e0);
+          th[1] = sg * cvt<R>(e1);
+          th[2] = sg * cvt<R>(e2);
+          for (int c = 0; c < 3; ++c) xa.Th[(long long)c * nsub * g.N + i0] = th[c];
+        }
+        const R im = xa.os.inv_mm[a];
+        const R B[3] = {b[0] * im + th[0], b[1] * im + th[1], b[2] * im + th[2]};
+        llg_rhs_t<R>(s, B, xa.h.g, xa.h.alpha, f);
+        R xs[3] = {s[0] + xa.h.dt * f[0], s[1] + xa.h.dt * f[1], s[2] + xa.h.dt * f[2]};
+        unit_r(xs);
+        for (int c = 0; c < 3; ++c) {
+          xa.St[(long long)c * nsub * g.N + i0] = xs[c];
+          xa.F0[(long long)c * nsub * g.N + i0] = f[c];
+        }
+      } else {
+        R s[3], th[3] = {(R)0, (R)0, (R)0}, f[3], d[3];
+        double s64[3], o[3];
+        for (int c = 0; c < 3; ++c) {
+          s[c] = xa.Sr[(long long)c * nsub * g.N + i0];
+          s64[c] = xa.S[(long long)c * nsub * g.N + i0];
+          if (xa.h.thermal) th[c] = xa.Th[(long long)c * nsub * g.N + i0];
+        }
+        onsite_r<R>(xa.os, a, s, b);
+        const R im = xa.os.inv_mm[a];
+        const R B[3] = {b[0] * im + th[0], b[1] * im + th[1], b[2] * im + th[2]};
+        llg_rhs_t<R>(s, B, xa.h.g, xa.h.alpha, f);
+        for (int c = 0; c < 3; ++c) d[c] = xa.h.hdt * (xa.F0[(long long)c * nsub * g.N + i0] + f[c]);
+        report_numeric(xa.status, correct_r(s64, d, o));
+        for (int c = 0; c < 3; ++c) xa.Snew[(long long)c * nsub * g.N + i0] = o[c];
+      }
     }
   }
-  for (int k = 0; k < nch; ++k) b[(long long)k * N + i] = cvt<Tout>(v[k]);
+}
+
+// kernel spectrum of the half spectrum from the full FP64 spectrum Zb
+template <typename R>
+__global__ void k_store_diag_h(const double2 *__restrict__ Zb, R *__restrict__ Md, FftGeo g) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.Nh) return;
+  const long long row = i / g.nh, qx = i - row * g.nh;
+  Md[i] = (R)Zb[row * g.nx + qx].x;
+}
+template <typename R>
+__global__ void k_store_off_h(const double2 *__restrict__ Zb, typename CxT<R>::T *__restrict__ Mo, FftGeo g) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.Nh) return;
+  const long long row = i / g.nh, qx = i - row * g.nh;
+  typename CxT<R>::T v;
+  v.x = (R)Zb[row * g.nx + qx].x;
+  v.y = (R)Zb[row * g.nx + qx].y;
+  Mo[i] = v;
 }
 
 // ---------------------------------------------------------------- Heun
@@ -501,22 +750,6 @@ __global__ void k_add_taps(double2 *__restrict__ Zb, const DevTap *__restrict__ 
   }
 }
 
-template <typename R>
-__global__ void k_store_diag(const double2 *__restrict__ Zb, R *__restrict__ Md, long long N) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) Md[i] = (R)Zb[i].x;
-}
-template <typename R>
-__global__ void k_store_off(const double2 *__restrict__ Zb, typename CxT<R>::T *__restrict__ Mo, long long N) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) {
-    typename CxT<R>::T v;
-    v.x = (R)Zb[i].x;
-    v.y = (R)Zb[i].y;
-    Mo[i] = v;
-  }
-}
-
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 int ilog2(int n) {
@@ -578,17 +811,69 @@ cudaError_t fft3d(const FftPlan &fp, typename CxT<R>::T *Z, int nfields, const v
   return cudaSuccess;
 }
 
-template <typename R>
-cudaError_t kmul(const FftPlan &fp, cudaStream_t st) {
+FftGeo fft_geo(const FftPlan &fp) {
+  FftGeo g;
+  g.nx = fp.n[0];
+  g.ny = fp.n[1];
+  g.nz = fp.n[2];
+  g.m = g.nx / 2;
+  g.nh = g.m + 1;
+  g.logx = fp.logn[0];
+  g.logm = fp.logn[0] - 1;
+  g.N = fp.N;
+  g.Nh = fp.Nh;
+  return g;
+}
+
+// The half spectrum b^ = M s^ of the real channels `in`, left in fp.Z (x, y forward, z with the
+// kernel multiply, y inverse); k_xc2r then brings it back along x.
+template <typename R, typename Tin>
+cudaError_t spectrum_field(const FftPlan &fp, const Tin *in, cudaStream_t st) {
   using C = typename CxT<R>::T;
-  const unsigned g = blocks_for(fp.N, 256);
   C *Z = static_cast<C *>(fp.Z);
-  const R *Md = static_cast<const R *>(fp.Md);
-  const C *Mo = static_cast<const C *>(fp.Mo);
-  if (fp.nch == 3)
-    k_kmul<R, 3><<<g, 256, 0, st>>>(Z, Md, Mo, fp.n[0], fp.n[1], fp.n[2], fp.N);
+  const FftGeo g = fft_geo(fp);
+  const C *twm = static_cast<const C *>(fp.twm), *twr = static_cast<const C *>(fp.twr);
+  const size_t cs = sizeof(C);
+  k_xr2c<R, Tin><<<dim3((g.ny + fp.wx - 1) / fp.wx, g.nz), kFftThreads, fp.wx * fft_pitch(g.m) * cs, st>>>(
+      in, Z, g, fp.nch, fp.wx, twm, twr);
+  cudaError_t e = cudaGetLastError();
+  const dim3 gy((g.nh + fp.wy - 1) / fp.wy, g.nz, fp.nch);
+  const size_t smy = fp.wy * fft_pitch(g.ny) * cs;
+  if (e == cudaSuccess && g.ny > 1) {
+    k_hpass<R><<<gy, kFftThreads, smy, st>>>(Z, fp.logn[1], fp.wy, g.nh, (long long)g.ny * g.nh, g.nh, g.Nh,
+                                             static_cast<const C *>(fp.tw[1]), 0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const dim3 gz((g.nh + fp.wz - 1) / fp.wz, g.ny);
+    const size_t smz = (size_t)fp.nch * fp.wz * fft_pitch(g.nz) * cs;
+    const R *Md = static_cast<const R *>(fp.Md);
+    const C *Mo = static_cast<const C *>(fp.Mo);
+    if (fp.nch == 3)
+      k_zkz<R, 3><<<gz, kFftThreads, smz, st>>>(Z, Md, Mo, g, fp.logn[2], fp.wz, static_cast<const C *>(fp.tw[2]));
+    else
+      k_zkz<R, 6><<<gz, kFftThreads, smz, st>>>(Z, Md, Mo, g, fp.logn[2], fp.wz, static_cast<const C *>(fp.tw[2]));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && g.ny > 1) {
+    k_hpass<R><<<gy, kFftThreads, smy, st>>>(Z, fp.logn[1], fp.wy, g.nh, (long long)g.ny * g.nh, g.nh, g.Nh,
+                                             static_cast<const C *>(fp.tw[1]), 1);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+template <typename R, int MODE, typename Tout>
+cudaError_t launch_xc2r(const FftPlan &fp, const XArgs<R, Tout> &xa, cudaStream_t st) {
+  using C = typename CxT<R>::T;
+  const FftGeo g = fft_geo(fp);
+  const size_t sm = (size_t)fp.nch * fp.wc * fft_pitch(g.m) * sizeof(C);
+  const dim3 grid((g.ny + fp.wc - 1) / fp.wc, g.nz);
+  const C *Z = static_cast<const C *>(fp.Z), *twm = static_cast<const C *>(fp.twm), *twr = static_cast<const C *>(fp.twr);
+  if (fp.nsub == 1)
+    k_xc2r<R, MODE, Tout, 1><<<grid, kFftThreads, sm, st>>>(Z, g, fp.wc, twm, twr, xa);
   else
-    k_kmul<R, 6><<<g, 256, 0, st>>>(Z, Md, Mo, fp.n[0], fp.n[1], fp.n[2], fp.N);
+    k_xc2r<R, MODE, Tout, 2><<<grid, kFftThreads, sm, st>>>(Z, g, fp.wc, twm, twr, xa);
   return cudaGetLastError();
 }
 
@@ -596,35 +881,42 @@ cudaError_t kmul(const FftPlan &fp, cudaStream_t st) {
 template <typename R, typename Tin, typename Tout>
 cudaError_t field_pipeline(const sx_ctx *c, const Tin *in, Tout *out, bool onsite, cudaStream_t st) {
   const FftPlan &fp = *c->fft;
-  using C = typename CxT<R>::T;
-  C *Z = static_cast<C *>(fp.Z);
-  k_pack<Tin, R><<<blocks_for(fp.N, 256), 256, 0, st>>>(in, Z, fp.nch, fp.N);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = fft3d<R>(fp, Z, fp.nzf, fp.tw, 0, st);
-  if (e == cudaSuccess) e = kmul<R>(fp, st);
-  if (e == cudaSuccess) e = fft3d<R>(fp, Z, fp.nzf, fp.tw, 1, st);
+  cudaError_t e = spectrum_field<R, Tin>(fp, in, st);
   if (e != cudaSuccess) return e;
-  k_unpack<R, Tout, Tin><<<blocks_for(fp.N, 256), 256, 0, st>>>(Z, out, fp.nsub, fp.N, (R)(1.0 / (double)fp.N), in,
-                                                                onsite_cast<R>(c->onsite), onsite ? 1 : 0);
-  return cudaGetLastError();
+  XArgs<R, Tout> xa;
+  memset(&xa, 0, sizeof(xa));
+  if constexpr (sizeof(Tin) == sizeof(double))
+    xa.S = reinterpret_cast<const double *>(in);
+  else
+    xa.Sr = reinterpret_cast<const R *>(in);
+  xa.out = out;
+  xa.os = onsite_cast<R>(c->onsite);
+  xa.onsite = onsite ? 1 : 0;
+  return launch_xc2r<R, XE_FIELD, Tout>(fp, xa, st);
 }
 
+// field(S^n) -> predictor (in the x pass) -> field(S~) -> corrector (in the x pass)
 template <typename R>
 cudaError_t heun_pipeline(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                           cudaStream_t st) {
   const FftPlan &fp = *c->fft;
-  R *St = static_cast<R *>(fp.St), *F0 = static_cast<R *>(fp.F0), *Bf = static_cast<R *>(fp.Bf);
-  R *Th = static_cast<R *>(fp.Th);
-  cudaError_t e = field_pipeline<R, double, R>(c, src, Bf, false, st);
-  if (e != cudaSuccess) return e;
-  k_fft_predict<R><<<blocks_for(fp.N, 256), 256, 0, st>>>(src, Bf, St, F0, Th, fp.nsub, fp.N, onsite_cast<R>(c->onsite),
-                                                          heun_cast<R>(h), step);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  e = field_pipeline<R, R, R>(c, St, Bf, false, st);
-  if (e != cudaSuccess) return e;
-  k_fft_correct<R><<<blocks_for(fp.N, 256), 256, 0, st>>>(src, St, F0, Bf, Th, dst, fp.nsub, fp.N,
-                                                          onsite_cast<R>(c->onsite), heun_cast<R>(h), c->d_status);
-  return cudaGetLastError();
+  XArgs<R, R> xa;
+  memset(&xa, 0, sizeof(xa));
+  xa.S = src;
+  xa.St = static_cast<R *>(fp.St);
+  xa.F0 = static_cast<R *>(fp.F0);
+  xa.Th = static_cast<R *>(fp.Th);
+  xa.Sr = static_cast<const R *>(fp.St);
+  xa.Snew = dst;
+  xa.status = c->d_status;
+  xa.os = onsite_cast<R>(c->onsite);
+  xa.h = heun_cast<R>(h);
+  xa.step = step;
+  cudaError_t e = spectrum_field<R, double>(fp, src, st);
+  if (e == cudaSuccess) e = launch_xc2r<R, XE_PRED, R>(fp, xa, st);
+  if (e == cudaSuccess) e = spectrum_field<R, R>(fp, static_cast<const R *>(fp.St), st);
+  if (e == cudaSuccess) e = launch_xc2r<R, XE_CORR, R>(fp, xa, st);
+  return e;
 }
 
 template <typename R>
@@ -652,7 +944,27 @@ cudaError_t alloc_twiddles(const FftPlan &fp, void *tw[3]) {
 
 template <typename R>
 cudaError_t set_fft_smem() {
-  return cudaFuncSetAttribute(k_fft_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFftSmem);
+  const int b = (int)kFftSmem;
+  cudaError_t e = cudaFuncSetAttribute(k_fft_pass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xr2c<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xr2c<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hpass<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zkz<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_zkz<R, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  for (auto fn : {k_xc2r<R, XE_FIELD, double, 1>, k_xc2r<R, XE_FIELD, double, 2>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  for (auto fn : {k_xc2r<R, XE_PRED, R, 1>, k_xc2r<R, XE_PRED, R, 2>, k_xc2r<R, XE_CORR, R, 1>,
+                  k_xc2r<R, XE_CORR, R, 2>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return e;
+}
+
+// lines per CTA: the largest power of two up to 16 whose staging (bytes_per_line each) fits in half of the
+// shared memory (two CTAs per SM) and that does not exceed the extent of the grouping axis
+inline int pick_lines(size_t bytes_per_line, int extent) {
+  int w = 16;
+  while (w > 1 && ((size_t)w * bytes_per_line > 113 * 1024 || w > extent)) w >>= 1;
+  return w;
 }
 
 // M(q) in FP64: fill each upper-triangle component in real space, transform
@@ -692,10 +1004,12 @@ cudaError_t build_kernel(sx_ctx *c, FftPlan &fp) {
       e = cudaGetLastError();
       if (e == cudaSuccess) e = fft3d<double>(fp, Zb, 1, tw64, 1, 0);
       if (e != cudaSuccess) break;
+      const FftGeo g = fft_geo(fp);
       if (ka == kb) {
-        k_store_diag<R><<<blocks_for(N, 256), 256>>>(Zb, static_cast<R *>(fp.Md) + ka * N, N);
+        k_store_diag_h<R><<<blocks_for(fp.Nh, 256), 256>>>(Zb, static_cast<R *>(fp.Md) + ka * fp.Nh, g);
       } else {
-        k_store_off<R><<<blocks_for(N, 256), 256>>>(Zb, static_cast<typename CxT<R>::T *>(fp.Mo) + p * N, N);
+        k_store_off_h<R><<<blocks_for(fp.Nh, 256), 256>>>(Zb, static_cast<typename CxT<R>::T *>(fp.Mo) + p * fp.Nh,
+                                                          g);
         ++p;
       }
       e = cudaGetLastError();
@@ -709,16 +1023,35 @@ cudaError_t build_kernel(sx_ctx *c, FftPlan &fp) {
 template <typename R>
 cudaError_t alloc_plan(FftPlan &fp) {
   using C = typename CxT<R>::T;
-  const long long N = fp.N;
-  cudaError_t e = cudaMalloc(&fp.Z, (size_t)fp.nzf * N * sizeof(C));
-  if (e == cudaSuccess) e = cudaMalloc(&fp.Md, (size_t)fp.nch * N * sizeof(R));
-  if (e == cudaSuccess && fp.noff) e = cudaMalloc(&fp.Mo, (size_t)fp.noff * N * sizeof(C));
+  const long long N = fp.N, Nh = fp.Nh;
+  cudaError_t e = cudaMalloc(&fp.Z, (size_t)fp.nch * Nh * sizeof(C));
+  if (e == cudaSuccess) e = cudaMalloc(&fp.Md, (size_t)fp.nch * Nh * sizeof(R));
+  if (e == cudaSuccess && fp.noff) e = cudaMalloc(&fp.Mo, (size_t)fp.noff * Nh * sizeof(C));
   if (e == cudaSuccess) e = cudaMalloc(&fp.St, (size_t)fp.nch * N * sizeof(R));
   if (e == cudaSuccess) e = cudaMalloc(&fp.F0, (size_t)fp.nch * N * sizeof(R));
-  if (e == cudaSuccess) e = cudaMalloc(&fp.Bf, (size_t)fp.nch * N * sizeof(R));
   if (e == cudaSuccess) e = cudaMalloc(&fp.Th, (size_t)fp.nch * N * sizeof(R));
   if (e == cudaSuccess) e = alloc_twiddles<R>(fp, fp.tw);
+  if (e == cudaSuccess) {
+    // the nx/2-point transform of the x passes and the split factors of the real-to-complex step
+    const int m = fp.n[0] / 2;
+    std::vector<C> tm = twiddles<R>(m), tr(m + 1);
+    const double pi = 3.14159265358979323846;
+    for (int q = 0; q <= m; ++q) {
+      tr[q].x = (R)cos(-2.0 * pi * q / fp.n[0]);
+      tr[q].y = (R)sin(-2.0 * pi * q / fp.n[0]);
+    }
+    e = cudaMalloc(&fp.twm, tm.size() * sizeof(C));
+    if (e == cudaSuccess) e = cudaMemcpy(fp.twm, tm.data(), tm.size() * sizeof(C), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&fp.twr, tr.size() * sizeof(C));
+    if (e == cudaSuccess) e = cudaMemcpy(fp.twr, tr.data(), tr.size() * sizeof(C), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = set_fft_smem<R>();
+  const size_t cs = sizeof(C);
+  const int nh = fp.n[0] / 2 + 1;
+  fp.wx = pick_lines((size_t)fft_pitch(fp.n[0] / 2) * cs, fp.n[1]);
+  fp.wy = pick_lines((size_t)fft_pitch(fp.n[1]) * cs, nh);
+  fp.wz = pick_lines((size_t)fp.nch * fft_pitch(fp.n[2]) * cs, nh);
+  fp.wc = pick_lines((size_t)fp.nch * fft_pitch(fp.n[0] / 2) * cs, fp.n[1]);
   return e;
 }
 
@@ -732,8 +1065,9 @@ void fft_free(sx_ctx *c) {
   cudaFree(fp->Mo);
   cudaFree(fp->St);
   cudaFree(fp->F0);
-  cudaFree(fp->Bf);
   cudaFree(fp->Th);
+  cudaFree(fp->twm);
+  cudaFree(fp->twr);
   for (int k = 0; k < 3; ++k) cudaFree(fp->tw[k]);
   delete fp;
   c->fft = nullptr;
@@ -747,6 +1081,7 @@ int fft_plan(sx_ctx *c) {
     const int n = c->lat.n[k];
     if (!c->lat.pbc[k]) return set_error(SX_ERR_UNSUPPORTED, "the FFT backend needs periodic boundaries on every axis");
     if (n & (n - 1)) return set_error(SX_ERR_UNSUPPORTED, "the FFT backend needs power-of-two cell counts");
+    if (k == 0 && n < 2) return set_error(SX_ERR_UNSUPPORTED, "the FFT backend needs at least two cells along x");
     if (n > 4096) return set_error(SX_ERR_UNSUPPORTED, "the FFT backend supports up to 4096 cells per axis");
   }
   FftPlan *fp = new (std::nothrow) FftPlan();
@@ -759,9 +1094,9 @@ int fft_plan(sx_ctx *c) {
   }
   fp->nsub = c->lat.nsub;
   fp->nch = 3 * fp->nsub;
-  fp->nzf = (fp->nch + 1) / 2;
   fp->noff = fp->nch * (fp->nch - 1) / 2;
   fp->N = c->geo.ncell;
+  fp->Nh = (long long)(fp->n[0] / 2 + 1) * fp->n[1] * fp->n[2];
   c->fft = fp;
   cudaError_t e = (fp->prec == SX_PREC_FP32) ? alloc_plan<float>(*fp) : alloc_plan<double>(*fp);
   if (e == cudaSuccess) e = (fp->prec == SX_PREC_FP32) ? build_kernel<float>(c, *fp) : build_kernel<double>(c, *fp);
@@ -769,7 +1104,7 @@ int fft_plan(sx_ctx *c) {
     fft_free(c);
     return cuda_error(e, "FFT plan");
   }
-  c->launches_per_step = 2 * (1 + 2 * ((fp->n[0] > 1) + (fp->n[1] > 1) + (fp->n[2] > 1)) + 1 + 1) + 2;
+  c->launches_per_step = 2 * (3 + 2 * (fp->n[1] > 1));
   return SX_OK;
 }
 
