@@ -25,6 +25,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -50,7 +51,7 @@ struct FftPlan {
   int n[3], logn[3];
   int nsub, nch, noff;
   long long N;   // cells
-  long long Nh;  // half-spectrum points (nx/2 + 1) ny nz
+  long long Nh;  // half-spectrum storage per channel: np ny nz, np = nx/2 + 1 rounded up to a multiple of 16
   void *Z;       // [nch][Nh] complex: half spectra of the channels
   void *Md;      // [nch][Nh] real: diagonal of M(q)
   void *Mo;      // [noff][Nh] complex: upper triangle of M(q)
@@ -64,7 +65,9 @@ struct FftPlan {
 
 namespace {
 
-constexpr int kFftThreads = 512;
+constexpr int kFftThreads = 512;   // the full-length complex passes of the plan-time kernel transform
+constexpr int kHalfThreads = 256;  // the half-spectrum passes of every field evaluation
+constexpr size_t kHalfBudget = 56 * 1024;  // shared memory per CTA of the half-spectrum passes (four CTAs per SM)
 constexpr size_t kFftSmem = 200 * 1024;
 
 template <typename C>
@@ -134,7 +137,7 @@ __device__ __forceinline__ void dit_stages(typename CxT<R>::T *sm, int pitch, in
   const int h = 1 << s;
   const int logng = logn - LR;
   const int total = W << logng;
-  for (int t = threadIdx.x; t < total; t += kFftThreads) {
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int w = t >> logng, j = t & ((1 << logng) - 1);
     const int k = j & (h - 1);
     C *line = sm + w * pitch;
@@ -232,7 +235,9 @@ __global__ void __launch_bounds__(kFftThreads)
 //
 // The spin channels and fields are real, so only the half spectrum qx = 0 .. nx/2 (nh = nx/2 + 1
 // values) is kept, one complex spectrum per real channel k = c * nsub + a:
-//   Zh[k * Nh + (qz * ny + qy) * nh + qx],  Nh = nh * ny * nz.
+//   Zh[k * Nh + (qz * ny + qy) * np + qx],  Nh = np * ny * nz,
+// with the row pitch np = nh rounded up to a multiple of 16, so that every row starts on a 128-byte
+// boundary and the y and z passes read whole 32-byte sectors (the padding columns are never read back).
 // One field evaluation is five passes over it:
 //   k_xr2c   x lines of every channel, real to complex: the nx/2-point complex transform of the
 //            (even, odd) sample pairs, then its split into the half spectrum;
@@ -244,12 +249,26 @@ __global__ void __launch_bounds__(kFftThreads)
 //            lines by the field output, the Heun predictor or the Heun corrector.
 
 struct FftGeo {
-  int nx, ny, nz, nh, m, logm, logx;
+  int nx, ny, nz, nh, np, m, logm, logx;
   long long N, Nh;
 };
 
 __device__ __forceinline__ int brev_n(int i, int logn) {
   return logn ? (int)(__brev((unsigned)i) >> (32 - logn)) : 0;
+}
+
+// asynchronous global -> shared copy of one complex value (8 or 16 bytes), so that a CTA's whole staging
+// load is in flight at once
+template <typename C>
+__device__ __forceinline__ void cp_async_c(C *smem_dst, const C *gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(C) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // every radix-2 DIT stage of nlines staged lines of length 2^logn (bit-reversed input, natural output)
@@ -276,29 +295,43 @@ __device__ __forceinline__ void fft_stages(typename CxT<R>::T *sm, int pitch, in
 // z_j = x_2j + i x_2j+1 (j < m = nx/2), Z = FFT_m(z); X_q = E_q + w^q O_q for q = 0 .. m with
 // E_q = (Z_q + conj Z_{m-q}) / 2, O_q = (Z_q - conj Z_{m-q}) / (2i), w = exp(-2 pi i / nx), Z_m = Z_0.
 template <typename R, typename Tin>
-__global__ void __launch_bounds__(kFftThreads)
-    k_xr2c(const Tin *__restrict__ src, typename CxT<R>::T *__restrict__ Zh, FftGeo g, int nch, int W,
-           const typename CxT<R>::T *__restrict__ twm, const typename CxT<R>::T *__restrict__ twr) {
+__device__ __forceinline__ void r2c_lines(const Tin *__restrict__ src, typename CxT<R>::T *Zh, const FftGeo &g,
+                                          int nch, int W, int y0, int z, typename CxT<R>::T *sm,
+                                          const typename CxT<R>::T *__restrict__ twm,
+                                          const typename CxT<R>::T *__restrict__ twr) {
   using C = typename CxT<R>::T;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C *sm = reinterpret_cast<C *>(smraw);
   const int m = g.m, logm = g.logm, pitch = fft_pitch(m);
-  const int y0 = blockIdx.x * W, z = blockIdx.y;
   const int nw = min(W, g.ny - y0);
   for (int k = 0; k < nch; ++k) {
     const Tin *in = src + (long long)k * g.N + ((long long)z * g.ny + y0) * g.nx;
-    for (int e = threadIdx.x; e < nw * m; e += kFftThreads) {
-      const int w = e >> logm, j = e & (m - 1);
-      const Tin *pq = in + (long long)w * g.nx + 2 * j;
-      C v;
-      v.x = cvt<R>(pq[0]);
-      v.y = cvt<R>(pq[1]);
-      sm[w * pitch + fft_slot(brev_n(j, logm))] = v;
+    // four sample pairs per thread and round, loaded before any is converted
+    constexpr int U = 4;
+    for (int e0 = threadIdx.x; e0 < nw * m; e0 += U * kHalfThreads) {
+      Tin a[U], b[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * kHalfThreads;
+        if (e < nw * m) {
+          const Tin *pq = in + (long long)(e >> logm) * g.nx + 2 * (e & (m - 1));
+          a[u] = pq[0];
+          b[u] = pq[1];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * kHalfThreads;
+        if (e < nw * m) {
+          C v;
+          v.x = cvt<R>(a[u]);
+          v.y = cvt<R>(b[u]);
+          sm[(e >> logm) * pitch + fft_slot(brev_n(e & (m - 1), logm))] = v;
+        }
+      }
     }
     __syncthreads();
     fft_stages<R>(sm, pitch, nw, logm, twm, 0);
-    C *dst = Zh + (long long)k * g.Nh + ((long long)z * g.ny + y0) * g.nh;
-    for (int e = threadIdx.x; e < nw * (m + 1); e += kFftThreads) {
+    C *dst = Zh + (long long)k * g.Nh + ((long long)z * g.ny + y0) * g.np;
+    for (int e = threadIdx.x; e < nw * (m + 1); e += kHalfThreads) {
       const int w = e / (m + 1), q = e - w * (m + 1);
       const C a = sm[w * pitch + fft_slot(q & (m - 1))];
       const C b = sm[w * pitch + fft_slot((m - q) & (m - 1))];
@@ -308,17 +341,26 @@ __global__ void __launch_bounds__(kFftThreads)
       C X;
       X.x = ex + (t.x * ox - t.y * oy);
       X.y = ey + (t.x * oy + t.y * ox);
-      dst[(long long)w * g.nh + q] = X;
+      dst[(long long)w * g.np + q] = X;
     }
     __syncthreads();
   }
+}
+
+template <typename R, typename Tin>
+__global__ void __launch_bounds__(kHalfThreads)
+    k_xr2c(const Tin *__restrict__ src, typename CxT<R>::T *__restrict__ Zh, FftGeo g, int nch, int W,
+           const typename CxT<R>::T *__restrict__ twm, const typename CxT<R>::T *__restrict__ twr) {
+  using C = typename CxT<R>::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  r2c_lines<R, Tin>(src, Zh, g, nch, W, blockIdx.x * W, blockIdx.y, reinterpret_cast<C *>(smraw), twm, twr);
 }
 
 // One pass of complex transforms on the half spectrum: lines of length 2^logn (element stride is),
 // W lines adjacent along the contiguous qx axis (ngroup = nh lines in all, the last group partial),
 // outer index blockIdx.y (stride os), channel blockIdx.z (stride fs).
 template <typename R>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kHalfThreads)
     k_hpass(typename CxT<R>::T *__restrict__ data, int logn, int W, int ngroup, long long os, long long is,
             long long fs, const typename CxT<R>::T *__restrict__ tw, int inverse) {
   using C = typename CxT<R>::T;
@@ -327,13 +369,14 @@ __global__ void __launch_bounds__(kFftThreads)
   const int n = 1 << logn, pitch = fft_pitch(n);
   const int g0 = blockIdx.x * W, nw = min(W, ngroup - g0);
   C *base = data + blockIdx.z * fs + g0 + (long long)blockIdx.y * os;
-  for (int e = threadIdx.x; e < nw * n; e += kFftThreads) {
+  for (int e = threadIdx.x; e < nw * n; e += kHalfThreads) {
     const int i = e / nw, w = e - i * nw;
-    sm[w * pitch + fft_slot(brev_n(i, logn))] = base[w + i * is];
+    cp_async_c(&sm[w * pitch + fft_slot(brev_n(i, logn))], &base[w + i * is]);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_stages<R>(sm, pitch, nw, logn, tw, inverse);
-  for (int e = threadIdx.x; e < nw * n; e += kFftThreads) {
+  for (int e = threadIdx.x; e < nw * n; e += kHalfThreads) {
     const int i = e / nw, w = e - i * nw;
     base[w + i * is] = sm[w * pitch + fft_slot(i)];
   }
@@ -371,7 +414,7 @@ __device__ __forceinline__ void kmul_point(const R *__restrict__ Md, const typen
 // result to the bit-reversed position of its wave vector (pairs i <-> brev(i) are handled by one
 // thread), which is the input order of the inverse DIT.
 template <typename R, int NCH>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kHalfThreads)
     k_zkz(typename CxT<R>::T *__restrict__ Zh, const R *__restrict__ Md, const typename CxT<R>::T *__restrict__ Mo,
           FftGeo g, int logz, int W, const typename CxT<R>::T *__restrict__ tw) {
   using C = typename CxT<R>::T;
@@ -379,21 +422,22 @@ __global__ void __launch_bounds__(kFftThreads)
   C *sm = reinterpret_cast<C *>(smraw);
   const int n = 1 << logz, pitch = fft_pitch(n);
   const int qx0 = blockIdx.x * W, qy = blockIdx.y, nw = min(W, g.nh - qx0);
-  const long long zs = (long long)g.ny * g.nh;  // stride between z planes
-  C *base = Zh + (long long)qy * g.nh + qx0;
-  for (int e = threadIdx.x; e < NCH * nw * n; e += kFftThreads) {
+  const long long zs = (long long)g.ny * g.np;  // stride between z planes
+  C *base = Zh + (long long)qy * g.np + qx0;
+  for (int e = threadIdx.x; e < NCH * nw * n; e += kHalfThreads) {
     const int k = e / (nw * n), r2 = e - k * nw * n, i = r2 / nw, w = r2 - i * nw;
-    sm[(k * W + w) * pitch + fft_slot(brev_n(i, logz))] = base[k * g.Nh + i * zs + w];
+    cp_async_c(&sm[(k * W + w) * pitch + fft_slot(brev_n(i, logz))], &base[k * g.Nh + i * zs + w]);
   }
+  cp_async_wait_all();
   __syncthreads();
   fft_stages<R>(sm, pitch, NCH * W, logz, tw, 0);
-  for (int e = threadIdx.x; e < nw * n; e += kFftThreads) {
+  for (int e = threadIdx.x; e < nw * n; e += kHalfThreads) {
     const int i = e / nw, w = e - i * nw, r = brev_n(i, logz);
     if (r < i) continue;
     C si[NCH], bi[NCH];
 #pragma unroll
     for (int k = 0; k < NCH; ++k) si[k] = sm[(k * W + w) * pitch + fft_slot(i)];
-    const long long q0 = (long long)qy * g.nh + qx0 + w;
+    const long long q0 = (long long)qy * g.np + qx0 + w;
     kmul_point<R, NCH>(Md, Mo, g.Nh, q0 + i * zs, si, bi);
     if (r == i) {
 #pragma unroll
@@ -412,7 +456,7 @@ __global__ void __launch_bounds__(kFftThreads)
   }
   __syncthreads();
   fft_stages<R>(sm, pitch, NCH * W, logz, tw, 1);
-  for (int e = threadIdx.x; e < NCH * nw * n; e += kFftThreads) {
+  for (int e = threadIdx.x; e < NCH * nw * n; e += kHalfThreads) {
     const int k = e / (nw * n), r2 = e - k * nw * n, i = r2 / nw, w = r2 - i * nw;
     base[k * g.Nh + i * zs + w] = sm[(k * W + w) * pitch + fft_slot(i)];
   }
@@ -471,8 +515,8 @@ __device__ __forceinline__ bool correct_r(const double S[3], const double d[3], 
 // O'_q = (X_q - conj X_{m-q}) conj(w^q); the unnormalised inverse m-point transform of Z' holds
 // (x_2j, x_2j+1) times N of the 3D transform.
 template <typename R, int MODE, typename Tout, int NSUB>
-__global__ void __launch_bounds__(kFftThreads)
-    k_xc2r(const typename CxT<R>::T *__restrict__ Zh, FftGeo g, int W, const typename CxT<R>::T *__restrict__ twm,
+__global__ void __launch_bounds__(kHalfThreads)
+    k_xc2r(typename CxT<R>::T *Zh, FftGeo g, int W, const typename CxT<R>::T *__restrict__ twm,
            const typename CxT<R>::T *__restrict__ twr, XArgs<R, Tout> xa) {
   using C = typename CxT<R>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -481,22 +525,41 @@ __global__ void __launch_bounds__(kFftThreads)
   const int m = g.m, logm = g.logm, pitch = fft_pitch(m);
   const int y0 = blockIdx.x * W, z = blockIdx.y;
   const int nw = min(W, g.ny - y0);
-  for (int e = threadIdx.x; e < nch * nw * m; e += kFftThreads) {
-    const int k = e / (nw * m), r2 = e - k * nw * m, w = r2 >> logm, q = r2 & (m - 1);
-    const C *row = Zh + (long long)k * g.Nh + ((long long)z * g.ny + y0 + w) * g.nh;
-    const C x = row[q], y = row[m - q];
-    const R ex = x.x + y.x, ey = x.y - y.y, dx = x.x - y.x, dy = x.y + y.y;
-    const C t = twr[q];
-    const R ox = dx * t.x + dy * t.y, oy = dy * t.x - dx * t.y;  // (d) conj(t)
-    C v;
-    v.x = ex - oy;
-    v.y = ey + ox;
-    sm[(k * W + w) * pitch + fft_slot(brev_n(q, logm))] = v;
+  // four elements per thread and round: their eight loads are issued before any is used
+  constexpr int U = 4;
+  const int total = nch * nw * m;
+  for (int e0 = threadIdx.x; e0 < total; e0 += U * kHalfThreads) {
+    C xs[U], ys[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * kHalfThreads;
+      if (e < total) {
+        const int k = e / (nw * m), r2 = e - k * nw * m, w = r2 >> logm, q = r2 & (m - 1);
+        const C *row = Zh + (long long)k * g.Nh + ((long long)z * g.ny + y0 + w) * g.np;
+        xs[u] = row[q];
+        ys[u] = row[m - q];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * kHalfThreads;
+      if (e < total) {
+        const int k = e / (nw * m), r2 = e - k * nw * m, w = r2 >> logm, q = r2 & (m - 1);
+        const C x = xs[u], y = ys[u];
+        const R ex = x.x + y.x, ey = x.y - y.y, dx = x.x - y.x, dy = x.y + y.y;
+        const C t = twr[q];
+        const R ox = dx * t.x + dy * t.y, oy = dy * t.x - dx * t.y;  // (d) conj(t)
+        C v;
+        v.x = ex - oy;
+        v.y = ey + ox;
+        sm[(k * W + w) * pitch + fft_slot(brev_n(q, logm))] = v;
+      }
+    }
   }
   __syncthreads();
   fft_stages<R>(sm, pitch, nch * W, logm, twm, 1);
   const R scale = (R)(1.0 / (double)g.N);
-  for (int e = threadIdx.x; e < nw * g.nx; e += kFftThreads) {
+  for (int e = threadIdx.x; e < nw * g.nx; e += kHalfThreads) {
     const int w = e >> g.logx, x = e & (g.nx - 1);
     const long long cell = ((long long)z * g.ny + y0 + w) * g.nx + x;
     R v[nch];
@@ -557,6 +620,12 @@ __global__ void __launch_bounds__(kFftThreads)
       }
     }
   }
+  if constexpr (MODE == XE_PRED) {
+    // the forward transform of S~ along these x lines, for the corrector's field: S~ was just written by
+    // this CTA (visible to it after the barrier, L2-resident), and the spectrum rows are this CTA's own
+    __syncthreads();
+    r2c_lines<R, R>(xa.St, Zh, g, nch, W, y0, z, sm, twm, twr);
+  }
 }
 
 // kernel spectrum of the half spectrum from the full FP64 spectrum Zb
@@ -564,17 +633,17 @@ template <typename R>
 __global__ void k_store_diag_h(const double2 *__restrict__ Zb, R *__restrict__ Md, FftGeo g) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.Nh) return;
-  const long long row = i / g.nh, qx = i - row * g.nh;
-  Md[i] = (R)Zb[row * g.nx + qx].x;
+  const long long row = i / g.np, qx = i - row * g.np;
+  Md[i] = qx < g.nh ? (R)Zb[row * g.nx + qx].x : (R)0;
 }
 template <typename R>
 __global__ void k_store_off_h(const double2 *__restrict__ Zb, typename CxT<R>::T *__restrict__ Mo, FftGeo g) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.Nh) return;
-  const long long row = i / g.nh, qx = i - row * g.nh;
+  const long long row = i / g.np, qx = i - row * g.np;
   typename CxT<R>::T v;
-  v.x = (R)Zb[row * g.nx + qx].x;
-  v.y = (R)Zb[row * g.nx + qx].y;
+  v.x = qx < g.nh ? (R)Zb[row * g.nx + qx].x : (R)0;
+  v.y = qx < g.nh ? (R)Zb[row * g.nx + qx].y : (R)0;
   Mo[i] = v;
 }
 
@@ -818,6 +887,7 @@ FftGeo fft_geo(const FftPlan &fp) {
   g.nz = fp.n[2];
   g.m = g.nx / 2;
   g.nh = g.m + 1;
+  g.np = (g.nh + 15) & ~15;
   g.logx = fp.logn[0];
   g.logm = fp.logn[0] - 1;
   g.N = fp.N;
@@ -827,6 +897,7 @@ FftGeo fft_geo(const FftPlan &fp) {
 
 // The half spectrum b^ = M s^ of the real channels `in`, left in fp.Z (x, y forward, z with the
 // kernel multiply, y inverse); k_xc2r then brings it back along x.
+// in == nullptr: the x pass has been done already (the predictor's pass transforms S~ along x).
 template <typename R, typename Tin>
 cudaError_t spectrum_field(const FftPlan &fp, const Tin *in, cudaStream_t st) {
   using C = typename CxT<R>::T;
@@ -834,13 +905,16 @@ cudaError_t spectrum_field(const FftPlan &fp, const Tin *in, cudaStream_t st) {
   const FftGeo g = fft_geo(fp);
   const C *twm = static_cast<const C *>(fp.twm), *twr = static_cast<const C *>(fp.twr);
   const size_t cs = sizeof(C);
-  k_xr2c<R, Tin><<<dim3((g.ny + fp.wx - 1) / fp.wx, g.nz), kFftThreads, fp.wx * fft_pitch(g.m) * cs, st>>>(
-      in, Z, g, fp.nch, fp.wx, twm, twr);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (in) {
+    k_xr2c<R, Tin><<<dim3((g.ny + fp.wx - 1) / fp.wx, g.nz), kHalfThreads, fp.wx * fft_pitch(g.m) * cs, st>>>(
+        in, Z, g, fp.nch, fp.wx, twm, twr);
+    e = cudaGetLastError();
+  }
   const dim3 gy((g.nh + fp.wy - 1) / fp.wy, g.nz, fp.nch);
   const size_t smy = fp.wy * fft_pitch(g.ny) * cs;
   if (e == cudaSuccess && g.ny > 1) {
-    k_hpass<R><<<gy, kFftThreads, smy, st>>>(Z, fp.logn[1], fp.wy, g.nh, (long long)g.ny * g.nh, g.nh, g.Nh,
+    k_hpass<R><<<gy, kHalfThreads, smy, st>>>(Z, fp.logn[1], fp.wy, g.nh, (long long)g.ny * g.np, g.np, g.Nh,
                                              static_cast<const C *>(fp.tw[1]), 0);
     e = cudaGetLastError();
   }
@@ -850,13 +924,13 @@ cudaError_t spectrum_field(const FftPlan &fp, const Tin *in, cudaStream_t st) {
     const R *Md = static_cast<const R *>(fp.Md);
     const C *Mo = static_cast<const C *>(fp.Mo);
     if (fp.nch == 3)
-      k_zkz<R, 3><<<gz, kFftThreads, smz, st>>>(Z, Md, Mo, g, fp.logn[2], fp.wz, static_cast<const C *>(fp.tw[2]));
+      k_zkz<R, 3><<<gz, kHalfThreads, smz, st>>>(Z, Md, Mo, g, fp.logn[2], fp.wz, static_cast<const C *>(fp.tw[2]));
     else
-      k_zkz<R, 6><<<gz, kFftThreads, smz, st>>>(Z, Md, Mo, g, fp.logn[2], fp.wz, static_cast<const C *>(fp.tw[2]));
+      k_zkz<R, 6><<<gz, kHalfThreads, smz, st>>>(Z, Md, Mo, g, fp.logn[2], fp.wz, static_cast<const C *>(fp.tw[2]));
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && g.ny > 1) {
-    k_hpass<R><<<gy, kFftThreads, smy, st>>>(Z, fp.logn[1], fp.wy, g.nh, (long long)g.ny * g.nh, g.nh, g.Nh,
+    k_hpass<R><<<gy, kHalfThreads, smy, st>>>(Z, fp.logn[1], fp.wy, g.nh, (long long)g.ny * g.np, g.np, g.Nh,
                                              static_cast<const C *>(fp.tw[1]), 1);
     e = cudaGetLastError();
   }
@@ -869,11 +943,12 @@ cudaError_t launch_xc2r(const FftPlan &fp, const XArgs<R, Tout> &xa, cudaStream_
   const FftGeo g = fft_geo(fp);
   const size_t sm = (size_t)fp.nch * fp.wc * fft_pitch(g.m) * sizeof(C);
   const dim3 grid((g.ny + fp.wc - 1) / fp.wc, g.nz);
-  const C *Z = static_cast<const C *>(fp.Z), *twm = static_cast<const C *>(fp.twm), *twr = static_cast<const C *>(fp.twr);
+  C *Z = static_cast<C *>(fp.Z);
+  const C *twm = static_cast<const C *>(fp.twm), *twr = static_cast<const C *>(fp.twr);
   if (fp.nsub == 1)
-    k_xc2r<R, MODE, Tout, 1><<<grid, kFftThreads, sm, st>>>(Z, g, fp.wc, twm, twr, xa);
+    k_xc2r<R, MODE, Tout, 1><<<grid, kHalfThreads, sm, st>>>(Z, g, fp.wc, twm, twr, xa);
   else
-    k_xc2r<R, MODE, Tout, 2><<<grid, kFftThreads, sm, st>>>(Z, g, fp.wc, twm, twr, xa);
+    k_xc2r<R, MODE, Tout, 2><<<grid, kHalfThreads, sm, st>>>(Z, g, fp.wc, twm, twr, xa);
   return cudaGetLastError();
 }
 
@@ -895,7 +970,7 @@ cudaError_t field_pipeline(const sx_ctx *c, const Tin *in, Tout *out, bool onsit
   return launch_xc2r<R, XE_FIELD, Tout>(fp, xa, st);
 }
 
-// field(S^n) -> predictor (in the x pass) -> field(S~) -> corrector (in the x pass)
+// field(S^n) -> predictor and the x transform of S~ (in one x pass) -> field(S~) -> corrector (in the x pass)
 template <typename R>
 cudaError_t heun_pipeline(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                           cudaStream_t st) {
@@ -914,7 +989,7 @@ cudaError_t heun_pipeline(const sx_ctx *c, const double *src, double *dst, const
   xa.step = step;
   cudaError_t e = spectrum_field<R, double>(fp, src, st);
   if (e == cudaSuccess) e = launch_xc2r<R, XE_PRED, R>(fp, xa, st);
-  if (e == cudaSuccess) e = spectrum_field<R, R>(fp, static_cast<const R *>(fp.St), st);
+  if (e == cudaSuccess) e = spectrum_field<R, R>(fp, nullptr, st);  // S~ was transformed along x by the predictor
   if (e == cudaSuccess) e = launch_xc2r<R, XE_CORR, R>(fp, xa, st);
   return e;
 }
@@ -959,11 +1034,11 @@ cudaError_t set_fft_smem() {
   return e;
 }
 
-// lines per CTA: the largest power of two up to 16 whose staging (bytes_per_line each) fits in half of the
-// shared memory (two CTAs per SM) and that does not exceed the extent of the grouping axis
-inline int pick_lines(size_t bytes_per_line, int extent) {
+// lines per CTA: the largest power of two up to 16 whose staging (bytes_per_line each) fits in a quarter of
+// the shared memory (four CTAs per SM) and that does not exceed the extent of the grouping axis
+inline int pick_lines(size_t bytes_per_line, int extent, size_t budget = kHalfBudget) {
   int w = 16;
-  while (w > 1 && ((size_t)w * bytes_per_line > 113 * 1024 || w > extent)) w >>= 1;
+  while (w > 1 && ((size_t)w * bytes_per_line > budget || w > extent)) w >>= 1;
   return w;
 }
 
@@ -1050,7 +1125,10 @@ cudaError_t alloc_plan(FftPlan &fp) {
   const int nh = fp.n[0] / 2 + 1;
   fp.wx = pick_lines((size_t)fft_pitch(fp.n[0] / 2) * cs, fp.n[1]);
   fp.wy = pick_lines((size_t)fft_pitch(fp.n[1]) * cs, nh);
+  // the z pass reads rows of W adjacent qx: at least four (a whole 32-byte sector) even at two CTAs per SM
   fp.wz = pick_lines((size_t)fp.nch * fft_pitch(fp.n[2]) * cs, nh);
+  if (fp.wz < 4) fp.wz = std::max(fp.wz, pick_lines((size_t)fp.nch * fft_pitch(fp.n[2]) * cs, std::min(nh, 4),
+                                                      2 * kHalfBudget + 1024));
   fp.wc = pick_lines((size_t)fp.nch * fft_pitch(fp.n[0] / 2) * cs, fp.n[1]);
   return e;
 }
@@ -1096,7 +1174,7 @@ int fft_plan(sx_ctx *c) {
   fp->nch = 3 * fp->nsub;
   fp->noff = fp->nch * (fp->nch - 1) / 2;
   fp->N = c->geo.ncell;
-  fp->Nh = (long long)(fp->n[0] / 2 + 1) * fp->n[1] * fp->n[2];
+  fp->Nh = (long long)((fp->n[0] / 2 + 1 + 15) & ~15) * fp->n[1] * fp->n[2];
   c->fft = fp;
   cudaError_t e = (fp->prec == SX_PREC_FP32) ? alloc_plan<float>(*fp) : alloc_plan<double>(*fp);
   if (e == cudaSuccess) e = (fp->prec == SX_PREC_FP32) ? build_kernel<float>(c, *fp) : build_kernel<double>(c, *fp);
@@ -1104,7 +1182,7 @@ int fft_plan(sx_ctx *c) {
     fft_free(c);
     return cuda_error(e, "FFT plan");
   }
-  c->launches_per_step = 2 * (3 + 2 * (fp->n[1] > 1));
+  c->launches_per_step = 2 * (3 + 2 * (fp->n[1] > 1)) - 1;
   return SX_OK;
 }
 
