@@ -532,6 +532,127 @@ def _profile_batch(argv):
     print(json.dumps(out))
 
 
+def _profile_field(argv):
+    """field [WORKLOAD=dense7] [N=100] [BACKENDS=igemm_tc/tf32,igemm_tc/bf16,stencil/fp32,gather/fp32,fft/fp32]
+    [REPS=20]: time the field (FP64 output, on-site terms) of one backend after another on seeded random spins of an
+    N^3 lattice.  dense7 is a 3x3 tensor coupling on every offset of the 7x7x7 window (workloads.dense_window_bonds);
+    other names are the workloads of this file."""
+    import torch
+    import paper_2605_26016_gb300 as sx
+    from workloads import cubic_cell, dense_window_bonds, random_spins_torch
+    name = argv[0] if len(argv) > 0 else "dense7"
+    n = (int(argv[1]),) * 3 if len(argv) > 1 else (100, 100, 100)
+    backends = (argv[2] if len(argv) > 2 else "igemm_tc/tf32,igemm_tc/bf16,stencil/fp32,gather/fp32,fft/fp32").split(",")
+    reps = int(argv[3]) if len(argv) > 3 else 20
+
+    def system():
+        if name == "dense7":
+            s = sx.SpinSystem(n, (1, 1, 1), cubic_cell(), [[0, 0, 0]], [1.0])
+            s.add_bonds(dense_window_bonds())
+            return s
+        return sx.system_from_workload(name, n)[0]
+
+    s0 = system()
+    S = random_spins_torch(s0.nsub, n, 1)
+    out = torch.empty_like(S)
+    res = {"profile": "field", "workload": f"{name} {n[0]}x{n[1]}x{n[2]}", "nsite": s0.nsite}
+    s0.close()
+    for bp in backends:
+        backend, prec = bp.split("/")
+        s = system()
+        try:
+            s.plan(backend, prec)
+        except sx.SxError as e:
+            res[bp] = f"unsupported: {e}"
+            continue
+        for _ in range(3):
+            s.field(S, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            s.field(S, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        res[bp] = {"us": 1e3 * e0.elapsed_time(e1) / reps}
+        s.close()
+    print(json.dumps(res))
+
+
+def _profile_ensemble(argv):
+    """ensemble [WORKLOAD=bcc_4shell] [NREP=64] [LMIN=24] [LMAX=96] [STEPS=20] [NIMG=32] [IMG_L=64] [SEED=4]: uneven
+    replicas (cubes of L^3 cells, L ~ U{LMIN..LMAX}) advanced STEPS Heun steps plus the field of NIMG chain images
+    (IMG_L^3 cells): one persistent sx_batch_run against per-step batched launches plus one field launch per image,
+    and against one launch pair per replica and step."""
+    import numpy as np
+    import torch
+    import paper_2605_26016_gb300 as sx
+    from workloads import random_spins
+    name = argv[0] if len(argv) > 0 else "bcc_4shell"
+    nrep = int(argv[1]) if len(argv) > 1 else 64
+    lmin = int(argv[2]) if len(argv) > 2 else 24
+    lmax = int(argv[3]) if len(argv) > 3 else 96
+    steps = int(argv[4]) if len(argv) > 4 else 20
+    nimg = int(argv[5]) if len(argv) > 5 else 32
+    limg = int(argv[6]) if len(argv) > 6 else 64
+    seed = int(argv[7]) if len(argv) > 7 else 4
+    rng = np.random.default_rng(seed)
+    edges = rng.integers(lmin, lmax + 1, size=nrep)
+    systems = []
+    for L in edges:
+        s, w = sx.system_from_workload(name, (int(L), int(L), int(L)))
+        sx.sx_set_stencil_scheme(s.ctx, "two_pass")
+        s.plan("stencil", "fp32")
+        systems.append(s)
+    img_s, _ = sx.system_from_workload(name, (limg, limg, limg))
+    img_s.plan("stencil", "fp32")
+    nsite = sum(s.nsite for s in systems)
+    batch = sx.Batch(systems, image_system=img_s, nimg=nimg)
+    p = sx.llg_params(w["dt"], w["alpha"], w["T"], seed=seed)
+    A = [torch.from_numpy(random_spins(s.nsub, s.n, 100 + r)).cuda() for r, s in enumerate(systems)]
+    B = [torch.empty_like(x) for x in A]
+    images = torch.from_numpy(np.stack([random_spins(img_s.nsub, img_s.n, 500 + k) for k in range(nimg)])).cuda()
+    fields = torch.empty_like(images)
+    batch.bind(A, B, images, fields)
+    state = {"A": A, "B": B}
+
+    def run_combined(k0):
+        batch.run(p, k0, steps)
+
+    def run_batched(k0):
+        for k in range(steps):
+            batch.heun_step(state["A"], state["B"], p, k0 + k)
+            state["A"], state["B"] = state["B"], state["A"]
+        for k in range(nimg):
+            img_s.field(images[k], out=fields[k])
+
+    def run_single(k0):
+        for k in range(steps):
+            for r, s in enumerate(systems):
+                pr = sx.llg_params(w["dt"], w["alpha"], w["T"], seed=seed, replica=r)
+                sx.sx_llg_heun_step_out(s.ctx, state["A"][r], state["B"][r], pr, k0 + k, s.nsite)
+            state["A"], state["B"] = state["B"], state["A"]
+        for k in range(nimg):
+            img_s.field(images[k], out=fields[k])
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"profile": "ensemble", "workload": f"{name}: {nrep} replicas, L ~ U{{{lmin}..{lmax}}} cells, {nsite} spins, "
+           f"{steps} steps; {nimg} images of {limg}^3 cells", "persistent": batch.info()["persistent"]}
+    for label, fn in (("one_persistent_launch", run_combined), ("batched_launch_pairs_plus_field_per_image",
+                                                                 run_batched),
+                      ("launch_pair_per_replica_plus_field_per_image", run_single)):
+        fn(0)
+        torch.cuda.synchronize()
+        e0.record()
+        fn(1000)
+        e1.record()
+        torch.cuda.synchronize()
+        batch.status()
+        ms = e0.elapsed_time(e1)
+        out[label] = {"ms": ms, "replica_spin_steps_per_s": nsite * steps / (ms * 1e-3)}
+    print(json.dumps(out))
+
+
 def _profile_cnn(argv):
     """cnn [NX,NY,NZ=64,64,64] [BATCH=30] [REPEATS=20] [MODE=both|forward|train]: the chain proposer's
     inference and one training step on seeded random unit fields."""
@@ -585,7 +706,7 @@ def _profile_cnn(argv):
 
 
 PROFILES = {"step": _profile_step, "min": _profile_min, "path": _profile_path, "batch": _profile_batch,
-            "cnn": _profile_cnn}
+            "ensemble": _profile_ensemble, "field": _profile_field, "cnn": _profile_cnn}
 
 
 def main():

@@ -296,6 +296,47 @@ void sx_batch_destroy(sx_batch *b);
 int sx_batch_heun_step(sx_batch *b, const double *const *S_in, double *const *S_out, const sx_llg_params *p,
                        uint64_t step, void *stream);
 
+/* Ensembles and minimum-energy-path chains in one launch (ensemble scaling of
+ * "GPU performance regimes and scaling"; the images of "Static optimization
+ * and minimum-energy paths").  A batch created with images also owns nimg
+ * spin fields of img_ctx's lattice (a planned STENCIL context with the
+ * replicas' lattice family and couplings; it may be one of the replicas),
+ * whose fields sx_batch_run evaluates next to the replicas' steps.  Errors as
+ * sx_batch_create; SX_ERR_ARG for nimg outside 1..65536. */
+int sx_batch_create_with_images(sx_batch **out, sx_ctx *const *ctxs, int nrep, sx_ctx *img_ctx, int nimg);
+
+/* Bind the device buffers of sx_batch_run (host arrays of nrep device
+ * pointers): replica r alternates between S_a[r] and S_b[r] (no overlap) and
+ * draws its noise with replica index replica0 + r; image k is images + k *
+ * 3 nsite_img (doubles, layout of sx_field) and its field, FP64 with on-site
+ * terms, goes to fields + k * 3 nsite_img (images and fields NULL for a
+ * batch without images).  Uploads the unit table once; synchronous.  The
+ * buffers must outlive every sx_batch_run that uses them. */
+int sx_batch_bind(sx_batch *b, double *const *S_a, double *const *S_b, const double *images, double *fields,
+                  uint32_t replica0);
+
+/* nsteps >= 1 Heun steps (counters step0 .. step0 + nsteps - 1) of every
+ * bound replica, S_a -> S_b -> S_a ... (the result is in S_b[r] for odd
+ * nsteps, else in S_a[r]), and the field of every bound image, evaluated in
+ * the first step's predictor phase.  One persistent cooperative launch: its
+ * CTAs walk a balanced schedule of the column-plane units of all replicas and
+ * images, with a grid barrier after each predictor and corrector phase; the
+ * barrier waits are bounded and report through sx_batch_status.  When the
+ * schedule's CTAs cannot all be resident, the same units run as one launch
+ * per phase.  Bit-identical to sx_batch_heun_step steps and sx_field calls.
+ * No allocation, no host copy and no synchronisation: a call can be captured
+ * in a CUDA graph.  SX_ERR_STATE before sx_batch_bind or after a re-plan. */
+int sx_batch_run(sx_batch *b, const sx_llg_params *p, uint64_t step0, int nsteps, void *stream);
+
+/* Synchronise the stream.  SX_ERR_TIMEOUT if a grid barrier of sx_batch_run
+ * gave up since the last check (its results are invalid), SX_ERR_NUMERIC if a
+ * replica state update met a non-finite or zero-length spin, else SX_OK. */
+int sx_batch_status(sx_batch *b, void *stream);
+
+/* out[0] replicas, out[1] images, out[2] 1 when sx_batch_run is one
+ * persistent launch (0: one launch per phase), out[3] reserved (0). */
+int sx_batch_info(const sx_batch *b, int64_t out[4]);
+
 /* Synchronise the stream and report whether a bounded device wait of this
  * context's kernels gave up since the last check (tensor-core MMA waits, the
  * grid barrier of the persistent multi-step stencil launch): SX_ERR_TIMEOUT

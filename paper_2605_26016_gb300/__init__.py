@@ -32,7 +32,8 @@ EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shel
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
            "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise", "sx_path_step",
            "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune", "sx_device_status",
-           "sx_batch_create", "sx_batch_destroy", "sx_batch_heun_step",
+           "sx_batch_create", "sx_batch_destroy", "sx_batch_heun_step", "sx_batch_create_with_images",
+           "sx_batch_bind", "sx_batch_run", "sx_batch_status", "sx_batch_info",
            "sx_cnn_num_params", "sx_cnn_create", "sx_cnn_destroy", "sx_cnn_set_params", "sx_cnn_get_params",
            "sx_cnn_pack", "sx_cnn_forward", "sx_cnn_loss_grad", "sx_cnn_adam_step", "sx_cnn_interpolate",
            "sx_cnn_propose")
@@ -137,6 +138,12 @@ def lib():
             "sx_batch_destroy": (None, [vp]),
             "sx_batch_heun_step": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                   ctypes.POINTER(sx_llg_params), ctypes.c_uint64, vp]),
+            "sx_batch_create_with_images": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, vp,
+                                                           ctypes.c_int]),
+            "sx_batch_bind": (ctypes.c_int, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, ctypes.c_uint32]),
+            "sx_batch_run": (ctypes.c_int, [vp, ctypes.POINTER(sx_llg_params), ctypes.c_uint64, ctypes.c_int, vp]),
+            "sx_batch_status": (ctypes.c_int, [vp, vp]),
+            "sx_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
             "sx_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_int, dp, vp]),
             "sx_cnn_num_params": (i64, []),
             "sx_cnn_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -381,14 +388,22 @@ def sx_geodesic(ctx, A, B, nsite, stream=None):
 
 class Batch:
     """Replicas sharing one Hamiltonian (SpinSystem objects with stencil plans), advanced together by
-    sx_batch_heun_step.  Keeps the systems alive while it exists."""
+    sx_batch_heun_step, and optionally nimg images of `image_system`'s lattice whose fields sx_batch_run
+    evaluates in the same launch.  Keeps the systems (and the buffers given to bind) alive while it exists."""
 
-    def __init__(self, systems):
+    def __init__(self, systems, image_system=None, nimg=0):
         self.systems = list(systems)
+        self.image_system = image_system
+        self.nimg = nimg if image_system is not None else 0
         arr = (ctypes.c_void_p * len(self.systems))(*[s.ctx for s in self.systems])
         h = ctypes.c_void_p()
-        _chk(lib().sx_batch_create(ctypes.byref(h), arr, len(self.systems)), "sx_batch_create")
+        if image_system is None:
+            _chk(lib().sx_batch_create(ctypes.byref(h), arr, len(self.systems)), "sx_batch_create")
+        else:
+            _chk(lib().sx_batch_create_with_images(ctypes.byref(h), arr, len(self.systems), image_system.ctx, int(nimg)),
+                 "sx_batch_create_with_images")
         self.h = h
+        self._bound = None
 
     def close(self):
         if getattr(self, "h", None):
@@ -400,6 +415,31 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def bind(self, S_a, S_b, images=None, fields=None, replica0=0):
+        """Device buffers of run(): replica r alternates between S_a[r] and S_b[r]; images (nimg x 3 x
+        nsite of the image system, float64) in, their FP64 fields out."""
+        n = len(self.systems)
+        a = (ctypes.c_void_p * n)(*[_dev_ptr(x, 3 * s.nsite).value for x, s in zip(S_a, self.systems)])
+        b = (ctypes.c_void_p * n)(*[_dev_ptr(x, 3 * s.nsite).value for x, s in zip(S_b, self.systems)])
+        ip = fp = None
+        if self.nimg:
+            m = self.nimg * 3 * self.image_system.nsite
+            ip, fp = _dev_ptr(images, m), _dev_ptr(fields, m)
+        _chk(lib().sx_batch_bind(self.h, a, b, ip, fp, int(replica0)), "sx_batch_bind")
+        self._bound = (list(S_a), list(S_b), images, fields)
+
+    def run(self, params, step0, nsteps, stream=None):
+        return _chk(lib().sx_batch_run(self.h, ctypes.byref(params), int(step0), int(nsteps), _stream(stream)),
+                    "sx_batch_run")
+
+    def status(self, stream=None):
+        return _chk(lib().sx_batch_status(self.h, _stream(stream)), "sx_batch_status")
+
+    def info(self):
+        out = (ctypes.c_int64 * 4)()
+        _chk(lib().sx_batch_info(self.h, out), "sx_batch_info")
+        return {"replicas": out[0], "images": out[1], "persistent": bool(out[2])}
 
     def heun_step(self, S_in, S_out, params, step, stream=None):
         n = len(self.systems)

@@ -603,12 +603,17 @@ struct sx_batch {
   sx::StencilBatch *sb;
   std::vector<sx_ctx *> ctxs;
   std::vector<int> plan_gens;
+  sx_ctx *img_ctx;
+  int img_gen;
+  int nimg;
 };
 
-int sx_batch_create(sx_batch **out, sx_ctx *const *ctxs, int nrep) {
+namespace {
+int batch_create(sx_batch **out, sx_ctx *const *ctxs, int nrep, sx_ctx *img_ctx, int nimg) {
   if (!out) return set_error(SX_ERR_ARG, "null output");
   *out = nullptr;
   if (!ctxs || nrep < 1 || nrep > 65536) return set_error(SX_ERR_ARG, "a batch needs 1 .. 65536 contexts");
+  if (img_ctx && (nimg < 1 || nimg > 65536)) return set_error(SX_ERR_ARG, "nimg must be in 1 .. 65536");
   for (int r = 0; r < nrep; ++r) {
     int rc = check_ready(ctxs[r]);
     if (rc) return rc;
@@ -616,6 +621,12 @@ int sx_batch_create(sx_batch **out, sx_ctx *const *ctxs, int nrep) {
       return set_error(SX_ERR_UNSUPPORTED, "batched steps run on STENCIL plans only");
     for (int q = 0; q < r; ++q)
       if (ctxs[q] == ctxs[r]) return set_error(SX_ERR_ARG, "a context appears twice in the batch");
+  }
+  if (img_ctx) {
+    int rc = check_ready(img_ctx);
+    if (rc) return rc;
+    if (img_ctx->backend != SX_BACKEND_STENCIL)
+      return set_error(SX_ERR_UNSUPPORTED, "batched images run on STENCIL plans only");
   }
   int cur = 0;
   cudaGetDevice(&cur);
@@ -630,7 +641,7 @@ int sx_batch_create(sx_batch **out, sx_ctx *const *ctxs, int nrep) {
     }
   }
   sx::StencilBatch *sb = nullptr;
-  const int rc = stencil_batch_create(&sb, ctxs, nrep);
+  const int rc = stencil_batch_create(&sb, ctxs, nrep, img_ctx, img_ctx ? nimg : 0);
   cudaSetDevice(cur);
   if (rc != SX_OK) return rc;
   sx_batch *b = new (std::nothrow) sx_batch();
@@ -641,8 +652,36 @@ int sx_batch_create(sx_batch **out, sx_ctx *const *ctxs, int nrep) {
   b->sb = sb;
   b->ctxs.assign(ctxs, ctxs + nrep);
   for (int r = 0; r < nrep; ++r) b->plan_gens.push_back(ctxs[r]->plan_gen);
+  b->img_ctx = img_ctx;
+  b->img_gen = img_ctx ? img_ctx->plan_gen : 0;
+  b->nimg = img_ctx ? nimg : 0;
   *out = b;
   return SX_OK;
+}
+
+int batch_check_plans(const sx_batch *b) {
+  for (size_t r = 0; r < b->ctxs.size(); ++r) {
+    const sx_ctx *c = b->ctxs[r];
+    int rc = check_ready(c);
+    if (rc) return rc;
+    if (c->plan_gen != b->plan_gens[r] || stencil_scheme(c) != SX_STENCIL_TWO_PASS)
+      return set_error(SX_ERR_STATE, "a batched context was re-planned: create the batch again");
+  }
+  if (b->img_ctx) {
+    int rc = check_ready(b->img_ctx);
+    if (rc) return rc;
+    if (b->img_ctx->plan_gen != b->img_gen)
+      return set_error(SX_ERR_STATE, "the image context was re-planned: create the batch again");
+  }
+  return SX_OK;
+}
+}  // namespace
+
+int sx_batch_create(sx_batch **out, sx_ctx *const *ctxs, int nrep) { return batch_create(out, ctxs, nrep, nullptr, 0); }
+
+int sx_batch_create_with_images(sx_batch **out, sx_ctx *const *ctxs, int nrep, sx_ctx *img_ctx, int nimg) {
+  if (!img_ctx) return set_error(SX_ERR_ARG, "null image context");
+  return batch_create(out, ctxs, nrep, img_ctx, nimg);
 }
 
 void sx_batch_destroy(sx_batch *b) {
@@ -654,22 +693,74 @@ void sx_batch_destroy(sx_batch *b) {
 int sx_batch_heun_step(sx_batch *b, const double *const *S_in, double *const *S_out, const sx_llg_params *p,
                        uint64_t step, void *stream) {
   if (!b || !S_in || !S_out) return set_error(SX_ERR_ARG, "null argument");
+  int rc = batch_check_plans(b);
+  if (rc) return rc;
   const int nrep = (int)b->ctxs.size();
   for (int r = 0; r < nrep; ++r) {
     const sx_ctx *c = b->ctxs[r];
-    int rc = check_ready(c);
-    if (rc) return rc;
-    if (c->plan_gen != b->plan_gens[r] || stencil_scheme(c) != SX_STENCIL_TWO_PASS)
-      return set_error(SX_ERR_STATE, "a batched context was re-planned: create the batch again");
     if ((rc = check_spin_ptr(S_in[r], "S_in")) || (rc = check_spin_ptr(S_out[r], "S_out"))) return rc;
     if (overlaps(S_in[r], S_out[r], 3 * (size_t)c->geo.nsite * sizeof(double)))
       return set_error(SX_ERR_ARG, "S_in and S_out of a replica overlap");
   }
   HeunConst h;
-  int rc = make_heun_const(b->ctxs[0], p, h);
+  rc = make_heun_const(b->ctxs[0], p, h);
   if (rc) return rc;
   cudaError_t e = stencil_batch_step(b->sb, S_in, S_out, h, step, (cudaStream_t)stream);
   return e == cudaSuccess ? SX_OK : cuda_error(e, "batched Heun step");
+}
+
+int sx_batch_bind(sx_batch *b, double *const *S_a, double *const *S_b, const double *images, double *fields,
+                  uint32_t replica0) {
+  if (!b || !S_a || !S_b) return set_error(SX_ERR_ARG, "null argument");
+  int rc = batch_check_plans(b);
+  if (rc) return rc;
+  const int nrep = (int)b->ctxs.size();
+  for (int r = 0; r < nrep; ++r) {
+    const size_t bytes = 3 * (size_t)b->ctxs[r]->geo.nsite * sizeof(double);
+    if ((rc = check_spin_ptr(S_a[r], "S_a")) || (rc = check_spin_ptr(S_b[r], "S_b"))) return rc;
+    if (overlaps(S_a[r], S_b[r], bytes)) return set_error(SX_ERR_ARG, "S_a and S_b of a replica overlap");
+  }
+  if (b->nimg > 0) {
+    if ((rc = check_spin_ptr(images, "images")) || (rc = check_spin_ptr(fields, "fields"))) return rc;
+    const size_t bytes = (size_t)b->nimg * 3 * (size_t)b->img_ctx->geo.nsite * sizeof(double);
+    if (overlaps(images, fields, bytes)) return set_error(SX_ERR_ARG, "images and fields overlap");
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(b->ctxs[0]->device);
+  rc = stencil_batch_bind(b->sb, S_a, S_b, images, fields, replica0);
+  cudaSetDevice(cur);
+  return rc;
+}
+
+int sx_batch_run(sx_batch *b, const sx_llg_params *p, uint64_t step0, int nsteps, void *stream) {
+  if (!b) return set_error(SX_ERR_ARG, "null batch");
+  if (nsteps < 1) return set_error(SX_ERR_ARG, "nsteps must be >= 1");
+  int rc = batch_check_plans(b);
+  if (rc) return rc;
+  if (!stencil_batch_bound(b->sb)) return set_error(SX_ERR_STATE, "sx_batch_bind must precede sx_batch_run");
+  HeunConst h;
+  if ((rc = make_heun_const(b->ctxs[0], p, h))) return rc;
+  const cudaError_t e = stencil_batch_run(b->sb, h, step0, nsteps, (cudaStream_t)stream);
+  return e == cudaSuccess ? SX_OK : cuda_error(e, "batched run");
+}
+
+int sx_batch_status(sx_batch *b, void *stream) {
+  if (!b) return set_error(SX_ERR_ARG, "null batch");
+  const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "batch status");
+  if (stencil_batch_check_error(b->sb))
+    return set_error(SX_ERR_TIMEOUT, "a grid barrier of sx_batch_run gave up; its results are invalid");
+  return take_status(b->ctxs[0], (cudaStream_t)stream);
+}
+
+int sx_batch_info(const sx_batch *b, int64_t out[4]) {
+  if (!b || !out) return set_error(SX_ERR_ARG, "null argument");
+  out[0] = (int64_t)b->ctxs.size();
+  out[1] = b->nimg;
+  out[2] = stencil_batch_persistent(b->sb);
+  out[3] = 0;
+  return SX_OK;
 }
 
 int sx_device_status(sx_ctx *c, void *stream) {
@@ -700,6 +791,8 @@ int sx_field(sx_ctx *c, const double *S, void *b, int out_prec, void *stream) {
     e = backend_field(c, S, static_cast<double *>(b), true, st);
   } else if (c->backend == SX_BACKEND_STENCIL) {
     e = stencil_field_f32(c, S, static_cast<float *>(b), true, st);
+  } else if (c->backend == SX_BACKEND_IGEMM_TC) {
+    e = tc_field_f32(c, S, static_cast<float *>(b), true, st);
   } else {
     e = backend_field(c, S, c->d_field, true, st);
     if (e == cudaSuccess) e = to_f32(c->d_field, static_cast<float *>(b), (int64_t)n3, st);

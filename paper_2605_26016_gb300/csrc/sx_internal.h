@@ -198,7 +198,14 @@ cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S
 int stencil_check_error(const sx_ctx *c);
 // batches of replicas sharing one coupling table (two-pass stencil plans)
 struct StencilBatch;
-int stencil_batch_create(StencilBatch **out, sx_ctx *const *ctxs, int nrep);
+// replicas ctxs[0..nrep) and, when img_ctx is set, nimg images of img_ctx's lattice (field only)
+int stencil_batch_create(StencilBatch **out, sx_ctx *const *ctxs, int nrep, const sx_ctx *img_ctx, int nimg);
+int stencil_batch_bind(StencilBatch *b, double *const *S_a, double *const *S_b, const double *images,
+                       double *fields, uint32_t replica0);
+int stencil_batch_bound(const StencilBatch *b);
+int stencil_batch_persistent(const StencilBatch *b);
+cudaError_t stencil_batch_run(StencilBatch *b, const HeunConst &h, uint64_t step0, int nsteps, cudaStream_t st);
+int stencil_batch_check_error(StencilBatch *b);
 void stencil_batch_free(StencilBatch *b);
 cudaError_t stencil_batch_step(StencilBatch *b, const double *const *S_in, double *const *S_out, const HeunConst &h,
                                uint64_t step, cudaStream_t st);
@@ -238,6 +245,7 @@ int minimise(sx_ctx *c, double *S, double *S_scratch, const sx_min_params *p, in
 int tc_plan(sx_ctx *c);
 void tc_free(sx_ctx *c);
 cudaError_t tc_field(const sx_ctx *c, const double *S, double *b, bool onsite, cudaStream_t st);
+cudaError_t tc_field_f32(const sx_ctx *c, const double *S, float *b, bool onsite, cudaStream_t st);
 cudaError_t tc_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                          cudaStream_t st);
 int tc_check_error(const sx_ctx *c);

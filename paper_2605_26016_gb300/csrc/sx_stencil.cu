@@ -946,8 +946,10 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
 
 // ------------------------------------------------------------------ batches of replicas
 
-// One replica of a batch: its geometry, its noise replica index, the first global
-// column-plane unit it owns, and its state and two-pass workspace.
+// One unit owner of a batch: a replica (Heun step) or an image of a chain (field only), with its
+// geometry, its noise replica index, the first global column-plane unit it owns, its state
+// (replicas: S and Sout, swapped on odd steps of a multi-step run) and two-pass workspace, or its
+// field output (images).
 struct SGeo {
   int nx, ny, nz, px, py, pz;
   long long nsite;
@@ -959,21 +961,23 @@ struct BatchRep {
   const double *S;
   double *Sout;
   float *St, *f0, *eta;
+  double *b;  // images: field output (FP64, on-site terms included)
+  int kind;   // 0: replica, 1: image
+  int pad;
 };
 
-// One two-pass stage over a batch of replicas that share the couplings in p: CTA k
-// walks the global column-plane units of schedule entry k, which may span replicas
-// (units are replica-major; within a replica u = column * nz + z).
+// The units [e.x, e.x + e.y) of one schedule entry, which may span owners (units are owner-major;
+// within an owner u = column * nz + z).  Replicas run MODE with the state roles swapped when
+// parity is 1; images run the field pass in the predictor phase when `images` is set and are
+// skipped otherwise.
 template <int FID, int MODE>
-__global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
-    k_batch_pass(const StencilArgs p, const BatchRep *__restrict__ reps, int nrep, const int2 *__restrict__ sched,
-                 unsigned long long step) {
+__device__ __forceinline__ void batch_units(const StencilArgs &p, const BatchRep *__restrict__ reps, int nrep,
+                                            int2 e, unsigned long long step, int parity, bool images,
+                                            unsigned char *smem_raw) {
   using F = Family<FID>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int2 e = sched[blockIdx.x];
   long long u = e.x;
   const long long uend = (long long)e.x + e.y;
-  int lo = 0, hi = nrep - 1;  // last replica with u0 <= u
+  int lo = 0, hi = nrep - 1;  // last owner with u0 <= u
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
     if (reps[mid].u0 <= u)
@@ -985,25 +989,72 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
   while (u < uend) {  // uniform over the block
     while (r + 1 < nrep && reps[r + 1].u0 <= u) ++r;
     const SGeo gg = reps[r].g;
-    PassIO io;
-    io.S = reps[r].S;
-    io.St = reps[r].St;
-    io.St_out = reps[r].St;
-    io.b = nullptr;
-    io.f0 = reps[r].f0;
-    io.eta = reps[r].eta;
-    io.Sout = reps[r].Sout;
-    io.nzc = 1;
-    io.istride = 0;
-    io.step = step;
-    io.sched = nullptr;
     const long long ul = u - reps[r].u0;
     const int ncx = (gg.nx + 31) / 32;
     const int col = (int)(ul / gg.nz), z = (int)(ul - (long long)col * gg.nz);
     const int len = (int)min((long long)(gg.nz - z), uend - u);
-    pass_segment<FID, MODE>(p, gg, 1, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+    PassIO io;
+    io.nzc = 1;
+    io.istride = 0;
+    io.step = step;
+    io.sched = nullptr;
+    io.bf = nullptr;
+    if (reps[r].kind == 0) {
+      io.S = parity ? reps[r].Sout : reps[r].S;
+      io.Sout = parity ? const_cast<double *>(reps[r].S) : reps[r].Sout;
+      io.St = reps[r].St;
+      io.St_out = reps[r].St;
+      io.b = nullptr;
+      io.f0 = reps[r].f0;
+      io.eta = reps[r].eta;
+      pass_segment<FID, MODE>(p, gg, 1, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+    } else if (MODE == PASS_PRED && images) {
+      io.S = reps[r].S;
+      io.Sout = nullptr;
+      io.St = nullptr;
+      io.St_out = nullptr;
+      io.b = reps[r].b;
+      io.f0 = nullptr;
+      io.eta = nullptr;
+      pass_segment<FID, PASS_FIELD>(p, gg, 1, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+    }
     u += len;
     __syncthreads();  // shared memory is reused by the next segment
+  }
+}
+
+// One two-pass stage over a batch of owners that share the couplings in p: CTA k walks the
+// global column-plane units of schedule entry k.
+template <int FID, int MODE>
+__global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
+    k_batch_pass(const StencilArgs p, const BatchRep *__restrict__ reps, int nrep, const int2 *__restrict__ sched,
+                 unsigned long long step, int parity, int images) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  batch_units<FID, MODE>(p, reps, nrep, sched[blockIdx.x], step, parity, images != 0, smem_raw);
+}
+
+// nsteps Heun steps of every replica and the field of every image in one cooperative launch:
+// step k runs the predictor units of all replicas (plus, at k = 0, the field units of all
+// images), a grid barrier, the corrector units, a grid barrier.  Replica states alternate
+// S -> Sout -> S ...  Same per-site arithmetic as the separate launches, so bit-identical to them.
+// Two schedules over the same owner list: `sched_all` (replicas and images) for the first
+// predictor phase, `sched_rep` (replicas only, whose units come first) for every other phase, each
+// balanced on its own; a CTA past the end of a schedule idles through that phase.
+template <int FID>
+__global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
+    k_batch_persistent(const StencilArgs p, const BatchRep *__restrict__ reps, int nown,
+                       const int2 *__restrict__ sched_all, int nall, const int2 *__restrict__ sched_rep, int nrsch,
+                       unsigned long long step0, int nsteps, GridBar *gb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 none = make_int2(0, 0);
+  const int2 ea = (int)blockIdx.x < nall ? sched_all[blockIdx.x] : none;
+  const int2 er = (int)blockIdx.x < nrsch ? sched_rep[blockIdx.x] : none;
+  for (int k = 0; k < nsteps; ++k) {
+    batch_units<FID, PASS_PRED>(p, reps, nown, k == 0 ? ea : er, step0 + (unsigned long long)k, k & 1, k == 0,
+                                smem_raw);
+    if (!grid_sync(gb, gridDim.x)) return;
+    batch_units<FID, PASS_CORR>(p, reps, nown, er, step0 + (unsigned long long)k, k & 1, false, smem_raw);
+    if (!grid_sync(gb, gridDim.x)) return;
   }
 }
 
@@ -1100,6 +1151,9 @@ cudaError_t set_smem() {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GF<Family<FID>>::SMEM);
     if (e != cudaSuccess) return e;
   }
+  e = cudaFuncSetAttribute(k_batch_persistent<FID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)GF<Family<FID>>::SMEM);
+  if (e != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -1601,12 +1655,22 @@ cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S
 // ------------------------------------------------------------------ batches (host)
 
 struct StencilBatch {
-  int nrep = 0, family = -1;
+  int nrep = 0, nimg = 0, family = -1;
   const sx_ctx *proto = nullptr;
-  std::vector<BatchRep> h_reps;
+  std::vector<BatchRep> h_reps;  // replicas (the per-step schedule)
   BatchRep *d_reps = nullptr;
   int2 *d_sched = nullptr;
   int nsched = 0;
+  // sx_batch_run: replicas then images, bound once; own schedule sized for the persistent kernel
+  std::vector<BatchRep> h_run;
+  BatchRep *d_run = nullptr;
+  int2 *d_rsched = nullptr;      // replicas and images (first predictor phase)
+  int nrsched = 0;
+  int2 *d_rsched_rep = nullptr;  // replicas only (every other phase)
+  int nrsched_rep = 0;
+  int persistent = 0;  // 1: the nrsched CTAs of the persistent kernel are resident at once
+  int bound = 0;
+  GridBar *d_bar = nullptr;
 };
 
 namespace {
@@ -1620,22 +1684,85 @@ template <int FID>
 cudaError_t launch_batch(const StencilBatch &b, const StencilArgs &a, unsigned long long step, cudaStream_t st) {
   using g = GF<Family<FID>>;
   const dim3 grid(b.nsched), block(32, GF<Family<FID>>::TYT);
-  k_batch_pass<FID, PASS_PRED><<<grid, block, g::SMEM, st>>>(a, b.d_reps, b.nrep, b.d_sched, step);
-  k_batch_pass<FID, PASS_CORR><<<grid, block, g::SMEM, st>>>(a, b.d_reps, b.nrep, b.d_sched, step);
+  k_batch_pass<FID, PASS_PRED><<<grid, block, g::SMEM, st>>>(a, b.d_reps, b.nrep, b.d_sched, step, 0, 0);
+  k_batch_pass<FID, PASS_CORR><<<grid, block, g::SMEM, st>>>(a, b.d_reps, b.nrep, b.d_sched, step, 0, 0);
   return cudaGetLastError();
+}
+
+template <int FID>
+cudaError_t launch_batch_run(const StencilBatch &b, const StencilArgs &a, unsigned long long step0, int nsteps,
+                             cudaStream_t st) {
+  using g = GF<Family<FID>>;
+  const dim3 block(32, GF<Family<FID>>::TYT);
+  const int nown = b.nrep + b.nimg;
+  if (b.persistent) {
+    cudaError_t e = cudaMemsetAsync(b.d_bar, 0, 2 * sizeof(unsigned), st);  // count, gen (err is sticky)
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(std::max(b.nrsched, b.nrsched_rep));
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = g::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_persistent<FID>, a, (const BatchRep *)b.d_run, nown,
+                              (const int2 *)b.d_rsched, b.nrsched, (const int2 *)b.d_rsched_rep, b.nrsched_rep, step0,
+                              nsteps, b.d_bar);
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    if (k == 0)
+      k_batch_pass<FID, PASS_PRED><<<dim3(b.nrsched), block, g::SMEM, st>>>(a, b.d_run, nown, b.d_rsched, step0, 0, 1);
+    else
+      k_batch_pass<FID, PASS_PRED><<<dim3(b.nrsched_rep), block, g::SMEM, st>>>(a, b.d_run, nown, b.d_rsched_rep,
+                                                                               step0 + k, k & 1, 0);
+    k_batch_pass<FID, PASS_CORR><<<dim3(b.nrsched_rep), block, g::SMEM, st>>>(a, b.d_run, nown, b.d_rsched_rep,
+                                                                             step0 + k, k & 1, 0);
+  }
+  return cudaGetLastError();
+}
+
+template <int FID>
+cudaError_t batch_persistent_occupancy(int *occ) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_batch_persistent<FID>, GF<Family<FID>>::NT,
+                                                       GF<Family<FID>>::SMEM);
+}
+
+BatchRep owner_of(const sx_ctx *c, int kind) {
+  BatchRep rep;
+  memset(&rep, 0, sizeof(rep));
+  rep.g.nx = c->geo.nx;
+  rep.g.ny = c->geo.ny;
+  rep.g.nz = c->geo.nz;
+  rep.g.px = c->geo.px;
+  rep.g.py = c->geo.py;
+  rep.g.pz = c->geo.pz;
+  rep.g.nsite = c->geo.nsite;
+  rep.kind = kind;
+  if (kind == 0) {
+    rep.St = c->stencil->d_St;
+    rep.f0 = c->stencil->d_f0;
+    rep.eta = c->stencil->d_eta;
+  }
+  return rep;
 }
 }  // namespace
 
-int stencil_batch_create(StencilBatch **out, sx_ctx *const *ctxs, int nrep) {
+int stencil_batch_create(StencilBatch **out, sx_ctx *const *ctxs, int nrep, const sx_ctx *img_ctx, int nimg) {
   StencilBatch *b = new (std::nothrow) StencilBatch();
   if (!b) return set_error(SX_ERR_OOM, "host allocation failed");
   b->nrep = nrep;
+  b->nimg = img_ctx ? nimg : 0;
   b->proto = ctxs[0];
   b->family = ctxs[0]->stencil->family;
-  std::vector<long long> ncol(nrep);
-  std::vector<int> nz(nrep);
-  long long u0 = 0;
   const int BY = family_by(b->family), R = family_r(b->family);
+  std::vector<long long> ncol, rcol;
+  std::vector<int> nz, rnz;
+  long long u0 = 0;
+  auto columns = [&](const sx_ctx *c) { return (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY); };
   for (int r = 0; r < nrep; ++r) {
     const sx_ctx *c = ctxs[r];
     if (c->stencil->family != b->family || !same_couplings(c->stencil->base, ctxs[0]->stencil->base)) {
@@ -1646,34 +1773,72 @@ int stencil_batch_create(StencilBatch **out, sx_ctx *const *ctxs, int nrep) {
       delete b;
       return set_error(SX_ERR_ARG, "batched replicas must be planned on one device");
     }
-    BatchRep rep;
-    memset(&rep, 0, sizeof(rep));
-    rep.g.nx = c->geo.nx;
-    rep.g.ny = c->geo.ny;
-    rep.g.nz = c->geo.nz;
-    rep.g.px = c->geo.px;
-    rep.g.py = c->geo.py;
-    rep.g.pz = c->geo.pz;
-    rep.g.nsite = c->geo.nsite;
+    BatchRep rep = owner_of(c, 0);
     rep.u0 = u0;
-    rep.St = c->stencil->d_St;
-    rep.f0 = c->stencil->d_f0;
-    rep.eta = c->stencil->d_eta;
-    ncol[r] = (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY);
-    nz[r] = c->geo.nz;
-    u0 += ncol[r] * nz[r];
+    ncol.push_back(columns(c));
+    nz.push_back(c->geo.nz);
+    u0 += ncol.back() * nz.back();
     b->h_reps.push_back(rep);
   }
-  if (u0 >= (1LL << 31)) {
+  long long ru0 = u0;
+  b->h_run = b->h_reps;
+  rcol = ncol;
+  rnz = nz;
+  if (b->nimg > 0) {
+    if (img_ctx->stencil->family != b->family || !same_couplings(img_ctx->stencil->base, ctxs[0]->stencil->base) ||
+        img_ctx->device != ctxs[0]->device) {
+      delete b;
+      return set_error(SX_ERR_ARG, "the images must share the batch's lattice family, couplings and device");
+    }
+    for (int k = 0; k < b->nimg; ++k) {
+      BatchRep rep = owner_of(img_ctx, 1);
+      rep.u0 = ru0;
+      rcol.push_back(columns(img_ctx));
+      rnz.push_back(img_ctx->geo.nz);
+      ru0 += rcol.back() * rnz.back();
+      b->h_run.push_back(rep);
+    }
+  }
+  if (ru0 >= (1LL << 31)) {
     delete b;
     return set_error(SX_ERR_UNSUPPORTED, "batch too large for one schedule (2^31 column-plane units)");
   }
   const StencilPlan &sp0 = *ctxs[0]->stencil;
   std::vector<int2> sch = balanced_schedule_multi(ncol, nz, R, (long long)sp0.nsm * sp0.occ_field);
   b->nsched = (int)sch.size();
-  cudaError_t e = cudaMalloc(&b->d_reps, nrep * sizeof(BatchRep));
+  // the run schedule: as many CTAs as the persistent kernel keeps resident
+  int occ = 0;
+  cudaError_t e = cudaSuccess;
+  switch (b->family) {
+    case FAM_SC6_ISO: e = batch_persistent_occupancy<FAM_SC6_ISO>(&occ); break;
+    case FAM_SC6_TEN: e = batch_persistent_occupancy<FAM_SC6_TEN>(&occ); break;
+    case FAM_SC26_ISO: e = batch_persistent_occupancy<FAM_SC26_ISO>(&occ); break;
+    case FAM_SC26_TEN: e = batch_persistent_occupancy<FAM_SC26_TEN>(&occ); break;
+    case FAM_SC26_SHELL: e = batch_persistent_occupancy<FAM_SC26_SHELL>(&occ); break;
+    case FAM_SC32_ISO: e = batch_persistent_occupancy<FAM_SC32_ISO>(&occ); break;
+    default: e = batch_persistent_occupancy<FAM_BCC4>(&occ); break;
+  }
+  if (e != cudaSuccess || occ < 1) occ = 0;
+  const long long rslots = (long long)sp0.nsm * (occ > 0 ? occ : sp0.occ_field);
+  std::vector<int2> rsch = balanced_schedule_multi(rcol, rnz, R, rslots);
+  std::vector<int2> rsch_rep = balanced_schedule_multi(ncol, nz, R, rslots);
+  b->nrsched = (int)rsch.size();
+  b->nrsched_rep = (int)rsch_rep.size();
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctxs[0]->device);
+  b->persistent = coop && occ > 0 && std::max(b->nrsched, b->nrsched_rep) <= rslots ? 1 : 0;
+  e = cudaMalloc(&b->d_reps, nrep * sizeof(BatchRep));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_sched, sch.size() * sizeof(int2));
   if (e == cudaSuccess) e = cudaMemcpy(b->d_sched, sch.data(), sch.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_run, b->h_run.size() * sizeof(BatchRep));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_rsched, rsch.size() * sizeof(int2));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_rsched, rsch.data(), rsch.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_rsched_rep, rsch_rep.size() * sizeof(int2));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_rsched_rep, rsch_rep.data(), rsch_rep.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(GridBar));
+  if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, sizeof(GridBar));
   if (e != cudaSuccess) {
     stencil_batch_free(b);
     return cuda_error(e, "batch plan");
@@ -1686,6 +1851,10 @@ void stencil_batch_free(StencilBatch *b) {
   if (!b) return;
   cudaFree(b->d_reps);
   cudaFree(b->d_sched);
+  cudaFree(b->d_run);
+  cudaFree(b->d_rsched);
+  cudaFree(b->d_rsched_rep);
+  cudaFree(b->d_bar);
   delete b;
 }
 
@@ -1710,6 +1879,50 @@ cudaError_t stencil_batch_step(StencilBatch *b, const double *const *S_in, doubl
     case FAM_SC32_ISO: return launch_batch<FAM_SC32_ISO>(*b, a, step, st);
     default: return launch_batch<FAM_BCC4>(*b, a, step, st);
   }
+}
+
+int stencil_batch_bind(StencilBatch *b, double *const *S_a, double *const *S_b, const double *images,
+                       double *fields, uint32_t replica0) {
+  for (int r = 0; r < b->nrep; ++r) {
+    b->h_run[r].S = S_a[r];
+    b->h_run[r].Sout = S_b[r];
+    b->h_run[r].g.replica = replica0 + (uint32_t)r;
+  }
+  for (int k = 0; k < b->nimg; ++k) {
+    BatchRep &o = b->h_run[b->nrep + k];
+    const long long n3 = 3 * o.g.nsite;
+    o.S = images + n3 * k;
+    o.b = fields + n3 * k;
+  }
+  const cudaError_t e =
+      cudaMemcpy(b->d_run, b->h_run.data(), b->h_run.size() * sizeof(BatchRep), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "batch bind");
+  b->bound = 1;
+  return SX_OK;
+}
+
+int stencil_batch_bound(const StencilBatch *b) { return b->bound; }
+int stencil_batch_persistent(const StencilBatch *b) { return b->persistent; }
+
+cudaError_t stencil_batch_run(StencilBatch *b, const HeunConst &h, uint64_t step0, int nsteps, cudaStream_t st) {
+  const StencilArgs a = heun_args(b->proto, h, step0);
+  switch (b->family) {
+    case FAM_SC6_ISO: return launch_batch_run<FAM_SC6_ISO>(*b, a, step0, nsteps, st);
+    case FAM_SC6_TEN: return launch_batch_run<FAM_SC6_TEN>(*b, a, step0, nsteps, st);
+    case FAM_SC26_ISO: return launch_batch_run<FAM_SC26_ISO>(*b, a, step0, nsteps, st);
+    case FAM_SC26_TEN: return launch_batch_run<FAM_SC26_TEN>(*b, a, step0, nsteps, st);
+    case FAM_SC26_SHELL: return launch_batch_run<FAM_SC26_SHELL>(*b, a, step0, nsteps, st);
+    case FAM_SC32_ISO: return launch_batch_run<FAM_SC32_ISO>(*b, a, step0, nsteps, st);
+    default: return launch_batch_run<FAM_BCC4>(*b, a, step0, nsteps, st);
+  }
+}
+
+// 1 if a grid barrier of sx_batch_run gave up since the last check (clears it)
+int stencil_batch_check_error(StencilBatch *b) {
+  GridBar h;
+  if (cudaMemcpy(&h, b->d_bar, sizeof(GridBar), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+  if (h.err) cudaMemset(b->d_bar, 0, sizeof(GridBar));
+  return h.err ? 1 : 0;
 }
 
 cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,

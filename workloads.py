@@ -136,6 +136,21 @@ def nlerp_chain(A, B, nimg, jitter=0.0, seed=0):
     return np.ascontiguousarray(out)
 
 
+def dense_window_bonds(seed=9, radius=3):
+    """A 3x3 tensor coupling on every cell offset of the (2 radius + 1)^3 window of one sublattice (the
+    genuinely dense kernel the tensor-core backend is for): J(d) = g I / (1 + |d|^2) + 0.02 G, g and G standard
+    normal from numpy's PCG64 seeded generator, one unordered bond per offset pair (d, -d)."""
+    rng = np.random.default_rng(seed)
+    bonds = []
+    w = 2 * radius + 1
+    for d in np.ndindex(w, w, w):
+        d = tuple(int(v) - radius for v in d)
+        if d > (0, 0, 0):
+            bonds.append((0, 0, d, np.eye(3) * rng.normal() / (1.0 + sum(v * v for v in d))
+                          + 0.02 * rng.normal(size=(3, 3))))
+    return bonds
+
+
 def random_spins_torch(nsub, n, seed, device="cuda"):
     """Uniform random unit spins generated on a torch device (for lattices too large to generate in
     numpy in reasonable time), shape (3, nsub, nz, ny, nx), float64: z = 2u - 1, phi = 2 pi v with u, v
