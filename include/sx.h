@@ -265,13 +265,19 @@ int sx_plan(sx_ctx *ctx, int backend, int precision);
  * two-pass workspace cannot be allocated (the plan is left unchanged). */
 int sx_set_stencil_scheme(sx_ctx *ctx, int scheme);
 
-/* Time the candidate Heun schemes of the plan on the caller's data and keep
- * the fastest: each runs `steps` (>= 1) out-of-place steps S -> S_scratch
+/* Time the candidate tile shapes of the plan on the caller's data and keep
+ * the fastest.  STENCIL: the Heun scheme (SX_STENCIL_FUSED, TWO_PASS), the z
+ * chunk of a CTA, and for the two-pass scheme the launch shape (a z-chunked
+ * grid, or a balanced schedule over 1 or 2 times the resident CTA slots).
+ * IGEMM_TC: the depth of the B-operand ring (2..4) and the CTAs per SM (1 or
+ * 2).  Each candidate runs `steps` (>= 1) out-of-place steps S -> S_scratch
  * (S is not modified; S_scratch is overwritten) after one warm-up step.
- * times_ms (may be NULL) receives the mean step time of SX_STENCIL_FUSED and
- * SX_STENCIL_TWO_PASS (-1 when a scheme was not timed).  Returns the chosen
- * scheme (> 0) or a negative status.  Plans other than STENCIL have a single
- * scheme and return SX_STENCIL_FUSED untimed.  Synchronises the stream. */
+ * times_ms (may be NULL) receives the best mean step time of
+ * SX_STENCIL_FUSED and of SX_STENCIL_TWO_PASS (STENCIL), or the best time in
+ * times_ms[0] (IGEMM_TC); -1 when not timed.  sx_plan_tiles reports the
+ * choice.  Returns the chosen scheme (> 0; SX_STENCIL_FUSED for plans with
+ * one scheme) or a negative status.  Other backends are not timed.
+ * Synchronises the stream. */
 int sx_autotune(sx_ctx *ctx, const double *S, double *S_scratch, const sx_llg_params *p, int steps,
                 double times_ms[2], void *stream);
 
@@ -452,6 +458,13 @@ int sx_torque_max_noalloc(const double *S, const double *b, int64_t nsite, doubl
  * a pure function of (seed, replica, site, step), see sx_llg_params. */
 int sx_thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64_t n, uint64_t step, float *eta_dev,
                        void *stream);
+
+/* Tile shape of the plan (after sx_plan or sx_autotune): out[0] = stencil
+ * scheme (0 for other backends), out[1..3] = output tile extent in x, y, z
+ * (cells; out[3] = 0 when a balanced schedule assigns z ranges), out[4] = CTAs
+ * per launch, out[5] = stencil: schedule factor (0: z-chunked grid),
+ * tensor core: B-operand ring depth.  Zeros for the other backends. */
+int sx_plan_tiles(const sx_ctx *ctx, int64_t out[6]);
 
 /* Plan facts for callers and tests: out[0] = nsite, out[1] = max taps per
  * sublattice, out[2..4] = halo radius per axis (cells), out[5] = backend,

@@ -31,7 +31,7 @@ EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shel
            "sx_add_dmi", "sx_add_bonds", "sx_set_zeeman", "sx_set_anisotropy", "sx_set_dipolar", "sx_get_taps",
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
            "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise", "sx_path_step",
-           "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune", "sx_device_status",
+           "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune", "sx_plan_tiles", "sx_device_status",
            "sx_batch_create", "sx_batch_destroy", "sx_batch_heun_step", "sx_batch_create_with_images",
            "sx_batch_bind", "sx_batch_run", "sx_batch_status", "sx_batch_info",
            "sx_cnn_num_params", "sx_cnn_create", "sx_cnn_destroy", "sx_cnn_set_params", "sx_cnn_get_params",
@@ -145,6 +145,7 @@ def lib():
             "sx_batch_status": (ctypes.c_int, [vp, vp]),
             "sx_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
             "sx_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_int, dp, vp]),
+            "sx_plan_tiles": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
             "sx_cnn_num_params": (i64, []),
             "sx_cnn_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
             "sx_cnn_destroy": (None, [vp]),
@@ -460,8 +461,8 @@ def sx_set_stencil_scheme(ctx, scheme):
 
 
 def sx_autotune(ctx, S, S_scratch, p, nsite, steps=5, stream=None):
-    """Time the stencil Heun schemes on S (unchanged) and keep the fastest; returns
-    (chosen scheme name, {"fused": ms, "two_pass": ms})."""
+    """Time the plan's candidate tile shapes on S (unchanged) and keep the fastest; returns
+    (chosen scheme name, {"fused": ms, "two_pass": ms}) -- for a tensor-core plan "fused" holds the best time."""
     t = (ctypes.c_double * 2)()
     rc = lib().sx_autotune(ctx, _dev_ptr(S, 3 * nsite), _dev_ptr(S_scratch, 3 * nsite), ctypes.byref(p), int(steps),
                            t, _stream(stream))
@@ -469,6 +470,13 @@ def sx_autotune(ctx, S, S_scratch, p, nsite, steps=5, stream=None):
         _chk(rc, "sx_autotune")
     name = {v: k for k, v in STENCIL_SCHEMES.items()}[rc]
     return name, {"fused": t[0], "two_pass": t[1]}
+
+
+def sx_plan_tiles(ctx):
+    out = (ctypes.c_int64 * 6)()
+    _chk(lib().sx_plan_tiles(ctx, out), "sx_plan_tiles")
+    keys = ("scheme", "tile_x", "tile_y", "tile_z", "ctas", "ring_or_schedule")
+    return dict(zip(keys, list(out)))
 
 
 def sx_thermal_normals(seed, replica, site0, n, step, eta, stream=None):

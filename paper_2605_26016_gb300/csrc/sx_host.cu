@@ -563,40 +563,81 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
   HeunConst h;
   if ((rc = make_heun_const(c, p, h))) return rc;
   if (times_ms) times_ms[0] = times_ms[1] = -1.0;
-  if (c->backend != SX_BACKEND_STENCIL) return SX_STENCIL_FUSED;
+  if (c->backend != SX_BACKEND_STENCIL && c->backend != SX_BACKEND_IGEMM_TC) return SX_STENCIL_FUSED;
   cudaStream_t st = (cudaStream_t)stream;
-  const int keep = c->opt_scheme;
-  double best = -1.0;
-  int best_scheme = stencil_scheme(c);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  for (int scheme = SX_STENCIL_FUSED; scheme <= SX_STENCIL_TWO_PASS && e == cudaSuccess; ++scheme) {
-    if (stencil_set_scheme(c, scheme) != SX_OK || stencil_scheme(c) != scheme) continue;  // no workspace
-    if ((e = backend_step(c, S, S_scratch, h, 0, st)) != cudaSuccess) break;
-    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+  // mean step time of the current tile shape: one warm-up step, then `steps` timed steps S -> S_scratch
+  auto time_steps = [&](double *ms_out) {
+    if ((e = backend_step(c, S, S_scratch, h, 0, st)) != cudaSuccess) return;
+    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) return;
     for (int k = 0; k < steps && e == cudaSuccess; ++k) e = backend_step(c, S, S_scratch, h, (uint64_t)k, st);
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    if (e != cudaSuccess) break;
-    const double t = ms / steps;
-    if (times_ms) times_ms[scheme - 1] = t;
-    if (best < 0.0 || t < best) {
-      best = t;
-      best_scheme = scheme;
+    *ms_out = ms / steps;
+  };
+  int result = SX_STENCIL_FUSED;
+  if (c->backend == SX_BACKEND_STENCIL) {
+    // scheme x z chunk x launch shape (z-chunked grid or balanced schedule over 1 or 2 x the CTA slots)
+    const TileChoice keep = stencil_current_tiles(c);
+    const int keep_tz = stencil_fused_tz(c);
+    TileChoice best = keep;
+    double best_ms = -1.0;
+    for (const TileChoice &t : stencil_tile_candidates(c)) {
+      if (e != cudaSuccess) break;
+      if (stencil_apply_tiles(c, t) != SX_OK) continue;  // e.g. no room for the two-pass workspace
+      double ms = 0.0;
+      time_steps(&ms);
+      if (e != cudaSuccess) break;
+      double &slot = times_ms ? times_ms[t.scheme - 1] : ms;
+      if (times_ms && (slot < 0.0 || ms < slot)) slot = ms;
+      if (best_ms < 0.0 || ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
     }
+    stencil_restore_fused_tz(c, keep_tz);  // the two-pass candidates leave the fused chunk as planned
+    const int rc2 = stencil_apply_tiles(c, e == cudaSuccess ? best : keep);
+    if (e == cudaSuccess && rc2 != SX_OK) rc = rc2;
+    c->opt_scheme = stencil_scheme(c);
+    result = stencil_scheme(c);
+  } else {
+    // ring depth x CTAs per SM of the tensor-core tile kernel
+    const TcTiles keep = tc_current_tiles(c);
+    TcTiles best = keep;
+    double best_ms = -1.0;
+    for (const TcTiles &t : tc_tile_candidates(c)) {
+      if (e != cudaSuccess) break;
+      if (tc_apply_tiles(c, t) != SX_OK) continue;
+      double ms = 0.0;
+      time_steps(&ms);
+      if (e != cudaSuccess) break;
+      if (best_ms < 0.0 || ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    tc_apply_tiles(c, e == cudaSuccess ? best : keep);
+    if (times_ms) times_ms[0] = best_ms;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  if (e != cudaSuccess) {
-    stencil_set_scheme(c, keep);
-    return cuda_error(e, "autotune");
-  }
-  c->opt_scheme = best_scheme;
-  if ((rc = stencil_set_scheme(c, best_scheme)) != SX_OK) return rc;
-  return best_scheme;
+  if (e != cudaSuccess) return cuda_error(e, "autotune");
+  if (rc != SX_OK) return rc;
+  return result;
+}
+
+int sx_plan_tiles(const sx_ctx *c, int64_t out[6]) {
+  if (!c || !out) return set_error(SX_ERR_ARG, "null argument");
+  int rc = check_ready(c);
+  if (rc) return rc;
+  for (int k = 0; k < 6; ++k) out[k] = 0;
+  if (c->backend == SX_BACKEND_STENCIL) stencil_tiles_info(c, out);
+  if (c->backend == SX_BACKEND_IGEMM_TC) tc_tiles_info(c, out);
+  return SX_OK;
 }
 
 struct sx_batch {

@@ -196,6 +196,27 @@ bool stencil_persistent_ok(const sx_ctx *c);
 cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S1, const HeunConst &h,
                                           uint64_t step0, int nsteps, cudaStream_t st);
 int stencil_check_error(const sx_ctx *c);
+// Tile shapes searched by sx_autotune.  Stencil: scheme, z chunk (tz), and for the two-pass scheme
+// either a z-chunked grid (sched = 0) or a balanced schedule over sched x the resident CTA slots.
+struct TileChoice {
+  int scheme, tz, sched;
+};
+std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c);
+int stencil_apply_tiles(sx_ctx *c, const TileChoice &t);
+TileChoice stencil_current_tiles(const sx_ctx *c);
+int stencil_fused_tz(const sx_ctx *c);                 // z chunk of the fused step and of single field launches
+void stencil_restore_fused_tz(sx_ctx *c, int tz);
+// out: scheme, tile x, tile y, z chunk (0: schedule), CTAs per launch, schedule factor (0: grid)
+void stencil_tiles_info(const sx_ctx *c, int64_t out[6]);
+// Tensor-core tile layouts searched by sx_autotune: ring depth and CTAs per SM.
+struct TcTiles {
+  int nbuf, ctas;
+};
+std::vector<TcTiles> tc_tile_candidates(const sx_ctx *c);
+int tc_apply_tiles(sx_ctx *c, const TcTiles &t);
+TcTiles tc_current_tiles(const sx_ctx *c);
+// out: 0, tile x, tile y, tile z, persistent CTAs, ring depth
+void tc_tiles_info(const sx_ctx *c, int64_t out[6]);
 // batches of replicas sharing one coupling table (two-pass stencil plans)
 struct StencilBatch;
 // replicas ctxs[0..nrep) and, when img_ctx is set, nimg images of img_ctx's lattice (field only)

@@ -204,6 +204,8 @@ struct StencilPlan {
   int nsched;
   GridBar *d_bar;   // grid barrier and error word of the persistent multi-step kernel
   int persistent;   // 1: nsched CTAs of the persistent kernel fit on the device at once
+  int occ_persist;  // resident CTAs per SM of the persistent kernel (0: not available)
+  int sched_factor; // balanced schedule over sched_factor x the resident CTA slots (0: grid-tiled passes)
   StencilArgs base;
 };
 
@@ -1158,9 +1160,9 @@ cudaError_t set_smem() {
 }
 
 template <int FID>
-cudaError_t launch_heun(const StencilPlan &sp, const StencilArgs &a, const double *src, double *dst,
-                        cudaStream_t st) {
+cudaError_t launch_heun(const StencilPlan &sp, StencilArgs a, const double *src, double *dst, cudaStream_t st) {
   using g = G<Family<FID>>;
+  a.tz = sp.tz;  // the grid and the kernel take the z chunk from the same place
   const dim3 grid((a.nx + g::TX - 1) / g::TX, (a.ny + g::TY - 1) / g::TY, (a.nz + sp.tz - 1) / sp.tz);
   k_heun_fused<FID><<<grid, dim3(32, g::TYT), g::SMEM, st>>>(a, src, dst);
   return cudaGetLastError();
@@ -1517,8 +1519,10 @@ int stencil_plan(sx_ctx *c) {
       cudaGetLastError();
       occ = 0;
     }
+    sp->occ_persist = occ;
     sp->persistent = sp->d_bar && (long long)occ * sp->nsm >= sp->nsched ? 1 : 0;
   }
+  sp->sched_factor = sp->d_sched ? 1 : 0;
   c->stencil = sp;
   const int rc = stencil_set_scheme(c, c->opt_scheme);
   if (rc != SX_OK) {
@@ -1923,6 +1927,123 @@ int stencil_batch_check_error(StencilBatch *b) {
   if (cudaMemcpy(&h, b->d_bar, sizeof(GridBar), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
   if (h.err) cudaMemset(b->d_bar, 0, sizeof(GridBar));
   return h.err ? 1 : 0;
+}
+
+// ------------------------------------------------------------------ tile shapes (autotuner)
+
+namespace {
+template <int FID>
+void fused_tile(int *tx, int *ty) {
+  *tx = G<Family<FID>>::TX;
+  *ty = G<Family<FID>>::TY;
+}
+void fused_tile_of(int fam, int *tx, int *ty) {
+  switch (fam) {
+    case FAM_SC6_ISO: fused_tile<FAM_SC6_ISO>(tx, ty); break;
+    case FAM_SC6_TEN: fused_tile<FAM_SC6_TEN>(tx, ty); break;
+    case FAM_SC26_ISO: fused_tile<FAM_SC26_ISO>(tx, ty); break;
+    case FAM_SC26_TEN: fused_tile<FAM_SC26_TEN>(tx, ty); break;
+    case FAM_SC26_SHELL: fused_tile<FAM_SC26_SHELL>(tx, ty); break;
+    case FAM_SC32_ISO: fused_tile<FAM_SC32_ISO>(tx, ty); break;
+    default: fused_tile<FAM_BCC4>(tx, ty); break;
+  }
+}
+// balanced z-chunk lengths near nz / k
+std::vector<int> chunk_lengths(int nz, int around) {
+  std::vector<int> out;
+  auto add = [&](int tz) {
+    if (tz < 1 || tz > nz) return;
+    const int nchunk = (nz + tz - 1) / tz;
+    tz = (nz + nchunk - 1) / nchunk;  // the balanced length of that chunk count
+    if (std::find(out.begin(), out.end(), tz) == out.end()) out.push_back(tz);
+  };
+  add(around);
+  for (int k : {1, 2, 3, 4, 6, 8}) add((nz + k - 1) / k);
+  for (int tz : {8, 16, 32, 64}) add(tz);
+  return out;
+}
+}  // namespace
+
+std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c) {
+  const StencilPlan &sp = *c->stencil;
+  std::vector<TileChoice> out;
+  for (int tz : chunk_lengths(c->geo.nz, sp.tz)) out.push_back({SX_STENCIL_FUSED, tz, 0});
+  for (int tz : chunk_lengths(c->geo.nz, sp.tz2)) out.push_back({SX_STENCIL_TWO_PASS, tz, 0});
+  const int BY = family_by(sp.family);
+  const long long ncol = (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY);
+  if (ncol * c->geo.nz < (1LL << 31))
+    for (int f : {1, 2}) out.push_back({SX_STENCIL_TWO_PASS, sp.tz2, f});
+  return out;
+}
+
+int stencil_apply_tiles(sx_ctx *c, const TileChoice &t) {
+  StencilPlan &sp = *c->stencil;
+  int rc = stencil_set_scheme(c, t.scheme);
+  if (rc != SX_OK) return rc;
+  if (stencil_scheme(c) != t.scheme) return set_error(SX_ERR_OOM, "two-pass workspace unavailable");
+  if (t.scheme == SX_STENCIL_FUSED) {
+    sp.tz = t.tz;
+    sp.base.tz = t.tz;
+    return SX_OK;
+  }
+  sp.tz2 = t.tz;
+  if (t.sched == sp.sched_factor && (t.sched == 0 || sp.d_sched)) return SX_OK;
+  cudaFree(sp.d_sched);
+  sp.d_sched = nullptr;
+  sp.nsched = 0;
+  sp.persistent = 0;
+  sp.sched_factor = 0;
+  if (t.sched > 0) {
+    const int R = family_r(sp.family), BY = family_by(sp.family);
+    const long long ncol = (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY);
+    const std::vector<int2> sch =
+        balanced_schedule(ncol, c->geo.nz, R, (long long)t.sched * sp.nsm * std::max(sp.occ_field, 1));
+    if (cudaMalloc(&sp.d_sched, sch.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMemcpy(sp.d_sched, sch.data(), sch.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(sp.d_sched);
+      sp.d_sched = nullptr;
+      return set_error(SX_ERR_OOM, "stencil schedule: device allocation failed");
+    }
+    sp.nsched = (int)sch.size();
+    sp.sched_factor = t.sched;
+    sp.persistent = sp.d_bar && sp.occ_persist > 0 && (long long)sp.occ_persist * sp.nsm >= sp.nsched ? 1 : 0;
+  }
+  return SX_OK;
+}
+
+int stencil_fused_tz(const sx_ctx *c) { return c->stencil->tz; }
+void stencil_restore_fused_tz(sx_ctx *c, int tz) {
+  c->stencil->tz = tz;
+  c->stencil->base.tz = tz;
+}
+
+TileChoice stencil_current_tiles(const sx_ctx *c) {
+  const StencilPlan &sp = *c->stencil;
+  if (sp.scheme == SX_STENCIL_FUSED) return {SX_STENCIL_FUSED, sp.tz, 0};
+  return {SX_STENCIL_TWO_PASS, sp.tz2, sp.d_sched ? sp.sched_factor : 0};
+}
+
+void stencil_tiles_info(const sx_ctx *c, int64_t out[6]) {
+  const StencilPlan &sp = *c->stencil;
+  const int BY = family_by(sp.family), nz = c->geo.nz;
+  const long long cx = (c->geo.nx + 31) / 32, cy = (c->geo.ny + BY - 1) / BY;
+  out[0] = sp.scheme;
+  if (sp.scheme == SX_STENCIL_FUSED) {
+    int tx = 0, ty = 0;
+    fused_tile_of(sp.family, &tx, &ty);
+    out[1] = tx;
+    out[2] = ty;
+    out[3] = sp.tz;
+    out[4] = (long long)((c->geo.nx + tx - 1) / tx) * ((c->geo.ny + ty - 1) / ty) * ((nz + sp.tz - 1) / sp.tz);
+    out[5] = 0;
+  } else {
+    out[1] = 32;
+    out[2] = BY;
+    out[3] = sp.d_sched ? 0 : sp.tz2;
+    out[4] = sp.d_sched ? sp.nsched : cx * cy * ((nz + sp.tz2 - 1) / sp.tz2);
+    out[5] = sp.d_sched ? sp.sched_factor : 0;
+  }
 }
 
 cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,

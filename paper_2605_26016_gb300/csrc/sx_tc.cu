@@ -117,6 +117,9 @@ struct TcArgs {
 
 struct TcPlan {
   int tf32;
+  int nsm;
+  int ctas;          // CTAs per SM the layout is sized for (1 or 2)
+  size_t jp_bytes;   // plane values (bytes)
   TcArgs base;
   CUtensorMap tmap;     // 4-D view of Wp: (4 yp words, zp, nch, ncopy nbx)
   uint4 *Wp;            // packed input windows
@@ -710,6 +713,52 @@ int encode_window_map(TcPlan *tp, int ncopy) {
   return SX_OK;
 }
 
+// Shared-memory layout of the tile kernel for a ring of nbuf B buffers and `ctas` CTAs per SM:
+// window | nbuf B buffers | plane values (when they fit) | barriers.  The ring also stages the
+// epilogue (C x 128 rows x (xo | 1) floats).  False when it does not fit.
+bool tc_layout(TcPlan &tp, int nbuf, int ctas) {
+  TcArgs &a = tp.base;
+  const TcGeo &t = a.t;
+  const size_t stage_bytes = (size_t)t.C * 128 * (t.xo | 1) * 4;
+  if (nbuf < 2 || nbuf > kTcMaxRing || (size_t)nbuf * a.b_bytes < stage_bytes) return false;
+  const size_t budget = ctas == 2 ? kTcSmemMax / 2 - 1024 : kTcSmemMax;
+  auto size = [&](bool jsm) {
+    const size_t off = (size_t)a.win_bytes + (size_t)nbuf * a.b_bytes + (jsm ? tp.jp_bytes : 0);
+    return ((off + 15) / 16) * 16 + 128;
+  };
+  bool jsm = size(true) <= budget;
+  if (!jsm && size(false) > budget) return false;
+  a.nbuf = nbuf;
+  a.jp_smem = jsm ? 1 : 0;
+  a.smem = (unsigned)size(jsm);
+  a.bar_off = a.smem - 128;
+  tp.ctas = ctas;
+  return true;
+}
+
+// candidate (ring depth, CTAs per SM) pairs, the plan's default first: two CTAs per SM with the
+// deepest ring that allows it, else one CTA with the deepest ring
+std::vector<TcTiles> tc_tile_candidates_of(TcPlan &tp) {
+  const TcArgs keep = tp.base;
+  const int keep_ctas = tp.ctas;
+  std::vector<TcTiles> out;
+  for (int ctas : {2, 1})
+    for (int nb = (ctas == 2 ? 3 : kTcMaxRing); nb >= 2; --nb)
+      if (tc_layout(tp, nb, ctas)) out.push_back({nb, ctas});
+  tp.base = keep;
+  tp.ctas = keep_ctas;
+  return out;
+}
+
+cudaError_t tc_set_grid(TcPlan &tp) {
+  int occ = 1;
+  const cudaError_t e = occupancy(tp.base.t.nsub, tp.tf32 != 0, (int)tp.base.smem, &occ);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (long long)tp.base.t.nbx * tp.base.t.nby * tp.base.t.nbz;
+  tp.base.grid = (int)std::max(1LL, std::min(ntiles, (long long)tp.nsm * std::max(1, std::min(occ, tp.ctas))));
+  return cudaSuccess;
+}
+
 }  // namespace
 
 int tc_plan(sx_ctx *c) {
@@ -787,43 +836,22 @@ int tc_plan(sx_ctx *c) {
   if (Jp.empty()) Jp.assign(1, 0.0f);
   const int esz = tf32 ? 4 : 2;
   std::vector<uint32_t> ent = band_entries(t, tf32, a.ept);
-  a.win_bytes = (unsigned)(ncopy * t.nch * t.yr * t.zr * 16);
-  a.b_bytes = (unsigned)(ncopy * kTcN * t.kb * esz);
-  // shared memory: window | nbuf B buffers | plane values (when they fit) | barriers.  Prefer two
-  // CTAs per SM (the window load and epilogue of one overlap the MMAs of the other), else the
-  // deepest ring that fits one CTA.  Band entries live in the builder threads' registers.
-  const size_t jp_bytes = Jp.size() * 4;
   const int ept_max = nsub == 1 ? 16 : nsub == 2 ? 30 : 44;
   if (a.ept > ept_max) {
     delete tp;
     return set_error(SX_ERR_UNSUPPORTED, "the tensor-core band table exceeds its register budget");
   }
-  auto layout = [&](int nbuf, bool jsm) {
-    const size_t off = (size_t)a.win_bytes + (size_t)nbuf * a.b_bytes + (jsm ? jp_bytes : 0);
-    return ((off + 15) / 16) * 16 + 128;
-  };
-  // the ring also stages the epilogue: C x 128 rows x (xo | 1) floats
-  const size_t stage_bytes = (size_t)t.C * 128 * (t.xo | 1) * 4;
-  const int nb_min = std::max(2, (int)((stage_bytes + a.b_bytes - 1) / a.b_bytes));
-  const size_t kHalf = kTcSmemMax / 2 - 1024;
-  int nbuf = 0;
-  bool jsm = true;
-  for (int nb = 3; nb >= nb_min && !nbuf; --nb)
-    if (layout(nb, true) <= kHalf) nbuf = nb;
-  for (int nb = kTcMaxRing; nb >= nb_min && !nbuf; --nb)
-    if (layout(nb, true) <= kTcSmemMax) nbuf = nb;
-  if (!nbuf && nb_min <= kTcMaxRing) {
-    jsm = false;
-    if (layout(nb_min, false) <= kTcSmemMax) nbuf = nb_min;
-  }
-  if (!nbuf) {
+  a.win_bytes = (unsigned)(ncopy * t.nch * t.yr * t.zr * 16);
+  a.b_bytes = (unsigned)(ncopy * kTcN * t.kb * esz);
+  tp->jp_bytes = Jp.size() * 4;
+  // Prefer two CTAs per SM (the window load and epilogue of one overlap the MMAs of the other), else
+  // the deepest ring that fits one CTA; sx_autotune may pick another of tc_tile_candidates.
+  std::vector<TcTiles> cand = tc_tile_candidates_of(*tp);
+  if (cand.empty()) {
     delete tp;
     return set_error(SX_ERR_UNSUPPORTED, "the tensor-core tile does not fit in shared memory");
   }
-  a.nbuf = nbuf;
-  a.jp_smem = jsm ? 1 : 0;
-  a.bar_off = (unsigned)(layout(nbuf, jsm) - 128);
-  a.smem = (unsigned)layout(nbuf, jsm);
+  tc_layout(*tp, cand[0].nbuf, cand[0].ctas);
   const size_t n3 = 3 * (size_t)c->geo.nsite;
   const size_t wunits = (size_t)t.nbx * ncopy * t.nch * t.zp * t.yp;
   cudaError_t e = cudaMalloc(&tp->Wp, wunits * sizeof(uint4));
@@ -837,12 +865,11 @@ int tc_plan(sx_ctx *c) {
   if (e == cudaSuccess) e = cudaMalloc(&tp->Th, n3 * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&tp->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(tp->err, 0, sizeof(int));
-  if (e == cudaSuccess) e = set_smem(nsub, tf32, (int)a.smem);
-  int occ = 1, nsm = 152;
-  if (e == cudaSuccess) e = occupancy(nsub, tf32, (int)a.smem, &occ);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-  const long long ntiles = (long long)t.nbx * t.nby * t.nbz;
-  a.grid = (int)std::max(1LL, std::min(ntiles, (long long)nsm * std::max(occ, 1)));
+  // every layout up to the limit may be launched (sx_autotune switches between them)
+  if (e == cudaSuccess) e = set_smem(nsub, tf32, (int)kTcSmemMax);
+  tp->nsm = 152;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&tp->nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = tc_set_grid(*tp);
   a.Jp = tp->Jp;
   a.ent = tp->ent;
   a.err = tp->err;
@@ -905,6 +932,38 @@ int tc_check_error(const sx_ctx *c) {
   if (!c->tc || cudaMemcpy(&h, c->tc->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
   if (h) cudaMemset(c->tc->err, 0, sizeof(int));
   return h;
+}
+
+std::vector<TcTiles> tc_tile_candidates(const sx_ctx *c) { return tc_tile_candidates_of(*c->tc); }
+
+int tc_apply_tiles(sx_ctx *c, const TcTiles &t) {
+  TcPlan &tp = *c->tc;
+  const TcArgs keep = tp.base;
+  const int keep_ctas = tp.ctas;
+  if (!tc_layout(tp, t.nbuf, t.ctas)) {
+    tp.base = keep;
+    tp.ctas = keep_ctas;
+    return set_error(SX_ERR_ARG, "tile layout does not fit");
+  }
+  const cudaError_t e = tc_set_grid(tp);
+  if (e != cudaSuccess) {
+    tp.base = keep;
+    tp.ctas = keep_ctas;
+    return cuda_error(e, "tensor-core occupancy");
+  }
+  return SX_OK;
+}
+
+TcTiles tc_current_tiles(const sx_ctx *c) { return {c->tc->base.nbuf, c->tc->ctas}; }
+
+void tc_tiles_info(const sx_ctx *c, int64_t out[6]) {
+  const TcArgs &a = c->tc->base;
+  out[0] = 0;
+  out[1] = a.t.xo;
+  out[2] = kTcTY;
+  out[3] = kTcTZ;
+  out[4] = a.grid;
+  out[5] = a.nbuf;
 }
 
 }  // namespace sx

@@ -132,3 +132,22 @@ def test_heun_step_out_is_cuda_graph_capturable(scheme):
         sx.sx_llg_heun_step_out(s.ctx, tmp, ref, p, 1, s.nsite)
     torch.cuda.synchronize()
     assert torch.equal(A, ref)
+
+
+def test_autotune_tile_shapes_keep_the_step_bit_identical():
+    # every candidate (scheme x z chunk x launch shape) runs the same per-site arithmetic
+    n = (40, 33, 29)
+    s, w = sx.system_from_workload("sc_j123_dmi", n)
+    s.plan("stencil", "fp32")
+    S = torch.from_numpy(random_spins(1, n, 3)).cuda()
+    p = sx.llg_params(w["dt"], w["alpha"], w["T"], seed=2)
+    ref = torch.empty_like(S)
+    sx.sx_llg_heun_step_out(s.ctx, S, ref, p, 4, s.nsite)
+    name, t = sx.sx_autotune(s.ctx, S, torch.empty_like(S), p, s.nsite, steps=2)
+    tiles = sx.sx_plan_tiles(s.ctx)
+    assert tiles["scheme"] == {"fused": 1, "two_pass": 2}[name]
+    assert tiles["tile_x"] > 0 and tiles["tile_y"] > 0 and tiles["ctas"] > 0
+    assert min(v for v in t.values() if v > 0) > 0
+    got = torch.empty_like(S)
+    sx.sx_llg_heun_step_out(s.ctx, S, got, p, 4, s.nsite)
+    assert torch.equal(got, ref)

@@ -204,3 +204,18 @@ def test_tc_rejects_unsupported_hamiltonians():
     with pytest.raises(sx.SxError) as e:
         five.plan("igemm_tc", "bf16")
     assert e.value.code == sx.SX_ERR_UNSUPPORTED
+
+
+def test_tc_autotune_layouts_keep_the_field():
+    # ring depth and CTAs per SM change the schedule of tiles, not the arithmetic of one
+    n = (40, 24, 32)
+    s, w = sx.system_from_workload("sc_j123_dmi", n)
+    s.plan("igemm_tc", "tf32")
+    Sd = dev(random_spins(1, n, 8))
+    b0 = s.field(Sd)
+    p = sx.llg_params(w["dt"], w["alpha"], w["T"], seed=1)
+    name, t = sx.sx_autotune(s.ctx, Sd, torch.empty_like(Sd), p, s.nsite, steps=2)
+    assert name == "fused" and t["fused"] > 0
+    tiles = sx.sx_plan_tiles(s.ctx)
+    assert 2 <= tiles["ring_or_schedule"] <= 4 and tiles["ctas"] > 0 and tiles["tile_z"] == 16
+    assert torch.equal(s.field(Sd), b0)
