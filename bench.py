@@ -224,6 +224,13 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# DRAM bytes per spin-step of the Heun step measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of both
+# two-pass launches of one step, profiles/heun_bench_sc_j123_dmi_1024.md), keyed by (workload, scheme, schedule
+# factor); reported as roofline.traffic when the bench runs that shape
+MEASURED_TRAFFIC = {("sc_j123_dmi_1024", "two_pass", 0): (152.7, "ncu of the 1024^3 bench step, z chunk 512 "
+                                                                  "(profiles/heun_bench_sc_j123_dmi_1024.md)")}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -253,8 +260,9 @@ def run_ours(args):
     tune = None
     if args.scheme == "autotune" and args.backend == "stencil":
         # setup, untimed: time both stencil schemes on this replica's spins and keep the faster
-        chosen, tune = sx.sx_autotune(s.ctx, S, S2, p, nsite, steps=5, stream=stream)
+        chosen, tune = sx.sx_autotune(s.ctx, S, S2, p, nsite, steps=3, stream=stream)
         info = s.info()
+    tiles = sx.sx_plan_tiles(s.ctx)
     scheme = {1: "fused", 2: "two_pass"}.get(info["launches_per_step"], "fused") if args.backend == "stencil" \
         else "single"
 
@@ -324,8 +332,12 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     launches = info["launches_per_step"]
     achieved = BYTES_PER_SPIN_STEP * nsite / (ms_per_step * 1e-3) / 1e9
+    traffic, traffic_src = args.traffic, "--traffic" if args.traffic is not None else None
+    meas = MEASURED_TRAFFIC.get((args.workload, scheme, tiles.get("ring_or_schedule", 0)))
+    if traffic is None and meas is not None and args.backend == "stencil":
+        traffic, traffic_src = meas[0] * nsite, meas[1]
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": args.traffic, "peak_kind": peak_kind,
+            "traffic": traffic, "traffic_source": traffic_src, "peak_kind": peak_kind,
             "kernel": "heun step, %s scheme (%d launch%s per step)" % (scheme, launches,
                                                                        "" if launches == 1 else "es"),
             "bytes_per_unit": BYTES_PER_SPIN_STEP, "units_per_launch": nsite}
@@ -352,7 +364,7 @@ def run_ours(args):
            "data": "synthetic: seeded random unit spins; every rank an independent replica",
            "config": {"workload": args.workload, "lattice": wl["desc"], "backend": args.backend, "dipolar": args.dipolar,
                       "precision": args.precision, "nsite_per_gpu": nsite, "parallelism": f"replicas x{world}",
-                      "stencil_scheme": scheme, "autotune_ms": tune, "initial_spins": gen,
+                      "stencil_scheme": scheme, "autotune_ms": tune, "tiles": tiles, "initial_spins": gen,
                       "l2": ("flushed before every timed step (256 MB write + 256 MB read)" if need_flush else
                              "no flush: the %.1f GB state is far larger than the 126 MB L2" % (state_bytes / 1e9)),
                       "median_step_ms": statistics.median(times), "wall_s": t_wall, "max_norm_error": norm_err},

@@ -19,8 +19,9 @@ refinement in the paper: GNEB until the largest site force is below 1e-2 meV, th
 it is below 1e-3 meV (J1 = 1 meV; the paper keeps the path force below about 1e-3 J1), at most max_iters
 iterations in all.  A run whose barrier exceeds the hopfion energy scale E(A) - E(B) has left the basin of
 the path and is stopped as diverged.  Training paths start from the
-geodesic interpolation; only converged paths with a barrier between 0 and E(A) - E(B) are kept.  Paths are
-generated on 8 CUDA streams from 8 host threads (distinct contexts are independent).
+geodesic interpolation; only converged paths with a barrier between 1% of E(A) - E(B) and E(A) - E(B) are
+kept (near-zero barriers are paths along which the hopfion hardly resists and teach the proposer nothing about
+the saddle).  Paths are generated on 8 CUDA streams from 8 host threads (distinct contexts are independent).
 
 The proposer (include/sx.h, sx_cnn_*) is trained with Adam on (interpolated image, A, B, s) -> converged
 image over all interior images of the training paths, batches of 28 samples, cosine learning-rate decay.
@@ -31,7 +32,9 @@ when its run diverges, the fallback's time included), recording wall-clock secon
 iterations, the converged barrier (climbing-image energy minus E(A)) and the force.  With params_in the
 training paths and the training are skipped and the proposer's parameters are read from that file.  Two
 converged barriers are the same when they differ by at most 1e-3 of the hopfion energy scale E(A) - E(B);
-otherwise the runs found different annihilation channels.  Prints one JSON line per stage and a summary.
+otherwise the runs found different annihilation channels.  Where the learned run finds the lower barrier, a
+third arm checks that channel: a plain run from the piecewise geodesic chain through the learned run's
+climbing image (A -> saddle -> B) must reach the same barrier.  Prints one JSON line per stage and a summary.
 """
 import json
 import os
@@ -55,6 +58,7 @@ def main(argv):
     train_s = float(argv[3]) if len(argv) > 3 else 200.0
     max_iters = int(argv[4]) if len(argv) > 4 else 20000
     ftol, chunk = 1e-3, 1000
+    min_barrier_frac = 0.01
     nimg, dt = 16, 0.05
     n = (L, L, L)
     ncell = L ** 3
@@ -116,7 +120,7 @@ def main(argv):
             stream.synchronize()
             s.close()
             done, _, barrier, fm, scale = hist[-1]
-            ok = conv and 0.0 < barrier < scale
+            ok = conv and min_barrier_frac * scale <= barrier < scale
             return dict(A=A, chain=chain, barrier=barrier, scale=scale, fmax=fm, iters=done, ok=ok)
 
     params_in = argv[6] if len(argv) > 6 else None
@@ -220,12 +224,26 @@ def main(argv):
                       "test_mean_angle_interp_deg": float(np.mean(err["interp_deg"])),
                       "test_mean_angle_proposal_deg": float(np.mean(err["proposal_deg"]))}), flush=True)
 
+    def seeded_chain(A, learned_chain, E_learned):
+        """Piecewise geodesic chain A -> the learned run's highest interior image -> B, on the same image count."""
+        k = 1 + int(np.argmax(E_learned[1:-1]))
+        chain = torch.empty((nimg, 3, ncell), dtype=torch.float64, device="cuda")
+        chain[0].copy_(A.view(3, ncell))
+        chain[-1].copy_(FM.view(3, ncell))
+        chain[k].copy_(learned_chain[k])
+        if k > 1:
+            helper.interpolate(chain[0:k + 1])
+        if k < nimg - 2:
+            helper.interpolate(chain[k:])
+        return chain
+
     # ------------------------------------------------------------ evaluation
     results = []
     for i in test_ids:
         h = hams[i]
         s = system(h)
         row = dict(path=i, B=h["B"], f=h["f"])
+        chains = {}
         for arm in ("plain", "learned"):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -247,7 +265,18 @@ def main(argv):
             row[arm] = dict(converged=conv, diverged=div, fallback=fallback, iterations=done, seconds=sec,
                             t_init=t_init, barrier=barrier, fmax=fm, first_barrier=hist[0][2])
             row["scale"] = scale
-        row["same_barrier"] = abs(row["plain"]["barrier"] - row["learned"]["barrier"]) <= 1e-3 * abs(row["scale"])
+            chains[arm] = c
+        tol_b = 1e-3 * abs(row["scale"])
+        row["same_barrier"] = abs(row["plain"]["barrier"] - row["learned"]["barrier"]) <= tol_b
+        if (row["plain"]["converged"] and row["learned"]["converged"] and
+                row["learned"]["barrier"] < row["plain"]["barrier"] - tol_b):
+            E_l = [s.energy(chains["learned"][k])["total"] for k in range(nimg)]
+            c = seeded_chain(paths[i]["A"], chains["learned"], E_l)
+            t0 = time.perf_counter()
+            hist, conv, div = relax(s, c, t0)
+            done, sec, barrier, fm, _ = hist[-1]
+            row["plain_seeded"] = dict(converged=conv, diverged=div, iterations=done, seconds=sec, barrier=barrier,
+                                       fmax=fm, same_as_learned=abs(barrier - row["learned"]["barrier"]) <= tol_b)
         results.append(row)
         print(json.dumps({"stage": "eval", **row}), flush=True)
         s.close()
@@ -255,6 +284,7 @@ def main(argv):
     same = [r for r in conv if r["same_barrier"]]
     sp_all = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in conv]
     sp_same = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in same]
+    seeded = [r for r in conv if "plain_seeded" in r]
     direct = [r for r in conv if not r["learned"]["fallback"]]
     sp_direct = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in direct]
     print(json.dumps({"stage": "summary", "test_paths": len(results), "both_converged": len(conv),
@@ -265,6 +295,10 @@ def main(argv):
                                         "plain": sum(r["plain"]["barrier"] < r["learned"]["barrier"] -
                                                      1e-3 * abs(r["scale"]) for r in conv)},
                       "learned_faster": sum(r["learned"]["seconds"] < r["plain"]["seconds"] for r in conv),
+                      "lower_channel_confirmed_by_seeded_plain": sum(r["plain_seeded"]["converged"] and
+                                                                    r["plain_seeded"]["same_as_learned"]
+                                                                    for r in seeded),
+                      "lower_channel_checked": len(seeded),
                       "median_speedup_all": float(np.median(sp_all)) if sp_all else None,
                       "median_speedup_same_barrier": float(np.median(sp_same)) if sp_same else None,
                       "median_speedup_without_fallback": float(np.median(sp_direct)) if sp_direct else None,
