@@ -459,12 +459,28 @@ int sx_torque_max_noalloc(const double *S, const double *b, int64_t nsite, doubl
 int sx_thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64_t n, uint64_t step, float *eta_dev,
                        void *stream);
 
+/* Set a tile shape directly (e.g. one that sx_autotune chose earlier, without
+ * timing again).  STENCIL: in[0] = scheme (SX_STENCIL_FUSED / TWO_PASS),
+ * in[1] = z chunk of a CTA (1 .. n[2]), in[2] = two-pass launch shape (0:
+ * z-chunked grid, f = 1..4: balanced schedule over f x the resident CTA
+ * slots), in[3] = 1 when the two-pass corrector regenerates the thermal
+ * normals (0 for the fused scheme).  IGEMM_TC: in[0] = 0, in[1] = B-ring
+ * depth (2..4), in[2] = CTAs per SM (1 or 2), in[3] = 0.  Results do not
+ * depend on the shape (every shape runs the same per-site arithmetic).
+ * SX_ERR_ARG for values out of range or a layout that does not fit,
+ * SX_ERR_OOM when the two-pass workspace cannot be allocated,
+ * SX_ERR_UNSUPPORTED for other backends. */
+int sx_set_tiles(sx_ctx *ctx, const int64_t in[4]);
+
 /* Tile shape of the plan (after sx_plan or sx_autotune): out[0] = stencil
  * scheme (0 for other backends), out[1..3] = output tile extent in x, y, z
  * (cells; out[3] = 0 when a balanced schedule assigns z ranges), out[4] = CTAs
  * per launch, out[5] = stencil: schedule factor (0: z-chunked grid),
- * tensor core: B-operand ring depth.  Zeros for the other backends. */
-int sx_plan_tiles(const sx_ctx *ctx, int64_t out[6]);
+ * tensor core: B-operand ring depth, out[6] = 1 when the two-pass corrector
+ * regenerates the thermal normals instead of reading the predictor's (the
+ * same numbers: a pure function of seed, replica, site and step), out[7] = 0.
+ * Zeros for the other backends. */
+int sx_plan_tiles(const sx_ctx *ctx, int64_t out[8]);
 
 /* Plan facts for callers and tests: out[0] = nsite, out[1] = max taps per
  * sublattice, out[2..4] = halo radius per axis (cells), out[5] = backend,

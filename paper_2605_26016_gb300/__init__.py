@@ -31,7 +31,7 @@ EXPORTS = ("sx_create", "sx_destroy", "sx_last_error", "sx_num_shells", "sx_shel
            "sx_add_dmi", "sx_add_bonds", "sx_set_zeeman", "sx_set_anisotropy", "sx_set_dipolar", "sx_get_taps",
            "sx_plan", "sx_field", "sx_llg_heun_step", "sx_llg_heun_step_out", "sx_llg_heun_host", "sx_energy", "sx_torque_max",
            "sx_thermal_normals", "sx_plan_info", "sx_torque_max_noalloc", "sx_minimise", "sx_path_step",
-           "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune", "sx_plan_tiles", "sx_device_status",
+           "sx_geodesic", "sx_set_stencil_scheme", "sx_autotune", "sx_plan_tiles", "sx_set_tiles", "sx_device_status",
            "sx_batch_create", "sx_batch_destroy", "sx_batch_heun_step", "sx_batch_create_with_images",
            "sx_batch_bind", "sx_batch_run", "sx_batch_status", "sx_batch_info",
            "sx_cnn_num_params", "sx_cnn_create", "sx_cnn_destroy", "sx_cnn_set_params", "sx_cnn_get_params",
@@ -146,6 +146,7 @@ def lib():
             "sx_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
             "sx_autotune": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(sx_llg_params), ctypes.c_int, dp, vp]),
             "sx_plan_tiles": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
+            "sx_set_tiles": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
             "sx_cnn_num_params": (i64, []),
             "sx_cnn_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
             "sx_cnn_destroy": (None, [vp]),
@@ -472,10 +473,18 @@ def sx_autotune(ctx, S, S_scratch, p, nsite, steps=5, stream=None):
     return name, {"fused": t[0], "two_pass": t[1]}
 
 
+def sx_set_tiles(ctx, scheme, zchunk_or_ring, sched_or_ctas=0, regen_noise=0):
+    """Set the tile shape (see include/sx.h): stencil (scheme, z chunk, schedule factor, regenerate normals) or
+    tensor core (0, ring depth, CTAs per SM, 0); scheme may be "fused" / "two_pass"."""
+    v = (ctypes.c_int64 * 4)(STENCIL_SCHEMES.get(scheme, scheme), int(zchunk_or_ring), int(sched_or_ctas),
+                             int(regen_noise))
+    return _chk(lib().sx_set_tiles(ctx, v), "sx_set_tiles")
+
+
 def sx_plan_tiles(ctx):
-    out = (ctypes.c_int64 * 6)()
+    out = (ctypes.c_int64 * 8)()
     _chk(lib().sx_plan_tiles(ctx, out), "sx_plan_tiles")
-    keys = ("scheme", "tile_x", "tile_y", "tile_z", "ctas", "ring_or_schedule")
+    keys = ("scheme", "tile_x", "tile_y", "tile_z", "ctas", "ring_or_schedule", "regen_noise", "reserved")
     return dict(zip(keys, list(out)))
 
 

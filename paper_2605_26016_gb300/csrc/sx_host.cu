@@ -586,7 +586,7 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
     const int keep_tz = stencil_fused_tz(c);
     TileChoice best = keep;
     double best_ms = -1.0;
-    for (const TileChoice &t : stencil_tile_candidates(c)) {
+    for (const TileChoice &t : stencil_tile_candidates(c, h.thermal != 0)) {
       if (e != cudaSuccess) break;
       if (stencil_apply_tiles(c, t) != SX_OK) continue;  // e.g. no room for the two-pass workspace
       double ms = 0.0;
@@ -630,11 +630,43 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
   return result;
 }
 
-int sx_plan_tiles(const sx_ctx *c, int64_t out[6]) {
+int sx_set_tiles(sx_ctx *c, const int64_t in[4]) {
+  if (!c || !in) return set_error(SX_ERR_ARG, "null argument");
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (c->backend == SX_BACKEND_STENCIL) {
+    if (in[0] != SX_STENCIL_FUSED && in[0] != SX_STENCIL_TWO_PASS) return set_error(SX_ERR_ARG, "unknown scheme");
+    if (in[1] < 1 || in[1] > c->geo.nz) return set_error(SX_ERR_ARG, "z chunk must be in 1 .. n[2]");
+    if (in[2] < 0 || in[2] > 4) return set_error(SX_ERR_ARG, "schedule factor must be in 0 .. 4");
+    if (in[3] != 0 && in[3] != 1) return set_error(SX_ERR_ARG, "noise regeneration flag must be 0 or 1");
+    if (in[0] == SX_STENCIL_FUSED && (in[2] != 0 || in[3] != 0))
+      return set_error(SX_ERR_ARG, "the fused scheme has no schedule and no stored normals");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(c->device);
+    rc = stencil_apply_tiles(c, {(int)in[0], (int)in[1], (int)in[2], (int)in[3]});
+    cudaSetDevice(cur);
+    if (rc == SX_OK) c->opt_scheme = stencil_scheme(c);
+    return rc;
+  }
+  if (c->backend == SX_BACKEND_IGEMM_TC) {
+    if (in[0] != 0 || in[3] != 0) return set_error(SX_ERR_ARG, "the tensor-core plan has one scheme");
+    if (in[2] != 1 && in[2] != 2) return set_error(SX_ERR_ARG, "CTAs per SM must be 1 or 2");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(c->device);
+    rc = tc_apply_tiles(c, {(int)in[1], (int)in[2]});
+    cudaSetDevice(cur);
+    return rc;
+  }
+  return set_error(SX_ERR_UNSUPPORTED, "this backend has no tile shapes to set");
+}
+
+int sx_plan_tiles(const sx_ctx *c, int64_t out[8]) {
   if (!c || !out) return set_error(SX_ERR_ARG, "null argument");
   int rc = check_ready(c);
   if (rc) return rc;
-  for (int k = 0; k < 6; ++k) out[k] = 0;
+  for (int k = 0; k < 8; ++k) out[k] = 0;
   if (c->backend == SX_BACKEND_STENCIL) stencil_tiles_info(c, out);
   if (c->backend == SX_BACKEND_IGEMM_TC) tc_tiles_info(c, out);
   return SX_OK;

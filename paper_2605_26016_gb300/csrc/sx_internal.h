@@ -200,14 +200,16 @@ int stencil_check_error(const sx_ctx *c);
 // either a z-chunked grid (sched = 0) or a balanced schedule over sched x the resident CTA slots.
 struct TileChoice {
   int scheme, tz, sched;
+  int regen;  // two-pass thermal steps: the corrector regenerates the normals instead of reading them
 };
-std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c);
+std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c, bool thermal);
 int stencil_apply_tiles(sx_ctx *c, const TileChoice &t);
 TileChoice stencil_current_tiles(const sx_ctx *c);
 int stencil_fused_tz(const sx_ctx *c);                 // z chunk of the fused step and of single field launches
 void stencil_restore_fused_tz(sx_ctx *c, int tz);
-// out: scheme, tile x, tile y, z chunk (0: schedule), CTAs per launch, schedule factor (0: grid)
-void stencil_tiles_info(const sx_ctx *c, int64_t out[6]);
+// out: scheme, tile x, tile y, z chunk (0: schedule), CTAs per launch, schedule factor (0: grid),
+// normals regenerated by the corrector
+void stencil_tiles_info(const sx_ctx *c, int64_t out[8]);
 // Tensor-core tile layouts searched by sx_autotune: ring depth and CTAs per SM.
 struct TcTiles {
   int nbuf, ctas;
@@ -216,7 +218,7 @@ std::vector<TcTiles> tc_tile_candidates(const sx_ctx *c);
 int tc_apply_tiles(sx_ctx *c, const TcTiles &t);
 TcTiles tc_current_tiles(const sx_ctx *c);
 // out: 0, tile x, tile y, tile z, persistent CTAs, ring depth
-void tc_tiles_info(const sx_ctx *c, int64_t out[6]);
+void tc_tiles_info(const sx_ctx *c, int64_t out[8]);
 // batches of replicas sharing one coupling table (two-pass stencil plans)
 struct StencilBatch;
 // replicas ctxs[0..nrep) and, when img_ctx is set, nimg images of img_ctx's lattice (field only)

@@ -177,6 +177,7 @@ struct StencilArgs {
   int nx, ny, nz, px, py, pz;
   int tz;  // output planes per CTA
   int thermal;
+  int regen;  // two-pass thermal steps: 1 = the corrector regenerates the normals, the predictor does not store them
   long long nsite;
   float Jiso[kMaxIso];
   float Jt[kMaxTen][9];
@@ -742,7 +743,7 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
             for (int m = 0; m < 3; ++m) {
               nS[j][a][m] = (io.S + m * N)[i];
               nf[j][a][m] = (io.f0 + m * N)[i];
-              ne[j][a][m] = p.thermal ? (io.eta + m * N)[i] : 0.0f;
+              ne[j][a][m] = (p.thermal && !p.regen) ? (io.eta + m * N)[i] : 0.0f;
             }
           }
         }
@@ -807,10 +808,15 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
             if constexpr (MODE == PASS_PRED) {
               if (p.thermal) {
                 normals3(p.keys, gg.replica, (unsigned long long)i, io.step, e0, e1, e2);
-                io.eta[i] = e0;
-                (io.eta + N)[i] = e1;
-                (io.eta + 2 * N)[i] = e2;
+                if (!p.regen) {
+                  io.eta[i] = e0;
+                  (io.eta + N)[i] = e1;
+                  (io.eta + 2 * N)[i] = e2;
+                }
               }
+            } else if (p.thermal && p.regen) {
+              // the same counter-based normals as the predictor's (a pure function of seed, replica, site, step)
+              normals3(p.keys, gg.replica, (unsigned long long)i, io.step, e0, e1, e2);
             } else {
               e0 = ne[j][a][0];
               e1 = ne[j][a][1];
@@ -1964,15 +1970,18 @@ std::vector<int> chunk_lengths(int nz, int around) {
 }
 }  // namespace
 
-std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c) {
+std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c, bool thermal) {
   const StencilPlan &sp = *c->stencil;
   std::vector<TileChoice> out;
-  for (int tz : chunk_lengths(c->geo.nz, sp.tz)) out.push_back({SX_STENCIL_FUSED, tz, 0});
-  for (int tz : chunk_lengths(c->geo.nz, sp.tz2)) out.push_back({SX_STENCIL_TWO_PASS, tz, 0});
-  const int BY = family_by(sp.family);
-  const long long ncol = (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY);
-  if (ncol * c->geo.nz < (1LL << 31))
-    for (int f : {1, 2}) out.push_back({SX_STENCIL_TWO_PASS, sp.tz2, f});
+  for (int tz : chunk_lengths(c->geo.nz, sp.tz)) out.push_back({SX_STENCIL_FUSED, tz, 0, 0});
+  // two-pass: normals stored by the predictor, and (thermal steps) regenerated by the corrector
+  for (int regen = 0; regen <= (thermal ? 1 : 0); ++regen) {
+    for (int tz : chunk_lengths(c->geo.nz, sp.tz2)) out.push_back({SX_STENCIL_TWO_PASS, tz, 0, regen});
+    const int BY = family_by(sp.family);
+    const long long ncol = (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY);
+    if (ncol * c->geo.nz < (1LL << 31))
+      for (int f : {1, 2}) out.push_back({SX_STENCIL_TWO_PASS, sp.tz2, f, regen});
+  }
   return out;
 }
 
@@ -1987,6 +1996,7 @@ int stencil_apply_tiles(sx_ctx *c, const TileChoice &t) {
     return SX_OK;
   }
   sp.tz2 = t.tz;
+  sp.base.regen = t.regen;
   if (t.sched == sp.sched_factor && (t.sched == 0 || sp.d_sched)) return SX_OK;
   cudaFree(sp.d_sched);
   sp.d_sched = nullptr;
@@ -1996,6 +2006,7 @@ int stencil_apply_tiles(sx_ctx *c, const TileChoice &t) {
   if (t.sched > 0) {
     const int R = family_r(sp.family), BY = family_by(sp.family);
     const long long ncol = (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY);
+    if (ncol * c->geo.nz >= (1LL << 31)) return set_error(SX_ERR_ARG, "lattice too large for a balanced schedule");
     const std::vector<int2> sch =
         balanced_schedule(ncol, c->geo.nz, R, (long long)t.sched * sp.nsm * std::max(sp.occ_field, 1));
     if (cudaMalloc(&sp.d_sched, sch.size() * sizeof(int2)) != cudaSuccess ||
@@ -2020,11 +2031,11 @@ void stencil_restore_fused_tz(sx_ctx *c, int tz) {
 
 TileChoice stencil_current_tiles(const sx_ctx *c) {
   const StencilPlan &sp = *c->stencil;
-  if (sp.scheme == SX_STENCIL_FUSED) return {SX_STENCIL_FUSED, sp.tz, 0};
-  return {SX_STENCIL_TWO_PASS, sp.tz2, sp.d_sched ? sp.sched_factor : 0};
+  if (sp.scheme == SX_STENCIL_FUSED) return {SX_STENCIL_FUSED, sp.tz, 0, 0};
+  return {SX_STENCIL_TWO_PASS, sp.tz2, sp.d_sched ? sp.sched_factor : 0, sp.base.regen};
 }
 
-void stencil_tiles_info(const sx_ctx *c, int64_t out[6]) {
+void stencil_tiles_info(const sx_ctx *c, int64_t out[8]) {
   const StencilPlan &sp = *c->stencil;
   const int BY = family_by(sp.family), nz = c->geo.nz;
   const long long cx = (c->geo.nx + 31) / 32, cy = (c->geo.ny + BY - 1) / BY;
@@ -2043,6 +2054,7 @@ void stencil_tiles_info(const sx_ctx *c, int64_t out[6]) {
     out[3] = sp.d_sched ? 0 : sp.tz2;
     out[4] = sp.d_sched ? sp.nsched : cx * cy * ((nz + sp.tz2 - 1) / sp.tz2);
     out[5] = sp.d_sched ? sp.sched_factor : 0;
+    out[6] = sp.base.regen;
   }
 }
 

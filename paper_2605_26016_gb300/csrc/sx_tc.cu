@@ -956,7 +956,7 @@ int tc_apply_tiles(sx_ctx *c, const TcTiles &t) {
 
 TcTiles tc_current_tiles(const sx_ctx *c) { return {c->tc->base.nbuf, c->tc->ctas}; }
 
-void tc_tiles_info(const sx_ctx *c, int64_t out[6]) {
+void tc_tiles_info(const sx_ctx *c, int64_t out[8]) {
   const TcArgs &a = c->tc->base;
   out[0] = 0;
   out[1] = a.t.xo;

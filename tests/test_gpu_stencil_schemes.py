@@ -151,3 +151,26 @@ def test_autotune_tile_shapes_keep_the_step_bit_identical():
     got = torch.empty_like(S)
     sx.sx_llg_heun_step_out(s.ctx, S, got, p, 4, s.nsite)
     assert torch.equal(got, ref)
+
+
+@pytest.mark.parametrize("name,n", [("sc_j123_dmi", (40, 33, 29)), ("bcc_4shell", (24, 20, 17))])
+def test_every_tile_shape_gives_the_same_step(name, n):
+    s, w = sx.system_from_workload(name, n)
+    s.plan("stencil", "fp32")
+    S = torch.from_numpy(random_spins(s.nsub, n, 3)).cuda()
+    p = sx.llg_params(w["dt"], w["alpha"], max(w["T"], 30.0), seed=2)
+    ref = torch.empty_like(S)
+    sx.sx_llg_heun_step_out(s.ctx, S, ref, p, 4, s.nsite)
+    nz = n[2]
+    shapes = [("fused", tz, 0, 0) for tz in (nz, 7, 3)]
+    shapes += [("two_pass", tz, 0, r) for tz in (nz, 5) for r in (0, 1)]
+    shapes += [("two_pass", nz, f, r) for f in (1, 2) for r in (0, 1)]
+    for shape in shapes:
+        sx.sx_set_tiles(s.ctx, *shape)
+        t = sx.sx_plan_tiles(s.ctx)
+        assert t["scheme"] == {"fused": 1, "two_pass": 2}[shape[0]] and t["regen_noise"] == shape[3]
+        got = torch.empty_like(S)
+        sx.sx_llg_heun_step_out(s.ctx, S, got, p, 4, s.nsite)
+        assert torch.equal(got, ref), shape
+    with pytest.raises(sx.SxError):
+        sx.sx_set_tiles(s.ctx, "fused", nz + 1)

@@ -219,3 +219,23 @@ def test_tc_autotune_layouts_keep_the_field():
     tiles = sx.sx_plan_tiles(s.ctx)
     assert 2 <= tiles["ring_or_schedule"] <= 4 and tiles["ctas"] > 0 and tiles["tile_z"] == 16
     assert torch.equal(s.field(Sd), b0)
+
+
+def test_tc_every_layout_gives_the_same_field():
+    n = (44, 24, 33)
+    s, w = sx.system_from_workload("bcc_4shell", n)
+    s.plan("igemm_tc", "bf16")
+    Sd = dev(random_spins(2, n, 4))
+    b0 = s.field(Sd)
+    tried = 0
+    for ring in (2, 3, 4):
+        for ctas in (1, 2):
+            try:
+                sx.sx_set_tiles(s.ctx, 0, ring, ctas)
+            except sx.SxError as e:
+                assert e.code == sx.SX_ERR_ARG  # the layout does not fit
+                continue
+            tried += 1
+            assert sx.sx_plan_tiles(s.ctx)["ring_or_schedule"] == ring
+            assert torch.equal(s.field(Sd), b0), (ring, ctas)
+    assert tried >= 2
