@@ -237,6 +237,12 @@ def main(argv):
             helper.interpolate(chain[k:])
         return chain
 
+    def max_jump_deg(chain):
+        """Largest angle (degrees) any site turns between adjacent images: a converged chain whose images
+        are this far apart does not resolve the energy between them."""
+        d = (chain[1:] * chain[:-1]).sum(1).clamp(-1.0, 1.0)
+        return float(torch.rad2deg(torch.acos(d)).max().item())
+
     # ------------------------------------------------------------ evaluation
     results = []
     for i in test_ids:
@@ -263,7 +269,8 @@ def main(argv):
                 fallback = True
             done, sec, barrier, fm, scale = hist[-1]
             row[arm] = dict(converged=conv, diverged=div, fallback=fallback, iterations=done, seconds=sec,
-                            t_init=t_init, barrier=barrier, fmax=fm, first_barrier=hist[0][2])
+                            t_init=t_init, barrier=barrier, fmax=fm, first_barrier=hist[0][2],
+                            max_jump_deg=max_jump_deg(c))
             row["scale"] = scale
             chains[arm] = c
         tol_b = 1e-3 * abs(row["scale"])
@@ -276,7 +283,8 @@ def main(argv):
             hist, conv, div = relax(s, c, t0)
             done, sec, barrier, fm, _ = hist[-1]
             row["plain_seeded"] = dict(converged=conv, diverged=div, iterations=done, seconds=sec, barrier=barrier,
-                                       fmax=fm, same_as_learned=abs(barrier - row["learned"]["barrier"]) <= tol_b)
+                                       fmax=fm, same_as_learned=abs(barrier - row["learned"]["barrier"]) <= tol_b,
+                                       max_jump_deg=max_jump_deg(c))
         results.append(row)
         print(json.dumps({"stage": "eval", **row}), flush=True)
         s.close()
@@ -285,6 +293,8 @@ def main(argv):
     sp_all = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in conv]
     sp_same = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in same]
     seeded = [r for r in conv if "plain_seeded" in r]
+    same_direct = [r for r in same if not r["learned"]["fallback"]]
+    sp_same_direct = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in same_direct]
     direct = [r for r in conv if not r["learned"]["fallback"]]
     sp_direct = [r["plain"]["seconds"] / r["learned"]["seconds"] for r in direct]
     print(json.dumps({"stage": "summary", "test_paths": len(results), "both_converged": len(conv),
@@ -301,6 +311,12 @@ def main(argv):
                       "lower_channel_checked": len(seeded),
                       "median_speedup_all": float(np.median(sp_all)) if sp_all else None,
                       "median_speedup_same_barrier": float(np.median(sp_same)) if sp_same else None,
+                      "same_barrier_without_fallback": len(same_direct),
+                      "median_speedup_same_barrier_without_fallback":
+                          float(np.median(sp_same_direct)) if sp_same_direct else None,
+                      "median_max_jump_deg": {arm: float(np.median([r[arm]["max_jump_deg"] for r in conv]))
+                                              for arm in ("plain", "learned")} if conv else None,
+                      "lower_learned_with_jump_over_90deg": sum(r["learned"]["max_jump_deg"] > 90.0 for r in seeded),
                       "median_speedup_without_fallback": float(np.median(sp_direct)) if sp_direct else None,
                       "median_plain_s": float(np.median([r["plain"]["seconds"] for r in conv])) if conv else None,
                       "median_learned_s": float(np.median([r["learned"]["seconds"] for r in conv])) if conv else None,
