@@ -332,7 +332,13 @@ __device__ __forceinline__ void r2c_lines(const Tin *__restrict__ src, typename 
     fft_stages<R>(sm, pitch, nw, logm, twm, 0);
     C *dst = Zh + (long long)k * g.Nh + ((long long)z * g.ny + y0) * g.np;
     for (int e = threadIdx.x; e < nw * (m + 1); e += kHalfThreads) {
-      const int w = e / (m + 1), q = e - w * (m + 1);
+      // e = w (m + 1) + q, 0 <= q <= m, without a division: e >> logm overshoots w by (w + q) >> logm
+      int w = e >> logm;
+      int q = e - w * (m + 1);
+      while (q < 0) {
+        --w;
+        q += m + 1;
+      }
       const C a = sm[w * pitch + fft_slot(q & (m - 1))];
       const C b = sm[w * pitch + fft_slot((m - q) & (m - 1))];
       const R ex = (R)0.5 * (a.x + b.x), ey = (R)0.5 * (a.y - b.y);
@@ -368,17 +374,18 @@ __global__ void __launch_bounds__(kHalfThreads)
   C *sm = reinterpret_cast<C *>(smraw);
   const int n = 1 << logn, pitch = fft_pitch(n);
   const int g0 = blockIdx.x * W, nw = min(W, ngroup - g0);
+  const int logw = 31 - __clz(W);  // W is a power of two; lines w >= nw of the last group are skipped
   C *base = data + blockIdx.z * fs + g0 + (long long)blockIdx.y * os;
-  for (int e = threadIdx.x; e < nw * n; e += kHalfThreads) {
-    const int i = e / nw, w = e - i * nw;
-    cp_async_c(&sm[w * pitch + fft_slot(brev_n(i, logn))], &base[w + i * is]);
+  for (int e = threadIdx.x; e < (n << logw); e += kHalfThreads) {
+    const int i = e >> logw, w = e & (W - 1);
+    if (w < nw) cp_async_c(&sm[w * pitch + fft_slot(brev_n(i, logn))], &base[w + i * is]);
   }
   cp_async_wait_all();
   __syncthreads();
   fft_stages<R>(sm, pitch, nw, logn, tw, inverse);
-  for (int e = threadIdx.x; e < nw * n; e += kHalfThreads) {
-    const int i = e / nw, w = e - i * nw;
-    base[w + i * is] = sm[w * pitch + fft_slot(i)];
+  for (int e = threadIdx.x; e < (n << logw); e += kHalfThreads) {
+    const int i = e >> logw, w = e & (W - 1);
+    if (w < nw) base[w + i * is] = sm[w * pitch + fft_slot(i)];
   }
 }
 
@@ -424,16 +431,17 @@ __global__ void __launch_bounds__(kHalfThreads)
   const int qx0 = blockIdx.x * W, qy = blockIdx.y, nw = min(W, g.nh - qx0);
   const long long zs = (long long)g.ny * g.np;  // stride between z planes
   C *base = Zh + (long long)qy * g.np + qx0;
-  for (int e = threadIdx.x; e < NCH * nw * n; e += kHalfThreads) {
-    const int k = e / (nw * n), r2 = e - k * nw * n, i = r2 / nw, w = r2 - i * nw;
-    cp_async_c(&sm[(k * W + w) * pitch + fft_slot(brev_n(i, logz))], &base[k * g.Nh + i * zs + w]);
+  const int logw = 31 - __clz(W);  // W is a power of two; lines w >= nw of the last group are skipped
+  for (int e = threadIdx.x; e < (NCH << (logw + logz)); e += kHalfThreads) {
+    const int k = e >> (logw + logz), i = (e >> logw) & (n - 1), w = e & (W - 1);
+    if (w < nw) cp_async_c(&sm[(k * W + w) * pitch + fft_slot(brev_n(i, logz))], &base[k * g.Nh + i * zs + w]);
   }
   cp_async_wait_all();
   __syncthreads();
   fft_stages<R>(sm, pitch, NCH * W, logz, tw, 0);
-  for (int e = threadIdx.x; e < nw * n; e += kHalfThreads) {
-    const int i = e / nw, w = e - i * nw, r = brev_n(i, logz);
-    if (r < i) continue;
+  for (int e = threadIdx.x; e < (n << logw); e += kHalfThreads) {
+    const int i = e >> logw, w = e & (W - 1), r = brev_n(i, logz);
+    if (w >= nw || r < i) continue;
     C si[NCH], bi[NCH];
 #pragma unroll
     for (int k = 0; k < NCH; ++k) si[k] = sm[(k * W + w) * pitch + fft_slot(i)];
@@ -456,9 +464,9 @@ __global__ void __launch_bounds__(kHalfThreads)
   }
   __syncthreads();
   fft_stages<R>(sm, pitch, NCH * W, logz, tw, 1);
-  for (int e = threadIdx.x; e < NCH * nw * n; e += kHalfThreads) {
-    const int k = e / (nw * n), r2 = e - k * nw * n, i = r2 / nw, w = r2 - i * nw;
-    base[k * g.Nh + i * zs + w] = sm[(k * W + w) * pitch + fft_slot(i)];
+  for (int e = threadIdx.x; e < (NCH << (logw + logz)); e += kHalfThreads) {
+    const int k = e >> (logw + logz), i = (e >> logw) & (n - 1), w = e & (W - 1);
+    if (w < nw) base[k * g.Nh + i * zs + w] = sm[(k * W + w) * pitch + fft_slot(i)];
   }
 }
 
@@ -525,16 +533,17 @@ __global__ void __launch_bounds__(kHalfThreads)
   const int m = g.m, logm = g.logm, pitch = fft_pitch(m);
   const int y0 = blockIdx.x * W, z = blockIdx.y;
   const int nw = min(W, g.ny - y0);
+  const int logw = 31 - __clz(W);  // W is a power of two; lines w >= nw of the last group are skipped
   // four elements per thread and round: their eight loads are issued before any is used
   constexpr int U = 4;
-  const int total = nch * nw * m;
+  const int total = nch << (logw + logm);
   for (int e0 = threadIdx.x; e0 < total; e0 += U * kHalfThreads) {
     C xs[U], ys[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * kHalfThreads;
-      if (e < total) {
-        const int k = e / (nw * m), r2 = e - k * nw * m, w = r2 >> logm, q = r2 & (m - 1);
+      const int k = e >> (logw + logm), w = (e >> logm) & (W - 1), q = e & (m - 1);
+      if (e < total && w < nw) {
         const C *row = Zh + (long long)k * g.Nh + ((long long)z * g.ny + y0 + w) * g.np;
         xs[u] = row[q];
         ys[u] = row[m - q];
@@ -543,8 +552,8 @@ __global__ void __launch_bounds__(kHalfThreads)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int e = e0 + u * kHalfThreads;
-      if (e < total) {
-        const int k = e / (nw * m), r2 = e - k * nw * m, w = r2 >> logm, q = r2 & (m - 1);
+      const int k = e >> (logw + logm), w = (e >> logm) & (W - 1), q = e & (m - 1);
+      if (e < total && w < nw) {
         const C x = xs[u], y = ys[u];
         const R ex = x.x + y.x, ey = x.y - y.y, dx = x.x - y.x, dy = x.y + y.y;
         const C t = twr[q];
