@@ -226,9 +226,10 @@ def run_reference(args):
 
 # DRAM bytes per spin-step of the Heun step measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of both
 # two-pass launches of one step, profiles/heun_bench_sc_j123_dmi_1024.md), keyed by (workload, scheme, schedule
-# factor); reported as roofline.traffic when the bench runs that shape
-MEASURED_TRAFFIC = {("sc_j123_dmi_1024", "two_pass", 0): (152.7, "ncu of the 1024^3 bench step, z chunk 512 "
-                                                                  "(profiles/heun_bench_sc_j123_dmi_1024.md)")}
+# factor, plane staging); reported as roofline.traffic when the bench runs that shape
+MEASURED_TRAFFIC = {("sc_j123_dmi_1024", "two_pass", 0, 0): (152.7, "ncu of the 1024^3 bench step, z chunk 512, "
+                                                                     "site-by-site plane copies "
+                                                                     "(profiles/heun_bench_sc_j123_dmi_1024.md)")}
 
 
 def run_ours(args):
@@ -333,7 +334,7 @@ def run_ours(args):
     launches = info["launches_per_step"]
     achieved = BYTES_PER_SPIN_STEP * nsite / (ms_per_step * 1e-3) / 1e9
     traffic, traffic_src = args.traffic, "--traffic" if args.traffic is not None else None
-    meas = MEASURED_TRAFFIC.get((args.workload, scheme, tiles.get("ring_or_schedule", 0)))
+    meas = MEASURED_TRAFFIC.get((args.workload, scheme, tiles.get("ring_or_schedule", 0), tiles.get("tma_staging", 0)))
     if traffic is None and meas is not None and args.backend == "stencil":
         traffic, traffic_src = meas[0] * nsite, meas[1]
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -387,7 +388,8 @@ def run_ours(args):
 
 def _profile_step(argv):
     """step WORKLOAD NX,NY,NZ [STEPS=3] [BACKEND=stencil] [PRECISION=fp32] [SCHEME=auto|fused|two_pass|field]
-    out-of-place Heun steps (or field evaluations with SCHEME=field) of a workload."""
+    [STAGING=default|tma|copy] out-of-place Heun steps (or field evaluations with SCHEME=field) of a workload;
+    STAGING sets the plane staging of the stencil pass kernels (tensor copies or site-by-site copies)."""
     import torch
     import paper_2605_26016_gb300 as sx
     name = argv[0]
@@ -400,6 +402,12 @@ def _profile_step(argv):
     if backend == "stencil" and scheme in ("auto", "fused", "two_pass"):
         sx.sx_set_stencil_scheme(s.ctx, scheme)
     info = s.plan(backend, prec)
+    staging = argv[6] if len(argv) > 6 else "default"
+    if backend == "stencil" and staging != "default":
+        t = sx.sx_plan_tiles(s.ctx)
+        sx.sx_set_tiles(s.ctx, t["scheme"], t["tile_z"] or n[2], t["ring_or_schedule"], t["regen_noise"],
+                        1 if staging == "tma" else 0)
+    tiles = sx.sx_plan_tiles(s.ctx)
     S, gen = initial_spins(s.nsub, n, 1, "cuda")
     bufs = [S, torch.empty_like(S)]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
@@ -413,7 +421,8 @@ def _profile_step(argv):
         ev[k + 1].record()
     torch.cuda.synchronize()
     ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
-    print(json.dumps({"profile": "step", "workload": f"{name} {n}", "plan": info, "ms": ms, "input": gen}))
+    print(json.dumps({"profile": "step", "workload": f"{name} {n}", "plan": info, "tiles": tiles, "ms": ms,
+                      "input": gen}))
 
 
 def _profile_min(argv):

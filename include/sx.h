@@ -268,7 +268,8 @@ int sx_set_stencil_scheme(sx_ctx *ctx, int scheme);
 /* Time the candidate tile shapes of the plan on the caller's data and keep
  * the fastest.  STENCIL: the Heun scheme (SX_STENCIL_FUSED, TWO_PASS), the z
  * chunk of a CTA, and for the two-pass scheme the launch shape (a z-chunked
- * grid, or a balanced schedule over 1 or 2 times the resident CTA slots).
+ * grid, or a balanced schedule over 1 or 2 times the resident CTA slots) and,
+ * at the fastest shape, the other plane staging (sx_set_tiles in[4]).
  * IGEMM_TC: the depth of the B-operand ring (2..4) and the CTAs per SM (1 or
  * 2).  Each candidate runs `steps` (>= 1) out-of-place steps S -> S_scratch
  * (S is not modified; S_scratch is overwritten) after one warm-up step.
@@ -464,13 +465,17 @@ int sx_thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64_t 
  * in[1] = z chunk of a CTA (1 .. n[2]), in[2] = two-pass launch shape (0:
  * z-chunked grid, f = 1..4: balanced schedule over f x the resident CTA
  * slots), in[3] = 1 when the two-pass corrector regenerates the thermal
- * normals (0 for the fused scheme).  IGEMM_TC: in[0] = 0, in[1] = B-ring
- * depth (2..4), in[2] = CTAs per SM (1 or 2), in[3] = 0.  Results do not
- * depend on the shape (every shape runs the same per-site arithmetic).
- * SX_ERR_ARG for values out of range or a layout that does not fit,
- * SX_ERR_OOM when the two-pass workspace cannot be allocated,
- * SX_ERR_UNSUPPORTED for other backends. */
-int sx_set_tiles(sx_ctx *ctx, const int64_t in[4]);
+ * normals (0 for the fused scheme), in[4] = plane staging of the pass
+ * kernels (two-pass steps and field evaluations): 1 = a tile whose load
+ * region lies inside the lattice in x and y stages each plane with one
+ * tensor copy (TMA), 0 = every tile copies site by site.  IGEMM_TC: in[0] =
+ * 0, in[1] = B-ring depth (2..4), in[2] = CTAs per SM (1 or 2), in[3] =
+ * in[4] = 0.  Results do not depend on the shape (every shape runs the same
+ * per-site arithmetic).  SX_ERR_ARG for values out of range or a layout that
+ * does not fit, SX_ERR_OOM when the two-pass workspace cannot be allocated,
+ * SX_ERR_UNSUPPORTED for other backends and for in[4] = 1 on a lattice
+ * whose n[0] is not a multiple of 4. */
+int sx_set_tiles(sx_ctx *ctx, const int64_t in[5]);
 
 /* Tile shape of the plan (after sx_plan or sx_autotune): out[0] = stencil
  * scheme (0 for other backends), out[1..3] = output tile extent in x, y, z
@@ -478,8 +483,9 @@ int sx_set_tiles(sx_ctx *ctx, const int64_t in[4]);
  * per launch, out[5] = stencil: schedule factor (0: z-chunked grid),
  * tensor core: B-operand ring depth, out[6] = 1 when the two-pass corrector
  * regenerates the thermal normals instead of reading the predictor's (the
- * same numbers: a pure function of seed, replica, site and step), out[7] = 0.
- * Zeros for the other backends. */
+ * same numbers: a pure function of seed, replica, site and step), out[7] =
+ * stencil: 1 when the pass kernels stage interior tiles' planes with tensor
+ * copies (see sx_set_tiles).  Zeros for the other backends. */
 int sx_plan_tiles(const sx_ctx *ctx, int64_t out[8]);
 
 /* Plan facts for callers and tests: out[0] = nsite, out[1] = max taps per

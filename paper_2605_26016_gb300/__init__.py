@@ -473,18 +473,21 @@ def sx_autotune(ctx, S, S_scratch, p, nsite, steps=5, stream=None):
     return name, {"fused": t[0], "two_pass": t[1]}
 
 
-def sx_set_tiles(ctx, scheme, zchunk_or_ring, sched_or_ctas=0, regen_noise=0):
-    """Set the tile shape (see include/sx.h): stencil (scheme, z chunk, schedule factor, regenerate normals) or
-    tensor core (0, ring depth, CTAs per SM, 0); scheme may be "fused" / "two_pass"."""
-    v = (ctypes.c_int64 * 4)(STENCIL_SCHEMES.get(scheme, scheme), int(zchunk_or_ring), int(sched_or_ctas),
-                             int(regen_noise))
+def sx_set_tiles(ctx, scheme, zchunk_or_ring, sched_or_ctas=0, regen_noise=0, tma_staging=None):
+    """Set the tile shape (see include/sx.h): stencil (scheme, z chunk, schedule factor, regenerate normals,
+    tensor-copied planes) or tensor core (0, ring depth, CTAs per SM, 0, 0); scheme may be "fused" /
+    "two_pass".  tma_staging None keeps the plan's current staging."""
+    if tma_staging is None:
+        tma_staging = sx_plan_tiles(ctx)["tma_staging"]
+    v = (ctypes.c_int64 * 5)(STENCIL_SCHEMES.get(scheme, scheme), int(zchunk_or_ring), int(sched_or_ctas),
+                             int(regen_noise), int(tma_staging))
     return _chk(lib().sx_set_tiles(ctx, v), "sx_set_tiles")
 
 
 def sx_plan_tiles(ctx):
     out = (ctypes.c_int64 * 8)()
     _chk(lib().sx_plan_tiles(ctx, out), "sx_plan_tiles")
-    keys = ("scheme", "tile_x", "tile_y", "tile_z", "ctas", "ring_or_schedule", "regen_noise", "reserved")
+    keys = ("scheme", "tile_x", "tile_y", "tile_z", "ctas", "ring_or_schedule", "regen_noise", "tma_staging")
     return dict(zip(keys, list(out)))
 
 

@@ -599,6 +599,20 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
         best = t;
       }
     }
+    // the best shape with the other plane staging of the pass kernels (tensor copies or site by site)
+    if (e == cudaSuccess && best_ms >= 0.0 && best.scheme == SX_STENCIL_TWO_PASS) {
+      TileChoice t = best;
+      t.tma = !best.tma;
+      if (stencil_apply_tiles(c, t) == SX_OK) {
+        double ms = 0.0;
+        time_steps(&ms);
+        if (e == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best = t;
+          if (times_ms) times_ms[t.scheme - 1] = ms;
+        }
+      }
+    }
     stencil_restore_fused_tz(c, keep_tz);  // the two-pass candidates leave the fused chunk as planned
     const int rc2 = stencil_apply_tiles(c, e == cudaSuccess ? best : keep);
     if (e == cudaSuccess && rc2 != SX_OK) rc = rc2;
@@ -630,7 +644,7 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
   return result;
 }
 
-int sx_set_tiles(sx_ctx *c, const int64_t in[4]) {
+int sx_set_tiles(sx_ctx *c, const int64_t in[5]) {
   if (!c || !in) return set_error(SX_ERR_ARG, "null argument");
   int rc = check_ready(c);
   if (rc) return rc;
@@ -641,16 +655,17 @@ int sx_set_tiles(sx_ctx *c, const int64_t in[4]) {
     if (in[3] != 0 && in[3] != 1) return set_error(SX_ERR_ARG, "noise regeneration flag must be 0 or 1");
     if (in[0] == SX_STENCIL_FUSED && (in[2] != 0 || in[3] != 0))
       return set_error(SX_ERR_ARG, "the fused scheme has no schedule and no stored normals");
+    if (in[4] != 0 && in[4] != 1) return set_error(SX_ERR_ARG, "plane staging flag must be 0 or 1");
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(c->device);
-    rc = stencil_apply_tiles(c, {(int)in[0], (int)in[1], (int)in[2], (int)in[3]});
+    rc = stencil_apply_tiles(c, {(int)in[0], (int)in[1], (int)in[2], (int)in[3], (int)in[4]});
     cudaSetDevice(cur);
     if (rc == SX_OK) c->opt_scheme = stencil_scheme(c);
     return rc;
   }
   if (c->backend == SX_BACKEND_IGEMM_TC) {
-    if (in[0] != 0 || in[3] != 0) return set_error(SX_ERR_ARG, "the tensor-core plan has one scheme");
+    if (in[0] != 0 || in[3] != 0 || in[4] != 0) return set_error(SX_ERR_ARG, "the tensor-core plan has one scheme");
     if (in[2] != 1 && in[2] != 2) return set_error(SX_ERR_ARG, "CTAs per SM must be 1 or 2");
     int cur = 0;
     cudaGetDevice(&cur);

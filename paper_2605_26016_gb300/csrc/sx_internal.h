@@ -201,6 +201,7 @@ int stencil_check_error(const sx_ctx *c);
 struct TileChoice {
   int scheme, tz, sched;
   int regen;  // two-pass thermal steps: the corrector regenerates the normals instead of reading them
+  int tma;    // pass kernels: interior tiles stage their planes with tensor copies
 };
 std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c, bool thermal);
 int stencil_apply_tiles(sx_ctx *c, const TileChoice &t);
@@ -272,5 +273,8 @@ cudaError_t tc_field_f32(const sx_ctx *c, const double *S, float *b, bool onsite
 cudaError_t tc_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,
                          cudaStream_t st);
 int tc_check_error(const sx_ctx *c);
+// cuTensorMapEncodeTiled (a PFN_cuTensorMapEncodeTiled_v12000) from the driver entry point; null when the
+// driver does not provide it
+void *tensor_map_encode_fn();
 
 }  // namespace sx

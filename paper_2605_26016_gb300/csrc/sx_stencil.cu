@@ -24,6 +24,8 @@
 //    state sum S^n + dt/2 (f0 + f1) and its renormalisation in FP64 (GB300's
 //    FP64 pipe is ~1/70 of FP32, so conversions use integer bit operations and
 //    the FP64 pipe only runs the normalisation).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <string.h>
 
 #include <algorithm>
@@ -207,6 +209,8 @@ struct StencilPlan {
   int persistent;   // 1: nsched CTAs of the persistent kernel fit on the device at once
   int occ_persist;  // resident CTAs per SM of the persistent kernel (0: not available)
   int sched_factor; // balanced schedule over sched_factor x the resident CTA slots (0: grid-tiled passes)
+  int tma_ok;       // the lattice allows tensor-copied planes (x rows of a multiple of 16 bytes in FP32)
+  int tma;          // pass kernels stage the planes of interior tiles with tensor copies
   StencilArgs base;
 };
 
@@ -624,6 +628,10 @@ __global__ void __launch_bounds__(G<Family<FID>>::NT, Family<FID>::MINBF)
 
 // Pass-kernel geometry: a CTA of 32 x TYT threads owns a 32 x BY column tile, each thread RY = BY / TYT
 // adjacent rows of one column.
+// A tile whose load region lies inside the lattice in x and y (interior tiles) stages each plane with one
+// tensor copy (TMA) of a box of LXA x LY sites x NS sublattices x 3 components: its x start is rounded
+// down to 16 bytes (RA columns of halo instead of R: 2 for FP64 input, 4 for the FP32 S~ of the
+// corrector) and the box lands as [component][sublattice][row][LXA].  Other tiles copy site by site.
 template <class F>
 struct GF {
   static constexpr int NS = F::NSUB, R = F::R, BY = F::BY, TYT = F::TYP, RY = BY / TYT;
@@ -631,9 +639,15 @@ struct GF {
   static constexpr int NT = 32 * TYT, LX = 32 + 2 * R, LY = BY + 2 * R;
   static constexpr int SN = NS * LY * LX;
   static constexpr int NLOAD = (SN + NT - 1) / NT;
+  static constexpr int RA64 = (R + 1) & ~1, LXA64 = 32 + 2 * RA64;  // FP64 box (x start even)
+  static constexpr int RA32 = 4, LXA32 = 32 + 2 * RA32;             // FP32 box (x start a multiple of 4)
+  static_assert(R <= RA32, "the FP32 box covers halos up to 4 columns");
+  static constexpr size_t BOX64 = (size_t)3 * NS * LY * LXA64 * 8, BOX32 = (size_t)3 * NS * LY * LXA32 * 4;
+  static constexpr size_t STAGE_BYTES = std::max(std::max((size_t)3 * SN * 8, BOX64), BOX32);
   static constexpr size_t OFF_CQ = 2 * (size_t)SN * 16;
-  static constexpr size_t OFF_STAGE = OFF_CQ + (size_t)(R + 1) * NS * RY * NT * 16;
-  static constexpr size_t SMEM = OFF_STAGE + (size_t)3 * SN * 8;
+  static constexpr size_t OFF_STAGE = (OFF_CQ + (size_t)(R + 1) * NS * RY * NT * 16 + 127) / 128 * 128;
+  static constexpr size_t OFF_MBAR = (OFF_STAGE + STAGE_BYTES + 15) / 16 * 16;  // mbarrier, abort word
+  static constexpr size_t SMEM = OFF_MBAR + 16;
 };
 
 // One plane-marching pass over 32 x BY output columns: the field of an input
@@ -663,7 +677,42 @@ struct PassIO {
   unsigned long long step;  // noise counter of the step (PRED)
   const int2 *sched; // balanced schedule (one image): CTA k owns column-plane units
                      // [sched[k].x, sched[k].x + sched[k].y) of u = column * nz + z; null: the grid tiles
+  int tma;           // 1: interior tiles stage planes with the launch's tensor map (k_stencil_pass only)
+  int *werr;         // set when a bounded wait on a tensor copy gives up
 };
+
+// ------------------------------------------------------------------ tensor copies of the pass kernels
+
+__device__ __forceinline__ void tma_plane(const CUtensorMap *tm, void *dst, uint64_t *mbar, uint32_t bytes, int x,
+                                          int y, int z) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic accesses of dst come first
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(0), "r"(0), "r"(smem_addr(mbar))
+      : "memory");
+}
+
+// Wait for phase `parity` of the plane barrier, about a second at most; a thread whose wait gives up (or
+// finds that another one did) sets the CTA's abort word and the error word and returns false.
+__device__ __forceinline__ bool tma_wait(uint64_t *mbar, uint32_t parity, volatile int *abort, int *werr) {
+  for (long it = 0; it < (1L << 24); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*abort) return false;
+    if (it > 1024) __nanosleep(64);
+  }
+  *abort = 1;
+  if (werr) atomicExch(werr, 1);
+  return false;
+}
 
 __device__ __forceinline__ void cp_async4(unsigned dst, const void *src, bool ok) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
@@ -695,16 +744,41 @@ __device__ __forceinline__ void issue_plane_f32(const GEO &p, const float *__res
 // of image img.  p carries the couplings and constants, gg the lattice geometry (nx .. pz,
 // nsite) and the noise replica index: the launch arguments themselves for one system, a
 // per-replica record in a batch.
+// tm: the launch's tensor map over the input planes (S, or S~ for PASS_CORR), or null; tphase: the
+// parity of the CTA's next plane-barrier phase (advanced by every tensor-copied plane).
 template <int FID, int MODE, class GEO>
 __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg, int onsite, const PassIO &io,
-                                             unsigned char *smem_raw, int img, int x0, int y0, int z0, int tzc) {
+                                             unsigned char *smem_raw, int img, int x0, int y0, int z0, int tzc,
+                                             const CUtensorMap *tm, uint32_t &tphase) {
   using F = Family<FID>;
   using g = GF<F>;
   constexpr int NS = F::NSUB, R = F::R, RY = g::RY;
   float4 *sn = reinterpret_cast<float4 *>(smem_raw);                    // [2][SN]
   float4 *cq = reinterpret_cast<float4 *>(smem_raw + g::OFF_CQ);        // [R+1][NS][RY][NT] centre values
-  double *stage = reinterpret_cast<double *>(smem_raw + g::OFF_STAGE);  // [3][SN] (FP64 input)
+  double *stage = reinterpret_cast<double *>(smem_raw + g::OFF_STAGE);  // [3][SN] (FP64 input) or a tensor box
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + g::OFF_MBAR);
+  volatile int *abort = reinterpret_cast<volatile int *>(smem_raw + g::OFF_MBAR + 8);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  // tensor-copied planes: the box starts RA columns left of the tile (RA >= R, 16-byte aligned)
+  constexpr bool F32IN = MODE == PASS_CORR;
+  constexpr int RA = F32IN ? g::RA32 : g::RA64, LXA = F32IN ? g::LXA32 : g::LXA64;
+  constexpr int CS = NS * g::LY * LXA;  // elements per component in the box
+  constexpr uint32_t BOX_BYTES = (uint32_t)(F32IN ? g::BOX32 : g::BOX64);
+  const bool tma = tm && x0 >= RA && x0 + 32 + RA <= gg.nx && y0 >= R && y0 + F::BY + R <= gg.ny;
+  int sidx[g::NLOAD];  // box element of this thread's load-region sites
+#pragma unroll
+  for (int j = 0; j < g::NLOAD; ++j) {
+    const int e = tid + j * g::NT;
+    const int a = e / (g::LX * g::LY), r = e - a * (g::LX * g::LY), ly = r / g::LX, lx = r - ly * g::LX;
+    sidx[j] = (a * g::LY + ly) * LXA + lx + (RA - R);
+  }
+  auto tma_issue = [&](int q) {
+    if (tid == 0 && !*abort) {
+      bool zok = true;  // open z faces: out-of-range planes are read as zeros by the copy itself
+      const int gz = gg.pz ? wrap_axis(q, gg.nz, 1, zok) : q;
+      tma_plane(tm, stage, mbar, BOX_BYTES, x0 - RA, y0 - R, gz);
+    }
+  };
   const int ry0 = ty * RY;  // first tile row of this thread
   const double *Sin = io.S + img * io.istride;
   double *bout = io.b + img * io.istride;
@@ -751,7 +825,9 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
     }
   };
   prefetch(z0);
-  if constexpr (MODE == PASS_CORR)
+  if (tma)
+    tma_issue(z0 - R);
+  else if constexpr (MODE == PASS_CORR)
     issue_plane_f32<g::NLOAD, g::NT, g::SN>(gg, io.St, z0 - R, tid, off, okmask, sn);
   else
     issue_plane<g::NLOAD, g::NT, g::SN>(gg, Sin, z0 - R, tid, off, okmask, stage);
@@ -759,17 +835,39 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
   for (int k = 0; k < niter; ++k) {
     const int q = z0 - R + k;
     float4 *buf = sn + (k & 1) * g::SN;
-    cp_wait<0>();
-    if constexpr (MODE == PASS_CORR) {
+    if (tma) {
+      // the box of plane q has landed: this thread's sites into the FP32 ring (the same values, and for
+      // FP64 input the same integer conversion, as the site-by-site copies)
+      tma_wait(mbar, tphase, abort, io.werr);
+      tphase ^= 1u;
+#pragma unroll
+      for (int j = 0; j < g::NLOAD; ++j) {
+        const int e = tid + j * g::NT;
+        if (e < g::SN) {
+          if constexpr (F32IN) {
+            const float *sf = reinterpret_cast<const float *>(stage);
+            buf[e] = make_float4(sf[sidx[j]], sf[CS + sidx[j]], sf[2 * CS + sidx[j]], 0.0f);
+          } else {
+            buf[e] = make_float4(f64_to_f32(stage[sidx[j]]), f64_to_f32(stage[CS + sidx[j]]),
+                                 f64_to_f32(stage[2 * CS + sidx[j]]), 0.0f);
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // these reads before the next copy's writes
+      __syncthreads();  // every site of plane q is in the ring and the box is free again
+      if (k + 1 < niter) tma_issue(q + 1);
+    } else if constexpr (MODE == PASS_CORR) {
+      cp_wait<0>();
       __syncthreads();  // every thread's copies of plane q have landed
       if (k + 1 < niter)
         issue_plane_f32<g::NLOAD, g::NT, g::SN>(gg, io.St, q + 1, tid, off, okmask, sn + ((k + 1) & 1) * g::SN);
     } else {
+      cp_wait<0>();
       convert_plane<g::NLOAD, g::NT, g::SN>(stage, buf, tid);
       if (k + 1 < niter) issue_plane<g::NLOAD, g::NT, g::SN>(gg, Sin, q + 1, tid, off, okmask, stage);
     }
     cp_commit();
-    if constexpr (MODE != PASS_CORR) __syncthreads();
+    if (MODE != PASS_CORR && !tma) __syncthreads();
     const float4 *base = buf + (ry0 + R) * g::LX + (tx + R);
 #pragma unroll
     for (int j = 0; j < RY; ++j) push_plane<F>(p, base + j * g::LX, g::LX * g::LY, g::LX, acc[j]);
@@ -864,7 +962,8 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
 // The column-plane units of schedule entry k, segment by segment.
 template <int FID, int MODE>
 __device__ __forceinline__ void run_scheduled(const StencilArgs &p, int onsite, const PassIO &io,
-                                              unsigned char *smem_raw, int k) {
+                                              unsigned char *smem_raw, int k, const CUtensorMap *tm,
+                                              uint32_t &tphase) {
   using F = Family<FID>;
   const int2 e = io.sched[k];
   const int ncx = (p.nx + 31) / 32;
@@ -873,7 +972,8 @@ __device__ __forceinline__ void run_scheduled(const StencilArgs &p, int onsite, 
   while (u < uend) {  // uniform over the block
     const int col = (int)(u / p.nz), z = (int)(u - (long long)col * p.nz);
     const int len = (int)min((long long)(p.nz - z), uend - u);
-    pass_segment<FID, MODE>(p, p, onsite, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+    pass_segment<FID, MODE>(p, p, onsite, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len, tm,
+                            tphase);
     u += len;
     __syncthreads();  // shared memory is reused by the next segment
   }
@@ -881,16 +981,28 @@ __device__ __forceinline__ void run_scheduled(const StencilArgs &p, int onsite, 
 
 template <int FID, int MODE>
 __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
-    k_stencil_pass(const StencilArgs p, int onsite, const PassIO io) {
+    k_stencil_pass(const StencilArgs p, int onsite, const PassIO io, const __grid_constant__ CUtensorMap tmap) {
   using F = Family<FID>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using g = GF<F>;
+  extern __shared__ __align__(128) unsigned char smem_pass[];  // the box of a tensor copy starts 128-byte aligned
+  unsigned char *smem_raw = smem_pass;
+  const CUtensorMap *tm = io.tma ? &tmap : nullptr;
+  uint32_t tphase = 0;
+  if (tm) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(smem_raw + g::OFF_MBAR)));
+      *reinterpret_cast<volatile int *>(smem_raw + g::OFF_MBAR + 8) = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
   if (io.sched) {
-    run_scheduled<FID, MODE>(p, onsite, io, smem_raw, blockIdx.x);
+    run_scheduled<FID, MODE>(p, onsite, io, smem_raw, blockIdx.x, tm, tphase);
   } else {
     const int img = blockIdx.z / io.nzc, zc = blockIdx.z - img * io.nzc;
     const int z0 = zc * p.tz;
     pass_segment<FID, MODE>(p, p, onsite, io, smem_raw, img, blockIdx.x * 32, blockIdx.y * F::BY, z0,
-                            min(p.tz, p.nz - z0));
+                            min(p.tz, p.nz - z0), tm, tphase);
   }
 }
 
@@ -941,13 +1053,14 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
     k_heun_persistent(const StencilArgs p, PassIO io, double *S0, double *S1, int nsteps,
                       unsigned long long step0, GridBar *gb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t tph = 0;  // unused: the persistent launch copies site by site
   for (int k = 0; k < nsteps; ++k) {
     io.S = (k & 1) ? S1 : S0;
     io.Sout = (k & 1) ? S0 : S1;
     io.step = step0 + (unsigned long long)k;
-    run_scheduled<FID, PASS_PRED>(p, 1, io, smem_raw, blockIdx.x);
+    run_scheduled<FID, PASS_PRED>(p, 1, io, smem_raw, blockIdx.x, nullptr, tph);
     if (!grid_sync(gb, gridDim.x)) return;
-    run_scheduled<FID, PASS_CORR>(p, 1, io, smem_raw, blockIdx.x);
+    run_scheduled<FID, PASS_CORR>(p, 1, io, smem_raw, blockIdx.x, nullptr, tph);
     if (!grid_sync(gb, gridDim.x)) return;
   }
 }
@@ -1002,9 +1115,12 @@ __device__ __forceinline__ void batch_units(const StencilArgs &p, const BatchRep
     const int col = (int)(ul / gg.nz), z = (int)(ul - (long long)col * gg.nz);
     const int len = (int)min((long long)(gg.nz - z), uend - u);
     PassIO io;
+    uint32_t tph = 0;  // unused: batch segments copy site by site
     io.nzc = 1;
     io.istride = 0;
     io.step = step;
+    io.tma = 0;
+    io.werr = nullptr;
     io.sched = nullptr;
     io.bf = nullptr;
     if (reps[r].kind == 0) {
@@ -1015,7 +1131,8 @@ __device__ __forceinline__ void batch_units(const StencilArgs &p, const BatchRep
       io.b = nullptr;
       io.f0 = reps[r].f0;
       io.eta = reps[r].eta;
-      pass_segment<FID, MODE>(p, gg, 1, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+      pass_segment<FID, MODE>(p, gg, 1, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len, nullptr,
+                              tph);
     } else if (MODE == PASS_PRED && images) {
       io.S = reps[r].S;
       io.Sout = nullptr;
@@ -1024,7 +1141,8 @@ __device__ __forceinline__ void batch_units(const StencilArgs &p, const BatchRep
       io.b = reps[r].b;
       io.f0 = nullptr;
       io.eta = nullptr;
-      pass_segment<FID, PASS_FIELD>(p, gg, 1, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len);
+      pass_segment<FID, PASS_FIELD>(p, gg, 1, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len,
+                                    nullptr, tph);
     }
     u += len;
     __syncthreads();  // shared memory is reused by the next segment
@@ -1196,6 +1314,30 @@ int field_tz(const StencilPlan &sp, const StencilArgs &a, int count) {
   return best_tz;
 }
 
+// 5-D tensor map (x, y, z, sublattice, component) over a spin-like array [3][nsub][nz][ny][nx] of FP64 (or
+// FP32) values, whose box is the load region of a pass-kernel tile with its x start rounded down to 16
+// bytes.  False (the pass then copies site by site) without the driver's encoder, for a base address that
+// is not 16-byte aligned, or for a layout the encoder rejects.
+template <int FID>
+bool encode_plane_map(const StencilPlan &sp, const StencilArgs &a, const void *base, bool f32, CUtensorMap *tm) {
+  using g = GF<Family<FID>>;
+  memset(tm, 0, sizeof(*tm));
+  if (!sp.tma || !sp.tma_ok || !base || ((uintptr_t)base & 15u)) return false;
+  const auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encode_fn());
+  if (!enc) return false;
+  const cuuint64_t es = f32 ? 4 : 8;
+  const cuuint64_t nx = (cuuint64_t)a.nx, ny = (cuuint64_t)a.ny, nz = (cuuint64_t)a.nz;
+  const cuuint64_t dims[5] = {nx, ny, nz, (cuuint64_t)g::NS, 3};
+  const cuuint64_t strides[4] = {nx * es, nx * ny * es, nx * ny * nz * es, (cuuint64_t)a.nsite * es};
+  const cuuint32_t box[5] = {(cuuint32_t)(f32 ? g::LXA32 : g::LXA64), (cuuint32_t)g::LY, 1, (cuuint32_t)g::NS, 3};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = enc(tm, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5,
+                         const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 template <int FID>
 cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &base, int onsite, const double *S, double *b,
                          int count, long long stride, cudaStream_t st, float *bf = nullptr) {
@@ -1209,9 +1351,12 @@ cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &base, int ons
   io.bf = bf;
   io.nzc = (a.nz + a.tz - 1) / a.tz;
   io.istride = stride;
+  io.werr = sp.d_bar ? &sp.d_bar->err : nullptr;
   if ((long long)io.nzc * count > 65535) return cudaErrorInvalidConfiguration;
+  CUtensorMap tm;
+  io.tma = count == 1 && encode_plane_map<FID>(sp, a, S, false, &tm) ? 1 : 0;  // one image: a 5-D box
   const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc * count);
-  k_stencil_pass<FID, PASS_FIELD><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, onsite, io);
+  k_stencil_pass<FID, PASS_FIELD><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, onsite, io, tm);
   return cudaGetLastError();
 }
 
@@ -1232,10 +1377,14 @@ cudaError_t launch_heun2(const StencilPlan &sp, StencilArgs a, const double *src
   io.sched = sp.d_sched;
   io.step = a.step;
   io.nzc = (a.nz + a.tz - 1) / a.tz;
+  io.werr = sp.d_bar ? &sp.d_bar->err : nullptr;
   const dim3 grid = sp.d_sched ? dim3(sp.nsched)
                                : dim3((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc);
-  k_stencil_pass<FID, PASS_PRED><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io);
-  k_stencil_pass<FID, PASS_CORR><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io);
+  CUtensorMap tm;
+  io.tma = encode_plane_map<FID>(sp, a, src, false, &tm) ? 1 : 0;
+  k_stencil_pass<FID, PASS_PRED><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io, tm);
+  io.tma = encode_plane_map<FID>(sp, a, sp.d_St, true, &tm) ? 1 : 0;
+  k_stencil_pass<FID, PASS_CORR><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io, tm);
   return cudaGetLastError();
 }
 
@@ -1506,10 +1655,19 @@ int stencil_plan(sx_ctx *c) {
       return set_error(SX_ERR_OOM, "stencil schedule: device allocation failed");
     }
   }
+  // error word of the bounded waits (tensor-copy planes, grid barriers of the persistent launch)
+  if (cudaMalloc(&sp->d_bar, sizeof(GridBar)) != cudaSuccess || cudaMemset(sp->d_bar, 0, sizeof(GridBar)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(sp->d_sched);
+    cudaFree(sp->d_bar);
+    delete sp;
+    return set_error(SX_ERR_OOM, "stencil error word: device allocation failed");
+  }
+  sp->tma_ok = (a.nx % 4 == 0 && tensor_map_encode_fn()) ? 1 : 0;
+  sp->tma = sp->tma_ok;
   if (sp->d_sched) {
     int occ = 0;
-    cudaError_t e2 = cudaMalloc(&sp->d_bar, sizeof(GridBar));
-    if (e2 == cudaSuccess) e2 = cudaMemset(sp->d_bar, 0, sizeof(GridBar));
+    cudaError_t e2 = cudaSuccess;
     if (e2 == cudaSuccess) {
       switch (fam) {
         case FAM_SC6_ISO: e2 = persistent_occupancy<FAM_SC6_ISO>(&occ); break;
@@ -1973,20 +2131,23 @@ std::vector<int> chunk_lengths(int nz, int around) {
 std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c, bool thermal) {
   const StencilPlan &sp = *c->stencil;
   std::vector<TileChoice> out;
-  for (int tz : chunk_lengths(c->geo.nz, sp.tz)) out.push_back({SX_STENCIL_FUSED, tz, 0, 0});
+  for (int tz : chunk_lengths(c->geo.nz, sp.tz)) out.push_back({SX_STENCIL_FUSED, tz, 0, 0, sp.tma_ok});
   // two-pass: normals stored by the predictor, and (thermal steps) regenerated by the corrector
   for (int regen = 0; regen <= (thermal ? 1 : 0); ++regen) {
-    for (int tz : chunk_lengths(c->geo.nz, sp.tz2)) out.push_back({SX_STENCIL_TWO_PASS, tz, 0, regen});
+    for (int tz : chunk_lengths(c->geo.nz, sp.tz2)) out.push_back({SX_STENCIL_TWO_PASS, tz, 0, regen, sp.tma_ok});
     const int BY = family_by(sp.family);
     const long long ncol = (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY);
     if (ncol * c->geo.nz < (1LL << 31))
-      for (int f : {1, 2}) out.push_back({SX_STENCIL_TWO_PASS, sp.tz2, f, regen});
+      for (int f : {1, 2}) out.push_back({SX_STENCIL_TWO_PASS, sp.tz2, f, regen, sp.tma_ok});
   }
   return out;
 }
 
 int stencil_apply_tiles(sx_ctx *c, const TileChoice &t) {
   StencilPlan &sp = *c->stencil;
+  if (t.tma && !sp.tma_ok)
+    return set_error(SX_ERR_UNSUPPORTED, "tensor-copied planes need n[0] a multiple of 4 and the driver's encoder");
+  sp.tma = t.tma;
   int rc = stencil_set_scheme(c, t.scheme);
   if (rc != SX_OK) return rc;
   if (stencil_scheme(c) != t.scheme) return set_error(SX_ERR_OOM, "two-pass workspace unavailable");
@@ -2031,8 +2192,8 @@ void stencil_restore_fused_tz(sx_ctx *c, int tz) {
 
 TileChoice stencil_current_tiles(const sx_ctx *c) {
   const StencilPlan &sp = *c->stencil;
-  if (sp.scheme == SX_STENCIL_FUSED) return {SX_STENCIL_FUSED, sp.tz, 0, 0};
-  return {SX_STENCIL_TWO_PASS, sp.tz2, sp.d_sched ? sp.sched_factor : 0, sp.base.regen};
+  if (sp.scheme == SX_STENCIL_FUSED) return {SX_STENCIL_FUSED, sp.tz, 0, 0, sp.tma};
+  return {SX_STENCIL_TWO_PASS, sp.tz2, sp.d_sched ? sp.sched_factor : 0, sp.base.regen, sp.tma};
 }
 
 void stencil_tiles_info(const sx_ctx *c, int64_t out[8]) {
@@ -2056,6 +2217,7 @@ void stencil_tiles_info(const sx_ctx *c, int64_t out[8]) {
     out[5] = sp.d_sched ? sp.sched_factor : 0;
     out[6] = sp.base.regen;
   }
+  out[7] = sp.tma;
 }
 
 cudaError_t stencil_heun_step(const sx_ctx *c, const double *src, double *dst, const HeunConst &h, uint64_t step,

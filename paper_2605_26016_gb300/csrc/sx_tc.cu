@@ -688,17 +688,9 @@ cudaError_t set_smem(int nsub, bool tf32, int bytes) {
   }
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver library)
 int encode_window_map(TcPlan *tp, int ncopy) {
-  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
-  if (!enc) {
-    cudaDriverEntryPointQueryResult q;
-    void *fn = nullptr;
-    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-      return set_error(SX_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+  const auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encode_fn());
+  if (!enc) return set_error(SX_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   // 4-D view (words of the y rows, z, chunk, copy and tile column): the y rows of one chunk and
   // z plane are contiguous, so each box row is 16 (8 + 2 ry) bytes instead of one 16-byte unit
   const TcGeo &t = tp->base.t;
@@ -927,6 +919,19 @@ cudaError_t tc_heun_step(const sx_ctx *c, const double *src, double *dst, const 
 }
 
 // 1 if a bounded wait of the tensor-core kernel gave up since the last check (clears it)
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver library)
+void *tensor_map_encode_fn() {
+  static void *fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *f = nullptr;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+    if (e == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = f;
+    else cudaGetLastError();
+  }
+  return fn;
+}
+
 int tc_check_error(const sx_ctx *c) {
   int h = 0;
   if (!c->tc || cudaMemcpy(&h, c->tc->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;

@@ -174,3 +174,42 @@ def test_every_tile_shape_gives_the_same_step(name, n):
         assert torch.equal(got, ref), shape
     with pytest.raises(sx.SxError):
         sx.sx_set_tiles(s.ctx, "fused", nz + 1)
+
+
+# Lattices with interior tiles (load region inside the lattice in x and y), whose planes the pass kernels
+# stage with tensor copies: periodic, open z (planes beyond the faces read as zeros by the copy), all open
+# with a partial last tile column, and two sublattices with a 2-cell halo.
+@pytest.mark.parametrize("name,n,pbc", [("sc_j123_dmi", (96, 80, 24), (1, 1, 1)),
+                                         ("sc_j123_dmi", (96, 80, 24), (1, 1, 0)),
+                                         ("sc_j123_dmi", (100, 84, 21), (0, 0, 0)),
+                                         ("bcc_4shell", (96, 72, 20), (1, 1, 1)),
+                                         ("sc_4shell", (104, 50, 16), (1, 0, 1))])
+def test_tensor_copied_planes_give_the_same_step_and_field(name, n, pbc):
+    s, w = sx.system_from_workload(name, n, pbc=pbc)
+    s.plan("stencil", "fp32")
+    S = torch.from_numpy(random_spins(s.nsub, n, 5)).cuda()
+    p = sx.llg_params(w["dt"], w["alpha"], max(w["T"], 30.0), seed=3)
+    nz = n[2]
+    sx.sx_set_tiles(s.ctx, "two_pass", nz, 0, 0, 0)  # every tile copies site by site
+    assert sx.sx_plan_tiles(s.ctx)["tma_staging"] == 0
+    ref = torch.empty_like(S)
+    sx.sx_llg_heun_step_out(s.ctx, S, ref, p, 4, s.nsite)
+    ref_b64 = s.field(S)
+    ref_b32 = s.field(S, dtype=torch.float32)
+    for shape in [(nz, 0, 0), (5, 0, 1), (nz, 1, 0), (nz, 2, 1)]:
+        sx.sx_set_tiles(s.ctx, "two_pass", *shape, 1)
+        assert sx.sx_plan_tiles(s.ctx)["tma_staging"] == 1
+        got = torch.empty_like(S)
+        sx.sx_llg_heun_step_out(s.ctx, S, got, p, 4, s.nsite)
+        assert torch.equal(got, ref), shape
+        assert torch.equal(s.field(S), ref_b64), shape
+        assert torch.equal(s.field(S, dtype=torch.float32), ref_b32), shape
+    sx.sx_device_status(s.ctx)  # no bounded wait gave up
+
+
+def test_tensor_copied_planes_need_rows_of_16_bytes():
+    s, w = sx.system_from_workload("sc_j123_dmi", (90, 40, 12))
+    s.plan("stencil", "fp32")
+    assert sx.sx_plan_tiles(s.ctx)["tma_staging"] == 0
+    with pytest.raises(sx.SxError):
+        sx.sx_set_tiles(s.ctx, "two_pass", 12, 0, 0, 1)
