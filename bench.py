@@ -388,8 +388,10 @@ def run_ours(args):
 
 def _profile_step(argv):
     """step WORKLOAD NX,NY,NZ [STEPS=3] [BACKEND=stencil] [PRECISION=fp32] [SCHEME=auto|fused|two_pass|field]
-    [STAGING=default|tma|copy] out-of-place Heun steps (or field evaluations with SCHEME=field) of a workload;
-    STAGING sets the plane staging of the stencil pass kernels (tensor copies or site-by-site copies)."""
+    [STAGING=default|tma|copy|MASK] [SHAPE=TZ,LAUNCH] out-of-place Heun steps (or field evaluations with
+    SCHEME=field) of a workload; STAGING sets the plane staging of the stencil pass kernels (tensor copies for
+    every pass, site-by-site copies, or the mask of sx_set_tiles in[4]), SHAPE the two-pass z chunk and launch
+    shape (sx_set_tiles in[1], in[2])."""
     import torch
     import paper_2605_26016_gb300 as sx
     name = argv[0]
@@ -403,10 +405,13 @@ def _profile_step(argv):
         sx.sx_set_stencil_scheme(s.ctx, scheme)
     info = s.plan(backend, prec)
     staging = argv[6] if len(argv) > 6 else "default"
-    if backend == "stencil" and staging != "default":
+    staging = int(staging) if staging.isdigit() else staging
+    shape = [int(v) for v in argv[7].split(",")] if len(argv) > 7 else None
+    if backend == "stencil" and (staging != "default" or shape):
         t = sx.sx_plan_tiles(s.ctx)
-        sx.sx_set_tiles(s.ctx, t["scheme"], t["tile_z"] or n[2], t["ring_or_schedule"], t["regen_noise"],
-                        1 if staging == "tma" else 0)
+        tz, launch = shape if shape else (t["tile_z"] or n[2], t["ring_or_schedule"])
+        sx.sx_set_tiles(s.ctx, t["scheme"], tz, launch, t["regen_noise"],
+                        t["tma_staging"] if staging == "default" else {"copy": 0, "tma": 3}.get(staging, staging))
     tiles = sx.sx_plan_tiles(s.ctx)
     S, gen = initial_spins(s.nsub, n, 1, "cuda")
     bufs = [S, torch.empty_like(S)]

@@ -268,8 +268,9 @@ int sx_set_stencil_scheme(sx_ctx *ctx, int scheme);
 /* Time the candidate tile shapes of the plan on the caller's data and keep
  * the fastest.  STENCIL: the Heun scheme (SX_STENCIL_FUSED, TWO_PASS), the z
  * chunk of a CTA, and for the two-pass scheme the launch shape (a z-chunked
- * grid, or a balanced schedule over 1 or 2 times the resident CTA slots) and,
- * at the fastest shape, the other plane staging (sx_set_tiles in[4]).
+ * grid, a balanced schedule over 1 or 2 times the resident CTA slots, or the
+ * overlapped launch with z chunks of about n[2]/4 .. n[2]/16 planes) and, at
+ * the fastest shape, the other plane staging (sx_set_tiles in[4]).
  * IGEMM_TC: the depth of the B-operand ring (2..4) and the CTAs per SM (1 or
  * 2).  Each candidate runs `steps` (>= 1) out-of-place steps S -> S_scratch
  * (S is not modified; S_scratch is overwritten) after one warm-up step.
@@ -464,28 +465,34 @@ int sx_thermal_normals(uint64_t seed, uint32_t replica, uint64_t site0, int64_t 
  * timing again).  STENCIL: in[0] = scheme (SX_STENCIL_FUSED / TWO_PASS),
  * in[1] = z chunk of a CTA (1 .. n[2]), in[2] = two-pass launch shape (0:
  * z-chunked grid, f = 1..4: balanced schedule over f x the resident CTA
- * slots), in[3] = 1 when the two-pass corrector regenerates the thermal
+ * slots, 5: one persistent launch whose CTAs take predictor and corrector
+ * units of in[1] planes from a dependency-ordered queue, so that the
+ * issue-bound predictor and the memory-bound corrector share the SMs; it
+ * needs edge tile columns (32 cells), rows and the last z chunk at least as
+ * wide as the halo, and one context's steps on one stream at a time), in[3] =
+ * 1 when the two-pass corrector regenerates the thermal
  * normals (0 for the fused scheme), in[4] = plane staging of the pass
- * kernels (two-pass steps and field evaluations): 1 = a tile whose load
- * region lies inside the lattice in x and y stages each plane with one
- * tensor copy (TMA), 0 = every tile copies site by site.  IGEMM_TC: in[0] =
+ * kernels, a mask: bit 0 for the predictor and field passes, bit 1 for the
+ * corrector; a set bit makes a tile whose load region lies inside the
+ * lattice in x and y stage each plane with one tensor copy (TMA), a clear
+ * bit makes every tile copy site by site.  IGEMM_TC: in[0] =
  * 0, in[1] = B-ring depth (2..4), in[2] = CTAs per SM (1 or 2), in[3] =
  * in[4] = 0.  Results do not depend on the shape (every shape runs the same
  * per-site arithmetic).  SX_ERR_ARG for values out of range or a layout that
  * does not fit, SX_ERR_OOM when the two-pass workspace cannot be allocated,
- * SX_ERR_UNSUPPORTED for other backends and for in[4] = 1 on a lattice
+ * SX_ERR_UNSUPPORTED for other backends and for in[4] != 0 on a lattice
  * whose n[0] is not a multiple of 4. */
 int sx_set_tiles(sx_ctx *ctx, const int64_t in[5]);
 
 /* Tile shape of the plan (after sx_plan or sx_autotune): out[0] = stencil
  * scheme (0 for other backends), out[1..3] = output tile extent in x, y, z
  * (cells; out[3] = 0 when a balanced schedule assigns z ranges), out[4] = CTAs
- * per launch, out[5] = stencil: schedule factor (0: z-chunked grid),
+ * per launch, out[5] = stencil: two-pass launch shape (see sx_set_tiles in[2]),
  * tensor core: B-operand ring depth, out[6] = 1 when the two-pass corrector
  * regenerates the thermal normals instead of reading the predictor's (the
  * same numbers: a pure function of seed, replica, site and step), out[7] =
- * stencil: 1 when the pass kernels stage interior tiles' planes with tensor
- * copies (see sx_set_tiles).  Zeros for the other backends. */
+ * stencil: the plane staging mask of the pass kernels (see sx_set_tiles).
+ * Zeros for the other backends. */
 int sx_plan_tiles(const sx_ctx *ctx, int64_t out[8]);
 
 /* Plan facts for callers and tests: out[0] = nsite, out[1] = max taps per

@@ -474,9 +474,10 @@ def sx_autotune(ctx, S, S_scratch, p, nsite, steps=5, stream=None):
 
 
 def sx_set_tiles(ctx, scheme, zchunk_or_ring, sched_or_ctas=0, regen_noise=0, tma_staging=None):
-    """Set the tile shape (see include/sx.h): stencil (scheme, z chunk, schedule factor, regenerate normals,
-    tensor-copied planes) or tensor core (0, ring depth, CTAs per SM, 0, 0); scheme may be "fused" /
-    "two_pass".  tma_staging None keeps the plan's current staging."""
+    """Set the tile shape (see include/sx.h): stencil (scheme, z chunk, two-pass launch shape, regenerate
+    normals, plane-staging mask: bit 0 predictor and field passes, bit 1 corrector use tensor copies) or tensor
+    core (0, ring depth, CTAs per SM, 0, 0); scheme may be "fused" / "two_pass".  tma_staging None keeps the
+    plan's current staging."""
     if tma_staging is None:
         tma_staging = sx_plan_tiles(ctx)["tma_staging"]
     v = (ctypes.c_int64 * 5)(STENCIL_SCHEMES.get(scheme, scheme), int(zchunk_or_ring), int(sched_or_ctas),

@@ -599,18 +599,21 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
         best = t;
       }
     }
-    // the best shape with the other plane staging of the pass kernels (tensor copies or site by site)
-    if (e == cudaSuccess && best_ms >= 0.0 && best.scheme == SX_STENCIL_TWO_PASS) {
-      TileChoice t = best;
-      t.tma = !best.tma;
-      if (stencil_apply_tiles(c, t) == SX_OK) {
-        double ms = 0.0;
-        time_steps(&ms);
-        if (e == cudaSuccess && ms < best_ms) {
-          best_ms = ms;
-          best = t;
-          if (times_ms) times_ms[t.scheme - 1] = ms;
-        }
+    // the best shape with the other plane stagings of the pass kernels (tensor copies or site by site for
+    // the predictor and for the corrector)
+    const TileChoice top = best;
+    for (int mask = 0; mask < 4 && e == cudaSuccess && best_ms >= 0.0 && top.scheme == SX_STENCIL_TWO_PASS;
+         ++mask) {
+      if (mask == top.tma) continue;
+      TileChoice t = top;
+      t.tma = mask;
+      if (stencil_apply_tiles(c, t) != SX_OK) continue;
+      double ms = 0.0;
+      time_steps(&ms);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = t;
+        if (times_ms) times_ms[t.scheme - 1] = ms;
       }
     }
     stencil_restore_fused_tz(c, keep_tz);  // the two-pass candidates leave the fused chunk as planned
@@ -651,11 +654,11 @@ int sx_set_tiles(sx_ctx *c, const int64_t in[5]) {
   if (c->backend == SX_BACKEND_STENCIL) {
     if (in[0] != SX_STENCIL_FUSED && in[0] != SX_STENCIL_TWO_PASS) return set_error(SX_ERR_ARG, "unknown scheme");
     if (in[1] < 1 || in[1] > c->geo.nz) return set_error(SX_ERR_ARG, "z chunk must be in 1 .. n[2]");
-    if (in[2] < 0 || in[2] > 4) return set_error(SX_ERR_ARG, "schedule factor must be in 0 .. 4");
+    if (in[2] < 0 || in[2] > 5) return set_error(SX_ERR_ARG, "two-pass launch shape must be in 0 .. 5");
     if (in[3] != 0 && in[3] != 1) return set_error(SX_ERR_ARG, "noise regeneration flag must be 0 or 1");
     if (in[0] == SX_STENCIL_FUSED && (in[2] != 0 || in[3] != 0))
       return set_error(SX_ERR_ARG, "the fused scheme has no schedule and no stored normals");
-    if (in[4] != 0 && in[4] != 1) return set_error(SX_ERR_ARG, "plane staging flag must be 0 or 1");
+    if (in[4] < 0 || in[4] > 3) return set_error(SX_ERR_ARG, "plane staging mask must be in 0 .. 3");
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(c->device);

@@ -210,9 +210,20 @@ struct StencilPlan {
   int occ_persist;  // resident CTAs per SM of the persistent kernel (0: not available)
   int sched_factor; // balanced schedule over sched_factor x the resident CTA slots (0: grid-tiled passes)
   int tma_ok;       // the lattice allows tensor-copied planes (x rows of a multiple of 16 bytes in FP32)
-  int tma;          // pass kernels stage the planes of interior tiles with tensor copies
+  int tma;          // interior tiles stage their planes with tensor copies: bit 0 predictor and field
+                    // passes, bit 1 corrector
+  // overlapped two-pass launch (sched_factor == kSchedOverlap): unit queue, one done flag per predictor
+  // unit, queue counter; ovl_grid CTAs (0: not set up)
+  int *d_order;
+  int *d_done;
+  int *d_queue;
+  int n_order;
+  int n_done;
+  int ovl_grid;
   StencilArgs base;
 };
+
+constexpr int kSchedOverlap = 5;  // two-pass launch shape: one launch of overlapped predictor/corrector units
 
 // ------------------------------------------------------------------ helpers
 
@@ -744,9 +755,10 @@ __device__ __forceinline__ void issue_plane_f32(const GEO &p, const float *__res
 // of image img.  p carries the couplings and constants, gg the lattice geometry (nx .. pz,
 // nsite) and the noise replica index: the launch arguments themselves for one system, a
 // per-replica record in a batch.
-// tm: the launch's tensor map over the input planes (S, or S~ for PASS_CORR), or null; tphase: the
-// parity of the CTA's next plane-barrier phase (advanced by every tensor-copied plane).
-template <int FID, int MODE, class GEO>
+// TMAP: compiled with the tensor-copy staging (otherwise every tile copies site by site and tm is
+// ignored); tm: the launch's tensor map over the input planes (S, or S~ for PASS_CORR), or null;
+// tphase: the parity of the CTA's next plane-barrier phase (advanced by every tensor-copied plane).
+template <int FID, int MODE, bool TMAP = false, class GEO>
 __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg, int onsite, const PassIO &io,
                                              unsigned char *smem_raw, int img, int x0, int y0, int z0, int tzc,
                                              const CUtensorMap *tm, uint32_t &tphase) {
@@ -764,13 +776,15 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
   constexpr int RA = F32IN ? g::RA32 : g::RA64, LXA = F32IN ? g::LXA32 : g::LXA64;
   constexpr int CS = NS * g::LY * LXA;  // elements per component in the box
   constexpr uint32_t BOX_BYTES = (uint32_t)(F32IN ? g::BOX32 : g::BOX64);
-  const bool tma = tm && x0 >= RA && x0 + 32 + RA <= gg.nx && y0 >= R && y0 + F::BY + R <= gg.ny;
+  const bool tma = TMAP && tm && x0 >= RA && x0 + 32 + RA <= gg.nx && y0 >= R && y0 + F::BY + R <= gg.ny;
   int sidx[g::NLOAD];  // box element of this thread's load-region sites
+  if constexpr (TMAP) {
 #pragma unroll
-  for (int j = 0; j < g::NLOAD; ++j) {
-    const int e = tid + j * g::NT;
-    const int a = e / (g::LX * g::LY), r = e - a * (g::LX * g::LY), ly = r / g::LX, lx = r - ly * g::LX;
-    sidx[j] = (a * g::LY + ly) * LXA + lx + (RA - R);
+    for (int j = 0; j < g::NLOAD; ++j) {
+      const int e = tid + j * g::NT;
+      const int a = e / (g::LX * g::LY), r = e - a * (g::LX * g::LY), ly = r / g::LX, lx = r - ly * g::LX;
+      sidx[j] = (a * g::LY + ly) * LXA + lx + (RA - R);
+    }
   }
   auto tma_issue = [&](int q) {
     if (tid == 0 && !*abort) {
@@ -835,7 +849,7 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
   for (int k = 0; k < niter; ++k) {
     const int q = z0 - R + k;
     float4 *buf = sn + (k & 1) * g::SN;
-    if (tma) {
+    if (TMAP && tma) {
       // the box of plane q has landed: this thread's sites into the FP32 ring (the same values, and for
       // FP64 input the same integer conversion, as the site-by-site copies)
       tma_wait(mbar, tphase, abort, io.werr);
@@ -960,7 +974,7 @@ __device__ __forceinline__ void pass_segment(const StencilArgs &p, const GEO &gg
 }
 
 // The column-plane units of schedule entry k, segment by segment.
-template <int FID, int MODE>
+template <int FID, int MODE, bool TMAP = false>
 __device__ __forceinline__ void run_scheduled(const StencilArgs &p, int onsite, const PassIO &io,
                                               unsigned char *smem_raw, int k, const CUtensorMap *tm,
                                               uint32_t &tphase) {
@@ -972,23 +986,25 @@ __device__ __forceinline__ void run_scheduled(const StencilArgs &p, int onsite, 
   while (u < uend) {  // uniform over the block
     const int col = (int)(u / p.nz), z = (int)(u - (long long)col * p.nz);
     const int len = (int)min((long long)(p.nz - z), uend - u);
-    pass_segment<FID, MODE>(p, p, onsite, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len, tm,
-                            tphase);
+    pass_segment<FID, MODE, TMAP>(p, p, onsite, io, smem_raw, 0, (col % ncx) * 32, (col / ncx) * F::BY, z, len,
+                                  tm, tphase);
     u += len;
     __syncthreads();  // shared memory is reused by the next segment
   }
 }
 
-template <int FID, int MODE>
+// TMAP: the instantiation with tensor-copied planes (io.tma set); the other one is the site-by-site
+// staging alone, so that the extra registers of the copy path never weigh on it.
+template <int FID, int MODE, bool TMAP>
 __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
     k_stencil_pass(const StencilArgs p, int onsite, const PassIO io, const __grid_constant__ CUtensorMap tmap) {
   using F = Family<FID>;
   using g = GF<F>;
   extern __shared__ __align__(128) unsigned char smem_pass[];  // the box of a tensor copy starts 128-byte aligned
   unsigned char *smem_raw = smem_pass;
-  const CUtensorMap *tm = io.tma ? &tmap : nullptr;
+  const CUtensorMap *tm = TMAP && io.tma ? &tmap : nullptr;
   uint32_t tphase = 0;
-  if (tm) {
+  if (TMAP && tm) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(smem_raw + g::OFF_MBAR)));
       *reinterpret_cast<volatile int *>(smem_raw + g::OFF_MBAR + 8) = 0;
@@ -997,12 +1013,12 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
     __syncthreads();
   }
   if (io.sched) {
-    run_scheduled<FID, MODE>(p, onsite, io, smem_raw, blockIdx.x, tm, tphase);
+    run_scheduled<FID, MODE, TMAP>(p, onsite, io, smem_raw, blockIdx.x, tm, tphase);
   } else {
     const int img = blockIdx.z / io.nzc, zc = blockIdx.z - img * io.nzc;
     const int z0 = zc * p.tz;
-    pass_segment<FID, MODE>(p, p, onsite, io, smem_raw, img, blockIdx.x * 32, blockIdx.y * F::BY, z0,
-                            min(p.tz, p.nz - z0), tm, tphase);
+    pass_segment<FID, MODE, TMAP>(p, p, onsite, io, smem_raw, img, blockIdx.x * 32, blockIdx.y * F::BY, z0,
+                                  min(p.tz, p.nz - z0), tm, tphase);
   }
 }
 
@@ -1062,6 +1078,89 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
     if (!grid_sync(gb, gridDim.x)) return;
     run_scheduled<FID, PASS_CORR>(p, 1, io, smem_raw, blockIdx.x, nullptr, tph);
     if (!grid_sync(gb, gridDim.x)) return;
+  }
+}
+
+// ------------------------------------------------------------------ overlapped two-pass step
+
+// Codes of the overlapped step's work units: idx = chunk * ncol + column (column = cy * ncx + cx of the
+// 32 x BY tiles, chunk = z / tz), plus kUnitCorr for a corrector unit.
+constexpr int kUnitCorr = 1 << 30;
+
+// One two-pass Heun step in a single launch whose CTAs take predictor and corrector units from a queue
+// (`order`, built on the host): the predictor is issue-bound and the corrector bound by DRAM and the
+// FP64 pipe, so a predictor and a corrector unit resident on one SM share its resources better than
+// two passes that each fill the whole device.  A corrector unit (chunk z, column c) reads S~ on its
+// halo: it starts once the predictor units of the 3 x 3 neighbouring columns in chunks z - 1 .. z + 1
+// (wrapped on periodic axes, absent beyond open faces) have published their done flags; the queue puts
+// every corrector unit after those units, so a wait only ever waits for running predictor units, which
+// wait for nothing.  Publication: the unit's stores, a CTA barrier, a device fence, the flag; the
+// reader: the flag, a device fence, a CTA barrier, the loads.  Each flag wait gives up after about
+// two seconds (error word set).  Per-site arithmetic is that of the two pass launches.
+template <int FID, bool TMAP>
+__global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
+    k_heun_overlap(const StencilArgs p, const PassIO io, const int *__restrict__ order, int nunits, int *queue,
+                   int *done, const __grid_constant__ CUtensorMap tm_pred, const __grid_constant__ CUtensorMap tm_corr,
+                   int tma_pred, int tma_corr) {
+  using F = Family<FID>;
+  using g = GF<F>;
+  extern __shared__ __align__(128) unsigned char smem_ovl[];
+  unsigned char *smem_raw = smem_ovl;
+  volatile int *abort = reinterpret_cast<volatile int *>(smem_raw + g::OFF_MBAR + 8);
+  volatile int *s_unit = reinterpret_cast<volatile int *>(smem_raw + g::OFF_MBAR + 12);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(smem_raw + g::OFF_MBAR)));
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t tphase = 0;
+  const int ncx = (p.nx + 31) / 32, ncy = (p.ny + F::BY - 1) / F::BY, ncol = ncx * ncy;
+  const int nchunk = (p.nz + p.tz - 1) / p.tz;
+  for (;;) {
+    if (tid == 0) {
+      const int i = atomicAdd(queue, 1);
+      *s_unit = i < nunits ? order[i] : -1;
+    }
+    __syncthreads();
+    const int code = *s_unit;
+    __syncthreads();  // s_unit is rewritten only after every thread has read it
+    if (code < 0) break;
+    const int idx = code & (kUnitCorr - 1), z = idx / ncol, col = idx - z * ncol;
+    const int cx = col % ncx, cy = col / ncx, z0 = z * p.tz, len = min(p.tz, p.nz - z0);
+    if (code & kUnitCorr) {
+      if (tid < 27) {
+        bool ok = true;
+        const int zz = wrap_axis(z + tid / 9 - 1, nchunk, p.pz, ok);
+        const int yy = wrap_axis(cy + (tid / 3) % 3 - 1, ncy, p.py, ok);
+        const int xx = wrap_axis(cx + tid % 3 - 1, ncx, p.px, ok);
+        if (ok) {
+          volatile int *f = done + (long long)zz * ncol + yy * ncx + xx;
+          for (long it = 0; *f == 0; ++it) {
+            if (*abort || it > (1L << 24)) {
+              *abort = 1;
+              if (io.werr) atomicExch(io.werr, 1);
+              break;
+            }
+            if (it > 32) __nanosleep(128);
+          }
+          __threadfence();
+        }
+      }
+      __syncthreads();
+      pass_segment<FID, PASS_CORR, TMAP>(p, p, 1, io, smem_raw, 0, cx * 32, cy * F::BY, z0, len,
+                                         TMAP && tma_corr ? &tm_corr : nullptr, tphase);
+    } else {
+      pass_segment<FID, PASS_PRED, TMAP>(p, p, 1, io, smem_raw, 0, cx * 32, cy * F::BY, z0, len,
+                                         TMAP && tma_pred ? &tm_pred : nullptr, tphase);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        *reinterpret_cast<volatile int *>(done + idx) = 1;
+      }
+    }
+    __syncthreads();  // shared memory is reused by the next unit
   }
 }
 
@@ -1269,7 +1368,9 @@ cudaError_t set_smem() {
   cudaError_t e = cudaFuncSetAttribute(k_heun_fused<FID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)G<Family<FID>>::SMEM);
   if (e != cudaSuccess) return e;
-  for (auto fn : {k_stencil_pass<FID, PASS_FIELD>, k_stencil_pass<FID, PASS_PRED>, k_stencil_pass<FID, PASS_CORR>}) {
+  for (auto fn : {k_stencil_pass<FID, PASS_FIELD, false>, k_stencil_pass<FID, PASS_PRED, false>,
+                  k_stencil_pass<FID, PASS_CORR, false>, k_stencil_pass<FID, PASS_FIELD, true>,
+                  k_stencil_pass<FID, PASS_PRED, true>, k_stencil_pass<FID, PASS_CORR, true>}) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GF<Family<FID>>::SMEM);
     if (e != cudaSuccess) return e;
   }
@@ -1280,6 +1381,10 @@ cudaError_t set_smem() {
   e = cudaFuncSetAttribute(k_batch_persistent<FID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)GF<Family<FID>>::SMEM);
   if (e != cudaSuccess) return e;
+  for (auto fn : {k_heun_overlap<FID, false>, k_heun_overlap<FID, true>}) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GF<Family<FID>>::SMEM);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
@@ -1322,7 +1427,8 @@ template <int FID>
 bool encode_plane_map(const StencilPlan &sp, const StencilArgs &a, const void *base, bool f32, CUtensorMap *tm) {
   using g = GF<Family<FID>>;
   memset(tm, 0, sizeof(*tm));
-  if (!sp.tma || !sp.tma_ok || !base || ((uintptr_t)base & 15u)) return false;
+  // the FP32 map serves the corrector (S~), the FP64 one the predictor and field passes (S)
+  if (!(sp.tma & (f32 ? 2 : 1)) || !sp.tma_ok || !base || ((uintptr_t)base & 15u)) return false;
   const auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encode_fn());
   if (!enc) return false;
   const cuuint64_t es = f32 ? 4 : 8;
@@ -1356,7 +1462,8 @@ cudaError_t launch_field(const StencilPlan &sp, const StencilArgs &base, int ons
   CUtensorMap tm;
   io.tma = count == 1 && encode_plane_map<FID>(sp, a, S, false, &tm) ? 1 : 0;  // one image: a 5-D box
   const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc * count);
-  k_stencil_pass<FID, PASS_FIELD><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, onsite, io, tm);
+  (io.tma ? k_stencil_pass<FID, PASS_FIELD, true> : k_stencil_pass<FID, PASS_FIELD, false>)
+      <<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, onsite, io, tm);
   return cudaGetLastError();
 }
 
@@ -1378,13 +1485,29 @@ cudaError_t launch_heun2(const StencilPlan &sp, StencilArgs a, const double *src
   io.step = a.step;
   io.nzc = (a.nz + a.tz - 1) / a.tz;
   io.werr = sp.d_bar ? &sp.d_bar->err : nullptr;
+  if (sp.ovl_grid) {
+    // one launch: clear the done flags and the queue counter, then the overlapped units
+    io.sched = nullptr;
+    CUtensorMap tp, tc;
+    const int use_p = encode_plane_map<FID>(sp, a, src, false, &tp) ? 1 : 0;
+    const int use_c = encode_plane_map<FID>(sp, a, sp.d_St, true, &tc) ? 1 : 0;
+    cudaError_t e = cudaMemsetAsync(sp.d_done, 0, (size_t)sp.n_done * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sp.d_queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    ((use_p || use_c) ? k_heun_overlap<FID, true> : k_heun_overlap<FID, false>)
+        <<<sp.ovl_grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, io, sp.d_order, sp.n_order, sp.d_queue,
+                                                                       sp.d_done, tp, tc, use_p, use_c);
+    return cudaGetLastError();
+  }
   const dim3 grid = sp.d_sched ? dim3(sp.nsched)
                                : dim3((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, io.nzc);
   CUtensorMap tm;
   io.tma = encode_plane_map<FID>(sp, a, src, false, &tm) ? 1 : 0;
-  k_stencil_pass<FID, PASS_PRED><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io, tm);
+  (io.tma ? k_stencil_pass<FID, PASS_PRED, true> : k_stencil_pass<FID, PASS_PRED, false>)
+      <<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io, tm);
   io.tma = encode_plane_map<FID>(sp, a, sp.d_St, true, &tm) ? 1 : 0;
-  k_stencil_pass<FID, PASS_CORR><<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io, tm);
+  (io.tma ? k_stencil_pass<FID, PASS_CORR, true> : k_stencil_pass<FID, PASS_CORR, false>)
+      <<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io, tm);
   return cudaGetLastError();
 }
 
@@ -1532,9 +1655,18 @@ cudaError_t persistent_occupancy(int *occ) {
 }
 
 template <int FID>
+cudaError_t overlap_occupancy(int *occ) {
+  cudaError_t e = cudaFuncSetAttribute(k_heun_overlap<FID, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)GF<Family<FID>>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_heun_overlap<FID, true>, GF<Family<FID>>::NT,
+                                                       GF<Family<FID>>::SMEM);
+}
+
+template <int FID>
 int field_occupancy() {
   int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stencil_pass<FID, PASS_CORR>, GF<Family<FID>>::NT,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stencil_pass<FID, PASS_CORR, false>, GF<Family<FID>>::NT,
                                                     GF<Family<FID>>::SMEM) != cudaSuccess ||
       occ < 1)
     occ = 1;
@@ -1664,7 +1796,7 @@ int stencil_plan(sx_ctx *c) {
     return set_error(SX_ERR_OOM, "stencil error word: device allocation failed");
   }
   sp->tma_ok = (a.nx % 4 == 0 && tensor_map_encode_fn()) ? 1 : 0;
-  sp->tma = sp->tma_ok;
+  sp->tma = sp->tma_ok ? 1 : 0;  // the predictor's tensor-copy path has no spills; the corrector's has more
   if (sp->d_sched) {
     int occ = 0;
     cudaError_t e2 = cudaSuccess;
@@ -1720,7 +1852,7 @@ int stencil_set_scheme(sx_ctx *c, int scheme) {
   }
   if (sp->scheme != scheme) ++c->plan_gen;  // workspace allocated or freed
   sp->scheme = scheme;
-  c->launches_per_step = scheme == SX_STENCIL_TWO_PASS ? 2 : 1;
+  c->launches_per_step = scheme == SX_STENCIL_TWO_PASS && !sp->ovl_grid ? 2 : 1;
   return SX_OK;
 }
 
@@ -1746,6 +1878,9 @@ void stencil_free(sx_ctx *c) {
     cudaFree(c->stencil->d_eta);
     cudaFree(c->stencil->d_sched);
     cudaFree(c->stencil->d_bar);
+    cudaFree(c->stencil->d_order);
+    cudaFree(c->stencil->d_done);
+    cudaFree(c->stencil->d_queue);
   }
   delete c->stencil;
   c->stencil = nullptr;
@@ -2126,25 +2261,148 @@ std::vector<int> chunk_lengths(int nz, int around) {
   for (int tz : {8, 16, 32, 64}) add(tz);
   return out;
 }
+
+// Queue of the overlapped step (k_heun_overlap).  Predictor units chunk by chunk (on a periodic z axis
+// the last chunk first: chunk 0's corrector reads it), columns in order.  Corrector units chunk by
+// chunk, tile rows 1 .. ncy - 1 before row 0 (whose periodic y halo is the last row), each queued
+// one-for-one with the predictor stream once `lag` more predictor units have been queued after the
+// last predictor unit it depends on (every dependency is queued before the unit itself).
+std::vector<int> overlap_order(int ncx, int ncy, int nchunk, int px, int py, int pz, long long lag) {
+  const int ncol = ncx * ncy;
+  const long long P = (long long)nchunk * ncol;
+  std::vector<int> pred, corr;
+  std::vector<long long> pos(P), need;
+  pred.reserve(P);
+  corr.reserve(P);
+  need.reserve(P);
+  std::vector<int> zorder;
+  if (pz && nchunk > 1) zorder.push_back(nchunk - 1);
+  for (int z = 0; z < nchunk; ++z)
+    if (!(pz && nchunk > 1 && z == nchunk - 1)) zorder.push_back(z);
+  for (int z : zorder)
+    for (int col = 0; col < ncol; ++col) {
+      pos[(long long)z * ncol + col] = (long long)pred.size();
+      pred.push_back(z * ncol + col);
+    }
+  auto wrap = [](int c, int n, int per, bool &ok) {
+    if (c >= 0 && c < n) return c;
+    if (!per) {
+      ok = false;
+      return 0;
+    }
+    return ((c % n) + n) % n;
+  };
+  for (int z = 0; z < nchunk; ++z)
+    for (int r = 0; r < ncy; ++r) {
+      const int cy = (r + 1) % ncy;
+      for (int cx = 0; cx < ncx; ++cx) {
+        long long nd = 0;
+        for (int t = 0; t < 27; ++t) {
+          bool ok = true;
+          const int zz = wrap(z + t / 9 - 1, nchunk, pz, ok), yy = wrap(cy + (t / 3) % 3 - 1, ncy, py, ok),
+                    xx = wrap(cx + t % 3 - 1, ncx, px, ok);
+          if (ok) nd = std::max(nd, pos[(long long)zz * ncol + yy * ncx + xx]);
+        }
+        corr.push_back((z * ncol + cy * ncx + cx) | kUnitCorr);
+        need.push_back(nd);
+      }
+    }
+  std::vector<int> out;
+  out.reserve(2 * P);
+  long long pi = 0, ci = 0;
+  while (pi < P || ci < P) {
+    if (pi < P) out.push_back(pred[pi++]);
+    if (ci < P && (pi >= P || need[ci] + lag < pi)) out.push_back(corr[ci++]);
+  }
+  return out;
+}
+
+void overlap_free(StencilPlan &sp) {
+  cudaFree(sp.d_order);
+  cudaFree(sp.d_done);
+  cudaFree(sp.d_queue);
+  sp.d_order = sp.d_done = sp.d_queue = nullptr;
+  sp.n_order = sp.n_done = sp.ovl_grid = 0;
+}
+
+// The overlapped launch needs every halo inside the neighbouring units: edge tile columns, rows and
+// the last z chunk at least R wide.
+bool overlap_fits(const sx_ctx *c, const StencilPlan &sp, int tz) {
+  const int R = family_r(sp.family), BY = family_by(sp.family);
+  const int nx = c->geo.nx, ny = c->geo.ny, nz = c->geo.nz;
+  const long long units = (long long)((nx + 31) / 32) * ((ny + BY - 1) / BY) * ((nz + tz - 1) / tz);
+  return tz >= R && (nx % 32 == 0 || nx % 32 >= R) && (ny % BY == 0 || ny % BY >= R) &&
+         nz - (nz + tz - 1) / tz * tz + tz >= R && units < (1LL << 29);
+}
+
+int overlap_setup(sx_ctx *c, StencilPlan &sp, int tz) {
+  overlap_free(sp);
+  if (!overlap_fits(c, sp, tz))
+    return set_error(SX_ERR_ARG, "overlapped launch: an edge tile or the last z chunk is narrower than the halo");
+  int occ = 0;
+  cudaError_t e;
+  switch (sp.family) {
+    case FAM_SC6_ISO: e = overlap_occupancy<FAM_SC6_ISO>(&occ); break;
+    case FAM_SC6_TEN: e = overlap_occupancy<FAM_SC6_TEN>(&occ); break;
+    case FAM_SC26_ISO: e = overlap_occupancy<FAM_SC26_ISO>(&occ); break;
+    case FAM_SC26_TEN: e = overlap_occupancy<FAM_SC26_TEN>(&occ); break;
+    case FAM_SC26_SHELL: e = overlap_occupancy<FAM_SC26_SHELL>(&occ); break;
+    case FAM_SC32_ISO: e = overlap_occupancy<FAM_SC32_ISO>(&occ); break;
+    default: e = overlap_occupancy<FAM_BCC4>(&occ); break;
+  }
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    return set_error(SX_ERR_CUDA, "overlapped launch: no resident CTA");
+  }
+  const int BY = family_by(sp.family);
+  const int ncx = (c->geo.nx + 31) / 32, ncy = (c->geo.ny + BY - 1) / BY, nchunk = (c->geo.nz + tz - 1) / tz;
+  const int grid = occ * sp.nsm;
+  const std::vector<int> order = overlap_order(ncx, ncy, nchunk, c->geo.px, c->geo.py, c->geo.pz, grid);
+  const int ndone = ncx * ncy * nchunk;
+  if (cudaMalloc(&sp.d_order, order.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&sp.d_done, (size_t)ndone * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&sp.d_queue, sizeof(int)) != cudaSuccess ||
+      cudaMemcpy(sp.d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    overlap_free(sp);
+    return set_error(SX_ERR_OOM, "overlapped launch: device allocation failed");
+  }
+  sp.n_order = (int)order.size();
+  sp.n_done = ndone;
+  sp.ovl_grid = grid;
+  return SX_OK;
+}
 }  // namespace
 
 std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c, bool thermal) {
   const StencilPlan &sp = *c->stencil;
   std::vector<TileChoice> out;
-  for (int tz : chunk_lengths(c->geo.nz, sp.tz)) out.push_back({SX_STENCIL_FUSED, tz, 0, 0, sp.tma_ok});
+  const int tma0 = sp.tma_ok ? 1 : 0;
+  for (int tz : chunk_lengths(c->geo.nz, sp.tz)) out.push_back({SX_STENCIL_FUSED, tz, 0, 0, tma0});
   // two-pass: normals stored by the predictor, and (thermal steps) regenerated by the corrector
   for (int regen = 0; regen <= (thermal ? 1 : 0); ++regen) {
-    for (int tz : chunk_lengths(c->geo.nz, sp.tz2)) out.push_back({SX_STENCIL_TWO_PASS, tz, 0, regen, sp.tma_ok});
+    for (int tz : chunk_lengths(c->geo.nz, sp.tz2)) out.push_back({SX_STENCIL_TWO_PASS, tz, 0, regen, tma0});
     const int BY = family_by(sp.family);
     const long long ncol = (long long)((c->geo.nx + 31) / 32) * ((c->geo.ny + BY - 1) / BY);
     if (ncol * c->geo.nz < (1LL << 31))
-      for (int f : {1, 2}) out.push_back({SX_STENCIL_TWO_PASS, sp.tz2, f, regen, sp.tma_ok});
+      for (int f : {1, 2}) out.push_back({SX_STENCIL_TWO_PASS, sp.tz2, f, regen, tma0});
+    // one overlapped launch, z chunks of about nz/4 .. nz/16 planes, when the predictor units are at least
+    // four times the resident CTA slots
+    std::vector<int> otz;
+    for (int k : {4, 8, 16}) {
+      const int nch = std::min(k, c->geo.nz), tz = (c->geo.nz + nch - 1) / nch;
+      if (std::find(otz.begin(), otz.end(), tz) == otz.end() && overlap_fits(c, sp, tz) &&
+          ncol * ((c->geo.nz + tz - 1) / tz) >= 4LL * sp.nsm * std::max(sp.occ_field, 1))
+        otz.push_back(tz);
+    }
+    for (int tz : otz) out.push_back({SX_STENCIL_TWO_PASS, tz, kSchedOverlap, regen, tma0});
   }
   return out;
 }
 
 int stencil_apply_tiles(sx_ctx *c, const TileChoice &t) {
   StencilPlan &sp = *c->stencil;
+  if (t.tma < 0 || t.tma > 3) return set_error(SX_ERR_ARG, "plane staging mask must be in 0 .. 3");
   if (t.tma && !sp.tma_ok)
     return set_error(SX_ERR_UNSUPPORTED, "tensor-copied planes need n[0] a multiple of 4 and the driver's encoder");
   sp.tma = t.tma;
@@ -2158,6 +2416,23 @@ int stencil_apply_tiles(sx_ctx *c, const TileChoice &t) {
   }
   sp.tz2 = t.tz;
   sp.base.regen = t.regen;
+  if (t.sched == kSchedOverlap) {
+    cudaFree(sp.d_sched);
+    sp.d_sched = nullptr;
+    sp.nsched = 0;
+    sp.persistent = 0;
+    sp.sched_factor = 0;
+    c->launches_per_step = 2;
+    if ((rc = overlap_setup(c, sp, t.tz)) != SX_OK) return rc;
+    sp.sched_factor = kSchedOverlap;
+    c->launches_per_step = 1;
+    return SX_OK;
+  }
+  if (sp.ovl_grid) {
+    overlap_free(sp);
+    sp.sched_factor = 0;
+    c->launches_per_step = 2;
+  }
   if (t.sched == sp.sched_factor && (t.sched == 0 || sp.d_sched)) return SX_OK;
   cudaFree(sp.d_sched);
   sp.d_sched = nullptr;
@@ -2193,7 +2468,7 @@ void stencil_restore_fused_tz(sx_ctx *c, int tz) {
 TileChoice stencil_current_tiles(const sx_ctx *c) {
   const StencilPlan &sp = *c->stencil;
   if (sp.scheme == SX_STENCIL_FUSED) return {SX_STENCIL_FUSED, sp.tz, 0, 0, sp.tma};
-  return {SX_STENCIL_TWO_PASS, sp.tz2, sp.d_sched ? sp.sched_factor : 0, sp.base.regen, sp.tma};
+  return {SX_STENCIL_TWO_PASS, sp.tz2, (sp.d_sched || sp.ovl_grid) ? sp.sched_factor : 0, sp.base.regen, sp.tma};
 }
 
 void stencil_tiles_info(const sx_ctx *c, int64_t out[8]) {
@@ -2213,8 +2488,8 @@ void stencil_tiles_info(const sx_ctx *c, int64_t out[8]) {
     out[1] = 32;
     out[2] = BY;
     out[3] = sp.d_sched ? 0 : sp.tz2;
-    out[4] = sp.d_sched ? sp.nsched : cx * cy * ((nz + sp.tz2 - 1) / sp.tz2);
-    out[5] = sp.d_sched ? sp.sched_factor : 0;
+    out[4] = sp.d_sched ? sp.nsched : sp.ovl_grid ? sp.ovl_grid : cx * cy * ((nz + sp.tz2 - 1) / sp.tz2);
+    out[5] = (sp.d_sched || sp.ovl_grid) ? sp.sched_factor : 0;
     out[6] = sp.base.regen;
   }
   out[7] = sp.tma;

@@ -196,14 +196,14 @@ def test_tensor_copied_planes_give_the_same_step_and_field(name, n, pbc):
     sx.sx_llg_heun_step_out(s.ctx, S, ref, p, 4, s.nsite)
     ref_b64 = s.field(S)
     ref_b32 = s.field(S, dtype=torch.float32)
-    for shape in [(nz, 0, 0), (5, 0, 1), (nz, 1, 0), (nz, 2, 1)]:
-        sx.sx_set_tiles(s.ctx, "two_pass", *shape, 1)
-        assert sx.sx_plan_tiles(s.ctx)["tma_staging"] == 1
+    for shape, mask in [((nz, 0, 0), 3), ((5, 0, 1), 1), ((nz, 1, 0), 2), ((nz, 2, 1), 3)]:
+        sx.sx_set_tiles(s.ctx, "two_pass", *shape, mask)
+        assert sx.sx_plan_tiles(s.ctx)["tma_staging"] == mask
         got = torch.empty_like(S)
         sx.sx_llg_heun_step_out(s.ctx, S, got, p, 4, s.nsite)
-        assert torch.equal(got, ref), shape
-        assert torch.equal(s.field(S), ref_b64), shape
-        assert torch.equal(s.field(S, dtype=torch.float32), ref_b32), shape
+        assert torch.equal(got, ref), (shape, mask)
+        assert torch.equal(s.field(S), ref_b64), (shape, mask)
+        assert torch.equal(s.field(S, dtype=torch.float32), ref_b32), (shape, mask)
     sx.sx_device_status(s.ctx)  # no bounded wait gave up
 
 
@@ -213,3 +213,45 @@ def test_tensor_copied_planes_need_rows_of_16_bytes():
     assert sx.sx_plan_tiles(s.ctx)["tma_staging"] == 0
     with pytest.raises(sx.SxError):
         sx.sx_set_tiles(s.ctx, "two_pass", 12, 0, 0, 1)
+
+
+# One overlapped launch per step (predictor and corrector units from a dependency-ordered queue) against
+# the two pass launches: periodic and open faces, partial edge tiles, the last z chunk shorter than the
+# others, 1- and 2-cell halos, stored and regenerated normals, both plane stagings, and three steps in a
+# row (the queue and the done flags are reset by every step).
+@pytest.mark.parametrize("name,n,pbc,tzs", [("sc_j123_dmi", (96, 80, 40), (1, 1, 1), (10, 7)),
+                                             ("sc_j123_dmi", (100, 84, 21), (0, 0, 0), (5, 21)),
+                                             ("sc_j123_dmi", (64, 48, 30), (1, 0, 1), (4, 30)),
+                                             ("bcc_4shell", (64, 48, 24), (1, 1, 1), (6, 5)),
+                                             ("sc_4shell", (96, 50, 26), (1, 1, 0), (7, 8))])
+def test_overlapped_launch_gives_the_same_steps(name, n, pbc, tzs):
+    s, w = sx.system_from_workload(name, n, pbc=pbc)
+    s.plan("stencil", "fp32")
+    S = torch.from_numpy(random_spins(s.nsub, n, 7)).cuda()
+    p = sx.llg_params(w["dt"], w["alpha"], max(w["T"], 30.0), seed=5)
+    nz = n[2]
+    sx.sx_set_tiles(s.ctx, "two_pass", nz, 0, 0, 0)
+    ref = S.clone()
+    sx.sx_llg_heun_step(s.ctx, ref, torch.empty_like(S), p, 11, 3, s.nsite)
+    for tz, regen, tma in [(tzs[0], 0, 3), (tzs[1], 1, 0), (tzs[0], 1, 1), (tzs[1], 0, 2)]:
+        sx.sx_set_tiles(s.ctx, "two_pass", tz, 5, regen, tma)
+        t = sx.sx_plan_tiles(s.ctx)
+        assert t["ring_or_schedule"] == 5 and t["tile_z"] == tz and t["ctas"] > 0
+        assert sx.sx_plan_info(s.ctx)["launches_per_step"] == 1
+        got = S.clone()
+        sx.sx_llg_heun_step(s.ctx, got, torch.empty_like(S), p, 11, 3, s.nsite)
+        assert torch.equal(got, ref), (tz, regen, tma)
+    sx.sx_device_status(s.ctx)  # no bounded wait gave up
+    sx.sx_set_tiles(s.ctx, "two_pass", nz, 0, 0, 0)
+    assert sx.sx_plan_info(s.ctx)["launches_per_step"] == 2
+
+
+def test_overlapped_launch_needs_edge_tiles_as_wide_as_the_halo():
+    s, w = sx.system_from_workload("sc_4shell", (65, 48, 20))  # halo 2, last tile column 1 cell wide
+    s.plan("stencil", "fp32")
+    with pytest.raises(sx.SxError):
+        sx.sx_set_tiles(s.ctx, "two_pass", 5, 5, 0, 0)
+    s2, _ = sx.system_from_workload("sc_4shell", (64, 48, 21))  # last z chunk of 1 plane
+    s2.plan("stencil", "fp32")
+    with pytest.raises(sx.SxError):
+        sx.sx_set_tiles(s2.ctx, "two_pass", 5, 5, 0, 0)
