@@ -225,11 +225,14 @@ def run_reference(args):
 
 
 # DRAM bytes per spin-step of the Heun step measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of both
-# two-pass launches of one step, profiles/heun_bench_sc_j123_dmi_1024.md), keyed by (workload, scheme, schedule
-# factor, plane staging); reported as roofline.traffic when the bench runs that shape
-MEASURED_TRAFFIC = {("sc_j123_dmi_1024", "two_pass", 0, 0): (152.7, "ncu of the 1024^3 bench step, z chunk 512, "
-                                                                     "site-by-site plane copies "
-                                                                     "(profiles/heun_bench_sc_j123_dmi_1024.md)")}
+# two-pass launches of one step, profiles/heun_bench_sc_j123_dmi_1024.md), keyed by (workload, scheme, launch
+# shape, plane staging, z chunk); reported as roofline.traffic when the bench runs that shape
+MEASURED_TRAFFIC = {
+    ("sc_j123_dmi_1024", "two_pass", 0, 0, 171): (147.6, "ncu of the 1024^3 bench step, z chunk 171, site-by-site "
+                                                         "plane copies (profiles/heun_bench_sc_j123_dmi_1024.md)"),
+    ("sc_j123_dmi_1024", "two_pass", 0, 0, 512): (152.7, "ncu of the 1024^3 bench step, z chunk 512, site-by-site "
+                                                         "plane copies (profiles/heun_bench_sc_j123_dmi_1024.md)"),
+}
 
 
 def run_ours(args):
@@ -259,7 +262,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     p = sx.llg_params(w["dt"], w["alpha"], w["T"], seed=rep["seed"], replica=rep["replica"])
     tune = None
-    if args.scheme == "autotune" and args.backend == "stencil":
+    if args.tiles and args.backend == "stencil":
+        sx.sx_set_tiles(s.ctx, "two_pass", *[int(v) for v in args.tiles.split(",")])
+        info = s.info()
+    elif args.scheme == "autotune" and args.backend == "stencil":
         # setup, untimed: time both stencil schemes on this replica's spins and keep the faster
         chosen, tune = sx.sx_autotune(s.ctx, S, S2, p, nsite, steps=3, stream=stream)
         info = s.info()
@@ -334,7 +340,8 @@ def run_ours(args):
     launches = info["launches_per_step"]
     achieved = BYTES_PER_SPIN_STEP * nsite / (ms_per_step * 1e-3) / 1e9
     traffic, traffic_src = args.traffic, "--traffic" if args.traffic is not None else None
-    meas = MEASURED_TRAFFIC.get((args.workload, scheme, tiles.get("ring_or_schedule", 0), tiles.get("tma_staging", 0)))
+    meas = MEASURED_TRAFFIC.get((args.workload, scheme, tiles.get("ring_or_schedule", 0), tiles.get("tma_staging", 0),
+                                 tiles.get("tile_z", 0)))
     if traffic is None and meas is not None and args.backend == "stencil":
         traffic, traffic_src = meas[0] * nsite, meas[1]
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -755,6 +762,9 @@ def main():
                     help="dram bytes per launch of the step kernel from an ncu capture (GB/s roofline context)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dipolar", action="store_true", help="add the point-dipole field (FFT backend)")
+    ap.add_argument("--tiles", default=None,
+                    help="TZ,LAUNCH,REGEN,MASK: run the two-pass scheme with this tile shape (sx_set_tiles in[1..4]) "
+                         "instead of autotuning")
     ap.add_argument("--scheme", choices=["autotune", "auto", "fused", "two_pass"], default="autotune",
                     help="stencil Heun scheme (default: time both on the bench's spins, keep the faster)")
     args = ap.parse_args()

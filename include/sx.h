@@ -270,7 +270,8 @@ int sx_set_stencil_scheme(sx_ctx *ctx, int scheme);
  * chunk of a CTA, and for the two-pass scheme the launch shape (a z-chunked
  * grid, a balanced schedule over 1 or 2 times the resident CTA slots, or the
  * overlapped launch with z chunks of about n[2]/4 .. n[2]/16 planes) and, at
- * the fastest shape, the other plane staging (sx_set_tiles in[4]).
+ * the fastest shape, the other plane stagings (sx_set_tiles in[4]; kept
+ * only when at least 1% faster than the plan's site-by-site staging).
  * IGEMM_TC: the depth of the B-operand ring (2..4) and the CTAs per SM (1 or
  * 2).  Each candidate runs `steps` (>= 1) out-of-place steps S -> S_scratch
  * (S is not modified; S_scratch is overwritten) after one warm-up step.

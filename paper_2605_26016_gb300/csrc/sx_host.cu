@@ -600,7 +600,7 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
       }
     }
     // the best shape with the other plane stagings of the pass kernels (tensor copies or site by site for
-    // the predictor and for the corrector)
+    // the predictor and for the corrector), kept only when at least 1% faster
     const TileChoice top = best;
     for (int mask = 0; mask < 4 && e == cudaSuccess && best_ms >= 0.0 && top.scheme == SX_STENCIL_TWO_PASS;
          ++mask) {
@@ -610,7 +610,7 @@ int sx_autotune(sx_ctx *c, const double *S, double *S_scratch, const sx_llg_para
       if (stencil_apply_tiles(c, t) != SX_OK) continue;
       double ms = 0.0;
       time_steps(&ms);
-      if (e == cudaSuccess && ms < best_ms) {
+      if (e == cudaSuccess && ms < 0.99 * best_ms) {
         best_ms = ms;
         best = t;
         if (times_ms) times_ms[t.scheme - 1] = ms;

@@ -1796,7 +1796,7 @@ int stencil_plan(sx_ctx *c) {
     return set_error(SX_ERR_OOM, "stencil error word: device allocation failed");
   }
   sp->tma_ok = (a.nx % 4 == 0 && tensor_map_encode_fn()) ? 1 : 0;
-  sp->tma = sp->tma_ok ? 1 : 0;  // the predictor's tensor-copy path has no spills; the corrector's has more
+  sp->tma = 0;  // site-by-site staging unless the autotuner or sx_set_tiles chooses tensor copies
   if (sp->d_sched) {
     int occ = 0;
     cudaError_t e2 = cudaSuccess;
@@ -2377,7 +2377,7 @@ int overlap_setup(sx_ctx *c, StencilPlan &sp, int tz) {
 std::vector<TileChoice> stencil_tile_candidates(const sx_ctx *c, bool thermal) {
   const StencilPlan &sp = *c->stencil;
   std::vector<TileChoice> out;
-  const int tma0 = sp.tma_ok ? 1 : 0;
+  const int tma0 = 0;  // the autotuner tries the tensor-copy stagings at its best shape
   for (int tz : chunk_lengths(c->geo.nz, sp.tz)) out.push_back({SX_STENCIL_FUSED, tz, 0, 0, tma0});
   // two-pass: normals stored by the predictor, and (thermal steps) regenerated by the corrector
   for (int regen = 0; regen <= (thermal ? 1 : 0); ++regen) {

@@ -190,8 +190,8 @@ def test_tensor_copied_planes_give_the_same_step_and_field(name, n, pbc):
     S = torch.from_numpy(random_spins(s.nsub, n, 5)).cuda()
     p = sx.llg_params(w["dt"], w["alpha"], max(w["T"], 30.0), seed=3)
     nz = n[2]
-    sx.sx_set_tiles(s.ctx, "two_pass", nz, 0, 0, 0)  # every tile copies site by site
-    assert sx.sx_plan_tiles(s.ctx)["tma_staging"] == 0
+    assert sx.sx_plan_tiles(s.ctx)["tma_staging"] == 0  # the plan's default: every tile copies site by site
+    sx.sx_set_tiles(s.ctx, "two_pass", nz, 0, 0, 0)
     ref = torch.empty_like(S)
     sx.sx_llg_heun_step_out(s.ctx, S, ref, p, 4, s.nsite)
     ref_b64 = s.field(S)
