@@ -948,6 +948,15 @@ int sx_llg_heun_host(sx_ctx *c, double *S_host, const sx_llg_params *p, uint64_t
       if (e != cudaSuccess) return cuda_error(e, "cudaMalloc host-path buffers");
     }
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->backend == SX_BACKEND_STENCIL) {
+    // two-pass stencil plans pipeline chunked transfers against the passes
+    e = stencil_heun_host(c, S_host, c->d_host_S[0], c->d_host_S[1], h, step0, nsteps, st);
+    if (e == cudaSuccess) {
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(e, "stream synchronize");
+      return take_status(c, st);
+    }
+    if (e != cudaErrorNotSupported) return cuda_error(e, "pipelined host-array step");
+  }
   if ((e = cudaMemcpyAsync(c->d_host_S[0], S_host, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_error(e, "host to device copy");
   for (int k = 0; k < nsteps; ++k) {

@@ -193,6 +193,10 @@ int stencil_set_scheme(sx_ctx *c, int scheme);  // SX_STENCIL_*, on a planned st
 int stencil_scheme(const sx_ctx *c);
 // the two-pass scheme's persistent multi-step launch (lattices with fewer tile columns than CTA slots)
 bool stencil_persistent_ok(const sx_ctx *c);
+// Heun steps on a host array with chunked transfers overlapping the two passes; cudaErrorNotSupported
+// when the plan does not take that path
+cudaError_t stencil_heun_host(const sx_ctx *c, double *S_host, double *dA, double *dB, const HeunConst &h,
+                              uint64_t step0, int nsteps, cudaStream_t st);
 cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S1, const HeunConst &h,
                                           uint64_t step0, int nsteps, cudaStream_t st);
 int stencil_check_error(const sx_ctx *c);

@@ -690,6 +690,7 @@ struct PassIO {
                      // [sched[k].x, sched[k].x + sched[k].y) of u = column * nz + z; null: the grid tiles
   int tma;           // 1: interior tiles stage planes with the launch's tensor map (k_stencil_pass only)
   int *werr;         // set when a bounded wait on a tensor copy gives up
+  int zc0;           // k_stencil_pass on the grid: first z chunk of the launch (chunk zc0 + blockIdx.z)
 };
 
 // ------------------------------------------------------------------ tensor copies of the pass kernels
@@ -1016,7 +1017,7 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
     run_scheduled<FID, MODE, TMAP>(p, onsite, io, smem_raw, blockIdx.x, tm, tphase);
   } else {
     const int img = blockIdx.z / io.nzc, zc = blockIdx.z - img * io.nzc;
-    const int z0 = zc * p.tz;
+    const int z0 = (io.zc0 + zc) * p.tz;
     pass_segment<FID, MODE, TMAP>(p, p, onsite, io, smem_raw, img, blockIdx.x * 32, blockIdx.y * F::BY, z0,
                                   min(p.tz, p.nz - z0), tm, tphase);
   }
@@ -1220,6 +1221,7 @@ __device__ __forceinline__ void batch_units(const StencilArgs &p, const BatchRep
     io.step = step;
     io.tma = 0;
     io.werr = nullptr;
+    io.zc0 = 0;
     io.sched = nullptr;
     io.bf = nullptr;
     if (reps[r].kind == 0) {
@@ -1508,6 +1510,37 @@ cudaError_t launch_heun2(const StencilPlan &sp, StencilArgs a, const double *src
   io.tma = encode_plane_map<FID>(sp, a, sp.d_St, true, &tm) ? 1 : 0;
   (io.tma ? k_stencil_pass<FID, PASS_CORR, true> : k_stencil_pass<FID, PASS_CORR, false>)
       <<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io, tm);
+  return cudaGetLastError();
+}
+
+// One pass (PRED or CORR) of the two-pass step over z chunk zc (a.tz planes) on the grid of tile columns.
+template <int FID>
+cudaError_t launch_pass_chunk(const StencilPlan &sp, const StencilArgs &a, const double *src, double *dst, int mode,
+                              int zc, cudaStream_t st) {
+  using g = GF<Family<FID>>;
+  PassIO io;
+  memset(&io, 0, sizeof(io));
+  io.S = src;
+  io.St = sp.d_St;
+  io.St_out = sp.d_St;
+  io.f0 = sp.d_f0;
+  io.eta = sp.d_eta;
+  io.Sout = dst;
+  io.step = a.step;
+  io.nzc = 1;
+  io.zc0 = zc;
+  io.werr = sp.d_bar ? &sp.d_bar->err : nullptr;
+  const dim3 grid((a.nx + 31) / 32, (a.ny + Family<FID>::BY - 1) / Family<FID>::BY, 1);
+  CUtensorMap tm;
+  if (mode == PASS_PRED) {
+    io.tma = encode_plane_map<FID>(sp, a, src, false, &tm) ? 1 : 0;
+    (io.tma ? k_stencil_pass<FID, PASS_PRED, true> : k_stencil_pass<FID, PASS_PRED, false>)
+        <<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io, tm);
+  } else {
+    io.tma = encode_plane_map<FID>(sp, a, sp.d_St, true, &tm) ? 1 : 0;
+    (io.tma ? k_stencil_pass<FID, PASS_CORR, true> : k_stencil_pass<FID, PASS_CORR, false>)
+        <<<grid, dim3(32, GF<Family<FID>>::TYT), g::SMEM, st>>>(a, 1, io, tm);
+  }
   return cudaGetLastError();
 }
 
@@ -1937,6 +1970,134 @@ StencilArgs heun_args(const sx_ctx *c, const HeunConst &h, uint64_t step) {
   return a;
 }
 }  // namespace
+
+namespace {
+cudaError_t pass_chunk(const StencilPlan &sp, const StencilArgs &a, const double *src, double *dst, int mode, int zc,
+                       cudaStream_t st) {
+  switch (sp.family) {
+    case FAM_SC6_ISO: return launch_pass_chunk<FAM_SC6_ISO>(sp, a, src, dst, mode, zc, st);
+    case FAM_SC6_TEN: return launch_pass_chunk<FAM_SC6_TEN>(sp, a, src, dst, mode, zc, st);
+    case FAM_SC26_ISO: return launch_pass_chunk<FAM_SC26_ISO>(sp, a, src, dst, mode, zc, st);
+    case FAM_SC26_TEN: return launch_pass_chunk<FAM_SC26_TEN>(sp, a, src, dst, mode, zc, st);
+    case FAM_SC26_SHELL: return launch_pass_chunk<FAM_SC26_SHELL>(sp, a, src, dst, mode, zc, st);
+    case FAM_SC32_ISO: return launch_pass_chunk<FAM_SC32_ISO>(sp, a, src, dst, mode, zc, st);
+    default: return launch_pass_chunk<FAM_BCC4>(sp, a, src, dst, mode, zc, st);
+  }
+}
+}  // namespace
+
+// Steps on a host array with the transfers pipelined against the two passes.  The state is cut into K
+// z chunks (about 16, each at least max(r, 4) planes) and goes up chunk by chunk on a copy stream.  In the
+// first step the predictor of chunk c waits only for the chunks holding its planes and their halo (c - 1 ..
+// c + 1, wrapped on a periodic z axis), so it runs while later chunks are still in flight.  In the last
+// step each corrector chunk is launched as soon as the predictor chunks of its S~ halo have been, and
+// goes down on a second copy stream right after it, overlapping the uploads (the link is full duplex)
+// and the remaining passes.  The per-site arithmetic is that of the two-pass step on any z chunk, so the
+// results equal those of whole copies and sx_llg_heun_step.  cudaErrorNotSupported when the plan does
+// not take this path (not the two-pass scheme, too few planes); the caller then copies whole arrays.
+cudaError_t stencil_heun_host(const sx_ctx *c, double *S_host, double *dA, double *dB, const HeunConst &h,
+                              uint64_t step0, int nsteps, cudaStream_t st) {
+  const StencilPlan &sp = *c->stencil;
+  if (sp.scheme != SX_STENCIL_TWO_PASS || nsteps < 1) return cudaErrorNotSupported;
+  const int R = family_r(sp.family), nz = c->geo.nz;
+  int K = std::min(16, nz / std::max(R, 4));
+  if (K < 4) return cudaErrorNotSupported;
+  const int tzh = (nz + K - 1) / K;
+  K = (nz + tzh - 1) / tzh;
+  if (nz - (K - 1) * tzh < R) return cudaErrorNotSupported;
+  const bool pz = c->geo.pz != 0;
+  const long long plane = (long long)c->geo.nx * c->geo.ny, subvol = plane * nz, nsite = c->geo.nsite;
+  const int nsub = c->lat.nsub;
+  // the chunks whose planes chunk z needs (itself and its neighbours), as indices 0 .. K - 1
+  auto neighbours = [&](int z, int out[3]) {
+    int n = 0;
+    for (int d = -1; d <= 1; ++d) {
+      int q = z + d;
+      if (q < 0 || q >= K) {
+        if (!pz) continue;
+        q = (q + K) % K;
+      }
+      out[n++] = q;
+    }
+    return n;
+  };
+  auto copy_chunk = [&](double *dev, int z, bool up, cudaStream_t cs) {
+    const long long z0 = (long long)z * tzh, len = std::min<long long>(tzh, nz - z0);
+    cudaError_t e = cudaSuccess;
+    for (int m = 0; m < 3 && e == cudaSuccess; ++m)
+      for (int a = 0; a < nsub && e == cudaSuccess; ++a) {
+        const long long off = m * nsite + a * subvol + z0 * plane;
+        e = up ? cudaMemcpyAsync(dev + off, S_host + off, len * plane * sizeof(double), cudaMemcpyHostToDevice, cs)
+               : cudaMemcpyAsync(S_host + off, dev + off, len * plane * sizeof(double), cudaMemcpyDeviceToHost, cs);
+      }
+    return e;
+  };
+  cudaStream_t sin = nullptr, sout = nullptr;
+  std::vector<cudaEvent_t> ev(2 * K + 2, nullptr);  // [0, K): chunk uploaded, [K, 2K): chunk corrected, start, end
+  cudaError_t e = cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking);
+  for (auto &x : ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+  cudaEvent_t &start = ev[2 * K], &done = ev[2 * K + 1];
+  if (e == cudaSuccess) e = cudaEventRecord(start, st);  // after the caller's earlier work on st
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, start, 0);
+  for (int z = 0; z < K && e == cudaSuccess; ++z) {
+    e = copy_chunk(dA, z, true, sin);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[z], sin);
+  }
+  double *src = dA, *dst = dB;
+  for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+    StencilArgs a = heun_args(c, h, step0 + (uint64_t)k);
+    a.tz = tzh;
+    const bool first = k == 0, last = k == nsteps - 1;
+    // predictor chunks in the order their inputs arrive (uploads run in chunk order)
+    std::vector<int> order(K), need(K);
+    for (int z = 0; z < K; ++z) {
+      int nb[3];
+      const int n = neighbours(z, nb);
+      need[z] = *std::max_element(nb, nb + n);
+      order[z] = z;
+    }
+    if (first) std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return need[x] < need[y]; });
+    std::vector<char> pred_done(K, 0), corr_done(K, 0);
+    auto corr = [&](int z) {
+      cudaError_t r = pass_chunk(sp, a, src, dst, PASS_CORR, z, st);
+      corr_done[z] = 1;
+      if (r == cudaSuccess && last) {
+        r = cudaEventRecord(ev[K + z], st);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(sout, ev[K + z], 0);
+        if (r == cudaSuccess) r = copy_chunk(dst, z, false, sout);
+      }
+      return r;
+    };
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
+      const int z = order[i];
+      if (first) e = cudaStreamWaitEvent(st, ev[need[z]], 0);
+      if (e == cudaSuccess) e = pass_chunk(sp, a, src, dst, PASS_PRED, z, st);
+      pred_done[z] = 1;
+      // corrector chunks whose S~ halo is complete, as early as possible in the last step
+      for (int y = 0; y < K && e == cudaSuccess && last; ++y) {
+        if (corr_done[y]) continue;
+        int nb[3];
+        const int n = neighbours(y, nb);
+        bool ready = true;
+        for (int j = 0; j < n; ++j) ready = ready && pred_done[nb[j]];
+        if (ready) e = corr(y);
+      }
+    }
+    for (int y = 0; y < K && e == cudaSuccess; ++y)
+      if (!corr_done[y]) e = corr(y);
+    std::swap(src, dst);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(done, sout);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, done, 0);
+  for (auto &x : ev)
+    if (x) cudaEventDestroy(x);
+  if (sin) cudaStreamDestroy(sin);
+  if (sout) cudaStreamDestroy(sout);
+  return e;
+}
 
 // nsteps steps in one persistent launch, S0 -> S1 -> S0 ...; the result is in S_{nsteps mod 2}
 cudaError_t stencil_heun_steps_persistent(const sx_ctx *c, double *S0, double *S1, const HeunConst &h,

@@ -255,3 +255,28 @@ def test_overlapped_launch_needs_edge_tiles_as_wide_as_the_halo():
     s2.plan("stencil", "fp32")
     with pytest.raises(sx.SxError):
         sx.sx_set_tiles(s2.ctx, "two_pass", 5, 5, 0, 0)
+
+
+# Host-array steps of the two-pass scheme pipeline chunked uploads and downloads against the passes; the
+# results equal device steps bit for bit: periodic and open z, last chunk shorter than the others, 2-cell
+# halos, one and several steps, a pageable host array, and the fused scheme (whole copies).
+@pytest.mark.parametrize("name,n,pbc", [("sc_j123_dmi", (40, 36, 64), (1, 1, 1)),
+                                         ("sc_j123_dmi", (33, 20, 30), (1, 1, 0)),
+                                         ("sc_4shell", (40, 24, 37), (1, 1, 1)),
+                                         ("bcc_4shell", (20, 18, 24), (1, 0, 1))])
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_pipelined_host_steps_equal_device_steps(name, n, pbc, nsteps):
+    s, w = sx.system_from_workload(name, n, pbc=pbc)
+    s.plan("stencil", "fp32")
+    S = torch.from_numpy(random_spins(s.nsub, n, 12)).cuda()
+    kw = dict(dt=w["dt"], alpha=w["alpha"], T=max(w["T"], 30.0), seed=4, step0=7, nsteps=nsteps)
+    for scheme, pinned in [("two_pass", True), ("two_pass", False), ("fused", True)]:
+        sx.sx_set_stencil_scheme(s.ctx, scheme)
+        Sd = S.clone()
+        s.heun(Sd, torch.empty_like(Sd), **kw)
+        Sh = S.cpu()
+        if pinned:
+            Sh = Sh.pin_memory()
+        s.heun_host(Sh, **kw)
+        torch.cuda.synchronize()
+        assert torch.equal(Sd.cpu(), Sh), (scheme, pinned)
