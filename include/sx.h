@@ -384,7 +384,12 @@ int sx_llg_heun_step_out(sx_ctx *ctx, const double *S_in, double *S_out, const s
 /* End-to-end variant on HOST memory: copies S_host to the device, runs
  * nsteps Heun steps in library-owned device buffers and copies the result
  * back into S_host.  Synchronises the stream.  S_host may be pinned or
- * pageable; pinned memory gives full copy bandwidth. */
+ * pageable; pinned memory gives full copy bandwidth.  On two-pass STENCIL
+ * plans with at least 4 z chunks of max(range, 4) planes the copies go in
+ * z chunks on two library streams, pipelined against the passes: the first
+ * step's predictor chunks start as their planes (and halo planes) arrive,
+ * the last step's corrector chunks go back as soon as they are written,
+ * uploads and downloads overlapping.  The results are those of whole copies. */
 int sx_llg_heun_host(sx_ctx *ctx, double *S_host, const sx_llg_params *p, uint64_t step0, int nsteps,
                      void *stream);
 
