@@ -108,3 +108,31 @@ def test_path_step_does_not_converge_on_nan(method, optimizer):
     chain[3].reshape(3, -1)[0, 17] = math.nan
     X = torch.from_numpy(np.ascontiguousarray(chain)).cuda()
     _expect_numeric(s.path, X, method=method, optimizer=optimizer, dt=0.01, tol=1e30, max_iter=10, check_every=1)
+
+
+# The FP32 field path rounds the FP64 spins to the nearest FP32 value, a value exactly halfway between two
+# FP32 values to the one of larger magnitude: nearest-neighbour exchange J = 1 around one non-zero spin
+# whose components are such halfway values (and one whose are not), open faces, so each neighbour's FP32
+# field is that spin rounded.
+@pytest.mark.parametrize("fam", ["stencil", "fft"])
+def test_fp32_field_rounds_spins_to_nearest_even(fam):
+    from workloads import SC_POS, cubic_cell
+    n = (32, 8, 8)
+    pbc = (1, 1, 1) if fam == "fft" else (0, 0, 0)
+    s = sx.SpinSystem(n, pbc, cubic_cell(), SC_POS, [1.0])
+    s.add_shell_exchange(1, 1.0)
+    s.plan(fam, "fp32")
+    ties = [1 + 2.0 ** -24, -(0.5 + 2.0 ** -25), 0.75 + 2.0 ** -25]   # halfway between FP32 neighbours
+    away = [1 + 2.0 ** -23, -(0.5 + 2.0 ** -24), 0.75 + 2.0 ** -24]   # their larger-magnitude neighbours
+    plain = [0.3, -0.6, 0.7]
+    for comps, rounded in ((ties, away), (plain, plain)):
+        S = torch.zeros(3, 1, n[2], n[1], n[0], dtype=torch.float64, device="cuda")
+        S[:, 0, 4, 4, 10] = torch.tensor(comps, dtype=torch.float64)
+        b = s.field(S, dtype=torch.float32)
+        want = torch.tensor(rounded, dtype=torch.float64).float().cuda()
+        if fam == "stencil":  # sums of exact FP32 products with zeros: the rounded spin itself
+            for z, y, x in [(4, 4, 9), (4, 4, 11), (4, 3, 10), (4, 5, 10), (3, 4, 10), (5, 4, 10)]:
+                assert torch.equal(b[:, 0, z, y, x], want), (comps, (z, y, x))
+        else:  # transforms in FP32 round further: within a few FP32 ulps of the rounded spin
+            for z, y, x in [(4, 4, 9), (4, 4, 11)]:
+                assert torch.allclose(b[:, 0, z, y, x], want, atol=2e-6, rtol=0)
