@@ -47,8 +47,10 @@ def pair(name, n, dipolar, **override):
     return s, m, w
 
 
+# the last case has z lines of 1024 points: its z pass holds four lines of three channels (111 KB) and runs
+# with 512 threads per CTA
 CASES = [("sc_j123_dmi", (16, 8, 4), False), ("sc_j123_dmi", (8, 8, 8), True), ("bcc_4shell", (8, 4, 8), False),
-         ("bcc_4shell", (4, 8, 4), True), ("sc_nn", (32, 1, 2), True)]
+         ("bcc_4shell", (4, 8, 4), True), ("sc_nn", (32, 1, 2), True), ("sc_j123_dmi", (8, 4, 1024), False)]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -70,7 +72,7 @@ def test_fft_field_and_energy(prec, case):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", [0, 1, 3])
+@pytest.mark.parametrize("case", [0, 1, 3, 5])
 def test_fft_heun(prec, case):
     name, n, dip = CASES[case]
     s, m, w = pair(name, n, dip)
