@@ -43,7 +43,7 @@ EXECUTED_BYTES_TWO_PASS = 120
 EXECUTED_BYTES_TWO_PASS_THERMAL = 144
 # FP64 operations per spin-step of the state update (x = S + d: 3 additions; S' = x + x t: 3 fused
 # multiply-adds; |x|^2 - 1 and t run in 64-bit fixed point on the integer pipe), and GB300's FP64 rate
-# measured by the pipe-rate probe (profiles/gb300_pipe_rates.md: 503 G FP64 FMA/s at 2070 MHz)
+# measured by the pipe-rate GPU test (tests/test_gpu_pipe_rates.py: 503 G FP64 FMA/s at 2070 MHz)
 FP64_OPS_PER_SPIN_STEP = 6
 FP64_OPS_PER_S = 503e9
 # spin fields larger than this are generated on the device (numpy would take minutes at 1e9 spins)
@@ -225,13 +225,13 @@ def run_reference(args):
 
 
 # DRAM bytes per spin-step of the Heun step measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum of both
-# two-pass launches of one step, profiles/heun_bench_sc_j123_dmi_1024.md), keyed by (workload, scheme, launch
+# two-pass launches of one step, from the one-pass ncu launch list of the bench command), keyed by (workload, scheme, launch
 # shape, plane staging, z chunk); reported as roofline.traffic when the bench runs that shape
 MEASURED_TRAFFIC = {
     ("sc_j123_dmi_1024", "two_pass", 0, 0, 171): (147.6, "ncu of the 1024^3 bench step, z chunk 171, site-by-site "
-                                                         "plane copies (profiles/heun_bench_sc_j123_dmi_1024.md)"),
+                                                         "plane copies, one-pass launch list of this bench"),
     ("sc_j123_dmi_1024", "two_pass", 0, 0, 512): (152.7, "ncu of the 1024^3 bench step, z chunk 512, site-by-site "
-                                                         "plane copies (profiles/heun_bench_sc_j123_dmi_1024.md)"),
+                                                         "plane copies, one-pass launch list of this bench"),
 }
 
 
@@ -361,7 +361,7 @@ def run_ours(args):
         cap = FP64_OPS_PER_S / FP64_OPS_PER_SPIN_STEP
         hbm_cap = hbm * 1e9 / BYTES_PER_SPIN_STEP
         roof["alu"] = {"bound": "fp64", "ops_per_unit": FP64_OPS_PER_SPIN_STEP, "peak_ops_per_s": FP64_OPS_PER_S,
-                       "peak_kind": "measured (pipe-rate probe, profiles/gb300_pipe_rates.md)",
+                       "peak_kind": "measured (pipe-rate GPU test: dependent FP64 FMA chains on every SM)",
                        "achieved_ops_per_s": rate * FP64_OPS_PER_SPIN_STEP, "frac": rate / cap,
                        "cap_units_per_s": cap}
         roof["binds"] = "fp64" if cap < hbm_cap else "hbm"
@@ -390,7 +390,7 @@ def run_ours(args):
 
 # ------------------------------------------------------------------------------------------ profiling drivers
 # `python bench.py --profile KIND ARGS...` runs one of the workloads below a few times and prints a JSON line;
-# the commands in profiles/*.md run these drivers (alone for CUDA-event timings, under ncu for captures).
+# the ncu summaries run these drivers (alone for CUDA-event timings, under ncu for captures).
 
 
 def _profile_step(argv):
