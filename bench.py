@@ -361,7 +361,7 @@ def run_ours(args):
         cap = FP64_OPS_PER_S / FP64_OPS_PER_SPIN_STEP
         hbm_cap = hbm * 1e9 / BYTES_PER_SPIN_STEP
         roof["alu"] = {"bound": "fp64", "ops_per_unit": FP64_OPS_PER_SPIN_STEP, "peak_ops_per_s": FP64_OPS_PER_S,
-                       "peak_kind": "measured (pipe-rate GPU test: dependent FP64 FMA chains on every SM)",
+                       "peak_kind": "measured (pipe-rate GPU test: independent FP64 FMA chains on every SM)",
                        "achieved_ops_per_s": rate * FP64_OPS_PER_SPIN_STEP, "frac": rate / cap,
                        "cap_units_per_s": cap}
         roof["binds"] = "fp64" if cap < hbm_cap else "hbm"
