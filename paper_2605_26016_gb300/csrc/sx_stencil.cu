@@ -36,6 +36,7 @@
 #include "sx_device.cuh"
 #include "sx_internal.h"
 #include "sx_noise.cuh"
+#include "sx_schedule.h"
 
 namespace sx {
 
@@ -1084,9 +1085,9 @@ __global__ void __launch_bounds__(GF<Family<FID>>::NT, Family<FID>::MINB)
 
 // ------------------------------------------------------------------ overlapped two-pass step
 
-// Codes of the overlapped step's work units: idx = chunk * ncol + column (column = cy * ncx + cx of the
-// 32 x BY tiles, chunk = z / tz), plus kUnitCorr for a corrector unit.
-constexpr int kUnitCorr = 1 << 30;
+// Codes of the overlapped step's work units (sx_schedule.h): idx = chunk * ncol + column (column =
+// cy * ncx + cx of the 32 x BY tiles, chunk = z / tz), plus kUnitCorr for a corrector unit.
+using sched::kUnitCorr;
 
 // One two-pass Heun step in a single launch whose CTAs take predictor and corrector units from a queue
 // (`order`, built on the host): the predictor is issue-bound and the corrector bound by DRAM and the
@@ -2008,19 +2009,6 @@ cudaError_t stencil_heun_host(const sx_ctx *c, double *S_host, double *dA, doubl
   const bool pz = c->geo.pz != 0;
   const long long plane = (long long)c->geo.nx * c->geo.ny, subvol = plane * nz, nsite = c->geo.nsite;
   const int nsub = c->lat.nsub;
-  // the chunks whose planes chunk z needs (itself and its neighbours), as indices 0 .. K - 1
-  auto neighbours = [&](int z, int out[3]) {
-    int n = 0;
-    for (int d = -1; d <= 1; ++d) {
-      int q = z + d;
-      if (q < 0 || q >= K) {
-        if (!pz) continue;
-        q = (q + K) % K;
-      }
-      out[n++] = q;
-    }
-    return n;
-  };
   auto copy_chunk = [&](double *dev, int z, bool up, cudaStream_t cs) {
     const long long z0 = (long long)z * tzh, len = std::min<long long>(tzh, nz - z0);
     cudaError_t e = cudaSuccess;
@@ -2050,44 +2038,21 @@ cudaError_t stencil_heun_host(const sx_ctx *c, double *S_host, double *dA, doubl
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
     StencilArgs a = heun_args(c, h, step0 + (uint64_t)k);
     a.tz = tzh;
-    const bool first = k == 0, last = k == nsteps - 1;
-    // predictor chunks in the order their inputs arrive (uploads run in chunk order)
-    std::vector<int> order(K), need(K);
-    for (int z = 0; z < K; ++z) {
-      int nb[3];
-      const int n = neighbours(z, nb);
-      need[z] = *std::max_element(nb, nb + n);
-      order[z] = z;
-    }
-    if (first) std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return need[x] < need[y]; });
-    std::vector<char> pred_done(K, 0), corr_done(K, 0);
-    auto corr = [&](int z) {
-      cudaError_t r = pass_chunk(sp, a, src, dst, PASS_CORR, z, st);
-      corr_done[z] = 1;
-      if (r == cudaSuccess && last) {
-        r = cudaEventRecord(ev[K + z], st);
-        if (r == cudaSuccess) r = cudaStreamWaitEvent(sout, ev[K + z], 0);
-        if (r == cudaSuccess) r = copy_chunk(dst, z, false, sout);
+    const bool last = k == nsteps - 1;
+    for (const sched::ChunkOp &op : sched::host_step_ops(K, pz, k == 0, last)) {
+      if (e != cudaSuccess) break;
+      if (!op.corr) {
+        if (op.wait >= 0) e = cudaStreamWaitEvent(st, ev[op.wait], 0);
+        if (e == cudaSuccess) e = pass_chunk(sp, a, src, dst, PASS_PRED, op.z, st);
+        continue;
       }
-      return r;
-    };
-    for (int i = 0; i < K && e == cudaSuccess; ++i) {
-      const int z = order[i];
-      if (first) e = cudaStreamWaitEvent(st, ev[need[z]], 0);
-      if (e == cudaSuccess) e = pass_chunk(sp, a, src, dst, PASS_PRED, z, st);
-      pred_done[z] = 1;
-      // corrector chunks whose S~ halo is complete, as early as possible in the last step
-      for (int y = 0; y < K && e == cudaSuccess && last; ++y) {
-        if (corr_done[y]) continue;
-        int nb[3];
-        const int n = neighbours(y, nb);
-        bool ready = true;
-        for (int j = 0; j < n; ++j) ready = ready && pred_done[nb[j]];
-        if (ready) e = corr(y);
+      e = pass_chunk(sp, a, src, dst, PASS_CORR, op.z, st);
+      if (e == cudaSuccess && last) {  // this corrector chunk goes down while the rest of the step runs
+        e = cudaEventRecord(ev[K + op.z], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ev[K + op.z], 0);
+        if (e == cudaSuccess) e = copy_chunk(dst, op.z, false, sout);
       }
     }
-    for (int y = 0; y < K && e == cudaSuccess; ++y)
-      if (!corr_done[y]) e = corr(y);
     std::swap(src, dst);
   }
   if (e == cudaSuccess) e = cudaEventRecord(done, sout);
@@ -2423,61 +2388,6 @@ std::vector<int> chunk_lengths(int nz, int around) {
   return out;
 }
 
-// Queue of the overlapped step (k_heun_overlap).  Predictor units chunk by chunk (on a periodic z axis
-// the last chunk first: chunk 0's corrector reads it), columns in order.  Corrector units chunk by
-// chunk, tile rows 1 .. ncy - 1 before row 0 (whose periodic y halo is the last row), each queued
-// one-for-one with the predictor stream once `lag` more predictor units have been queued after the
-// last predictor unit it depends on (every dependency is queued before the unit itself).
-std::vector<int> overlap_order(int ncx, int ncy, int nchunk, int px, int py, int pz, long long lag) {
-  const int ncol = ncx * ncy;
-  const long long P = (long long)nchunk * ncol;
-  std::vector<int> pred, corr;
-  std::vector<long long> pos(P), need;
-  pred.reserve(P);
-  corr.reserve(P);
-  need.reserve(P);
-  std::vector<int> zorder;
-  if (pz && nchunk > 1) zorder.push_back(nchunk - 1);
-  for (int z = 0; z < nchunk; ++z)
-    if (!(pz && nchunk > 1 && z == nchunk - 1)) zorder.push_back(z);
-  for (int z : zorder)
-    for (int col = 0; col < ncol; ++col) {
-      pos[(long long)z * ncol + col] = (long long)pred.size();
-      pred.push_back(z * ncol + col);
-    }
-  auto wrap = [](int c, int n, int per, bool &ok) {
-    if (c >= 0 && c < n) return c;
-    if (!per) {
-      ok = false;
-      return 0;
-    }
-    return ((c % n) + n) % n;
-  };
-  for (int z = 0; z < nchunk; ++z)
-    for (int r = 0; r < ncy; ++r) {
-      const int cy = (r + 1) % ncy;
-      for (int cx = 0; cx < ncx; ++cx) {
-        long long nd = 0;
-        for (int t = 0; t < 27; ++t) {
-          bool ok = true;
-          const int zz = wrap(z + t / 9 - 1, nchunk, pz, ok), yy = wrap(cy + (t / 3) % 3 - 1, ncy, py, ok),
-                    xx = wrap(cx + t % 3 - 1, ncx, px, ok);
-          if (ok) nd = std::max(nd, pos[(long long)zz * ncol + yy * ncx + xx]);
-        }
-        corr.push_back((z * ncol + cy * ncx + cx) | kUnitCorr);
-        need.push_back(nd);
-      }
-    }
-  std::vector<int> out;
-  out.reserve(2 * P);
-  long long pi = 0, ci = 0;
-  while (pi < P || ci < P) {
-    if (pi < P) out.push_back(pred[pi++]);
-    if (ci < P && (pi >= P || need[ci] + lag < pi)) out.push_back(corr[ci++]);
-  }
-  return out;
-}
-
 void overlap_free(StencilPlan &sp) {
   cudaFree(sp.d_order);
   cudaFree(sp.d_done);
@@ -2518,7 +2428,7 @@ int overlap_setup(sx_ctx *c, StencilPlan &sp, int tz) {
   const int BY = family_by(sp.family);
   const int ncx = (c->geo.nx + 31) / 32, ncy = (c->geo.ny + BY - 1) / BY, nchunk = (c->geo.nz + tz - 1) / tz;
   const int grid = occ * sp.nsm;
-  const std::vector<int> order = overlap_order(ncx, ncy, nchunk, c->geo.px, c->geo.py, c->geo.pz, grid);
+  const std::vector<int> order = sched::overlap_order(ncx, ncy, nchunk, c->geo.px, c->geo.py, c->geo.pz, grid);
   const int ndone = ncx * ncy * nchunk;
   if (cudaMalloc(&sp.d_order, order.size() * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&sp.d_done, (size_t)ndone * sizeof(int)) != cudaSuccess ||
