@@ -98,7 +98,7 @@ int main(void) {
     if (r) { printf("queue bench %d: %d\n", b, r); return 1; }
     ++n;
   }
-  for (int K = 1; K <= 20; ++K)
+  for (int K : {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 20, 31, 32, 63, 64})
     for (int pz = 0; pz < 2; ++pz)
       for (int f = 0; f < 2; ++f)
         for (int l = 0; l < 2; ++l) {
@@ -107,7 +107,7 @@ int main(void) {
           ++n;
         }
   // the first and last step of a one-step call overlap: some corrector comes before the last predictor
-  const std::vector<ChunkOp> one = host_step_ops(16, true, true, true);
+  const std::vector<ChunkOp> one = host_step_ops(64, true, true, true);
   int first_corr = -1, last_pred = -1;
   for (int i = 0; i < (int)one.size(); ++i) {
     if (one[i].corr && first_corr < 0) first_corr = i;
