@@ -1566,87 +1566,12 @@ cudaError_t launch_persistent(const StencilPlan &sp, const StencilArgs &a, doubl
                                      dim3(32, GF<Family<FID>>::TYT), args, g::SMEM, st);
 }
 
-// Balanced schedule of a one-image pass over `slots` resident CTAs: the column-plane
-// units u = column * nz + z are cut into contiguous ranges, one per CTA, so that the
-// largest cost (planes + 2R warm-up planes per column segment) is as small as the
-// greedy packing allows.
-// Same packing over several replicas whose units follow each other (replica r: ncol[r]
-// columns of nz[r] planes each, starting at global unit off[r]).
 std::vector<int2> balanced_schedule_multi(const std::vector<long long> &ncol, const std::vector<int> &nz, int R,
                                           long long slots) {
-  const int nr = (int)ncol.size();
-  std::vector<long long> off(nr + 1, 0);
-  for (int r = 0; r < nr; ++r) off[r + 1] = off[r] + ncol[r] * nz[r];
-  const long long U = off[nr], w = 2LL * R;
-  long long colsum = 0;
-  for (int r = 0; r < nr; ++r) colsum += ncol[r];
-  auto pack = [&](long long B, std::vector<int2> *out) {
-    long long u = 0, n = 0;
-    int r = 0;
-    while (u < U) {
-      const long long u0 = u;
-      long long cost = 0;
-      while (u < U) {
-        while (u >= off[r + 1]) ++r;
-        const long long avail = nz[r] - (u - off[r]) % nz[r];
-        if (cost + w + 1 > B) break;
-        const long long t = std::min(avail, B - cost - w);
-        cost += w + t;
-        u += t;
-        if (t < avail) break;
-      }
-      if (out) out->push_back(make_int2((int)u0, (int)(u - u0)));
-      ++n;
-    }
-    return n;
-  };
-  long long lo = std::max<long long>(w + 1, (U + slots - 1) / slots + w);
-  long long hi = std::max(lo, U + w * colsum);  // one CTA taking everything always fits
-  while (lo < hi) {
-    const long long mid = (lo + hi) / 2;
-    if (pack(mid, nullptr) <= slots)
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
-  std::vector<int2> out;
-  pack(lo, &out);
-  return out;
+  return sched::balanced_schedule_multi<int2>(ncol, nz, R, slots);
 }
-
 std::vector<int2> balanced_schedule(long long ncol, int nz, int R, long long slots) {
-  const long long U = ncol * nz, w = 2LL * R;
-  auto pack = [&](long long B, std::vector<int2> *out) {
-    long long u = 0, n = 0;
-    while (u < U) {
-      const long long u0 = u;
-      long long cost = 0;
-      while (u < U) {
-        const long long avail = nz - u % nz;
-        if (cost + w + 1 > B) break;
-        const long long t = std::min(avail, B - cost - w);
-        cost += w + t;
-        u += t;
-        if (t < avail) break;
-      }
-      if (out) out->push_back(make_int2((int)u0, (int)(u - u0)));
-      ++n;
-    }
-    return n;
-  };
-  // hi: whole columns, ceil(ncol / slots) of them per CTA, always fits
-  long long lo = std::max<long long>(w + 1, (U + slots - 1) / slots + w);
-  long long hi = std::max(lo, ((ncol + slots - 1) / slots) * (nz + w));
-  while (lo < hi) {
-    const long long mid = (lo + hi) / 2;
-    if (pack(mid, nullptr) <= slots)
-      hi = mid;
-    else
-      lo = mid + 1;
-  }
-  std::vector<int2> out;
-  pack(lo, &out);
-  return out;
+  return sched::balanced_schedule<int2>(ncol, nz, R, slots);
 }
 
 // z chunk per CTA: each chunk pays 4R warm-up planes, and the grid runs in

@@ -1,6 +1,8 @@
 """Work orders of the stencil backend's multi-unit launches (csrc/sx_schedule.h), compiled for the host.
 
-The overlapped two-pass launch takes predictor and corrector units from one queue, and the pipelined
+The balanced schedule of small lattices cuts the column-plane units into one contiguous range per
+resident CTA; it must cover every unit exactly once within the CTA slots.  The overlapped two-pass
+launch takes predictor and corrector units from one queue, and the pipelined
 host-array step issues predictor and corrector passes over z chunks while the uploads and downloads of
 other chunks are in flight.  Both are correct only if every unit appears once and every corrector unit
 comes after the predictor units of its S~ halo (the 3 x 3 neighbouring columns in the chunks z - 1 ..
@@ -82,8 +84,66 @@ static int check_host(int K, bool pz, bool first, bool last) {
   return 0;
 }
 
+struct Rg {
+  int x, y;
+};
+
+// ranges tile [0, U) in order, at most `slots` of them, each costing (planes + w per column segment,
+// columns of nz units) no more than `bound`
+static int check_ranges(const std::vector<Rg> &rs, const std::vector<long long> &ncol, const std::vector<int> &nz,
+                        long long slots, long long w, long long bound) {
+  std::vector<long long> off(ncol.size() + 1, 0);
+  for (size_t r = 0; r < ncol.size(); ++r) off[r + 1] = off[r] + ncol[r] * nz[r];
+  const long long U = off.back();
+  if ((long long)rs.size() > slots) return 21;
+  long long u = 0;
+  for (const Rg &g : rs) {
+    if (g.x != u || g.y < 1) return 22;
+    long long cost = 0, v = g.x;
+    size_t r = 0;
+    while (v < (long long)g.x + g.y) {
+      while (v >= off[r + 1]) ++r;
+      const long long end = std::min<long long>((long long)g.x + g.y, off[r] + ((v - off[r]) / nz[r] + 1) * nz[r]);
+      cost += w + (end - v);  // one column segment
+      v = end;
+    }
+    if (cost > bound) return 23;
+    u += g.y;
+  }
+  return u == U ? 0 : 24;
+}
+
 int main(void) {
   long n = 0;
+  for (int R = 1; R <= 2; ++R)
+    for (long long ncol : {1LL, 3LL, 32LL, 100LL, 151LL})
+      for (int nz : {1, 2, 5, 17, 64, 128})
+        for (long long slots : {1LL, 7LL, 152LL, 304LL}) {
+          const long long w = 2 * R;
+          const std::vector<Rg> rs = balanced_schedule<Rg>(ncol, nz, R, slots);
+          const long long hi = std::max<long long>(std::max<long long>(w + 1, (ncol * nz + slots - 1) / slots + w),
+                                                   ((ncol + slots - 1) / slots) * (nz + w));
+          const int r = check_ranges(rs, {ncol}, {nz}, slots, w, hi);
+          if (r) { printf("balanced %lld %d %d %lld: %d\n", ncol, nz, R, slots, r); return 1; }
+          ++n;
+        }
+  {  // replicas of different sizes, the units of one after the other's
+    const std::vector<long long> ncol = {4, 12, 1, 30};
+    const std::vector<int> nz = {24, 48, 7, 96};
+    for (long long slots : {1LL, 5LL, 152LL}) {
+      const std::vector<Rg> rs = balanced_schedule_multi<Rg>(ncol, nz, 2, slots);
+      long long U = 0, cols = 0;
+      for (size_t r = 0; r < ncol.size(); ++r) { U += ncol[r] * nz[r]; cols += ncol[r]; }
+      const int r = check_ranges(rs, ncol, nz, slots, 4, U + 4 * cols);
+      if (r) { printf("multi %lld: %d\n", slots, r); return 1; }
+      ++n;
+    }
+  }
+  // the point of the schedule: 32 columns of 128 planes over 152 CTAs cost far less than whole columns
+  {
+    const std::vector<Rg> rs = balanced_schedule<Rg>(32, 128, 2, 152);
+    if (check_ranges(rs, {32}, {128}, 152, 4, 4 * 4 + 128 * 32 / 152 + 1) != 0) { printf("not balanced\n"); return 1; }
+  }
   for (int ncx = 1; ncx <= 4; ++ncx)
     for (int ncy = 1; ncy <= 4; ++ncy)
       for (int K = 1; K <= 5; ++K)
