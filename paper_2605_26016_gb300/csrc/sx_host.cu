@@ -235,10 +235,11 @@ int check_ready(const sx_ctx *c) {
   return SX_OK;
 }
 
-bool overlaps(const void *p, const void *q, size_t bytes) {
+bool overlaps(const void *p, size_t pbytes, const void *q, size_t qbytes) {
   const char *a = (const char *)p, *b = (const char *)q;
-  return a < b + bytes && b < a + bytes;
+  return a < b + qbytes && b < a + pbytes;
 }
+bool overlaps(const void *p, const void *q, size_t bytes) { return overlaps(p, bytes, q, bytes); }
 
 int check_spin_ptr(const void *p, const char *name) {
   if (!p) return set_error(SX_ERR_ARG, std::string(name) + " is null");
@@ -875,7 +876,8 @@ int sx_field(sx_ctx *c, const double *S, void *b, int out_prec, void *stream) {
   if (!b) return set_error(SX_ERR_ARG, "b is null");
   const size_t n3 = 3 * (size_t)c->geo.nsite;
   if (((uintptr_t)b) & (out_prec == SX_PREC_FP64 ? 7u : 3u)) return set_error(SX_ERR_ARG, "b is misaligned");
-  if (overlaps(S, b, n3 * sizeof(double))) return set_error(SX_ERR_ARG, "S and b overlap");
+  if (overlaps(S, n3 * sizeof(double), b, n3 * (out_prec == SX_PREC_FP64 ? sizeof(double) : sizeof(float))))
+    return set_error(SX_ERR_ARG, "S and b overlap");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (out_prec == SX_PREC_FP64) {

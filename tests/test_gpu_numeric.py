@@ -136,3 +136,21 @@ def test_fp32_field_rounds_spins_to_nearest_even(fam):
         else:  # transforms in FP32 round further: within a few FP32 ulps of the rounded spin
             for z, y, x in [(4, 4, 9), (4, 4, 11)]:
                 assert torch.allclose(b[:, 0, z, y, x], want, atol=2e-6, rtol=0)
+
+
+def test_fp32_field_may_sit_right_before_the_spins():
+    # an FP32 field is half as long as the FP64 spins: a field array that ends where S begins does not
+    # overlap it (one allocation, the field in its first 12 nsite bytes, S in the next 24 nsite bytes)
+    n = (16, 12, 10)
+    s, w = sx.system_from_workload("sc_j123_dmi", n)
+    s.plan("stencil", "fp32")
+    n3 = 3 * s.nsite
+    raw = torch.empty(n3 * 12, dtype=torch.uint8, device="cuda")
+    b = raw[: n3 * 4].view(torch.float32)
+    S = raw[n3 * 4:].view(torch.float64)
+    S.copy_(torch.from_numpy(random_spins(1, n, 4)).reshape(-1))
+    sx.sx_field(s.ctx, S, b, s.nsite)
+    ref = s.field(S.clone(), dtype=torch.float32).reshape(-1)
+    assert torch.equal(b, ref)
+    with pytest.raises(sx.SxError):  # one float of real overlap is still refused
+        sx.sx_field(s.ctx, S, raw[4: n3 * 4 + 4].view(torch.float32), s.nsite)
